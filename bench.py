@@ -1,0 +1,304 @@
+"""Benchmark: standalone MGCG solve K(x) u = f to a relative residual of 1e-8 on a 2048 x 1024 Q1
+plane-stress grid (4.2M DOFs, 9 levels), densities 10^U(-3,0) smoothed by a 5x5 box filter, load
+N(0,1) on the free DOFs, left edge clamped.  One step = Galerkin hierarchy build + PCG solve
+(Algorithm MG / Algorithm PCG), inputs resident in HBM.  Metric: free DOFs x CG iterations / s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+The headline is the mixed-precision solver (FP32 V-cycle, FP64 CG); the plain FP64 solver is
+reported beside it.  ``--impl reference`` times the CPU oracle (plain scipy MGCG) on a bounded
+sample of the same recipe.  Under torchrun every rank solves its own copy (replicas: the method
+has no exchange step on one grid) and rank 0 prints one JSON line.
+"""
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1606_06201_gb300 import workloads as W  # noqa: E402
+
+NX, NY, LEVELS, TOL = 2048, 1024, 9, 1e-8
+METRIC = "MGCG DOF·iterations/s at 1e-8 rel. residual (mixed: FP32 V-cycle, FP64 CG)"
+UNIT = "DOF·it/s"
+WORKLOAD = "mgcg_2d_q1_2048x1024_9lev_logunif_box5_normal_load"
+# FP64 CUDA-core peak: 152 SMs x 2 DFMA/clock x 2 flop x 2.07 GHz (probe on this part: 1.20 TF/s)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def oracle_mgcg_sample(nx, ny, levels, seconds=None, reps=1):
+    """Time the CPU oracle's MGCG (scipy sparse, Algorithm PCG + Algorithm MG) on the same recipe."""
+    from oracle import fe, mg
+    cfg = W.random_field_2d(nx, ny)
+    grid = fe.Grid(nx, ny)
+    fixed = cfg["fixed"].astype(bool)
+    free = fe.free_dofs(fixed)
+    total_t, total_work, runs = 0.0, 0.0, 0
+    while True:
+        t0 = time.perf_counter()
+        K = fe.assemble(grid, fe.element_stiffness(2), cfg["x"])[free][:, free].tocsr()
+        levs = mg.hierarchy(grid, fixed, K, levels)
+        _, it, _ = mg.pcg(K, cfg["f"][free], lambda r: mg.vcycle(levs, r, 2, 2, 0.6), tol=TOL)
+        total_t += time.perf_counter() - t0
+        total_work += free.size * it
+        runs += 1
+        if (seconds is None and runs >= reps) or (seconds is not None and total_t >= seconds):
+            break
+    return total_work / total_t, total_t, runs, free.size, it
+
+
+def reference_arm(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    nx, ny, lev = 512, 256, 7
+    for _ in range(args.warmup):
+        oracle_mgcg_sample(nx, ny, lev)
+    t0 = time.perf_counter()
+    work = 0.0
+    for _ in range(args.steps):
+        v, t, _, nfree, it = oracle_mgcg_sample(nx, ny, lev)
+        work += nfree * it
+    el = time.perf_counter() - t0
+    value = work / el
+    sample = "oracle MGCG (scipy sparse, FP64) on the same recipe at 512x256 (263,168 free DOFs, 7 levels), " \
+             "hierarchy build + PCG to 1e-8 per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "512x256"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["mixed", "fp64"], default=None,
+                    help="run one solver configuration only (for profiler launch lists); no JSON line")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_1606_06201_gb300 import build as B
+    if not os.path.exists(B.LIB):
+        B.build()
+    from paper_1606_06201_gb300 import topo
+
+    cfg = W.random_field_2d(NX, NY)
+    nfree = int(np.count_nonzero(cfg["fixed"] == 0))
+    x_d = torch.as_tensor(cfg["x"], device=dev)
+    f_d = torch.as_tensor(cfg["f"], device=dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def run(precision, steps, warmup, profile=False, host_io=False):
+        s = topo.Solver(NX, NY, fixed=cfg["fixed"], levels=LEVELS, precision=precision)
+        u_d = torch.zeros_like(f_d)
+        if host_io:
+            x_h = torch.as_tensor(cfg["x"]).pin_memory()
+            f_h = torch.as_tensor(cfg["f"]).pin_memory()
+            u_h = torch.empty_like(f_h).pin_memory()
+            x_in, f_in = torch.empty_like(x_d), torch.empty_like(f_d)
+
+        def step():
+            if host_io:
+                x_in.copy_(x_h, non_blocking=True)
+                f_in.copy_(f_h, non_blocking=True)
+                s.set_density(x_in)
+                _, info = s.solve(f_in, u_d, tol=TOL)
+                u_h.copy_(u_d, non_blocking=True)
+            else:
+                s.set_density(x_d)
+                _, info = s.solve(f_d, u_d, tol=TOL)
+            return info
+
+        for _ in range(warmup):
+            step()
+        if profile:
+            s.set_profiling(True)
+            step()  # capture the instrumented graph outside the timed region
+            s.set_profiling(True)
+        barrier()
+        l0 = s.launch_count
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        iters = 0
+        res = 0.0
+        e0.record()
+        for _ in range(steps):
+            info = step()
+            iters += info.iterations
+            res = max(res, info.rel_residual)
+        e1.record()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        launches = s.launch_count - l0
+        prof = s.profile() if profile else None
+        s.close()
+        return dict(ms=ms, iters=iters, res=res, launches=launches, prof=prof)
+
+    if args.only:
+        r = run(topo.MIXED if args.only == "mixed" else topo.FP64, args.steps, args.warmup)
+        print("only=%s ms_per_step=%.3f iterations=%d launches=%d" % (
+            args.only, r["ms"] / args.steps, r["iters"], r["launches"]), flush=True)
+        return 0
+    # warm-up + timed steps: mixed (headline, with live operator timing), FP64, end-to-end
+    with ClockSampler(dev.index) as clk:
+        mixed = run(topo.MIXED, args.steps, args.warmup, profile=True)
+        fp64 = run(topo.FP64, args.steps, args.warmup)
+        e2e = run(topo.MIXED, args.steps, args.warmup, host_io=True)
+
+    def gather_max(v):
+        if ws == 1:
+            return v
+        t = torch.tensor([v], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    ms_mixed = gather_max(mixed["ms"])
+    ms_fp64 = gather_max(fp64["ms"])
+    ms_e2e = gather_max(e2e["ms"])
+    value = ws * nfree * mixed["iters"] / (ms_mixed * 1e-3)
+    line = None
+    if rank == 0:
+        m, n = NX * NY, cfg["f"].size
+        flop_per_launch = 144.0 * m + 2.0 * n
+        op_ms, op_cnt = mixed["prof"]
+        op_avg_ms = op_ms / op_cnt if op_cnt else float("nan")
+        achieved = flop_per_launch / (op_avg_ms * 1e-3) / 1e12
+        roof = {"kernel": "k_apply_dot_fine<2> (outer FP64 operator q = K(x) p with p^T q)",
+                "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                "algorithmic_flop_per_launch": flop_per_launch,
+                "algorithmic_bytes_per_launch": 8.0 * m + 16.0 * n + 1.0 * n,
+                "avg_launch_ms": op_avg_ms, "launches_timed": op_cnt}
+        cpu = None
+        if not args.no_cpu_baseline:
+            v, t, runs, nf, it = oracle_mgcg_sample(1024, 512, 8, seconds=10.0)
+            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "oracle MGCG (scipy sparse, FP64, single thread) on the same recipe at "
+                             "1024x512 (%d free DOFs, 8 levels), %d run(s), %.1f s" % (nf, runs, t)}
+        bi = 8 * (m + n)
+        bo = 8 * n
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycle + f64 CG",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "levels": LEVELS, "tol": TOL,
+                       "free_dofs": nfree, "smoother": "damped Jacobi omega=0.6 nu1=nu2=2",
+                       "step": "hierarchy build + PCG solve", "parallelism": "replicas" if ws > 1 else "1 GPU",
+                       "l2": "working set > L2 (vectors 33.6 MB each, ~0.5 GB resident)"},
+            "iterations_per_solve": mixed["iters"] / args.steps, "final_rel_residual": mixed["res"],
+            "fp64": {"value": ws * nfree * fp64["iters"] / (ms_fp64 * 1e-3), "unit": UNIT,
+                     "ms_per_step": ms_fp64 / args.steps, "iterations_per_solve": fp64["iters"] / args.steps},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": ws * nfree * e2e["iters"] / (ms_e2e * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+            "gpu_launches": mixed["launches"],
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,500 @@
+// Finite-element kernels on structured grids: the operator K(x) v = sum_e x_e L_e^T K0 L_e v on
+// the finest level (matrix-free, element by element: Eq. (to), Sec. 7), the same with assembled
+// Galerkin element matrices on coarse levels (Sec. 5.1), damped Jacobi sweeps (the smoother opt()
+// of Algorithm MG), the bilinear/trilinear transfers of Sec. 7 (prolongation stencil
+// [1/4 1/2 1/4; 1/2 1 1/2; 1/4 1/2 1/4], restriction = transpose) and element energies.
+//
+// All operators are gather formulations: one thread owns one node and sums the contributions of
+// the 4 (2D) or 8 (3D) elements around it in a fixed order, so results are deterministic and no
+// atomics are used.  Fixed DOFs are masked: their outputs are 0.
+#include "topo_internal.cuh"
+
+namespace topo {
+
+namespace {
+
+template <int DIM>
+struct Elem {
+  static constexpr int NN = DIM == 2 ? 4 : 8;       // nodes per element
+  static constexpr int NE = NN * DIM;               // DOFs per element
+};
+
+// Local node offsets: counter-clockwise (0,0) (1,0) (1,1) (0,1), bottom face then top face.
+__device__ __forceinline__ int loc_ox(int a) { return ((a & 3) == 1 || (a & 3) == 2) ? 1 : 0; }
+__device__ __forceinline__ int loc_oy(int a) { return ((a & 3) >= 2) ? 1 : 0; }
+__device__ __forceinline__ int loc_oz(int a) { return a >> 2; }
+__device__ __forceinline__ int loc_of(int lx, int ly, int lz) {
+  return (ly ? (lx ? 2 : 3) : (lx ? 1 : 0)) + 4 * lz;
+}
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+// Sum over the elements around node (i,j,k) of rows (loc*DIM + c) of the element matrix times
+// the element's DOF values.  FINE: element matrix x_e K0; otherwise Ae[e].
+template <int DIM, typename T, bool FINE>
+__device__ __forceinline__ void node_apply(const Dims& d, int i, int j, int k,
+                                           const T* __restrict__ K0, const T* __restrict__ x,
+                                           const T* __restrict__ Ae, const T* __restrict__ v,
+                                           T acc[DIM]) {
+  constexpr int NN = Elem<DIM>::NN, NE = Elem<DIM>::NE;
+  const int nnx = d.nx + 1, nny = d.ny + 1;
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+#pragma unroll 1
+  for (int s = 0; s < NN; ++s) {
+    const int dx = s & 1, dy = (s >> 1) & 1, dz = (DIM == 3) ? (s >> 2) : 0;
+    const int ex = i - 1 + dx, ey = j - 1 + dy, ez = (DIM == 3) ? k - 1 + dz : 0;
+    if (ex < 0 || ex >= d.nx || ey < 0 || ey >= d.ny) continue;
+    if (DIM == 3 && (ez < 0 || ez >= d.nz)) continue;
+    const int loc = loc_of(1 - dx, 1 - dy, DIM == 3 ? 1 - dz : 0);
+    const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
+    T ve[NE];
+#pragma unroll
+    for (int a = 0; a < NN; ++a) {
+      const long long nid = (ex + loc_ox(a)) + (long long)nnx * ((ey + loc_oy(a)) +
+                                                                 (long long)nny * (ez + loc_oz(a)));
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) ve[a * DIM + c] = ldg(v + DIM * nid + c);
+    }
+    const T* A = FINE ? K0 : Ae + e * (NE * NE);
+    const T scale = FINE ? ldg(x + e) : T(1);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      const T* row = A + (loc * DIM + c) * NE;
+      T t = T(0);
+#pragma unroll
+      for (int q = 0; q < NE; ++q) t = fma(ldg(row + q), ve[q], t);
+      acc[c] = fma(scale, t, acc[c]);
+    }
+  }
+}
+
+// mode 0: y = A v;  1: y = b - A v;  2: y = v + omega invd (b - A v);  3: y = omega invd b.
+template <int DIM, typename T, int MODE, bool FINE>
+__global__ void __launch_bounds__(kThreads) k_apply(Dims d, const T* __restrict__ K0,
+                                                    const T* __restrict__ x,
+                                                    const T* __restrict__ Ae,
+                                                    const T* __restrict__ v,
+                                                    const T* __restrict__ b, T* __restrict__ y,
+                                                    const T* __restrict__ invd, T omega,
+                                                    const uint8_t* __restrict__ fixed,
+                                                    const CgScalars* __restrict__ sc) {
+  const int rhs = blockIdx.y;
+  if (sc && sc[rhs].done) return;
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nodes = d.nodes();
+  if (node >= nodes) return;
+  const long long n = nodes * DIM;
+  const int nnx = d.nx + 1, nny = d.ny + 1;
+  const int i = (int)(node % nnx);
+  const int j = (int)((node / nnx) % nny);
+  const int k = (DIM == 3) ? (int)(node / ((long long)nnx * nny)) : 0;
+  v += rhs * n;
+  b += rhs * n;
+  y += rhs * n;
+  T acc[DIM];
+  if (MODE != 3) node_apply<DIM, T, FINE>(d, i, j, k, K0, x, Ae, v, acc);
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const long long id = DIM * node + c;
+    T out;
+    if (fixed[id]) {
+      out = T(0);
+    } else if (MODE == 0) {
+      out = acc[c];
+    } else if (MODE == 1) {
+      out = b[id] - acc[c];
+    } else if (MODE == 2) {
+      out = v[id] + omega * invd[id] * (b[id] - acc[c]);
+    } else {
+      out = omega * invd[id] * b[id];
+    }
+    y[id] = out;
+  }
+}
+
+template <int DIM, typename T, int MODE>
+void apply_dispatch(const Dims& d, const T* K0, const T* x, const T* Ae, const T* v, const T* b,
+                    T* y, const T* invd, T omega, const uint8_t* fixed, int nrhs,
+                    const CgScalars* sc, cudaStream_t st) {
+  dim3 grid(blocks_for(d.nodes()), nrhs);
+  if (x)
+    k_apply<DIM, T, MODE, true><<<grid, kThreads, 0, st>>>(d, K0, x, Ae, v, b, y, invd, omega,
+                                                           fixed, sc);
+  else
+    k_apply<DIM, T, MODE, false><<<grid, kThreads, 0, st>>>(d, K0, x, Ae, v, b, y, invd, omega,
+                                                            fixed, sc);
+}
+
+// Block sum of one double per thread (deterministic tree), result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double warp_sums[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) warp_sums[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (wid == 0) {
+    s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  return s;
+}
+
+// q = A p (FP64, finest level) with the partial sums of p^T q; the last block to finish adds the
+// partials in block order and forms alpha = r^T y / p^T A p (Algorithm PCG).
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_apply_dot_fine(Dims d, const double* __restrict__ K0,
+                                                             const double* __restrict__ x,
+                                                             const double* __restrict__ v,
+                                                             double* __restrict__ y,
+                                                             const uint8_t* __restrict__ fixed,
+                                                             double* partials, unsigned* counters,
+                                                             CgScalars* sc) {
+  const int rhs = blockIdx.y;
+  if (sc[rhs].done) return;
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nodes = d.nodes();
+  const long long n = nodes * DIM;
+  v += rhs * n;
+  y += rhs * n;
+  double part = 0.0;
+  if (node < nodes) {
+    const int nnx = d.nx + 1, nny = d.ny + 1;
+    const int i = (int)(node % nnx);
+    const int j = (int)((node / nnx) % nny);
+    const int k = (DIM == 3) ? (int)(node / ((long long)nnx * nny)) : 0;
+    double acc[DIM];
+    node_apply<DIM, double, true>(d, i, j, k, K0, x, nullptr, v, acc);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      const long long id = DIM * node + c;
+      const double out = fixed[id] ? 0.0 : acc[c];
+      y[id] = out;
+      part = fma(v[id], out, part);
+    }
+  }
+  const double bs = block_sum(part);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[(long long)rhs * gridDim.x + blockIdx.x] = bs;
+    __threadfence();
+    last = (atomicAdd(&counters[rhs], 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  double s = 0.0;
+  for (unsigned t = threadIdx.x; t < gridDim.x; t += blockDim.x)
+    s += __ldcg(partials + (long long)rhs * gridDim.x + t);
+  s = block_sum(s);
+  if (threadIdx.x == 0) {
+    CgScalars& S = sc[rhs];
+    S.pq = s;
+    const double alpha = S.ry / s;
+    if (!(s > 0.0) || !isfinite(alpha)) {
+      S.status = TOPO_E_BREAKDOWN;
+      S.done = 1;
+      S.alpha = 0.0;
+    } else {
+      S.alpha = alpha;
+    }
+    counters[rhs] = 0;
+  }
+}
+
+// Restriction r_c = P^T r_f: each coarse node gathers the 3x3(x3) fine nodes around its
+// coincident fine node with weights prod_d w(offset), w(0) = 1, w(+-1) = 1/2.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(kThreads) k_restrict(Dims df, const T* __restrict__ rf,
+                                                       T* __restrict__ rc,
+                                                       const uint8_t* __restrict__ fixed_c,
+                                                       const CgScalars* __restrict__ sc) {
+  const int rhs = blockIdx.y;
+  if (sc && sc[rhs].done) return;
+  Dims dc{df.nx / 2, df.ny / 2, DIM == 3 ? df.nz / 2 : 1, DIM};
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nodes_c = dc.nodes();
+  if (node >= nodes_c) return;
+  const int cnx = dc.nx + 1, cny = dc.ny + 1;
+  const int I = (int)(node % cnx), J = (int)((node / cnx) % cny);
+  const int K = (DIM == 3) ? (int)(node / ((long long)cnx * cny)) : 0;
+  const int fnx = df.nx + 1, fny = df.ny + 1;
+  rf += rhs * df.dofs();
+  rc += rhs * dc.dofs();
+  T acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+  const int zlo = (DIM == 3) ? -1 : 0, zhi = (DIM == 3) ? 1 : 0;
+  for (int oz = zlo; oz <= zhi; ++oz) {
+    const int fk = 2 * K + oz;
+    if (DIM == 3 && (fk < 0 || fk > df.nz)) continue;
+    const T wz = (oz == 0) ? T(1) : T(0.5);
+    for (int oy = -1; oy <= 1; ++oy) {
+      const int fj = 2 * J + oy;
+      if (fj < 0 || fj > df.ny) continue;
+      const T wy = (oy == 0) ? wz : wz * T(0.5);
+      for (int ox = -1; ox <= 1; ++ox) {
+        const int fi = 2 * I + ox;
+        if (fi < 0 || fi > df.nx) continue;
+        const T w = (ox == 0) ? wy : wy * T(0.5);
+        const long long fid = fi + (long long)fnx * (fj + (long long)fny * (DIM == 3 ? fk : 0));
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) acc[c] = fma(w, rf[DIM * fid + c], acc[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const long long id = DIM * node + c;
+    rc[id] = fixed_c[id] ? T(0) : acc[c];
+  }
+}
+
+// Prolongation and correction z_f += P z_c (bilinear / trilinear interpolation).
+template <int DIM, typename T>
+__global__ void __launch_bounds__(kThreads) k_prolong_add(Dims df, const T* __restrict__ zc,
+                                                          T* __restrict__ zf,
+                                                          const uint8_t* __restrict__ fixed_f,
+                                                          const CgScalars* __restrict__ sc) {
+  const int rhs = blockIdx.y;
+  if (sc && sc[rhs].done) return;
+  Dims dc{df.nx / 2, df.ny / 2, DIM == 3 ? df.nz / 2 : 1, DIM};
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nodes_f = df.nodes();
+  if (node >= nodes_f) return;
+  const int fnx = df.nx + 1, fny = df.ny + 1;
+  const int i = (int)(node % fnx), j = (int)((node / fnx) % fny);
+  const int k = (DIM == 3) ? (int)(node / ((long long)fnx * fny)) : 0;
+  const int cnx = dc.nx + 1, cny = dc.ny + 1;
+  zc += rhs * dc.dofs();
+  zf += rhs * df.dofs();
+  T acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+  const int i0 = i >> 1, i1 = (i + 1) >> 1;
+  const int j0 = j >> 1, j1 = (j + 1) >> 1;
+  const int k0 = k >> 1, k1 = (k + 1) >> 1;
+  const T wxh = (i & 1) ? T(0.5) : T(1);
+  const T wyh = (j & 1) ? T(0.5) : T(1);
+  const T wzh = (DIM == 3 && (k & 1)) ? T(0.5) : T(1);
+  const int nzi = (DIM == 3 && (k & 1)) ? 2 : 1;
+  const int nyi = (j & 1) ? 2 : 1, nxi = (i & 1) ? 2 : 1;
+  for (int a = 0; a < nzi; ++a) {
+    const int K = a ? k1 : k0;
+    for (int bq = 0; bq < nyi; ++bq) {
+      const int J = bq ? j1 : j0;
+      for (int cq = 0; cq < nxi; ++cq) {
+        const int I = cq ? i1 : i0;
+        const T w = wxh * wyh * wzh;
+        const long long cid = I + (long long)cnx * (J + (long long)cny * (DIM == 3 ? K : 0));
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) acc[c] = fma(w, zc[DIM * cid + c], acc[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const long long id = DIM * node + c;
+    if (!fixed_f[id]) zf[id] += acc[c];
+  }
+}
+
+// 1 / diag(A) per DOF (1 on fixed DOFs).
+template <int DIM>
+__global__ void k_inv_diag(Dims d, const double* __restrict__ K0, const double* __restrict__ x,
+                           const double* __restrict__ Ae, const uint8_t* __restrict__ fixed,
+                           double* __restrict__ invd) {
+  constexpr int NN = Elem<DIM>::NN, NE = Elem<DIM>::NE;
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= d.nodes()) return;
+  const int nnx = d.nx + 1, nny = d.ny + 1;
+  const int i = (int)(node % nnx), j = (int)((node / nnx) % nny);
+  const int k = (DIM == 3) ? (int)(node / ((long long)nnx * nny)) : 0;
+  double acc[DIM] = {};
+  for (int s = 0; s < NN; ++s) {
+    const int dx = s & 1, dy = (s >> 1) & 1, dz = (DIM == 3) ? (s >> 2) : 0;
+    const int ex = i - 1 + dx, ey = j - 1 + dy, ez = (DIM == 3) ? k - 1 + dz : 0;
+    if (ex < 0 || ex >= d.nx || ey < 0 || ey >= d.ny) continue;
+    if (DIM == 3 && (ez < 0 || ez >= d.nz)) continue;
+    const int loc = loc_of(1 - dx, 1 - dy, DIM == 3 ? 1 - dz : 0);
+    const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
+    for (int c = 0; c < DIM; ++c) {
+      const int r = loc * DIM + c;
+      acc[c] += x ? x[e] * K0[r * NE + r] : Ae[e * NE * NE + r * NE + r];
+    }
+  }
+  for (int c = 0; c < DIM; ++c) {
+    const long long id = DIM * node + c;
+    invd[id] = (fixed[id] || !(acc[c] > 0.0)) ? 1.0 : 1.0 / acc[c];
+  }
+}
+
+// E_e = scale * lam_e^T K0 u_e (lam = u gives the element energy u_e^T K0 u_e).
+template <int DIM>
+__global__ void k_element_energy(Dims d, const double* __restrict__ K0,
+                                 const double* __restrict__ u, const double* __restrict__ lam,
+                                 double* __restrict__ out, double scale) {
+  constexpr int NN = Elem<DIM>::NN, NE = Elem<DIM>::NE;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.elems()) return;
+  const int ex = (int)(e % d.nx), ey = (int)((e / d.nx) % d.ny);
+  const int ez = (DIM == 3) ? (int)(e / ((long long)d.nx * d.ny)) : 0;
+  const int nnx = d.nx + 1, nny = d.ny + 1;
+  double ue[NE], le[NE];
+#pragma unroll
+  for (int a = 0; a < NN; ++a) {
+    const long long nid = (ex + loc_ox(a)) + (long long)nnx * ((ey + loc_oy(a)) +
+                                                               (long long)nny * (ez + loc_oz(a)));
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      ue[a * DIM + c] = u[DIM * nid + c];
+      le[a * DIM + c] = lam[DIM * nid + c];
+    }
+  }
+  double s = 0.0;
+  for (int r = 0; r < NE; ++r) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < NE; ++q) t = fma(__ldg(K0 + r * NE + q), ue[q], t);
+    s = fma(le[r], t, s);
+  }
+  out[e] = scale * s;
+}
+
+// flag = 1 if any x_i is not finite or not > 0 (x_i > 0 is false for NaN).
+__global__ void k_check_positive(const double* __restrict__ x, long long m, int* flag) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) {
+    const double v = x[i];
+    if (!(v > 0.0) || !isfinite(v)) *flag = 1;
+  }
+}
+
+__global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+__global__ void k_f2d(const float* __restrict__ a, double* __restrict__ b, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_apply(const Dims& d, int mode, const T* K0, const T* x, const T* Ae, const T* v,
+                         const T* b, T* y, const T* invd, T omega, const uint8_t* fixed, int nrhs,
+                         const CgScalars* sc, cudaStream_t st) {
+#define TOPO_APPLY_CASE(DIM)                                                                    \
+  switch (mode) {                                                                               \
+    case 0: apply_dispatch<DIM, T, 0>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st); \
+      break;                                                                                    \
+    case 1: apply_dispatch<DIM, T, 1>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st); \
+      break;                                                                                    \
+    case 2: apply_dispatch<DIM, T, 2>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st); \
+      break;                                                                                    \
+    default: apply_dispatch<DIM, T, 3>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st);\
+  }
+  if (d.dim == 2) {
+    TOPO_APPLY_CASE(2)
+  } else {
+    TOPO_APPLY_CASE(3)
+  }
+#undef TOPO_APPLY_CASE
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_apply<double>(const Dims&, int, const double*, const double*,
+                                          const double*, const double*, const double*, double*,
+                                          const double*, double, const uint8_t*, int,
+                                          const CgScalars*, cudaStream_t);
+template cudaError_t launch_apply<float>(const Dims&, int, const float*, const float*, const float*,
+                                         const float*, const float*, float*, const float*, float,
+                                         const uint8_t*, int, const CgScalars*, cudaStream_t);
+
+cudaError_t launch_apply_dot_fine(const Dims& d, const double* K0, const double* x, const double* v,
+                                  double* y, const uint8_t* fixed, int nrhs, double* partials,
+                                  unsigned* counters, CgScalars* sc, cudaStream_t st) {
+  dim3 grid(blocks_for(d.nodes()), nrhs);
+  if (d.dim == 2)
+    k_apply_dot_fine<2><<<grid, kThreads, 0, st>>>(d, K0, x, v, y, fixed, partials, counters, sc);
+  else
+    k_apply_dot_fine<3><<<grid, kThreads, 0, st>>>(d, K0, x, v, y, fixed, partials, counters, sc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_restrict(const Dims& fine, const T* rf, T* rc, const uint8_t* fixed_c, int nrhs,
+                            const CgScalars* sc, cudaStream_t st) {
+  Dims dc{fine.nx / 2, fine.ny / 2, fine.dim == 3 ? fine.nz / 2 : 1, fine.dim};
+  dim3 grid(blocks_for(dc.nodes()), nrhs);
+  if (fine.dim == 2)
+    k_restrict<2, T><<<grid, kThreads, 0, st>>>(fine, rf, rc, fixed_c, sc);
+  else
+    k_restrict<3, T><<<grid, kThreads, 0, st>>>(fine, rf, rc, fixed_c, sc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_restrict<double>(const Dims&, const double*, double*, const uint8_t*,
+                                             int, const CgScalars*, cudaStream_t);
+template cudaError_t launch_restrict<float>(const Dims&, const float*, float*, const uint8_t*, int,
+                                            const CgScalars*, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_prolong_add(const Dims& fine, const T* zc, T* zf, const uint8_t* fixed_f,
+                               int nrhs, const CgScalars* sc, cudaStream_t st) {
+  dim3 grid(blocks_for(fine.nodes()), nrhs);
+  if (fine.dim == 2)
+    k_prolong_add<2, T><<<grid, kThreads, 0, st>>>(fine, zc, zf, fixed_f, sc);
+  else
+    k_prolong_add<3, T><<<grid, kThreads, 0, st>>>(fine, zc, zf, fixed_f, sc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_prolong_add<double>(const Dims&, const double*, double*,
+                                                const uint8_t*, int, const CgScalars*,
+                                                cudaStream_t);
+template cudaError_t launch_prolong_add<float>(const Dims&, const float*, float*, const uint8_t*,
+                                               int, const CgScalars*, cudaStream_t);
+
+cudaError_t launch_inv_diag(const Dims& d, const double* K0, const double* x, const double* Ae,
+                            const uint8_t* fixed, double* invd, cudaStream_t st) {
+  if (d.dim == 2)
+    k_inv_diag<2><<<blocks_for(d.nodes()), kThreads, 0, st>>>(d, K0, x, Ae, fixed, invd);
+  else
+    k_inv_diag<3><<<blocks_for(d.nodes()), kThreads, 0, st>>>(d, K0, x, Ae, fixed, invd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_element_energy(const Dims& d, const double* K0, const double* u,
+                                  const double* lam, double* out, double scale, cudaStream_t st) {
+  if (d.dim == 2)
+    k_element_energy<2><<<blocks_for(d.elems()), kThreads, 0, st>>>(d, K0, u, lam, out, scale);
+  else
+    k_element_energy<3><<<blocks_for(d.elems()), kThreads, 0, st>>>(d, K0, u, lam, out, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_d2f(const double* a, float* b, long long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_d2f<<<blocks_for(n), kThreads, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_positive(const double* x, long long m, int* flag, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+  if (e != cudaSuccess || m <= 0) return e;
+  k_check_positive<<<blocks_for(m), kThreads, 0, st>>>(x, m, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_f2d(const float* a, double* b, long long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_f2d<<<blocks_for(n), kThreads, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+}  // namespace topo

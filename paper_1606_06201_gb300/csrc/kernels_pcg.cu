@@ -1,0 +1,325 @@
+// Vector kernels of Algorithm PCG (Sec. 5.2) in FP64 with the paper's sign convention
+// r = A z - b, p = -y:  alpha = r^T y / p^T A p,  z += alpha p,  r~ = r + alpha A p,
+// beta = r~^T y~ / r^T y,  p = -y~ + beta p.  Stop test ||r||_2 / ||b||_2 <= tol.
+//
+// Every reduction is a fixed-grid grid-stride kernel writing one partial per block; the last
+// block to finish (atomic ticket) adds the partials in block order, so sums are deterministic,
+// and updates the device-resident scalars of its right-hand side.  Kernels return at once for a
+// right-hand side whose recurrence has stopped, which lets a captured graph of several
+// iterations run past convergence at the cost of empty launches.
+#include "topo_internal.cuh"
+
+namespace topo {
+
+namespace {
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double warp_sums[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) warp_sums[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (wid == 0) {
+    s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  return s;
+}
+
+// Writes this block's partials (NV values) and returns true in the whole block of the last block
+// to finish; the sums are then returned in tot[] (valid in every thread of that block).
+template <int NV>
+__device__ bool last_block_sums(const double (&part)[NV], double* partials, unsigned* counters,
+                                int rhs, double (&tot)[NV]) {
+  __shared__ bool last;
+  __shared__ double res[NV];
+  double bs[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) bs[q] = block_sum(part[q]);
+  const long long base = (long long)rhs * gridDim.x * NV;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) partials[base + (long long)q * gridDim.x + blockIdx.x] = bs[q];
+    __threadfence();
+    last = (atomicAdd(&counters[rhs], 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double s = 0.0;
+    for (unsigned t = threadIdx.x; t < gridDim.x; t += blockDim.x)
+      s += __ldcg(partials + base + (long long)q * gridDim.x + t);
+    s = block_sum(s);
+    if (threadIdx.x == 0) res[q] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) tot[q] = res[q];
+  if (threadIdx.x == 0) counters[rhs] = 0;
+  return true;
+}
+
+// r = A z0 - b (use_x0) or r = -b, z = 0; ||b||, ||r|| -> initial scalars and stop test.
+__global__ void __launch_bounds__(kThreads) k_cg_init(long long n, const double* __restrict__ b,
+                                                      double* __restrict__ z,
+                                                      double* __restrict__ r,
+                                                      const double* __restrict__ Az, int use_x0,
+                                                      double* partials, unsigned* counters,
+                                                      CgScalars* sc, double tol, int max_iter) {
+  const int rhs = blockIdx.y;
+  b += rhs * n;
+  z += rhs * n;
+  r += rhs * n;
+  if (Az) Az += rhs * n;
+  double part[2] = {0.0, 0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    const double ri = use_x0 ? Az[i] - bi : -bi;
+    if (!use_x0) z[i] = 0.0;
+    r[i] = ri;
+    part[0] = fma(bi, bi, part[0]);
+    part[1] = fma(ri, ri, part[1]);
+  }
+  double tot[2];
+  if (!last_block_sums<2>(part, partials, counters, rhs, tot)) return;
+  if (threadIdx.x == 0) {
+    CgScalars S = {};
+    S.bnorm = sqrt(tot[0]);
+    S.rr = tot[1];
+    S.rel = S.bnorm > 0.0 ? sqrt(tot[1]) / S.bnorm : 0.0;
+    S.iter = 0;
+    S.status = TOPO_OK;
+    if (!isfinite(S.rel)) {
+      S.status = TOPO_E_BREAKDOWN;
+      S.done = 1;
+    } else {
+      S.done = (S.bnorm == 0.0 || S.rel <= tol) ? 1 : 0;
+      if (!S.done && max_iter <= 0) {
+        S.done = 1;
+        S.status = TOPO_E_NOT_CONVERGED;
+      }
+    }
+    sc[rhs] = S;
+  }
+}
+
+// p = -y (first direction), y_old = y, and r^T y.
+template <typename TV>
+__global__ void __launch_bounds__(kThreads) k_cg_start_p(long long n, const double* __restrict__ r,
+                                                         const TV* __restrict__ y,
+                                                         double* __restrict__ p,
+                                                         TV* __restrict__ y_old, int flexible,
+                                                         double* partials, unsigned* counters,
+                                                         CgScalars* sc) {
+  const int rhs = blockIdx.y;
+  if (sc[rhs].done) return;
+  r += rhs * n;
+  y += rhs * n;
+  p += rhs * n;
+  if (flexible) y_old += rhs * n;
+  double part[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const TV yi = y[i];
+    p[i] = -(double)yi;
+    if (flexible) y_old[i] = yi;
+    part[0] = fma(r[i], (double)yi, part[0]);
+  }
+  double tot[1];
+  if (!last_block_sums<1>(part, partials, counters, rhs, tot)) return;
+  if (threadIdx.x == 0) {
+    sc[rhs].ry = tot[0];
+    if (!isfinite(tot[0])) {
+      sc[rhs].status = TOPO_E_BREAKDOWN;
+      sc[rhs].done = 1;
+    }
+  }
+}
+
+// z += alpha p, r += alpha q, rv = r (V-cycle input precision), ||r||^2 and the stop test.
+template <typename TV>
+__global__ void __launch_bounds__(kThreads) k_cg_update(long long n, double* __restrict__ z,
+                                                        double* __restrict__ r,
+                                                        const double* __restrict__ p,
+                                                        const double* __restrict__ q,
+                                                        TV* __restrict__ rv, double* partials,
+                                                        unsigned* counters, CgScalars* sc,
+                                                        double tol, int max_iter) {
+  const int rhs = blockIdx.y;
+  if (sc[rhs].done) return;
+  const double alpha = sc[rhs].alpha;
+  z += rhs * n;
+  r += rhs * n;
+  p += rhs * n;
+  q += rhs * n;
+  if (rv) rv += rhs * n;
+  double part[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    z[i] = fma(alpha, p[i], z[i]);
+    const double ri = fma(alpha, q[i], r[i]);
+    r[i] = ri;
+    if (rv) rv[i] = (TV)ri;
+    part[0] = fma(ri, ri, part[0]);
+  }
+  double tot[1];
+  if (!last_block_sums<1>(part, partials, counters, rhs, tot)) return;
+  if (threadIdx.x == 0) {
+    CgScalars& S = sc[rhs];
+    S.rr = tot[0];
+    S.rel = sqrt(tot[0]) / S.bnorm;
+    S.iter += 1;
+    if (!isfinite(S.rel)) {
+      S.status = TOPO_E_BREAKDOWN;
+      S.done = 1;
+    } else if (S.rel <= tol) {
+      S.done = 1;
+    } else if (S.iter >= max_iter) {
+      S.status = TOPO_E_NOT_CONVERGED;
+      S.done = 1;
+    }
+  }
+}
+
+// beta = r~^T y~ / r^T y (flexible: (r~^T y~ - r~^T y) / r^T y).
+template <typename TV>
+__global__ void __launch_bounds__(kThreads) k_cg_beta(long long n, const double* __restrict__ r,
+                                                      const TV* __restrict__ y,
+                                                      const TV* __restrict__ y_old, int flexible,
+                                                      double* partials, unsigned* counters,
+                                                      CgScalars* sc) {
+  const int rhs = blockIdx.y;
+  if (sc[rhs].done) return;
+  r += rhs * n;
+  y += rhs * n;
+  if (flexible) y_old += rhs * n;
+  double part[2] = {0.0, 0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double ri = r[i];
+    part[0] = fma(ri, (double)y[i], part[0]);
+    if (flexible) part[1] = fma(ri, (double)y_old[i], part[1]);
+  }
+  double tot[2];
+  if (!last_block_sums<2>(part, partials, counters, rhs, tot)) return;
+  if (threadIdx.x == 0) {
+    CgScalars& S = sc[rhs];
+    const double num = flexible ? tot[0] - tot[1] : tot[0];
+    const double beta = num / S.ry;
+    S.ry_new = tot[0];
+    S.ry_old = tot[1];
+    S.beta = beta;
+    S.ry = tot[0];
+    if (!isfinite(beta)) {
+      S.status = TOPO_E_BREAKDOWN;
+      S.done = 1;
+    }
+  }
+}
+
+// p = -y + beta p, y_old = y.
+template <typename TV>
+__global__ void __launch_bounds__(kThreads) k_cg_p(long long n, const TV* __restrict__ y,
+                                                   double* __restrict__ p, TV* __restrict__ y_old,
+                                                   int flexible, const CgScalars* sc) {
+  const int rhs = blockIdx.y;
+  if (sc[rhs].done) return;
+  const double beta = sc[rhs].beta;
+  y += rhs * n;
+  p += rhs * n;
+  if (flexible) y_old += rhs * n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const TV yi = y[i];
+    p[i] = fma(beta, p[i], -(double)yi);
+    if (flexible) y_old[i] = yi;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_dot(long long n, const double* __restrict__ a,
+                                                  const double* __restrict__ b, double* partials,
+                                                  unsigned* counters, double* out) {
+  const int rhs = blockIdx.y;
+  a += rhs * n;
+  b += rhs * n;
+  double part[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    part[0] = fma(a[i], b[i], part[0]);
+  double tot[1];
+  if (!last_block_sums<1>(part, partials, counters, rhs, tot)) return;
+  if (threadIdx.x == 0) out[rhs] = tot[0];
+}
+
+inline unsigned red_blocks(long long n) {
+  const long long b = (n + kThreads - 1) / kThreads;
+  return (unsigned)(b < kRedBlocks ? (b < 1 ? 1 : b) : kRedBlocks);
+}
+
+}  // namespace
+
+cudaError_t launch_cg_init(long long n, int nrhs, const double* b, double* z, double* r,
+                           const double* Az, int use_x0, double* partials, unsigned* counters,
+                           CgScalars* sc, double tol, int max_iter, cudaStream_t st) {
+  k_cg_init<<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, b, z, r, Az, use_x0, partials,
+                                                            counters, sc, tol, max_iter);
+  return cudaGetLastError();
+}
+
+template <typename TV>
+cudaError_t launch_cg_start_p(long long n, int nrhs, const double* r, const TV* y, double* p,
+                              TV* y_old, int flexible, double* partials, unsigned* counters,
+                              CgScalars* sc, cudaStream_t st) {
+  k_cg_start_p<TV><<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, r, y, p, y_old, flexible,
+                                                                   partials, counters, sc);
+  return cudaGetLastError();
+}
+
+template <typename TV>
+cudaError_t launch_cg_update(long long n, int nrhs, double* z, double* r, const double* p,
+                             const double* q, TV* rv, double* partials, unsigned* counters,
+                             CgScalars* sc, double tol, int max_iter, cudaStream_t st) {
+  k_cg_update<TV><<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, z, r, p, q, rv, partials,
+                                                                  counters, sc, tol, max_iter);
+  return cudaGetLastError();
+}
+
+template <typename TV>
+cudaError_t launch_cg_direction(long long n, int nrhs, const double* r, const TV* y, double* p,
+                                TV* y_old, int flexible, double* partials, unsigned* counters,
+                                CgScalars* sc, cudaStream_t st) {
+  k_cg_beta<TV><<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, r, y, y_old, flexible,
+                                                                partials, counters, sc);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_cg_p<TV><<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, y, p, y_old, flexible, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot(long long n, int nrhs, const double* a, const double* b, double* partials,
+                       unsigned* counters, double* out, cudaStream_t st) {
+  k_dot<<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, a, b, partials, counters, out);
+  return cudaGetLastError();
+}
+
+#define TOPO_INST(TV)                                                                            \
+  template cudaError_t launch_cg_start_p<TV>(long long, int, const double*, const TV*, double*,  \
+                                             TV*, int, double*, unsigned*, CgScalars*,           \
+                                             cudaStream_t);                                      \
+  template cudaError_t launch_cg_update<TV>(long long, int, double*, double*, const double*,     \
+                                            const double*, TV*, double*, unsigned*, CgScalars*,  \
+                                            double, int, cudaStream_t);                          \
+  template cudaError_t launch_cg_direction<TV>(long long, int, const double*, const TV*,         \
+                                               double*, TV*, int, double*, unsigned*,            \
+                                               CgScalars*, cudaStream_t);
+TOPO_INST(double)
+TOPO_INST(float)
+#undef TOPO_INST
+
+}  // namespace topo

@@ -1,0 +1,275 @@
+// Finest-level operator of the 2D Q1 grid, K(x) v = sum_e x_e L_e^T K0 L_e v (Eq. (to), Sec. 7),
+// specialised for square plane-stress elements.
+//
+// Element product.  Writing the bilinear field of an element as
+//   u = 1/4 (S + X xi + Y eta + H xi eta),  v = 1/4 (S' + X' xi + Y' eta + H' xi eta)
+// with X = sum_a xi_a u_a, Y = sum_a eta_a u_a, H = sum_a xi_a eta_a u_a (xi_a, eta_a = +-1 at the
+// corners) and likewise for v, the strain energy of a unit square element is
+//   1/2 t^T Khat t,  t = (X, Y', G = Y + X', H, H'),
+//   Khat = diag-blocks [[D11, D12], [D12, D22]]/4 on (X, Y'), D33/4 on G,
+//          (D11 + D33)/12 on H, (D22 + D33)/12 on H'
+// (the cross terms between constant and linear parts integrate to zero).  So K0 = T^T Khat T and
+// K0 v_e costs two 4-point butterflies, 13 multiplies and two inverse butterflies: 40 operations
+// instead of 64 multiply-adds.  The host checks T^T Khat T == K0 before using this path.
+//
+// Data movement.  A warp owns 30 consecutive node columns and a strip of node rows.  Lane l holds
+// node column c = i0 - 1 + l and element column c; it walks the strip row by row, loading one node
+// of v and one density per row (coalesced), gets its right neighbour's nodes with a shuffle, forms
+// its element's eight results, passes the right-hand results to the next lane with a shuffle and
+// carries the top results in registers to the next row.  Each output node is summed from its four
+// elements in a fixed order (deterministic, no atomics); lanes 0 and 31 only supply halo values.
+// The Jacobi diagonal K0_ii sum_{e at node} x_e is formed on the fly from the same densities.
+#include "topo_internal.cuh"
+
+namespace topo {
+
+namespace {
+
+constexpr int kQ1Cols = 30;   // output node columns per warp
+constexpr int kQ1Rows = 16;   // output node rows per warp strip
+constexpr int kQ1Warps = 8;   // warps per block
+
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+
+template <typename T>
+struct Q1K {
+  T c11, c12, c22, c33, cH, cHp, kd;
+};
+
+template <typename T>
+__device__ __forceinline__ void q1_element(const Q1K<T>& k, T xe, const T u[4], const T v[4],
+                                           T ru[4], T rv[4]) {
+  const T d1 = u[2] - u[0], d2 = u[1] - u[3], s1 = u[0] + u[2], s2 = u[1] + u[3];
+  const T X = d2 + d1, Y = d1 - d2, H = s1 - s2;
+  const T e1 = v[2] - v[0], e2 = v[1] - v[3], t1 = v[0] + v[2], t2 = v[1] + v[3];
+  const T Xp = e2 + e1, Yp = e1 - e2, Hp = t1 - t2;
+  const T G = Y + Xp;
+  const T a11 = xe * k.c11, a12 = xe * k.c12, a22 = xe * k.c22;
+  const T gX = fma(a11, X, a12 * Yp);
+  const T gYp = fma(a12, X, a22 * Yp);
+  const T gG = (xe * k.c33) * G, gH = (xe * k.cH) * H, gHp = (xe * k.cHp) * Hp;
+  const T A = gX + gG, B = gX - gG;
+  ru[0] = gH - A;
+  ru[1] = B - gH;
+  ru[2] = A + gH;
+  ru[3] = -B - gH;
+  const T C = gYp + gG, Dd = gYp - gG;
+  rv[0] = gHp - C;
+  rv[1] = -Dd - gHp;
+  rv[2] = C + gHp;
+  rv[3] = Dd - gHp;
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_dn(T v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+template <typename T>
+__device__ __forceinline__ T shfl_up1(T v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+
+__device__ __forceinline__ double block_sum_q1(double v) {
+  __shared__ double warp_sums[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) warp_sums[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (wid == 0) {
+    s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  return s;
+}
+
+// MODE 0: y = K v; 1: y = b - K v; 2: y = v + omega D^{-1} (b - K v); 3: y = omega D^{-1} b.
+// DOT (MODE 0, FP64): also p^T q with the last-block finalisation alpha = r^T y / p^T q.
+template <typename T, int MODE, bool DOT>
+__global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, Q1K<T> k,
+                                                             const T* __restrict__ x,
+                                                             const T* __restrict__ v,
+                                                             const T* __restrict__ b,
+                                                             T* __restrict__ y, T omega,
+                                                             const uint8_t* __restrict__ fixed,
+                                                             CgScalars* sc, double* partials,
+                                                             unsigned* counters) {
+  using V2 = typename Vec2<T>::type;
+  const int rhs = blockIdx.y;
+  if (sc && sc[rhs].done) return;
+  const long long n = 2LL * (nx + 1) * (ny + 1);
+  v += rhs * n;
+  y += rhs * n;
+  if (MODE == 1 || MODE == 2 || MODE == 3) b += rhs * n;
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kQ1Warps + (threadIdx.x >> 5);
+  const int ncolw = (nx + 1 + kQ1Cols - 1) / kQ1Cols;
+  const int nstrip = (ny + 1 + kQ1Rows - 1) / kQ1Rows;
+  const int wc = gw % ncolw, ws = gw / ncolw;
+  double part = 0.0;
+  if (ws < nstrip) {
+    const int c = wc * kQ1Cols - 1 + lane;           // node column and element column of the lane
+    const bool col_ok = (c >= 0 && c <= nx);
+    const bool out_lane = (lane >= 1 && lane <= kQ1Cols && col_ok);
+    const bool el_col = (lane <= kQ1Cols && c >= 0 && c < nx);
+    const int j0 = ws * kQ1Rows;
+    const int j1 = min(j0 + kQ1Rows, ny + 1);
+    const V2* v2 = reinterpret_cast<const V2*>(v);
+    V2 pb;
+    pb.x = T(0);
+    pb.y = T(0);
+    if (MODE != 3 && col_ok && j0 >= 1) pb = v2[c + (long long)(nx + 1) * (j0 - 1)];
+    T cu = T(0), cv = T(0), xcarry = T(0);
+    for (int ey = j0 - 1; ey < j1; ++ey) {
+      V2 pt;
+      pt.x = T(0);
+      pt.y = T(0);
+      if (MODE != 3 && col_ok && ey + 1 <= ny) pt = v2[c + (long long)(nx + 1) * (ey + 1)];
+      const bool el_ok = el_col && ey >= 0 && ey < ny;
+      const T xe = el_ok ? x[c + (long long)nx * ey] : T(0);
+      const T pbr_u = shfl_dn(pb.x), pbr_v = shfl_dn(pb.y);
+      const T ptr_u = shfl_dn(pt.x), ptr_v = shfl_dn(pt.y);
+      T ru[4], rv[4];
+      if (MODE != 3) {
+        const T uu[4] = {pb.x, pbr_u, ptr_u, pt.x};
+        const T vv[4] = {pb.y, pbr_v, ptr_v, pt.y};
+        q1_element<T>(k, xe, uu, vv, ru, rv);
+      } else {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) ru[a] = rv[a] = T(0);
+      }
+      const T l1u = shfl_up1(ru[1]), l1v = shfl_up1(rv[1]);
+      const T l2u = shfl_up1(ru[2]), l2v = shfl_up1(rv[2]);
+      const T xl = shfl_up1(xe);
+      const T xpair = xe + (lane >= 1 ? xl : T(0));
+      if (ey >= j0 && out_lane) {
+        const T qu = cu + ru[0] + l1u, qv = cv + rv[0] + l1v;
+        const long long node = c + (long long)(nx + 1) * ey;
+        const uint16_t fx = *reinterpret_cast<const uint16_t*>(fixed + 2 * node);
+        V2 out;
+        if (MODE == 0) {
+          out.x = qu;
+          out.y = qv;
+        } else if (MODE == 1) {
+          const V2 bb = reinterpret_cast<const V2*>(b)[node];
+          out.x = bb.x - qu;
+          out.y = bb.y - qv;
+        } else {
+          const V2 bb = reinterpret_cast<const V2*>(b)[node];
+          const T xs = xcarry + xpair;
+          const T dinv = xs > T(0) ? T(1) / (k.kd * xs) : T(1);
+          if (MODE == 2) {
+            out.x = fma(omega * dinv, bb.x - qu, pb.x);
+            out.y = fma(omega * dinv, bb.y - qv, pb.y);
+          } else {
+            out.x = omega * dinv * bb.x;
+            out.y = omega * dinv * bb.y;
+          }
+        }
+        if (fx & 0xff) out.x = T(0);
+        if (fx >> 8) out.y = T(0);
+        reinterpret_cast<V2*>(y)[node] = out;
+        if (DOT) part = fma((double)pb.x, (double)out.x, fma((double)pb.y, (double)out.y, part));
+      }
+      cu = ru[3] + l2u;
+      cv = rv[3] + l2v;
+      xcarry = xpair;
+      pb = pt;
+    }
+  }
+  if (!DOT) return;
+  const double bs = block_sum_q1(part);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[(long long)rhs * gridDim.x + blockIdx.x] = bs;
+    __threadfence();
+    last = (atomicAdd(&counters[rhs], 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  double s = 0.0;
+  for (unsigned t = threadIdx.x; t < gridDim.x; t += blockDim.x)
+    s += __ldcg(partials + (long long)rhs * gridDim.x + t);
+  s = block_sum_q1(s);
+  if (threadIdx.x == 0) {
+    CgScalars& S = sc[rhs];
+    S.pq = s;
+    const double alpha = S.ry / s;
+    if (!(s > 0.0) || !isfinite(alpha)) {
+      S.status = TOPO_E_BREAKDOWN;
+      S.done = 1;
+      S.alpha = 0.0;
+    } else {
+      S.alpha = alpha;
+    }
+    counters[rhs] = 0;
+  }
+}
+
+template <typename T>
+Q1K<T> coef_cast(const Q1Coef& c) {
+  return Q1K<T>{(T)c.c11, (T)c.c12, (T)c.c22, (T)c.c33, (T)c.cH, (T)c.cHp, (T)c.kd};
+}
+
+unsigned q1_blocks(int nx, int ny) {
+  const long long warps = (long long)((nx + 1 + kQ1Cols - 1) / kQ1Cols) *
+                          ((ny + 1 + kQ1Rows - 1) / kQ1Rows);
+  return (unsigned)((warps + kQ1Warps - 1) / kQ1Warps);
+}
+
+}  // namespace
+
+long long q1_partial_blocks(int nx, int ny) { return q1_blocks(nx, ny); }
+
+template <typename T>
+cudaError_t launch_q1_apply(int nx, int ny, int mode, const Q1Coef& coef, const T* x, const T* v,
+                            const T* b, T* y, T omega, const uint8_t* fixed, int nrhs,
+                            const CgScalars* sc, cudaStream_t st) {
+  dim3 grid(q1_blocks(nx, ny), nrhs);
+  const Q1K<T> k = coef_cast<T>(coef);
+  CgScalars* scm = const_cast<CgScalars*>(sc);
+  switch (mode) {
+    case 0:
+      k_q1_sweep<T, 0, false><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, k, x, v, b, y, omega, fixed,
+                                                               scm, nullptr, nullptr);
+      break;
+    case 1:
+      k_q1_sweep<T, 1, false><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, k, x, v, b, y, omega, fixed,
+                                                               scm, nullptr, nullptr);
+      break;
+    case 2:
+      k_q1_sweep<T, 2, false><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, k, x, v, b, y, omega, fixed,
+                                                               scm, nullptr, nullptr);
+      break;
+    default:
+      k_q1_sweep<T, 3, false><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, k, x, v, b, y, omega, fixed,
+                                                               scm, nullptr, nullptr);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_q1_apply<double>(int, int, int, const Q1Coef&, const double*,
+                                             const double*, const double*, double*, double,
+                                             const uint8_t*, int, const CgScalars*, cudaStream_t);
+template cudaError_t launch_q1_apply<float>(int, int, int, const Q1Coef&, const float*,
+                                            const float*, const float*, float*, float,
+                                            const uint8_t*, int, const CgScalars*, cudaStream_t);
+
+cudaError_t launch_q1_apply_dot(int nx, int ny, const Q1Coef& coef, const double* x,
+                                const double* v, double* y, const uint8_t* fixed, int nrhs,
+                                double* partials, unsigned* counters, CgScalars* sc,
+                                cudaStream_t st) {
+  dim3 grid(q1_blocks(nx, ny), nrhs);
+  k_q1_sweep<double, 0, true><<<grid, kQ1Warps * 32, 0, st>>>(
+      nx, ny, coef_cast<double>(coef), x, v, nullptr, y, 0.0, fixed, sc, partials, counters);
+  return cudaGetLastError();
+}
+
+}  // namespace topo

@@ -1,0 +1,268 @@
+// Hierarchy construction: Galerkin coarse operators A_{k-1} = P^T A_k P (Sec. 5.1) computed
+// element by element, the dense coarsest operator, its Cholesky factorisation and inverse (the
+// exact coarsest-grid solve of Algorithm MG), and the application of that inverse.
+//
+// Element-local Galerkin product: the bilinear (trilinear) prolongation of Sec. 7 interpolates
+// the values inside a coarse element from that element's own nodes only, so restricted to one
+// fine child element c of coarse element E it is a small matrix P_c (node weights W_c times the
+// identity on components) and  P^T A P = sum_E L_E^T ( sum_{c in E} P_c^T A_c P_c ) L_E.
+// For the first coarsening A_c = x_c K0, so sum_c x_c (P_c^T K0 P_c) with four (eight) constant
+// matrices C_c = P_c^T K0 P_c prepared on the host.
+#include "topo_internal.cuh"
+
+namespace topo {
+
+namespace {
+
+__device__ __forceinline__ int loc_ox(int a) { return ((a & 3) == 1 || (a & 3) == 2) ? 1 : 0; }
+__device__ __forceinline__ int loc_oy(int a) { return ((a & 3) >= 2) ? 1 : 0; }
+__device__ __forceinline__ int loc_oz(int a) { return a >> 2; }
+__device__ __forceinline__ int loc_of(int lx, int ly, int lz) {
+  return (ly ? (lx ? 2 : 3) : (lx ? 1 : 0)) + 4 * lz;
+}
+
+// 1-D weight of the coarse-element-local node coordinate q in {0,1} at the fine position
+// p in {0,1,2} (in fine units, inside the coarse element): 1 - |p - 2q| / 2.
+__device__ __forceinline__ double w1(int p, int q) {
+  const int dd = p - 2 * q;
+  return dd == 0 ? 1.0 : ((dd == 1 || dd == -1) ? 0.5 : 0.0);
+}
+
+// W_c[a][A]: weight of coarse local node A at fine local node a of child c.
+template <int DIM>
+__device__ __forceinline__ double wchild(int c, int a, int A) {
+  const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+  double w = w1(cx + loc_ox(a), loc_ox(A)) * w1(cy + loc_oy(a), loc_oy(A));
+  if (DIM == 3) w *= w1(cz + loc_oz(a), loc_oz(A));
+  return w;
+}
+
+template <int DIM>
+__global__ void k_rap_from_fine(Dims df, const double* __restrict__ C,
+                                const double* __restrict__ x, double* __restrict__ Ac) {
+  constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM, NE2 = NE * NE;
+  const int cnx = df.nx / 2, cny = df.ny / 2, cnz = DIM == 3 ? df.nz / 2 : 1;
+  const long long mc = (long long)cnx * cny * cnz;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= mc * NE2) return;
+  const long long E = t / NE2;
+  const int entry = (int)(t % NE2);
+  const int EX = (int)(E % cnx), EY = (int)((E / cnx) % cny), EZ = (int)(E / ((long long)cnx * cny));
+  double acc = 0.0;
+#pragma unroll
+  for (int c = 0; c < NN; ++c) {
+    const int fx = 2 * EX + (c & 1), fy = 2 * EY + ((c >> 1) & 1), fz = 2 * EZ + (c >> 2);
+    const long long fe = fx + (long long)df.nx * (fy + (long long)df.ny * (DIM == 3 ? fz : 0));
+    acc = fma(x[fe], __ldg(C + c * NE2 + entry), acc);
+  }
+  Ac[t] = acc;
+}
+
+template <int DIM>
+__global__ void k_rap_coarse(Dims df, const double* __restrict__ Af, double* __restrict__ Ac) {
+  constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM, NE2 = NE * NE;
+  const int cnx = df.nx / 2, cny = df.ny / 2, cnz = DIM == 3 ? df.nz / 2 : 1;
+  const long long mc = (long long)cnx * cny * cnz;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= mc * NE2) return;
+  const long long E = t / NE2;
+  const int entry = (int)(t % NE2);
+  const int I = entry / NE, J = entry % NE;
+  const int A = I / DIM, al = I % DIM, B = J / DIM, be = J % DIM;
+  const int EX = (int)(E % cnx), EY = (int)((E / cnx) % cny), EZ = (int)(E / ((long long)cnx * cny));
+  double acc = 0.0;
+  for (int c = 0; c < NN; ++c) {
+    const int fx = 2 * EX + (c & 1), fy = 2 * EY + ((c >> 1) & 1), fz = 2 * EZ + (c >> 2);
+    const long long fe = fx + (long long)df.nx * (fy + (long long)df.ny * (DIM == 3 ? fz : 0));
+    const double* Ach = Af + fe * NE2;
+    for (int a = 0; a < NN; ++a) {
+      const double wa = wchild<DIM>(c, a, A);
+      if (wa == 0.0) continue;
+      double s = 0.0;
+      for (int b = 0; b < NN; ++b) {
+        const double wb = wchild<DIM>(c, b, B);
+        if (wb == 0.0) continue;
+        s = fma(__ldg(Ach + (a * DIM + al) * NE + b * DIM + be), wb, s);
+      }
+      acc = fma(wa, s, acc);
+    }
+  }
+  Ac[t] = acc;
+}
+
+// Dense operator of a level (used for the coarsest level): entry (i, j) gathers the elements that
+// hold both DOFs' nodes.  Fixed DOFs get identity rows and columns.
+template <int DIM>
+__global__ void k_assemble_dense(Dims d, const double* __restrict__ K0,
+                                 const double* __restrict__ x, const double* __restrict__ Ae,
+                                 const uint8_t* __restrict__ fixed, double* __restrict__ A) {
+  constexpr int NE = (DIM == 2 ? 4 : 8) * DIM;
+  const long long n = d.dofs();
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const long long i = t / n, j = t % n;
+  if (fixed[i] || fixed[j]) {
+    A[t] = (i == j) ? 1.0 : 0.0;
+    return;
+  }
+  const int nnx = d.nx + 1, nny = d.ny + 1;
+  const long long ni = i / DIM, nj = j / DIM;
+  const int al = (int)(i % DIM), be = (int)(j % DIM);
+  const int xi = (int)(ni % nnx), yi = (int)((ni / nnx) % nny), zi = (int)(ni / ((long long)nnx * nny));
+  const int xj = (int)(nj % nnx), yj = (int)((nj / nnx) % nny), zj = (int)(nj / ((long long)nnx * nny));
+  double acc = 0.0;
+  for (int s = 0; s < (DIM == 2 ? 4 : 8); ++s) {
+    const int ex = xi - 1 + (s & 1), ey = yi - 1 + ((s >> 1) & 1), ez = DIM == 3 ? zi - 1 + (s >> 2) : 0;
+    if (ex < 0 || ex >= d.nx || ey < 0 || ey >= d.ny) continue;
+    if (DIM == 3 && (ez < 0 || ez >= d.nz)) continue;
+    const int lxj = xj - ex, lyj = yj - ey, lzj = DIM == 3 ? zj - ez : 0;
+    if (lxj < 0 || lxj > 1 || lyj < 0 || lyj > 1 || lzj < 0 || lzj > 1) continue;
+    const int li = loc_of(xi - ex, yi - ey, DIM == 3 ? zi - ez : 0);
+    const int lj = loc_of(lxj, lyj, lzj);
+    const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
+    const int r = li * DIM + al, q = lj * DIM + be;
+    acc += x ? x[e] * K0[r * NE + q] : Ae[e * NE * NE + r * NE + q];
+  }
+  A[t] = acc;
+}
+
+// In-place Cholesky A = L L^T of a dense SPD matrix in one block (right-looking), then L^T is
+// mirrored into the strict upper triangle.  info = 0, or k+1 if the k-th pivot is not positive.
+__global__ void __launch_bounds__(1024) k_cholesky(int n, double* A, int* info) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      const double akk = A[(long long)k * n + k];
+      if (!(akk > 0.0) || !isfinite(akk)) bad = k + 1;
+      else A[(long long)k * n + k] = sqrt(akk);
+    }
+    __syncthreads();
+    if (bad) break;
+    const double lkk = A[(long long)k * n + k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[(long long)i * n + k] /= lkk;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = k + 1 + warp; i < n; i += nw) {
+      const double lik = A[(long long)i * n + k];
+      for (int j = k + 1 + lane; j <= i; j += 32)
+        A[(long long)i * n + j] -= lik * A[(long long)j * n + k];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *info = bad;
+  if (bad) return;
+  for (long long idx = threadIdx.x; idx < (long long)n * n; idx += blockDim.x) {
+    const int i = (int)(idx / n), j = (int)(idx % n);
+    if (j > i) A[idx] = A[(long long)j * n + i];
+  }
+}
+
+// Row j of A^{-1} = solution of A w = e_j with the factor (L lower, L^T upper): one warp per row.
+__global__ void k_chol_inverse(int n, const double* __restrict__ LU, double* Ainv,
+                               const int* info) {
+  if (*info) return;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const int j = warp;
+  volatile double* w = Ainv + (long long)j * n;
+  for (int k = lane; k < n; k += 32) w[k] = 0.0;
+  __syncwarp();
+  for (int i = j; i < n; ++i) {  // forward: L w = e_j
+    const double* Li = LU + (long long)i * n;
+    double s = 0.0;
+    for (int k = j + lane; k < i; k += 32) s = fma(Li[k], w[k], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) w[i] = ((i == j ? 1.0 : 0.0) - s) / Li[i];
+    __syncwarp();
+  }
+  for (int i = n - 1; i >= 0; --i) {  // backward: L^T w = y
+    const double* Ui = LU + (long long)i * n;
+    double s = 0.0;
+    for (int k = i + 1 + lane; k < n; k += 32) s = fma(Ui[k], w[k], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) w[i] = (w[i] - s) / Ui[i];
+    __syncwarp();
+  }
+}
+
+// z = A^{-1} b: one warp per row, FP64 accumulation whatever the vector type.
+template <typename T>
+__global__ void k_dense_solve(int n, const double* __restrict__ Ainv, const T* __restrict__ b,
+                              T* __restrict__ z, const CgScalars* __restrict__ sc) {
+  const int rhs = blockIdx.y;
+  if (sc && sc[rhs].done) return;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  b += (long long)rhs * n;
+  z += (long long)rhs * n;
+  const double* row = Ainv + (long long)warp * n;
+  double s = 0.0;
+  for (int k = lane; k < n; k += 32) s = fma(row[k], (double)b[k], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) z[warp] = (T)s;
+}
+
+}  // namespace
+
+cudaError_t launch_rap_from_fine(const Dims& fine, const double* C, const double* x, double* Ac,
+                                 cudaStream_t st) {
+  const int ne = fine.dim == 2 ? 8 : 24;
+  const long long mc = fine.elems() / (fine.dim == 2 ? 4 : 8);
+  const long long total = mc * ne * ne;
+  if (fine.dim == 2)
+    k_rap_from_fine<2><<<blocks_for(total), kThreads, 0, st>>>(fine, C, x, Ac);
+  else
+    k_rap_from_fine<3><<<blocks_for(total), kThreads, 0, st>>>(fine, C, x, Ac);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rap_coarse(const Dims& fine, const double* Af, double* Ac, cudaStream_t st) {
+  const int ne = fine.dim == 2 ? 8 : 24;
+  const long long mc = fine.elems() / (fine.dim == 2 ? 4 : 8);
+  const long long total = mc * ne * ne;
+  if (fine.dim == 2)
+    k_rap_coarse<2><<<blocks_for(total), kThreads, 0, st>>>(fine, Af, Ac);
+  else
+    k_rap_coarse<3><<<blocks_for(total), kThreads, 0, st>>>(fine, Af, Ac);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_dense(const Dims& d, const double* K0, const double* x,
+                                  const double* Ae, const uint8_t* fixed, double* A,
+                                  cudaStream_t st) {
+  const long long n = d.dofs();
+  if (d.dim == 2)
+    k_assemble_dense<2><<<blocks_for(n * n), kThreads, 0, st>>>(d, K0, x, Ae, fixed, A);
+  else
+    k_assemble_dense<3><<<blocks_for(n * n), kThreads, 0, st>>>(d, K0, x, Ae, fixed, A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cholesky_inverse(int n, double* A, double* Ainv, int* info, cudaStream_t st) {
+  k_cholesky<<<1, 1024, 0, st>>>(n, A, info);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_chol_inverse<<<blocks_for((long long)n * 32), kThreads, 0, st>>>(n, A, Ainv, info);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dense_solve(int n, const double* Ainv, const T* b, T* z, int nrhs,
+                               const CgScalars* sc, cudaStream_t st) {
+  dim3 grid(blocks_for((long long)n * 32), nrhs);
+  k_dense_solve<T><<<grid, kThreads, 0, st>>>(n, Ainv, b, z, sc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_dense_solve<double>(int, const double*, const double*, double*, int,
+                                                const CgScalars*, cudaStream_t);
+template cudaError_t launch_dense_solve<float>(int, const double*, const float*, float*, int,
+                                               const CgScalars*, cudaStream_t);
+
+}  // namespace topo

@@ -1,0 +1,821 @@
+// Host side of the MGCG library: solver objects, the Galerkin hierarchy, the V-cycle (Algorithm
+// MG, Sec. 5.1) and the preconditioned CG loop (Algorithm PCG, Sec. 5.2) driven through CUDA
+// graphs, and the C ABI of include/topo.h.
+//
+// The library runs on a private non-blocking stream.  Each call orders itself after the caller's
+// stream (topo_set_stream, default the legacy stream) with an event and makes the caller's stream
+// wait for its work on exit, so device pointers from the caller may be used on either side.
+// A block of CG iterations is captured once per solver into a CUDA graph; the kernels of a
+// right-hand side whose recurrence has stopped return at once, so the host replays the graph and
+// reads the scalars back once per block.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <type_traits>
+#include <utility>
+#include <string>
+#include <vector>
+
+#include "topo_internal.cuh"
+
+namespace topo {
+
+thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+topo_status cuda_status(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? TOPO_E_OOM : TOPO_E_CUDA;
+}
+
+}  // namespace topo
+
+using namespace topo;
+
+struct topo_solver {
+  topo_solver_desc desc{};
+  int dim = 2, nlev = 1, prec = TOPO_FP64, nrhs = 1, ne = 8;
+  cudaStream_t st = nullptr;     // private stream
+  cudaStream_t user = nullptr;   // caller's stream (nullptr = legacy default stream)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+  std::vector<Level> L;
+  std::vector<uint8_t> fixed_host;
+  double* K0 = nullptr;
+  float* K0f = nullptr;
+  double* C = nullptr;           // constant child matrices P_c^T K0 P_c
+  Q1Coef q1{};                   // butterfly coefficients of the 2D K0
+  bool q1_ok = false;            // 2D and T^T Khat T reproduces K0: use the warp-sweep kernels
+  double* x = nullptr;
+  float* x32 = nullptr;
+  int nc = 0;                    // DOFs of the coarsest level
+  double* Adense = nullptr;
+  double* Ainv = nullptr;
+  int* info = nullptr;
+  double *z = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+  void* yold = nullptr;          // previous preconditioned residual (flexible beta)
+  void* rv = nullptr;            // residual in V-cycle precision (mixed)
+  void* yv = nullptr;            // where the captured V-cycle leaves its result
+  double* partials = nullptr;
+  unsigned* counters = nullptr;
+  CgScalars* sc = nullptr;
+  CgScalars* sc_host = nullptr;  // pinned
+  double* dots = nullptr;
+  double* dots_host = nullptr;
+  double* bbuf = nullptr;        // solver-owned copy of the right-hand side
+  cudaGraphExec_t graph = nullptr;        // graph_iters CG iterations
+  int graph_kernels = 0;
+  double graph_tol = -1.0;                // tolerance baked into the captured graphs
+  cudaGraphExec_t setup[2] = {nullptr, nullptr};  // CG start (use_x0 = 0 / 1)
+  int setup_kernels[2] = {0, 0};
+  double setup_tol[2] = {-1.0, -1.0};
+  cudaGraphExec_t build = nullptr;        // Galerkin hierarchy and coarsest factorisation
+  int build_kernels = 0;
+  int graph_iters = 4;
+  unsigned long long launches = 0;        // kernels launched by this solver
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_ev;       // event pairs around the outer operator per slot
+  double prof_ms = 0.0;
+  long long prof_count = 0;
+  bool have_density = false;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+
+  template <typename T>
+  topo_status alloc(T** ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
+    if (e != cudaSuccess) return cuda_status(e, "cudaMalloc");
+    allocs.push_back((void*)*ptr);
+    bytes += count * sizeof(T);
+    return TOPO_OK;
+  }
+};
+
+namespace {
+
+#define TOPO_TRY(expr)                  \
+  do {                                  \
+    topo_status _s = (expr);            \
+    if (_s != TOPO_OK) return _s;       \
+  } while (0)
+
+// Caller-stream ordering around a library call.
+struct StreamGuard {
+  topo_solver* s;
+  explicit StreamGuard(topo_solver* s_) : s(s_) {
+    cudaEventRecord(s->ev_in, s->user);
+    cudaStreamWaitEvent(s->st, s->ev_in, 0);
+  }
+  ~StreamGuard() {
+    cudaEventRecord(s->ev_out, s->st);
+    cudaStreamWaitEvent(s->user, s->ev_out, 0);
+  }
+};
+
+double w1h(int p, int q) {
+  const int d = p - 2 * q;
+  return d == 0 ? 1.0 : ((d == 1 || d == -1) ? 0.5 : 0.0);
+}
+int lox(int a) { return ((a & 3) == 1 || (a & 3) == 2) ? 1 : 0; }
+int loy(int a) { return ((a & 3) >= 2) ? 1 : 0; }
+int loz(int a) { return a >> 2; }
+
+// C_c = P_c^T K0 P_c for the 2^dim children of a coarse element.
+void child_matrices(int dim, const double* K0, std::vector<double>& C) {
+  const int NN = dim == 2 ? 4 : 8, NE = NN * dim;
+  C.assign((size_t)NN * NE * NE, 0.0);
+  for (int c = 0; c < NN; ++c) {
+    const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+    std::vector<double> W(NN * NN);
+    for (int a = 0; a < NN; ++a)
+      for (int A = 0; A < NN; ++A) {
+        double w = w1h(cx + lox(a), lox(A)) * w1h(cy + loy(a), loy(A));
+        if (dim == 3) w *= w1h(cz + loz(a), loz(A));
+        W[a * NN + A] = w;
+      }
+    for (int I = 0; I < NE; ++I)
+      for (int J = 0; J < NE; ++J) {
+        const int A = I / dim, al = I % dim, B = J / dim, be = J % dim;
+        double acc = 0.0;
+        for (int a = 0; a < NN; ++a)
+          for (int b = 0; b < NN; ++b)
+            acc += W[a * NN + A] * K0[(a * dim + al) * NE + b * dim + be] * W[b * NN + B];
+        C[(size_t)c * NE * NE + I * NE + J] = acc;
+      }
+  }
+}
+
+// Butterfly coefficients of the plane-stress Q1 K0 (see kernels_q1.cu) and a check that they
+// reproduce the quadrature K0.
+bool q1_coefficients(double E, double nu, const double* K0, Q1Coef& q) {
+  const double c = E / (1.0 - nu * nu);
+  const double D11 = c, D22 = c, D12 = c * nu, D33 = 0.5 * c * (1.0 - nu);
+  q = Q1Coef{D11 / 4.0, D12 / 4.0, D22 / 4.0, D33 / 4.0, (D11 + D33) / 12.0, (D22 + D33) / 12.0,
+             K0[0]};
+  const double xi[4] = {-1, 1, 1, -1}, eta[4] = {-1, -1, 1, 1};
+  double T[5][8] = {};
+  for (int a = 0; a < 4; ++a) {
+    T[0][2 * a] = xi[a];
+    T[1][2 * a + 1] = eta[a];
+    T[2][2 * a] = eta[a];
+    T[2][2 * a + 1] = xi[a];
+    T[3][2 * a] = xi[a] * eta[a];
+    T[4][2 * a + 1] = xi[a] * eta[a];
+  }
+  double Kh[5][5] = {};
+  Kh[0][0] = q.c11;
+  Kh[0][1] = Kh[1][0] = q.c12;
+  Kh[1][1] = q.c22;
+  Kh[2][2] = q.c33;
+  Kh[3][3] = q.cH;
+  Kh[4][4] = q.cHp;
+  double scale = 0.0, err = 0.0;
+  for (int i = 0; i < 8; ++i) {
+    if (std::fabs(K0[i * 8 + i] - K0[0]) > 1e-14 * std::fabs(K0[0])) return false;
+    for (int j = 0; j < 8; ++j) {
+      double acc = 0.0;
+      for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 5; ++b) acc += T[a][i] * Kh[a][b] * T[b][j];
+      err = std::max(err, std::fabs(acc - K0[i * 8 + j]));
+      scale = std::max(scale, std::fabs(K0[i * 8 + j]));
+    }
+  }
+  return err <= 1e-14 * scale;
+}
+
+// Coarse mask by injection; check that every fixed fine DOF interpolates only from fixed coarse
+// DOFs (then the element-local Galerkin product of the unmasked operators equals the masked one).
+bool coarsen_mask(const Dims& df, const std::vector<uint8_t>& ff, std::vector<uint8_t>& fc,
+                  std::string& why) {
+  const int dim = df.dim;
+  Dims dc{df.nx / 2, df.ny / 2, dim == 3 ? df.nz / 2 : 1, dim};
+  fc.assign((size_t)dc.dofs(), 0);
+  const int fnx = df.nx + 1, fny = df.ny + 1, cnx = dc.nx + 1, cny = dc.ny + 1;
+  for (long long cn = 0; cn < dc.nodes(); ++cn) {
+    const int I = (int)(cn % cnx), J = (int)((cn / cnx) % cny), K = (int)(cn / ((long long)cnx * cny));
+    const long long fn = 2 * I + (long long)fnx * (2 * J + (long long)fny * 2 * K);
+    for (int c = 0; c < dim; ++c) fc[dim * cn + c] = ff[dim * fn + c] ? 1 : 0;
+  }
+  for (long long fnode = 0; fnode < df.nodes(); ++fnode) {
+    const int i = (int)(fnode % fnx), j = (int)((fnode / fnx) % fny), k = (int)(fnode / ((long long)fnx * fny));
+    for (int c = 0; c < dim; ++c) {
+      if (!ff[dim * fnode + c]) continue;
+      const int kmax = dim == 3 ? ((k + 1) >> 1) : 0;
+      for (int K = k >> 1; K <= kmax; ++K)
+        for (int J = j >> 1; J <= ((j + 1) >> 1); ++J)
+          for (int I = i >> 1; I <= ((i + 1) >> 1); ++I) {
+            const long long cn = I + (long long)cnx * (J + (long long)cny * K);
+            if (!fc[dim * cn + c]) {
+              why = "fixed DOF mask is not compatible with geometric coarsening";
+              return false;
+            }
+          }
+    }
+  }
+  return true;
+}
+
+template <typename T>
+struct Prec;
+template <>
+struct Prec<double> {
+  static const double* K0(topo_solver* s) { return s->K0; }
+  static const double* x(topo_solver* s) { return s->x; }
+  static const double* Ae(const Level& l) { return l.Ae; }
+  static const double* invd(const Level& l) { return l.invd; }
+};
+template <>
+struct Prec<float> {
+  static const float* K0(topo_solver* s) { return s->K0f; }
+  static const float* x(topo_solver* s) { return s->x32; }
+  static const float* Ae(const Level& l) { return l.Ae32; }
+  static const float* invd(const Level& l) { return l.invd32; }
+};
+
+// Operator application on level k (mode as launch_apply): the warp-sweep Q1 kernels on the 2D
+// finest level, the generic element-matrix kernels elsewhere.
+template <typename TV>
+topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* b, TV* y,
+                        const CgScalars* sc) {
+  Level& lv = s->L[k];
+  const TV omega = (TV)s->desc.omega;
+  if (k == 0 && s->q1_ok) {
+    TOPO_CUDA(launch_q1_apply<TV>(lv.d.nx, lv.d.ny, mode, s->q1, Prec<TV>::x(s), v, b, y, omega,
+                                  lv.fixed, s->nrhs, sc, s->st));
+    return TOPO_OK;
+  }
+  const TV* x = k == 0 ? Prec<TV>::x(s) : nullptr;
+  const TV* Ae = k == 0 ? nullptr : Prec<TV>::Ae(lv);
+  TOPO_CUDA(launch_apply<TV>(lv.d, mode, Prec<TV>::K0(s), x, Ae, v, b, y, Prec<TV>::invd(lv), omega,
+                             lv.fixed, s->nrhs, sc, s->st));
+  return TOPO_OK;
+}
+
+// One V-cycle at level k with right-hand side b (Algorithm MG, function mgm, from z = 0).
+template <typename TV>
+topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScalars* sc) {
+  Level& lv = s->L[k];
+  const int nrhs = s->nrhs;
+  TV* zk = (TV*)lv.z;
+  if (k == s->nlev - 1) {
+    TOPO_CUDA(launch_dense_solve<TV>(s->nc, s->Ainv, b, zk, nrhs, sc, s->st));
+    *result = zk;
+    return TOPO_OK;
+  }
+  TV* cur = zk;
+  TV* oth = (TV*)lv.t;
+  const int nu1 = s->desc.nu1, nu2 = s->desc.nu2;
+  if (nu1 >= 1) {
+    TOPO_TRY(apply_level<TV>(s, k, 3, cur, b, cur, sc));
+    for (int it = 1; it < nu1; ++it) {
+      TOPO_TRY(apply_level<TV>(s, k, 2, cur, b, oth, sc));
+      std::swap(cur, oth);
+    }
+  } else {
+    TOPO_CUDA(cudaMemsetAsync(cur, 0, sizeof(TV) * lv.n * nrhs, s->st));
+  }
+  TOPO_TRY(apply_level<TV>(s, k, 1, cur, b, oth, sc));
+  Level& lc = s->L[k + 1];
+  TOPO_CUDA(launch_restrict<TV>(lv.d, oth, (TV*)lc.b, lc.fixed, nrhs, sc, s->st));
+  TV* zc = nullptr;
+  TOPO_TRY(vcycle<TV>(s, k + 1, (const TV*)lc.b, &zc, sc));
+  TOPO_CUDA(launch_prolong_add<TV>(lv.d, zc, cur, lv.fixed, nrhs, sc, s->st));
+  for (int it = 0; it < nu2; ++it) {
+    TOPO_TRY(apply_level<TV>(s, k, 2, cur, b, oth, sc));
+    std::swap(cur, oth);
+  }
+  *result = cur;
+  return TOPO_OK;
+}
+
+// Preconditioner on the PCG residual r: y = M^{-1} r (result pointer returned).
+template <typename TV>
+topo_status precondition(topo_solver* s, const CgScalars* sc, void** y) {
+  TV* out = nullptr;
+  const TV* b = std::is_same<TV, double>::value ? (const TV*)s->r : (const TV*)s->rv;
+  TOPO_TRY(vcycle<TV>(s, 0, b, &out, sc));
+  *y = out;
+  return TOPO_OK;
+}
+
+// One PCG iteration (q = A p, update, precondition, new direction), enqueued on s->st.
+template <typename TV>
+topo_status cg_iteration(topo_solver* s, int slot, double tol, int max_iter) {
+  Level& l0 = s->L[0];
+  const long long n = l0.n;
+  // external event-record nodes: a plain record during capture only tracks dependencies
+  if (s->profiling)
+    TOPO_CUDA(cudaEventRecordWithFlags(s->prof_ev[2 * slot], s->st, cudaEventRecordExternal));
+  if (s->q1_ok)
+    TOPO_CUDA(launch_q1_apply_dot(l0.d.nx, l0.d.ny, s->q1, s->x, s->p, s->q, l0.fixed, s->nrhs,
+                                  s->partials, s->counters, s->sc, s->st));
+  else
+    TOPO_CUDA(launch_apply_dot_fine(l0.d, s->K0, s->x, s->p, s->q, l0.fixed, s->nrhs, s->partials,
+                                    s->counters, s->sc, s->st));
+  if (s->profiling)
+    TOPO_CUDA(cudaEventRecordWithFlags(s->prof_ev[2 * slot + 1], s->st, cudaEventRecordExternal));
+  TV* rv = std::is_same<TV, double>::value ? nullptr : (TV*)s->rv;
+  TOPO_CUDA(launch_cg_update<TV>(n, s->nrhs, s->z, s->r, s->p, s->q, rv, s->partials, s->counters,
+                                 s->sc, tol, max_iter, s->st));
+  void* y = nullptr;
+  TOPO_TRY(precondition<TV>(s, s->sc, &y));
+  s->yv = y;
+  TOPO_CUDA(launch_cg_direction<TV>(n, s->nrhs, s->r, (const TV*)y, s->p, (TV*)s->yold,
+                                    s->desc.flexible, s->partials, s->counters, s->sc, s->st));
+  return TOPO_OK;
+}
+
+// Capture whatever `body` enqueues on s->st into an executable graph; count its kernel nodes.
+template <typename F>
+topo_status capture(topo_solver* s, cudaGraphExec_t* exec, int* kernels, F body) {
+  if (*exec) {
+    cudaGraphExecDestroy(*exec);
+    *exec = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  TOPO_CUDA(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+  topo_status st = body();
+  cudaError_t e = cudaStreamEndCapture(s->st, &g);
+  if (st != TOPO_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
+  size_t nn = 0;
+  cudaGraphGetNodes(g, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+  int kn = 0;
+  for (size_t i = 0; i < nn; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kn;
+  }
+  *kernels = kn;
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_status(e, "cudaGraphInstantiate");
+  return TOPO_OK;
+}
+
+topo_status launch_graph(topo_solver* s, cudaGraphExec_t g, int kernels) {
+  TOPO_CUDA(cudaGraphLaunch(g, s->st));
+  s->launches += (unsigned long long)kernels;
+  return TOPO_OK;
+}
+
+template <typename TV>
+topo_status cg_setup(topo_solver* s, int use_x0, double tol, int max_iter) {
+  Level& l0 = s->L[0];
+  const long long n = l0.n;
+  const int nrhs = s->nrhs;
+  const double* Az = nullptr;
+  if (use_x0) {
+    TOPO_TRY(apply_level<double>(s, 0, 0, s->z, nullptr, s->q, nullptr));
+    Az = s->q;
+  }
+  TOPO_CUDA(launch_cg_init(n, nrhs, s->bbuf, s->z, s->r, Az, use_x0, s->partials, s->counters,
+                           s->sc, tol, max_iter, s->st));
+  if (!std::is_same<TV, double>::value)
+    TOPO_CUDA(launch_convert_d2f(s->r, (float*)s->rv, n * nrhs, s->st));
+  void* y = nullptr;
+  TOPO_TRY(precondition<TV>(s, s->sc, &y));
+  TOPO_CUDA(launch_cg_start_p<TV>(n, nrhs, s->r, (const TV*)y, s->p, (TV*)s->yold,
+                                  s->desc.flexible, s->partials, s->counters, s->sc, s->st));
+  return TOPO_OK;
+}
+
+template <typename TV>
+topo_status solve_impl(topo_solver* s, const double* b, double* u, double tol, int use_x0,
+                       topo_solve_info* info) {
+  Level& l0 = s->L[0];
+  const long long n = l0.n;
+  const int nrhs = s->nrhs;
+  const int max_iter = s->desc.max_iter;
+  const int ux = use_x0 ? 1 : 0;
+  // The graphs bake in tol and max_iter: recapture when the tolerance changes.
+  if (!s->setup[ux] || s->setup_tol[ux] != tol) {
+    TOPO_TRY(capture(s, &s->setup[ux], &s->setup_kernels[ux],
+                     [&]() { return cg_setup<TV>(s, ux, tol, max_iter); }));
+    s->setup_tol[ux] = tol;
+  }
+  if (!s->graph || s->graph_tol != tol) {
+    TOPO_TRY(capture(s, &s->graph, &s->graph_kernels, [&]() {
+      for (int it = 0; it < s->graph_iters; ++it) TOPO_TRY(cg_iteration<TV>(s, it, tol, max_iter));
+      return TOPO_OK;
+    }));
+    s->graph_tol = tol;
+  }
+  TOPO_CUDA(cudaEventRecord(s->ev_t0, s->st));
+  TOPO_CUDA(cudaMemcpyAsync(s->bbuf, b, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s->st));
+  if (use_x0)
+    TOPO_CUDA(cudaMemcpyAsync(s->z, u, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s->st));
+  TOPO_TRY(launch_graph(s, s->setup[ux], s->setup_kernels[ux]));
+  int blocks = 0;
+  const int max_blocks = (max_iter + s->graph_iters - 1) / s->graph_iters + 1;
+  bool all_done = false;
+  int iter_before = 0;
+  while (!all_done && blocks < max_blocks) {
+    TOPO_TRY(launch_graph(s, s->graph, s->graph_kernels));
+    ++blocks;
+    TOPO_CUDA(cudaMemcpyAsync(s->sc_host, s->sc, sizeof(CgScalars) * nrhs, cudaMemcpyDeviceToHost,
+                              s->st));
+    TOPO_CUDA(cudaStreamSynchronize(s->st));
+    all_done = true;
+    int iter_after = 0;
+    for (int k = 0; k < nrhs; ++k) {
+      all_done = all_done && s->sc_host[k].done;
+      iter_after = std::max(iter_after, s->sc_host[k].iter);
+    }
+    if (s->profiling) {
+      const int ran = std::min(iter_after - iter_before, s->graph_iters);
+      for (int slot = 0; slot < ran; ++slot) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, s->prof_ev[2 * slot], s->prof_ev[2 * slot + 1]) ==
+            cudaSuccess) {
+          s->prof_ms += ms;
+          s->prof_count += 1;
+        } else {
+          cudaGetLastError();  // timing unavailable: leave no sticky error behind
+        }
+      }
+    }
+    iter_before = iter_after;
+  }
+  TOPO_CUDA(cudaMemcpyAsync(u, s->z, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s->st));
+  TOPO_CUDA(cudaEventRecord(s->ev_t1, s->st));
+  TOPO_CUDA(cudaEventSynchronize(s->ev_t1));
+  topo_status worst = TOPO_OK;
+  int it_max = 0;
+  double rel_max = 0.0;
+  for (int k = 0; k < nrhs; ++k) {
+    const CgScalars& S = s->sc_host[k];
+    if (S.iter > it_max) it_max = S.iter;
+    if (S.rel > rel_max) rel_max = S.rel;
+    if (S.status != TOPO_OK && worst == TOPO_OK) worst = (topo_status)S.status;
+  }
+  if (info) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, s->ev_t0, s->ev_t1);
+    info->iterations = it_max;
+    info->rel_residual = rel_max;
+    info->wall_ms = ms;
+    info->status = worst;
+  }
+  if (worst == TOPO_E_NOT_CONVERGED) set_error("CG reached max_iter before the tolerance");
+  if (worst == TOPO_E_BREAKDOWN) set_error("CG breakdown (p^T A p <= 0 or a non-finite scalar)");
+  return worst;
+}
+
+topo_status enqueue_build(topo_solver* s) {
+  const int nl = s->nlev;
+  cudaStream_t st = s->st;
+  TOPO_CUDA(launch_check_positive(s->x, s->L[0].m, s->info + 1, st));
+  if (s->prec == TOPO_MIXED) TOPO_CUDA(launch_convert_d2f(s->x, s->x32, s->L[0].m, st));
+  for (int k = 1; k < nl; ++k) {
+    if (k == 1)
+      TOPO_CUDA(launch_rap_from_fine(s->L[0].d, s->C, s->x, s->L[1].Ae, st));
+    else
+      TOPO_CUDA(launch_rap_coarse(s->L[k - 1].d, s->L[k - 1].Ae, s->L[k].Ae, st));
+  }
+  for (int k = 0; k < nl - 1; ++k) {
+    Level& lv = s->L[k];
+    TOPO_CUDA(launch_inv_diag(lv.d, s->K0, k == 0 ? s->x : nullptr, lv.Ae, lv.fixed, lv.invd, st));
+    if (s->prec == TOPO_MIXED) {
+      TOPO_CUDA(launch_convert_d2f(lv.invd, lv.invd32, lv.n, st));
+      if (k >= 1) TOPO_CUDA(launch_convert_d2f(lv.Ae, lv.Ae32, lv.m * s->ne * s->ne, st));
+    }
+  }
+  Level& lc = s->L[nl - 1];
+  TOPO_CUDA(launch_assemble_dense(lc.d, s->K0, nl == 1 ? s->x : nullptr, lc.Ae, lc.fixed, s->Adense,
+                                  st));
+  TOPO_CUDA(launch_cholesky_inverse(s->nc, s->Adense, s->Ainv, s->info, st));
+  return TOPO_OK;
+}
+
+topo_status build_hierarchy(topo_solver* s) {
+  if (!s->build) TOPO_TRY(capture(s, &s->build, &s->build_kernels, [&]() { return enqueue_build(s); }));
+  TOPO_TRY(launch_graph(s, s->build, s->build_kernels));
+  int info_h[2] = {0, 0};
+  TOPO_CUDA(cudaMemcpyAsync(info_h, s->info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  TOPO_CUDA(cudaStreamSynchronize(s->st));
+  if (info_h[1]) {
+    set_error("topo_set_density: densities must be finite and > 0");
+    return TOPO_E_INVALID_ARG;
+  }
+  if (info_h[0]) {
+    set_error("coarsest operator is not positive definite (pivot " + std::to_string(info_h[0]) + ")");
+    return TOPO_E_BREAKDOWN;
+  }
+  return TOPO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* topo_last_error(void) { return g_last_error.c_str(); }
+
+topo_status topo_element_stiffness(int dim, double E, double nu, double* K0_out) {
+  if ((dim != 2 && dim != 3) || !K0_out || !(E > 0.0) || !(nu > -1.0 && nu < 0.5)) {
+    set_error("topo_element_stiffness: dim must be 2 or 3, E > 0, -1 < nu < 1/2");
+    return TOPO_E_INVALID_ARG;
+  }
+  element_stiffness_host(dim, E, nu, K0_out);
+  return TOPO_OK;
+}
+
+topo_status topo_solver_destroy(topo_solver* s) {
+  if (!s) return TOPO_OK;
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  for (int k = 0; k < 2; ++k)
+    if (s->setup[k]) cudaGraphExecDestroy(s->setup[k]);
+  if (s->build) cudaGraphExecDestroy(s->build);
+  for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
+  for (void* p : s->allocs) cudaFree(p);
+  if (s->sc_host) cudaFreeHost(s->sc_host);
+  if (s->dots_host) cudaFreeHost(s->dots_host);
+  if (s->ev_in) cudaEventDestroy(s->ev_in);
+  if (s->ev_out) cudaEventDestroy(s->ev_out);
+  if (s->ev_t0) cudaEventDestroy(s->ev_t0);
+  if (s->ev_t1) cudaEventDestroy(s->ev_t1);
+  if (s->st) cudaStreamDestroy(s->st);
+  delete s;
+  return TOPO_OK;
+}
+
+static topo_status create_impl(const topo_solver_desc* d, topo_solver* s) {
+  s->desc = *d;
+  s->dim = d->dim;
+  s->nlev = d->levels;
+  s->prec = d->precision;
+  s->nrhs = d->nrhs;
+  s->ne = d->dim == 2 ? 8 : 24;
+  TOPO_CUDA(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking));
+  TOPO_CUDA(cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming));
+  TOPO_CUDA(cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming));
+  TOPO_CUDA(cudaEventCreate(&s->ev_t0));
+  TOPO_CUDA(cudaEventCreate(&s->ev_t1));
+  const int ne = s->ne, nrhs = s->nrhs;
+  // element data
+  std::vector<double> K0(ne * ne), C;
+  element_stiffness_host(s->dim, d->E, d->nu, K0.data());
+  child_matrices(s->dim, K0.data(), C);
+  s->q1_ok = (s->dim == 2) && q1_coefficients(d->E, d->nu, K0.data(), s->q1) && !d->generic_kernels;
+  std::vector<float> K0f(K0.begin(), K0.end());
+  TOPO_TRY(s->alloc(&s->K0, ne * ne));
+  TOPO_TRY(s->alloc(&s->K0f, ne * ne));
+  TOPO_TRY(s->alloc(&s->C, C.size()));
+  TOPO_CUDA(cudaMemcpy(s->K0, K0.data(), sizeof(double) * ne * ne, cudaMemcpyHostToDevice));
+  TOPO_CUDA(cudaMemcpy(s->K0f, K0f.data(), sizeof(float) * ne * ne, cudaMemcpyHostToDevice));
+  TOPO_CUDA(cudaMemcpy(s->C, C.data(), sizeof(double) * C.size(), cudaMemcpyHostToDevice));
+  // levels and masks
+  Dims d0{d->nx, d->ny, d->dim == 3 ? d->nz : 1, d->dim};
+  s->L.resize(s->nlev);
+  std::vector<uint8_t> mask((size_t)d0.dofs());
+  for (long long i = 0; i < d0.dofs(); ++i) mask[i] = d->fixed[i] ? 1 : 0;
+  s->fixed_host = mask;
+  Dims dk = d0;
+  const size_t vbytes = s->prec == TOPO_MIXED ? sizeof(float) : sizeof(double);
+  for (int k = 0; k < s->nlev; ++k) {
+    Level& lv = s->L[k];
+    lv.d = dk;
+    lv.n = dk.dofs();
+    lv.m = dk.elems();
+    TOPO_TRY(s->alloc(&lv.fixed, lv.n));
+    TOPO_CUDA(cudaMemcpy(lv.fixed, mask.data(), lv.n, cudaMemcpyHostToDevice));
+    const bool coarsest = (k == s->nlev - 1);
+    if (k >= 1) {
+      TOPO_TRY(s->alloc(&lv.Ae, lv.m * ne * ne));
+      if (s->prec == TOPO_MIXED && !coarsest) TOPO_TRY(s->alloc(&lv.Ae32, lv.m * ne * ne));
+    }
+    if (!coarsest) {
+      TOPO_TRY(s->alloc(&lv.invd, lv.n));
+      if (s->prec == TOPO_MIXED) TOPO_TRY(s->alloc(&lv.invd32, lv.n));
+      TOPO_TRY(s->alloc((char**)&lv.t, vbytes * lv.n * nrhs));
+    }
+    if (k >= 1) TOPO_TRY(s->alloc((char**)&lv.b, vbytes * lv.n * nrhs));
+    TOPO_TRY(s->alloc((char**)&lv.z, vbytes * lv.n * nrhs));
+    if (!coarsest) {
+      std::vector<uint8_t> next;
+      std::string why;
+      if (!coarsen_mask(dk, mask, next, why)) {
+        set_error(why);
+        return TOPO_E_INVALID_ARG;
+      }
+      mask.swap(next);
+      dk = Dims{dk.nx / 2, dk.ny / 2, dk.dim == 3 ? dk.nz / 2 : 1, dk.dim};
+    }
+  }
+  Level& lc = s->L[s->nlev - 1];
+  s->nc = (int)lc.n;
+  TOPO_TRY(s->alloc(&s->Adense, (size_t)s->nc * s->nc));
+  TOPO_TRY(s->alloc(&s->Ainv, (size_t)s->nc * s->nc));
+  TOPO_TRY(s->alloc(&s->info, 2));
+  // densities and CG vectors
+  const long long n = s->L[0].n, m = s->L[0].m;
+  TOPO_TRY(s->alloc(&s->x, m));
+  if (s->prec == TOPO_MIXED) {
+    TOPO_TRY(s->alloc(&s->x32, m));
+    TOPO_TRY(s->alloc((float**)&s->rv, n * nrhs));
+  }
+  TOPO_TRY(s->alloc(&s->bbuf, n * nrhs));
+  TOPO_TRY(s->alloc(&s->z, n * nrhs));
+  TOPO_TRY(s->alloc(&s->r, n * nrhs));
+  TOPO_TRY(s->alloc(&s->p, n * nrhs));
+  TOPO_TRY(s->alloc(&s->q, n * nrhs));
+  if (d->flexible) TOPO_TRY(s->alloc((char**)&s->yold, vbytes * n * nrhs));
+  const long long pb = std::max<long long>(2LL * kRedBlocks, blocks_for(s->L[0].d.nodes()));
+  TOPO_TRY(s->alloc(&s->partials, pb * nrhs));
+  TOPO_TRY(s->alloc(&s->counters, nrhs));
+  TOPO_CUDA(cudaMemset(s->counters, 0, sizeof(unsigned) * nrhs));
+  TOPO_TRY(s->alloc(&s->sc, nrhs));
+  TOPO_CUDA(cudaMemset(s->sc, 0, sizeof(CgScalars) * nrhs));
+  TOPO_TRY(s->alloc(&s->dots, nrhs));
+  TOPO_CUDA(cudaMallocHost((void**)&s->sc_host, sizeof(CgScalars) * nrhs));
+  TOPO_CUDA(cudaMallocHost((void**)&s->dots_host, sizeof(double) * nrhs));
+  s->prof_ev.resize(2 * s->graph_iters);
+  for (auto& e : s->prof_ev) TOPO_CUDA(cudaEventCreate(&e));
+  TOPO_CUDA(cudaDeviceSynchronize());
+  return TOPO_OK;
+}
+
+topo_status topo_solver_create(const topo_solver_desc* d, topo_solver** out) {
+  if (!d || !out || !d->fixed) {
+    set_error("topo_solver_create: null argument");
+    return TOPO_E_INVALID_ARG;
+  }
+  *out = nullptr;
+  if ((d->dim != 2 && d->dim != 3) || d->nx < 1 || d->ny < 1 || (d->dim == 3 && d->nz < 1) ||
+      d->levels < 1 || d->levels > 16 || (d->precision != TOPO_FP64 && d->precision != TOPO_MIXED) ||
+      d->nu1 < 0 || d->nu2 < 0 || !(d->omega > 0.0 && d->omega <= 1.0) || d->max_iter < 0 ||
+      d->nrhs < 1 || d->nrhs > kMaxRhs || !(d->E > 0.0) || !(d->nu > -1.0 && d->nu < 0.5)) {
+    set_error("topo_solver_create: invalid descriptor field");
+    return TOPO_E_INVALID_ARG;
+  }
+  const int f = 1 << (d->levels - 1);
+  if (d->nx % f || d->ny % f || (d->dim == 3 && d->nz % f)) {
+    set_error("topo_solver_create: grid not divisible by 2^(levels-1)");
+    return TOPO_E_INVALID_ARG;
+  }
+  Dims dc{d->nx / f, d->ny / f, d->dim == 3 ? d->nz / f : 1, d->dim};
+  if (dc.dofs() > 4096) {
+    set_error("topo_solver_create: coarsest level has more than 4096 DOFs; use more levels");
+    return TOPO_E_INVALID_ARG;
+  }
+  topo_solver* s = new topo_solver();
+  topo_status st = create_impl(d, s);
+  if (st != TOPO_OK) {
+    std::string keep = g_last_error;
+    topo_solver_destroy(s);
+    g_last_error = keep;
+    return st;
+  }
+  *out = s;
+  return TOPO_OK;
+}
+
+topo_status topo_set_stream(topo_solver* s, void* stream) {
+  if (!s) return TOPO_E_INVALID_ARG;
+  s->user = (cudaStream_t)stream;
+  return TOPO_OK;
+}
+
+size_t topo_solver_device_bytes(const topo_solver* s) { return s ? s->bytes : 0; }
+
+unsigned long long topo_solver_launch_count(const topo_solver* s) { return s ? s->launches : 0; }
+
+topo_status topo_set_profiling(topo_solver* s, int on) {
+  if (!s) return TOPO_E_INVALID_ARG;
+  if ((bool)on != s->profiling) {
+    s->profiling = on != 0;
+    if (s->graph) {  // the iteration graph gains or loses its event nodes
+      cudaGraphExecDestroy(s->graph);
+      s->graph = nullptr;
+    }
+  }
+  s->prof_ms = 0.0;
+  s->prof_count = 0;
+  return TOPO_OK;
+}
+
+topo_status topo_get_profile(const topo_solver* s, double* operator_ms_total, long long* count) {
+  if (!s || !operator_ms_total || !count) return TOPO_E_INVALID_ARG;
+  *operator_ms_total = s->prof_ms;
+  *count = s->prof_count;
+  return TOPO_OK;
+}
+
+int topo_level_elems(const topo_solver* s, int level) {
+  if (!s || level < 0 || level >= s->nlev) return -1;
+  return (int)s->L[level].m;
+}
+
+topo_status topo_set_density(topo_solver* s, const double* x) {
+  if (!s || !x) {
+    set_error("topo_set_density: null argument");
+    return TOPO_E_INVALID_ARG;
+  }
+  StreamGuard g(s);
+  const long long m = s->L[0].m;
+  TOPO_CUDA(cudaMemcpyAsync(s->x, x, sizeof(double) * m, cudaMemcpyDeviceToDevice, s->st));
+  topo_status st = build_hierarchy(s);
+  s->have_density = (st == TOPO_OK);
+  return st;
+}
+
+topo_status topo_solve(topo_solver* s, const double* b, double* u, double tol, int use_x0,
+                       topo_solve_info* info) {
+  if (!s || !b || !u || !(tol >= 0.0)) {
+    set_error("topo_solve: invalid argument");
+    return TOPO_E_INVALID_ARG;
+  }
+  if (!s->have_density) {
+    set_error("topo_solve: call topo_set_density first");
+    return TOPO_E_INVALID_ARG;
+  }
+  StreamGuard g(s);
+  if (s->prec == TOPO_MIXED) return solve_impl<float>(s, b, u, tol, use_x0, info);
+  return solve_impl<double>(s, b, u, tol, use_x0, info);
+}
+
+topo_status topo_apply_K(topo_solver* s, const double* v, double* y) {
+  if (!s || !v || !y || !s->have_density) {
+    set_error("topo_apply_K: invalid argument or no density set");
+    return TOPO_E_INVALID_ARG;
+  }
+  StreamGuard g(s);
+  return apply_level<double>(s, 0, 0, v, nullptr, y, nullptr);
+}
+
+topo_status topo_apply_vcycle(topo_solver* s, const double* r, double* y) {
+  if (!s || !r || !y || !s->have_density) {
+    set_error("topo_apply_vcycle: invalid argument or no density set");
+    return TOPO_E_INVALID_ARG;
+  }
+  StreamGuard g(s);
+  const long long n = s->L[0].n * s->nrhs;
+  if (s->prec == TOPO_MIXED) {
+    TOPO_CUDA(launch_convert_d2f(r, (float*)s->rv, n, s->st));
+    float* out = nullptr;
+    TOPO_TRY(vcycle<float>(s, 0, (const float*)s->rv, &out, nullptr));
+    TOPO_CUDA(launch_convert_f2d(out, y, n, s->st));
+    return TOPO_OK;
+  }
+  TOPO_CUDA(cudaMemcpyAsync(s->r, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->st));
+  double* out = nullptr;
+  TOPO_TRY(vcycle<double>(s, 0, s->r, &out, nullptr));
+  TOPO_CUDA(cudaMemcpyAsync(y, out, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->st));
+  return TOPO_OK;
+}
+
+topo_status topo_get_level_matrices(topo_solver* s, int level, double* out_host) {
+  if (!s || !out_host || level < 1 || level >= s->nlev || !s->have_density) {
+    set_error("topo_get_level_matrices: level must be in [1, levels) after topo_set_density");
+    return TOPO_E_INVALID_ARG;
+  }
+  StreamGuard g(s);
+  const Level& lv = s->L[level];
+  TOPO_CUDA(cudaMemcpyAsync(out_host, lv.Ae, sizeof(double) * lv.m * s->ne * s->ne,
+                            cudaMemcpyDeviceToHost, s->st));
+  TOPO_CUDA(cudaStreamSynchronize(s->st));
+  return TOPO_OK;
+}
+
+topo_status topo_compliance(topo_solver* s, const double* f, const double* u, double* c) {
+  if (!s || !f || !u || !c) {
+    set_error("topo_compliance: null argument");
+    return TOPO_E_INVALID_ARG;
+  }
+  StreamGuard g(s);
+  TOPO_CUDA(launch_dot(s->L[0].n, s->nrhs, f, u, s->partials, s->counters, s->dots, s->st));
+  TOPO_CUDA(cudaMemcpyAsync(s->dots_host, s->dots, sizeof(double) * s->nrhs, cudaMemcpyDeviceToHost,
+                            s->st));
+  TOPO_CUDA(cudaStreamSynchronize(s->st));
+  for (int k = 0; k < s->nrhs; ++k) c[k] = s->dots_host[k];
+  return TOPO_OK;
+}
+
+topo_status topo_element_energy(topo_solver* s, const double* u, double* E) {
+  if (!s || !u || !E) {
+    set_error("topo_element_energy: null argument");
+    return TOPO_E_INVALID_ARG;
+  }
+  StreamGuard g(s);
+  TOPO_CUDA(launch_element_energy(s->L[0].d, s->K0, u, u, E, 1.0, s->st));
+  return TOPO_OK;
+}
+
+topo_status topo_grad_x(topo_solver* s, const double* lam, const double* u, double* gx) {
+  if (!s || !lam || !u || !gx) {
+    set_error("topo_grad_x: null argument");
+    return TOPO_E_INVALID_ARG;
+  }
+  StreamGuard g(s);
+  TOPO_CUDA(launch_element_energy(s->L[0].d, s->K0, u, lam, gx, -1.0, s->st));
+  return TOPO_OK;
+}
+
+}  // extern "C"

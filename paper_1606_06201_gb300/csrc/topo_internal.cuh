@@ -1,0 +1,162 @@
+// Internal definitions shared by the CUDA translation units of the topology-optimisation MGCG
+// library.  Grid conventions follow include/topo.h: x-fastest node and element numbering,
+// interleaved DOFs, counter-clockwise local nodes (bottom face then top face in 3D).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/topo.h"
+
+namespace topo {
+
+constexpr int kThreads = 256;         // threads per block of the node-parallel kernels
+constexpr int kRedBlocks = 4 * 152;   // blocks of the grid-stride reduction kernels (4 per SM)
+constexpr int kMaxRhs = 64;
+
+// Dimensions of one grid level.
+struct Dims {
+  int nx, ny, nz;  // elements per direction (nz = 1 in 2D so that products stay valid)
+  int dim;
+  __host__ __device__ int nnx() const { return nx + 1; }
+  __host__ __device__ int nny() const { return ny + 1; }
+  __host__ __device__ int nnz() const { return dim == 3 ? nz + 1 : 1; }
+  __host__ __device__ long long nodes() const { return (long long)nnx() * nny() * nnz(); }
+  __host__ __device__ long long dofs() const { return nodes() * dim; }
+  __host__ __device__ long long elems() const { return (long long)nx * ny * (dim == 3 ? nz : 1); }
+};
+
+// Scalars of one CG recurrence, device resident (one per right-hand side).
+struct CgScalars {
+  double ry;       // r^T y of the current iterate
+  double pq;       // p^T A p
+  double rr;       // r^T r
+  double ry_new;   // r~^T y~
+  double ry_old;   // r~^T y (flexible beta)
+  double bnorm;    // ||b||
+  double alpha, beta;
+  double rel;      // ||r|| / ||b||
+  int iter;
+  int done;        // 0 running, 1 stopped
+  int status;      // topo_status
+  int pad;
+};
+
+// Per-level data of the multigrid hierarchy.  Level 0 is the finest.
+struct Level {
+  Dims d;
+  long long n = 0, m = 0;          // DOFs, elements
+  uint8_t* fixed = nullptr;        // [n] 1 = fixed DOF
+  double* Ae = nullptr;            // coarse levels: element matrices [m][ne][ne] FP64
+  float* Ae32 = nullptr;           // FP32 copy (mixed precision)
+  double* invd = nullptr;          // 1 / diag(A) [n] (1 on fixed DOFs)
+  float* invd32 = nullptr;
+  void* b = nullptr;               // V-cycle right-hand side   [nrhs][n] (FP64 or FP32)
+  void* z = nullptr;               // V-cycle iterate
+  void* t = nullptr;               // ping-pong / residual scratch
+};
+
+// Coefficients of the 2D Q1 element matrix in its butterfly basis (kernels_q1.cu):
+// K0 = T^T Khat T with Khat built from c11, c12, c22 (normal block), c33 (shear), cH, cHp
+// (hourglass); kd = K0_ii (all diagonal entries are equal for the square element).
+struct Q1Coef {
+  double c11, c12, c22, c33, cH, cHp, kd;
+};
+
+// Host-side error reporting.
+void set_error(const std::string& msg);
+topo_status cuda_status(cudaError_t e, const char* what);
+
+#define TOPO_CUDA(call)                                         \
+  do {                                                          \
+    cudaError_t _e = (call);                                    \
+    if (_e != cudaSuccess) return topo::cuda_status(_e, #call); \
+  } while (0)
+
+#define TOPO_CHECK_LAUNCH(what)                                 \
+  do {                                                          \
+    cudaError_t _e = cudaGetLastError();                        \
+    if (_e != cudaSuccess) return topo::cuda_status(_e, what);  \
+  } while (0)
+
+inline unsigned blocks_for(long long n, int threads = kThreads) {
+  return (unsigned)((n + threads - 1) / threads);
+}
+
+// ---- kernels (launchers), defined in kernels_*.cu --------------------------------------------
+// Element stiffness on the host (2-point Gauss per direction).
+void element_stiffness_host(int dim, double E, double nu, double* K0);
+
+// Operator application on one level.  mode: 0 y = A v; 1 y = b - A v; 2 y = v + omega invd (b - A v);
+// 3 y = omega invd b (first Jacobi sweep from zero, v unused).  x != nullptr: finest level with
+// element matrices x_e K0; otherwise Ae holds element matrices.  nrhs vectors of length n.
+template <typename T>
+cudaError_t launch_apply(const Dims& d, int mode, const T* K0, const T* x, const T* Ae, const T* v,
+                         const T* b,
+                         T* y, const T* invd, T omega, const uint8_t* fixed, int nrhs,
+                         const CgScalars* sc, cudaStream_t st);
+// y = A v in FP64 on the finest level with a fused per-block partial of v^T y (for p^T A p).
+cudaError_t launch_apply_dot_fine(const Dims& d, const double* K0, const double* x, const double* v,
+                                  double* y,
+                                  const uint8_t* fixed, int nrhs, double* partials,
+                                  unsigned* counters, CgScalars* sc, cudaStream_t st);
+template <typename T>
+cudaError_t launch_restrict(const Dims& fine, const T* rf, T* rc, const uint8_t* fixed_c, int nrhs,
+                            const CgScalars* sc, cudaStream_t st);
+template <typename T>
+cudaError_t launch_prolong_add(const Dims& fine, const T* zc, T* zf, const uint8_t* fixed_f,
+                               int nrhs, const CgScalars* sc, cudaStream_t st);
+cudaError_t launch_inv_diag(const Dims& d, const double* K0, const double* x, const double* Ae,
+                            const uint8_t* fixed, double* invd, cudaStream_t st);
+cudaError_t launch_element_energy(const Dims& d, const double* K0, const double* u,
+                                  const double* lam, double* out, double scale, cudaStream_t st);
+
+// Finest-level 2D Q1 operator, warp-sweep kernels (kernels_q1.cu); same modes as launch_apply.
+template <typename T>
+cudaError_t launch_q1_apply(int nx, int ny, int mode, const Q1Coef& coef, const T* x, const T* v,
+                            const T* b, T* y, T omega, const uint8_t* fixed, int nrhs,
+                            const CgScalars* sc, cudaStream_t st);
+cudaError_t launch_q1_apply_dot(int nx, int ny, const Q1Coef& coef, const double* x,
+                                const double* v, double* y, const uint8_t* fixed, int nrhs,
+                                double* partials, unsigned* counters, CgScalars* sc,
+                                cudaStream_t st);
+long long q1_partial_blocks(int nx, int ny);
+
+// Hierarchy construction (kernels_rap.cu).
+cudaError_t launch_rap_from_fine(const Dims& fine, const double* C, const double* x, double* Ac,
+                                 cudaStream_t st);
+cudaError_t launch_rap_coarse(const Dims& fine, const double* Af, double* Ac, cudaStream_t st);
+cudaError_t launch_assemble_dense(const Dims& d, const double* K0, const double* x,
+                                  const double* Ae,
+                                  const uint8_t* fixed, double* A, cudaStream_t st);
+cudaError_t launch_cholesky_inverse(int n, double* A, double* Ainv, int* info, cudaStream_t st);
+template <typename T>
+cudaError_t launch_dense_solve(int n, const double* Ainv, const T* b, T* z, int nrhs,
+                               const CgScalars* sc, cudaStream_t st);
+cudaError_t launch_convert_d2f(const double* a, float* b, long long n, cudaStream_t st);
+cudaError_t launch_convert_f2d(const float* a, double* b, long long n, cudaStream_t st);
+cudaError_t launch_check_positive(const double* x, long long m, int* flag, cudaStream_t st);
+
+// CG vector kernels (kernels_pcg.cu).
+cudaError_t launch_cg_init(long long n, int nrhs, const double* b, double* z, double* r,
+                           const double* Az, int use_x0, double* partials, unsigned* counters,
+                           CgScalars* sc, double tol, int max_iter, cudaStream_t st);
+template <typename TV>
+cudaError_t launch_cg_start_p(long long n, int nrhs, const double* r, const TV* y, double* p,
+                              TV* y_old, int flexible, double* partials, unsigned* counters,
+                              CgScalars* sc, cudaStream_t st);
+template <typename TV>
+cudaError_t launch_cg_update(long long n, int nrhs, double* z, double* r, const double* p,
+                             const double* q, TV* rv, double* partials, unsigned* counters,
+                             CgScalars* sc, double tol, int max_iter, cudaStream_t st);
+template <typename TV>
+cudaError_t launch_cg_direction(long long n, int nrhs, const double* r, const TV* y, double* p,
+                                TV* y_old, int flexible, double* partials, unsigned* counters,
+                                CgScalars* sc, cudaStream_t st);
+cudaError_t launch_dot(long long n, int nrhs, const double* a, const double* b, double* partials,
+                       unsigned* counters, double* out, cudaStream_t st);
+
+}  // namespace topo

@@ -1,0 +1,209 @@
+"""ctypes binding of the C ABI in include/topo.h (argument marshalling only).
+
+Device arrays are torch CUDA tensors (FP64, contiguous); every computation runs in the CUDA
+library.  Importing this module loads ``libtopo_gb300.so`` and raises ImportError if it has not
+been built (``python -m paper_1606_06201_gb300.build``): there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtopo_gb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libtopo_gb300.so is missing: build it with "
+                      "`python -m paper_1606_06201_gb300.build` (nvcc, sm_103a)")
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, E_INVALID_ARG, E_NOT_CONVERGED, E_BREAKDOWN, E_INFEASIBLE, E_TIMEOUT, E_OOM, E_CUDA = range(8)
+FP64, MIXED = 0, 1
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_CONVERGED", 3: "BREAKDOWN", 4: "INFEASIBLE",
+                5: "TIMEOUT", 6: "OOM", 7: "CUDA"}
+
+
+class SolverDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nz", ctypes.c_int), ("E", ctypes.c_double), ("nu", ctypes.c_double),
+                ("fixed", ctypes.POINTER(ctypes.c_uint8)), ("levels", ctypes.c_int),
+                ("precision", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("omega", ctypes.c_double), ("max_iter", ctypes.c_int), ("nrhs", ctypes.c_int),
+                ("flexible", ctypes.c_int), ("generic_kernels", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("wall_ms", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+_vp = ctypes.c_void_p
+_SIGS = {
+    "topo_last_error": (ctypes.c_char_p, []),
+    "topo_element_stiffness": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, _vp]),
+    "topo_solver_create": (ctypes.c_int, [ctypes.POINTER(SolverDesc), ctypes.POINTER(_vp)]),
+    "topo_solver_destroy": (ctypes.c_int, [_vp]),
+    "topo_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "topo_solver_device_bytes": (ctypes.c_size_t, [_vp]),
+    "topo_solver_launch_count": (ctypes.c_ulonglong, [_vp]),
+    "topo_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "topo_get_profile": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_longlong)]),
+    "topo_set_density": (ctypes.c_int, [_vp, _vp]),
+    "topo_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int,
+                                  ctypes.POINTER(SolveInfo)]),
+    "topo_apply_K": (ctypes.c_int, [_vp, _vp, _vp]),
+    "topo_apply_vcycle": (ctypes.c_int, [_vp, _vp, _vp]),
+    "topo_get_level_matrices": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "topo_level_elems": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "topo_compliance": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "topo_element_energy": (ctypes.c_int, [_vp, _vp, _vp]),
+    "topo_grad_x": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class TopoError(RuntimeError):
+    def __init__(self, status, where):
+        msg = _lib.topo_last_error().decode(errors="replace")
+        super().__init__("%s: %s (%s)" % (where, STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def _check(status, where, allow=()):
+    if status != OK and status not in allow:
+        raise TopoError(status, where)
+    return status
+
+
+def _ptr(t):
+    """Device pointer of a contiguous FP64 CUDA tensor."""
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def element_stiffness(dim, E=1.0, nu=0.3):
+    ne = 8 if dim == 2 else 24
+    K0 = np.zeros((ne, ne))
+    _check(_lib.topo_element_stiffness(dim, E, nu, K0.ctypes.data_as(_vp)), "topo_element_stiffness")
+    return K0
+
+
+class Solver:
+    """MGCG solver for K(x) u = b on one structured grid (see include/topo.h)."""
+
+    def __init__(self, nx, ny, nz=0, fixed=None, levels=3, precision=FP64, nu1=2, nu2=2,
+                 omega=None, max_iter=1000, nrhs=1, flexible=None, E=1.0, nu=0.3,
+                 generic_kernels=False):
+        dim = 3 if nz else 2
+        n = dim * (nx + 1) * (ny + 1) * ((nz + 1) if nz else 1)
+        if fixed is None:
+            fixed = np.zeros(n, dtype=np.uint8)
+        self._fixed = np.ascontiguousarray(np.asarray(fixed, dtype=np.uint8))
+        if self._fixed.size != n:
+            raise ValueError("fixed mask has %d entries, expected %d" % (self._fixed.size, n))
+        if omega is None:
+            omega = 0.6 if dim == 2 else 0.5
+        if flexible is None:
+            flexible = 1 if precision == MIXED else 0
+        d = SolverDesc(dim, nx, ny, nz, E, nu,
+                       self._fixed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), levels,
+                       precision, nu1, nu2, omega, max_iter, nrhs, flexible, int(generic_kernels))
+        h = _vp()
+        _check(_lib.topo_solver_create(ctypes.byref(d), ctypes.byref(h)), "topo_solver_create")
+        self._h = h
+        self.dim, self.nx, self.ny, self.nz = dim, nx, ny, nz
+        self.n, self.m = n, nx * ny * (nz if nz else 1)
+        self.levels, self.precision, self.nrhs = levels, precision, nrhs
+        import torch
+        _check(_lib.topo_set_stream(self._h, _vp(torch.cuda.current_stream().cuda_stream)),
+               "topo_set_stream")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.topo_solver_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def device_bytes(self):
+        return int(_lib.topo_solver_device_bytes(self._h))
+
+    @property
+    def launch_count(self):
+        return int(_lib.topo_solver_launch_count(self._h))
+
+    def set_profiling(self, on):
+        _check(_lib.topo_set_profiling(self._h, int(bool(on))), "topo_set_profiling")
+
+    def profile(self):
+        """(summed ms, launches) of the outer operator kernel since set_profiling."""
+        ms, cnt = ctypes.c_double(), ctypes.c_longlong()
+        _check(_lib.topo_get_profile(self._h, ctypes.byref(ms), ctypes.byref(cnt)), "topo_get_profile")
+        return ms.value, cnt.value
+
+    def set_density(self, x):
+        _check(_lib.topo_set_density(self._h, _ptr(x)), "topo_set_density")
+
+    def solve(self, b, u=None, tol=1e-8, use_x0=False, allow_not_converged=False):
+        import torch
+        if u is None:
+            u = torch.zeros_like(b)
+        info = SolveInfo()
+        allow = (E_NOT_CONVERGED,) if allow_not_converged else ()
+        _check(_lib.topo_solve(self._h, _ptr(b), _ptr(u), float(tol), int(bool(use_x0)),
+                               ctypes.byref(info)), "topo_solve", allow)
+        return u, info
+
+    def apply_K(self, v, y=None):
+        import torch
+        y = torch.empty_like(v) if y is None else y
+        _check(_lib.topo_apply_K(self._h, _ptr(v), _ptr(y)), "topo_apply_K")
+        return y
+
+    def apply_vcycle(self, r, y=None):
+        import torch
+        y = torch.empty_like(r) if y is None else y
+        _check(_lib.topo_apply_vcycle(self._h, _ptr(r), _ptr(y)), "topo_apply_vcycle")
+        return y
+
+    def level_matrices(self, level):
+        m = _lib.topo_level_elems(self._h, level)
+        ne = 8 if self.dim == 2 else 24
+        out = np.zeros((m, ne, ne))
+        _check(_lib.topo_get_level_matrices(self._h, level, out.ctypes.data_as(_vp)),
+               "topo_get_level_matrices")
+        return out
+
+    def compliance(self, f, u):
+        c = np.zeros(self.nrhs)
+        _check(_lib.topo_compliance(self._h, _ptr(f), _ptr(u), c.ctypes.data_as(_vp)),
+               "topo_compliance")
+        return c
+
+    def element_energy(self, u, out=None):
+        import torch
+        out = torch.empty(self.m, dtype=torch.float64, device=u.device) if out is None else out
+        _check(_lib.topo_element_energy(self._h, _ptr(u), _ptr(out)), "topo_element_energy")
+        return out
+
+    def grad_x(self, lam, u, out=None):
+        import torch
+        out = torch.empty(self.m, dtype=torch.float64, device=u.device) if out is None else out
+        _check(_lib.topo_grad_x(self._h, _ptr(lam), _ptr(u), _ptr(out)), "topo_grad_x")
+        return out
+
+
+def exported_symbols():
+    """Names of the C-ABI entry points this binding expects (for the symbol check)."""
+    return sorted(_SIGS)

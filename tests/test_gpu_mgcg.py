@@ -1,0 +1,224 @@
+"""CUDA path against the CPU oracle through the C ABI: the matrix-free operator K(x) v, Galerkin
+coarse operators, one V-cycle (Algorithm MG), the full MGCG solve (Algorithm PCG) in FP64 and
+mixed precision, batched right-hand sides, element energies and the adjoint gradient."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import fe, mg
+from oracle.linsolve import SPDSolver
+from paper_1606_06201_gb300 import workloads as W
+
+from gpu_helpers import dev, host, oracle_hierarchy, oracle_K_free, rel_err, topo_lib, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+SHAPES_2D = [(1, 1, 0, 1), (2, 1, 0, 1), (6, 4, 0, 2), (16, 8, 0, 3), (64, 32, 0, 3), (96, 40, 0, 4)]
+SHAPES_3D = [(2, 2, 2, 2), (4, 2, 2, 2), (6, 4, 2, 2), (8, 4, 4, 3)]
+
+
+def _x(nx, ny, nz, seed=11):
+    shape = (nz, ny, nx) if nz else (ny, nx)
+    return W.log_uniform_field(shape, seed)
+
+
+@pytest.mark.parametrize("generic", [False, True])
+@pytest.mark.parametrize("shape", SHAPES_2D + SHAPES_3D + [(61, 33, 0, 1), (200, 50, 0, 2)])
+def test_apply_K_matches_assembled(shape, generic):
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny, nz, levels = shape
+    fixed = W.clamp_xmin(nx, ny, nz)
+    x = _x(nx, ny, nz)
+    s = topo.Solver(nx, ny, nz, fixed=fixed, levels=levels, generic_kernels=generic)
+    s.set_density(dev(torch, x))
+    v = W.random_vector(s.n, 3, fixed)
+    y = host(s.apply_K(dev(torch, v)))
+    K, free, _ = oracle_K_free(nx, ny, nz, x, fixed.astype(bool))
+    ref = np.zeros(s.n)
+    ref[free] = K @ v[free]
+    assert np.all(y[fixed.astype(bool)] == 0.0)
+    np.testing.assert_allclose(y, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("shape", [(16, 8, 0, 3), (64, 32, 0, 4), (8, 4, 4, 3)])
+def test_galerkin_level_matrices_match_sparse_rap(shape):
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny, nz, levels = shape
+    fixed = W.clamp_xmin(nx, ny, nz)
+    x = _x(nx, ny, nz, 12)
+    s = topo.Solver(nx, ny, nz, fixed=fixed, levels=levels)
+    s.set_density(dev(torch, x))
+    levs, _, _, _ = oracle_hierarchy(nx, ny, nz, x, fixed, levels)
+    g = fe.Grid(nx, ny, nz)
+    fx = fixed.astype(bool)
+    for k in range(1, levels):
+        from oracle.mg import coarse_fixed
+        g, fx = coarse_fixed(g, fx)
+        Ae = s.level_matrices(k)
+        free = fe.free_dofs(fx)
+        A = fe.assemble_elementwise(g, Ae)[free][:, free].toarray()
+        ref = levs[k].A.toarray()
+        np.testing.assert_allclose(A, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("generic", [False, True])
+@pytest.mark.parametrize("shape", [(16, 8, 0, 3), (64, 32, 0, 3), (96, 40, 0, 4), (8, 4, 4, 3)])
+@pytest.mark.parametrize("nu", [(2, 2), (1, 1), (0, 1)])
+def test_vcycle_fp64_matches_oracle(shape, nu, generic):
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny, nz, levels = shape
+    fixed = W.clamp_xmin(nx, ny, nz)
+    x = _x(nx, ny, nz, 13)
+    omega = 0.6 if not nz else 0.5
+    s = topo.Solver(nx, ny, nz, fixed=fixed, levels=levels, nu1=nu[0], nu2=nu[1], omega=omega,
+                    generic_kernels=generic)
+    s.set_density(dev(torch, x))
+    levs, free, _, _ = oracle_hierarchy(nx, ny, nz, x, fixed, levels)
+    r = W.random_vector(s.n, 5, fixed)
+    y = host(s.apply_vcycle(dev(torch, r)))
+    ref = np.zeros(s.n)
+    ref[free] = mg.vcycle(levs, r[free], nu[0], nu[1], omega)
+    assert rel_err(y, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("shape", [(64, 32, 0, 3), (128, 64, 0, 5), (8, 4, 4, 2)])
+def test_vcycle_mixed_close_to_fp64(shape):
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny, nz, levels = shape
+    fixed = W.clamp_xmin(nx, ny, nz)
+    x = _x(nx, ny, nz, 14)
+    s64 = topo.Solver(nx, ny, nz, fixed=fixed, levels=levels)
+    s32 = topo.Solver(nx, ny, nz, fixed=fixed, levels=levels, precision=topo.MIXED)
+    xd = dev(torch, x)
+    s64.set_density(xd)
+    s32.set_density(xd)
+    r = dev(torch, W.random_vector(s64.n, 6, fixed))
+    assert rel_err(host(s32.apply_vcycle(r)), host(s64.apply_vcycle(r))) <= 1e-4
+
+
+def _solve_case(torch, topo, nx, ny, nz, levels, precision, tol, seed=21):
+    fixed = W.clamp_xmin(nx, ny, nz)
+    x = _x(nx, ny, nz, seed)
+    f = W.normal_load(fixed, seed + 1)
+    s = topo.Solver(nx, ny, nz, fixed=fixed, levels=levels, precision=precision)
+    s.set_density(dev(torch, x))
+    u, info = s.solve(dev(torch, f), tol=tol)
+    K, free, grid = oracle_K_free(nx, ny, nz, x, fixed.astype(bool))
+    exact = np.zeros(s.n)
+    exact[free] = SPDSolver(K, grid, free).solve(f[free])
+    return host(u), exact, f, info, s
+
+
+@pytest.mark.parametrize("shape", [(64, 32, 0, 3), (96, 40, 0, 4), (256, 128, 0, 6), (8, 4, 4, 3)])
+def test_solve_fp64_matches_cholesky(shape):
+    torch = torch_cuda()
+    topo = topo_lib()
+    u, exact, f, info, _ = _solve_case(torch, topo, *shape, topo.FP64, 1e-13)
+    assert info.status == topo.OK and info.rel_residual <= 1e-13
+    assert rel_err(u, exact) <= 1e-10
+    assert abs(f @ u - f @ exact) <= 1e-10 * abs(f @ exact)
+
+
+@pytest.mark.parametrize("shape", [(64, 32, 0, 3), (256, 128, 0, 6), (8, 4, 4, 3)])
+def test_solve_mixed_matches_cholesky(shape):
+    torch = torch_cuda()
+    topo = topo_lib()
+    u, exact, f, info, _ = _solve_case(torch, topo, *shape, topo.MIXED, 1e-8)
+    assert info.status == topo.OK and info.rel_residual <= 1e-8
+    assert rel_err(u, exact) <= 1e-6
+    assert abs(f @ u - f @ exact) <= 1e-6 * abs(f @ exact)
+
+
+def test_solve_warm_start_and_zero_rhs():
+    torch = torch_cuda()
+    topo = topo_lib()
+    u, exact, f, info, s = _solve_case(torch, topo, 64, 32, 0, 3, topo.FP64, 1e-10)
+    u2, info2 = s.solve(dev(torch, f), u=dev(torch, u), tol=1e-10, use_x0=True)
+    assert info2.iterations <= 1
+    z, info3 = s.solve(dev(torch, np.zeros(s.n)), tol=1e-8)
+    assert info3.iterations == 0 and float(host(z).max()) == 0.0
+
+
+def test_batched_rhs_equal_individual_solves():
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny = 64, 32
+    fixed = W.clamp_xmin(nx, ny)
+    x = dev(torch, _x(nx, ny, 0, 31))
+    F = np.stack([W.normal_load(fixed, 40 + k) for k in range(3)])
+    sb = topo.Solver(nx, ny, fixed=fixed, levels=3, nrhs=3)
+    sb.set_density(x)
+    U, info = sb.solve(dev(torch, F), tol=1e-12)
+    s1 = topo.Solver(nx, ny, fixed=fixed, levels=3)
+    s1.set_density(x)
+    for k in range(3):
+        u, _ = s1.solve(dev(torch, F[k]), tol=1e-12)
+        np.testing.assert_allclose(host(U)[k], host(u), rtol=0, atol=1e-14 * np.abs(host(u)).max())
+
+
+def test_energy_gradient_and_compliance():
+    torch = torch_cuda()
+    topo = topo_lib()
+    u, exact, f, info, s = _solve_case(torch, topo, 16, 8, 0, 2, topo.FP64, 1e-13)
+    grid = fe.Grid(16, 8)
+    K0 = fe.element_stiffness(2)
+    ud = dev(torch, u)
+    E = host(s.element_energy(ud))
+    ue = fe.element_values(grid, u)
+    # rounding bound of a bilinear form: a few ulps of |u_e|^T |K0| |u_e| (cancellation-free scale)
+    scale_u = np.einsum("ei,ij,ej->e", np.abs(ue), np.abs(K0), np.abs(ue))
+    assert np.all(np.abs(E - fe.element_energy(grid, K0, u)) <= 64 * 2.2e-16 * scale_u + 1e-300)
+    w = W.random_vector(s.n, 9, W.clamp_xmin(16, 8))
+    g = host(s.grad_x(dev(torch, w), ud))
+    we = fe.element_values(grid, w)
+    ref = -np.einsum("ei,ij,ej->e", we, K0, ue)
+    scale_w = np.einsum("ei,ij,ej->e", np.abs(we), np.abs(K0), np.abs(ue))
+    assert np.all(np.abs(g - ref) <= 64 * 2.2e-16 * scale_w + 1e-300)
+    c = s.compliance(dev(torch, f), ud)
+    assert abs(c[0] - f @ u) <= 1e-14 * (np.abs(f) @ np.abs(u))
+
+
+def test_invalid_density_and_breakdown_paths():
+    torch = torch_cuda()
+    topo = topo_lib()
+    s = topo.Solver(16, 8, fixed=W.clamp_xmin(16, 8), levels=2)
+    bad = np.full(128, 0.5)
+    bad[3] = np.nan
+    with pytest.raises(topo.TopoError) as e:
+        s.set_density(dev(torch, bad))
+    assert e.value.status == topo.E_INVALID_ARG
+    bad[3] = -1.0
+    with pytest.raises(topo.TopoError):
+        s.set_density(dev(torch, bad))
+    s.set_density(dev(torch, np.full(128, 0.5)))
+    f = dev(torch, W.normal_load(W.clamp_xmin(16, 8), 3))
+    # max_iter = 1 cannot reach 1e-12: NOT_CONVERGED, with the iterate still returned
+    s1 = topo.Solver(16, 8, fixed=W.clamp_xmin(16, 8), levels=2, max_iter=1)
+    s1.set_density(dev(torch, np.full(128, 0.5)))
+    u, info = s1.solve(f, tol=1e-12, allow_not_converged=True)
+    assert info.status == topo.E_NOT_CONVERGED and info.iterations == 1
+    with pytest.raises(topo.TopoError):
+        s1.solve(f, tol=1e-12)
+
+
+def test_full_size_standalone_solve_residual():
+    """2048 x 1024 grid (4.2M DOFs, 9 levels) in the timed configuration: the true residual of the
+    returned u, by the oracle's sparse matrix, meets the tolerance in both precisions."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    cfg = W.random_field_2d(2048, 1024)
+    K, free, _ = oracle_K_free(2048, 1024, 0, cfg["x"], cfg["fixed"].astype(bool))
+    f = cfg["f"]
+    for prec in (topo.FP64, topo.MIXED):
+        s = topo.Solver(2048, 1024, fixed=cfg["fixed"], levels=9, precision=prec)
+        s.set_density(dev(torch, cfg["x"]))
+        u, info = s.solve(dev(torch, f), tol=1e-8)
+        uh = host(u)
+        res = np.linalg.norm(f[free] - K @ uh[free]) / np.linalg.norm(f[free])
+        assert info.status == topo.OK
+        assert res <= 2e-8, (prec, res, info.iterations)
+        s.close()
