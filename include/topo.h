@@ -140,6 +140,97 @@ topo_status topo_element_energy(topo_solver* s, const double* u, double* E);
  * lam, u [device, n], g [device, m]. */
 topo_status topo_grad_x(topo_solver* s, const double* lam, const double* u, double* g);
 
+/* ---- Primal-dual interior-point method (Sec. 2-3) ----------------------------------------
+ * Newton steps on the KKT conditions KKT1-3 with the perturbed complementarity KKT4p/5p,
+ * reduced to the SPD augmented system Z [d_u; d_lambda] = Res^Z of Eq. (nwtr2)-(nwtr2rhs), which
+ * is solved by MGCG with the lambda unknown carried to every level by the identity (Sec. 7).
+ * Readings: row 3 of Eq. (nwt) uses the right-hand side -1/2 u^T K_i u - lambda - phi_i + psi_i;
+ * d_psi = (xbar - x)^{-1} (Res5 + Psi d_x); d_x = D^{-1} (B^T d_u + e d_lambda - tilde Res3);
+ * Euclidean norms in the Newton test, evaluated at the new iterate. */
+typedef struct topo_ip topo_ip;
+
+typedef struct {
+  double sigma;        /* barrier reduction (Sec. 3.2: 0.2) */
+  double tau_nwt;      /* Newton stopping tolerance (Sec. 3.4: 0.1) */
+  double tau_ip;       /* IP stopping tolerance on max(s, r) (Sec. 3.4: 1e-8) */
+  double frac;         /* fraction to the boundary (Sec. 3.3: 0.9) */
+  int step_x_only;     /* 1: the step rule bounds x only (the literal Sec. 3.3); 0: also phi, psi */
+  int max_newton;      /* Newton step budget */
+  double cg_tol;       /* relative residual for the Z systems (Sec. 6.1 uses 1e-2) */
+  double cg_tol_init;  /* relative residual of the initial K(x) u = f solve (<= 0: cg_tol) */
+} topo_ip_opts;
+
+typedef struct {
+  int newton;          /* Newton steps so far */
+  int ip_iters;        /* barrier reductions so far */
+  int feval;           /* linear systems solved (initial solve included) */
+  int cg_iters;        /* CG iterations over all systems */
+  double s, r, lam, alpha, crit; /* barrier parameters, multiplier, last step, Newton test value */
+  int done;            /* 1 once max(s, r) <= tau_IP */
+  int status;
+  double wall_ms;      /* topo_ip_run: elapsed time of the run */
+} topo_ip_info;
+
+/* f [device, n], copied.  Returns TOPO_E_INFEASIBLE unless 0 < V < m xbar. */
+topo_status topo_ip_create(const topo_solver_desc* desc, const double* f, double V, double xbar,
+                           topo_ip** out);
+topo_status topo_ip_destroy(topo_ip* ip);
+topo_status topo_ip_set_stream(topo_ip* ip, void* cuda_stream);
+/* x = V/m, u = K(x)^{-1} f, lambda = 1, phi = psi = e, s = r = 1 (Sec. 3.1). */
+topo_status topo_ip_init(topo_ip* ip, const topo_ip_opts* opts);
+/* One Newton step (Sec. 3.1 steps 1-4); info after the step. */
+topo_status topo_ip_step(topo_ip* ip, const topo_ip_opts* opts, topo_ip_info* info);
+/* init + steps until max(s, r) <= tau_IP or max_newton steps. */
+topo_status topo_ip_run(topo_ip* ip, const topo_ip_opts* opts, topo_ip_info* info);
+/* Checkpoint / resume: u [device, n], x, phi, psi [device, m], scal [host, 3] = lambda, s, r. */
+topo_status topo_ip_get_state(topo_ip* ip, double* u, double* x, double* phi, double* psi,
+                              double* scal);
+topo_status topo_ip_set_state(topo_ip* ip, const double* u, const double* x, const double* phi,
+                              const double* psi, const double* scal);
+
+/* ---- Optimality Conditions methods (Sec. 4) ----------------------------------------------
+ * OC: u = K(x)^{-1} f, E_i = u^T K_i u, bisection on lambda in [0, lam_hi] until the interval is
+ * <= tau_lambda, x^NEW = min(max(x E / lambda, xlow), xbar) with x fixed during the bisection and
+ * the sum compared with V after a single rounding of an error-free (double-double) reduction.
+ * DOC: E replaced by E^q.  AOC: x <- (OC(x) + OC(OC(x))) / 2.  The CG tolerance starts at cg_tol0
+ * and, if adaptive_tol, is divided by 10 whenever the compliance increases (Sec. 6.2).
+ * The linear systems are warm-started from the previous displacement. */
+typedef struct topo_oc topo_oc;
+enum { TOPO_OC_PLAIN = 0, TOPO_OC_DOC = 1, TOPO_OC_AOC = 2 };
+
+typedef struct {
+  int variant;         /* TOPO_OC_PLAIN, TOPO_OC_DOC or TOPO_OC_AOC */
+  double q;            /* DOC damping exponent (Sec. 4.2: 1/2) */
+  double xlow;         /* lower bound keeping K(x) nonsingular (Sec. 9.2: 1e-6) */
+  double lam_hi;       /* initial upper end of the bisection (Sec. 4.1: 1e4) */
+  double tau_lambda;   /* bisection tolerance (Sec. 4.1: 1e-11) */
+  double tau_oc;       /* stop when |f^T u_k - f^T u_{k-1}| <= tau_oc (Eq. (OCstop): 1e-5) */
+  int max_feval;       /* linear-solve budget */
+  double cg_tol0;      /* initial CG tolerance (Sec. 6.2: 1e-4) */
+  int adaptive_tol;    /* 1: the Sec. 6.2 heuristic */
+} topo_oc_opts;
+
+typedef struct {
+  int iters, feval, cg_iters;
+  double compliance;       /* f^T u at the iterate of the last step (before its update) */
+  double compliance_prev;
+  double lam;              /* last bisection midpoint */
+  double cg_tol;
+  int status;
+  double wall_ms;          /* topo_oc_run: elapsed time */
+} topo_oc_info;
+
+topo_status topo_oc_create(const topo_solver_desc* desc, const double* f, double V, double xbar,
+                           topo_oc** out);
+topo_status topo_oc_destroy(topo_oc* oc);
+topo_status topo_oc_set_stream(topo_oc* oc, void* cuda_stream);
+/* x0 [device, m] or NULL for x = V/m. */
+topo_status topo_oc_init(topo_oc* oc, const double* x0);
+topo_status topo_oc_step(topo_oc* oc, const topo_oc_opts* opts, topo_oc_info* info);
+topo_status topo_oc_run(topo_oc* oc, const topo_oc_opts* opts, topo_oc_info* info);
+topo_status topo_oc_get_x(topo_oc* oc, double* x);
+topo_status topo_oc_get_u(topo_oc* oc, double* u);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,9 @@ template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
 // Sum over the elements around node (i,j,k) of rows (loc*DIM + c) of the element matrix times
-// the element's DOF values.  FINE: element matrix x_e K0; otherwise Ae[e].
+// the element's DOF values.  FINE: element matrix x_e K0; otherwise the Galerkin element matrices
+// stored entry-major, Ae[(row * NE + col) * m + e], so that a warp reading one entry of 32
+// consecutive elements reads contiguous memory.
 template <int DIM, typename T, bool FINE>
 __device__ __forceinline__ void node_apply(const Dims& d, int i, int j, int k,
                                            const T* __restrict__ K0, const T* __restrict__ x,
@@ -39,6 +41,7 @@ __device__ __forceinline__ void node_apply(const Dims& d, int i, int j, int k,
                                            T acc[DIM]) {
   constexpr int NN = Elem<DIM>::NN, NE = Elem<DIM>::NE;
   const int nnx = d.nx + 1, nny = d.ny + 1;
+  const long long m = d.elems();
 #pragma unroll
   for (int c = 0; c < DIM; ++c) acc[c] = T(0);
 #pragma unroll 1
@@ -57,15 +60,20 @@ __device__ __forceinline__ void node_apply(const Dims& d, int i, int j, int k,
 #pragma unroll
       for (int c = 0; c < DIM; ++c) ve[a * DIM + c] = ldg(v + DIM * nid + c);
     }
-    const T* A = FINE ? K0 : Ae + e * (NE * NE);
-    const T scale = FINE ? ldg(x + e) : T(1);
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
-      const T* row = A + (loc * DIM + c) * NE;
       T t = T(0);
+      if (FINE) {
+        const T* row = K0 + (loc * DIM + c) * NE;
 #pragma unroll
-      for (int q = 0; q < NE; ++q) t = fma(ldg(row + q), ve[q], t);
-      acc[c] = fma(scale, t, acc[c]);
+        for (int q = 0; q < NE; ++q) t = fma(ldg(row + q), ve[q], t);
+        acc[c] = fma(ldg(x + e), t, acc[c]);
+      } else {
+        const T* row = Ae + (long long)((loc * DIM + c) * NE) * m + e;
+#pragma unroll
+        for (int q = 0; q < NE; ++q) t = fma(ldg(row + (long long)q * m), ve[q], t);
+        acc[c] += t;
+      }
     }
   }
 }
@@ -79,7 +87,8 @@ __global__ void __launch_bounds__(kThreads) k_apply(Dims d, const T* __restrict_
                                                     const T* __restrict__ b, T* __restrict__ y,
                                                     const T* __restrict__ invd, T omega,
                                                     const uint8_t* __restrict__ fixed,
-                                                    const CgScalars* __restrict__ sc) {
+                                                    const CgScalars* __restrict__ sc,
+                                                    const T* __restrict__ w) {
   const int rhs = blockIdx.y;
   if (sc && sc[rhs].done) return;
   const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -94,7 +103,14 @@ __global__ void __launch_bounds__(kThreads) k_apply(Dims d, const T* __restrict_
   b += rhs * n;
   y += rhs * n;
   T acc[DIM];
-  if (MODE != 3) node_apply<DIM, T, FINE>(d, i, j, k, K0, x, Ae, v, acc);
+  if (MODE != 3) {
+    node_apply<DIM, T, FINE>(d, i, j, k, K0, x, Ae, v, acc);
+    if (w) {
+      const T vl = v[n];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) acc[c] = fma(w[DIM * node + c], vl, acc[c]);
+    }
+  }
 #pragma unroll
   for (int c = 0; c < DIM; ++c) {
     const long long id = DIM * node + c;
@@ -114,17 +130,84 @@ __global__ void __launch_bounds__(kThreads) k_apply(Dims d, const T* __restrict_
   }
 }
 
+// First coarse level of the 2D grid without stored element matrices: the Galerkin element matrix
+// of coarse element E is sum_c x_c C_c over its four children (C_c = P_c^T K0 P_c), so
+// (A v)_node = sum_{E at node} sum_c x_c (C_c v_E)_row.  xf: densities of the finest level.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) k_apply_l1(Dims d, const T* __restrict__ C,
+                                                       const T* __restrict__ xf,
+                                                       const T* __restrict__ v,
+                                                       const T* __restrict__ b, T* __restrict__ y,
+                                                       const T* __restrict__ invd, T omega,
+                                                       const uint8_t* __restrict__ fixed,
+                                                       const CgScalars* __restrict__ sc) {
+  constexpr int NE = 8, NE2 = 64;
+  const int rhs = blockIdx.y;
+  if (sc && sc[rhs].done) return;
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nodes = d.nodes();
+  if (node >= nodes) return;
+  const long long n = nodes * 2;
+  const int nnx = d.nx + 1;
+  const int i = (int)(node % nnx), j = (int)(node / nnx);
+  v += rhs * n;
+  b += rhs * n;
+  y += rhs * n;
+  T acc[2] = {T(0), T(0)};
+  const int fnx = 2 * d.nx;
+  if (MODE != 3) {
+#pragma unroll 1
+    for (int s = 0; s < 4; ++s) {
+      const int dx = s & 1, dy = s >> 1;
+      const int ex = i - 1 + dx, ey = j - 1 + dy;
+      if (ex < 0 || ex >= d.nx || ey < 0 || ey >= d.ny) continue;
+      const int loc = loc_of(1 - dx, 1 - dy, 0);
+      T ve[NE];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const long long nid = (ex + loc_ox(a)) + (long long)nnx * (ey + loc_oy(a));
+        ve[2 * a] = ldg(v + 2 * nid);
+        ve[2 * a + 1] = ldg(v + 2 * nid + 1);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const long long fe = (2 * ex + (c & 1)) + (long long)fnx * (2 * ey + (c >> 1));
+        const T xc = ldg(xf + fe);
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const T* row = C + c * NE2 + (loc * 2 + cc) * NE;
+          T t = T(0);
+#pragma unroll
+          for (int q = 0; q < NE; ++q) t = fma(ldg(row + q), ve[q], t);
+          acc[cc] = fma(xc, t, acc[cc]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const long long id = 2 * node + c;
+    T out;
+    if (fixed[id]) out = T(0);
+    else if (MODE == 0) out = acc[c];
+    else if (MODE == 1) out = b[id] - acc[c];
+    else if (MODE == 2) out = v[id] + omega * invd[id] * (b[id] - acc[c]);
+    else out = omega * invd[id] * b[id];
+    y[id] = out;
+  }
+}
+
 template <int DIM, typename T, int MODE>
 void apply_dispatch(const Dims& d, const T* K0, const T* x, const T* Ae, const T* v, const T* b,
                     T* y, const T* invd, T omega, const uint8_t* fixed, int nrhs,
-                    const CgScalars* sc, cudaStream_t st) {
+                    const CgScalars* sc, cudaStream_t st, const T* w) {
   dim3 grid(blocks_for(d.nodes()), nrhs);
   if (x)
     k_apply<DIM, T, MODE, true><<<grid, kThreads, 0, st>>>(d, K0, x, Ae, v, b, y, invd, omega,
-                                                           fixed, sc);
+                                                           fixed, sc, w);
   else
     k_apply<DIM, T, MODE, false><<<grid, kThreads, 0, st>>>(d, K0, x, Ae, v, b, y, invd, omega,
-                                                            fixed, sc);
+                                                            fixed, sc, w);
 }
 
 // Block sum of one double per thread (deterministic tree), result valid in thread 0.
@@ -212,12 +295,14 @@ template <int DIM, typename T>
 __global__ void __launch_bounds__(kThreads) k_restrict(Dims df, const T* __restrict__ rf,
                                                        T* __restrict__ rc,
                                                        const uint8_t* __restrict__ fixed_c,
-                                                       const CgScalars* __restrict__ sc) {
+                                                       const CgScalars* __restrict__ sc,
+                                                       int arrow) {
   const int rhs = blockIdx.y;
   if (sc && sc[rhs].done) return;
   Dims dc{df.nx / 2, df.ny / 2, DIM == 3 ? df.nz / 2 : 1, DIM};
   const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nodes_c = dc.nodes();
+  if (arrow && node == 0) rc[dc.dofs()] = rf[df.dofs()];
   if (node >= nodes_c) return;
   const int cnx = dc.nx + 1, cny = dc.ny + 1;
   const int I = (int)(node % cnx), J = (int)((node / cnx) % cny);
@@ -259,12 +344,14 @@ template <int DIM, typename T>
 __global__ void __launch_bounds__(kThreads) k_prolong_add(Dims df, const T* __restrict__ zc,
                                                           T* __restrict__ zf,
                                                           const uint8_t* __restrict__ fixed_f,
-                                                          const CgScalars* __restrict__ sc) {
+                                                          const CgScalars* __restrict__ sc,
+                                                          int arrow) {
   const int rhs = blockIdx.y;
   if (sc && sc[rhs].done) return;
   Dims dc{df.nx / 2, df.ny / 2, DIM == 3 ? df.nz / 2 : 1, DIM};
   const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nodes_f = df.nodes();
+  if (arrow && node == 0) zf[df.dofs()] += zc[dc.dofs()];
   if (node >= nodes_f) return;
   const int fnx = df.nx + 1, fny = df.ny + 1;
   const int i = (int)(node % fnx), j = (int)((node / fnx) % fny);
@@ -324,7 +411,7 @@ __global__ void k_inv_diag(Dims d, const double* __restrict__ K0, const double* 
     const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
     for (int c = 0; c < DIM; ++c) {
       const int r = loc * DIM + c;
-      acc[c] += x ? x[e] * K0[r * NE + r] : Ae[e * NE * NE + r * NE + r];
+      acc[c] += x ? x[e] * K0[r * NE + r] : Ae[(long long)(r * NE + r) * d.elems() + e];
     }
   }
   for (int c = 0; c < DIM; ++c) {
@@ -389,16 +476,20 @@ __global__ void k_f2d(const float* __restrict__ a, double* __restrict__ b, long 
 template <typename T>
 cudaError_t launch_apply(const Dims& d, int mode, const T* K0, const T* x, const T* Ae, const T* v,
                          const T* b, T* y, const T* invd, T omega, const uint8_t* fixed, int nrhs,
-                         const CgScalars* sc, cudaStream_t st) {
+                         const CgScalars* sc, cudaStream_t st, const T* w) {
 #define TOPO_APPLY_CASE(DIM)                                                                    \
   switch (mode) {                                                                               \
-    case 0: apply_dispatch<DIM, T, 0>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st); \
+    case 0:                                                                                     \
+      apply_dispatch<DIM, T, 0>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st, w);    \
       break;                                                                                    \
-    case 1: apply_dispatch<DIM, T, 1>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st); \
+    case 1:                                                                                     \
+      apply_dispatch<DIM, T, 1>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st, w);    \
       break;                                                                                    \
-    case 2: apply_dispatch<DIM, T, 2>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st); \
+    case 2:                                                                                     \
+      apply_dispatch<DIM, T, 2>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st, w);    \
       break;                                                                                    \
-    default: apply_dispatch<DIM, T, 3>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st);\
+    default:                                                                                    \
+      apply_dispatch<DIM, T, 3>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st, w);    \
   }
   if (d.dim == 2) {
     TOPO_APPLY_CASE(2)
@@ -412,10 +503,40 @@ cudaError_t launch_apply(const Dims& d, int mode, const T* K0, const T* x, const
 template cudaError_t launch_apply<double>(const Dims&, int, const double*, const double*,
                                           const double*, const double*, const double*, double*,
                                           const double*, double, const uint8_t*, int,
-                                          const CgScalars*, cudaStream_t);
+                                          const CgScalars*, cudaStream_t, const double*);
 template cudaError_t launch_apply<float>(const Dims&, int, const float*, const float*, const float*,
                                          const float*, const float*, float*, const float*, float,
-                                         const uint8_t*, int, const CgScalars*, cudaStream_t);
+                                         const uint8_t*, int, const CgScalars*, cudaStream_t,
+                                         const float*);
+
+template <typename T>
+cudaError_t launch_apply_l1(const Dims& d, int mode, const T* C, const T* xf, const T* v,
+                            const T* b, T* y, const T* invd, T omega, const uint8_t* fixed,
+                            int nrhs, const CgScalars* sc, cudaStream_t st) {
+  dim3 grid(blocks_for(d.nodes()), nrhs);
+  switch (mode) {
+    case 0:
+      k_apply_l1<T, 0><<<grid, kThreads, 0, st>>>(d, C, xf, v, b, y, invd, omega, fixed, sc);
+      break;
+    case 1:
+      k_apply_l1<T, 1><<<grid, kThreads, 0, st>>>(d, C, xf, v, b, y, invd, omega, fixed, sc);
+      break;
+    case 2:
+      k_apply_l1<T, 2><<<grid, kThreads, 0, st>>>(d, C, xf, v, b, y, invd, omega, fixed, sc);
+      break;
+    default:
+      k_apply_l1<T, 3><<<grid, kThreads, 0, st>>>(d, C, xf, v, b, y, invd, omega, fixed, sc);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_apply_l1<float>(const Dims&, int, const float*, const float*,
+                                            const float*, const float*, float*, const float*,
+                                            float, const uint8_t*, int, const CgScalars*,
+                                            cudaStream_t);
+template cudaError_t launch_apply_l1<double>(const Dims&, int, const double*, const double*,
+                                             const double*, const double*, double*,
+                                             const double*, double, const uint8_t*, int,
+                                             const CgScalars*, cudaStream_t);
 
 cudaError_t launch_apply_dot_fine(const Dims& d, const double* K0, const double* x, const double* v,
                                   double* y, const uint8_t* fixed, int nrhs, double* partials,
@@ -430,35 +551,35 @@ cudaError_t launch_apply_dot_fine(const Dims& d, const double* K0, const double*
 
 template <typename T>
 cudaError_t launch_restrict(const Dims& fine, const T* rf, T* rc, const uint8_t* fixed_c, int nrhs,
-                            const CgScalars* sc, cudaStream_t st) {
+                            const CgScalars* sc, cudaStream_t st, int arrow) {
   Dims dc{fine.nx / 2, fine.ny / 2, fine.dim == 3 ? fine.nz / 2 : 1, fine.dim};
   dim3 grid(blocks_for(dc.nodes()), nrhs);
   if (fine.dim == 2)
-    k_restrict<2, T><<<grid, kThreads, 0, st>>>(fine, rf, rc, fixed_c, sc);
+    k_restrict<2, T><<<grid, kThreads, 0, st>>>(fine, rf, rc, fixed_c, sc, arrow);
   else
-    k_restrict<3, T><<<grid, kThreads, 0, st>>>(fine, rf, rc, fixed_c, sc);
+    k_restrict<3, T><<<grid, kThreads, 0, st>>>(fine, rf, rc, fixed_c, sc, arrow);
   return cudaGetLastError();
 }
 template cudaError_t launch_restrict<double>(const Dims&, const double*, double*, const uint8_t*,
-                                             int, const CgScalars*, cudaStream_t);
+                                             int, const CgScalars*, cudaStream_t, int);
 template cudaError_t launch_restrict<float>(const Dims&, const float*, float*, const uint8_t*, int,
-                                            const CgScalars*, cudaStream_t);
+                                            const CgScalars*, cudaStream_t, int);
 
 template <typename T>
 cudaError_t launch_prolong_add(const Dims& fine, const T* zc, T* zf, const uint8_t* fixed_f,
-                               int nrhs, const CgScalars* sc, cudaStream_t st) {
+                               int nrhs, const CgScalars* sc, cudaStream_t st, int arrow) {
   dim3 grid(blocks_for(fine.nodes()), nrhs);
   if (fine.dim == 2)
-    k_prolong_add<2, T><<<grid, kThreads, 0, st>>>(fine, zc, zf, fixed_f, sc);
+    k_prolong_add<2, T><<<grid, kThreads, 0, st>>>(fine, zc, zf, fixed_f, sc, arrow);
   else
-    k_prolong_add<3, T><<<grid, kThreads, 0, st>>>(fine, zc, zf, fixed_f, sc);
+    k_prolong_add<3, T><<<grid, kThreads, 0, st>>>(fine, zc, zf, fixed_f, sc, arrow);
   return cudaGetLastError();
 }
 template cudaError_t launch_prolong_add<double>(const Dims&, const double*, double*,
                                                 const uint8_t*, int, const CgScalars*,
-                                                cudaStream_t);
+                                                cudaStream_t, int);
 template cudaError_t launch_prolong_add<float>(const Dims&, const float*, float*, const uint8_t*,
-                                               int, const CgScalars*, cudaStream_t);
+                                               int, const CgScalars*, cudaStream_t, int);
 
 cudaError_t launch_inv_diag(const Dims& d, const double* K0, const double* x, const double* Ae,
                             const uint8_t* fixed, double* invd, cudaStream_t st) {

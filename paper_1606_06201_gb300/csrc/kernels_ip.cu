@@ -1,0 +1,691 @@
+// Kernels of the primal-dual interior-point method (Sec. 2-3) and of the OC methods (Sec. 4).
+//
+// IP.  With B(u) = (K_1 u, ..., K_m u), column e of B is L_e^T g_e with g_e = K0 u_e, and
+// D = X^{-1} Phi + (xbar - X)^{-1} Psi is diagonal, so the augmented matrix of Eq. (nwtr2Z),
+//   Z = [K(x) 0; 0 0] + [B; e^T] D^{-1} [B^T e],
+// acts element by element:  s_e = (g_e^T v_e + v_lambda) / D_e,
+//   (Z v)_u = K(x) v_u + sum_e L_e^T g_e s_e,   (Z v)_lambda = sum_e s_e.
+// The right-hand side Eq. (nwtr2rhs) is Res1 + sum_e L_e^T g_e t_e, Res2 + sum_e t_e with
+// t_e = tilde Res3_e / D_e.  The direction is completed element-wise: d_x from row 3 of
+// Eq. (nwtr) and d_phi, d_psi from Eq. (phipsi1)-(phipsi2); the step is the 0.9 fraction-to-
+// boundary rule of Sec. 3.3.  Row 3 of Eq. (nwt) uses the right-hand side
+// F3 = -1/2 u^T K_i u - lambda - phi_i + psi_i (the printed matrix with the sign that makes the
+// direction a Newton step of the KKT map).
+//
+// OC.  The bisection on lambda of Algorithm OC compares sum_i x_i^NEW(lambda) with V using a
+// double-double (error-free TwoSum) reduction rounded once at the end, so the decision does not
+// depend on the summation order.
+//
+// All reductions write one partial per block; the last block to finish combines them in block
+// order and updates the device-resident scalars.
+#include "topo_internal.cuh"
+
+namespace topo {
+
+namespace {
+
+__device__ __forceinline__ int loc_ox(int a) { return ((a & 3) == 1 || (a & 3) == 2) ? 1 : 0; }
+__device__ __forceinline__ int loc_oy(int a) { return ((a & 3) >= 2) ? 1 : 0; }
+__device__ __forceinline__ int loc_oz(int a) { return a >> 2; }
+__device__ __forceinline__ int loc_of(int lx, int ly, int lz) {
+  return (ly ? (lx ? 2 : 3) : (lx ? 1 : 0)) + 4 * lz;
+}
+
+template <int DIM>
+__device__ __forceinline__ long long elem_node(const Dims& d, long long e, int a) {
+  const int ex = (int)(e % d.nx), ey = (int)((e / d.nx) % d.ny);
+  const int ez = (DIM == 3) ? (int)(e / ((long long)d.nx * d.ny)) : 0;
+  return (ex + loc_ox(a)) + (long long)(d.nx + 1) * ((ey + loc_oy(a)) + (long long)(d.ny + 1) *
+                                                                              (ez + loc_oz(a)));
+}
+
+// Block reduction of NV doubles; result valid in thread 0.
+template <int NV>
+__device__ void block_reduce(double (&v)[NV], int op_min) {
+  __shared__ double sh[NV][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double a = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double b = __shfl_down_sync(0xffffffffu, a, o);
+      a = op_min ? fmin(a, b) : a + b;
+    }
+    v[q] = a;
+  }
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[q][wid] = v[q];
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double a = lane < nw ? sh[q][lane] : (op_min ? INFINITY : 0.0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double b = __shfl_down_sync(0xffffffffu, a, o);
+        a = op_min ? fmin(a, b) : a + b;
+      }
+      v[q] = a;
+    }
+  }
+}
+
+// Writes the block's NV partials; returns true in the last block, with the combined values in
+// tot (every thread of that block).
+template <int NV>
+__device__ bool last_block(double (&part)[NV], int op_min, double* partials, unsigned* counter,
+                           double (&tot)[NV]) {
+  __shared__ bool last;
+  __shared__ double res[NV];
+  block_reduce<NV>(part, op_min);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) partials[(long long)q * gridDim.x + blockIdx.x] = part[q];
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  double acc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    acc[q] = op_min ? INFINITY : 0.0;
+    for (unsigned t = threadIdx.x; t < gridDim.x; t += blockDim.x) {
+      const double b = __ldcg(partials + (long long)q * gridDim.x + t);
+      acc[q] = op_min ? fmin(acc[q], b) : acc[q] + b;
+    }
+  }
+  block_reduce<NV>(acc, op_min);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) res[q] = acc[q];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) tot[q] = res[q];
+  if (threadIdx.x == 0) *counter = 0;
+  return true;
+}
+
+// ---- Z operator ---------------------------------------------------------------------------
+// s_e = (g_e^T v_e + v_lambda) Dinv_e and the lambda row (Z v)_lambda = sum_e s_e, written into
+// y[n] according to MODE (0: Zv, 1: b - Zv, 2: Jacobi, 3: first Jacobi sweep).
+template <int DIM, typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) k_z_elem(Dims d, const T* __restrict__ g,
+                                                     const T* __restrict__ Dinv,
+                                                     const T* __restrict__ v,
+                                                     const T* __restrict__ b, T* __restrict__ y,
+                                                     T* __restrict__ se, const double* zll,
+                                                     double omega, double* partials,
+                                                     unsigned* counter, const CgScalars* sc) {
+  constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM;
+  if (sc && sc[0].done) return;
+  const long long m = d.elems();
+  const long long n = d.dofs();
+  const T vl = v[n];
+  double part[1] = {0.0};
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (long long)gridDim.x * blockDim.x) {
+    T acc = vl;
+#pragma unroll
+    for (int a = 0; a < NN; ++a) {
+      const long long nid = elem_node<DIM>(d, e, a);
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) acc = fma(g[e * NE + a * DIM + c], v[DIM * nid + c], acc);
+    }
+    const T s = acc * Dinv[e];
+    se[e] = s;
+    part[0] += (double)s;
+  }
+  double tot[1];
+  if (!last_block<1>(part, 0, partials, counter, tot)) return;
+  if (threadIdx.x == 0) {
+    const double q = tot[0];
+    double out;
+    if (MODE == 0) out = q;
+    else if (MODE == 1) out = (double)b[n] - q;
+    else out = (double)v[n] + omega * ((double)b[n] - q) / *zll;
+    y[n] = (T)out;
+  }
+}
+
+// (Z v)_u on the finest level: node gather of x_e K0 v_e + g_e s_e; MODE as k_z_elem.  MODE 3 also
+// writes the lambda entry omega b_lambda / Z_ll.
+template <int DIM, typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) k_z_node(Dims d, const T* __restrict__ K0,
+                                                     const T* __restrict__ x,
+                                                     const T* __restrict__ g,
+                                                     const T* __restrict__ se,
+                                                     const T* __restrict__ v,
+                                                     const T* __restrict__ b, T* __restrict__ y,
+                                                     const T* __restrict__ invd, T omega,
+                                                     const uint8_t* __restrict__ fixed,
+                                                     const double* zll, const CgScalars* sc) {
+  constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM;
+  if (sc && sc[0].done) return;
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nodes = d.nodes();
+  const long long n = nodes * DIM;
+  if (MODE == 3 && node == 0) y[n] = (T)((double)omega * (double)b[n] / *zll);
+  if (node >= nodes) return;
+  const int nnx = d.nx + 1, nny = d.ny + 1;
+  const int i = (int)(node % nnx), j = (int)((node / nnx) % nny);
+  const int k = (DIM == 3) ? (int)(node / ((long long)nnx * nny)) : 0;
+  T acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+  if (MODE != 3) {
+    for (int s = 0; s < NN; ++s) {
+      const int dx = s & 1, dy = (s >> 1) & 1, dz = (DIM == 3) ? (s >> 2) : 0;
+      const int ex = i - 1 + dx, ey = j - 1 + dy, ez = (DIM == 3) ? k - 1 + dz : 0;
+      if (ex < 0 || ex >= d.nx || ey < 0 || ey >= d.ny) continue;
+      if (DIM == 3 && (ez < 0 || ez >= d.nz)) continue;
+      const int loc = loc_of(1 - dx, 1 - dy, DIM == 3 ? 1 - dz : 0);
+      const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
+      T ve[NE];
+#pragma unroll
+      for (int a = 0; a < NN; ++a) {
+        const long long nid = elem_node<DIM>(d, e, a);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) ve[a * DIM + c] = v[DIM * nid + c];
+      }
+      const T xe = x[e], s_e = se[e];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        const T* row = K0 + (loc * DIM + c) * NE;
+        T t = T(0);
+#pragma unroll
+        for (int q = 0; q < NE; ++q) t = fma(row[q], ve[q], t);
+        acc[c] = fma(xe, t, acc[c]);
+        acc[c] = fma(g[e * NE + loc * DIM + c], s_e, acc[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const long long id = DIM * node + c;
+    T out;
+    if (fixed[id]) out = T(0);
+    else if (MODE == 0) out = acc[c];
+    else if (MODE == 1) out = b[id] - acc[c];
+    else if (MODE == 2) out = v[id] + omega * invd[id] * (b[id] - acc[c]);
+    else out = omega * invd[id] * b[id];
+    y[id] = out;
+  }
+}
+
+// Lambda row on a coarse level: (Z v)_lambda = w^T v_u + Z_ll v_lambda, written per MODE.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) k_arrow_row(long long n, const T* __restrict__ w,
+                                                        const T* __restrict__ v,
+                                                        const T* __restrict__ b,
+                                                        T* __restrict__ y, const double* zll,
+                                                        double omega, double* partials,
+                                                        unsigned* counter, const CgScalars* sc) {
+  if (sc && sc[0].done) return;
+  double part[1] = {0.0};
+  if (MODE != 3)
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+      part[0] = fma((double)w[i], (double)v[i], part[0]);
+  double tot[1];
+  if (!last_block<1>(part, 0, partials, counter, tot)) return;
+  if (threadIdx.x == 0) {
+    const double z = *zll;
+    const double q = tot[0] + z * (double)v[n];
+    double out;
+    if (MODE == 0) out = q;
+    else if (MODE == 1) out = (double)b[n] - q;
+    else if (MODE == 2) out = (double)v[n] + omega * ((double)b[n] - q) / z;
+    else out = omega * (double)b[n] / z;
+    y[n] = (T)out;
+  }
+}
+
+// ---- IP element and node kernels ---------------------------------------------------------
+// Per element at z = (u, lambda, x, phi, psi) and barrier (s, r):
+//   g_e = K0 u_e, F3 = -1/2 u_e^T g_e - lambda - phi + psi, Res4 = s - phi x,
+//   Res5 = r - psi (xbar - x), tR3 = F3 - Res4/x + Res5/(xbar - x), D = phi/x + psi/(xbar - x),
+//   Dinv = 1/D, t = tR3 Dinv.  Sums: sum x, sum t, ||tR3||^2, ||phi||^2, ||psi||^2, sum Dinv.
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_ip_elem(Dims d, const double* __restrict__ K0,
+                                                      const double* __restrict__ u,
+                                                      const double* __restrict__ x,
+                                                      const double* __restrict__ phi,
+                                                      const double* __restrict__ psi,
+                                                      IpScalars* ip, double* __restrict__ g,
+                                                      double* __restrict__ tR3,
+                                                      double* __restrict__ Dinv,
+                                                      double* __restrict__ t, double* partials,
+                                                      unsigned* counter) {
+  constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM;
+  const long long m = d.elems();
+  const double lam = ip->lam, s = ip->s, r = ip->r, xbar = ip->xbar;
+  double part[6] = {0, 0, 0, 0, 0, 0};
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (long long)gridDim.x * blockDim.x) {
+    double ue[NE];
+#pragma unroll
+    for (int a = 0; a < NN; ++a) {
+      const long long nid = elem_node<DIM>(d, e, a);
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) ue[a * DIM + c] = u[DIM * nid + c];
+    }
+    double en = 0.0;
+    for (int q = 0; q < NE; ++q) {
+      double acc = 0.0;
+#pragma unroll
+      for (int p = 0; p < NE; ++p) acc = fma(__ldg(K0 + q * NE + p), ue[p], acc);
+      g[e * NE + q] = acc;
+      en = fma(ue[q], acc, en);
+    }
+    const double xe = x[e], ph = phi[e], ps = psi[e];
+    const double xu = xbar - xe;
+    const double F3 = -0.5 * en - lam - ph + ps;
+    const double R4 = s - ph * xe, R5 = r - ps * xu;
+    const double tr = F3 - R4 / xe + R5 / xu;
+    const double De = ph / xe + ps / xu;
+    const double di = 1.0 / De;
+    tR3[e] = tr;
+    Dinv[e] = di;
+    t[e] = tr * di;
+    part[0] += xe;
+    part[1] += tr * di;
+    part[2] = fma(tr, tr, part[2]);
+    part[3] = fma(ph, ph, part[3]);
+    part[4] = fma(ps, ps, part[4]);
+    part[5] += di;
+  }
+  double tot[6];
+  if (!last_block<6>(part, 0, partials, counter, tot)) return;
+  if (threadIdx.x == 0) {
+    ip->sum_x = tot[0];
+    ip->sum_t = tot[1];
+    ip->nrm_tr3 = sqrt(tot[2]);
+    ip->nrm_phi = sqrt(tot[3]);
+    ip->nrm_psi = sqrt(tot[4]);
+    ip->zll = tot[5];
+  }
+}
+
+// Per node: Res1 = f - K(x) u; rhs_u = Res1 + sum_e g_e t_e; w = sum_e g_e Dinv_e (the Z_ul
+// column); invd = 1 / (sum_e x_e K0_ii + g_e,i^2 Dinv_e); ||Res1||^2.  Last block: rhs_lambda.
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_ip_node(Dims d, const double* __restrict__ K0,
+                                                      const double* __restrict__ x,
+                                                      const double* __restrict__ u,
+                                                      const double* __restrict__ f,
+                                                      const double* __restrict__ g,
+                                                      const double* __restrict__ t,
+                                                      const double* __restrict__ Dinv,
+                                                      const uint8_t* __restrict__ fixed,
+                                                      double* __restrict__ rhs,
+                                                      double* __restrict__ w,
+                                                      double* __restrict__ invd, IpScalars* ip,
+                                                      double* partials, unsigned* counter) {
+  constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM;
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nodes = d.nodes();
+  double part[1] = {0.0};
+  if (node < nodes) {
+    const int nnx = d.nx + 1, nny = d.ny + 1;
+    const int i = (int)(node % nnx), j = (int)((node / nnx) % nny);
+    const int k = (DIM == 3) ? (int)(node / ((long long)nnx * nny)) : 0;
+    double ku[DIM] = {}, gt[DIM] = {}, gw[DIM] = {}, dg[DIM] = {};
+    for (int s = 0; s < NN; ++s) {
+      const int dx = s & 1, dy = (s >> 1) & 1, dz = (DIM == 3) ? (s >> 2) : 0;
+      const int ex = i - 1 + dx, ey = j - 1 + dy, ez = (DIM == 3) ? k - 1 + dz : 0;
+      if (ex < 0 || ex >= d.nx || ey < 0 || ey >= d.ny) continue;
+      if (DIM == 3 && (ez < 0 || ez >= d.nz)) continue;
+      const int loc = loc_of(1 - dx, 1 - dy, DIM == 3 ? 1 - dz : 0);
+      const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
+      const double xe = x[e], te = t[e], de = Dinv[e];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        const double gi = g[e * NE + loc * DIM + c];
+        // K(x) u row = x_e (K0 u_e)_row = x_e g_e,row
+        ku[c] = fma(xe, gi, ku[c]);
+        gt[c] = fma(gi, te, gt[c]);
+        gw[c] = fma(gi, de, gw[c]);
+        dg[c] = fma(xe, K0[(loc * DIM + c) * NE + loc * DIM + c], dg[c]);
+        dg[c] = fma(gi * gi, de, dg[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      const long long id = DIM * node + c;
+      if (fixed[id]) {
+        rhs[id] = 0.0;
+        w[id] = 0.0;
+        invd[id] = 1.0;
+      } else {
+        const double r1 = f[id] - ku[c];
+        rhs[id] = r1 + gt[c];
+        w[id] = gw[c];
+        invd[id] = dg[c] > 0.0 ? 1.0 / dg[c] : 1.0;
+        part[0] = fma(r1, r1, part[0]);
+      }
+    }
+  }
+  double tot[1];
+  if (!last_block<1>(part, 0, partials, counter, tot)) return;
+  if (threadIdx.x == 0) {
+    ip->nrm_res1 = sqrt(tot[0]);
+    const double res2 = ip->V - ip->sum_x;
+    ip->res2 = res2;
+    rhs[d.dofs()] = res2 + ip->sum_t;
+  }
+}
+
+// Direction completion and step length: d_x = (g_e^T d_u,e + d_lambda - tR3) Dinv,
+// d_phi = (Res4 - phi d_x)/x, d_psi = (Res5 + psi d_x)/(xbar - x); minima of the ratios of the
+// 0.9 rule over x (both bounds), phi and psi.
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_ip_recover(Dims d, const double* __restrict__ g,
+                                                         const double* __restrict__ du,
+                                                         const double* __restrict__ tR3,
+                                                         const double* __restrict__ Dinv,
+                                                         const double* __restrict__ x,
+                                                         const double* __restrict__ phi,
+                                                         const double* __restrict__ psi,
+                                                         double* __restrict__ dx,
+                                                         double* __restrict__ dphi,
+                                                         double* __restrict__ dpsi,
+                                                         IpScalars* ip, double* partials,
+                                                         unsigned* counter) {
+  constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM;
+  const long long m = d.elems();
+  const long long n = d.dofs();
+  const double dl = du[n];
+  const double s = ip->s, r = ip->r, xbar = ip->xbar;
+  double part[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (long long)gridDim.x * blockDim.x) {
+    double acc = dl - tR3[e];
+#pragma unroll
+    for (int a = 0; a < NN; ++a) {
+      const long long nid = elem_node<DIM>(d, e, a);
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) acc = fma(g[e * NE + a * DIM + c], du[DIM * nid + c], acc);
+    }
+    const double ddx = acc * Dinv[e];
+    const double xe = x[e], ph = phi[e], ps = psi[e], xu = xbar - xe;
+    const double R4 = s - ph * xe, R5 = r - ps * xu;
+    const double dph = (R4 - ph * ddx) / xe;
+    const double dps = (R5 + ps * ddx) / xu;
+    dx[e] = ddx;
+    dphi[e] = dph;
+    dpsi[e] = dps;
+    if (ddx < 0.0) part[0] = fmin(part[0], -xe / ddx);
+    if (ddx > 0.0) part[1] = fmin(part[1], xu / ddx);
+    if (dph < 0.0) part[2] = fmin(part[2], -ph / dph);
+    if (dps < 0.0) part[3] = fmin(part[3], -ps / dps);
+  }
+  double tot[4];
+  if (!last_block<4>(part, 1, partials, counter, tot)) return;
+  if (threadIdx.x == 0) {
+    const double fr = ip->frac;
+    double a = fmin(1.0, fmin(fr * tot[0], fr * tot[1]));
+    if (ip->step_all) a = fmin(a, fmin(fr * tot[2], fr * tot[3]));
+    ip->alpha = a;
+    ip->dlam = dl;
+  }
+}
+
+// z += alpha d on the element variables and lambda.
+__global__ void k_ip_update_elem(long long m, double* x, double* phi, double* psi,
+                                 const double* dx, const double* dphi, const double* dpsi,
+                                 IpScalars* ip) {
+  const double a = ip->alpha;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e == 0) ip->lam += a * ip->dlam;
+  if (e >= m) return;
+  x[e] = fma(a, dx[e], x[e]);
+  phi[e] = fma(a, dphi[e], phi[e]);
+  psi[e] = fma(a, dpsi[e], psi[e]);
+}
+
+__global__ void k_axpy_alpha(long long n, double* u, const double* du, const IpScalars* ip) {
+  const double a = ip->alpha;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    u[i] = fma(a, du[i], u[i]);
+}
+
+// ---- OC kernels --------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  s = a + b;
+  const double bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void dd_add(double& hi, double& lo, double bh, double bl) {
+  double s, e;
+  two_sum(hi, bh, s, e);
+  e += lo + bl;
+  two_sum(s, e, hi, lo);
+}
+
+__device__ __forceinline__ double oc_new(double xo, double E, double lam, double xlow,
+                                         double xbar) {
+  return fmin(fmax(xo * E / lam, xlow), xbar);
+}
+
+// One bisection step of Algorithm OC: x^NEW(lambda_mid), its sum in double-double, and in the
+// last block: "sum > V" raises the lower end, otherwise lowers the upper end; next midpoint.
+__global__ void __launch_bounds__(kThreads) k_oc_bisect(long long m, const double* __restrict__ x,
+                                                        const double* __restrict__ E,
+                                                        OcScalars* oc, double* partials,
+                                                        unsigned* counter) {
+  if (oc->hi - oc->lo <= oc->tau) return;
+  const double lam = 0.5 * (oc->hi + oc->lo);
+  const double xlow = oc->xlow, xbar = oc->xbar;
+  double hi = 0.0, lo = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (long long)gridDim.x * blockDim.x)
+    dd_add(hi, lo, oc_new(x[e], E[e], lam, xlow, xbar), 0.0);
+  // warp and block combination of (hi, lo) pairs in a fixed order
+  __shared__ double sh[2][32];
+  __shared__ bool last;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double bh = __shfl_down_sync(0xffffffffu, hi, o);
+    const double bl = __shfl_down_sync(0xffffffffu, lo, o);
+    dd_add(hi, lo, bh, bl);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh[0][wid] = hi;
+    sh[1][wid] = lo;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double h = 0.0, l = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) dd_add(h, l, sh[0][w], sh[1][w]);
+    partials[2 * blockIdx.x] = h;
+    partials[2 * blockIdx.x + 1] = l;
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  double h = 0.0, l = 0.0;
+  for (unsigned bidx = 0; bidx < gridDim.x; ++bidx)
+    dd_add(h, l, __ldcg(partials + 2 * bidx), __ldcg(partials + 2 * bidx + 1));
+  const double total = h + l;  // round the double-double once
+  if (total > oc->V) oc->lo = lam;
+  else oc->hi = lam;
+  oc->lam_last = lam;
+  oc->steps += 1;
+  *counter = 0;
+}
+
+// x_out = x^NEW(lambda_last); optionally averaged with x_avg (AOC: 1/2 (x1 + x2)).
+__global__ void k_oc_apply(long long m, const double* __restrict__ x, const double* __restrict__ E,
+                           const OcScalars* oc, double* __restrict__ xout) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  xout[e] = oc_new(x[e], E[e], oc->lam_last, oc->xlow, oc->xbar);
+}
+
+__global__ void k_pow(long long m, double* E, double q) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < m) E[e] = pow(fmax(E[e], 0.0), q);
+}
+
+__global__ void k_average(long long m, const double* a, const double* b, double* out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < m) out[e] = 0.5 * (a[e] + b[e]);
+}
+
+inline unsigned red_grid(long long n) {
+  const long long b = (n + kThreads - 1) / kThreads;
+  return (unsigned)(b < kRedBlocks ? (b < 1 ? 1 : b) : kRedBlocks);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_z_apply_fine(const Dims& d, int mode, const T* K0, const T* x, const T* g,
+                                const T* Dinv, T* se, const T* v, const T* b, T* y, const T* invd,
+                                T omega, const uint8_t* fixed, const double* zll, double* partials,
+                                unsigned* counter, const CgScalars* sc, cudaStream_t st) {
+  const unsigned ge = red_grid(d.elems());
+  const unsigned gn = blocks_for(d.nodes());
+#define TOPO_ZF(DIM, MODE)                                                                      \
+  do {                                                                                          \
+    if (MODE != 3)                                                                              \
+      k_z_elem<DIM, T, MODE><<<ge, kThreads, 0, st>>>(d, g, Dinv, v, b, y, se, zll, omega,      \
+                                                      partials, counter, sc);                   \
+    k_z_node<DIM, T, MODE><<<gn, kThreads, 0, st>>>(d, K0, x, g, se, v, b, y, invd, omega,      \
+                                                    fixed, zll, sc);                            \
+  } while (0)
+  if (d.dim == 2) {
+    switch (mode) {
+      case 0: TOPO_ZF(2, 0); break;
+      case 1: TOPO_ZF(2, 1); break;
+      case 2: TOPO_ZF(2, 2); break;
+      default: TOPO_ZF(2, 3);
+    }
+  } else {
+    switch (mode) {
+      case 0: TOPO_ZF(3, 0); break;
+      case 1: TOPO_ZF(3, 1); break;
+      case 2: TOPO_ZF(3, 2); break;
+      default: TOPO_ZF(3, 3);
+    }
+  }
+#undef TOPO_ZF
+  return cudaGetLastError();
+}
+template cudaError_t launch_z_apply_fine<double>(const Dims&, int, const double*, const double*,
+                                                 const double*, const double*, double*,
+                                                 const double*, const double*, double*,
+                                                 const double*, double, const uint8_t*,
+                                                 const double*, double*, unsigned*,
+                                                 const CgScalars*, cudaStream_t);
+template cudaError_t launch_z_apply_fine<float>(const Dims&, int, const float*, const float*,
+                                                const float*, const float*, float*, const float*,
+                                                const float*, float*, const float*, float,
+                                                const uint8_t*, const double*, double*, unsigned*,
+                                                const CgScalars*, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_arrow_row(long long n, int mode, const T* w, const T* v, const T* b, T* y,
+                             const double* zll, double omega, double* partials, unsigned* counter,
+                             const CgScalars* sc, cudaStream_t st) {
+  const unsigned gr = red_grid(n);
+  switch (mode) {
+    case 0:
+      k_arrow_row<T, 0><<<gr, kThreads, 0, st>>>(n, w, v, b, y, zll, omega, partials, counter, sc);
+      break;
+    case 1:
+      k_arrow_row<T, 1><<<gr, kThreads, 0, st>>>(n, w, v, b, y, zll, omega, partials, counter, sc);
+      break;
+    case 2:
+      k_arrow_row<T, 2><<<gr, kThreads, 0, st>>>(n, w, v, b, y, zll, omega, partials, counter, sc);
+      break;
+    default:
+      k_arrow_row<T, 3><<<gr, kThreads, 0, st>>>(n, w, v, b, y, zll, omega, partials, counter, sc);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_arrow_row<double>(long long, int, const double*, const double*,
+                                              const double*, double*, const double*, double,
+                                              double*, unsigned*, const CgScalars*, cudaStream_t);
+template cudaError_t launch_arrow_row<float>(long long, int, const float*, const float*,
+                                             const float*, float*, const double*, double, double*,
+                                             unsigned*, const CgScalars*, cudaStream_t);
+
+cudaError_t launch_ip_residuals(const Dims& d, const double* K0, const double* u, const double* x,
+                                const double* phi, const double* psi, const double* f,
+                                const uint8_t* fixed, IpScalars* ip, double* g, double* tR3,
+                                double* Dinv, double* t, double* rhs, double* w, double* invd,
+                                double* partials, unsigned* counter, cudaStream_t st) {
+  const unsigned ge = red_grid(d.elems());
+  if (d.dim == 2)
+    k_ip_elem<2><<<ge, kThreads, 0, st>>>(d, K0, u, x, phi, psi, ip, g, tR3, Dinv, t, partials,
+                                          counter);
+  else
+    k_ip_elem<3><<<ge, kThreads, 0, st>>>(d, K0, u, x, phi, psi, ip, g, tR3, Dinv, t, partials,
+                                          counter);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const unsigned gn = blocks_for(d.nodes());
+  if (d.dim == 2)
+    k_ip_node<2><<<gn, kThreads, 0, st>>>(d, K0, x, u, f, g, t, Dinv, fixed, rhs, w, invd, ip,
+                                          partials, counter);
+  else
+    k_ip_node<3><<<gn, kThreads, 0, st>>>(d, K0, x, u, f, g, t, Dinv, fixed, rhs, w, invd, ip,
+                                          partials, counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ip_recover_update(const Dims& d, const double* g, const double* du,
+                                     const double* tR3, const double* Dinv, double* u, double* x,
+                                     double* phi, double* psi, double* dx, double* dphi,
+                                     double* dpsi, IpScalars* ip, double* partials,
+                                     unsigned* counter, cudaStream_t st) {
+  const unsigned ge = red_grid(d.elems());
+  if (d.dim == 2)
+    k_ip_recover<2><<<ge, kThreads, 0, st>>>(d, g, du, tR3, Dinv, x, phi, psi, dx, dphi, dpsi, ip,
+                                             partials, counter);
+  else
+    k_ip_recover<3><<<ge, kThreads, 0, st>>>(d, g, du, tR3, Dinv, x, phi, psi, dx, dphi, dpsi, ip,
+                                             partials, counter);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long m = d.elems(), n = d.dofs();
+  k_ip_update_elem<<<blocks_for(m), kThreads, 0, st>>>(m, x, phi, psi, dx, dphi, dpsi, ip);
+  k_axpy_alpha<<<red_grid(n), kThreads, 0, st>>>(n, u, du, ip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oc_bisection(long long m, const double* x, const double* E, OcScalars* oc,
+                                int steps, double* xout, double* partials, unsigned* counter,
+                                cudaStream_t st) {
+  const unsigned gr = red_grid(m);
+  for (int k = 0; k < steps; ++k) {
+    k_oc_bisect<<<gr, kThreads, 0, st>>>(m, x, E, oc, partials, counter);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_oc_apply<<<blocks_for(m), kThreads, 0, st>>>(m, x, E, oc, xout);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pow_inplace(long long m, double* E, double q, cudaStream_t st) {
+  k_pow<<<blocks_for(m), kThreads, 0, st>>>(m, E, q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_average(long long m, const double* a, const double* b, double* out,
+                           cudaStream_t st) {
+  k_average<<<blocks_for(m), kThreads, 0, st>>>(m, a, b, out);
+  return cudaGetLastError();
+}
+
+}  // namespace topo

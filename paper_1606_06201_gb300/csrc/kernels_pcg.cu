@@ -257,6 +257,34 @@ __global__ void __launch_bounds__(kThreads) k_dot(long long n, const double* __r
   if (threadIdx.x == 0) out[rhs] = tot[0];
 }
 
+__global__ void __launch_bounds__(kThreads) k_cg_alpha(long long n, const double* __restrict__ p,
+                                                       const double* __restrict__ q,
+                                                       double* partials, unsigned* counters,
+                                                       CgScalars* sc) {
+  const int rhs = blockIdx.y;
+  if (sc[rhs].done) return;
+  p += rhs * n;
+  q += rhs * n;
+  double part[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    part[0] = fma(p[i], q[i], part[0]);
+  double tot[1];
+  if (!last_block_sums<1>(part, partials, counters, rhs, tot)) return;
+  if (threadIdx.x == 0) {
+    CgScalars& S = sc[rhs];
+    S.pq = tot[0];
+    const double alpha = S.ry / tot[0];
+    if (!(tot[0] > 0.0) || !isfinite(alpha)) {
+      S.status = TOPO_E_BREAKDOWN;
+      S.done = 1;
+      S.alpha = 0.0;
+    } else {
+      S.alpha = alpha;
+    }
+  }
+}
+
 inline unsigned red_blocks(long long n) {
   const long long b = (n + kThreads - 1) / kThreads;
   return (unsigned)(b < kRedBlocks ? (b < 1 ? 1 : b) : kRedBlocks);
@@ -299,6 +327,12 @@ cudaError_t launch_cg_direction(long long n, int nrhs, const double* r, const TV
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_cg_p<TV><<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, y, p, y_old, flexible, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_alpha(long long n, int nrhs, const double* p, const double* q,
+                            double* partials, unsigned* counters, CgScalars* sc, cudaStream_t st) {
+  k_cg_alpha<<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, p, q, partials, counters, sc);
   return cudaGetLastError();
 }
 

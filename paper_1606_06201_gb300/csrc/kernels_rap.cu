@@ -37,16 +37,19 @@ __device__ __forceinline__ double wchild(int c, int a, int A) {
   return w;
 }
 
+// Output layout: entry-major, Ac[entry * mc + E]; thread t -> (entry = t / mc, E = t % mc), so
+// the entry (and the constants it reads) is uniform within a warp.
 template <int DIM>
 __global__ void k_rap_from_fine(Dims df, const double* __restrict__ C,
-                                const double* __restrict__ x, double* __restrict__ Ac) {
+                                const double* __restrict__ x, double* __restrict__ Ac,
+                                const double* __restrict__ g, const double* __restrict__ Dinv) {
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM, NE2 = NE * NE;
   const int cnx = df.nx / 2, cny = df.ny / 2, cnz = DIM == 3 ? df.nz / 2 : 1;
   const long long mc = (long long)cnx * cny * cnz;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= mc * NE2) return;
-  const long long E = t / NE2;
-  const int entry = (int)(t % NE2);
+  const int entry = (int)(t / mc);
+  const long long E = t % mc;
   const int EX = (int)(E % cnx), EY = (int)((E / cnx) % cny), EZ = (int)(E / ((long long)cnx * cny));
   double acc = 0.0;
 #pragma unroll
@@ -54,19 +57,39 @@ __global__ void k_rap_from_fine(Dims df, const double* __restrict__ C,
     const int fx = 2 * EX + (c & 1), fy = 2 * EY + ((c >> 1) & 1), fz = 2 * EZ + (c >> 2);
     const long long fe = fx + (long long)df.nx * (fy + (long long)df.ny * (DIM == 3 ? fz : 0));
     acc = fma(x[fe], __ldg(C + c * NE2 + entry), acc);
+    if (g) {  // rank-one term (P_c^T g_c)_I (P_c^T g_c)_J / D_c
+      const int I = entry / NE, J = entry % NE;
+      const int A = I / DIM, al = I % DIM, B = J / DIM, be = J % DIM;
+      double hI = 0.0, hJ = 0.0;
+      for (int a = 0; a < NN; ++a) {
+        hI = fma(wchild<DIM>(c, a, A), g[fe * NE + a * DIM + al], hI);
+        hJ = fma(wchild<DIM>(c, a, B), g[fe * NE + a * DIM + be], hJ);
+      }
+      acc = fma(hI * hJ, Dinv[fe], acc);
+    }
   }
   Ac[t] = acc;
 }
 
+// General Galerkin step from level matrices Af (entry-major, mf elements) to Ac (entry-major):
+// A_E = sum_c P_c^T A_c P_c with the interpolation weights W_c[a][A] tabulated in shared memory
+// (exact binary fractions) and their zeros skipped.
 template <int DIM>
 __global__ void k_rap_coarse(Dims df, const double* __restrict__ Af, double* __restrict__ Ac) {
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM, NE2 = NE * NE;
+  __shared__ float W[NN][NN][NN];  // [child][fine local node a][coarse local node A]
+  for (int idx = threadIdx.x; idx < NN * NN * NN; idx += blockDim.x) {
+    const int c = idx / (NN * NN), a = (idx / NN) % NN, A = idx % NN;
+    W[c][a][A] = (float)wchild<DIM>(c, a, A);
+  }
+  __syncthreads();
   const int cnx = df.nx / 2, cny = df.ny / 2, cnz = DIM == 3 ? df.nz / 2 : 1;
   const long long mc = (long long)cnx * cny * cnz;
+  const long long mf = df.elems();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= mc * NE2) return;
-  const long long E = t / NE2;
-  const int entry = (int)(t % NE2);
+  const int entry = (int)(t / mc);
+  const long long E = t % mc;
   const int I = entry / NE, J = entry % NE;
   const int A = I / DIM, al = I % DIM, B = J / DIM, be = J % DIM;
   const int EX = (int)(E % cnx), EY = (int)((E / cnx) % cny), EZ = (int)(E / ((long long)cnx * cny));
@@ -74,17 +97,16 @@ __global__ void k_rap_coarse(Dims df, const double* __restrict__ Af, double* __r
   for (int c = 0; c < NN; ++c) {
     const int fx = 2 * EX + (c & 1), fy = 2 * EY + ((c >> 1) & 1), fz = 2 * EZ + (c >> 2);
     const long long fe = fx + (long long)df.nx * (fy + (long long)df.ny * (DIM == 3 ? fz : 0));
-    const double* Ach = Af + fe * NE2;
     for (int a = 0; a < NN; ++a) {
-      const double wa = wchild<DIM>(c, a, A);
-      if (wa == 0.0) continue;
+      const float wa = W[c][a][A];
+      if (wa == 0.0f) continue;
       double s = 0.0;
       for (int b = 0; b < NN; ++b) {
-        const double wb = wchild<DIM>(c, b, B);
-        if (wb == 0.0) continue;
-        s = fma(__ldg(Ach + (a * DIM + al) * NE + b * DIM + be), wb, s);
+        const float wb = W[c][b][B];
+        if (wb == 0.0f) continue;
+        s = fma(__ldg(Af + (long long)((a * DIM + al) * NE + b * DIM + be) * mf + fe), (double)wb, s);
       }
-      acc = fma(wa, s, acc);
+      acc = fma((double)wa, s, acc);
     }
   }
   Ac[t] = acc;
@@ -95,14 +117,27 @@ __global__ void k_rap_coarse(Dims df, const double* __restrict__ Af, double* __r
 template <int DIM>
 __global__ void k_assemble_dense(Dims d, const double* __restrict__ K0,
                                  const double* __restrict__ x, const double* __restrict__ Ae,
-                                 const uint8_t* __restrict__ fixed, double* __restrict__ A) {
+                                 const uint8_t* __restrict__ fixed, double* __restrict__ A,
+                                 long long ld, const double* __restrict__ w,
+                                 const double* __restrict__ zll, const double* __restrict__ g,
+                                 const double* __restrict__ Dinv) {
   constexpr int NE = (DIM == 2 ? 4 : 8) * DIM;
   const long long n = d.dofs();
+  const long long na = w ? n + 1 : n;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n * n) return;
-  const long long i = t / n, j = t % n;
+  if (t >= na * na) return;
+  const long long i = t / na, j = t % na;
+  double* out = A + i * ld + j;
+  if (i == n || j == n) {  // arrow row / column
+    if (i == n && j == n) *out = *zll;
+    else {
+      const long long k = (i == n) ? j : i;
+      *out = fixed[k] ? 0.0 : w[k];
+    }
+    return;
+  }
   if (fixed[i] || fixed[j]) {
-    A[t] = (i == j) ? 1.0 : 0.0;
+    *out = (i == j) ? 1.0 : 0.0;
     return;
   }
   const int nnx = d.nx + 1, nny = d.ny + 1;
@@ -121,9 +156,10 @@ __global__ void k_assemble_dense(Dims d, const double* __restrict__ K0,
     const int lj = loc_of(lxj, lyj, lzj);
     const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
     const int r = li * DIM + al, q = lj * DIM + be;
-    acc += x ? x[e] * K0[r * NE + q] : Ae[e * NE * NE + r * NE + q];
+    acc += x ? x[e] * K0[r * NE + q] : Ae[(long long)(r * NE + q) * d.elems() + e];
+    if (x && g) acc += g[e * NE + r] * g[e * NE + q] * Dinv[e];
   }
-  A[t] = acc;
+  *out = acc;
 }
 
 // In-place Cholesky A = L L^T of a dense SPD matrix in one block (right-looking), then L^T is
@@ -212,14 +248,14 @@ __global__ void k_dense_solve(int n, const double* __restrict__ Ainv, const T* _
 }  // namespace
 
 cudaError_t launch_rap_from_fine(const Dims& fine, const double* C, const double* x, double* Ac,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, const double* g, const double* Dinv) {
   const int ne = fine.dim == 2 ? 8 : 24;
   const long long mc = fine.elems() / (fine.dim == 2 ? 4 : 8);
   const long long total = mc * ne * ne;
   if (fine.dim == 2)
-    k_rap_from_fine<2><<<blocks_for(total), kThreads, 0, st>>>(fine, C, x, Ac);
+    k_rap_from_fine<2><<<blocks_for(total), kThreads, 0, st>>>(fine, C, x, Ac, g, Dinv);
   else
-    k_rap_from_fine<3><<<blocks_for(total), kThreads, 0, st>>>(fine, C, x, Ac);
+    k_rap_from_fine<3><<<blocks_for(total), kThreads, 0, st>>>(fine, C, x, Ac, g, Dinv);
   return cudaGetLastError();
 }
 
@@ -236,12 +272,17 @@ cudaError_t launch_rap_coarse(const Dims& fine, const double* Af, double* Ac, cu
 
 cudaError_t launch_assemble_dense(const Dims& d, const double* K0, const double* x,
                                   const double* Ae, const uint8_t* fixed, double* A,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, long long ld, const double* w,
+                                  const double* zll, const double* g, const double* Dinv) {
   const long long n = d.dofs();
+  const long long na = w ? n + 1 : n;
+  if (ld <= 0) ld = na;
   if (d.dim == 2)
-    k_assemble_dense<2><<<blocks_for(n * n), kThreads, 0, st>>>(d, K0, x, Ae, fixed, A);
+    k_assemble_dense<2><<<blocks_for(na * na), kThreads, 0, st>>>(d, K0, x, Ae, fixed, A, ld, w,
+                                                                  zll, g, Dinv);
   else
-    k_assemble_dense<3><<<blocks_for(n * n), kThreads, 0, st>>>(d, K0, x, Ae, fixed, A);
+    k_assemble_dense<3><<<blocks_for(na * na), kThreads, 0, st>>>(d, K0, x, Ae, fixed, A, ld, w,
+                                                                  zll, g, Dinv);
   return cudaGetLastError();
 }
 

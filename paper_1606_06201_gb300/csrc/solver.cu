@@ -17,7 +17,7 @@
 #include <string>
 #include <vector>
 
-#include "topo_internal.cuh"
+#include "solver.cuh"
 
 namespace topo {
 
@@ -34,86 +34,7 @@ topo_status cuda_status(cudaError_t e, const char* what) {
 
 using namespace topo;
 
-struct topo_solver {
-  topo_solver_desc desc{};
-  int dim = 2, nlev = 1, prec = TOPO_FP64, nrhs = 1, ne = 8;
-  cudaStream_t st = nullptr;     // private stream
-  cudaStream_t user = nullptr;   // caller's stream (nullptr = legacy default stream)
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
-  std::vector<Level> L;
-  std::vector<uint8_t> fixed_host;
-  double* K0 = nullptr;
-  float* K0f = nullptr;
-  double* C = nullptr;           // constant child matrices P_c^T K0 P_c
-  Q1Coef q1{};                   // butterfly coefficients of the 2D K0
-  bool q1_ok = false;            // 2D and T^T Khat T reproduces K0: use the warp-sweep kernels
-  double* x = nullptr;
-  float* x32 = nullptr;
-  int nc = 0;                    // DOFs of the coarsest level
-  double* Adense = nullptr;
-  double* Ainv = nullptr;
-  int* info = nullptr;
-  double *z = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
-  void* yold = nullptr;          // previous preconditioned residual (flexible beta)
-  void* rv = nullptr;            // residual in V-cycle precision (mixed)
-  void* yv = nullptr;            // where the captured V-cycle leaves its result
-  double* partials = nullptr;
-  unsigned* counters = nullptr;
-  CgScalars* sc = nullptr;
-  CgScalars* sc_host = nullptr;  // pinned
-  double* dots = nullptr;
-  double* dots_host = nullptr;
-  double* bbuf = nullptr;        // solver-owned copy of the right-hand side
-  cudaGraphExec_t graph = nullptr;        // graph_iters CG iterations
-  int graph_kernels = 0;
-  double graph_tol = -1.0;                // tolerance baked into the captured graphs
-  cudaGraphExec_t setup[2] = {nullptr, nullptr};  // CG start (use_x0 = 0 / 1)
-  int setup_kernels[2] = {0, 0};
-  double setup_tol[2] = {-1.0, -1.0};
-  cudaGraphExec_t build = nullptr;        // Galerkin hierarchy and coarsest factorisation
-  int build_kernels = 0;
-  int graph_iters = 4;
-  unsigned long long launches = 0;        // kernels launched by this solver
-  bool profiling = false;
-  std::vector<cudaEvent_t> prof_ev;       // event pairs around the outer operator per slot
-  double prof_ms = 0.0;
-  long long prof_count = 0;
-  bool have_density = false;
-  size_t bytes = 0;
-  std::vector<void*> allocs;
-
-  template <typename T>
-  topo_status alloc(T** ptr, size_t count) {
-    *ptr = nullptr;
-    if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
-    if (e != cudaSuccess) return cuda_status(e, "cudaMalloc");
-    allocs.push_back((void*)*ptr);
-    bytes += count * sizeof(T);
-    return TOPO_OK;
-  }
-};
-
 namespace {
-
-#define TOPO_TRY(expr)                  \
-  do {                                  \
-    topo_status _s = (expr);            \
-    if (_s != TOPO_OK) return _s;       \
-  } while (0)
-
-// Caller-stream ordering around a library call.
-struct StreamGuard {
-  topo_solver* s;
-  explicit StreamGuard(topo_solver* s_) : s(s_) {
-    cudaEventRecord(s->ev_in, s->user);
-    cudaStreamWaitEvent(s->st, s->ev_in, 0);
-  }
-  ~StreamGuard() {
-    cudaEventRecord(s->ev_out, s->st);
-    cudaStreamWaitEvent(s->user, s->ev_out, 0);
-  }
-};
 
 double w1h(int p, int q) {
   const int d = p - 2 * q;
@@ -238,13 +159,59 @@ struct Prec<float> {
 // Operator application on level k (mode as launch_apply): the warp-sweep Q1 kernels on the 2D
 // finest level, the generic element-matrix kernels elsewhere.
 template <typename TV>
+const TV* arrow_w(const Level& l);
+template <>
+const double* arrow_w<double>(const Level& l) { return l.w; }
+template <>
+const float* arrow_w<float>(const Level& l) { return l.w32; }
+
+template <typename TV>
+struct ArrowFine;
+template <>
+struct ArrowFine<double> {
+  static const double* g(topo_solver* s) { return s->g; }
+  static const double* Dinv(topo_solver* s) { return s->Dinv; }
+  static double* se(topo_solver* s) { return s->se; }
+};
+template <>
+struct ArrowFine<float> {
+  static const float* g(topo_solver* s) { return s->g32; }
+  static const float* Dinv(topo_solver* s) { return s->Dinv32; }
+  static float* se(topo_solver* s) { return s->se32; }
+};
+
+// Operator application on level k (mode as launch_apply): the warp-sweep Q1 kernels on the 2D
+// finest level, the matrix-free first coarse level in mixed precision, the Z operator (element
+// rank-one terms and lambda row) for IP systems, the generic element-matrix kernels elsewhere.
+template <typename TV>
 topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* b, TV* y,
                         const CgScalars* sc) {
   Level& lv = s->L[k];
   const TV omega = (TV)s->desc.omega;
+  if (s->arrow) {
+    if (k == 0) {
+      TOPO_CUDA(launch_z_apply_fine<TV>(lv.d, mode, Prec<TV>::K0(s), Prec<TV>::x(s),
+                                        ArrowFine<TV>::g(s), ArrowFine<TV>::Dinv(s),
+                                        ArrowFine<TV>::se(s), v, b, y, Prec<TV>::invd(lv), omega,
+                                        lv.fixed, s->zll, s->partials, s->counters, sc, s->st));
+      return TOPO_OK;
+    }
+    TOPO_CUDA(launch_apply<TV>(lv.d, mode, Prec<TV>::K0(s), nullptr, Prec<TV>::Ae(lv), v, b, y,
+                               Prec<TV>::invd(lv), omega, lv.fixed, 1, sc, s->st,
+                               mode == 3 ? nullptr : arrow_w<TV>(lv)));
+    TOPO_CUDA(launch_arrow_row<TV>(lv.n, mode, arrow_w<TV>(lv), v, b, y, s->zll, (double)omega,
+                                   s->partials, s->counters, sc, s->st));
+    return TOPO_OK;
+  }
   if (k == 0 && s->q1_ok) {
     TOPO_CUDA(launch_q1_apply<TV>(lv.d.nx, lv.d.ny, mode, s->q1, Prec<TV>::x(s), v, b, y, omega,
                                   lv.fixed, s->nrhs, sc, s->st));
+    return TOPO_OK;
+  }
+  if (k == 1 && s->l1_free && std::is_same<TV, float>::value) {
+    TOPO_CUDA(launch_apply_l1<float>(lv.d, mode, s->C32, s->x32, (const float*)v, (const float*)b,
+                                     (float*)y, s->L[1].invd32, (float)omega, lv.fixed, s->nrhs,
+                                     sc, s->st));
     return TOPO_OK;
   }
   const TV* x = k == 0 ? Prec<TV>::x(s) : nullptr;
@@ -261,7 +228,7 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
   const int nrhs = s->nrhs;
   TV* zk = (TV*)lv.z;
   if (k == s->nlev - 1) {
-    TOPO_CUDA(launch_dense_solve<TV>(s->nc, s->Ainv, b, zk, nrhs, sc, s->st));
+    TOPO_CUDA(launch_dense_solve<TV>(s->nc + (s->arrow ? 1 : 0), s->Ainv, b, zk, nrhs, sc, s->st));
     *result = zk;
     return TOPO_OK;
   }
@@ -275,14 +242,14 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
       std::swap(cur, oth);
     }
   } else {
-    TOPO_CUDA(cudaMemsetAsync(cur, 0, sizeof(TV) * lv.n * nrhs, s->st));
+    TOPO_CUDA(cudaMemsetAsync(cur, 0, sizeof(TV) * s->vlen(k) * nrhs, s->st));
   }
   TOPO_TRY(apply_level<TV>(s, k, 1, cur, b, oth, sc));
   Level& lc = s->L[k + 1];
-  TOPO_CUDA(launch_restrict<TV>(lv.d, oth, (TV*)lc.b, lc.fixed, nrhs, sc, s->st));
+  TOPO_CUDA(launch_restrict<TV>(lv.d, oth, (TV*)lc.b, lc.fixed, nrhs, sc, s->st, s->arrow));
   TV* zc = nullptr;
   TOPO_TRY(vcycle<TV>(s, k + 1, (const TV*)lc.b, &zc, sc));
-  TOPO_CUDA(launch_prolong_add<TV>(lv.d, zc, cur, lv.fixed, nrhs, sc, s->st));
+  TOPO_CUDA(launch_prolong_add<TV>(lv.d, zc, cur, lv.fixed, nrhs, sc, s->st, s->arrow));
   for (int it = 0; it < nu2; ++it) {
     TOPO_TRY(apply_level<TV>(s, k, 2, cur, b, oth, sc));
     std::swap(cur, oth);
@@ -305,16 +272,20 @@ topo_status precondition(topo_solver* s, const CgScalars* sc, void** y) {
 template <typename TV>
 topo_status cg_iteration(topo_solver* s, int slot, double tol, int max_iter) {
   Level& l0 = s->L[0];
-  const long long n = l0.n;
+  const long long n = s->ncg();
   // external event-record nodes: a plain record during capture only tracks dependencies
   if (s->profiling)
     TOPO_CUDA(cudaEventRecordWithFlags(s->prof_ev[2 * slot], s->st, cudaEventRecordExternal));
-  if (s->q1_ok)
+  if (s->arrow) {
+    TOPO_TRY(apply_level<double>(s, 0, 0, s->p, nullptr, s->q, s->sc));
+    TOPO_CUDA(launch_cg_alpha(n, 1, s->p, s->q, s->partials, s->counters, s->sc, s->st));
+  } else if (s->q1_ok) {
     TOPO_CUDA(launch_q1_apply_dot(l0.d.nx, l0.d.ny, s->q1, s->x, s->p, s->q, l0.fixed, s->nrhs,
                                   s->partials, s->counters, s->sc, s->st));
-  else
+  } else {
     TOPO_CUDA(launch_apply_dot_fine(l0.d, s->K0, s->x, s->p, s->q, l0.fixed, s->nrhs, s->partials,
                                     s->counters, s->sc, s->st));
+  }
   if (s->profiling)
     TOPO_CUDA(cudaEventRecordWithFlags(s->prof_ev[2 * slot + 1], s->st, cudaEventRecordExternal));
   TV* rv = std::is_same<TV, double>::value ? nullptr : (TV*)s->rv;
@@ -368,8 +339,7 @@ topo_status launch_graph(topo_solver* s, cudaGraphExec_t g, int kernels) {
 
 template <typename TV>
 topo_status cg_setup(topo_solver* s, int use_x0, double tol, int max_iter) {
-  Level& l0 = s->L[0];
-  const long long n = l0.n;
+  const long long n = s->ncg();
   const int nrhs = s->nrhs;
   const double* Az = nullptr;
   if (use_x0) {
@@ -390,8 +360,7 @@ topo_status cg_setup(topo_solver* s, int use_x0, double tol, int max_iter) {
 template <typename TV>
 topo_status solve_impl(topo_solver* s, const double* b, double* u, double tol, int use_x0,
                        topo_solve_info* info) {
-  Level& l0 = s->L[0];
-  const long long n = l0.n;
+  const long long n = s->ncg();
   const int nrhs = s->nrhs;
   const int max_iter = s->desc.max_iter;
   const int ux = use_x0 ? 1 : 0;
@@ -471,27 +440,44 @@ topo_status solve_impl(topo_solver* s, const double* b, double* u, double tol, i
 
 topo_status enqueue_build(topo_solver* s) {
   const int nl = s->nlev;
+  const bool mixed = s->prec == TOPO_MIXED;
   cudaStream_t st = s->st;
-  TOPO_CUDA(launch_check_positive(s->x, s->L[0].m, s->info + 1, st));
-  if (s->prec == TOPO_MIXED) TOPO_CUDA(launch_convert_d2f(s->x, s->x32, s->L[0].m, st));
+  const long long m = s->L[0].m;
+  const int ne2 = s->ne * s->ne;
+  TOPO_CUDA(launch_check_positive(s->x, m, s->info + 1, st));
+  if (mixed) TOPO_CUDA(launch_convert_d2f(s->x, s->x32, m, st));
+  if (s->arrow && mixed) {
+    TOPO_CUDA(launch_convert_d2f(s->g, s->g32, m * s->ne, st));
+    TOPO_CUDA(launch_convert_d2f(s->Dinv, s->Dinv32, m, st));
+  }
   for (int k = 1; k < nl; ++k) {
     if (k == 1)
-      TOPO_CUDA(launch_rap_from_fine(s->L[0].d, s->C, s->x, s->L[1].Ae, st));
+      TOPO_CUDA(launch_rap_from_fine(s->L[0].d, s->C, s->x, s->L[1].Ae, st,
+                                     s->arrow ? s->g : nullptr, s->arrow ? s->Dinv : nullptr));
     else
       TOPO_CUDA(launch_rap_coarse(s->L[k - 1].d, s->L[k - 1].Ae, s->L[k].Ae, st));
+    if (s->arrow)
+      TOPO_CUDA(launch_restrict<double>(s->L[k - 1].d, s->L[k - 1].w, s->L[k].w, s->L[k].fixed, 1,
+                                        nullptr, st, 0));
   }
   for (int k = 0; k < nl - 1; ++k) {
     Level& lv = s->L[k];
-    TOPO_CUDA(launch_inv_diag(lv.d, s->K0, k == 0 ? s->x : nullptr, lv.Ae, lv.fixed, lv.invd, st));
-    if (s->prec == TOPO_MIXED) {
+    if (!(s->arrow && k == 0))  // the IP driver writes the finest diagonal of Z
+      TOPO_CUDA(launch_inv_diag(lv.d, s->K0, k == 0 ? s->x : nullptr, lv.Ae, lv.fixed, lv.invd, st));
+    if (mixed) {
       TOPO_CUDA(launch_convert_d2f(lv.invd, lv.invd32, lv.n, st));
-      if (k >= 1) TOPO_CUDA(launch_convert_d2f(lv.Ae, lv.Ae32, lv.m * s->ne * s->ne, st));
+      if (k >= 1 && lv.Ae32) TOPO_CUDA(launch_convert_d2f(lv.Ae, lv.Ae32, lv.m * ne2, st));
     }
   }
+  if (s->arrow && mixed)
+    for (int k = 0; k < nl; ++k) TOPO_CUDA(launch_convert_d2f(s->L[k].w, s->L[k].w32, s->L[k].n, st));
   Level& lc = s->L[nl - 1];
-  TOPO_CUDA(launch_assemble_dense(lc.d, s->K0, nl == 1 ? s->x : nullptr, lc.Ae, lc.fixed, s->Adense,
-                                  st));
-  TOPO_CUDA(launch_cholesky_inverse(s->nc, s->Adense, s->Ainv, s->info, st));
+  const bool fine_coarsest = (nl == 1);
+  TOPO_CUDA(launch_assemble_dense(lc.d, s->K0, fine_coarsest ? s->x : nullptr, lc.Ae, lc.fixed,
+                                  s->Adense, st, 0, s->arrow ? lc.w : nullptr, s->zll,
+                                  (s->arrow && fine_coarsest) ? s->g : nullptr,
+                                  (s->arrow && fine_coarsest) ? s->Dinv : nullptr));
+  TOPO_CUDA(launch_cholesky_inverse(s->nc + (s->arrow ? 1 : 0), s->Adense, s->Ainv, s->info, st));
   return TOPO_OK;
 }
 
@@ -546,8 +532,9 @@ topo_status topo_solver_destroy(topo_solver* s) {
   return TOPO_OK;
 }
 
-static topo_status create_impl(const topo_solver_desc* d, topo_solver* s) {
+static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool arrow) {
   s->desc = *d;
+  s->arrow = arrow;
   s->dim = d->dim;
   s->nlev = d->levels;
   s->prec = d->precision;
@@ -564,13 +551,17 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s) {
   element_stiffness_host(s->dim, d->E, d->nu, K0.data());
   child_matrices(s->dim, K0.data(), C);
   s->q1_ok = (s->dim == 2) && q1_coefficients(d->E, d->nu, K0.data(), s->q1) && !d->generic_kernels;
-  std::vector<float> K0f(K0.begin(), K0.end());
+  s->l1_free = (s->dim == 2) && !arrow && s->prec == TOPO_MIXED && s->nlev >= 3 &&
+               !d->generic_kernels;
+  std::vector<float> K0f(K0.begin(), K0.end()), C32(C.begin(), C.end());
   TOPO_TRY(s->alloc(&s->K0, ne * ne));
   TOPO_TRY(s->alloc(&s->K0f, ne * ne));
   TOPO_TRY(s->alloc(&s->C, C.size()));
+  TOPO_TRY(s->alloc(&s->C32, C32.size()));
   TOPO_CUDA(cudaMemcpy(s->K0, K0.data(), sizeof(double) * ne * ne, cudaMemcpyHostToDevice));
   TOPO_CUDA(cudaMemcpy(s->K0f, K0f.data(), sizeof(float) * ne * ne, cudaMemcpyHostToDevice));
   TOPO_CUDA(cudaMemcpy(s->C, C.data(), sizeof(double) * C.size(), cudaMemcpyHostToDevice));
+  TOPO_CUDA(cudaMemcpy(s->C32, C32.data(), sizeof(float) * C32.size(), cudaMemcpyHostToDevice));
   // levels and masks
   Dims d0{d->nx, d->ny, d->dim == 3 ? d->nz : 1, d->dim};
   s->L.resize(s->nlev);
@@ -587,17 +578,24 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s) {
     TOPO_TRY(s->alloc(&lv.fixed, lv.n));
     TOPO_CUDA(cudaMemcpy(lv.fixed, mask.data(), lv.n, cudaMemcpyHostToDevice));
     const bool coarsest = (k == s->nlev - 1);
+    const long long vl = lv.n + (arrow ? 2 : 0);
     if (k >= 1) {
       TOPO_TRY(s->alloc(&lv.Ae, lv.m * ne * ne));
-      if (s->prec == TOPO_MIXED && !coarsest) TOPO_TRY(s->alloc(&lv.Ae32, lv.m * ne * ne));
+      const bool l1_matrix_free = (k == 1 && s->l1_free);
+      if (s->prec == TOPO_MIXED && !coarsest && !l1_matrix_free)
+        TOPO_TRY(s->alloc(&lv.Ae32, lv.m * ne * ne));
+    }
+    if (arrow) {
+      TOPO_TRY(s->alloc(&lv.w, lv.n));
+      if (s->prec == TOPO_MIXED) TOPO_TRY(s->alloc(&lv.w32, lv.n));
     }
     if (!coarsest) {
       TOPO_TRY(s->alloc(&lv.invd, lv.n));
       if (s->prec == TOPO_MIXED) TOPO_TRY(s->alloc(&lv.invd32, lv.n));
-      TOPO_TRY(s->alloc((char**)&lv.t, vbytes * lv.n * nrhs));
+      TOPO_TRY(s->alloc((char**)&lv.t, vbytes * vl * nrhs));
     }
-    if (k >= 1) TOPO_TRY(s->alloc((char**)&lv.b, vbytes * lv.n * nrhs));
-    TOPO_TRY(s->alloc((char**)&lv.z, vbytes * lv.n * nrhs));
+    if (k >= 1) TOPO_TRY(s->alloc((char**)&lv.b, vbytes * vl * nrhs));
+    TOPO_TRY(s->alloc((char**)&lv.z, vbytes * vl * nrhs));
     if (!coarsest) {
       std::vector<uint8_t> next;
       std::string why;
@@ -611,15 +609,25 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s) {
   }
   Level& lc = s->L[s->nlev - 1];
   s->nc = (int)lc.n;
-  TOPO_TRY(s->alloc(&s->Adense, (size_t)s->nc * s->nc));
-  TOPO_TRY(s->alloc(&s->Ainv, (size_t)s->nc * s->nc));
+  const size_t na = (size_t)s->nc + (arrow ? 1 : 0);
+  TOPO_TRY(s->alloc(&s->Adense, na * na));
+  TOPO_TRY(s->alloc(&s->Ainv, na * na));
   TOPO_TRY(s->alloc(&s->info, 2));
-  // densities and CG vectors
-  const long long n = s->L[0].n, m = s->L[0].m;
+  // densities and CG vectors (IP systems: trailing lambda entry, padded to an even length)
+  const long long m = s->L[0].m;
+  const long long n = s->L[0].n + (arrow ? 2 : 0);
   TOPO_TRY(s->alloc(&s->x, m));
   if (s->prec == TOPO_MIXED) {
     TOPO_TRY(s->alloc(&s->x32, m));
     TOPO_TRY(s->alloc((float**)&s->rv, n * nrhs));
+  }
+  if (arrow) {
+    TOPO_TRY(s->alloc(&s->se, m));
+    if (s->prec == TOPO_MIXED) {
+      TOPO_TRY(s->alloc(&s->se32, m));
+      TOPO_TRY(s->alloc(&s->g32, m * ne));
+      TOPO_TRY(s->alloc(&s->Dinv32, m));
+    }
   }
   TOPO_TRY(s->alloc(&s->bbuf, n * nrhs));
   TOPO_TRY(s->alloc(&s->z, n * nrhs));
@@ -666,7 +674,7 @@ topo_status topo_solver_create(const topo_solver_desc* d, topo_solver** out) {
     return TOPO_E_INVALID_ARG;
   }
   topo_solver* s = new topo_solver();
-  topo_status st = create_impl(d, s);
+  topo_status st = create_impl(d, s, false);
   if (st != TOPO_OK) {
     std::string keep = g_last_error;
     topo_solver_destroy(s);
@@ -778,9 +786,13 @@ topo_status topo_get_level_matrices(topo_solver* s, int level, double* out_host)
   }
   StreamGuard g(s);
   const Level& lv = s->L[level];
-  TOPO_CUDA(cudaMemcpyAsync(out_host, lv.Ae, sizeof(double) * lv.m * s->ne * s->ne,
-                            cudaMemcpyDeviceToHost, s->st));
+  const long long ne2 = (long long)s->ne * s->ne;
+  std::vector<double> tmp(lv.m * ne2);
+  TOPO_CUDA(cudaMemcpyAsync(tmp.data(), lv.Ae, sizeof(double) * tmp.size(), cudaMemcpyDeviceToHost,
+                            s->st));
   TOPO_CUDA(cudaStreamSynchronize(s->st));
+  for (long long e = 0; e < lv.m; ++e)
+    for (long long q = 0; q < ne2; ++q) out_host[e * ne2 + q] = tmp[q * lv.m + e];
   return TOPO_OK;
 }
 
@@ -819,3 +831,40 @@ topo_status topo_grad_x(topo_solver* s, const double* lam, const double* u, doub
 }
 
 }  // extern "C"
+
+namespace topo {
+
+topo_status solver_create_internal(const topo_solver_desc* d, bool arrow, topo_solver** out) {
+  topo_status st = topo_solver_create(d, out);  // validates the descriptor
+  if (st != TOPO_OK || !arrow) return st;
+  topo_solver_destroy(*out);
+  *out = nullptr;
+  if (d->nrhs != 1) {
+    set_error("IP systems are solved one right-hand side at a time");
+    return TOPO_E_INVALID_ARG;
+  }
+  topo_solver* s = new topo_solver();
+  st = create_impl(d, s, true);
+  if (st != TOPO_OK) {
+    std::string keep = g_last_error;
+    topo_solver_destroy(s);
+    g_last_error = keep;
+    return st;
+  }
+  *out = s;
+  return TOPO_OK;
+}
+
+topo_status solver_build(topo_solver* s) {
+  topo_status st = build_hierarchy(s);
+  s->have_density = (st == TOPO_OK);
+  return st;
+}
+
+topo_status solver_solve(topo_solver* s, const double* b, double* u, double tol, int use_x0,
+                         topo_solve_info* info) {
+  if (s->prec == TOPO_MIXED) return solve_impl<float>(s, b, u, tol, use_x0, info);
+  return solve_impl<double>(s, b, u, tol, use_x0, info);
+}
+
+}  // namespace topo

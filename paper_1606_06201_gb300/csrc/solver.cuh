@@ -1,0 +1,113 @@
+// Solver object shared by the host translation units (solver.cu: MGCG; ipoc.cu: IP and OC).
+#pragma once
+
+#include <vector>
+
+#include "topo_internal.cuh"
+
+using namespace topo;
+
+#define TOPO_TRY(expr)            \
+  do {                            \
+    topo_status _s = (expr);      \
+    if (_s != TOPO_OK) return _s; \
+  } while (0)
+
+struct topo_solver {
+  topo_solver_desc desc{};
+  int dim = 2, nlev = 1, prec = TOPO_FP64, nrhs = 1, ne = 8;
+  cudaStream_t st = nullptr;     // private stream
+  cudaStream_t user = nullptr;   // caller's stream (nullptr = legacy default stream)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+  std::vector<Level> L;
+  std::vector<uint8_t> fixed_host;
+  double* K0 = nullptr;
+  float* K0f = nullptr;
+  double* C = nullptr;           // constant child matrices P_c^T K0 P_c
+  Q1Coef q1{};                   // butterfly coefficients of the 2D K0
+  bool q1_ok = false;            // 2D and T^T Khat T reproduces K0: use the warp-sweep kernels
+  double* x = nullptr;
+  float* x32 = nullptr;
+  float* C32 = nullptr;          // FP32 copy of C (matrix-free first coarse level)
+  bool l1_free = false;          // mixed 2D K systems: level 1 applied matrix-free in FP32
+  // Arrow (IP) systems Z = [K 0; 0 0] + [B; e^T] D^{-1} [B^T e] (Eq. (nwtr2Z)): vectors carry a
+  // trailing lambda entry; g_e = K0 u_e and Dinv = 1/D on the finest level are owned by the IP
+  // driver; zll points to Z_ll = sum 1/D on the device.
+  bool arrow = false;
+  const double* g = nullptr;
+  const double* Dinv = nullptr;
+  const double* zll = nullptr;
+  float* g32 = nullptr;
+  float* Dinv32 = nullptr;
+  double* se = nullptr;          // element scalars s_e of the Z operator
+  float* se32 = nullptr;
+  int nc = 0;                    // DOFs of the coarsest level
+  double* Adense = nullptr;
+  double* Ainv = nullptr;
+  int* info = nullptr;
+  double *z = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+  void* yold = nullptr;          // previous preconditioned residual (flexible beta)
+  void* rv = nullptr;            // residual in V-cycle precision (mixed)
+  void* yv = nullptr;            // where the captured V-cycle leaves its result
+  double* partials = nullptr;
+  unsigned* counters = nullptr;
+  CgScalars* sc = nullptr;
+  CgScalars* sc_host = nullptr;  // pinned
+  double* dots = nullptr;
+  double* dots_host = nullptr;
+  double* bbuf = nullptr;        // solver-owned copy of the right-hand side
+  cudaGraphExec_t graph = nullptr;        // graph_iters CG iterations
+  int graph_kernels = 0;
+  double graph_tol = -1.0;                // tolerance baked into the captured graphs
+  cudaGraphExec_t setup[2] = {nullptr, nullptr};  // CG start (use_x0 = 0 / 1)
+  int setup_kernels[2] = {0, 0};
+  double setup_tol[2] = {-1.0, -1.0};
+  cudaGraphExec_t build = nullptr;        // Galerkin hierarchy and coarsest factorisation
+  int build_kernels = 0;
+  int graph_iters = 4;
+  unsigned long long launches = 0;        // kernels launched by this solver
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_ev;       // event pairs around the outer operator per slot
+  double prof_ms = 0.0;
+  long long prof_count = 0;
+  bool have_density = false;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+
+  long long vlen(int k) const { return L[k].n + (arrow ? 2 : 0); }  // allocated vector length
+  long long ncg() const { return L[0].n + (arrow ? 1 : 0); }         // CG vector length
+
+  template <typename T>
+  topo_status alloc(T** ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
+    if (e != cudaSuccess) return cuda_status(e, "cudaMalloc");
+    allocs.push_back((void*)*ptr);
+    bytes += count * sizeof(T);
+    return TOPO_OK;
+  }
+};
+
+namespace topo {
+topo_status solver_create_internal(const topo_solver_desc* d, bool arrow, topo_solver** out);
+topo_status solver_build(topo_solver* s);
+topo_status solver_solve(topo_solver* s, const double* b, double* u, double tol, int use_x0,
+                         topo_solve_info* info);
+
+// Caller-stream ordering around a library call on the solver's private stream.
+struct StreamGuard {
+  cudaStream_t priv, user;
+  cudaEvent_t in, out;
+  StreamGuard(cudaStream_t priv_, cudaStream_t user_, cudaEvent_t in_, cudaEvent_t out_)
+      : priv(priv_), user(user_), in(in_), out(out_) {
+    cudaEventRecord(in, user);
+    cudaStreamWaitEvent(priv, in, 0);
+  }
+  explicit StreamGuard(topo_solver* s) : StreamGuard(s->st, s->user, s->ev_in, s->ev_out) {}
+  ~StreamGuard() {
+    cudaEventRecord(out, priv);
+    cudaStreamWaitEvent(user, out, 0);
+  }
+};
+}  // namespace topo

@@ -45,15 +45,36 @@ struct CgScalars {
   int pad;
 };
 
+// Device-resident scalars of the interior-point method.
+struct IpScalars {
+  double lam, s, r;              // multiplier of the volume constraint, barrier parameters
+  double V, xbar, frac;          // problem data, fraction-to-boundary factor (0.9)
+  double sum_x, sum_t, res2;     // sum x, sum tilde Res3 / D, V - sum x
+  double nrm_tr3, nrm_phi, nrm_psi, nrm_res1;
+  double zll;                    // Z_ll = sum 1 / D
+  double alpha, dlam;            // step length, lambda direction
+  int step_all;                  // 1: 0.9 rule also on phi and psi
+  int pad;
+};
+
+// Device-resident scalars of the OC bisection.
+struct OcScalars {
+  double lo, hi, tau, lam_last;
+  double V, xlow, xbar;
+  int steps, pad;
+};
+
 // Per-level data of the multigrid hierarchy.  Level 0 is the finest.
 struct Level {
   Dims d;
   long long n = 0, m = 0;          // DOFs, elements
   uint8_t* fixed = nullptr;        // [n] 1 = fixed DOF
-  double* Ae = nullptr;            // coarse levels: element matrices [m][ne][ne] FP64
+  double* Ae = nullptr;            // coarse levels: element matrices, entry-major [ne*ne][m] FP64
   float* Ae32 = nullptr;           // FP32 copy (mixed precision)
   double* invd = nullptr;          // 1 / diag(A) [n] (1 on fixed DOFs)
   float* invd32 = nullptr;
+  double* w = nullptr;             // arrow column Z_ul on this level (IP systems) [n]
+  float* w32 = nullptr;
   void* b = nullptr;               // V-cycle right-hand side   [nrhs][n] (FP64 or FP32)
   void* z = nullptr;               // V-cycle iterate
   void* t = nullptr;               // ping-pong / residual scratch
@@ -93,22 +114,31 @@ void element_stiffness_host(int dim, double E, double nu, double* K0);
 // Operator application on one level.  mode: 0 y = A v; 1 y = b - A v; 2 y = v + omega invd (b - A v);
 // 3 y = omega invd b (first Jacobi sweep from zero, v unused).  x != nullptr: finest level with
 // element matrices x_e K0; otherwise Ae holds element matrices.  nrhs vectors of length n.
+// w != nullptr adds the arrow column: y_u += w v_lambda with v_lambda = v[n] (nrhs = 1).
 template <typename T>
 cudaError_t launch_apply(const Dims& d, int mode, const T* K0, const T* x, const T* Ae, const T* v,
                          const T* b,
                          T* y, const T* invd, T omega, const uint8_t* fixed, int nrhs,
-                         const CgScalars* sc, cudaStream_t st);
+                         const CgScalars* sc, cudaStream_t st, const T* w = nullptr);
+// First coarse level of a 2D grid, matrix-free from the finest densities xf and the four child
+// matrices C (same modes as launch_apply).
+template <typename T>
+cudaError_t launch_apply_l1(const Dims& d, int mode, const T* C, const T* xf, const T* v,
+                            const T* b, T* y, const T* invd, T omega, const uint8_t* fixed,
+                            int nrhs, const CgScalars* sc, cudaStream_t st);
 // y = A v in FP64 on the finest level with a fused per-block partial of v^T y (for p^T A p).
 cudaError_t launch_apply_dot_fine(const Dims& d, const double* K0, const double* x, const double* v,
                                   double* y,
                                   const uint8_t* fixed, int nrhs, double* partials,
                                   unsigned* counters, CgScalars* sc, cudaStream_t st);
+// arrow: the trailing lambda entry is carried by the identity (restriction copies it,
+// prolongation adds it).
 template <typename T>
 cudaError_t launch_restrict(const Dims& fine, const T* rf, T* rc, const uint8_t* fixed_c, int nrhs,
-                            const CgScalars* sc, cudaStream_t st);
+                            const CgScalars* sc, cudaStream_t st, int arrow = 0);
 template <typename T>
 cudaError_t launch_prolong_add(const Dims& fine, const T* zc, T* zf, const uint8_t* fixed_f,
-                               int nrhs, const CgScalars* sc, cudaStream_t st);
+                               int nrhs, const CgScalars* sc, cudaStream_t st, int arrow = 0);
 cudaError_t launch_inv_diag(const Dims& d, const double* K0, const double* x, const double* Ae,
                             const uint8_t* fixed, double* invd, cudaStream_t st);
 cudaError_t launch_element_energy(const Dims& d, const double* K0, const double* u,
@@ -126,12 +156,19 @@ cudaError_t launch_q1_apply_dot(int nx, int ny, const Q1Coef& coef, const double
 long long q1_partial_blocks(int nx, int ny);
 
 // Hierarchy construction (kernels_rap.cu).
+// g, Dinv != nullptr: add the rank-one terms (P_c^T g_c)(P_c^T g_c)^T Dinv_c of Z.
 cudaError_t launch_rap_from_fine(const Dims& fine, const double* C, const double* x, double* Ac,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const double* g = nullptr,
+                                 const double* Dinv = nullptr);
 cudaError_t launch_rap_coarse(const Dims& fine, const double* Af, double* Ac, cudaStream_t st);
+// Dense operator of a level with leading dimension ld; with an arrow (w != nullptr) the row and
+// column n hold w (zero on fixed DOFs) and A[n][n] = *zll.  g, Dinv: rank-one terms (finest level).
 cudaError_t launch_assemble_dense(const Dims& d, const double* K0, const double* x,
                                   const double* Ae,
-                                  const uint8_t* fixed, double* A, cudaStream_t st);
+                                  const uint8_t* fixed, double* A, cudaStream_t st,
+                                  long long ld = 0, const double* w = nullptr,
+                                  const double* zll = nullptr, const double* g = nullptr,
+                                  const double* Dinv = nullptr);
 cudaError_t launch_cholesky_inverse(int n, double* A, double* Ainv, int* info, cudaStream_t st);
 template <typename T>
 cudaError_t launch_dense_solve(int n, const double* Ainv, const T* b, T* z, int nrhs,
@@ -158,5 +195,35 @@ cudaError_t launch_cg_direction(long long n, int nrhs, const double* r, const TV
                                 CgScalars* sc, cudaStream_t st);
 cudaError_t launch_dot(long long n, int nrhs, const double* a, const double* b, double* partials,
                        unsigned* counters, double* out, cudaStream_t st);
+// p^T q and alpha = r^T y / p^T q (breakdown checks as in the fused operator kernel).
+cudaError_t launch_cg_alpha(long long n, int nrhs, const double* p, const double* q,
+                            double* partials, unsigned* counters, CgScalars* sc, cudaStream_t st);
+
+// IP and OC kernels (kernels_ip.cu).
+template <typename T>
+cudaError_t launch_z_apply_fine(const Dims& d, int mode, const T* K0, const T* x, const T* g,
+                                const T* Dinv, T* se, const T* v, const T* b, T* y, const T* invd,
+                                T omega, const uint8_t* fixed, const double* zll, double* partials,
+                                unsigned* counter, const CgScalars* sc, cudaStream_t st);
+template <typename T>
+cudaError_t launch_arrow_row(long long n, int mode, const T* w, const T* v, const T* b, T* y,
+                             const double* zll, double omega, double* partials, unsigned* counter,
+                             const CgScalars* sc, cudaStream_t st);
+cudaError_t launch_ip_residuals(const Dims& d, const double* K0, const double* u, const double* x,
+                                const double* phi, const double* psi, const double* f,
+                                const uint8_t* fixed, IpScalars* ip, double* g, double* tR3,
+                                double* Dinv, double* t, double* rhs, double* w, double* invd,
+                                double* partials, unsigned* counter, cudaStream_t st);
+cudaError_t launch_ip_recover_update(const Dims& d, const double* g, const double* du,
+                                     const double* tR3, const double* Dinv, double* u, double* x,
+                                     double* phi, double* psi, double* dx, double* dphi,
+                                     double* dpsi, IpScalars* ip, double* partials,
+                                     unsigned* counter, cudaStream_t st);
+cudaError_t launch_oc_bisection(long long m, const double* x, const double* E, OcScalars* oc,
+                                int steps, double* xout, double* partials, unsigned* counter,
+                                cudaStream_t st);
+cudaError_t launch_average(long long m, const double* a, const double* b, double* out,
+                           cudaStream_t st);
+cudaError_t launch_pow_inplace(long long m, double* E, double q, cudaStream_t st);
 
 }  // namespace topo

@@ -37,6 +37,36 @@ class SolveInfo(ctypes.Structure):
                 ("wall_ms", ctypes.c_double), ("status", ctypes.c_int)]
 
 
+class IpOpts(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("tau_nwt", ctypes.c_double),
+                ("tau_ip", ctypes.c_double), ("frac", ctypes.c_double),
+                ("step_x_only", ctypes.c_int), ("max_newton", ctypes.c_int),
+                ("cg_tol", ctypes.c_double), ("cg_tol_init", ctypes.c_double)]
+
+
+class IpInfo(ctypes.Structure):
+    _fields_ = [("newton", ctypes.c_int), ("ip_iters", ctypes.c_int), ("feval", ctypes.c_int),
+                ("cg_iters", ctypes.c_int), ("s", ctypes.c_double), ("r", ctypes.c_double),
+                ("lam", ctypes.c_double), ("alpha", ctypes.c_double), ("crit", ctypes.c_double),
+                ("done", ctypes.c_int), ("status", ctypes.c_int), ("wall_ms", ctypes.c_double)]
+
+
+class OcOpts(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("q", ctypes.c_double), ("xlow", ctypes.c_double),
+                ("lam_hi", ctypes.c_double), ("tau_lambda", ctypes.c_double),
+                ("tau_oc", ctypes.c_double), ("max_feval", ctypes.c_int),
+                ("cg_tol0", ctypes.c_double), ("adaptive_tol", ctypes.c_int)]
+
+
+class OcInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("feval", ctypes.c_int), ("cg_iters", ctypes.c_int),
+                ("compliance", ctypes.c_double), ("compliance_prev", ctypes.c_double),
+                ("lam", ctypes.c_double), ("cg_tol", ctypes.c_double), ("status", ctypes.c_int),
+                ("wall_ms", ctypes.c_double)]
+
+
+OC_PLAIN, OC_DOC, OC_AOC = 0, 1, 2
+
 _vp = ctypes.c_void_p
 _SIGS = {
     "topo_last_error": (ctypes.c_char_p, []),
@@ -59,6 +89,24 @@ _SIGS = {
     "topo_compliance": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "topo_element_energy": (ctypes.c_int, [_vp, _vp, _vp]),
     "topo_grad_x": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "topo_ip_create": (ctypes.c_int, [ctypes.POINTER(SolverDesc), _vp, ctypes.c_double,
+                                      ctypes.c_double, ctypes.POINTER(_vp)]),
+    "topo_ip_destroy": (ctypes.c_int, [_vp]),
+    "topo_ip_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "topo_ip_init": (ctypes.c_int, [_vp, ctypes.POINTER(IpOpts)]),
+    "topo_ip_step": (ctypes.c_int, [_vp, ctypes.POINTER(IpOpts), ctypes.POINTER(IpInfo)]),
+    "topo_ip_run": (ctypes.c_int, [_vp, ctypes.POINTER(IpOpts), ctypes.POINTER(IpInfo)]),
+    "topo_ip_get_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "topo_ip_set_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "topo_oc_create": (ctypes.c_int, [ctypes.POINTER(SolverDesc), _vp, ctypes.c_double,
+                                      ctypes.c_double, ctypes.POINTER(_vp)]),
+    "topo_oc_destroy": (ctypes.c_int, [_vp]),
+    "topo_oc_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "topo_oc_init": (ctypes.c_int, [_vp, _vp]),
+    "topo_oc_step": (ctypes.c_int, [_vp, ctypes.POINTER(OcOpts), ctypes.POINTER(OcInfo)]),
+    "topo_oc_run": (ctypes.c_int, [_vp, ctypes.POINTER(OcOpts), ctypes.POINTER(OcInfo)]),
+    "topo_oc_get_x": (ctypes.c_int, [_vp, _vp]),
+    "topo_oc_get_u": (ctypes.c_int, [_vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -92,6 +140,148 @@ def element_stiffness(dim, E=1.0, nu=0.3):
     K0 = np.zeros((ne, ne))
     _check(_lib.topo_element_stiffness(dim, E, nu, K0.ctypes.data_as(_vp)), "topo_element_stiffness")
     return K0
+
+
+def _desc(nx, ny, nz, fixed, levels, precision, nu1, nu2, omega, max_iter, nrhs, flexible, E, nu,
+          generic_kernels):
+    dim = 3 if nz else 2
+    n = dim * (nx + 1) * (ny + 1) * ((nz + 1) if nz else 1)
+    if fixed is None:
+        fixed = np.zeros(n, dtype=np.uint8)
+    fixed = np.ascontiguousarray(np.asarray(fixed, dtype=np.uint8))
+    if fixed.size != n:
+        raise ValueError("fixed mask has %d entries, expected %d" % (fixed.size, n))
+    if omega is None:
+        omega = 0.6 if dim == 2 else 0.5
+    if flexible is None:
+        flexible = 1 if precision == MIXED else 0
+    d = SolverDesc(dim, nx, ny, nz, E, nu, fixed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                   levels, precision, nu1, nu2, omega, max_iter, nrhs, flexible,
+                   int(generic_kernels))
+    return d, fixed, dim, n
+
+
+def ip_options(sigma=0.2, tau_nwt=0.1, tau_ip=1e-8, frac=0.9, step_x_only=False, max_newton=500,
+               cg_tol=1e-8, cg_tol_init=None):
+    """Sec. 3 defaults; cg_tol is the relative residual of every Z solve."""
+    return IpOpts(sigma, tau_nwt, tau_ip, frac, int(step_x_only), max_newton, cg_tol,
+                  cg_tol if cg_tol_init is None else cg_tol_init)
+
+
+def oc_options(variant=OC_AOC, q=0.5, xlow=1e-6, lam_hi=1e4, tau_lambda=1e-11, tau_oc=1e-5,
+               max_feval=10000, cg_tol0=1e-4, adaptive_tol=True):
+    """Sec. 4 and Sec. 6.2 defaults."""
+    return OcOpts(variant, q, xlow, lam_hi, tau_lambda, tau_oc, max_feval, cg_tol0,
+                  int(adaptive_tol))
+
+
+class IP:
+    """Primal-dual interior-point method on the GPU (see include/topo.h)."""
+
+    def __init__(self, nx, ny, nz=0, fixed=None, f=None, V=None, xbar=1.0, levels=3,
+                 precision=FP64, nu1=2, nu2=2, omega=None, max_iter=1000, E=1.0, nu=0.3):
+        import torch
+        d, self._fixed, self.dim, self.n = _desc(nx, ny, nz, fixed, levels, precision, nu1, nu2,
+                                                 omega, max_iter, 1, None, E, nu, False)
+        self.m = nx * ny * (nz if nz else 1)
+        self._f = f
+        h = _vp()
+        _check(_lib.topo_ip_create(ctypes.byref(d), _ptr(f), float(V), float(xbar),
+                                   ctypes.byref(h)), "topo_ip_create")
+        self._h = h
+        _check(_lib.topo_ip_set_stream(h, _vp(torch.cuda.current_stream().cuda_stream)),
+               "topo_ip_set_stream")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.topo_ip_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, opts):
+        _check(_lib.topo_ip_init(self._h, ctypes.byref(opts)), "topo_ip_init")
+
+    def step(self, opts):
+        info = IpInfo()
+        _check(_lib.topo_ip_step(self._h, ctypes.byref(opts), ctypes.byref(info)), "topo_ip_step")
+        return info
+
+    def run(self, opts):
+        info = IpInfo()
+        _check(_lib.topo_ip_run(self._h, ctypes.byref(opts), ctypes.byref(info)), "topo_ip_run")
+        return info
+
+    def state(self):
+        import torch
+        u = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        x, phi, psi = (torch.empty(self.m, dtype=torch.float64, device="cuda") for _ in range(3))
+        scal = np.zeros(3)
+        _check(_lib.topo_ip_get_state(self._h, _ptr(u), _ptr(x), _ptr(phi), _ptr(psi),
+                                      scal.ctypes.data_as(_vp)), "topo_ip_get_state")
+        return u, x, phi, psi, scal
+
+    def set_state(self, u, x, phi, psi, scal):
+        scal = np.ascontiguousarray(scal, dtype=np.float64)
+        _check(_lib.topo_ip_set_state(self._h, _ptr(u), _ptr(x), _ptr(phi), _ptr(psi),
+                                      scal.ctypes.data_as(_vp)), "topo_ip_set_state")
+
+
+class OC:
+    """OC / DOC / AOC on the GPU (see include/topo.h)."""
+
+    def __init__(self, nx, ny, nz=0, fixed=None, f=None, V=None, xbar=1.0, levels=3,
+                 precision=FP64, nu1=2, nu2=2, omega=None, max_iter=1000, E=1.0, nu=0.3):
+        import torch
+        d, self._fixed, self.dim, self.n = _desc(nx, ny, nz, fixed, levels, precision, nu1, nu2,
+                                                 omega, max_iter, 1, None, E, nu, False)
+        self.m = nx * ny * (nz if nz else 1)
+        h = _vp()
+        _check(_lib.topo_oc_create(ctypes.byref(d), _ptr(f), float(V), float(xbar),
+                                   ctypes.byref(h)), "topo_oc_create")
+        self._h = h
+        _check(_lib.topo_oc_set_stream(h, _vp(torch.cuda.current_stream().cuda_stream)),
+               "topo_oc_set_stream")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.topo_oc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, x0=None):
+        _check(_lib.topo_oc_init(self._h, _ptr(x0) if x0 is not None else None), "topo_oc_init")
+
+    def step(self, opts):
+        info = OcInfo()
+        _check(_lib.topo_oc_step(self._h, ctypes.byref(opts), ctypes.byref(info)), "topo_oc_step")
+        return info
+
+    def run(self, opts):
+        info = OcInfo()
+        _check(_lib.topo_oc_run(self._h, ctypes.byref(opts), ctypes.byref(info)), "topo_oc_run")
+        return info
+
+    def x(self):
+        import torch
+        x = torch.empty(self.m, dtype=torch.float64, device="cuda")
+        _check(_lib.topo_oc_get_x(self._h, _ptr(x)), "topo_oc_get_x")
+        return x
+
+    def u(self):
+        import torch
+        u = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        _check(_lib.topo_oc_get_u(self._h, _ptr(u)), "topo_oc_get_u")
+        return u
 
 
 class Solver:

@@ -1,0 +1,136 @@
+"""Interior-point and OC trajectories on the GPU against the oracle, step by step (C1-shaped
+cantilever, Example 2 shape 425: 64 x 32, 3 levels), with the linear systems solved to a parity
+tolerance; checkpoint/resume; the paper's barrier schedule."""
+import numpy as np
+import pytest
+
+from oracle import fe, ip as oip, oc as ooc
+from paper_1606_06201_gb300 import workloads as W
+
+from gpu_helpers import dev, host, topo_lib, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(nx, ny, volfrac=0.5):
+    cfg = W.cantilever_2d(nx, ny, volfrac)
+    prob = oip.Problem(fe.Grid(nx, ny), fe.element_stiffness(2), cfg["fixed"], cfg["f"], cfg["V"],
+                       cfg["xbar"])
+    return cfg, prob
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.mark.parametrize("shape,levels", [((16, 8), 2), ((64, 32), 3)])
+def test_ip_trajectory_fp64_matches_oracle(shape, levels):
+    torch = torch_cuda()
+    topo = topo_lib()
+    cfg, prob = _problem(*shape)
+    _, oinfo = oip.ip_run(prob, record=True)
+    traj = oinfo["traj"]
+    solver = topo.IP(*shape, fixed=cfg["fixed"], f=dev(torch, cfg["f"]), V=cfg["V"],
+                     xbar=cfg["xbar"], levels=levels)
+    opts = topo.ip_options(cg_tol=1e-12, cg_tol_init=1e-13)
+    solver.init(opts)
+    worst_x = worst_u = 0.0
+    for k, st in enumerate(traj):
+        info = solver.step(opts)
+        u, x, phi, psi, scal = solver.state()
+        worst_x = max(worst_x, _rel(host(x), st["x"]))
+        worst_u = max(worst_u, _rel(host(u), st["u"]))
+        assert abs(scal[0] - st["lam"]) <= 1e-9 * max(1.0, abs(st["lam"])), k
+        assert abs(info.crit - st["crit"]) <= 1e-8 * st["crit"], k
+        assert info.ip_iters == sum(1 for t in traj[:k + 1] if t["crit"] <= 0.1), k
+    assert info.done == 1 and info.newton == oinfo["newton"] and info.ip_iters == oinfo["ip"] == 12
+    assert worst_x <= 1e-10 and worst_u <= 1e-10, (worst_x, worst_u)
+    c = float(cfg["f"] @ host(solver.state()[0]))
+    assert abs(c - oinfo["compliance"]) <= 1e-10 * abs(oinfo["compliance"])
+
+
+def test_ip_mixed_run_matches_oracle():
+    torch = torch_cuda()
+    topo = topo_lib()
+    cfg, prob = _problem(64, 32)
+    z, oinfo = oip.ip_run(prob)
+    solver = topo.IP(64, 32, fixed=cfg["fixed"], f=dev(torch, cfg["f"]), V=cfg["V"],
+                     xbar=cfg["xbar"], levels=3, precision=topo.MIXED)
+    info = solver.run(topo.ip_options(cg_tol=1e-10))
+    u, x, phi, psi, scal = solver.state()
+    assert info.done == 1 and info.ip_iters == 12
+    assert _rel(host(x), z[2]) <= 1e-6
+    c = float(cfg["f"] @ host(u))
+    assert abs(c - oinfo["compliance"]) <= 1e-6 * abs(oinfo["compliance"])
+    assert abs(float(host(x).sum()) - cfg["V"]) <= 1e-9 * cfg["V"]
+
+
+def test_ip_checkpoint_resume_is_bitwise():
+    torch = torch_cuda()
+    topo = topo_lib()
+    cfg, _ = _problem(32, 16)
+    opts = topo.ip_options(cg_tol=1e-10)
+    a = topo.IP(32, 16, fixed=cfg["fixed"], f=dev(torch, cfg["f"]), V=cfg["V"], xbar=1.0, levels=3)
+    a.init(opts)
+    for _ in range(5):
+        a.step(opts)
+    snap = [t.clone() if hasattr(t, "clone") else t.copy() for t in a.state()]
+    for _ in range(4):
+        a.step(opts)
+    ref = [host(t) if hasattr(t, "cpu") else t for t in a.state()]
+    b = topo.IP(32, 16, fixed=cfg["fixed"], f=dev(torch, cfg["f"]), V=cfg["V"], xbar=1.0, levels=3)
+    b.init(opts)
+    b.set_state(*snap)
+    for _ in range(4):
+        b.step(opts)
+    got = [host(t) if hasattr(t, "cpu") else t for t in b.state()]
+    for g_, r_ in zip(got, ref):
+        assert np.array_equal(g_, r_)
+
+
+def test_ip_rejects_infeasible_volume():
+    torch = torch_cuda()
+    topo = topo_lib()
+    cfg, _ = _problem(16, 8)
+    with pytest.raises(topo.TopoError) as e:
+        topo.IP(16, 8, fixed=cfg["fixed"], f=dev(torch, cfg["f"]), V=200.0, xbar=1.0, levels=2)
+    assert e.value.status == topo.E_INFEASIBLE
+
+
+@pytest.mark.parametrize("variant", ["aoc", "oc", "doc"])
+def test_oc_trajectory_matches_oracle(variant):
+    torch = torch_cuda()
+    topo = topo_lib()
+    cfg, prob = _problem(64, 32)
+    feval = 20
+    _, oinfo = ooc.oc_run(prob, variant=variant, tau_oc=0.0, max_feval=feval, xlow=1e-6,
+                          record=True)
+    vmap = {"aoc": topo.OC_AOC, "oc": topo.OC_PLAIN, "doc": topo.OC_DOC}
+    solver = topo.OC(64, 32, fixed=cfg["fixed"], f=dev(torch, cfg["f"]), V=cfg["V"], xbar=1.0,
+                     levels=3)
+    solver.init()
+    opts = topo.oc_options(variant=vmap[variant], tau_oc=0.0, max_feval=feval, cg_tol0=1e-13,
+                           adaptive_tol=False)
+    comps = []
+    for st in oinfo["traj"]:
+        info = solver.step(opts)
+        comps.append(info.compliance)
+        assert abs(info.compliance - st["c"]) <= 1e-10 * abs(st["c"])
+        assert abs(info.lam - st["lam"]) <= 1e-9 * st["lam"]
+    assert _rel(host(solver.x()), oinfo["x"]) <= 1e-10
+    assert len(comps) == len(oinfo["traj"])
+
+
+def test_oc_run_stops_on_compliance_change():
+    torch = torch_cuda()
+    topo = topo_lib()
+    cfg, prob = _problem(32, 16)
+    solver = topo.OC(32, 16, fixed=cfg["fixed"], f=dev(torch, cfg["f"]), V=cfg["V"], xbar=1.0,
+                     levels=3)
+    solver.init()
+    info = solver.run(topo.oc_options(tau_oc=1e-5, cg_tol0=1e-10, adaptive_tol=False))
+    assert abs(info.compliance - info.compliance_prev) <= 1e-5
+    x = host(solver.x())
+    assert abs(x.sum() - cfg["V"]) <= 1e-6 * cfg["V"] and x.min() >= 1e-6 and x.max() <= 1.0
+    _, oinfo = ooc.oc_run(prob, variant="aoc", tau_oc=1e-5, xlow=1e-6)
+    assert info.iters == oinfo["iters"]

@@ -23,7 +23,7 @@ def _x(nx, ny, nz, seed=11):
 
 
 @pytest.mark.parametrize("generic", [False, True])
-@pytest.mark.parametrize("shape", SHAPES_2D + SHAPES_3D + [(61, 33, 0, 1), (200, 50, 0, 2)])
+@pytest.mark.parametrize("shape", SHAPES_2D + SHAPES_3D + [(61, 31, 0, 1), (200, 48, 0, 3)])
 def test_apply_K_matches_assembled(shape, generic):
     torch = torch_cuda()
     topo = topo_lib()
