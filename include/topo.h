@@ -69,6 +69,11 @@ typedef struct {
   int flexible;         /* 1: Polak-Ribiere beta (safeguard for the FP32 V-cycle) */
   int generic_kernels;  /* 1: use the generic element-matrix kernels on the 2D finest level
                            instead of the specialised Q1 butterfly kernels (for testing) */
+  int omega_auto;       /* 1: per-level damping omega_k = min(omega, 4 / (3 lambda_k)) with
+                           lambda_k ~ lambda_max(D^{-1} A_k) from 15 power iterations at every
+                           hierarchy build (all levels of IP systems; levels >= 1 otherwise).
+                           IP drivers always use it: the element rank-one terms of Z push
+                           lambda_max(D^{-1} Z) well above the value for K(x). */
 } topo_solver_desc;
 
 typedef struct {
@@ -113,7 +118,8 @@ topo_status topo_set_density(topo_solver* s, const double* x);
 
 /* Solve K(x) u = b by Algorithm PCG with one V-cycle (Algorithm MG) as preconditioner
  * (Sec. 5.2), sign convention r = K u - b, stop at ||r||_2 / ||b||_2 <= tol or max_iter.
- * b, u [device, nrhs x n]; if use_x0, u holds the initial guess on entry.  info may be NULL. */
+ * b, u [device, nrhs x n]; if use_x0, u holds the initial guess on entry.  Entries of b and of
+ * the initial guess on fixed DOFs are ignored; u is zero there on return.  info may be NULL. */
 topo_status topo_solve(topo_solver* s, const double* b, double* u, double tol, int use_x0,
                        topo_solve_info* info);
 
@@ -214,7 +220,7 @@ typedef struct {
   int iters, feval, cg_iters;
   double compliance;       /* f^T u at the iterate of the last step (before its update) */
   double compliance_prev;
-  double lam;              /* last bisection midpoint */
+  double lam;              /* last bisection midpoint of the step's first OC operator */
   double cg_tol;
   int status;
   double wall_ms;          /* topo_oc_run: elapsed time */

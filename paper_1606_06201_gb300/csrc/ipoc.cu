@@ -146,7 +146,9 @@ topo_status topo_ip_create(const topo_solver_desc* desc, const double* f, double
   };
   topo_status st = topo::solver_create_internal(desc, false, &a->K);
   if (st != TOPO_OK) return fail(st);
-  st = topo::solver_create_internal(desc, true, &a->Z);
+  topo_solver_desc dz = *desc;
+  dz.omega_auto = 1;  // Z needs the per-level damping (see topo.h)
+  st = topo::solver_create_internal(&dz, true, &a->Z);
   if (st != TOPO_OK) return fail(st);
   topo_solver* Z = a->Z;
   a->d = Z->L[0].d;
@@ -490,16 +492,19 @@ topo_status topo_oc_step(topo_oc* a, const topo_oc_opts* o, topo_oc_info* info) 
   cudaStream_t st = a->K->st;
   if (a->cg_tol < 0.0) a->cg_tol = o->cg_tol0;
   double c = NAN, c2 = NAN;
+  double lam_first = NAN;
   topo_status ss;
   if (o->variant == TOPO_OC_AOC) {
     ss = oc_operator(a, o, a->x, a->x1, &c);
     if (ss != TOPO_OK && ss != TOPO_E_NOT_CONVERGED) return ss;
+    lam_first = a->oc_host->lam_last;
     ss = oc_operator(a, o, a->x1, a->x2, &c2);
     if (ss != TOPO_OK && ss != TOPO_E_NOT_CONVERGED) return ss;
     TOPO_CUDA(launch_average(a->m, a->x1, a->x2, a->x, st));
   } else {
     ss = oc_operator(a, o, a->x, a->x1, &c);
     if (ss != TOPO_OK && ss != TOPO_E_NOT_CONVERGED) return ss;
+    lam_first = a->oc_host->lam_last;
     TOPO_CUDA(cudaMemcpyAsync(a->x, a->x1, sizeof(double) * a->m, cudaMemcpyDeviceToDevice, st));
   }
   TOPO_CUDA(cudaStreamSynchronize(st));
@@ -514,7 +519,7 @@ topo_status topo_oc_step(topo_oc* a, const topo_oc_opts* o, topo_oc_info* info) 
     info->cg_iters = a->cg_iters;
     info->compliance = c;
     info->compliance_prev = a->c_prev;
-    info->lam = a->oc_host->lam_last;
+    info->lam = lam_first;
     info->cg_tol = a->cg_tol;
     info->status = ss;
     info->wall_ms = 0.0;

@@ -120,7 +120,8 @@ __global__ void __launch_bounds__(kThreads) k_z_elem(Dims d, const T* __restrict
                                                      const T* __restrict__ b, T* __restrict__ y,
                                                      T* __restrict__ se, const double* zll,
                                                      double omega, double* partials,
-                                                     unsigned* counter, const CgScalars* sc) {
+                                                     unsigned* counter, const CgScalars* sc,
+                                                     const double* wdev) {
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM;
   if (sc && sc[0].done) return;
   const long long m = d.elems();
@@ -144,10 +145,11 @@ __global__ void __launch_bounds__(kThreads) k_z_elem(Dims d, const T* __restrict
   if (!last_block<1>(part, 0, partials, counter, tot)) return;
   if (threadIdx.x == 0) {
     const double q = tot[0];
+    const double om = wdev ? *wdev : omega;
     double out;
     if (MODE == 0) out = q;
     else if (MODE == 1) out = (double)b[n] - q;
-    else out = (double)v[n] + omega * ((double)b[n] - q) / *zll;
+    else out = (double)v[n] + om * ((double)b[n] - q) / *zll;
     y[n] = (T)out;
   }
 }
@@ -163,13 +165,15 @@ __global__ void __launch_bounds__(kThreads) k_z_node(Dims d, const T* __restrict
                                                      const T* __restrict__ b, T* __restrict__ y,
                                                      const T* __restrict__ invd, T omega,
                                                      const uint8_t* __restrict__ fixed,
-                                                     const double* zll, const CgScalars* sc) {
+                                                     const double* zll, const CgScalars* sc,
+                                                     const double* wdev) {
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM;
   if (sc && sc[0].done) return;
   const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nodes = d.nodes();
   const long long n = nodes * DIM;
-  if (MODE == 3 && node == 0) y[n] = (T)((double)omega * (double)b[n] / *zll);
+  if (MODE == 3 && node == 0)
+    y[n] = (T)((wdev ? *wdev : (double)omega) * (double)b[n] / *zll);
   if (node >= nodes) return;
   const int nnx = d.nx + 1, nny = d.ny + 1;
   const int i = (int)(node % nnx), j = (int)((node / nnx) % nny);
@@ -224,8 +228,10 @@ __global__ void __launch_bounds__(kThreads) k_arrow_row(long long n, const T* __
                                                         const T* __restrict__ b,
                                                         T* __restrict__ y, const double* zll,
                                                         double omega, double* partials,
-                                                        unsigned* counter, const CgScalars* sc) {
+                                                        unsigned* counter, const CgScalars* sc,
+                                                        const double* wdev) {
   if (sc && sc[0].done) return;
+  if (wdev) omega = *wdev;
   double part[1] = {0.0};
   if (MODE != 3)
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -552,16 +558,17 @@ template <typename T>
 cudaError_t launch_z_apply_fine(const Dims& d, int mode, const T* K0, const T* x, const T* g,
                                 const T* Dinv, T* se, const T* v, const T* b, T* y, const T* invd,
                                 T omega, const uint8_t* fixed, const double* zll, double* partials,
-                                unsigned* counter, const CgScalars* sc, cudaStream_t st) {
+                                unsigned* counter, const CgScalars* sc, cudaStream_t st,
+                                const double* wdev) {
   const unsigned ge = red_grid(d.elems());
   const unsigned gn = blocks_for(d.nodes());
 #define TOPO_ZF(DIM, MODE)                                                                      \
   do {                                                                                          \
     if (MODE != 3)                                                                              \
       k_z_elem<DIM, T, MODE><<<ge, kThreads, 0, st>>>(d, g, Dinv, v, b, y, se, zll, omega,      \
-                                                      partials, counter, sc);                   \
+                                                      partials, counter, sc, wdev);             \
     k_z_node<DIM, T, MODE><<<gn, kThreads, 0, st>>>(d, K0, x, g, se, v, b, y, invd, omega,      \
-                                                    fixed, zll, sc);                            \
+                                                    fixed, zll, sc, wdev);                      \
   } while (0)
   if (d.dim == 2) {
     switch (mode) {
@@ -586,39 +593,45 @@ template cudaError_t launch_z_apply_fine<double>(const Dims&, int, const double*
                                                  const double*, const double*, double*,
                                                  const double*, double, const uint8_t*,
                                                  const double*, double*, unsigned*,
-                                                 const CgScalars*, cudaStream_t);
+                                                 const CgScalars*, cudaStream_t, const double*);
 template cudaError_t launch_z_apply_fine<float>(const Dims&, int, const float*, const float*,
                                                 const float*, const float*, float*, const float*,
                                                 const float*, float*, const float*, float,
                                                 const uint8_t*, const double*, double*, unsigned*,
-                                                const CgScalars*, cudaStream_t);
+                                                const CgScalars*, cudaStream_t, const double*);
 
 template <typename T>
 cudaError_t launch_arrow_row(long long n, int mode, const T* w, const T* v, const T* b, T* y,
                              const double* zll, double omega, double* partials, unsigned* counter,
-                             const CgScalars* sc, cudaStream_t st) {
+                             const CgScalars* sc, cudaStream_t st, const double* wdev) {
   const unsigned gr = red_grid(n);
   switch (mode) {
     case 0:
-      k_arrow_row<T, 0><<<gr, kThreads, 0, st>>>(n, w, v, b, y, zll, omega, partials, counter, sc);
+      k_arrow_row<T, 0><<<gr, kThreads, 0, st>>>(n, w, v, b, y, zll, omega, partials, counter, sc,
+                                                 wdev);
       break;
     case 1:
-      k_arrow_row<T, 1><<<gr, kThreads, 0, st>>>(n, w, v, b, y, zll, omega, partials, counter, sc);
+      k_arrow_row<T, 1><<<gr, kThreads, 0, st>>>(n, w, v, b, y, zll, omega, partials, counter, sc,
+                                                 wdev);
       break;
     case 2:
-      k_arrow_row<T, 2><<<gr, kThreads, 0, st>>>(n, w, v, b, y, zll, omega, partials, counter, sc);
+      k_arrow_row<T, 2><<<gr, kThreads, 0, st>>>(n, w, v, b, y, zll, omega, partials, counter, sc,
+                                                 wdev);
       break;
     default:
-      k_arrow_row<T, 3><<<gr, kThreads, 0, st>>>(n, w, v, b, y, zll, omega, partials, counter, sc);
+      k_arrow_row<T, 3><<<gr, kThreads, 0, st>>>(n, w, v, b, y, zll, omega, partials, counter, sc,
+                                                 wdev);
   }
   return cudaGetLastError();
 }
 template cudaError_t launch_arrow_row<double>(long long, int, const double*, const double*,
                                               const double*, double*, const double*, double,
-                                              double*, unsigned*, const CgScalars*, cudaStream_t);
+                                              double*, unsigned*, const CgScalars*, cudaStream_t,
+                                              const double*);
 template cudaError_t launch_arrow_row<float>(long long, int, const float*, const float*,
                                              const float*, float*, const double*, double, double*,
-                                             unsigned*, const CgScalars*, cudaStream_t);
+                                             unsigned*, const CgScalars*, cudaStream_t,
+                                             const double*);
 
 cudaError_t launch_ip_residuals(const Dims& d, const double* K0, const double* u, const double* x,
                                 const double* phi, const double* psi, const double* f,

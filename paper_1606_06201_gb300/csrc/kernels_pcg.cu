@@ -285,6 +285,85 @@ __global__ void __launch_bounds__(kThreads) k_cg_alpha(long long n, const double
   }
 }
 
+// dst = src with the fixed DOFs zeroed (n_mask DOFs carry a mask; entries beyond it, such as the
+// lambda entry of an IP system, are copied unchanged).
+__global__ void k_mask_copy(long long n, long long n_mask, const double* __restrict__ src,
+                            double* __restrict__ dst, const uint8_t* __restrict__ fixed) {
+  const int rhs = blockIdx.y;
+  src += rhs * n;
+  dst += rhs * n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (i < n_mask && fixed[i]) ? 0.0 : src[i];
+}
+
+// ---- largest eigenvalue of D^{-1} A by power iteration (per-level Jacobi damping) ----------
+// v0: a fixed pseudo-random vector (integer hash of the index), zero on fixed DOFs.
+__global__ void k_power_init(long long n, int arrow, double* v, const uint8_t* fixed) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    unsigned h = (unsigned)(i * 2654435761ull) ^ 0x9e3779b9u;
+    h ^= h >> 15;
+    h *= 0x2c1b3c6du;
+    h ^= h >> 12;
+    v[i] = fixed[i] ? 0.0 : 0.5 + (double)(h & 0xffffu) / 65536.0;
+  }
+  if (arrow && i == 0) v[n] = 1.0;
+}
+
+// w = D^{-1} y; partial sums of v^T y, v^T D v, w^T D w (D = 1/invd; lambda entry D = zll);
+// last block: est[0] = Rayleigh quotient v^T A v / v^T D v, est[1] = 1/||w||_D.
+__global__ void __launch_bounds__(kThreads) k_power_step(long long n, int arrow,
+                                                         const double* __restrict__ v,
+                                                         const double* __restrict__ y,
+                                                         const double* __restrict__ invd,
+                                                         const double* zll, double* __restrict__ w,
+                                                         double* partials, unsigned* counters,
+                                                         double* est) {
+  double part[3] = {0.0, 0.0, 0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double vi = v[i], yi = y[i], di = invd[i];
+    const double wi = di * yi;
+    w[i] = wi;
+    part[0] = fma(vi, yi, part[0]);
+    part[1] = fma(vi, vi / di, part[1]);
+    part[2] = fma(wi, wi / di, part[2]);
+  }
+  if (arrow && blockIdx.x == 0 && threadIdx.x == 0) {
+    const double z = *zll, vi = v[n], yi = y[n], wi = yi / z;
+    w[n] = wi;
+    part[0] = fma(vi, yi, part[0]);
+    part[1] = fma(vi, vi * z, part[1]);
+    part[2] = fma(wi, wi * z, part[2]);
+  }
+  double tot[3];
+  if (!last_block_sums<3>(part, partials, counters, 0, tot)) return;
+  if (threadIdx.x == 0) {
+    est[0] = tot[1] > 0.0 ? tot[0] / tot[1] : 0.0;
+    est[1] = tot[2] > 0.0 ? 1.0 / sqrt(tot[2]) : 0.0;
+  }
+}
+
+__global__ void k_power_scale(long long n, const double* __restrict__ w, double* __restrict__ v,
+                              const double* est) {
+  const double sc = est[1];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    v[i] = w[i] * sc;
+}
+
+// omega_k = min(omega, c / (1.05 lambda)); invd <- omega_k invd.
+__global__ void k_power_finish(long long n, const double* est, double omega, double c,
+                               double* omega_dev, double* invd) {
+  const double lam = est[0];
+  const double om = lam > 0.0 ? fmin(omega, c / (1.05 * lam)) : omega;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *omega_dev = om;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    invd[i] *= om;
+}
+
 inline unsigned red_blocks(long long n) {
   const long long b = (n + kThreads - 1) / kThreads;
   return (unsigned)(b < kRedBlocks ? (b < 1 ? 1 : b) : kRedBlocks);
@@ -327,6 +406,35 @@ cudaError_t launch_cg_direction(long long n, int nrhs, const double* r, const TV
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_cg_p<TV><<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, y, p, y_old, flexible, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_power_init(long long n, int arrow, double* v, const uint8_t* fixed,
+                              cudaStream_t st) {
+  k_power_init<<<blocks_for(n), kThreads, 0, st>>>(n, arrow, v, fixed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_power_step(long long n, int arrow, const double* v, const double* y,
+                              const double* invd, const double* zll, double* w, double* partials,
+                              unsigned* counters, double* est, cudaStream_t st) {
+  k_power_step<<<red_blocks(n), kThreads, 0, st>>>(n, arrow, v, y, invd, zll, w, partials,
+                                                   counters, est);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_power_scale<<<red_blocks(n + arrow), kThreads, 0, st>>>(n + arrow, w, (double*)v, est);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_power_finish(long long n, const double* est, double omega, double c,
+                                double* omega_dev, double* invd, cudaStream_t st) {
+  k_power_finish<<<red_blocks(n), kThreads, 0, st>>>(n, est, omega, c, omega_dev, invd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mask_copy(long long n, long long n_mask, int nrhs, const double* src,
+                             double* dst, const uint8_t* fixed, cudaStream_t st) {
+  k_mask_copy<<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, n_mask, src, dst, fixed);
   return cudaGetLastError();
 }
 

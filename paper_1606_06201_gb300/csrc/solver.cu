@@ -187,20 +187,24 @@ template <typename TV>
 topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* b, TV* y,
                         const CgScalars* sc) {
   Level& lv = s->L[k];
-  const TV omega = (TV)s->desc.omega;
+  // adaptive damping: omega_k is folded into invd at build time (and read from the device for the
+  // lambda entry), so the kernels take omega = 1
+  const TV omega = lv.omega_dev ? TV(1) : (TV)s->desc.omega;
   if (s->arrow) {
     if (k == 0) {
       TOPO_CUDA(launch_z_apply_fine<TV>(lv.d, mode, Prec<TV>::K0(s), Prec<TV>::x(s),
                                         ArrowFine<TV>::g(s), ArrowFine<TV>::Dinv(s),
                                         ArrowFine<TV>::se(s), v, b, y, Prec<TV>::invd(lv), omega,
-                                        lv.fixed, s->zll, s->partials, s->counters, sc, s->st));
+                                        lv.fixed, s->zll, s->partials, s->counters, sc, s->st,
+                                        lv.omega_dev));
       return TOPO_OK;
     }
     TOPO_CUDA(launch_apply<TV>(lv.d, mode, Prec<TV>::K0(s), nullptr, Prec<TV>::Ae(lv), v, b, y,
                                Prec<TV>::invd(lv), omega, lv.fixed, 1, sc, s->st,
                                mode == 3 ? nullptr : arrow_w<TV>(lv)));
-    TOPO_CUDA(launch_arrow_row<TV>(lv.n, mode, arrow_w<TV>(lv), v, b, y, s->zll, (double)omega,
-                                   s->partials, s->counters, sc, s->st));
+    TOPO_CUDA(launch_arrow_row<TV>(lv.n, mode, arrow_w<TV>(lv), v, b, y, s->zll,
+                                   (double)s->desc.omega, s->partials, s->counters, sc, s->st,
+                                   lv.omega_dev));
     return TOPO_OK;
   }
   if (k == 0 && s->q1_ok) {
@@ -378,9 +382,9 @@ topo_status solve_impl(topo_solver* s, const double* b, double* u, double tol, i
     s->graph_tol = tol;
   }
   TOPO_CUDA(cudaEventRecord(s->ev_t0, s->st));
-  TOPO_CUDA(cudaMemcpyAsync(s->bbuf, b, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s->st));
-  if (use_x0)
-    TOPO_CUDA(cudaMemcpyAsync(s->z, u, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s->st));
+  // entries on fixed DOFs are ignored: the eliminated system has no equations there
+  TOPO_CUDA(launch_mask_copy(n, s->L[0].n, nrhs, b, s->bbuf, s->L[0].fixed, s->st));
+  if (use_x0) TOPO_CUDA(launch_mask_copy(n, s->L[0].n, nrhs, u, s->z, s->L[0].fixed, s->st));
   TOPO_TRY(launch_graph(s, s->setup[ux], s->setup_kernels[ux]));
   int blocks = 0;
   const int max_blocks = (max_iter + s->graph_iters - 1) / s->graph_iters + 1;
@@ -464,6 +468,17 @@ topo_status enqueue_build(topo_solver* s) {
     Level& lv = s->L[k];
     if (!(s->arrow && k == 0))  // the IP driver writes the finest diagonal of Z
       TOPO_CUDA(launch_inv_diag(lv.d, s->K0, k == 0 ? s->x : nullptr, lv.Ae, lv.fixed, lv.invd, st));
+    if (lv.omega_dev) {  // lambda_max(D^{-1} A_k) by power iteration, then the damping
+      const int ar = s->arrow ? 1 : 0;
+      TOPO_CUDA(launch_power_init(lv.n, ar, s->p, lv.fixed, st));
+      for (int it = 0; it < 15; ++it) {
+        TOPO_TRY(apply_level<double>(s, k, 0, s->p, nullptr, s->q, nullptr));
+        TOPO_CUDA(launch_power_step(lv.n, ar, s->p, s->q, lv.invd, s->zll, s->r, s->partials,
+                                    s->counters, s->pw_est, st));
+      }
+      TOPO_CUDA(launch_power_finish(lv.n, s->pw_est, s->desc.omega, 4.0 / 3.0, lv.omega_dev,
+                                    lv.invd, st));
+    }
     if (mixed) {
       TOPO_CUDA(launch_convert_d2f(lv.invd, lv.invd32, lv.n, st));
       if (k >= 1 && lv.Ae32) TOPO_CUDA(launch_convert_d2f(lv.Ae, lv.Ae32, lv.m * ne2, st));
@@ -592,6 +607,7 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
     if (!coarsest) {
       TOPO_TRY(s->alloc(&lv.invd, lv.n));
       if (s->prec == TOPO_MIXED) TOPO_TRY(s->alloc(&lv.invd32, lv.n));
+      if (d->omega_auto && (arrow || k >= 1)) TOPO_TRY(s->alloc(&lv.omega_dev, 1));
       TOPO_TRY(s->alloc((char**)&lv.t, vbytes * vl * nrhs));
     }
     if (k >= 1) TOPO_TRY(s->alloc((char**)&lv.b, vbytes * vl * nrhs));
@@ -613,6 +629,7 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   TOPO_TRY(s->alloc(&s->Adense, na * na));
   TOPO_TRY(s->alloc(&s->Ainv, na * na));
   TOPO_TRY(s->alloc(&s->info, 2));
+  TOPO_TRY(s->alloc(&s->pw_est, 2));
   // densities and CG vectors (IP systems: trailing lambda entry, padded to an even length)
   const long long m = s->L[0].m;
   const long long n = s->L[0].n + (arrow ? 2 : 0);

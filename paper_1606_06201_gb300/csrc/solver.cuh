@@ -34,6 +34,7 @@ struct topo_solver {
   // trailing lambda entry; g_e = K0 u_e and Dinv = 1/D on the finest level are owned by the IP
   // driver; zll points to Z_ll = sum 1/D on the device.
   bool arrow = false;
+  double* pw_est = nullptr;      // power-iteration scalars (adaptive damping)
   const double* g = nullptr;
   const double* Dinv = nullptr;
   const double* zll = nullptr;

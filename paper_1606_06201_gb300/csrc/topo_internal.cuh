@@ -73,6 +73,7 @@ struct Level {
   float* Ae32 = nullptr;           // FP32 copy (mixed precision)
   double* invd = nullptr;          // 1 / diag(A) [n] (1 on fixed DOFs)
   float* invd32 = nullptr;
+  double* omega_dev = nullptr;     // per-level Jacobi damping (adaptive damping only)
   double* w = nullptr;             // arrow column Z_ul on this level (IP systems) [n]
   float* w32 = nullptr;
   void* b = nullptr;               // V-cycle right-hand side   [nrhs][n] (FP64 or FP32)
@@ -195,20 +196,35 @@ cudaError_t launch_cg_direction(long long n, int nrhs, const double* r, const TV
                                 CgScalars* sc, cudaStream_t st);
 cudaError_t launch_dot(long long n, int nrhs, const double* a, const double* b, double* partials,
                        unsigned* counters, double* out, cudaStream_t st);
+// Power iteration for lambda_max(D^{-1} A): v <- D^{-1} A v / ||.||_D (y = A v supplied by the
+// caller); est[0] = Rayleigh quotient, est[1] = normalisation.  finish: omega_k = min(omega,
+// c / (1.05 est[0])) written to omega_dev and folded into invd (invd <- omega_k invd).
+cudaError_t launch_power_init(long long n, int arrow, double* v, const uint8_t* fixed,
+                              cudaStream_t st);
+cudaError_t launch_power_step(long long n, int arrow, const double* v, const double* y,
+                              const double* invd, const double* zll, double* w, double* partials,
+                              unsigned* counters, double* est, cudaStream_t st);
+cudaError_t launch_power_finish(long long n, const double* est, double omega, double c,
+                                double* omega_dev, double* invd, cudaStream_t st);
+cudaError_t launch_mask_copy(long long n, long long n_mask, int nrhs, const double* src,
+                             double* dst, const uint8_t* fixed, cudaStream_t st);
 // p^T q and alpha = r^T y / p^T q (breakdown checks as in the fused operator kernel).
 cudaError_t launch_cg_alpha(long long n, int nrhs, const double* p, const double* q,
                             double* partials, unsigned* counters, CgScalars* sc, cudaStream_t st);
 
 // IP and OC kernels (kernels_ip.cu).
+// wdev != nullptr: the damping of the lambda entry is read from the device (the u-part then
+// takes omega folded into invd, with omega = 1 passed here).
 template <typename T>
 cudaError_t launch_z_apply_fine(const Dims& d, int mode, const T* K0, const T* x, const T* g,
                                 const T* Dinv, T* se, const T* v, const T* b, T* y, const T* invd,
                                 T omega, const uint8_t* fixed, const double* zll, double* partials,
-                                unsigned* counter, const CgScalars* sc, cudaStream_t st);
+                                unsigned* counter, const CgScalars* sc, cudaStream_t st,
+                                const double* wdev = nullptr);
 template <typename T>
 cudaError_t launch_arrow_row(long long n, int mode, const T* w, const T* v, const T* b, T* y,
                              const double* zll, double omega, double* partials, unsigned* counter,
-                             const CgScalars* sc, cudaStream_t st);
+                             const CgScalars* sc, cudaStream_t st, const double* wdev = nullptr);
 cudaError_t launch_ip_residuals(const Dims& d, const double* K0, const double* u, const double* x,
                                 const double* phi, const double* psi, const double* f,
                                 const uint8_t* fixed, IpScalars* ip, double* g, double* tR3,
