@@ -34,8 +34,17 @@ NX, NY, LEVELS, TOL = 2048, 1024, 9, 1e-8
 METRIC = "MGCG DOF·iterations/s at 1e-8 rel. residual (mixed: FP32 V-cycle, FP64 CG)"
 UNIT = "DOF·it/s"
 WORKLOAD = "mgcg_2d_q1_2048x1024_9lev_logunif_box5_normal_load"
-# FP64 CUDA-core peak: 152 SMs x 2 DFMA/clock x 2 flop x 2.07 GHz (probe on this part: 1.20 TF/s)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 pipe peak from unit counts and clock: 152 SMs x 2 FP64 instructions/clock x 2.07 GHz
+# (add, multiply and fused multiply-add each occupy one issue slot; a probe on this part measured
+# 0.60e12 FP64 FMA/s = 1.20 TFLOP/s).
+FP64_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
+# FP64 operations of the butterfly operator kernel: 40 per element (two 4-point butterflies per
+# displacement component, 13 scalings, two inverse butterflies) + 6 node-assembly adds + 2 FMA of
+# the fused p^T q per node.
+OPS_PER_ELEM, OPS_PER_NODE = 40.0, 8.0
+# DRAM bytes of one launch of that kernel on this workload from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum = 55.21 MB + 3.51 MB).
+OPERATOR_DRAM_BYTES = 58712320.0
 
 
 def _dist():
@@ -256,16 +265,19 @@ def main():
     line = None
     if rank == 0:
         m, n = NX * NY, cfg["f"].size
-        flop_per_launch = 144.0 * m + 2.0 * n
+        nodes = (NX + 1) * (NY + 1)
+        ops_per_launch = OPS_PER_ELEM * m + OPS_PER_NODE * nodes
         op_ms, op_cnt = mixed["prof"]
         op_avg_ms = op_ms / op_cnt if op_cnt else float("nan")
-        achieved = flop_per_launch / (op_avg_ms * 1e-3) / 1e12
-        roof = {"kernel": "k_apply_dot_fine<2> (outer FP64 operator q = K(x) p with p^T q)",
-                "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                "algorithmic_flop_per_launch": flop_per_launch,
+        achieved = ops_per_launch / (op_avg_ms * 1e-3) / 1e12
+        roof = {"kernel": "k_q1_sweep<double,0,1> (outer FP64 operator q = K(x) p, fused p^T q)",
+                "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TOPS,
+                "unit": "T FP64-op/s", "frac": achieved / FP64_PEAK_TOPS,
+                "traffic": OPERATOR_DRAM_BYTES,
+                "peak_source": "derived: 152 SMs x 2 FP64 issue slots/clk x 2.07 GHz",
+                "algorithmic_ops_per_launch": ops_per_launch,
                 "algorithmic_bytes_per_launch": 8.0 * m + 16.0 * n + 1.0 * n,
+                "dense_form_tflops": (144.0 * m + 2.0 * n) / (op_avg_ms * 1e-3) / 1e12,
                 "avg_launch_ms": op_avg_ms, "launches_timed": op_cnt}
         cpu = None
         if not args.no_cpu_baseline:
