@@ -214,6 +214,127 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, Q1K<
   }
 }
 
+// First coarse level, matrix-free Galerkin operator A_1 = P^T K(x) P applied element by element:
+// the coarse element's four nodal values are interpolated bilinearly to the 3 x 3 fine nodes of
+// its four children, each child's x_c K0 is applied in the butterfly form, and the 3 x 3 fine
+// forces are restricted back to the four coarse nodes (weights 1, 1/2, 1/4).  Same warp-sweep
+// data movement as k_q1_sweep on the coarse grid (nx, ny = coarse elements); xf holds the finest
+// densities (2nx x 2ny), invd the level's inverse diagonal (modes 2, 3).
+template <int MODE>
+__global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, Q1K<float> k,
+                                                              const float* __restrict__ xf,
+                                                              const float* __restrict__ v,
+                                                              const float* __restrict__ b,
+                                                              float* __restrict__ y, float omega,
+                                                              const float* __restrict__ invd,
+                                                              const uint8_t* __restrict__ fixed,
+                                                              const CgScalars* sc) {
+  const int rhs = blockIdx.y;
+  if (sc && sc[rhs].done) return;
+  const long long n = 2LL * (nx + 1) * (ny + 1);
+  v += rhs * n;
+  y += rhs * n;
+  b += rhs * n;
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kQ1Warps + (threadIdx.x >> 5);
+  const int ncolw = (nx + 1 + kQ1Cols - 1) / kQ1Cols;
+  const int nstrip = (ny + 1 + kQ1Rows - 1) / kQ1Rows;
+  const int wc = gw % ncolw, ws = gw / ncolw;
+  if (ws >= nstrip) return;
+  const int c = wc * kQ1Cols - 1 + lane;
+  const bool col_ok = (c >= 0 && c <= nx);
+  const bool out_lane = (lane >= 1 && lane <= kQ1Cols && col_ok);
+  const bool el_col = (lane <= kQ1Cols && c >= 0 && c < nx);
+  const int j0 = ws * kQ1Rows;
+  const int j1 = min(j0 + kQ1Rows, ny + 1);
+  const int fnx = 2 * nx;
+  const float2* v2 = reinterpret_cast<const float2*>(v);
+  float2 pb = make_float2(0.f, 0.f);
+  if (MODE != 3 && col_ok && j0 >= 1) pb = v2[c + (long long)(nx + 1) * (j0 - 1)];
+  float cu = 0.f, cv = 0.f;
+  for (int ey = j0 - 1; ey < j1; ++ey) {
+    float2 pt = make_float2(0.f, 0.f);
+    if (MODE != 3 && col_ok && ey + 1 <= ny) pt = v2[c + (long long)(nx + 1) * (ey + 1)];
+    const bool el_ok = el_col && ey >= 0 && ey < ny;
+    float2 xb = make_float2(0.f, 0.f), xt = make_float2(0.f, 0.f);
+    if (MODE != 3 && el_ok) {
+      xb = *reinterpret_cast<const float2*>(xf + 2 * c + (long long)fnx * (2 * ey));
+      xt = *reinterpret_cast<const float2*>(xf + 2 * c + (long long)fnx * (2 * ey + 1));
+    }
+    const float pbr_u = shfl_dn(pb.x), pbr_v = shfl_dn(pb.y);
+    const float ptr_u = shfl_dn(pt.x), ptr_v = shfl_dn(pt.y);
+    float R[4][2] = {};  // coarse local nodes (0,0) (1,0) (1,1) (0,1), components u, v
+    if (MODE != 3) {
+      // fine nodal values on the 3 x 3 grid F[i][j] (i along x, j along y), by interpolation
+      float fu[3][3], fv[3][3];
+      fu[0][0] = pb.x; fu[2][0] = pbr_u; fu[2][2] = ptr_u; fu[0][2] = pt.x;
+      fv[0][0] = pb.y; fv[2][0] = pbr_v; fv[2][2] = ptr_v; fv[0][2] = pt.y;
+      fu[1][0] = 0.5f * (fu[0][0] + fu[2][0]); fv[1][0] = 0.5f * (fv[0][0] + fv[2][0]);
+      fu[1][2] = 0.5f * (fu[0][2] + fu[2][2]); fv[1][2] = 0.5f * (fv[0][2] + fv[2][2]);
+      fu[0][1] = 0.5f * (fu[0][0] + fu[0][2]); fv[0][1] = 0.5f * (fv[0][0] + fv[0][2]);
+      fu[2][1] = 0.5f * (fu[2][0] + fu[2][2]); fv[2][1] = 0.5f * (fv[2][0] + fv[2][2]);
+      fu[1][1] = 0.5f * (fu[1][0] + fu[1][2]); fv[1][1] = 0.5f * (fv[1][0] + fv[1][2]);
+      float Fu[3][3] = {}, Fv[3][3] = {};
+      const float xc[2][2] = {{xb.x, xt.x}, {xb.y, xt.y}};  // [cx][cy]
+#pragma unroll
+      for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+        for (int cx = 0; cx < 2; ++cx) {
+          const float uu[4] = {fu[cx][cy], fu[cx + 1][cy], fu[cx + 1][cy + 1], fu[cx][cy + 1]};
+          const float vv[4] = {fv[cx][cy], fv[cx + 1][cy], fv[cx + 1][cy + 1], fv[cx][cy + 1]};
+          float ru[4], rv[4];
+          q1_element<float>(k, xc[cx][cy], uu, vv, ru, rv);
+          Fu[cx][cy] += ru[0]; Fv[cx][cy] += rv[0];
+          Fu[cx + 1][cy] += ru[1]; Fv[cx + 1][cy] += rv[1];
+          Fu[cx + 1][cy + 1] += ru[2]; Fv[cx + 1][cy + 1] += rv[2];
+          Fu[cx][cy + 1] += ru[3]; Fv[cx][cy + 1] += rv[3];
+        }
+      // restriction to the coarse corners: weight 1 at the corner, 1/2 on its two edges' midpoints,
+      // 1/4 at the centre
+      const int cxs[4] = {0, 2, 2, 0}, cys[4] = {0, 0, 2, 2};
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int i = cxs[a], j = cys[a];
+        R[a][0] = Fu[i][j] + 0.5f * (Fu[1][j] + Fu[i][1]) + 0.25f * Fu[1][1];
+        R[a][1] = Fv[i][j] + 0.5f * (Fv[1][j] + Fv[i][1]) + 0.25f * Fv[1][1];
+      }
+    }
+    const float l1u = shfl_up1(R[1][0]), l1v = shfl_up1(R[1][1]);
+    const float l2u = shfl_up1(R[2][0]), l2v = shfl_up1(R[2][1]);
+    if (ey >= j0 && out_lane) {
+      const float qu = cu + R[0][0] + l1u, qv = cv + R[0][1] + l1v;
+      const long long node = c + (long long)(nx + 1) * ey;
+      const uint16_t fx = *reinterpret_cast<const uint16_t*>(fixed + 2 * node);
+      float2 out;
+      if (MODE == 0) {
+        out.x = qu;
+        out.y = qv;
+      } else {
+        const float2 bb = reinterpret_cast<const float2*>(b)[node];
+        if (MODE == 1) {
+          out.x = bb.x - qu;
+          out.y = bb.y - qv;
+        } else {
+          const float2 di = reinterpret_cast<const float2*>(invd)[node];
+          if (MODE == 2) {
+            out.x = fmaf(omega * di.x, bb.x - qu, pb.x);
+            out.y = fmaf(omega * di.y, bb.y - qv, pb.y);
+          } else {
+            out.x = omega * di.x * bb.x;
+            out.y = omega * di.y * bb.y;
+          }
+        }
+      }
+      if (fx & 0xff) out.x = 0.f;
+      if (fx >> 8) out.y = 0.f;
+      reinterpret_cast<float2*>(y)[node] = out;
+    }
+    cu = R[3][0] + l2u;
+    cv = R[3][1] + l2v;
+    pb = pt;
+  }
+}
+
 template <typename T>
 Q1K<T> coef_cast(const Q1Coef& c) {
   return Q1K<T>{(T)c.c11, (T)c.c12, (T)c.c22, (T)c.c33, (T)c.cH, (T)c.cHp, (T)c.kd};
@@ -261,6 +382,28 @@ template cudaError_t launch_q1_apply<double>(int, int, int, const Q1Coef&, const
 template cudaError_t launch_q1_apply<float>(int, int, int, const Q1Coef&, const float*,
                                             const float*, const float*, float*, float,
                                             const uint8_t*, int, const CgScalars*, cudaStream_t);
+
+cudaError_t launch_q1g_apply(int nx, int ny, int mode, const Q1Coef& coef, const float* xf,
+                             const float* v, const float* b, float* y, float omega,
+                             const float* invd, const uint8_t* fixed, int nrhs,
+                             const CgScalars* sc, cudaStream_t st) {
+  dim3 grid(q1_blocks(nx, ny), nrhs);
+  const Q1K<float> k = coef_cast<float>(coef);
+  switch (mode) {
+    case 0:
+      k_q1g_sweep<0><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, k, xf, v, b, y, omega, invd, fixed, sc);
+      break;
+    case 1:
+      k_q1g_sweep<1><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, k, xf, v, b, y, omega, invd, fixed, sc);
+      break;
+    case 2:
+      k_q1g_sweep<2><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, k, xf, v, b, y, omega, invd, fixed, sc);
+      break;
+    default:
+      k_q1g_sweep<3><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, k, xf, v, b, y, omega, invd, fixed, sc);
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_q1_apply_dot(int nx, int ny, const Q1Coef& coef, const double* x,
                                 const double* v, double* y, const uint8_t* fixed, int nrhs,

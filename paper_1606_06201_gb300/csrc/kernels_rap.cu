@@ -71,6 +71,69 @@ __global__ void k_rap_from_fine(Dims df, const double* __restrict__ C,
   Ac[t] = acc;
 }
 
+// Second coarse level straight from the finest densities: A_E = sum_f x_f C2_f over the 4^dim fine
+// elements f below E, with C2_f = W_f^T K0 W_f (W_f: composite interpolation from E's nodes to the
+// nodes of f).  Entry-major output; thread t -> (entry = t / mc, E = t % mc).
+template <int DIM>
+__global__ void k_rap2_from_fine(Dims df, const double* __restrict__ C2,
+                                 const double* __restrict__ x, double* __restrict__ Ac) {
+  constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM, NE2 = NE * NE, NF = NN * NN;
+  const int cnx = df.nx / 4, cny = df.ny / 4, cnz = DIM == 3 ? df.nz / 4 : 1;
+  const long long mc = (long long)cnx * cny * cnz;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= mc * NE2) return;
+  const int entry = (int)(t / mc);
+  const long long E = t % mc;
+  const int EX = (int)(E % cnx), EY = (int)((E / cnx) % cny), EZ = (int)(E / ((long long)cnx * cny));
+  double acc = 0.0;
+#pragma unroll 4
+  for (int f = 0; f < NF; ++f) {
+    const int c1 = f / NN, c2 = f % NN;
+    const int fx = 4 * EX + 2 * (c1 & 1) + (c2 & 1);
+    const int fy = 4 * EY + 2 * ((c1 >> 1) & 1) + ((c2 >> 1) & 1);
+    const int fz = DIM == 3 ? 4 * EZ + 2 * (c1 >> 2) + (c2 >> 2) : 0;
+    const long long fe = fx + (long long)df.nx * (fy + (long long)df.ny * fz);
+    acc = fma(x[fe], __ldg(C2 + (long long)f * NE2 + entry), acc);
+  }
+  Ac[t] = acc;
+}
+
+// 1 / diag of the first coarse level straight from the finest densities:
+// diag(A_1)_i = sum_{E at node} sum_c x_c (C_c)_{ii}.
+template <int DIM>
+__global__ void k_inv_diag_l1(Dims dc, const double* __restrict__ C, const double* __restrict__ xf,
+                              const uint8_t* __restrict__ fixed, double* __restrict__ invd) {
+  constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM, NE2 = NE * NE;
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= dc.nodes()) return;
+  const int nnx = dc.nx + 1, nny = dc.ny + 1;
+  const int i = (int)(node % nnx), j = (int)((node / nnx) % nny);
+  const int k = (DIM == 3) ? (int)(node / ((long long)nnx * nny)) : 0;
+  const int fnx = 2 * dc.nx, fny = 2 * dc.ny;
+  double acc[DIM] = {};
+  for (int s = 0; s < NN; ++s) {
+    const int dx = s & 1, dy = (s >> 1) & 1, dz = (DIM == 3) ? (s >> 2) : 0;
+    const int ex = i - 1 + dx, ey = j - 1 + dy, ez = (DIM == 3) ? k - 1 + dz : 0;
+    if (ex < 0 || ex >= dc.nx || ey < 0 || ey >= dc.ny) continue;
+    if (DIM == 3 && (ez < 0 || ez >= dc.nz)) continue;
+    const int loc = loc_of(1 - dx, 1 - dy, DIM == 3 ? 1 - dz : 0);
+    for (int c = 0; c < NN; ++c) {
+      const long long fe = (2 * ex + (c & 1)) +
+                           (long long)fnx * ((2 * ey + ((c >> 1) & 1)) +
+                                             (long long)fny * (DIM == 3 ? 2 * ez + (c >> 2) : 0));
+      const double xc = xf[fe];
+      for (int cc = 0; cc < DIM; ++cc) {
+        const int r = loc * DIM + cc;
+        acc[cc] = fma(xc, C[c * NE2 + r * NE + r], acc[cc]);
+      }
+    }
+  }
+  for (int cc = 0; cc < DIM; ++cc) {
+    const long long id = DIM * node + cc;
+    invd[id] = (fixed[id] || !(acc[cc] > 0.0)) ? 1.0 : 1.0 / acc[cc];
+  }
+}
+
 // General Galerkin step from level matrices Af (entry-major, mf elements) to Ac (entry-major):
 // A_E = sum_c P_c^T A_c P_c with the interpolation weights W_c[a][A] tabulated in shared memory
 // (exact binary fractions) and their zeros skipped.
@@ -256,6 +319,27 @@ cudaError_t launch_rap_from_fine(const Dims& fine, const double* C, const double
     k_rap_from_fine<2><<<blocks_for(total), kThreads, 0, st>>>(fine, C, x, Ac, g, Dinv);
   else
     k_rap_from_fine<3><<<blocks_for(total), kThreads, 0, st>>>(fine, C, x, Ac, g, Dinv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rap2_from_fine(const Dims& fine, const double* C2, const double* x, double* Ac,
+                                  cudaStream_t st) {
+  const int ne = fine.dim == 2 ? 8 : 24;
+  const long long mc = fine.elems() / (fine.dim == 2 ? 16 : 64);
+  const long long total = mc * ne * ne;
+  if (fine.dim == 2)
+    k_rap2_from_fine<2><<<blocks_for(total), kThreads, 0, st>>>(fine, C2, x, Ac);
+  else
+    k_rap2_from_fine<3><<<blocks_for(total), kThreads, 0, st>>>(fine, C2, x, Ac);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inv_diag_l1(const Dims& coarse1, const double* C, const double* xf,
+                               const uint8_t* fixed, double* invd, cudaStream_t st) {
+  if (coarse1.dim == 2)
+    k_inv_diag_l1<2><<<blocks_for(coarse1.nodes()), kThreads, 0, st>>>(coarse1, C, xf, fixed, invd);
+  else
+    k_inv_diag_l1<3><<<blocks_for(coarse1.nodes()), kThreads, 0, st>>>(coarse1, C, xf, fixed, invd);
   return cudaGetLastError();
 }
 

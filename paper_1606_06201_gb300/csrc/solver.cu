@@ -69,6 +69,46 @@ void child_matrices(int dim, const double* K0, std::vector<double>& C) {
   }
 }
 
+// C2_f = W_f^T K0 W_f for the 4^dim fine elements f two levels below a coarse element, with the
+// composite node weights W_f[a][A] = sum_b W_c2[a][b] W_c1[b][A] (f = c1 * 2^dim + c2).
+void grandchild_matrices(int dim, const double* K0, std::vector<double>& C2) {
+  const int NN = dim == 2 ? 4 : 8, NE = NN * dim;
+  auto weights = [&](int c, std::vector<double>& W) {
+    const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+    W.assign(NN * NN, 0.0);
+    for (int a = 0; a < NN; ++a)
+      for (int A = 0; A < NN; ++A) {
+        double w = w1h(cx + lox(a), lox(A)) * w1h(cy + loy(a), loy(A));
+        if (dim == 3) w *= w1h(cz + loz(a), loz(A));
+        W[a * NN + A] = w;
+      }
+  };
+  C2.assign((size_t)NN * NN * NE * NE, 0.0);
+  std::vector<double> W1, W2, Wf(NN * NN);
+  for (int c1 = 0; c1 < NN; ++c1) {
+    weights(c1, W1);
+    for (int c2 = 0; c2 < NN; ++c2) {
+      weights(c2, W2);
+      for (int a = 0; a < NN; ++a)
+        for (int A = 0; A < NN; ++A) {
+          double w = 0.0;
+          for (int b = 0; b < NN; ++b) w += W2[a * NN + b] * W1[b * NN + A];
+          Wf[a * NN + A] = w;
+        }
+      double* Cf = C2.data() + (size_t)(c1 * NN + c2) * NE * NE;
+      for (int I = 0; I < NE; ++I)
+        for (int J = 0; J < NE; ++J) {
+          const int A = I / dim, al = I % dim, B = J / dim, be = J % dim;
+          double acc = 0.0;
+          for (int a = 0; a < NN; ++a)
+            for (int b = 0; b < NN; ++b)
+              acc += Wf[a * NN + A] * K0[(a * dim + al) * NE + b * dim + be] * Wf[b * NN + B];
+          Cf[I * NE + J] = acc;
+        }
+    }
+  }
+}
+
 // Butterfly coefficients of the plane-stress Q1 K0 (see kernels_q1.cu) and a check that they
 // reproduce the quadrature K0.
 bool q1_coefficients(double E, double nu, const double* K0, Q1Coef& q) {
@@ -213,9 +253,14 @@ topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* 
     return TOPO_OK;
   }
   if (k == 1 && s->l1_free && std::is_same<TV, float>::value) {
-    TOPO_CUDA(launch_apply_l1<float>(lv.d, mode, s->C32, s->x32, (const float*)v, (const float*)b,
-                                     (float*)y, s->L[1].invd32, (float)omega, lv.fixed, s->nrhs,
-                                     sc, s->st));
+    if (s->q1_ok)
+      TOPO_CUDA(launch_q1g_apply(lv.d.nx, lv.d.ny, mode, s->q1, s->x32, (const float*)v,
+                                 (const float*)b, (float*)y, (float)omega, s->L[1].invd32,
+                                 lv.fixed, s->nrhs, sc, s->st));
+    else
+      TOPO_CUDA(launch_apply_l1<float>(lv.d, mode, s->C32, s->x32, (const float*)v,
+                                       (const float*)b, (float*)y, s->L[1].invd32, (float)omega,
+                                       lv.fixed, s->nrhs, sc, s->st));
     return TOPO_OK;
   }
   const TV* x = k == 0 ? Prec<TV>::x(s) : nullptr;
@@ -455,18 +500,24 @@ topo_status enqueue_build(topo_solver* s) {
     TOPO_CUDA(launch_convert_d2f(s->Dinv, s->Dinv32, m, st));
   }
   for (int k = 1; k < nl; ++k) {
-    if (k == 1)
-      TOPO_CUDA(launch_rap_from_fine(s->L[0].d, s->C, s->x, s->L[1].Ae, st,
-                                     s->arrow ? s->g : nullptr, s->arrow ? s->Dinv : nullptr));
-    else
+    if (k == 1) {
+      if (s->L[1].Ae)  // stored unless the first coarse level is applied matrix-free
+        TOPO_CUDA(launch_rap_from_fine(s->L[0].d, s->C, s->x, s->L[1].Ae, st,
+                                       s->arrow ? s->g : nullptr, s->arrow ? s->Dinv : nullptr));
+    } else if (k == 2 && s->C2) {
+      TOPO_CUDA(launch_rap2_from_fine(s->L[0].d, s->C2, s->x, s->L[2].Ae, st));
+    } else {
       TOPO_CUDA(launch_rap_coarse(s->L[k - 1].d, s->L[k - 1].Ae, s->L[k].Ae, st));
+    }
     if (s->arrow)
       TOPO_CUDA(launch_restrict<double>(s->L[k - 1].d, s->L[k - 1].w, s->L[k].w, s->L[k].fixed, 1,
                                         nullptr, st, 0));
   }
   for (int k = 0; k < nl - 1; ++k) {
     Level& lv = s->L[k];
-    if (!(s->arrow && k == 0))  // the IP driver writes the finest diagonal of Z
+    if (k == 1 && !lv.Ae)
+      TOPO_CUDA(launch_inv_diag_l1(lv.d, s->C, s->x, lv.fixed, lv.invd, st));
+    else if (!(s->arrow && k == 0))  // the IP driver writes the finest diagonal of Z
       TOPO_CUDA(launch_inv_diag(lv.d, s->K0, k == 0 ? s->x : nullptr, lv.Ae, lv.fixed, lv.invd, st));
     if (lv.omega_dev) {  // lambda_max(D^{-1} A_k) by power iteration, then the damping
       const int ar = s->arrow ? 1 : 0;
@@ -565,6 +616,8 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   std::vector<double> K0(ne * ne), C;
   element_stiffness_host(s->dim, d->E, d->nu, K0.data());
   child_matrices(s->dim, K0.data(), C);
+  std::vector<double> C2;
+  if (!arrow && s->nlev >= 3) grandchild_matrices(s->dim, K0.data(), C2);
   s->q1_ok = (s->dim == 2) && q1_coefficients(d->E, d->nu, K0.data(), s->q1) && !d->generic_kernels;
   s->l1_free = (s->dim == 2) && !arrow && s->prec == TOPO_MIXED && s->nlev >= 3 &&
                !d->generic_kernels;
@@ -573,6 +626,10 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   TOPO_TRY(s->alloc(&s->K0f, ne * ne));
   TOPO_TRY(s->alloc(&s->C, C.size()));
   TOPO_TRY(s->alloc(&s->C32, C32.size()));
+  if (!C2.empty()) {
+    TOPO_TRY(s->alloc(&s->C2, C2.size()));
+    TOPO_CUDA(cudaMemcpy(s->C2, C2.data(), sizeof(double) * C2.size(), cudaMemcpyHostToDevice));
+  }
   TOPO_CUDA(cudaMemcpy(s->K0, K0.data(), sizeof(double) * ne * ne, cudaMemcpyHostToDevice));
   TOPO_CUDA(cudaMemcpy(s->K0f, K0f.data(), sizeof(float) * ne * ne, cudaMemcpyHostToDevice));
   TOPO_CUDA(cudaMemcpy(s->C, C.data(), sizeof(double) * C.size(), cudaMemcpyHostToDevice));
@@ -595,8 +652,8 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
     const bool coarsest = (k == s->nlev - 1);
     const long long vl = lv.n + (arrow ? 2 : 0);
     if (k >= 1) {
-      TOPO_TRY(s->alloc(&lv.Ae, lv.m * ne * ne));
       const bool l1_matrix_free = (k == 1 && s->l1_free);
+      if (!l1_matrix_free) TOPO_TRY(s->alloc(&lv.Ae, lv.m * ne * ne));
       if (s->prec == TOPO_MIXED && !coarsest && !l1_matrix_free)
         TOPO_TRY(s->alloc(&lv.Ae32, lv.m * ne * ne));
     }
@@ -799,6 +856,10 @@ topo_status topo_apply_vcycle(topo_solver* s, const double* r, double* y) {
 topo_status topo_get_level_matrices(topo_solver* s, int level, double* out_host) {
   if (!s || !out_host || level < 1 || level >= s->nlev || !s->have_density) {
     set_error("topo_get_level_matrices: level must be in [1, levels) after topo_set_density");
+    return TOPO_E_INVALID_ARG;
+  }
+  if (!s->L[level].Ae) {
+    set_error("topo_get_level_matrices: this level is applied matrix-free (mixed precision)");
     return TOPO_E_INVALID_ARG;
   }
   StreamGuard g(s);

@@ -29,6 +29,7 @@ struct topo_solver {
   double* x = nullptr;
   float* x32 = nullptr;
   float* C32 = nullptr;          // FP32 copy of C (matrix-free first coarse level)
+  double* C2 = nullptr;          // composite matrices two levels down (second coarse level)
   bool l1_free = false;          // mixed 2D K systems: level 1 applied matrix-free in FP32
   // Arrow (IP) systems Z = [K 0; 0 0] + [B; e^T] D^{-1} [B^T e] (Eq. (nwtr2Z)): vectors carry a
   // trailing lambda entry; g_e = K0 u_e and Dinv = 1/D on the finest level are owned by the IP

@@ -155,6 +155,12 @@ cudaError_t launch_q1_apply_dot(int nx, int ny, const Q1Coef& coef, const double
                                 double* partials, unsigned* counters, CgScalars* sc,
                                 cudaStream_t st);
 long long q1_partial_blocks(int nx, int ny);
+// First coarse level of the 2D Q1 hierarchy, matrix-free in FP32 (P^T K(x) P element by element);
+// nx, ny = coarse elements, xf = finest densities.
+cudaError_t launch_q1g_apply(int nx, int ny, int mode, const Q1Coef& coef, const float* xf,
+                             const float* v, const float* b, float* y, float omega,
+                             const float* invd, const uint8_t* fixed, int nrhs,
+                             const CgScalars* sc, cudaStream_t st);
 
 // Hierarchy construction (kernels_rap.cu).
 // g, Dinv != nullptr: add the rank-one terms (P_c^T g_c)(P_c^T g_c)^T Dinv_c of Z.
@@ -162,6 +168,12 @@ cudaError_t launch_rap_from_fine(const Dims& fine, const double* C, const double
                                  cudaStream_t st, const double* g = nullptr,
                                  const double* Dinv = nullptr);
 cudaError_t launch_rap_coarse(const Dims& fine, const double* Af, double* Ac, cudaStream_t st);
+// Second coarse level from the finest densities with the 4^dim composite matrices C2.
+cudaError_t launch_rap2_from_fine(const Dims& fine, const double* C2, const double* x, double* Ac,
+                                  cudaStream_t st);
+// Inverse diagonal of the first coarse level from the finest densities and the child matrices.
+cudaError_t launch_inv_diag_l1(const Dims& coarse1, const double* C, const double* xf,
+                               const uint8_t* fixed, double* invd, cudaStream_t st);
 // Dense operator of a level with leading dimension ld; with an arrow (w != nullptr) the row and
 // column n hold w (zero on fixed DOFs) and A[n][n] = *zll.  g, Dinv: rank-one terms (finest level).
 cudaError_t launch_assemble_dense(const Dims& d, const double* K0, const double* x,
