@@ -444,6 +444,17 @@ cudaError_t launch_cg_alpha(long long n, int nrhs, const double* p, const double
   return cudaGetLastError();
 }
 
+template <typename TV>
+cudaError_t launch_cg_p(long long n, int nrhs, const TV* y, double* p, TV* y_old, int flexible,
+                        CgScalars* sc, cudaStream_t st) {
+  k_cg_p<TV><<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, y, p, y_old, flexible, sc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cg_p<double>(long long, int, const double*, double*, double*, int,
+                                         CgScalars*, cudaStream_t);
+template cudaError_t launch_cg_p<float>(long long, int, const float*, double*, float*, int,
+                                        CgScalars*, cudaStream_t);
+
 cudaError_t launch_dot(long long n, int nrhs, const double* a, const double* b, double* partials,
                        unsigned* counters, double* out, cudaStream_t st) {
   k_dot<<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, a, b, partials, counters, out);

@@ -26,7 +26,7 @@ namespace topo {
 namespace {
 
 constexpr int kQ1Cols = 30;   // output node columns per warp
-constexpr int kQ1Rows = 16;   // output node rows per warp strip
+constexpr int kQ1MaxRows = 16;  // output node rows per warp strip (at most)
 constexpr int kQ1Warps = 8;   // warps per block
 
 template <typename T>
@@ -92,27 +92,31 @@ __device__ __forceinline__ double block_sum_q1(double v) {
 }
 
 // MODE 0: y = K v; 1: y = b - K v; 2: y = v + omega D^{-1} (b - K v); 3: y = omega D^{-1} b.
-// DOT (MODE 0, FP64): also p^T q with the last-block finalisation alpha = r^T y / p^T q.
-template <typename T, int MODE, bool DOT>
-__global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, Q1K<T> k,
+// DOT 1 (MODE 0, FP64): also p^T q with the last-block finalisation alpha = r^T y / p^T q.
+// DOT 2 (MODE 2, the last smoothing sweep of the preconditioner): also r~^T y~ against the FP64 CG
+// residual rdot, with the last-block finalisation beta = r~^T y~ / r^T y of Algorithm PCG.
+template <typename T, int MODE, int DOT>
+__global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, int rows, Q1K<T> k,
                                                              const T* __restrict__ x,
                                                              const T* __restrict__ v,
                                                              const T* __restrict__ b,
                                                              T* __restrict__ y, T omega,
                                                              const uint8_t* __restrict__ fixed,
                                                              CgScalars* sc, double* partials,
-                                                             unsigned* counters) {
+                                                             unsigned* counters,
+                                                             const double* __restrict__ rdot) {
   using V2 = typename Vec2<T>::type;
   const int rhs = blockIdx.y;
   if (sc && sc[rhs].done) return;
   const long long n = 2LL * (nx + 1) * (ny + 1);
   v += rhs * n;
   y += rhs * n;
+  if (DOT == 2) rdot += rhs * n;
   if (MODE == 1 || MODE == 2 || MODE == 3) b += rhs * n;
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * kQ1Warps + (threadIdx.x >> 5);
   const int ncolw = (nx + 1 + kQ1Cols - 1) / kQ1Cols;
-  const int nstrip = (ny + 1 + kQ1Rows - 1) / kQ1Rows;
+  const int nstrip = (ny + 1 + rows - 1) / rows;
   const int wc = gw % ncolw, ws = gw / ncolw;
   double part = 0.0;
   if (ws < nstrip) {
@@ -120,21 +124,43 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, Q1K<
     const bool col_ok = (c >= 0 && c <= nx);
     const bool out_lane = (lane >= 1 && lane <= kQ1Cols && col_ok);
     const bool el_col = (lane <= kQ1Cols && c >= 0 && c < nx);
-    const int j0 = ws * kQ1Rows;
-    const int j1 = min(j0 + kQ1Rows, ny + 1);
+    const int j0 = ws * rows;
+    const int j1 = min(j0 + rows, ny + 1);
     const V2* v2 = reinterpret_cast<const V2*>(v);
-    V2 pb;
-    pb.x = T(0);
-    pb.y = T(0);
-    if (MODE != 3 && col_ok && j0 >= 1) pb = v2[c + (long long)(nx + 1) * (j0 - 1)];
+    const V2* b2 = reinterpret_cast<const V2*>(b);
+    const long long rs = nx + 1;  // node row stride
+    V2 zero;
+    zero.x = T(0);
+    zero.y = T(0);
+    V2 pb = zero;
+    if (MODE != 3 && col_ok && j0 >= 1) pb = v2[c + rs * (j0 - 1)];
+    // the loads of row ey + 1 are issued one iteration ahead of their use
+    V2 pt_n = zero, bb_n = zero;
+    T xe_n = T(0);
+    uint16_t fx_n = 0;
+    {
+      const int ey = j0 - 1;
+      if (MODE != 3 && col_ok && ey + 1 <= ny) pt_n = v2[c + rs * (ey + 1)];
+      if (el_col && ey >= 0 && ey < ny) xe_n = x[c + (long long)nx * ey];
+    }
     T cu = T(0), cv = T(0), xcarry = T(0);
     for (int ey = j0 - 1; ey < j1; ++ey) {
-      V2 pt;
-      pt.x = T(0);
-      pt.y = T(0);
-      if (MODE != 3 && col_ok && ey + 1 <= ny) pt = v2[c + (long long)(nx + 1) * (ey + 1)];
-      const bool el_ok = el_col && ey >= 0 && ey < ny;
-      const T xe = el_ok ? x[c + (long long)nx * ey] : T(0);
+      const V2 pt = pt_n;
+      const T xe = xe_n;
+      const V2 bb = bb_n;
+      const uint16_t fx = fx_n;
+      // prefetch: v of node row ey + 2, x of element row ey + 1, b and mask of node row ey + 1
+      pt_n = zero;
+      xe_n = T(0);
+      if (ey + 1 < j1) {
+        if (MODE != 3 && col_ok && ey + 2 <= ny) pt_n = v2[c + rs * (ey + 2)];
+        if (el_col && ey + 1 < ny) xe_n = x[c + (long long)nx * (ey + 1)];
+        if (out_lane && ey + 1 >= j0) {
+          const long long nn = c + rs * (ey + 1);
+          fx_n = *reinterpret_cast<const uint16_t*>(fixed + 2 * nn);
+          if (MODE != 0) bb_n = b2[nn];
+        }
+      }
       const T pbr_u = shfl_dn(pb.x), pbr_v = shfl_dn(pb.y);
       const T ptr_u = shfl_dn(pt.x), ptr_v = shfl_dn(pt.y);
       T ru[4], rv[4];
@@ -152,18 +178,15 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, Q1K<
       const T xpair = xe + (lane >= 1 ? xl : T(0));
       if (ey >= j0 && out_lane) {
         const T qu = cu + ru[0] + l1u, qv = cv + rv[0] + l1v;
-        const long long node = c + (long long)(nx + 1) * ey;
-        const uint16_t fx = *reinterpret_cast<const uint16_t*>(fixed + 2 * node);
+        const long long node = c + rs * ey;
         V2 out;
         if (MODE == 0) {
           out.x = qu;
           out.y = qv;
         } else if (MODE == 1) {
-          const V2 bb = reinterpret_cast<const V2*>(b)[node];
           out.x = bb.x - qu;
           out.y = bb.y - qv;
         } else {
-          const V2 bb = reinterpret_cast<const V2*>(b)[node];
           const T xs = xcarry + xpair;
           const T dinv = xs > T(0) ? T(1) / (k.kd * xs) : T(1);
           if (MODE == 2) {
@@ -177,7 +200,11 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, Q1K<
         if (fx & 0xff) out.x = T(0);
         if (fx >> 8) out.y = T(0);
         reinterpret_cast<V2*>(y)[node] = out;
-        if (DOT) part = fma((double)pb.x, (double)out.x, fma((double)pb.y, (double)out.y, part));
+        if (DOT == 1) part = fma((double)pb.x, (double)out.x, fma((double)pb.y, (double)out.y, part));
+        if (DOT == 2) {
+          const double2 rr = reinterpret_cast<const double2*>(rdot)[node];
+          part = fma(rr.x, (double)out.x, fma(rr.y, (double)out.y, part));
+        }
       }
       cu = ru[3] + l2u;
       cv = rv[3] + l2v;
@@ -201,14 +228,25 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, Q1K<
   s = block_sum_q1(s);
   if (threadIdx.x == 0) {
     CgScalars& S = sc[rhs];
-    S.pq = s;
-    const double alpha = S.ry / s;
-    if (!(s > 0.0) || !isfinite(alpha)) {
-      S.status = TOPO_E_BREAKDOWN;
-      S.done = 1;
-      S.alpha = 0.0;
+    if (DOT == 1) {
+      S.pq = s;
+      const double alpha = S.ry / s;
+      if (!(s > 0.0) || !isfinite(alpha)) {
+        S.status = TOPO_E_BREAKDOWN;
+        S.done = 1;
+        S.alpha = 0.0;
+      } else {
+        S.alpha = alpha;
+      }
     } else {
-      S.alpha = alpha;
+      const double beta = s / S.ry;
+      S.ry_new = s;
+      S.beta = beta;
+      S.ry = s;
+      if (!isfinite(beta)) {
+        S.status = TOPO_E_BREAKDOWN;
+        S.done = 1;
+      }
     }
     counters[rhs] = 0;
   }
@@ -221,7 +259,8 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, Q1K<
 // data movement as k_q1_sweep on the coarse grid (nx, ny = coarse elements); xf holds the finest
 // densities (2nx x 2ny), invd the level's inverse diagonal (modes 2, 3).
 template <int MODE>
-__global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, Q1K<float> k,
+__global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, int rows,
+                                                              Q1K<float> k,
                                                               const float* __restrict__ xf,
                                                               const float* __restrict__ v,
                                                               const float* __restrict__ b,
@@ -238,15 +277,15 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, Q1K
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * kQ1Warps + (threadIdx.x >> 5);
   const int ncolw = (nx + 1 + kQ1Cols - 1) / kQ1Cols;
-  const int nstrip = (ny + 1 + kQ1Rows - 1) / kQ1Rows;
+  const int nstrip = (ny + 1 + rows - 1) / rows;
   const int wc = gw % ncolw, ws = gw / ncolw;
   if (ws >= nstrip) return;
   const int c = wc * kQ1Cols - 1 + lane;
   const bool col_ok = (c >= 0 && c <= nx);
   const bool out_lane = (lane >= 1 && lane <= kQ1Cols && col_ok);
   const bool el_col = (lane <= kQ1Cols && c >= 0 && c < nx);
-  const int j0 = ws * kQ1Rows;
-  const int j1 = min(j0 + kQ1Rows, ny + 1);
+  const int j0 = ws * rows;
+  const int j1 = min(j0 + rows, ny + 1);
   const int fnx = 2 * nx;
   const float2* v2 = reinterpret_cast<const float2*>(v);
   float2 pb = make_float2(0.f, 0.f);
@@ -335,14 +374,131 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, Q1K
   }
 }
 
+// 2D level with stored Galerkin element matrices (entry-major, Ae[q * m + e], q = row * 8 + col),
+// same warp-sweep data movement: lane = element column, the element product y_E = A_E v_E in
+// registers, assembly by shuffles and a carried row.  invd: the level's inverse diagonal; w: the
+// arrow column Z_ul (IP systems; adds w_i v_lambda with v_lambda = v[n]), nullptr otherwise.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kQ1Warps * 32) k_ae_sweep(int nx, int ny, int rows,
+                                                             const T* __restrict__ Ae,
+                                                             const T* __restrict__ v,
+                                                             const T* __restrict__ b,
+                                                             T* __restrict__ y, T omega,
+                                                             const T* __restrict__ invd,
+                                                             const uint8_t* __restrict__ fixed,
+                                                             const T* __restrict__ w,
+                                                             const CgScalars* sc) {
+  using V2 = typename Vec2<T>::type;
+  const int rhs = blockIdx.y;
+  if (sc && sc[rhs].done) return;
+  const long long n = 2LL * (nx + 1) * (ny + 1);
+  const long long m = (long long)nx * ny;
+  v += rhs * n;
+  y += rhs * n;
+  b += rhs * n;
+  const T vlam = (w && MODE != 3) ? v[n] : T(0);
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kQ1Warps + (threadIdx.x >> 5);
+  const int ncolw = (nx + 1 + kQ1Cols - 1) / kQ1Cols;
+  const int nstrip = (ny + 1 + rows - 1) / rows;
+  const int wc = gw % ncolw, ws = gw / ncolw;
+  if (ws >= nstrip) return;
+  const int c = wc * kQ1Cols - 1 + lane;
+  const bool col_ok = (c >= 0 && c <= nx);
+  const bool out_lane = (lane >= 1 && lane <= kQ1Cols && col_ok);
+  const bool el_col = (lane <= kQ1Cols && c >= 0 && c < nx);
+  const int j0 = ws * rows;
+  const int j1 = min(j0 + rows, ny + 1);
+  const V2* v2 = reinterpret_cast<const V2*>(v);
+  const long long rs = nx + 1;
+  V2 pb;
+  pb.x = T(0);
+  pb.y = T(0);
+  if (MODE != 3 && col_ok && j0 >= 1) pb = v2[c + rs * (j0 - 1)];
+  T cu = T(0), cv = T(0);
+  for (int ey = j0 - 1; ey < j1; ++ey) {
+    V2 pt;
+    pt.x = T(0);
+    pt.y = T(0);
+    if (MODE != 3 && col_ok && ey + 1 <= ny) pt = v2[c + rs * (ey + 1)];
+    const bool el_ok = el_col && ey >= 0 && ey < ny;
+    const T pbr_u = shfl_dn(pb.x), pbr_v = shfl_dn(pb.y);
+    const T ptr_u = shfl_dn(pt.x), ptr_v = shfl_dn(pt.y);
+    T r[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) r[q] = T(0);
+    if (MODE != 3 && el_ok) {
+      const T ve[8] = {pb.x, pb.y, pbr_u, pbr_v, ptr_u, ptr_v, pt.x, pt.y};
+      const T* Ael = Ae + c + (long long)nx * ey;
+#pragma unroll
+      for (int row = 0; row < 8; ++row) {
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc = fma(__ldg(Ael + (long long)(row * 8 + q) * m), ve[q], acc);
+        r[row] = acc;
+      }
+    }
+    const T l1u = shfl_up1(r[2]), l1v = shfl_up1(r[3]);
+    const T l2u = shfl_up1(r[4]), l2v = shfl_up1(r[5]);
+    if (ey >= j0 && out_lane) {
+      const long long node = c + rs * ey;
+      T qu = cu + r[0] + l1u, qv = cv + r[1] + l1v;
+      if (w && MODE != 3) {
+        const V2 ww = reinterpret_cast<const V2*>(w)[node];
+        qu = fma(ww.x, vlam, qu);
+        qv = fma(ww.y, vlam, qv);
+      }
+      const uint16_t fx = *reinterpret_cast<const uint16_t*>(fixed + 2 * node);
+      V2 out;
+      if (MODE == 0) {
+        out.x = qu;
+        out.y = qv;
+      } else {
+        const V2 bb = reinterpret_cast<const V2*>(b)[node];
+        if (MODE == 1) {
+          out.x = bb.x - qu;
+          out.y = bb.y - qv;
+        } else {
+          const V2 di = reinterpret_cast<const V2*>(invd)[node];
+          if (MODE == 2) {
+            out.x = fma(omega * di.x, bb.x - qu, pb.x);
+            out.y = fma(omega * di.y, bb.y - qv, pb.y);
+          } else {
+            out.x = omega * di.x * bb.x;
+            out.y = omega * di.y * bb.y;
+          }
+        }
+      }
+      if (fx & 0xff) out.x = T(0);
+      if (fx >> 8) out.y = T(0);
+      reinterpret_cast<V2*>(y)[node] = out;
+    }
+    cu = r[6] + l2u;
+    cv = r[7] + l2v;
+    pb = pt;
+  }
+}
+
 template <typename T>
 Q1K<T> coef_cast(const Q1Coef& c) {
   return Q1K<T>{(T)c.c11, (T)c.c12, (T)c.c22, (T)c.c33, (T)c.cH, (T)c.cHp, (T)c.kd};
 }
 
+// Strip height: short enough that the grid has about one full wave of warps (152 SMs x 32),
+// long enough to amortise the recomputed first element row of each strip.
+int q1_rows(int nx, int ny) {
+  const long long ncolw = (nx + 1 + kQ1Cols - 1) / kQ1Cols;
+  const long long target = 152LL * 32;
+  long long r = (ncolw * (ny + 1) + target - 1) / target;
+  if (r < 2) r = 2;
+  if (r > kQ1MaxRows) r = kQ1MaxRows;
+  return (int)r;
+}
+
 unsigned q1_blocks(int nx, int ny) {
+  const int rows = q1_rows(nx, ny);
   const long long warps = (long long)((nx + 1 + kQ1Cols - 1) / kQ1Cols) *
-                          ((ny + 1 + kQ1Rows - 1) / kQ1Rows);
+                          ((ny + 1 + rows - 1) / rows);
   return (unsigned)((warps + kQ1Warps - 1) / kQ1Warps);
 }
 
@@ -359,20 +515,20 @@ cudaError_t launch_q1_apply(int nx, int ny, int mode, const Q1Coef& coef, const 
   CgScalars* scm = const_cast<CgScalars*>(sc);
   switch (mode) {
     case 0:
-      k_q1_sweep<T, 0, false><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, k, x, v, b, y, omega, fixed,
-                                                               scm, nullptr, nullptr);
+      k_q1_sweep<T, 0, 0><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, q1_rows(nx, ny), k, x, v, b, y, omega, fixed,
+                                                               scm, nullptr, nullptr, nullptr);
       break;
     case 1:
-      k_q1_sweep<T, 1, false><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, k, x, v, b, y, omega, fixed,
-                                                               scm, nullptr, nullptr);
+      k_q1_sweep<T, 1, 0><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, q1_rows(nx, ny), k, x, v, b, y, omega, fixed,
+                                                               scm, nullptr, nullptr, nullptr);
       break;
     case 2:
-      k_q1_sweep<T, 2, false><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, k, x, v, b, y, omega, fixed,
-                                                               scm, nullptr, nullptr);
+      k_q1_sweep<T, 2, 0><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, q1_rows(nx, ny), k, x, v, b, y, omega, fixed,
+                                                               scm, nullptr, nullptr, nullptr);
       break;
     default:
-      k_q1_sweep<T, 3, false><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, k, x, v, b, y, omega, fixed,
-                                                               scm, nullptr, nullptr);
+      k_q1_sweep<T, 3, 0><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, q1_rows(nx, ny), k, x, v, b, y, omega, fixed,
+                                                               scm, nullptr, nullptr, nullptr);
   }
   return cudaGetLastError();
 }
@@ -391,27 +547,82 @@ cudaError_t launch_q1g_apply(int nx, int ny, int mode, const Q1Coef& coef, const
   const Q1K<float> k = coef_cast<float>(coef);
   switch (mode) {
     case 0:
-      k_q1g_sweep<0><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, k, xf, v, b, y, omega, invd, fixed, sc);
+      k_q1g_sweep<0><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, q1_rows(nx, ny), k, xf, v, b, y, omega, invd, fixed, sc);
       break;
     case 1:
-      k_q1g_sweep<1><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, k, xf, v, b, y, omega, invd, fixed, sc);
+      k_q1g_sweep<1><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, q1_rows(nx, ny), k, xf, v, b, y, omega, invd, fixed, sc);
       break;
     case 2:
-      k_q1g_sweep<2><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, k, xf, v, b, y, omega, invd, fixed, sc);
+      k_q1g_sweep<2><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, q1_rows(nx, ny), k, xf, v, b, y, omega, invd, fixed, sc);
       break;
     default:
-      k_q1g_sweep<3><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, k, xf, v, b, y, omega, invd, fixed, sc);
+      k_q1g_sweep<3><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, q1_rows(nx, ny), k, xf, v, b, y, omega, invd, fixed, sc);
   }
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_ae_sweep(int nx, int ny, int mode, const T* Ae, const T* v, const T* b, T* y,
+                            T omega, const T* invd, const uint8_t* fixed, const T* w, int nrhs,
+                            const CgScalars* sc, cudaStream_t st) {
+  dim3 grid(q1_blocks(nx, ny), nrhs);
+  const int rows = q1_rows(nx, ny);
+  switch (mode) {
+    case 0:
+      k_ae_sweep<T, 0><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, rows, Ae, v, b, y, omega, invd,
+                                                        fixed, w, sc);
+      break;
+    case 1:
+      k_ae_sweep<T, 1><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, rows, Ae, v, b, y, omega, invd,
+                                                        fixed, w, sc);
+      break;
+    case 2:
+      k_ae_sweep<T, 2><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, rows, Ae, v, b, y, omega, invd,
+                                                        fixed, w, sc);
+      break;
+    default:
+      k_ae_sweep<T, 3><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, rows, Ae, v, b, y, omega, invd,
+                                                        fixed, w, sc);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_ae_sweep<double>(int, int, int, const double*, const double*,
+                                             const double*, double*, double, const double*,
+                                             const uint8_t*, const double*, int,
+                                             const CgScalars*, cudaStream_t);
+template cudaError_t launch_ae_sweep<float>(int, int, int, const float*, const float*,
+                                            const float*, float*, float, const float*,
+                                            const uint8_t*, const float*, int, const CgScalars*,
+                                            cudaStream_t);
+
+template <typename T>
+cudaError_t launch_q1_smooth_beta(int nx, int ny, const Q1Coef& coef, const T* x, const T* v,
+                                  const T* b, T* y, T omega, const uint8_t* fixed, int nrhs,
+                                  const double* r, double* partials, unsigned* counters,
+                                  CgScalars* sc, cudaStream_t st) {
+  dim3 grid(q1_blocks(nx, ny), nrhs);
+  k_q1_sweep<T, 2, 2><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, q1_rows(nx, ny), coef_cast<T>(coef),
+                                                      x, v, b, y, omega, fixed, sc, partials,
+                                                      counters, r);
+  return cudaGetLastError();
+}
+template cudaError_t launch_q1_smooth_beta<double>(int, int, const Q1Coef&, const double*,
+                                                   const double*, const double*, double*, double,
+                                                   const uint8_t*, int, const double*, double*,
+                                                   unsigned*, CgScalars*, cudaStream_t);
+template cudaError_t launch_q1_smooth_beta<float>(int, int, const Q1Coef&, const float*,
+                                                  const float*, const float*, float*, float,
+                                                  const uint8_t*, int, const double*, double*,
+                                                  unsigned*, CgScalars*, cudaStream_t);
 
 cudaError_t launch_q1_apply_dot(int nx, int ny, const Q1Coef& coef, const double* x,
                                 const double* v, double* y, const uint8_t* fixed, int nrhs,
                                 double* partials, unsigned* counters, CgScalars* sc,
                                 cudaStream_t st) {
   dim3 grid(q1_blocks(nx, ny), nrhs);
-  k_q1_sweep<double, 0, true><<<grid, kQ1Warps * 32, 0, st>>>(
-      nx, ny, coef_cast<double>(coef), x, v, nullptr, y, 0.0, fixed, sc, partials, counters);
+  k_q1_sweep<double, 0, 1><<<grid, kQ1Warps * 32, 0, st>>>(
+      nx, ny, q1_rows(nx, ny), coef_cast<double>(coef), x, v, nullptr, y, 0.0, fixed, sc, partials,
+      counters, nullptr);
   return cudaGetLastError();
 }
 

@@ -258,34 +258,78 @@ __global__ void __launch_bounds__(1024) k_cholesky(int n, double* A, int* info) 
   }
 }
 
-// Row j of A^{-1} = solution of A w = e_j with the factor (L lower, L^T upper): one warp per row.
-__global__ void k_chol_inverse(int n, const double* __restrict__ LU, double* Ainv,
-                               const int* info) {
+// Row j of A^{-1} = solution of A w = e_j with the factor (L lower, L^T upper): one warp per row,
+// the row being built kept in shared memory (kInvWarps warps per block, n <= kMaxCoarse).
+constexpr int kInvWarps = 8;
+
+inline int inv_warps(int n) {
+  const int w = (int)((200 * 1024) / ((size_t)n * sizeof(double)));
+  return w < 1 ? 1 : (w > kInvWarps ? kInvWarps : w);
+}
+
+__global__ void __launch_bounds__(kInvWarps * 32) k_chol_inverse(int n, const double* __restrict__ LU,
+                                                                 double* Ainv, const int* info) {
+  extern __shared__ double wsh[];  // [warps per block][n]
   if (*info) return;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= n) return;
-  const int j = warp;
-  volatile double* w = Ainv + (long long)j * n;
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (j >= n) return;
+  double* w = wsh + (long long)wib * n;
   for (int k = lane; k < n; k += 32) w[k] = 0.0;
   __syncwarp();
   for (int i = j; i < n; ++i) {  // forward: L w = e_j
     const double* Li = LU + (long long)i * n;
     double s = 0.0;
-    for (int k = j + lane; k < i; k += 32) s = fma(Li[k], w[k], s);
+    for (int k = j + lane; k < i; k += 32) s = fma(__ldg(Li + k), w[k], s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) w[i] = ((i == j ? 1.0 : 0.0) - s) / Li[i];
+    if (lane == 0) w[i] = ((i == j ? 1.0 : 0.0) - s) / __ldg(Li + i);
     __syncwarp();
   }
   for (int i = n - 1; i >= 0; --i) {  // backward: L^T w = y
     const double* Ui = LU + (long long)i * n;
     double s = 0.0;
-    for (int k = i + 1 + lane; k < n; k += 32) s = fma(Ui[k], w[k], s);
+    for (int k = i + 1 + lane; k < n; k += 32) s = fma(__ldg(Ui + k), w[k], s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) w[i] = (w[i] - s) / Ui[i];
+    if (lane == 0) w[i] = (w[i] - s) / __ldg(Ui + i);
     __syncwarp();
+  }
+  double* out = Ainv + (long long)j * n;
+  for (int k = lane; k < n; k += 32) out[k] = w[k];
+}
+
+// Cholesky in shared memory for small n (n * n doubles fit in one block's shared memory).
+__global__ void __launch_bounds__(1024) k_cholesky_smem(int n, double* A, int* info) {
+  extern __shared__ double S[];
+  __shared__ int bad;
+  const long long nn = (long long)n * n;
+  for (long long t = threadIdx.x; t < nn; t += blockDim.x) S[t] = A[t];
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      const double akk = S[k * n + k];
+      if (!(akk > 0.0) || !isfinite(akk)) bad = k + 1;
+      else S[k * n + k] = sqrt(akk);
+    }
+    __syncthreads();
+    if (bad) break;
+    const double lkk = S[k * n + k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) S[i * n + k] /= lkk;
+    __syncthreads();
+    for (int i = k + 1 + warp; i < n; i += nw) {
+      const double lik = S[i * n + k];
+      for (int jj = k + 1 + lane; jj <= i; jj += 32) S[i * n + jj] -= lik * S[jj * n + k];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *info = bad;
+  if (bad) return;
+  for (long long t = threadIdx.x; t < nn; t += blockDim.x) {
+    const int i = (int)(t / n), jj = (int)(t % n);
+    A[t] = (jj > i) ? S[(long long)jj * n + i] : S[t];
   }
 }
 
@@ -370,11 +414,28 @@ cudaError_t launch_assemble_dense(const Dims& d, const double* K0, const double*
   return cudaGetLastError();
 }
 
+cudaError_t prepare_coarse_kernels(int n) {
+  const size_t smem = (size_t)n * n * sizeof(double);
+  if (smem <= 200 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_cholesky_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaFuncSetAttribute(k_chol_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              200 * 1024);
+}
+
 cudaError_t launch_cholesky_inverse(int n, double* A, double* Ainv, int* info, cudaStream_t st) {
-  k_cholesky<<<1, 1024, 0, st>>>(n, A, info);
+  const size_t smem = (size_t)n * n * sizeof(double);
+  if (smem <= 200 * 1024)
+    k_cholesky_smem<<<1, 1024, smem, st>>>(n, A, info);
+  else
+    k_cholesky<<<1, 1024, 0, st>>>(n, A, info);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_chol_inverse<<<blocks_for((long long)n * 32), kThreads, 0, st>>>(n, A, Ainv, info);
+  const int wpb = inv_warps(n);
+  const size_t wsm = (size_t)wpb * n * sizeof(double);
+  k_chol_inverse<<<(n + wpb - 1) / wpb, wpb * 32, wsm, st>>>(n, A, Ainv, info);
   return cudaGetLastError();
 }
 

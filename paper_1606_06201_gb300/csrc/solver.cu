@@ -239,9 +239,13 @@ topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* 
                                         lv.omega_dev));
       return TOPO_OK;
     }
-    TOPO_CUDA(launch_apply<TV>(lv.d, mode, Prec<TV>::K0(s), nullptr, Prec<TV>::Ae(lv), v, b, y,
-                               Prec<TV>::invd(lv), omega, lv.fixed, 1, sc, s->st,
-                               mode == 3 ? nullptr : arrow_w<TV>(lv)));
+    if (s->dim == 2 && !s->desc.generic_kernels)
+      TOPO_CUDA(launch_ae_sweep<TV>(lv.d.nx, lv.d.ny, mode, Prec<TV>::Ae(lv), v, b, y, omega,
+                                    Prec<TV>::invd(lv), lv.fixed, arrow_w<TV>(lv), 1, sc, s->st));
+    else
+      TOPO_CUDA(launch_apply<TV>(lv.d, mode, Prec<TV>::K0(s), nullptr, Prec<TV>::Ae(lv), v, b, y,
+                                 Prec<TV>::invd(lv), omega, lv.fixed, 1, sc, s->st,
+                                 mode == 3 ? nullptr : arrow_w<TV>(lv)));
     TOPO_CUDA(launch_arrow_row<TV>(lv.n, mode, arrow_w<TV>(lv), v, b, y, s->zll,
                                    (double)s->desc.omega, s->partials, s->counters, sc, s->st,
                                    lv.omega_dev));
@@ -265,14 +269,22 @@ topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* 
   }
   const TV* x = k == 0 ? Prec<TV>::x(s) : nullptr;
   const TV* Ae = k == 0 ? nullptr : Prec<TV>::Ae(lv);
+  if (k >= 1 && s->dim == 2 && !s->desc.generic_kernels) {
+    TOPO_CUDA(launch_ae_sweep<TV>(lv.d.nx, lv.d.ny, mode, Ae, v, b, y, omega, Prec<TV>::invd(lv),
+                                  lv.fixed, (const TV*)nullptr, s->nrhs, sc, s->st));
+    return TOPO_OK;
+  }
   TOPO_CUDA(launch_apply<TV>(lv.d, mode, Prec<TV>::K0(s), x, Ae, v, b, y, Prec<TV>::invd(lv), omega,
                              lv.fixed, s->nrhs, sc, s->st));
   return TOPO_OK;
 }
 
 // One V-cycle at level k with right-hand side b (Algorithm MG, function mgm, from z = 0).
+// fuse_beta: the last smoothing sweep of the finest level also forms r~^T y~ and beta (the CG
+// direction update then needs only the p kernel).
 template <typename TV>
-topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScalars* sc) {
+topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScalars* sc,
+                   bool fuse_beta = false) {
   Level& lv = s->L[k];
   const int nrhs = s->nrhs;
   TV* zk = (TV*)lv.z;
@@ -297,10 +309,15 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
   Level& lc = s->L[k + 1];
   TOPO_CUDA(launch_restrict<TV>(lv.d, oth, (TV*)lc.b, lc.fixed, nrhs, sc, s->st, s->arrow));
   TV* zc = nullptr;
-  TOPO_TRY(vcycle<TV>(s, k + 1, (const TV*)lc.b, &zc, sc));
+  TOPO_TRY(vcycle<TV>(s, k + 1, (const TV*)lc.b, &zc, sc, false));
   TOPO_CUDA(launch_prolong_add<TV>(lv.d, zc, cur, lv.fixed, nrhs, sc, s->st, s->arrow));
   for (int it = 0; it < nu2; ++it) {
-    TOPO_TRY(apply_level<TV>(s, k, 2, cur, b, oth, sc));
+    if (fuse_beta && k == 0 && it == nu2 - 1)
+      TOPO_CUDA(launch_q1_smooth_beta<TV>(lv.d.nx, lv.d.ny, s->q1, Prec<TV>::x(s), cur, b, oth,
+                                          (TV)s->desc.omega, lv.fixed, nrhs, s->r, s->partials,
+                                          s->counters, const_cast<CgScalars*>(sc), s->st));
+    else
+      TOPO_TRY(apply_level<TV>(s, k, 2, cur, b, oth, sc));
     std::swap(cur, oth);
   }
   *result = cur;
@@ -309,10 +326,10 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
 
 // Preconditioner on the PCG residual r: y = M^{-1} r (result pointer returned).
 template <typename TV>
-topo_status precondition(topo_solver* s, const CgScalars* sc, void** y) {
+topo_status precondition(topo_solver* s, const CgScalars* sc, void** y, bool fuse_beta = false) {
   TV* out = nullptr;
   const TV* b = std::is_same<TV, double>::value ? (const TV*)s->r : (const TV*)s->rv;
-  TOPO_TRY(vcycle<TV>(s, 0, b, &out, sc));
+  TOPO_TRY(vcycle<TV>(s, 0, b, &out, sc, fuse_beta));
   *y = out;
   return TOPO_OK;
 }
@@ -341,10 +358,15 @@ topo_status cg_iteration(topo_solver* s, int slot, double tol, int max_iter) {
   TOPO_CUDA(launch_cg_update<TV>(n, s->nrhs, s->z, s->r, s->p, s->q, rv, s->partials, s->counters,
                                  s->sc, tol, max_iter, s->st));
   void* y = nullptr;
-  TOPO_TRY(precondition<TV>(s, s->sc, &y));
+  const bool fuse = s->q1_ok && !s->arrow && s->desc.nu2 >= 1 && !s->desc.flexible &&
+                    s->nlev >= 2;
+  TOPO_TRY(precondition<TV>(s, s->sc, &y, fuse));
   s->yv = y;
-  TOPO_CUDA(launch_cg_direction<TV>(n, s->nrhs, s->r, (const TV*)y, s->p, (TV*)s->yold,
-                                    s->desc.flexible, s->partials, s->counters, s->sc, s->st));
+  if (fuse)
+    TOPO_CUDA(launch_cg_p<TV>(n, s->nrhs, (const TV*)y, s->p, (TV*)s->yold, 0, s->sc, s->st));
+  else
+    TOPO_CUDA(launch_cg_direction<TV>(n, s->nrhs, s->r, (const TV*)y, s->p, (TV*)s->yold,
+                                      s->desc.flexible, s->partials, s->counters, s->sc, s->st));
   return TOPO_OK;
 }
 
@@ -683,6 +705,7 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   Level& lc = s->L[s->nlev - 1];
   s->nc = (int)lc.n;
   const size_t na = (size_t)s->nc + (arrow ? 1 : 0);
+  TOPO_CUDA(prepare_coarse_kernels((int)na));
   TOPO_TRY(s->alloc(&s->Adense, na * na));
   TOPO_TRY(s->alloc(&s->Ainv, na * na));
   TOPO_TRY(s->alloc(&s->info, 2));

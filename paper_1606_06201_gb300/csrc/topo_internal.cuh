@@ -155,6 +155,18 @@ cudaError_t launch_q1_apply_dot(int nx, int ny, const Q1Coef& coef, const double
                                 double* partials, unsigned* counters, CgScalars* sc,
                                 cudaStream_t st);
 long long q1_partial_blocks(int nx, int ny);
+// Jacobi sweep (mode 2) on the 2D finest level fused with r^T y against the FP64 CG residual r and
+// the beta of Algorithm PCG (last smoothing sweep of the preconditioner).
+template <typename T>
+cudaError_t launch_q1_smooth_beta(int nx, int ny, const Q1Coef& coef, const T* x, const T* v,
+                                  const T* b, T* y, T omega, const uint8_t* fixed, int nrhs,
+                                  const double* r, double* partials, unsigned* counters,
+                                  CgScalars* sc, cudaStream_t st);
+// 2D level with stored (entry-major) element matrices, warp-sweep data movement; w: arrow column.
+template <typename T>
+cudaError_t launch_ae_sweep(int nx, int ny, int mode, const T* Ae, const T* v, const T* b, T* y,
+                            T omega, const T* invd, const uint8_t* fixed, const T* w, int nrhs,
+                            const CgScalars* sc, cudaStream_t st);
 // First coarse level of the 2D Q1 hierarchy, matrix-free in FP32 (P^T K(x) P element by element);
 // nx, ny = coarse elements, xf = finest densities.
 cudaError_t launch_q1g_apply(int nx, int ny, int mode, const Q1Coef& coef, const float* xf,
@@ -183,6 +195,8 @@ cudaError_t launch_assemble_dense(const Dims& d, const double* K0, const double*
                                   const double* zll = nullptr, const double* g = nullptr,
                                   const double* Dinv = nullptr);
 cudaError_t launch_cholesky_inverse(int n, double* A, double* Ainv, int* info, cudaStream_t st);
+// Shared-memory limits of the coarsest-level kernels (call once, outside stream capture).
+cudaError_t prepare_coarse_kernels(int n);
 template <typename T>
 cudaError_t launch_dense_solve(int n, const double* Ainv, const T* b, T* z, int nrhs,
                                const CgScalars* sc, cudaStream_t st);
@@ -206,6 +220,10 @@ template <typename TV>
 cudaError_t launch_cg_direction(long long n, int nrhs, const double* r, const TV* y, double* p,
                                 TV* y_old, int flexible, double* partials, unsigned* counters,
                                 CgScalars* sc, cudaStream_t st);
+// p = -y + beta p (beta already in the scalars), y_old = y if flexible.
+template <typename TV>
+cudaError_t launch_cg_p(long long n, int nrhs, const TV* y, double* p, TV* y_old, int flexible,
+                        CgScalars* sc, cudaStream_t st);
 cudaError_t launch_dot(long long n, int nrhs, const double* a, const double* b, double* partials,
                        unsigned* counters, double* out, cudaStream_t st);
 // Power iteration for lambda_max(D^{-1} A): v <- D^{-1} A v / ||.||_D (y = A v supplied by the

@@ -155,7 +155,7 @@ def _desc(nx, ny, nz, fixed, levels, precision, nu1, nu2, omega, max_iter, nrhs,
     if omega is None:
         omega = 0.6 if dim == 2 else 0.5
     if flexible is None:
-        flexible = 1 if precision == MIXED else 0
+        flexible = 0
     d = SolverDesc(dim, nx, ny, nz, E, nu, fixed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
                    levels, precision, nu1, nu2, omega, max_iter, nrhs, flexible,
                    int(generic_kernels), int(omega_auto))
@@ -301,7 +301,7 @@ class Solver:
         if omega is None:
             omega = 0.6 if dim == 2 else 0.5
         if flexible is None:
-            flexible = 1 if precision == MIXED else 0
+            flexible = 0
         d = SolverDesc(dim, nx, ny, nz, E, nu,
                        self._fixed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), levels,
                        precision, nu1, nu2, omega, max_iter, nrhs, flexible, int(generic_kernels),
