@@ -164,6 +164,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ip", action="store_true", help="skip the 512x256 IP/OC wall-time runs")
     ap.add_argument("--only", choices=["mixed", "fp64"], default=None,
                     help="run one solver configuration only (for profiler launch lists); no JSON line")
     args = ap.parse_args()
@@ -251,6 +252,32 @@ def main():
         fp64 = run(topo.FP64, args.steps, args.warmup)
         e2e = run(topo.MIXED, args.steps, args.warmup, host_io=True)
 
+    def ip_oc_runs():
+        """512x256 cantilever (Example 2 shape 428, V = 0.4 m, 6 levels): IP and AOC with 50 outer
+        iterations each (linear solves to 1e-8), FP64 and mixed."""
+        out = {}
+        c2 = W.cantilever_2d(512, 256, 0.4)
+        f2 = torch.as_tensor(c2["f"], device=dev)
+        for name, prec in (("fp64", topo.FP64), ("mixed", topo.MIXED)):
+            ip = topo.IP(512, 256, fixed=c2["fixed"], f=f2, V=c2["V"], xbar=1.0, levels=6,
+                         precision=prec, max_iter=5000)
+            info = ip.run(topo.ip_options(cg_tol=1e-8, max_newton=50))
+            u = ip.state()[0]
+            out["ip_" + name] = {"wall_s": info.wall_ms * 1e-3, "newton": info.newton,
+                                 "ip_iters": info.ip_iters, "cg_iters": info.cg_iters,
+                                 "feval": info.feval, "compliance": float(f2 @ u), "done": info.done}
+            ip.close()
+            oc = topo.OC(512, 256, fixed=c2["fixed"], f=f2, V=c2["V"], xbar=1.0, levels=6,
+                         precision=prec)
+            oc.init()
+            oinfo = oc.run(topo.oc_options(max_feval=50, tau_oc=0.0, cg_tol0=1e-8,
+                                           adaptive_tol=False))
+            out["aoc_" + name] = {"wall_s": oinfo.wall_ms * 1e-3, "feval": oinfo.feval,
+                                  "iters": oinfo.iters, "cg_iters": oinfo.cg_iters,
+                                  "compliance": oinfo.compliance}
+            oc.close()
+        return out
+
     def gather_max(v):
         if ws == 1:
             return v
@@ -306,6 +333,8 @@ def main():
             "gpu_launches": mixed["launches"],
             "clocks": clk.summary(),
         }
+        if not args.no_ip:
+            line["ip_oc_512x256"] = ip_oc_runs()
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

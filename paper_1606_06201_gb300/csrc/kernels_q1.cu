@@ -374,111 +374,6 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, int
   }
 }
 
-// 2D level with stored Galerkin element matrices (entry-major, Ae[q * m + e], q = row * 8 + col),
-// same warp-sweep data movement: lane = element column, the element product y_E = A_E v_E in
-// registers, assembly by shuffles and a carried row.  invd: the level's inverse diagonal; w: the
-// arrow column Z_ul (IP systems; adds w_i v_lambda with v_lambda = v[n]), nullptr otherwise.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kQ1Warps * 32) k_ae_sweep(int nx, int ny, int rows,
-                                                             const T* __restrict__ Ae,
-                                                             const T* __restrict__ v,
-                                                             const T* __restrict__ b,
-                                                             T* __restrict__ y, T omega,
-                                                             const T* __restrict__ invd,
-                                                             const uint8_t* __restrict__ fixed,
-                                                             const T* __restrict__ w,
-                                                             const CgScalars* sc) {
-  using V2 = typename Vec2<T>::type;
-  const int rhs = blockIdx.y;
-  if (sc && sc[rhs].done) return;
-  const long long n = 2LL * (nx + 1) * (ny + 1);
-  const long long m = (long long)nx * ny;
-  v += rhs * n;
-  y += rhs * n;
-  b += rhs * n;
-  const T vlam = (w && MODE != 3) ? v[n] : T(0);
-  const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * kQ1Warps + (threadIdx.x >> 5);
-  const int ncolw = (nx + 1 + kQ1Cols - 1) / kQ1Cols;
-  const int nstrip = (ny + 1 + rows - 1) / rows;
-  const int wc = gw % ncolw, ws = gw / ncolw;
-  if (ws >= nstrip) return;
-  const int c = wc * kQ1Cols - 1 + lane;
-  const bool col_ok = (c >= 0 && c <= nx);
-  const bool out_lane = (lane >= 1 && lane <= kQ1Cols && col_ok);
-  const bool el_col = (lane <= kQ1Cols && c >= 0 && c < nx);
-  const int j0 = ws * rows;
-  const int j1 = min(j0 + rows, ny + 1);
-  const V2* v2 = reinterpret_cast<const V2*>(v);
-  const long long rs = nx + 1;
-  V2 pb;
-  pb.x = T(0);
-  pb.y = T(0);
-  if (MODE != 3 && col_ok && j0 >= 1) pb = v2[c + rs * (j0 - 1)];
-  T cu = T(0), cv = T(0);
-  for (int ey = j0 - 1; ey < j1; ++ey) {
-    V2 pt;
-    pt.x = T(0);
-    pt.y = T(0);
-    if (MODE != 3 && col_ok && ey + 1 <= ny) pt = v2[c + rs * (ey + 1)];
-    const bool el_ok = el_col && ey >= 0 && ey < ny;
-    const T pbr_u = shfl_dn(pb.x), pbr_v = shfl_dn(pb.y);
-    const T ptr_u = shfl_dn(pt.x), ptr_v = shfl_dn(pt.y);
-    T r[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) r[q] = T(0);
-    if (MODE != 3 && el_ok) {
-      const T ve[8] = {pb.x, pb.y, pbr_u, pbr_v, ptr_u, ptr_v, pt.x, pt.y};
-      const T* Ael = Ae + c + (long long)nx * ey;
-#pragma unroll
-      for (int row = 0; row < 8; ++row) {
-        T acc = T(0);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc = fma(__ldg(Ael + (long long)(row * 8 + q) * m), ve[q], acc);
-        r[row] = acc;
-      }
-    }
-    const T l1u = shfl_up1(r[2]), l1v = shfl_up1(r[3]);
-    const T l2u = shfl_up1(r[4]), l2v = shfl_up1(r[5]);
-    if (ey >= j0 && out_lane) {
-      const long long node = c + rs * ey;
-      T qu = cu + r[0] + l1u, qv = cv + r[1] + l1v;
-      if (w && MODE != 3) {
-        const V2 ww = reinterpret_cast<const V2*>(w)[node];
-        qu = fma(ww.x, vlam, qu);
-        qv = fma(ww.y, vlam, qv);
-      }
-      const uint16_t fx = *reinterpret_cast<const uint16_t*>(fixed + 2 * node);
-      V2 out;
-      if (MODE == 0) {
-        out.x = qu;
-        out.y = qv;
-      } else {
-        const V2 bb = reinterpret_cast<const V2*>(b)[node];
-        if (MODE == 1) {
-          out.x = bb.x - qu;
-          out.y = bb.y - qv;
-        } else {
-          const V2 di = reinterpret_cast<const V2*>(invd)[node];
-          if (MODE == 2) {
-            out.x = fma(omega * di.x, bb.x - qu, pb.x);
-            out.y = fma(omega * di.y, bb.y - qv, pb.y);
-          } else {
-            out.x = omega * di.x * bb.x;
-            out.y = omega * di.y * bb.y;
-          }
-        }
-      }
-      if (fx & 0xff) out.x = T(0);
-      if (fx >> 8) out.y = T(0);
-      reinterpret_cast<V2*>(y)[node] = out;
-    }
-    cu = r[6] + l2u;
-    cv = r[7] + l2v;
-    pb = pt;
-  }
-}
-
 template <typename T>
 Q1K<T> coef_cast(const Q1Coef& c) {
   return Q1K<T>{(T)c.c11, (T)c.c12, (T)c.c22, (T)c.c33, (T)c.cH, (T)c.cHp, (T)c.kd};
@@ -560,40 +455,6 @@ cudaError_t launch_q1g_apply(int nx, int ny, int mode, const Q1Coef& coef, const
   }
   return cudaGetLastError();
 }
-
-template <typename T>
-cudaError_t launch_ae_sweep(int nx, int ny, int mode, const T* Ae, const T* v, const T* b, T* y,
-                            T omega, const T* invd, const uint8_t* fixed, const T* w, int nrhs,
-                            const CgScalars* sc, cudaStream_t st) {
-  dim3 grid(q1_blocks(nx, ny), nrhs);
-  const int rows = q1_rows(nx, ny);
-  switch (mode) {
-    case 0:
-      k_ae_sweep<T, 0><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, rows, Ae, v, b, y, omega, invd,
-                                                        fixed, w, sc);
-      break;
-    case 1:
-      k_ae_sweep<T, 1><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, rows, Ae, v, b, y, omega, invd,
-                                                        fixed, w, sc);
-      break;
-    case 2:
-      k_ae_sweep<T, 2><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, rows, Ae, v, b, y, omega, invd,
-                                                        fixed, w, sc);
-      break;
-    default:
-      k_ae_sweep<T, 3><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, rows, Ae, v, b, y, omega, invd,
-                                                        fixed, w, sc);
-  }
-  return cudaGetLastError();
-}
-template cudaError_t launch_ae_sweep<double>(int, int, int, const double*, const double*,
-                                             const double*, double*, double, const double*,
-                                             const uint8_t*, const double*, int,
-                                             const CgScalars*, cudaStream_t);
-template cudaError_t launch_ae_sweep<float>(int, int, int, const float*, const float*,
-                                            const float*, float*, float, const float*,
-                                            const uint8_t*, const float*, int, const CgScalars*,
-                                            cudaStream_t);
 
 template <typename T>
 cudaError_t launch_q1_smooth_beta(int nx, int ny, const Q1Coef& coef, const T* x, const T* v,

@@ -299,6 +299,61 @@ __global__ void __launch_bounds__(kInvWarps * 32) k_chol_inverse(int n, const do
   for (int k = lane; k < n; k += 32) out[k] = w[k];
 }
 
+// Cholesky and inverse in one block with everything in shared memory (small n): the factor, then
+// one warp per column j of A^{-1} (forward and backward substitution against e_j).
+__global__ void __launch_bounds__(1024) k_cholinv_smem(int n, double* A, double* Ainv, int* info) {
+  extern __shared__ double S[];   // [n][n] factor, then [32][n] work rows
+  __shared__ int bad;
+  const long long nn = (long long)n * n;
+  double* W = S + nn;
+  for (long long t = threadIdx.x; t < nn; t += blockDim.x) S[t] = A[t];
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      const double akk = S[k * n + k];
+      if (!(akk > 0.0) || !isfinite(akk)) bad = k + 1;
+      else S[k * n + k] = sqrt(akk);
+    }
+    __syncthreads();
+    if (bad) break;
+    const double rkk = 1.0 / S[k * n + k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) S[i * n + k] *= rkk;
+    __syncthreads();
+    for (int i = k + 1 + warp; i < n; i += nw) {
+      const double lik = S[i * n + k];
+      for (int jj = k + 1 + lane; jj <= i; jj += 32) S[i * n + jj] -= lik * S[jj * n + k];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *info = bad;
+  if (bad) return;
+  double* w = W + (long long)warp * n;
+  for (int j = warp; j < n; j += nw) {
+    for (int k = lane; k < n; k += 32) w[k] = 0.0;
+    __syncwarp();
+    for (int i = j; i < n; ++i) {  // L w = e_j
+      double t = 0.0;
+      for (int k = j + lane; k < i; k += 32) t = fma(S[i * n + k], w[k], t);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) w[i] = ((i == j ? 1.0 : 0.0) - t) / S[i * n + i];
+      __syncwarp();
+    }
+    for (int i = n - 1; i >= 0; --i) {  // L^T w = y (column i of L below the diagonal)
+      double t = 0.0;
+      for (int k = i + 1 + lane; k < n; k += 32) t = fma(S[k * n + i], w[k], t);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) w[i] = (w[i] - t) / S[i * n + i];
+      __syncwarp();
+    }
+    for (int k = lane; k < n; k += 32) Ainv[(long long)j * n + k] = w[k];
+    __syncwarp();
+  }
+}
+
 // Cholesky in shared memory for small n (n * n doubles fit in one block's shared memory).
 __global__ void __launch_bounds__(1024) k_cholesky_smem(int n, double* A, int* info) {
   extern __shared__ double S[];
@@ -414,7 +469,14 @@ cudaError_t launch_assemble_dense(const Dims& d, const double* K0, const double*
   return cudaGetLastError();
 }
 
+inline size_t cholinv_smem_bytes(int n) { return ((size_t)n * n + 32 * (size_t)n) * sizeof(double); }
+
 cudaError_t prepare_coarse_kernels(int n) {
+  if (cholinv_smem_bytes(n) <= 200 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_cholinv_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024);
+    if (e != cudaSuccess) return e;
+  }
   const size_t smem = (size_t)n * n * sizeof(double);
   if (smem <= 200 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_cholesky_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -426,6 +488,10 @@ cudaError_t prepare_coarse_kernels(int n) {
 }
 
 cudaError_t launch_cholesky_inverse(int n, double* A, double* Ainv, int* info, cudaStream_t st) {
+  if (cholinv_smem_bytes(n) <= 200 * 1024) {
+    k_cholinv_smem<<<1, 1024, cholinv_smem_bytes(n), st>>>(n, A, Ainv, info);
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)n * n * sizeof(double);
   if (smem <= 200 * 1024)
     k_cholesky_smem<<<1, 1024, smem, st>>>(n, A, info);

@@ -239,13 +239,9 @@ topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* 
                                         lv.omega_dev));
       return TOPO_OK;
     }
-    if (s->dim == 2 && !s->desc.generic_kernels)
-      TOPO_CUDA(launch_ae_sweep<TV>(lv.d.nx, lv.d.ny, mode, Prec<TV>::Ae(lv), v, b, y, omega,
-                                    Prec<TV>::invd(lv), lv.fixed, arrow_w<TV>(lv), 1, sc, s->st));
-    else
-      TOPO_CUDA(launch_apply<TV>(lv.d, mode, Prec<TV>::K0(s), nullptr, Prec<TV>::Ae(lv), v, b, y,
-                                 Prec<TV>::invd(lv), omega, lv.fixed, 1, sc, s->st,
-                                 mode == 3 ? nullptr : arrow_w<TV>(lv)));
+    TOPO_CUDA(launch_apply<TV>(lv.d, mode, Prec<TV>::K0(s), nullptr, Prec<TV>::Ae(lv), v, b, y,
+                               Prec<TV>::invd(lv), omega, lv.fixed, 1, sc, s->st,
+                               mode == 3 ? nullptr : arrow_w<TV>(lv)));
     TOPO_CUDA(launch_arrow_row<TV>(lv.n, mode, arrow_w<TV>(lv), v, b, y, s->zll,
                                    (double)s->desc.omega, s->partials, s->counters, sc, s->st,
                                    lv.omega_dev));
@@ -269,11 +265,6 @@ topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* 
   }
   const TV* x = k == 0 ? Prec<TV>::x(s) : nullptr;
   const TV* Ae = k == 0 ? nullptr : Prec<TV>::Ae(lv);
-  if (k >= 1 && s->dim == 2 && !s->desc.generic_kernels) {
-    TOPO_CUDA(launch_ae_sweep<TV>(lv.d.nx, lv.d.ny, mode, Ae, v, b, y, omega, Prec<TV>::invd(lv),
-                                  lv.fixed, (const TV*)nullptr, s->nrhs, sc, s->st));
-    return TOPO_OK;
-  }
   TOPO_CUDA(launch_apply<TV>(lv.d, mode, Prec<TV>::K0(s), x, Ae, v, b, y, Prec<TV>::invd(lv), omega,
                              lv.fixed, s->nrhs, sc, s->st));
   return TOPO_OK;

@@ -162,6 +162,13 @@ cudaError_t launch_q1_smooth_beta(int nx, int ny, const Q1Coef& coef, const T* x
                                   const T* b, T* y, T omega, const uint8_t* fixed, int nrhs,
                                   const double* r, double* partials, unsigned* counters,
                                   CgScalars* sc, cudaStream_t st);
+// Jacobi sweep (mode 2) on the 2D finest level fused with r^T y against the FP64 CG residual r and
+// the beta of Algorithm PCG (last smoothing sweep of the preconditioner).
+template <typename T>
+cudaError_t launch_q1_smooth_beta(int nx, int ny, const Q1Coef& coef, const T* x, const T* v,
+                                  const T* b, T* y, T omega, const uint8_t* fixed, int nrhs,
+                                  const double* r, double* partials, unsigned* counters,
+                                  CgScalars* sc, cudaStream_t st);
 // 2D level with stored (entry-major) element matrices, warp-sweep data movement; w: arrow column.
 template <typename T>
 cudaError_t launch_ae_sweep(int nx, int ny, int mode, const T* Ae, const T* v, const T* b, T* y,
