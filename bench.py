@@ -260,7 +260,7 @@ def main():
         f2 = torch.as_tensor(c2["f"], device=dev)
         for name, prec in (("fp64", topo.FP64), ("mixed", topo.MIXED)):
             ip = topo.IP(512, 256, fixed=c2["fixed"], f=f2, V=c2["V"], xbar=1.0, levels=6,
-                         precision=prec, max_iter=5000)
+                         precision=prec, max_iter=1000)
             info = ip.run(topo.ip_options(cg_tol=1e-8, max_newton=50))
             u = ip.state()[0]
             out["ip_" + name] = {"wall_s": info.wall_ms * 1e-3, "newton": info.newton,

@@ -65,13 +65,14 @@ struct topo_oc {
 namespace {
 
 __global__ void k_fill(long long n, double* a, double v) {
+  pdl_prologue();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) a[i] = v;
 }
 
 topo_status fill(double* a, long long n, double v, cudaStream_t st) {
   if (n <= 0) return TOPO_OK;
-  k_fill<<<blocks_for(n), kThreads, 0, st>>>(n, a, v);
+  topo::launch(k_fill, blocks_for(n), kThreads, 0, st, n, a, v);
   TOPO_CHECK_LAUNCH("fill");
   return TOPO_OK;
 }

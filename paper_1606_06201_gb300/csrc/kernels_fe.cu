@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(Dims d, const T* __restrict_
                                                     const uint8_t* __restrict__ fixed,
                                                     const CgScalars* __restrict__ sc,
                                                     const T* __restrict__ w) {
+  pdl_prologue();
   const int rhs = blockIdx.y;
   if (sc && sc[rhs].done) return;
   const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -141,6 +142,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_l1(Dims d, const T* __restri
                                                        const T* __restrict__ invd, T omega,
                                                        const uint8_t* __restrict__ fixed,
                                                        const CgScalars* __restrict__ sc) {
+  pdl_prologue();
   constexpr int NE = 8, NE2 = 64;
   const int rhs = blockIdx.y;
   if (sc && sc[rhs].done) return;
@@ -203,10 +205,10 @@ void apply_dispatch(const Dims& d, const T* K0, const T* x, const T* Ae, const T
                     const CgScalars* sc, cudaStream_t st, const T* w) {
   dim3 grid(blocks_for(d.nodes()), nrhs);
   if (x)
-    k_apply<DIM, T, MODE, true><<<grid, kThreads, 0, st>>>(d, K0, x, Ae, v, b, y, invd, omega,
+    topo::launch(k_apply<DIM, T, MODE, true>, grid, kThreads, 0, st, d, K0, x, Ae, v, b, y, invd, omega,
                                                            fixed, sc, w);
   else
-    k_apply<DIM, T, MODE, false><<<grid, kThreads, 0, st>>>(d, K0, x, Ae, v, b, y, invd, omega,
+    topo::launch(k_apply<DIM, T, MODE, false>, grid, kThreads, 0, st, d, K0, x, Ae, v, b, y, invd, omega,
                                                             fixed, sc, w);
 }
 
@@ -238,6 +240,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_dot_fine(Dims d, const doubl
                                                              const uint8_t* __restrict__ fixed,
                                                              double* partials, unsigned* counters,
                                                              CgScalars* sc) {
+  pdl_prologue();
   const int rhs = blockIdx.y;
   if (sc[rhs].done) return;
   const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -297,6 +300,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict(Dims df, const T* __restr
                                                        const uint8_t* __restrict__ fixed_c,
                                                        const CgScalars* __restrict__ sc,
                                                        int arrow) {
+  pdl_prologue();
   const int rhs = blockIdx.y;
   if (sc && sc[rhs].done) return;
   Dims dc{df.nx / 2, df.ny / 2, DIM == 3 ? df.nz / 2 : 1, DIM};
@@ -346,6 +350,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong_add(Dims df, const T* __re
                                                           const uint8_t* __restrict__ fixed_f,
                                                           const CgScalars* __restrict__ sc,
                                                           int arrow) {
+  pdl_prologue();
   const int rhs = blockIdx.y;
   if (sc && sc[rhs].done) return;
   Dims dc{df.nx / 2, df.ny / 2, DIM == 3 ? df.nz / 2 : 1, DIM};
@@ -395,6 +400,7 @@ template <int DIM>
 __global__ void k_inv_diag(Dims d, const double* __restrict__ K0, const double* __restrict__ x,
                            const double* __restrict__ Ae, const uint8_t* __restrict__ fixed,
                            double* __restrict__ invd) {
+  pdl_prologue();
   constexpr int NN = Elem<DIM>::NN, NE = Elem<DIM>::NE;
   const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= d.nodes()) return;
@@ -425,6 +431,7 @@ template <int DIM>
 __global__ void k_element_energy(Dims d, const double* __restrict__ K0,
                                  const double* __restrict__ u, const double* __restrict__ lam,
                                  double* __restrict__ out, double scale) {
+  pdl_prologue();
   constexpr int NN = Elem<DIM>::NN, NE = Elem<DIM>::NE;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= d.elems()) return;
@@ -454,6 +461,7 @@ __global__ void k_element_energy(Dims d, const double* __restrict__ K0,
 
 // flag = 1 if any x_i is not finite or not > 0 (x_i > 0 is false for NaN).
 __global__ void k_check_positive(const double* __restrict__ x, long long m, int* flag) {
+  pdl_prologue();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < m) {
     const double v = x[i];
@@ -462,11 +470,13 @@ __global__ void k_check_positive(const double* __restrict__ x, long long m, int*
 }
 
 __global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  pdl_prologue();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
 }
 
 __global__ void k_f2d(const float* __restrict__ a, double* __restrict__ b, long long n) {
+  pdl_prologue();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (double)a[i];
 }
@@ -516,16 +526,16 @@ cudaError_t launch_apply_l1(const Dims& d, int mode, const T* C, const T* xf, co
   dim3 grid(blocks_for(d.nodes()), nrhs);
   switch (mode) {
     case 0:
-      k_apply_l1<T, 0><<<grid, kThreads, 0, st>>>(d, C, xf, v, b, y, invd, omega, fixed, sc);
+      topo::launch(k_apply_l1<T, 0>, grid, kThreads, 0, st, d, C, xf, v, b, y, invd, omega, fixed, sc);
       break;
     case 1:
-      k_apply_l1<T, 1><<<grid, kThreads, 0, st>>>(d, C, xf, v, b, y, invd, omega, fixed, sc);
+      topo::launch(k_apply_l1<T, 1>, grid, kThreads, 0, st, d, C, xf, v, b, y, invd, omega, fixed, sc);
       break;
     case 2:
-      k_apply_l1<T, 2><<<grid, kThreads, 0, st>>>(d, C, xf, v, b, y, invd, omega, fixed, sc);
+      topo::launch(k_apply_l1<T, 2>, grid, kThreads, 0, st, d, C, xf, v, b, y, invd, omega, fixed, sc);
       break;
     default:
-      k_apply_l1<T, 3><<<grid, kThreads, 0, st>>>(d, C, xf, v, b, y, invd, omega, fixed, sc);
+      topo::launch(k_apply_l1<T, 3>, grid, kThreads, 0, st, d, C, xf, v, b, y, invd, omega, fixed, sc);
   }
   return cudaGetLastError();
 }
@@ -543,9 +553,9 @@ cudaError_t launch_apply_dot_fine(const Dims& d, const double* K0, const double*
                                   unsigned* counters, CgScalars* sc, cudaStream_t st) {
   dim3 grid(blocks_for(d.nodes()), nrhs);
   if (d.dim == 2)
-    k_apply_dot_fine<2><<<grid, kThreads, 0, st>>>(d, K0, x, v, y, fixed, partials, counters, sc);
+    topo::launch(k_apply_dot_fine<2>, grid, kThreads, 0, st, d, K0, x, v, y, fixed, partials, counters, sc);
   else
-    k_apply_dot_fine<3><<<grid, kThreads, 0, st>>>(d, K0, x, v, y, fixed, partials, counters, sc);
+    topo::launch(k_apply_dot_fine<3>, grid, kThreads, 0, st, d, K0, x, v, y, fixed, partials, counters, sc);
   return cudaGetLastError();
 }
 
@@ -555,9 +565,9 @@ cudaError_t launch_restrict(const Dims& fine, const T* rf, T* rc, const uint8_t*
   Dims dc{fine.nx / 2, fine.ny / 2, fine.dim == 3 ? fine.nz / 2 : 1, fine.dim};
   dim3 grid(blocks_for(dc.nodes()), nrhs);
   if (fine.dim == 2)
-    k_restrict<2, T><<<grid, kThreads, 0, st>>>(fine, rf, rc, fixed_c, sc, arrow);
+    topo::launch(k_restrict<2, T>, grid, kThreads, 0, st, fine, rf, rc, fixed_c, sc, arrow);
   else
-    k_restrict<3, T><<<grid, kThreads, 0, st>>>(fine, rf, rc, fixed_c, sc, arrow);
+    topo::launch(k_restrict<3, T>, grid, kThreads, 0, st, fine, rf, rc, fixed_c, sc, arrow);
   return cudaGetLastError();
 }
 template cudaError_t launch_restrict<double>(const Dims&, const double*, double*, const uint8_t*,
@@ -570,9 +580,9 @@ cudaError_t launch_prolong_add(const Dims& fine, const T* zc, T* zf, const uint8
                                int nrhs, const CgScalars* sc, cudaStream_t st, int arrow) {
   dim3 grid(blocks_for(fine.nodes()), nrhs);
   if (fine.dim == 2)
-    k_prolong_add<2, T><<<grid, kThreads, 0, st>>>(fine, zc, zf, fixed_f, sc, arrow);
+    topo::launch(k_prolong_add<2, T>, grid, kThreads, 0, st, fine, zc, zf, fixed_f, sc, arrow);
   else
-    k_prolong_add<3, T><<<grid, kThreads, 0, st>>>(fine, zc, zf, fixed_f, sc, arrow);
+    topo::launch(k_prolong_add<3, T>, grid, kThreads, 0, st, fine, zc, zf, fixed_f, sc, arrow);
   return cudaGetLastError();
 }
 template cudaError_t launch_prolong_add<double>(const Dims&, const double*, double*,
@@ -584,37 +594,37 @@ template cudaError_t launch_prolong_add<float>(const Dims&, const float*, float*
 cudaError_t launch_inv_diag(const Dims& d, const double* K0, const double* x, const double* Ae,
                             const uint8_t* fixed, double* invd, cudaStream_t st) {
   if (d.dim == 2)
-    k_inv_diag<2><<<blocks_for(d.nodes()), kThreads, 0, st>>>(d, K0, x, Ae, fixed, invd);
+    topo::launch(k_inv_diag<2>, blocks_for(d.nodes()), kThreads, 0, st, d, K0, x, Ae, fixed, invd);
   else
-    k_inv_diag<3><<<blocks_for(d.nodes()), kThreads, 0, st>>>(d, K0, x, Ae, fixed, invd);
+    topo::launch(k_inv_diag<3>, blocks_for(d.nodes()), kThreads, 0, st, d, K0, x, Ae, fixed, invd);
   return cudaGetLastError();
 }
 
 cudaError_t launch_element_energy(const Dims& d, const double* K0, const double* u,
                                   const double* lam, double* out, double scale, cudaStream_t st) {
   if (d.dim == 2)
-    k_element_energy<2><<<blocks_for(d.elems()), kThreads, 0, st>>>(d, K0, u, lam, out, scale);
+    topo::launch(k_element_energy<2>, blocks_for(d.elems()), kThreads, 0, st, d, K0, u, lam, out, scale);
   else
-    k_element_energy<3><<<blocks_for(d.elems()), kThreads, 0, st>>>(d, K0, u, lam, out, scale);
+    topo::launch(k_element_energy<3>, blocks_for(d.elems()), kThreads, 0, st, d, K0, u, lam, out, scale);
   return cudaGetLastError();
 }
 
 cudaError_t launch_convert_d2f(const double* a, float* b, long long n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_d2f<<<blocks_for(n), kThreads, 0, st>>>(a, b, n);
+  topo::launch(k_d2f, blocks_for(n), kThreads, 0, st, a, b, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_check_positive(const double* x, long long m, int* flag, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
   if (e != cudaSuccess || m <= 0) return e;
-  k_check_positive<<<blocks_for(m), kThreads, 0, st>>>(x, m, flag);
+  topo::launch(k_check_positive, blocks_for(m), kThreads, 0, st, x, m, flag);
   return cudaGetLastError();
 }
 
 cudaError_t launch_convert_f2d(const float* a, double* b, long long n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_f2d<<<blocks_for(n), kThreads, 0, st>>>(a, b, n);
+  topo::launch(k_f2d, blocks_for(n), kThreads, 0, st, a, b, n);
   return cudaGetLastError();
 }
 

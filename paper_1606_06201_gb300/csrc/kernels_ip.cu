@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(kThreads) k_z_elem(Dims d, const T* __restrict
                                                      double omega, double* partials,
                                                      unsigned* counter, const CgScalars* sc,
                                                      const double* wdev) {
+  pdl_prologue();
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM;
   if (sc && sc[0].done) return;
   const long long m = d.elems();
@@ -167,6 +168,7 @@ __global__ void __launch_bounds__(kThreads) k_z_node(Dims d, const T* __restrict
                                                      const uint8_t* __restrict__ fixed,
                                                      const double* zll, const CgScalars* sc,
                                                      const double* wdev) {
+  pdl_prologue();
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM;
   if (sc && sc[0].done) return;
   const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -230,6 +232,7 @@ __global__ void __launch_bounds__(kThreads) k_arrow_row(long long n, const T* __
                                                         double omega, double* partials,
                                                         unsigned* counter, const CgScalars* sc,
                                                         const double* wdev) {
+  pdl_prologue();
   if (sc && sc[0].done) return;
   if (wdev) omega = *wdev;
   double part[1] = {0.0};
@@ -267,6 +270,7 @@ __global__ void __launch_bounds__(kThreads) k_ip_elem(Dims d, const double* __re
                                                       double* __restrict__ Dinv,
                                                       double* __restrict__ t, double* partials,
                                                       unsigned* counter) {
+  pdl_prologue();
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM;
   const long long m = d.elems();
   const double lam = ip->lam, s = ip->s, r = ip->r, xbar = ip->xbar;
@@ -332,6 +336,7 @@ __global__ void __launch_bounds__(kThreads) k_ip_node(Dims d, const double* __re
                                                       double* __restrict__ w,
                                                       double* __restrict__ invd, IpScalars* ip,
                                                       double* partials, unsigned* counter) {
+  pdl_prologue();
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM;
   const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nodes = d.nodes();
@@ -402,6 +407,7 @@ __global__ void __launch_bounds__(kThreads) k_ip_recover(Dims d, const double* _
                                                          double* __restrict__ dpsi,
                                                          IpScalars* ip, double* partials,
                                                          unsigned* counter) {
+  pdl_prologue();
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM;
   const long long m = d.elems();
   const long long n = d.dofs();
@@ -445,6 +451,7 @@ __global__ void __launch_bounds__(kThreads) k_ip_recover(Dims d, const double* _
 __global__ void k_ip_update_elem(long long m, double* x, double* phi, double* psi,
                                  const double* dx, const double* dphi, const double* dpsi,
                                  IpScalars* ip) {
+  pdl_prologue();
   const double a = ip->alpha;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e == 0) ip->lam += a * ip->dlam;
@@ -455,6 +462,7 @@ __global__ void k_ip_update_elem(long long m, double* x, double* phi, double* ps
 }
 
 __global__ void k_axpy_alpha(long long n, double* u, const double* du, const IpScalars* ip) {
+  pdl_prologue();
   const double a = ip->alpha;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -486,6 +494,7 @@ __global__ void __launch_bounds__(kThreads) k_oc_bisect(long long m, const doubl
                                                         const double* __restrict__ E,
                                                         OcScalars* oc, double* partials,
                                                         unsigned* counter) {
+  pdl_prologue();
   if (oc->hi - oc->lo <= oc->tau) return;
   const double lam = 0.5 * (oc->hi + oc->lo);
   const double xlow = oc->xlow, xbar = oc->xbar;
@@ -532,17 +541,20 @@ __global__ void __launch_bounds__(kThreads) k_oc_bisect(long long m, const doubl
 // x_out = x^NEW(lambda_last); optionally averaged with x_avg (AOC: 1/2 (x1 + x2)).
 __global__ void k_oc_apply(long long m, const double* __restrict__ x, const double* __restrict__ E,
                            const OcScalars* oc, double* __restrict__ xout) {
+  pdl_prologue();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m) return;
   xout[e] = oc_new(x[e], E[e], oc->lam_last, oc->xlow, oc->xbar);
 }
 
 __global__ void k_pow(long long m, double* E, double q) {
+  pdl_prologue();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < m) E[e] = pow(fmax(E[e], 0.0), q);
 }
 
 __global__ void k_average(long long m, const double* a, const double* b, double* out) {
+  pdl_prologue();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < m) out[e] = 0.5 * (a[e] + b[e]);
 }
@@ -565,9 +577,9 @@ cudaError_t launch_z_apply_fine(const Dims& d, int mode, const T* K0, const T* x
 #define TOPO_ZF(DIM, MODE)                                                                      \
   do {                                                                                          \
     if (MODE != 3)                                                                              \
-      k_z_elem<DIM, T, MODE><<<ge, kThreads, 0, st>>>(d, g, Dinv, v, b, y, se, zll, omega,      \
+      topo::launch(k_z_elem<DIM, T, MODE>, ge, kThreads, 0, st, d, g, Dinv, v, b, y, se, zll, omega,      \
                                                       partials, counter, sc, wdev);             \
-    k_z_node<DIM, T, MODE><<<gn, kThreads, 0, st>>>(d, K0, x, g, se, v, b, y, invd, omega,      \
+    topo::launch(k_z_node<DIM, T, MODE>, gn, kThreads, 0, st, d, K0, x, g, se, v, b, y, invd, omega,      \
                                                     fixed, zll, sc, wdev);                      \
   } while (0)
   if (d.dim == 2) {
@@ -607,19 +619,19 @@ cudaError_t launch_arrow_row(long long n, int mode, const T* w, const T* v, cons
   const unsigned gr = red_grid(n);
   switch (mode) {
     case 0:
-      k_arrow_row<T, 0><<<gr, kThreads, 0, st>>>(n, w, v, b, y, zll, omega, partials, counter, sc,
+      topo::launch(k_arrow_row<T, 0>, gr, kThreads, 0, st, n, w, v, b, y, zll, omega, partials, counter, sc,
                                                  wdev);
       break;
     case 1:
-      k_arrow_row<T, 1><<<gr, kThreads, 0, st>>>(n, w, v, b, y, zll, omega, partials, counter, sc,
+      topo::launch(k_arrow_row<T, 1>, gr, kThreads, 0, st, n, w, v, b, y, zll, omega, partials, counter, sc,
                                                  wdev);
       break;
     case 2:
-      k_arrow_row<T, 2><<<gr, kThreads, 0, st>>>(n, w, v, b, y, zll, omega, partials, counter, sc,
+      topo::launch(k_arrow_row<T, 2>, gr, kThreads, 0, st, n, w, v, b, y, zll, omega, partials, counter, sc,
                                                  wdev);
       break;
     default:
-      k_arrow_row<T, 3><<<gr, kThreads, 0, st>>>(n, w, v, b, y, zll, omega, partials, counter, sc,
+      topo::launch(k_arrow_row<T, 3>, gr, kThreads, 0, st, n, w, v, b, y, zll, omega, partials, counter, sc,
                                                  wdev);
   }
   return cudaGetLastError();
@@ -640,19 +652,19 @@ cudaError_t launch_ip_residuals(const Dims& d, const double* K0, const double* u
                                 double* partials, unsigned* counter, cudaStream_t st) {
   const unsigned ge = red_grid(d.elems());
   if (d.dim == 2)
-    k_ip_elem<2><<<ge, kThreads, 0, st>>>(d, K0, u, x, phi, psi, ip, g, tR3, Dinv, t, partials,
+    topo::launch(k_ip_elem<2>, ge, kThreads, 0, st, d, K0, u, x, phi, psi, ip, g, tR3, Dinv, t, partials,
                                           counter);
   else
-    k_ip_elem<3><<<ge, kThreads, 0, st>>>(d, K0, u, x, phi, psi, ip, g, tR3, Dinv, t, partials,
+    topo::launch(k_ip_elem<3>, ge, kThreads, 0, st, d, K0, u, x, phi, psi, ip, g, tR3, Dinv, t, partials,
                                           counter);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const unsigned gn = blocks_for(d.nodes());
   if (d.dim == 2)
-    k_ip_node<2><<<gn, kThreads, 0, st>>>(d, K0, x, u, f, g, t, Dinv, fixed, rhs, w, invd, ip,
+    topo::launch(k_ip_node<2>, gn, kThreads, 0, st, d, K0, x, u, f, g, t, Dinv, fixed, rhs, w, invd, ip,
                                           partials, counter);
   else
-    k_ip_node<3><<<gn, kThreads, 0, st>>>(d, K0, x, u, f, g, t, Dinv, fixed, rhs, w, invd, ip,
+    topo::launch(k_ip_node<3>, gn, kThreads, 0, st, d, K0, x, u, f, g, t, Dinv, fixed, rhs, w, invd, ip,
                                           partials, counter);
   return cudaGetLastError();
 }
@@ -664,16 +676,16 @@ cudaError_t launch_ip_recover_update(const Dims& d, const double* g, const doubl
                                      unsigned* counter, cudaStream_t st) {
   const unsigned ge = red_grid(d.elems());
   if (d.dim == 2)
-    k_ip_recover<2><<<ge, kThreads, 0, st>>>(d, g, du, tR3, Dinv, x, phi, psi, dx, dphi, dpsi, ip,
+    topo::launch(k_ip_recover<2>, ge, kThreads, 0, st, d, g, du, tR3, Dinv, x, phi, psi, dx, dphi, dpsi, ip,
                                              partials, counter);
   else
-    k_ip_recover<3><<<ge, kThreads, 0, st>>>(d, g, du, tR3, Dinv, x, phi, psi, dx, dphi, dpsi, ip,
+    topo::launch(k_ip_recover<3>, ge, kThreads, 0, st, d, g, du, tR3, Dinv, x, phi, psi, dx, dphi, dpsi, ip,
                                              partials, counter);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long m = d.elems(), n = d.dofs();
-  k_ip_update_elem<<<blocks_for(m), kThreads, 0, st>>>(m, x, phi, psi, dx, dphi, dpsi, ip);
-  k_axpy_alpha<<<red_grid(n), kThreads, 0, st>>>(n, u, du, ip);
+  topo::launch(k_ip_update_elem, blocks_for(m), kThreads, 0, st, m, x, phi, psi, dx, dphi, dpsi, ip);
+  topo::launch(k_axpy_alpha, red_grid(n), kThreads, 0, st, n, u, du, ip);
   return cudaGetLastError();
 }
 
@@ -682,22 +694,22 @@ cudaError_t launch_oc_bisection(long long m, const double* x, const double* E, O
                                 cudaStream_t st) {
   const unsigned gr = red_grid(m);
   for (int k = 0; k < steps; ++k) {
-    k_oc_bisect<<<gr, kThreads, 0, st>>>(m, x, E, oc, partials, counter);
+    topo::launch(k_oc_bisect, gr, kThreads, 0, st, m, x, E, oc, partials, counter);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  k_oc_apply<<<blocks_for(m), kThreads, 0, st>>>(m, x, E, oc, xout);
+  topo::launch(k_oc_apply, blocks_for(m), kThreads, 0, st, m, x, E, oc, xout);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pow_inplace(long long m, double* E, double q, cudaStream_t st) {
-  k_pow<<<blocks_for(m), kThreads, 0, st>>>(m, E, q);
+  topo::launch(k_pow, blocks_for(m), kThreads, 0, st, m, E, q);
   return cudaGetLastError();
 }
 
 cudaError_t launch_average(long long m, const double* a, const double* b, double* out,
                            cudaStream_t st) {
-  k_average<<<blocks_for(m), kThreads, 0, st>>>(m, a, b, out);
+  topo::launch(k_average, blocks_for(m), kThreads, 0, st, m, a, b, out);
   return cudaGetLastError();
 }
 

@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(long long n, const double*
                                                       const double* __restrict__ Az, int use_x0,
                                                       double* partials, unsigned* counters,
                                                       CgScalars* sc, double tol, int max_iter) {
+  pdl_prologue();
   const int rhs = blockIdx.y;
   b += rhs * n;
   z += rhs * n;
@@ -117,6 +118,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_start_p(long long n, const doub
                                                          TV* __restrict__ y_old, int flexible,
                                                          double* partials, unsigned* counters,
                                                          CgScalars* sc) {
+  pdl_prologue();
   const int rhs = blockIdx.y;
   if (sc[rhs].done) return;
   r += rhs * n;
@@ -151,6 +153,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(long long n, double* __r
                                                         TV* __restrict__ rv, double* partials,
                                                         unsigned* counters, CgScalars* sc,
                                                         double tol, int max_iter) {
+  pdl_prologue();
   const int rhs = blockIdx.y;
   if (sc[rhs].done) return;
   const double alpha = sc[rhs].alpha;
@@ -194,6 +197,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_beta(long long n, const double*
                                                       const TV* __restrict__ y_old, int flexible,
                                                       double* partials, unsigned* counters,
                                                       CgScalars* sc) {
+  pdl_prologue();
   const int rhs = blockIdx.y;
   if (sc[rhs].done) return;
   r += rhs * n;
@@ -228,6 +232,7 @@ template <typename TV>
 __global__ void __launch_bounds__(kThreads) k_cg_p(long long n, const TV* __restrict__ y,
                                                    double* __restrict__ p, TV* __restrict__ y_old,
                                                    int flexible, const CgScalars* sc) {
+  pdl_prologue();
   const int rhs = blockIdx.y;
   if (sc[rhs].done) return;
   const double beta = sc[rhs].beta;
@@ -245,6 +250,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_p(long long n, const TV* __rest
 __global__ void __launch_bounds__(kThreads) k_dot(long long n, const double* __restrict__ a,
                                                   const double* __restrict__ b, double* partials,
                                                   unsigned* counters, double* out) {
+  pdl_prologue();
   const int rhs = blockIdx.y;
   a += rhs * n;
   b += rhs * n;
@@ -261,6 +267,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_alpha(long long n, const double
                                                        const double* __restrict__ q,
                                                        double* partials, unsigned* counters,
                                                        CgScalars* sc) {
+  pdl_prologue();
   const int rhs = blockIdx.y;
   if (sc[rhs].done) return;
   p += rhs * n;
@@ -289,6 +296,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_alpha(long long n, const double
 // lambda entry of an IP system, are copied unchanged).
 __global__ void k_mask_copy(long long n, long long n_mask, const double* __restrict__ src,
                             double* __restrict__ dst, const uint8_t* __restrict__ fixed) {
+  pdl_prologue();
   const int rhs = blockIdx.y;
   src += rhs * n;
   dst += rhs * n;
@@ -300,6 +308,7 @@ __global__ void k_mask_copy(long long n, long long n_mask, const double* __restr
 // ---- largest eigenvalue of D^{-1} A by power iteration (per-level Jacobi damping) ----------
 // v0: a fixed pseudo-random vector (integer hash of the index), zero on fixed DOFs.
 __global__ void k_power_init(long long n, int arrow, double* v, const uint8_t* fixed) {
+  pdl_prologue();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
     unsigned h = (unsigned)(i * 2654435761ull) ^ 0x9e3779b9u;
@@ -320,6 +329,7 @@ __global__ void __launch_bounds__(kThreads) k_power_step(long long n, int arrow,
                                                          const double* zll, double* __restrict__ w,
                                                          double* partials, unsigned* counters,
                                                          double* est) {
+  pdl_prologue();
   double part[3] = {0.0, 0.0, 0.0};
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -347,6 +357,7 @@ __global__ void __launch_bounds__(kThreads) k_power_step(long long n, int arrow,
 
 __global__ void k_power_scale(long long n, const double* __restrict__ w, double* __restrict__ v,
                               const double* est) {
+  pdl_prologue();
   const double sc = est[1];
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -356,6 +367,7 @@ __global__ void k_power_scale(long long n, const double* __restrict__ w, double*
 // omega_k = min(omega, c / (1.05 lambda)); invd <- omega_k invd.
 __global__ void k_power_finish(long long n, const double* est, double omega, double c,
                                double* omega_dev, double* invd) {
+  pdl_prologue();
   const double lam = est[0];
   const double om = lam > 0.0 ? fmin(omega, c / (1.05 * lam)) : omega;
   if (blockIdx.x == 0 && threadIdx.x == 0) *omega_dev = om;
@@ -374,7 +386,7 @@ inline unsigned red_blocks(long long n) {
 cudaError_t launch_cg_init(long long n, int nrhs, const double* b, double* z, double* r,
                            const double* Az, int use_x0, double* partials, unsigned* counters,
                            CgScalars* sc, double tol, int max_iter, cudaStream_t st) {
-  k_cg_init<<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, b, z, r, Az, use_x0, partials,
+  topo::launch(k_cg_init, dim3(red_blocks(n), nrhs), kThreads, 0, st, n, b, z, r, Az, use_x0, partials,
                                                             counters, sc, tol, max_iter);
   return cudaGetLastError();
 }
@@ -383,7 +395,7 @@ template <typename TV>
 cudaError_t launch_cg_start_p(long long n, int nrhs, const double* r, const TV* y, double* p,
                               TV* y_old, int flexible, double* partials, unsigned* counters,
                               CgScalars* sc, cudaStream_t st) {
-  k_cg_start_p<TV><<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, r, y, p, y_old, flexible,
+  topo::launch(k_cg_start_p<TV>, dim3(red_blocks(n), nrhs), kThreads, 0, st, n, r, y, p, y_old, flexible,
                                                                    partials, counters, sc);
   return cudaGetLastError();
 }
@@ -392,7 +404,7 @@ template <typename TV>
 cudaError_t launch_cg_update(long long n, int nrhs, double* z, double* r, const double* p,
                              const double* q, TV* rv, double* partials, unsigned* counters,
                              CgScalars* sc, double tol, int max_iter, cudaStream_t st) {
-  k_cg_update<TV><<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, z, r, p, q, rv, partials,
+  topo::launch(k_cg_update<TV>, dim3(red_blocks(n), nrhs), kThreads, 0, st, n, z, r, p, q, rv, partials,
                                                                   counters, sc, tol, max_iter);
   return cudaGetLastError();
 }
@@ -401,53 +413,53 @@ template <typename TV>
 cudaError_t launch_cg_direction(long long n, int nrhs, const double* r, const TV* y, double* p,
                                 TV* y_old, int flexible, double* partials, unsigned* counters,
                                 CgScalars* sc, cudaStream_t st) {
-  k_cg_beta<TV><<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, r, y, y_old, flexible,
+  topo::launch(k_cg_beta<TV>, dim3(red_blocks(n), nrhs), kThreads, 0, st, n, r, y, y_old, flexible,
                                                                 partials, counters, sc);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_cg_p<TV><<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, y, p, y_old, flexible, sc);
+  topo::launch(k_cg_p<TV>, dim3(red_blocks(n), nrhs), kThreads, 0, st, n, y, p, y_old, flexible, sc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_power_init(long long n, int arrow, double* v, const uint8_t* fixed,
                               cudaStream_t st) {
-  k_power_init<<<blocks_for(n), kThreads, 0, st>>>(n, arrow, v, fixed);
+  topo::launch(k_power_init, blocks_for(n), kThreads, 0, st, n, arrow, v, fixed);
   return cudaGetLastError();
 }
 
 cudaError_t launch_power_step(long long n, int arrow, const double* v, const double* y,
                               const double* invd, const double* zll, double* w, double* partials,
                               unsigned* counters, double* est, cudaStream_t st) {
-  k_power_step<<<red_blocks(n), kThreads, 0, st>>>(n, arrow, v, y, invd, zll, w, partials,
+  topo::launch(k_power_step, red_blocks(n), kThreads, 0, st, n, arrow, v, y, invd, zll, w, partials,
                                                    counters, est);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_power_scale<<<red_blocks(n + arrow), kThreads, 0, st>>>(n + arrow, w, (double*)v, est);
+  topo::launch(k_power_scale, red_blocks(n + arrow), kThreads, 0, st, n + arrow, w, (double*)v, est);
   return cudaGetLastError();
 }
 
 cudaError_t launch_power_finish(long long n, const double* est, double omega, double c,
                                 double* omega_dev, double* invd, cudaStream_t st) {
-  k_power_finish<<<red_blocks(n), kThreads, 0, st>>>(n, est, omega, c, omega_dev, invd);
+  topo::launch(k_power_finish, red_blocks(n), kThreads, 0, st, n, est, omega, c, omega_dev, invd);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mask_copy(long long n, long long n_mask, int nrhs, const double* src,
                              double* dst, const uint8_t* fixed, cudaStream_t st) {
-  k_mask_copy<<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, n_mask, src, dst, fixed);
+  topo::launch(k_mask_copy, dim3(red_blocks(n), nrhs), kThreads, 0, st, n, n_mask, src, dst, fixed);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_alpha(long long n, int nrhs, const double* p, const double* q,
                             double* partials, unsigned* counters, CgScalars* sc, cudaStream_t st) {
-  k_cg_alpha<<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, p, q, partials, counters, sc);
+  topo::launch(k_cg_alpha, dim3(red_blocks(n), nrhs), kThreads, 0, st, n, p, q, partials, counters, sc);
   return cudaGetLastError();
 }
 
 template <typename TV>
 cudaError_t launch_cg_p(long long n, int nrhs, const TV* y, double* p, TV* y_old, int flexible,
                         CgScalars* sc, cudaStream_t st) {
-  k_cg_p<TV><<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, y, p, y_old, flexible, sc);
+  topo::launch(k_cg_p<TV>, dim3(red_blocks(n), nrhs), kThreads, 0, st, n, y, p, y_old, flexible, sc);
   return cudaGetLastError();
 }
 template cudaError_t launch_cg_p<double>(long long, int, const double*, double*, double*, int,
@@ -457,7 +469,7 @@ template cudaError_t launch_cg_p<float>(long long, int, const float*, double*, f
 
 cudaError_t launch_dot(long long n, int nrhs, const double* a, const double* b, double* partials,
                        unsigned* counters, double* out, cudaStream_t st) {
-  k_dot<<<dim3(red_blocks(n), nrhs), kThreads, 0, st>>>(n, a, b, partials, counters, out);
+  topo::launch(k_dot, dim3(red_blocks(n), nrhs), kThreads, 0, st, n, a, b, partials, counters, out);
   return cudaGetLastError();
 }
 

@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, int 
                                                              CgScalars* sc, double* partials,
                                                              unsigned* counters,
                                                              const double* __restrict__ rdot) {
+  pdl_prologue();
   using V2 = typename Vec2<T>::type;
   const int rhs = blockIdx.y;
   if (sc && sc[rhs].done) return;
@@ -268,6 +269,7 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, int
                                                               const float* __restrict__ invd,
                                                               const uint8_t* __restrict__ fixed,
                                                               const CgScalars* sc) {
+  pdl_prologue();
   const int rhs = blockIdx.y;
   if (sc && sc[rhs].done) return;
   const long long n = 2LL * (nx + 1) * (ny + 1);
@@ -410,19 +412,19 @@ cudaError_t launch_q1_apply(int nx, int ny, int mode, const Q1Coef& coef, const 
   CgScalars* scm = const_cast<CgScalars*>(sc);
   switch (mode) {
     case 0:
-      k_q1_sweep<T, 0, 0><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, q1_rows(nx, ny), k, x, v, b, y, omega, fixed,
+      topo::launch(k_q1_sweep<T, 0, 0>, grid, kQ1Warps * 32, 0, st, nx, ny, q1_rows(nx, ny), k, x, v, b, y, omega, fixed,
                                                                scm, nullptr, nullptr, nullptr);
       break;
     case 1:
-      k_q1_sweep<T, 1, 0><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, q1_rows(nx, ny), k, x, v, b, y, omega, fixed,
+      topo::launch(k_q1_sweep<T, 1, 0>, grid, kQ1Warps * 32, 0, st, nx, ny, q1_rows(nx, ny), k, x, v, b, y, omega, fixed,
                                                                scm, nullptr, nullptr, nullptr);
       break;
     case 2:
-      k_q1_sweep<T, 2, 0><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, q1_rows(nx, ny), k, x, v, b, y, omega, fixed,
+      topo::launch(k_q1_sweep<T, 2, 0>, grid, kQ1Warps * 32, 0, st, nx, ny, q1_rows(nx, ny), k, x, v, b, y, omega, fixed,
                                                                scm, nullptr, nullptr, nullptr);
       break;
     default:
-      k_q1_sweep<T, 3, 0><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, q1_rows(nx, ny), k, x, v, b, y, omega, fixed,
+      topo::launch(k_q1_sweep<T, 3, 0>, grid, kQ1Warps * 32, 0, st, nx, ny, q1_rows(nx, ny), k, x, v, b, y, omega, fixed,
                                                                scm, nullptr, nullptr, nullptr);
   }
   return cudaGetLastError();
@@ -442,16 +444,16 @@ cudaError_t launch_q1g_apply(int nx, int ny, int mode, const Q1Coef& coef, const
   const Q1K<float> k = coef_cast<float>(coef);
   switch (mode) {
     case 0:
-      k_q1g_sweep<0><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, q1_rows(nx, ny), k, xf, v, b, y, omega, invd, fixed, sc);
+      topo::launch(k_q1g_sweep<0>, grid, kQ1Warps * 32, 0, st, nx, ny, q1_rows(nx, ny), k, xf, v, b, y, omega, invd, fixed, sc);
       break;
     case 1:
-      k_q1g_sweep<1><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, q1_rows(nx, ny), k, xf, v, b, y, omega, invd, fixed, sc);
+      topo::launch(k_q1g_sweep<1>, grid, kQ1Warps * 32, 0, st, nx, ny, q1_rows(nx, ny), k, xf, v, b, y, omega, invd, fixed, sc);
       break;
     case 2:
-      k_q1g_sweep<2><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, q1_rows(nx, ny), k, xf, v, b, y, omega, invd, fixed, sc);
+      topo::launch(k_q1g_sweep<2>, grid, kQ1Warps * 32, 0, st, nx, ny, q1_rows(nx, ny), k, xf, v, b, y, omega, invd, fixed, sc);
       break;
     default:
-      k_q1g_sweep<3><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, q1_rows(nx, ny), k, xf, v, b, y, omega, invd, fixed, sc);
+      topo::launch(k_q1g_sweep<3>, grid, kQ1Warps * 32, 0, st, nx, ny, q1_rows(nx, ny), k, xf, v, b, y, omega, invd, fixed, sc);
   }
   return cudaGetLastError();
 }
@@ -462,7 +464,7 @@ cudaError_t launch_q1_smooth_beta(int nx, int ny, const Q1Coef& coef, const T* x
                                   const double* r, double* partials, unsigned* counters,
                                   CgScalars* sc, cudaStream_t st) {
   dim3 grid(q1_blocks(nx, ny), nrhs);
-  k_q1_sweep<T, 2, 2><<<grid, kQ1Warps * 32, 0, st>>>(nx, ny, q1_rows(nx, ny), coef_cast<T>(coef),
+  topo::launch(k_q1_sweep<T, 2, 2>, grid, kQ1Warps * 32, 0, st, nx, ny, q1_rows(nx, ny), coef_cast<T>(coef),
                                                       x, v, b, y, omega, fixed, sc, partials,
                                                       counters, r);
   return cudaGetLastError();
@@ -481,7 +483,7 @@ cudaError_t launch_q1_apply_dot(int nx, int ny, const Q1Coef& coef, const double
                                 double* partials, unsigned* counters, CgScalars* sc,
                                 cudaStream_t st) {
   dim3 grid(q1_blocks(nx, ny), nrhs);
-  k_q1_sweep<double, 0, 1><<<grid, kQ1Warps * 32, 0, st>>>(
+  topo::launch(k_q1_sweep<double, 0, 1>, grid, kQ1Warps * 32, 0, st, 
       nx, ny, q1_rows(nx, ny), coef_cast<double>(coef), x, v, nullptr, y, 0.0, fixed, sc, partials,
       counters, nullptr);
   return cudaGetLastError();

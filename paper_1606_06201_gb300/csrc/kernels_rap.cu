@@ -43,6 +43,7 @@ template <int DIM>
 __global__ void k_rap_from_fine(Dims df, const double* __restrict__ C,
                                 const double* __restrict__ x, double* __restrict__ Ac,
                                 const double* __restrict__ g, const double* __restrict__ Dinv) {
+  pdl_prologue();
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM, NE2 = NE * NE;
   const int cnx = df.nx / 2, cny = df.ny / 2, cnz = DIM == 3 ? df.nz / 2 : 1;
   const long long mc = (long long)cnx * cny * cnz;
@@ -77,6 +78,7 @@ __global__ void k_rap_from_fine(Dims df, const double* __restrict__ C,
 template <int DIM>
 __global__ void k_rap2_from_fine(Dims df, const double* __restrict__ C2,
                                  const double* __restrict__ x, double* __restrict__ Ac) {
+  pdl_prologue();
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM, NE2 = NE * NE, NF = NN * NN;
   const int cnx = df.nx / 4, cny = df.ny / 4, cnz = DIM == 3 ? df.nz / 4 : 1;
   const long long mc = (long long)cnx * cny * cnz;
@@ -103,6 +105,7 @@ __global__ void k_rap2_from_fine(Dims df, const double* __restrict__ C2,
 template <int DIM>
 __global__ void k_inv_diag_l1(Dims dc, const double* __restrict__ C, const double* __restrict__ xf,
                               const uint8_t* __restrict__ fixed, double* __restrict__ invd) {
+  pdl_prologue();
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM, NE2 = NE * NE;
   const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= dc.nodes()) return;
@@ -139,6 +142,7 @@ __global__ void k_inv_diag_l1(Dims dc, const double* __restrict__ C, const doubl
 // (exact binary fractions) and their zeros skipped.
 template <int DIM>
 __global__ void k_rap_coarse(Dims df, const double* __restrict__ Af, double* __restrict__ Ac) {
+  pdl_prologue();
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM, NE2 = NE * NE;
   __shared__ float W[NN][NN][NN];  // [child][fine local node a][coarse local node A]
   for (int idx = threadIdx.x; idx < NN * NN * NN; idx += blockDim.x) {
@@ -184,6 +188,7 @@ __global__ void k_assemble_dense(Dims d, const double* __restrict__ K0,
                                  long long ld, const double* __restrict__ w,
                                  const double* __restrict__ zll, const double* __restrict__ g,
                                  const double* __restrict__ Dinv) {
+  pdl_prologue();
   constexpr int NE = (DIM == 2 ? 4 : 8) * DIM;
   const long long n = d.dofs();
   const long long na = w ? n + 1 : n;
@@ -225,17 +230,26 @@ __global__ void k_assemble_dense(Dims d, const double* __restrict__ K0,
   *out = acc;
 }
 
+// Pivots that rounding has pushed to or below kPivotFloor times the original diagonal entry are
+// raised to that floor (a modified Cholesky): the coarsest solve stays an SPD preconditioner when
+// the Schur complement of the IP multiplier cancels to rounding level in late interior-point steps.
+constexpr double kPivotFloor = 1e-13;
+
 // In-place Cholesky A = L L^T of a dense SPD matrix in one block (right-looking), then L^T is
-// mirrored into the strict upper triangle.  info = 0, or k+1 if the k-th pivot is not positive.
-__global__ void __launch_bounds__(1024) k_cholesky(int n, double* A, int* info) {
+// mirrored into the strict upper triangle.  info = 0, or k+1 if the k-th diagonal entry is not
+// positive or a pivot is not finite.
+__global__ void __launch_bounds__(1024) k_cholesky(int n, double* A, double* diag0, int* info) {
+  pdl_prologue();
   __shared__ int bad;
   if (threadIdx.x == 0) bad = 0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) diag0[k] = A[(long long)k * n + k];
   __syncthreads();
   for (int k = 0; k < n; ++k) {
     if (threadIdx.x == 0) {
-      const double akk = A[(long long)k * n + k];
-      if (!(akk > 0.0) || !isfinite(akk)) bad = k + 1;
-      else A[(long long)k * n + k] = sqrt(akk);
+      double akk = A[(long long)k * n + k];
+      const double a0 = diag0[k];
+      if (!(a0 > 0.0) || !isfinite(akk)) bad = k + 1;
+      else A[(long long)k * n + k] = sqrt(fmax(akk, kPivotFloor * a0));
     }
     __syncthreads();
     if (bad) break;
@@ -269,6 +283,7 @@ inline int inv_warps(int n) {
 
 __global__ void __launch_bounds__(kInvWarps * 32) k_chol_inverse(int n, const double* __restrict__ LU,
                                                                  double* Ainv, const int* info) {
+  pdl_prologue();
   extern __shared__ double wsh[];  // [warps per block][n]
   if (*info) return;
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -299,75 +314,23 @@ __global__ void __launch_bounds__(kInvWarps * 32) k_chol_inverse(int n, const do
   for (int k = lane; k < n; k += 32) out[k] = w[k];
 }
 
-// Cholesky and inverse in one block with everything in shared memory (small n): the factor, then
-// one warp per column j of A^{-1} (forward and backward substitution against e_j).
-__global__ void __launch_bounds__(1024) k_cholinv_smem(int n, double* A, double* Ainv, int* info) {
-  extern __shared__ double S[];   // [n][n] factor, then [32][n] work rows
-  __shared__ int bad;
-  const long long nn = (long long)n * n;
-  double* W = S + nn;
-  for (long long t = threadIdx.x; t < nn; t += blockDim.x) S[t] = A[t];
-  if (threadIdx.x == 0) bad = 0;
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) {
-      const double akk = S[k * n + k];
-      if (!(akk > 0.0) || !isfinite(akk)) bad = k + 1;
-      else S[k * n + k] = sqrt(akk);
-    }
-    __syncthreads();
-    if (bad) break;
-    const double rkk = 1.0 / S[k * n + k];
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) S[i * n + k] *= rkk;
-    __syncthreads();
-    for (int i = k + 1 + warp; i < n; i += nw) {
-      const double lik = S[i * n + k];
-      for (int jj = k + 1 + lane; jj <= i; jj += 32) S[i * n + jj] -= lik * S[jj * n + k];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *info = bad;
-  if (bad) return;
-  double* w = W + (long long)warp * n;
-  for (int j = warp; j < n; j += nw) {
-    for (int k = lane; k < n; k += 32) w[k] = 0.0;
-    __syncwarp();
-    for (int i = j; i < n; ++i) {  // L w = e_j
-      double t = 0.0;
-      for (int k = j + lane; k < i; k += 32) t = fma(S[i * n + k], w[k], t);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) w[i] = ((i == j ? 1.0 : 0.0) - t) / S[i * n + i];
-      __syncwarp();
-    }
-    for (int i = n - 1; i >= 0; --i) {  // L^T w = y (column i of L below the diagonal)
-      double t = 0.0;
-      for (int k = i + 1 + lane; k < n; k += 32) t = fma(S[k * n + i], w[k], t);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) w[i] = (w[i] - t) / S[i * n + i];
-      __syncwarp();
-    }
-    for (int k = lane; k < n; k += 32) Ainv[(long long)j * n + k] = w[k];
-    __syncwarp();
-  }
-}
-
 // Cholesky in shared memory for small n (n * n doubles fit in one block's shared memory).
-__global__ void __launch_bounds__(1024) k_cholesky_smem(int n, double* A, int* info) {
+__global__ void __launch_bounds__(1024) k_cholesky_smem(int n, double* A, double* diag0, int* info) {
+  pdl_prologue();
   extern __shared__ double S[];
   __shared__ int bad;
   const long long nn = (long long)n * n;
   for (long long t = threadIdx.x; t < nn; t += blockDim.x) S[t] = A[t];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) diag0[k] = A[(long long)k * n + k];
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int k = 0; k < n; ++k) {
     if (threadIdx.x == 0) {
       const double akk = S[k * n + k];
-      if (!(akk > 0.0) || !isfinite(akk)) bad = k + 1;
-      else S[k * n + k] = sqrt(akk);
+      const double a0 = diag0[k];
+      if (!(a0 > 0.0) || !isfinite(akk)) bad = k + 1;
+      else S[k * n + k] = sqrt(fmax(akk, kPivotFloor * a0));
     }
     __syncthreads();
     if (bad) break;
@@ -392,6 +355,7 @@ __global__ void __launch_bounds__(1024) k_cholesky_smem(int n, double* A, int* i
 template <typename T>
 __global__ void k_dense_solve(int n, const double* __restrict__ Ainv, const T* __restrict__ b,
                               T* __restrict__ z, const CgScalars* __restrict__ sc) {
+  pdl_prologue();
   const int rhs = blockIdx.y;
   if (sc && sc[rhs].done) return;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -415,9 +379,9 @@ cudaError_t launch_rap_from_fine(const Dims& fine, const double* C, const double
   const long long mc = fine.elems() / (fine.dim == 2 ? 4 : 8);
   const long long total = mc * ne * ne;
   if (fine.dim == 2)
-    k_rap_from_fine<2><<<blocks_for(total), kThreads, 0, st>>>(fine, C, x, Ac, g, Dinv);
+    topo::launch(k_rap_from_fine<2>, blocks_for(total), kThreads, 0, st, fine, C, x, Ac, g, Dinv);
   else
-    k_rap_from_fine<3><<<blocks_for(total), kThreads, 0, st>>>(fine, C, x, Ac, g, Dinv);
+    topo::launch(k_rap_from_fine<3>, blocks_for(total), kThreads, 0, st, fine, C, x, Ac, g, Dinv);
   return cudaGetLastError();
 }
 
@@ -427,18 +391,18 @@ cudaError_t launch_rap2_from_fine(const Dims& fine, const double* C2, const doub
   const long long mc = fine.elems() / (fine.dim == 2 ? 16 : 64);
   const long long total = mc * ne * ne;
   if (fine.dim == 2)
-    k_rap2_from_fine<2><<<blocks_for(total), kThreads, 0, st>>>(fine, C2, x, Ac);
+    topo::launch(k_rap2_from_fine<2>, blocks_for(total), kThreads, 0, st, fine, C2, x, Ac);
   else
-    k_rap2_from_fine<3><<<blocks_for(total), kThreads, 0, st>>>(fine, C2, x, Ac);
+    topo::launch(k_rap2_from_fine<3>, blocks_for(total), kThreads, 0, st, fine, C2, x, Ac);
   return cudaGetLastError();
 }
 
 cudaError_t launch_inv_diag_l1(const Dims& coarse1, const double* C, const double* xf,
                                const uint8_t* fixed, double* invd, cudaStream_t st) {
   if (coarse1.dim == 2)
-    k_inv_diag_l1<2><<<blocks_for(coarse1.nodes()), kThreads, 0, st>>>(coarse1, C, xf, fixed, invd);
+    topo::launch(k_inv_diag_l1<2>, blocks_for(coarse1.nodes()), kThreads, 0, st, coarse1, C, xf, fixed, invd);
   else
-    k_inv_diag_l1<3><<<blocks_for(coarse1.nodes()), kThreads, 0, st>>>(coarse1, C, xf, fixed, invd);
+    topo::launch(k_inv_diag_l1<3>, blocks_for(coarse1.nodes()), kThreads, 0, st, coarse1, C, xf, fixed, invd);
   return cudaGetLastError();
 }
 
@@ -447,9 +411,9 @@ cudaError_t launch_rap_coarse(const Dims& fine, const double* Af, double* Ac, cu
   const long long mc = fine.elems() / (fine.dim == 2 ? 4 : 8);
   const long long total = mc * ne * ne;
   if (fine.dim == 2)
-    k_rap_coarse<2><<<blocks_for(total), kThreads, 0, st>>>(fine, Af, Ac);
+    topo::launch(k_rap_coarse<2>, blocks_for(total), kThreads, 0, st, fine, Af, Ac);
   else
-    k_rap_coarse<3><<<blocks_for(total), kThreads, 0, st>>>(fine, Af, Ac);
+    topo::launch(k_rap_coarse<3>, blocks_for(total), kThreads, 0, st, fine, Af, Ac);
   return cudaGetLastError();
 }
 
@@ -461,22 +425,15 @@ cudaError_t launch_assemble_dense(const Dims& d, const double* K0, const double*
   const long long na = w ? n + 1 : n;
   if (ld <= 0) ld = na;
   if (d.dim == 2)
-    k_assemble_dense<2><<<blocks_for(na * na), kThreads, 0, st>>>(d, K0, x, Ae, fixed, A, ld, w,
+    topo::launch(k_assemble_dense<2>, blocks_for(na * na), kThreads, 0, st, d, K0, x, Ae, fixed, A, ld, w,
                                                                   zll, g, Dinv);
   else
-    k_assemble_dense<3><<<blocks_for(na * na), kThreads, 0, st>>>(d, K0, x, Ae, fixed, A, ld, w,
+    topo::launch(k_assemble_dense<3>, blocks_for(na * na), kThreads, 0, st, d, K0, x, Ae, fixed, A, ld, w,
                                                                   zll, g, Dinv);
   return cudaGetLastError();
 }
 
-inline size_t cholinv_smem_bytes(int n) { return ((size_t)n * n + 32 * (size_t)n) * sizeof(double); }
-
 cudaError_t prepare_coarse_kernels(int n) {
-  if (cholinv_smem_bytes(n) <= 200 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_cholinv_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024);
-    if (e != cudaSuccess) return e;
-  }
   const size_t smem = (size_t)n * n * sizeof(double);
   if (smem <= 200 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_cholesky_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -488,20 +445,17 @@ cudaError_t prepare_coarse_kernels(int n) {
 }
 
 cudaError_t launch_cholesky_inverse(int n, double* A, double* Ainv, int* info, cudaStream_t st) {
-  if (cholinv_smem_bytes(n) <= 200 * 1024) {
-    k_cholinv_smem<<<1, 1024, cholinv_smem_bytes(n), st>>>(n, A, Ainv, info);
-    return cudaGetLastError();
-  }
   const size_t smem = (size_t)n * n * sizeof(double);
+  // row 0 of Ainv holds the original diagonal until the inverse overwrites it
   if (smem <= 200 * 1024)
-    k_cholesky_smem<<<1, 1024, smem, st>>>(n, A, info);
+    topo::launch(k_cholesky_smem, 1, 1024, smem, st, n, A, Ainv, info);
   else
-    k_cholesky<<<1, 1024, 0, st>>>(n, A, info);
+    topo::launch(k_cholesky, 1, 1024, 0, st, n, A, Ainv, info);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int wpb = inv_warps(n);
   const size_t wsm = (size_t)wpb * n * sizeof(double);
-  k_chol_inverse<<<(n + wpb - 1) / wpb, wpb * 32, wsm, st>>>(n, A, Ainv, info);
+  topo::launch(k_chol_inverse, (n + wpb - 1) / wpb, wpb * 32, wsm, st, n, A, Ainv, info);
   return cudaGetLastError();
 }
 
@@ -509,7 +463,7 @@ template <typename T>
 cudaError_t launch_dense_solve(int n, const double* Ainv, const T* b, T* z, int nrhs,
                                const CgScalars* sc, cudaStream_t st) {
   dim3 grid(blocks_for((long long)n * 32), nrhs);
-  k_dense_solve<T><<<grid, kThreads, 0, st>>>(n, Ainv, b, z, sc);
+  topo::launch(k_dense_solve<T>, grid, kThreads, 0, st, n, Ainv, b, z, sc);
   return cudaGetLastError();
 }
 template cudaError_t launch_dense_solve<double>(int, const double*, const double*, double*, int,

@@ -9,6 +9,7 @@
 // right-hand side whose recurrence has stopped return at once, so the host replays the graph and
 // reads the scalars back once per block.
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
@@ -24,6 +25,15 @@ namespace topo {
 thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+// TOPO_NO_PDL=1 in the environment launches without programmatic dependent launch.
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("TOPO_NO_PDL");
+    return !(v && v[0] == '1');
+  }();
+  return on;
+}
 
 topo_status cuda_status(cudaError_t e, const char* what) {
   set_error(std::string(what) + ": " + cudaGetErrorString(e));

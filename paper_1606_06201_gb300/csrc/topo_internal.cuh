@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/topo.h"
@@ -103,6 +104,33 @@ topo_status cuda_status(cudaError_t e, const char* what);
     cudaError_t _e = cudaGetLastError();                        \
     if (_e != cudaSuccess) return topo::cuda_status(_e, what);  \
   } while (0)
+
+// Programmatic dependent launch: every kernel waits for its stream predecessor's completion before
+// touching memory (griddepcontrol.wait) and at once lets its own successor start launching, so
+// consecutive kernels of a CUDA graph overlap launch latency with execution.  Without the launch
+// attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_prologue() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+bool pdl_enabled();
+
+template <typename... KArgs, typename... Args>
+inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                   Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 inline unsigned blocks_for(long long n, int threads = kThreads) {
   return (unsigned)((n + threads - 1) / threads);
