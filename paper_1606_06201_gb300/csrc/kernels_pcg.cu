@@ -35,6 +35,7 @@ __device__ __forceinline__ double block_sum(double v) {
 template <int NV>
 __device__ bool last_block_sums(const double (&part)[NV], double* partials, unsigned* counters,
                                 int rhs, double (&tot)[NV]) {
+  static_assert(NV <= kMaxRedValues, "partials buffers hold kMaxRedValues values per block");
   __shared__ bool last;
   __shared__ double res[NV];
   double bs[NV];

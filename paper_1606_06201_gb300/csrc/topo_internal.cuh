@@ -16,6 +16,7 @@ namespace topo {
 
 constexpr int kThreads = 256;         // threads per block of the node-parallel kernels
 constexpr int kRedBlocks = 4 * 152;   // blocks of the grid-stride reduction kernels (4 per SM)
+constexpr int kMaxRedValues = 4;      // most values one fixed-grid reduction writes per block
 constexpr int kMaxRhs = 64;
 
 // Dimensions of one grid level.
@@ -105,10 +106,9 @@ topo_status cuda_status(cudaError_t e, const char* what);
     if (_e != cudaSuccess) return topo::cuda_status(_e, what);  \
   } while (0)
 
-// Programmatic dependent launch: every kernel waits for its stream predecessor's completion before
-// touching memory (griddepcontrol.wait) and at once lets its own successor start launching, so
-// consecutive kernels of a CUDA graph overlap launch latency with execution.  Without the launch
-// attribute both instructions are no-ops.
+// Programmatic dependent launch (optional, TOPO_PDL=1): every kernel waits for its stream
+// predecessor's completion before touching memory (griddepcontrol.wait) and at once lets its own
+// successor start launching.  Without the launch attribute both instructions are no-ops.
 __device__ __forceinline__ void pdl_prologue() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");

@@ -138,3 +138,27 @@ def test_oc_run_stops_on_compliance_change():
     assert abs(x.sum() - cfg["V"]) <= 1e-6 * cfg["V"] and x.min() >= 1e-6 and x.max() <= 1.0
     _, oinfo = ooc.oc_run(prob, variant="aoc", tau_oc=1e-5, xlow=1e-6)
     assert info.iters == oinfo["iters"]
+
+
+def test_ip_512x256_scalars_stay_consistent():
+    """Example-2 shape 428 (512 x 256, 6 levels): large enough that every fixed-grid reduction runs
+    its full grid.  After a few Newton steps the barrier parameters are exact powers of 0.2, lambda
+    is finite and the volume constraint holds to the solve tolerance."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    cfg = W.cantilever_2d(512, 256, 0.4)
+    for prec in (topo.FP64, topo.MIXED):
+        ip = topo.IP(512, 256, fixed=cfg["fixed"], f=dev(torch, cfg["f"]), V=cfg["V"], xbar=1.0,
+                     levels=6, precision=prec, max_iter=1000)
+        opts = topo.ip_options(cg_tol=1e-8)
+        ip.init(opts)
+        for _ in range(4):
+            info = ip.step(opts)
+            u, x, phi, psi, scal = ip.state()
+            assert scal[1] == 0.2 ** info.ip_iters and scal[2] == 0.2 ** info.ip_iters
+            assert np.isfinite(scal[0]) and abs(scal[0]) < 10.0
+            xh = host(x)
+            assert xh.min() > 0.0 and xh.max() < 1.0
+            assert info.alpha > 0.5, info.alpha
+        assert abs(xh.sum() - cfg["V"]) <= 1e-6 * cfg["V"]
+        ip.close()
