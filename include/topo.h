@@ -69,6 +69,9 @@ typedef struct {
   int flexible;         /* 1: Polak-Ribiere beta (safeguard for the FP32 V-cycle) */
   int generic_kernels;  /* 1: use the generic element-matrix kernels on the 2D finest level
                            instead of the specialised Q1 butterfly kernels (for testing) */
+  int smoother;         /* 0: damped Jacobi (default); 1: Chebyshev polynomial of degree nu1
+                           (pre) / nu2 (post) on D^{-1} A_k over [lambda_k / 4, 1.05 lambda_k],
+                           lambda_k from the power iteration (K systems only) */
   int omega_auto;       /* 1: per-level damping omega_k = min(omega, 4 / (3 lambda_k)) with
                            lambda_k ~ lambda_max(D^{-1} A_k) from 15 power iterations at every
                            hierarchy build (all levels of IP systems; levels >= 1 otherwise).

@@ -365,6 +365,11 @@ __global__ void k_power_scale(long long n, const double* __restrict__ w, double*
     v[i] = w[i] * sc;
 }
 
+__global__ void k_power_store(const double* est, double* lam_dev) {
+  pdl_prologue();
+  if (threadIdx.x == 0 && blockIdx.x == 0) *lam_dev = est[0];
+}
+
 // omega_k = min(omega, c / (1.05 lambda)); invd <- omega_k invd.
 __global__ void k_power_finish(long long n, const double* est, double omega, double c,
                                double* omega_dev, double* invd) {
@@ -375,6 +380,54 @@ __global__ void k_power_finish(long long n, const double* est, double omega, dou
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     invd[i] *= om;
+}
+
+// One step of the Chebyshev smoother on D^{-1} A over [lam/alpha, 1.05 lam] (lam from the power
+// iteration): theta = (a+b)/2, delta = (b-a)/2, sigma = theta/delta, rho_0 = 1/sigma,
+// rho_j = 1/(2 sigma - rho_{j-1});  d_0 = D^{-1} t / theta,
+// d_j = rho_j rho_{j-1} d_{j-1} + (2 rho_j / delta) D^{-1} t;  z += d_j;  t = b - A z.
+template <typename T>
+__global__ void k_cheb_update(long long n, int step, int z_zero, const double* lam_dev,
+                              double alpha, const T* __restrict__ invd, const T* __restrict__ t,
+                              T* __restrict__ d, T* __restrict__ z,
+                              const uint8_t* __restrict__ fixed, const CgScalars* sc) {
+  pdl_prologue();
+  const int rhs = blockIdx.y;
+  if (sc && sc[rhs].done) return;
+  const double lam = *lam_dev;
+  const double b = 1.05 * lam, a = lam / alpha;
+  const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
+  double rho_prev = 1.0 / sigma, rho = rho_prev;
+  for (int j = 1; j <= step; ++j) {
+    rho_prev = rho;
+    rho = 1.0 / (2.0 * sigma - rho_prev);
+  }
+  const T c_old = step == 0 ? T(0) : (T)(rho * rho_prev);
+  const T c_new = step == 0 ? (T)(1.0 / theta) : (T)(2.0 * rho / delta);
+  t += rhs * n;
+  d += rhs * n;
+  z += rhs * n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (fixed[i]) {
+      if (z_zero) z[i] = T(0);
+      continue;
+    }
+    const T di = (step == 0 ? T(0) : c_old * d[i]) + c_new * invd[i] * t[i];
+    d[i] = di;
+    z[i] = z_zero ? di : z[i] + di;
+  }
+}
+
+// Loop control of the persistent CG graph: keep iterating while any right-hand side runs.
+// The iteration count bounds the loop even if a right-hand side were never marked done.
+__global__ void k_loop_cond(cudaGraphConditionalHandle handle, const CgScalars* sc, int nrhs,
+                            int max_iter) {
+  pdl_prologue();
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  unsigned running = 0;
+  for (int k = 0; k < nrhs; ++k) running |= (!sc[k].done && sc[k].iter < max_iter) ? 1u : 0u;
+  cudaGraphSetConditional(handle, running);
 }
 
 inline unsigned red_blocks(long long n) {
@@ -439,9 +492,37 @@ cudaError_t launch_power_step(long long n, int arrow, const double* v, const dou
   return cudaGetLastError();
 }
 
+cudaError_t launch_power_store(const double* est, double* lam_dev, cudaStream_t st) {
+  topo::launch(k_power_store, 1, 32, 0, st, est, lam_dev);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_power_finish(long long n, const double* est, double omega, double c,
                                 double* omega_dev, double* invd, cudaStream_t st) {
   topo::launch(k_power_finish, red_blocks(n), kThreads, 0, st, n, est, omega, c, omega_dev, invd);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cheb_update(long long n, int nrhs, int step, int z_zero, const double* lam_dev,
+                               double alpha, const T* invd, const T* t, T* d, T* z,
+                               const uint8_t* fixed, const CgScalars* sc, cudaStream_t st) {
+  topo::launch(k_cheb_update<T>, dim3(blocks_for(n), nrhs), kThreads, 0, st, n, step, z_zero,
+               lam_dev, alpha, invd, t, d, z, fixed, sc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cheb_update<double>(long long, int, int, int, const double*, double,
+                                                const double*, const double*, double*, double*,
+                                                const uint8_t*, const CgScalars*, cudaStream_t);
+template cudaError_t launch_cheb_update<float>(long long, int, int, int, const double*, double,
+                                               const float*, const float*, float*, float*,
+                                               const uint8_t*, const CgScalars*, cudaStream_t);
+
+cudaError_t launch_power_store(const double* est, double* lam_dev, cudaStream_t st);
+
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle handle, const CgScalars* sc, int nrhs,
+                             int max_iter, cudaStream_t st) {
+  topo::launch(k_loop_cond, 1, 32, 0, st, handle, sc, nrhs, max_iter);
   return cudaGetLastError();
 }
 

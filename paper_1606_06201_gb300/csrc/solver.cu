@@ -5,9 +5,11 @@
 // The library runs on a private non-blocking stream.  Each call orders itself after the caller's
 // stream (topo_set_stream, default the legacy stream) with an event and makes the caller's stream
 // wait for its work on exit, so device pointers from the caller may be used on either side.
-// A block of CG iterations is captured once per solver into a CUDA graph; the kernels of a
-// right-hand side whose recurrence has stopped return at once, so the host replays the graph and
-// reads the scalars back once per block.
+// One CG iteration is captured once per solver as the body of a conditional while node; a
+// one-thread kernel at the end of the body clears the condition when every right-hand side has
+// stopped, so a whole solve is one graph launch and one read-back of the scalars.  The kernels
+// of a right-hand side whose recurrence has stopped return at once.  Profiling runs (and
+// TOPO_NO_LOOP=1) use a graph of a block of iterations that the host replays instead.
 #include <cmath>
 #include <cstdlib>
 #include <cstdio>
@@ -34,6 +36,14 @@ bool pdl_enabled() {
     return v && v[0] == '1';
   }();
   return on;
+}
+
+bool loop_disabled() {
+  static const bool off = [] {
+    const char* v = std::getenv("TOPO_NO_LOOP");
+    return v && v[0] == '1';
+  }();
+  return off;
 }
 
 topo_status cuda_status(cudaError_t e, const char* what) {
@@ -274,8 +284,18 @@ topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* 
                                        lv.fixed, s->nrhs, sc, s->st));
     return TOPO_OK;
   }
+  if (k == 1 && s->l1_free) {  // FP64 products on the matrix-free level (build-time power iteration)
+    TOPO_CUDA(launch_apply_l1<double>(lv.d, mode, s->C, s->x, (const double*)v, (const double*)b,
+                                      (double*)y, lv.invd, (double)omega, lv.fixed, s->nrhs, sc,
+                                      s->st));
+    return TOPO_OK;
+  }
   const TV* x = k == 0 ? Prec<TV>::x(s) : nullptr;
   const TV* Ae = k == 0 ? nullptr : Prec<TV>::Ae(lv);
+  if (k >= 1 && !Ae) {
+    set_error("apply_level: level " + std::to_string(k) + " holds no element matrices in this precision");
+    return TOPO_E_INVALID_ARG;
+  }
   TOPO_CUDA(launch_apply<TV>(lv.d, mode, Prec<TV>::K0(s), x, Ae, v, b, y, Prec<TV>::invd(lv), omega,
                              lv.fixed, s->nrhs, sc, s->st));
   return TOPO_OK;
@@ -298,6 +318,33 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
   TV* cur = zk;
   TV* oth = (TV*)lv.t;
   const int nu1 = s->desc.nu1, nu2 = s->desc.nu2;
+  if (lv.lam_dev) {  // Chebyshev smoothing, the same polynomial before and after the correction
+    const long long nv = lv.n;
+    const TV* inv = Prec<TV>::invd(lv);
+    for (int it = 0; it < nu1; ++it) {
+      const TV* t = b;
+      if (it > 0) {
+        TOPO_TRY(apply_level<TV>(s, k, 1, cur, b, oth, sc));
+        t = oth;
+      }
+      TOPO_CUDA(launch_cheb_update<TV>(nv, nrhs, it, it == 0 ? 1 : 0, lv.lam_dev, 4.0, inv, t,
+                                       (TV*)lv.cd, cur, lv.fixed, sc, s->st));
+    }
+    if (nu1 == 0) TOPO_CUDA(cudaMemsetAsync(cur, 0, sizeof(TV) * s->vlen(k) * nrhs, s->st));
+    TOPO_TRY(apply_level<TV>(s, k, 1, cur, b, oth, sc));
+    Level& lc = s->L[k + 1];
+    TOPO_CUDA(launch_restrict<TV>(lv.d, oth, (TV*)lc.b, lc.fixed, nrhs, sc, s->st, s->arrow));
+    TV* zc = nullptr;
+    TOPO_TRY(vcycle<TV>(s, k + 1, (const TV*)lc.b, &zc, sc, false));
+    TOPO_CUDA(launch_prolong_add<TV>(lv.d, zc, cur, lv.fixed, nrhs, sc, s->st, s->arrow));
+    for (int it = 0; it < nu2; ++it) {
+      TOPO_TRY(apply_level<TV>(s, k, 1, cur, b, oth, sc));
+      TOPO_CUDA(launch_cheb_update<TV>(nv, nrhs, it, 0, lv.lam_dev, 4.0, inv, oth, (TV*)lv.cd,
+                                       cur, lv.fixed, sc, s->st));
+    }
+    *result = cur;
+    return TOPO_OK;
+  }
   if (nu1 >= 1) {
     TOPO_TRY(apply_level<TV>(s, k, 3, cur, b, cur, sc));
     for (int it = 1; it < nu1; ++it) {
@@ -361,7 +408,7 @@ topo_status cg_iteration(topo_solver* s, int slot, double tol, int max_iter) {
                                  s->sc, tol, max_iter, s->st));
   void* y = nullptr;
   const bool fuse = s->q1_ok && !s->arrow && s->desc.nu2 >= 1 && !s->desc.flexible &&
-                    s->nlev >= 2;
+                    s->nlev >= 2 && s->desc.smoother == 0;
   TOPO_TRY(precondition<TV>(s, s->sc, &y, fuse));
   s->yv = y;
   if (fuse)
@@ -404,6 +451,74 @@ topo_status capture(topo_solver* s, cudaGraphExec_t* exec, int* kernels, F body)
   return TOPO_OK;
 }
 
+// One graph per solve after the setup: a conditional while node whose body is one CG iteration
+// followed by the loop-condition kernel.
+template <typename TV>
+topo_status capture_loop(topo_solver* s, double tol, int max_iter) {
+  if (s->loop) {
+    cudaGraphExecDestroy(s->loop);
+    s->loop = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  TOPO_CUDA(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle handle;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_status(e, "cudaGraphConditionalHandleCreate");
+  }
+  cudaGraphNodeParams prm = {};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = handle;
+  prm.conditional.type = cudaGraphCondTypeWhile;
+  prm.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &prm);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_status(e, "cudaGraphAddNode(conditional)");
+  }
+  cudaGraph_t body = prm.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(s->st, body, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_status(e, "cudaStreamBeginCaptureToGraph");
+  }
+  const bool prof = s->profiling;
+  s->profiling = false;  // no event nodes inside a conditional body
+  topo_status st = cg_iteration<TV>(s, 0, tol, max_iter);
+  s->profiling = prof;
+  if (st == TOPO_OK) {
+    cudaError_t le = launch_loop_cond(handle, s->sc, s->nrhs, max_iter, s->st);
+    if (le != cudaSuccess) st = cuda_status(le, "launch_loop_cond");
+  }
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(s->st, &captured);
+  if (st != TOPO_OK) {
+    cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_status(e, "cudaStreamEndCapture(loop body)");
+  }
+  size_t nn = 0;
+  cudaGraphGetNodes(body, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn) cudaGraphGetNodes(body, nodes.data(), &nn);
+  int kn = 0;
+  for (size_t i = 0; i < nn; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kn;
+  }
+  s->loop_kernels = kn;
+  e = cudaGraphInstantiate(&s->loop, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_status(e, "cudaGraphInstantiate(loop)");
+  return TOPO_OK;
+}
+
 topo_status launch_graph(topo_solver* s, cudaGraphExec_t g, int kernels) {
   TOPO_CUDA(cudaGraphLaunch(g, s->st));
   s->launches += (unsigned long long)kernels;
@@ -443,7 +558,18 @@ topo_status solve_impl(topo_solver* s, const double* b, double* u, double tol, i
                      [&]() { return cg_setup<TV>(s, ux, tol, max_iter); }));
     s->setup_tol[ux] = tol;
   }
-  if (!s->graph || s->graph_tol != tol) {
+  // Programmatic-launch attributes stay out of conditional bodies.
+  const bool use_loop = !s->profiling && !s->no_loop && !pdl_enabled() && !loop_disabled();
+  if (use_loop && (!s->loop || s->loop_tol != tol)) {
+    topo_status ls = capture_loop<TV>(s, tol, max_iter);
+    if (ls != TOPO_OK) {  // conditional graphs unavailable: fall back to blocks of iterations
+      cudaGetLastError();
+      s->no_loop = true;
+    } else {
+      s->loop_tol = tol;
+    }
+  }
+  if ((!use_loop || s->no_loop) && (!s->graph || s->graph_tol != tol)) {
     TOPO_TRY(capture(s, &s->graph, &s->graph_kernels, [&]() {
       for (int it = 0; it < s->graph_iters; ++it) TOPO_TRY(cg_iteration<TV>(s, it, tol, max_iter));
       return TOPO_OK;
@@ -455,9 +581,18 @@ topo_status solve_impl(topo_solver* s, const double* b, double* u, double tol, i
   TOPO_CUDA(launch_mask_copy(n, s->L[0].n, nrhs, b, s->bbuf, s->L[0].fixed, s->st));
   if (use_x0) TOPO_CUDA(launch_mask_copy(n, s->L[0].n, nrhs, u, s->z, s->L[0].fixed, s->st));
   TOPO_TRY(launch_graph(s, s->setup[ux], s->setup_kernels[ux]));
+  if (use_loop && !s->no_loop) {
+    TOPO_CUDA(cudaGraphLaunch(s->loop, s->st));
+    TOPO_CUDA(cudaMemcpyAsync(s->sc_host, s->sc, sizeof(CgScalars) * nrhs, cudaMemcpyDeviceToHost,
+                              s->st));
+    TOPO_CUDA(cudaStreamSynchronize(s->st));
+    int executed = 0;
+    for (int k = 0; k < nrhs; ++k) executed = std::max(executed, s->sc_host[k].iter);
+    s->launches += (unsigned long long)s->loop_kernels * std::max(executed, 1);
+  }
   int blocks = 0;
   const int max_blocks = (max_iter + s->graph_iters - 1) / s->graph_iters + 1;
-  bool all_done = false;
+  bool all_done = use_loop && !s->no_loop;
   int iter_before = 0;
   while (!all_done && blocks < max_blocks) {
     TOPO_TRY(launch_graph(s, s->graph, s->graph_kernels));
@@ -543,7 +678,7 @@ topo_status enqueue_build(topo_solver* s) {
       TOPO_CUDA(launch_inv_diag_l1(lv.d, s->C, s->x, lv.fixed, lv.invd, st));
     else if (!(s->arrow && k == 0))  // the IP driver writes the finest diagonal of Z
       TOPO_CUDA(launch_inv_diag(lv.d, s->K0, k == 0 ? s->x : nullptr, lv.Ae, lv.fixed, lv.invd, st));
-    if (lv.omega_dev) {  // lambda_max(D^{-1} A_k) by power iteration, then the damping
+    if (lv.omega_dev || lv.lam_dev) {  // lambda_max(D^{-1} A_k) by power iteration
       const int ar = s->arrow ? 1 : 0;
       TOPO_CUDA(launch_power_init(lv.n, ar, s->p, lv.fixed, st));
       for (int it = 0; it < 15; ++it) {
@@ -551,8 +686,11 @@ topo_status enqueue_build(topo_solver* s) {
         TOPO_CUDA(launch_power_step(lv.n, ar, s->p, s->q, lv.invd, s->zll, s->r, s->partials,
                                     s->counters, s->pw_est, st));
       }
-      TOPO_CUDA(launch_power_finish(lv.n, s->pw_est, s->desc.omega, 4.0 / 3.0, lv.omega_dev,
-                                    lv.invd, st));
+      if (lv.lam_dev)
+        TOPO_CUDA(launch_power_store(s->pw_est, lv.lam_dev, st));
+      else
+        TOPO_CUDA(launch_power_finish(lv.n, s->pw_est, s->desc.omega, 4.0 / 3.0, lv.omega_dev,
+                                      lv.invd, st));
     }
     if (mixed) {
       TOPO_CUDA(launch_convert_d2f(lv.invd, lv.invd32, lv.n, st));
@@ -606,6 +744,7 @@ topo_status topo_element_stiffness(int dim, double E, double nu, double* K0_out)
 topo_status topo_solver_destroy(topo_solver* s) {
   if (!s) return TOPO_OK;
   if (s->graph) cudaGraphExecDestroy(s->graph);
+  if (s->loop) cudaGraphExecDestroy(s->loop);
   for (int k = 0; k < 2; ++k)
     if (s->setup[k]) cudaGraphExecDestroy(s->setup[k]);
   if (s->build) cudaGraphExecDestroy(s->build);
@@ -688,7 +827,12 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
     if (!coarsest) {
       TOPO_TRY(s->alloc(&lv.invd, lv.n));
       if (s->prec == TOPO_MIXED) TOPO_TRY(s->alloc(&lv.invd32, lv.n));
-      if (d->omega_auto && (arrow || k >= 1)) TOPO_TRY(s->alloc(&lv.omega_dev, 1));
+      if (d->smoother == 1 && !arrow) {
+        TOPO_TRY(s->alloc(&lv.lam_dev, 1));
+        TOPO_TRY(s->alloc((char**)&lv.cd, vbytes * vl * nrhs));
+      } else if (d->omega_auto && (arrow || k >= 1)) {
+        TOPO_TRY(s->alloc(&lv.omega_dev, 1));
+      }
       TOPO_TRY(s->alloc((char**)&lv.t, vbytes * vl * nrhs));
     }
     if (k >= 1) TOPO_TRY(s->alloc((char**)&lv.b, vbytes * vl * nrhs));
@@ -761,7 +905,8 @@ topo_status topo_solver_create(const topo_solver_desc* d, topo_solver** out) {
   if ((d->dim != 2 && d->dim != 3) || d->nx < 1 || d->ny < 1 || (d->dim == 3 && d->nz < 1) ||
       d->levels < 1 || d->levels > 16 || (d->precision != TOPO_FP64 && d->precision != TOPO_MIXED) ||
       d->nu1 < 0 || d->nu2 < 0 || !(d->omega > 0.0 && d->omega <= 1.0) || d->max_iter < 0 ||
-      d->nrhs < 1 || d->nrhs > kMaxRhs || !(d->E > 0.0) || !(d->nu > -1.0 && d->nu < 0.5)) {
+      d->nrhs < 1 || d->nrhs > kMaxRhs || !(d->E > 0.0) || !(d->nu > -1.0 && d->nu < 0.5) ||
+      (d->smoother != 0 && d->smoother != 1)) {
     set_error("topo_solver_create: invalid descriptor field");
     return TOPO_E_INVALID_ARG;
   }

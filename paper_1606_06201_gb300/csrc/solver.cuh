@@ -58,7 +58,11 @@ struct topo_solver {
   double* dots = nullptr;
   double* dots_host = nullptr;
   double* bbuf = nullptr;        // solver-owned copy of the right-hand side
-  cudaGraphExec_t graph = nullptr;        // graph_iters CG iterations
+  cudaGraphExec_t loop = nullptr;         // persistent CG: while-node over one iteration
+  int loop_kernels = 0;                   // kernels per loop iteration
+  double loop_tol = -1.0;
+  bool no_loop = false;                   // conditional graphs unavailable (or TOPO_NO_LOOP=1)
+  cudaGraphExec_t graph = nullptr;        // graph_iters CG iterations (profiling runs)
   int graph_kernels = 0;
   double graph_tol = -1.0;                // tolerance baked into the captured graphs
   cudaGraphExec_t setup[2] = {nullptr, nullptr};  // CG start (use_x0 = 0 / 1)

@@ -76,6 +76,8 @@ struct Level {
   double* invd = nullptr;          // 1 / diag(A) [n] (1 on fixed DOFs)
   float* invd32 = nullptr;
   double* omega_dev = nullptr;     // per-level Jacobi damping (adaptive damping only)
+  double* lam_dev = nullptr;       // lambda_max(D^{-1} A) estimate (Chebyshev smoother)
+  void* cd = nullptr;              // Chebyshev direction vector
   double* w = nullptr;             // arrow column Z_ul on this level (IP systems) [n]
   float* w32 = nullptr;
   void* b = nullptr;               // V-cycle right-hand side   [nrhs][n] (FP64 or FP32)
@@ -271,6 +273,17 @@ cudaError_t launch_power_step(long long n, int arrow, const double* v, const dou
                               unsigned* counters, double* est, cudaStream_t st);
 cudaError_t launch_power_finish(long long n, const double* est, double omega, double c,
                                 double* omega_dev, double* invd, cudaStream_t st);
+// lam_dev <- est[0] (the Chebyshev smoother keeps the estimate instead of folding it into invd).
+cudaError_t launch_power_store(const double* est, double* lam_dev, cudaStream_t st);
+// One Chebyshev smoothing step (see kernels_pcg.cu): t = b - A z (t = b for step 0 from z = 0,
+// z_zero = 1, which overwrites z).
+template <typename T>
+cudaError_t launch_cheb_update(long long n, int nrhs, int step, int z_zero, const double* lam_dev,
+                               double alpha, const T* invd, const T* t, T* d, T* z,
+                               const uint8_t* fixed, const CgScalars* sc, cudaStream_t st);
+// Sets the while-loop condition of the persistent CG graph (1 while any right-hand side runs).
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle handle, const CgScalars* sc, int nrhs,
+                             int max_iter, cudaStream_t st);
 cudaError_t launch_mask_copy(long long n, long long n_mask, int nrhs, const double* src,
                              double* dst, const uint8_t* fixed, cudaStream_t st);
 // p^T q and alpha = r^T y / p^T q (breakdown checks as in the fused operator kernel).

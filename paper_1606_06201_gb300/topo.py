@@ -30,7 +30,7 @@ class SolverDesc(ctypes.Structure):
                 ("precision", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("omega", ctypes.c_double), ("max_iter", ctypes.c_int), ("nrhs", ctypes.c_int),
                 ("flexible", ctypes.c_int), ("generic_kernels", ctypes.c_int),
-                ("omega_auto", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("omega_auto", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -143,8 +143,11 @@ def element_stiffness(dim, E=1.0, nu=0.3):
     return K0
 
 
+JACOBI, CHEBYSHEV = 0, 1
+
+
 def _desc(nx, ny, nz, fixed, levels, precision, nu1, nu2, omega, max_iter, nrhs, flexible, E, nu,
-          generic_kernels, omega_auto=False):
+          generic_kernels, omega_auto=False, smoother=0):
     dim = 3 if nz else 2
     n = dim * (nx + 1) * (ny + 1) * ((nz + 1) if nz else 1)
     if fixed is None:
@@ -158,7 +161,7 @@ def _desc(nx, ny, nz, fixed, levels, precision, nu1, nu2, omega, max_iter, nrhs,
         flexible = 0
     d = SolverDesc(dim, nx, ny, nz, E, nu, fixed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
                    levels, precision, nu1, nu2, omega, max_iter, nrhs, flexible,
-                   int(generic_kernels), int(omega_auto))
+                   int(generic_kernels), int(smoother), int(omega_auto))
     return d, fixed, dim, n
 
 
@@ -290,7 +293,7 @@ class Solver:
 
     def __init__(self, nx, ny, nz=0, fixed=None, levels=3, precision=FP64, nu1=2, nu2=2,
                  omega=None, max_iter=1000, nrhs=1, flexible=None, E=1.0, nu=0.3,
-                 generic_kernels=False, omega_auto=False):
+                 generic_kernels=False, omega_auto=False, smoother=0):
         dim = 3 if nz else 2
         n = dim * (nx + 1) * (ny + 1) * ((nz + 1) if nz else 1)
         if fixed is None:
@@ -305,7 +308,7 @@ class Solver:
         d = SolverDesc(dim, nx, ny, nz, E, nu,
                        self._fixed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), levels,
                        precision, nu1, nu2, omega, max_iter, nrhs, flexible, int(generic_kernels),
-                       int(omega_auto))
+                       int(smoother), int(omega_auto))
         h = _vp()
         _check(_lib.topo_solver_create(ctypes.byref(d), ctypes.byref(h)), "topo_solver_create")
         self._h = h

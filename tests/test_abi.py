@@ -58,16 +58,16 @@ def test_descriptor_validation_needs_no_device():
     from paper_1606_06201_gb300 import topo
     fixed = np.zeros(2 * 9 * 5, dtype=np.uint8)
     bad = [dict(levels=5), dict(levels=0), dict(nu1=-1), dict(omega=1.5), dict(nrhs=0),
-           dict(precision=7)]
+           dict(precision=7), dict(smoother=2)]
     for kw in bad:
         args = dict(dim=2, nx=8, ny=4, nz=0, E=1.0, nu=0.3, levels=2, precision=0, nu1=2, nu2=2,
-                    omega=0.6, max_iter=10, nrhs=1, flexible=0, generic_kernels=0, omega_auto=0)
+                    omega=0.6, max_iter=10, nrhs=1, flexible=0, generic_kernels=0, smoother=0, omega_auto=0)
         args.update(kw)
         d = topo.SolverDesc(args["dim"], args["nx"], args["ny"], args["nz"], args["E"], args["nu"],
                             fixed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), args["levels"],
                             args["precision"], args["nu1"], args["nu2"], args["omega"],
                             args["max_iter"], args["nrhs"], args["flexible"],
-                            args["generic_kernels"], args["omega_auto"])
+                            args["generic_kernels"], args["smoother"], args["omega_auto"])
         h = ctypes.c_void_p()
         st = topo._lib.topo_solver_create(ctypes.byref(d), ctypes.byref(h))
         assert st == topo.E_INVALID_ARG, kw

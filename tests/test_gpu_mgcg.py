@@ -243,3 +243,52 @@ def test_batched_3d_point_loads_match_cholesky(precision):
         exact = np.zeros(s.n)
         exact[free] = solver.solve(cfg["f"][r][free])
         assert rel_err(Uh[r], exact) <= (1e-10 if precision == 0 else 1e-6)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_chebyshev_smoother_solves_and_is_symmetric(precision):
+    """Chebyshev smoothing (degree nu on D^{-1} A_k, interval from the power iteration): the solve
+    still matches the exact solution and, in FP64, the V-cycle is a symmetric operator."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny, L = 128, 64, 5
+    fixed = W.clamp_xmin(nx, ny)
+    x = _x(nx, ny, 0, 41)
+    f = W.normal_load(fixed, 42)
+    s = topo.Solver(nx, ny, fixed=fixed, levels=L, precision=precision, smoother=topo.CHEBYSHEV)
+    s.set_density(dev(torch, x))
+    tol = 1e-12 if precision == 0 else 1e-9
+    u, info = s.solve(dev(torch, f), tol=tol)
+    K, free, grid = oracle_K_free(nx, ny, 0, x, fixed.astype(bool))
+    exact = np.zeros(s.n)
+    exact[free] = SPDSolver(K, grid, free).solve(f[free])
+    assert info.status == topo.OK
+    assert rel_err(host(u), exact) <= (1e-10 if precision == 0 else 1e-6)
+    if precision == 0:
+        a = W.random_vector(s.n, 43, fixed)
+        c = W.random_vector(s.n, 44, fixed)
+        Ma = host(s.apply_vcycle(dev(torch, a)))
+        Mc = host(s.apply_vcycle(dev(torch, c)))
+        assert abs(Ma @ c - a @ Mc) <= 1e-11 * abs(Ma @ c)
+        assert a @ Ma > 0
+
+
+def test_autotuner_picks_a_converging_setting(tmp_path):
+    """The smoother autotuner times full solves over (omega, nu), caches the fastest converging
+    setting per (grid, precision, batch) and that setting solves to the tolerance."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    from paper_1606_06201_gb300 import autotune
+    cfg = W.random_field_3d(16, 8, 8, n_rhs=4)
+    x, F = dev(torch, cfg["x"]), dev(torch, cfg["f"])
+    path = str(tmp_path / "tune.json")
+    best = autotune.autotune(16, 8, 8, cfg["fixed"], x, F, levels=3, precision=topo.MIXED, nrhs=4,
+                             tol=1e-8, omegas=(0.3, 0.5), sweeps=(1, 2), cache_path=path)
+    assert best["omega"] in (0.3, 0.5) and best["nu"] in (1, 2) and best["ms"] > 0
+    import json
+    assert list(json.load(open(path)).values())[0] == best
+    s = topo.Solver(16, 8, 8, fixed=cfg["fixed"], levels=3, precision=topo.MIXED, nrhs=4,
+                    omega=best["omega"], nu1=best["nu"], nu2=best["nu"])
+    s.set_density(x)
+    _, info = s.solve(F, tol=1e-8)
+    assert info.status == topo.OK and info.rel_residual <= 1e-8
