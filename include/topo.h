@@ -149,6 +149,25 @@ topo_status topo_element_energy(topo_solver* s, const double* u, double* E);
  * lam, u [device, n], g [device, m]. */
 topo_status topo_grad_x(topo_solver* s, const double* lam, const double* u, double* g);
 
+/* ---- Allocation-free compliance (no counterpart in the paper) -------------------------------
+ * c[k] = f_k^T u_k for k < nrhs: the reduction of topo_compliance, without a solver object and
+ * without allocating anything (no cudaMalloc, cudaFree or pinned host memory).  It is meant for
+ * callers that cannot allocate at that point: code that holds no solver (creating one allocates
+ * the whole multigrid hierarchy) and code whose device memory a caching allocator has already
+ * reserved, where a fresh cudaMalloc can fail and cudaFree synchronizes the device.
+ * f, u [device, nrhs x n, right-hand side k at offset k*n]; c [device, nrhs], written by a
+ * kernel enqueued on cuda_stream (a cudaStream_t; NULL = the legacy default stream); the call
+ * returns without waiting for it.  n = 0 gives c = 0.
+ * Scratch: a fixed device array inside the library, 311,552 bytes per device, holding the
+ * partial sums of at most 64 right-hand sides; nrhs outside 1..64 or n < 0 -> E_INVALID_ARG with
+ * the reason in topo_last_error().  Its ticket counters must be zero when a call starts: they
+ * are zero when the library loads and every call leaves them at zero.
+ * The first call on a device looks the array up (cudaGetSymbolAddress) with that device
+ * current; make it before any stream capture.  Calls that overlap on one device (other
+ * streams or host threads) share the array and race: the caller orders them. */
+topo_status topo_compliance_noalloc(const double* f, const double* u, long long n, int nrhs,
+                                    double* c, void* cuda_stream);
+
 /* ---- Primal-dual interior-point method (Sec. 2-3) ----------------------------------------
  * Newton steps on the KKT conditions KKT1-3 with the perturbed complementarity KKT4p/5p,
  * reduced to the SPD augmented system Z [d_u; d_lambda] = Res^Z of Eq. (nwtr2)-(nwtr2rhs), which

@@ -90,6 +90,8 @@ _SIGS = {
     "topo_compliance": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "topo_element_energy": (ctypes.c_int, [_vp, _vp, _vp]),
     "topo_grad_x": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "topo_compliance_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_longlong, ctypes.c_int, _vp,
+                                               _vp]),
     "topo_ip_create": (ctypes.c_int, [ctypes.POINTER(SolverDesc), _vp, ctypes.c_double,
                                       ctypes.c_double, ctypes.POINTER(_vp)]),
     "topo_ip_destroy": (ctypes.c_int, [_vp]),
@@ -178,6 +180,24 @@ def oc_options(variant=OC_AOC, q=0.5, xlow=1e-6, lam_hi=1e4, tau_lambda=1e-11, t
     return OcOpts(variant, q, xlow, lam_hi, tau_lambda, tau_oc, max_feval, cg_tol0,
                   int(adaptive_tol))
 
+
+
+def compliance_noalloc(f, u, c, nrhs=1):
+    """c[k] = f_k^T u_k through topo_compliance_noalloc (static library scratch, no allocation).
+
+    f, u: contiguous FP64 CUDA tensors of nrhs * n entries; c: contiguous FP64 CUDA tensor of
+    nrhs entries, written asynchronously on the current stream.
+    """
+    import torch
+    if f.numel() != u.numel() or nrhs < 1 or f.numel() % nrhs:
+        raise ValueError("f and u must hold nrhs vectors of one length")
+    if c.numel() < nrhs:
+        raise ValueError("c must hold nrhs entries")
+    n = f.numel() // nrhs
+    _check(_lib.topo_compliance_noalloc(_ptr(f), _ptr(u), n, int(nrhs), _ptr(c),
+                                        _vp(torch.cuda.current_stream().cuda_stream)),
+           "topo_compliance_noalloc")
+    return c
 
 class IP:
     """Primal-dual interior-point method on the GPU (see include/topo.h)."""
