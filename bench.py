@@ -47,6 +47,15 @@ OPS_PER_ELEM, OPS_PER_NODE = 40.0, 8.0
 OPERATOR_DRAM_BYTES = 58712320.0
 
 
+def _measured_hbm_gbs():
+    """Measured copy bandwidth of this GPU model (MEASURED_PEAKS.json), else 6800 GB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -196,7 +205,7 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def run(precision, steps, warmup, profile=False, host_io=False):
+    def run(precision, steps, warmup, profile_mask=0, host_io=False):
         s = topo.Solver(NX, NY, fixed=cfg["fixed"], levels=LEVELS, precision=precision)
         u_d = torch.zeros_like(f_d)
         if host_io:
@@ -219,10 +228,11 @@ def main():
 
         for _ in range(warmup):
             step()
+        profile = profile_mask != 0
         if profile:
-            s.set_profiling(True)
+            s.set_profiling_mask(profile_mask)
             step()  # capture the instrumented graph outside the timed region
-            s.set_profiling(True)
+            s.set_profiling_mask(profile_mask)  # and restart the counters
         barrier()
         l0 = s.launch_count
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -238,8 +248,9 @@ def main():
         ms = e0.elapsed_time(e1)
         launches = s.launch_count - l0
         prof = s.profile() if profile else None
+        kinds = [s.profile_kernel(k) for k in range(len(topo.Solver.PROFILE_KINDS))] if profile else None
         s.close()
-        return dict(ms=ms, iters=iters, res=res, launches=launches, prof=prof)
+        return dict(ms=ms, iters=iters, res=res, launches=launches, prof=prof, kinds=kinds)
 
     if args.only:
         r = run(topo.MIXED if args.only == "mixed" else topo.FP64, args.steps, args.warmup)
@@ -248,9 +259,14 @@ def main():
         return 0
     # warm-up + timed steps: mixed (headline, with live operator timing), FP64, end-to-end
     with ClockSampler(dev.index) as clk:
-        mixed = run(topo.MIXED, args.steps, args.warmup, profile=True)
+        # headline: event pairs around the outer operator only (one pair adds ~nothing)
+        mixed = run(topo.MIXED, args.steps, args.warmup, profile_mask=1)
         fp64 = run(topo.FP64, args.steps, args.warmup)
         e2e = run(topo.MIXED, args.steps, args.warmup, host_io=True)
+        # separate run with every kind profiled, for the per-kernel and per-part times (its own
+        # step time is longer by the extra event nodes and is not reported)
+        kinds_run = run(topo.MIXED, max(1, min(args.steps, 5)), 3,
+                        profile_mask=(1 << len(topo.Solver.PROFILE_KINDS)) - 1)
 
     def ip_oc_runs():
         """512x256 cantilever (Example 2 shape 428, V = 0.4 m, 6 levels): IP and AOC with 50 outer
@@ -306,6 +322,45 @@ def main():
                 "algorithmic_bytes_per_launch": 8.0 * m + 16.0 * n + 1.0 * n,
                 "dense_form_tflops": (144.0 * m + 2.0 * n) / (op_avg_ms * 1e-3) / 1e12,
                 "avg_launch_ms": op_avg_ms, "launches_timed": op_cnt}
+        # HBM-bound kernels of the FP32 V-cycle on the finest level, timed live like the operator:
+        # algorithmic bytes per launch (FP32 vectors of n DOFs, FP32 densities of m elements, the
+        # byte mask) / average launch time, against the measured copy bandwidth.
+        hbm_peak = _measured_hbm_gbs()
+        nc = ((NX // 2) + 1) * ((NY // 2) + 1) * 2
+        hbm_bytes = {
+            "fine_smoothing_sweep": ("k_q1_sweep<float,2,0>: z' = z + omega D^-1 (b - K(x) z), "
+                                     "diag from x", 4.0 * m + 13.0 * n),
+            "fine_residual": ("k_q1_sweep<float,1,0>: r = b - K(x) z", 4.0 * m + 13.0 * n),
+            "fine_restriction": ("k_restrict<2,float>: b_c = P^T r", 4.0 * n + 5.0 * nc),
+            "fine_prolongation": ("k_prolong_add<2,float>: z += P z_c", 9.0 * n + 4.0 * nc),
+        }
+        hbm_kernels = []
+        for k, key in enumerate(topo.Solver.PROFILE_KINDS):
+            if key not in hbm_bytes or not kinds_run["kinds"]:
+                continue
+            kms, kcnt = kinds_run["kinds"][k]
+            if not kcnt:
+                continue
+            desc, nbytes = hbm_bytes[key]
+            avg = kms / kcnt
+            gbs = nbytes / (avg * 1e-3) / 1e9
+            hbm_kernels.append({"kernel": desc, "bound": "hbm", "bytes_per_launch": nbytes,
+                                "avg_launch_us": avg * 1e3, "achieved": gbs, "peak": hbm_peak,
+                                "unit": "GB/s", "frac": gbs / hbm_peak, "launches_timed": kcnt})
+        breakdown = None
+        if kinds_run["kinds"]:
+            avg = {key: (ms * 1e3 / cnt if cnt else None)
+                   for key, (ms, cnt) in zip(topo.Solver.PROFILE_KINDS, kinds_run["kinds"])}
+            step_us = ms_mixed * 1e3 / args.steps
+            breakdown = {"outer_operator": avg["outer_operator"], "vcycle": avg["vcycle"],
+                         "vcycle_finest_level": (avg["vcycle"] - avg["vcycle_levels_ge1"])
+                         if avg["vcycle"] and avg["vcycle_levels_ge1"] else None,
+                         "vcycle_first_coarse_level": (avg["vcycle_levels_ge1"] - avg["vcycle_levels_ge2"])
+                         if avg["vcycle_levels_ge1"] and avg["vcycle_levels_ge2"] else None,
+                         "vcycle_levels_ge2": avg["vcycle_levels_ge2"],
+                         "unit": "us per CG iteration (live CUDA events, mixed solver, separate fully "
+                                 "profiled run)",
+                         "step_us": step_us}
         cpu = None
         if not args.no_cpu_baseline:
             v, t, runs, nf, it = oracle_mgcg_sample(1024, 512, 8, seconds=10.0)
@@ -327,6 +382,8 @@ def main():
             "fp64": {"value": ws * nfree * fp64["iters"] / (ms_fp64 * 1e-3), "unit": UNIT,
                      "ms_per_step": ms_fp64 / args.steps, "iterations_per_solve": fp64["iters"] / args.steps},
             "roofline": roof,
+            "hbm_kernels": hbm_kernels,
+            "iteration_breakdown": breakdown,
             "cpu_baseline": cpu,
             "e2e": {"value": ws * nfree * e2e["iters"] / (ms_e2e * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},

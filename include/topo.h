@@ -103,6 +103,18 @@ topo_status topo_element_stiffness(int dim, double E, double nu, double* K0_out)
 topo_status topo_solver_create(const topo_solver_desc* desc, topo_solver** out);
 topo_status topo_solver_destroy(topo_solver* s);
 topo_status topo_set_stream(topo_solver* s, void* cuda_stream);
+/* How topo_solve drives the CG iterations of Algorithm PCG (Sec. 5.2); both give the same bits.
+ * mode 0 (default): a captured graph of 4 iterations that the host replays, reading the scalars
+ * back after each replay.  mode 1: one graph launch per solve, whose conditional while node
+ * repeats one captured iteration until every right-hand side has stopped or reached max_iter
+ * (falls back to mode 0 where conditional graph nodes are unavailable, and while profiling).
+ * Other modes -> E_INVALID_ARG. */
+topo_status topo_set_graph_mode(topo_solver* s, int mode);
+/* Algorithm MG on the deep levels of a 2D K system with Jacobi smoothing: on (default, where the
+ * device can run it) the levels from the first one of at most a few thousand nodes down to the
+ * coarsest run in one launch of a thread-block cluster per right-hand side; off, one launch per
+ * sweep, residual and transfer.  Both give the same bits.  Other systems ignore the setting. */
+topo_status topo_set_vcycle_fusion(topo_solver* s, int on);
 /* Device bytes held by the solver. */
 size_t topo_solver_device_bytes(const topo_solver* s);
 /* Number of CUDA kernels this solver has launched since its creation (graph kernel nodes
@@ -113,7 +125,20 @@ unsigned long long topo_solver_launch_count(const topo_solver* s);
  * topo_get_profile returns the summed duration in ms and the number of timed launches since the
  * last topo_set_profiling call.  Instrumentation, no counterpart in the paper. */
 topo_status topo_set_profiling(topo_solver* s, int on);
+/* Profile a set of kinds (bit k = kind k of topo_get_profile_kernel; 0 = off); topo_set_profiling
+ * (s, on) is the mask 1.  Every event pair is a graph node of its own, so each profiled kind adds
+ * some time to the iteration.  mask >= 2^8 -> E_INVALID_ARG. */
+topo_status topo_set_profiling_mask(topo_solver* s, unsigned mask);
 topo_status topo_get_profile(const topo_solver* s, double* operator_ms_total, long long* count);
+/* The same for other parts of the iteration (kind 0 = the outer operator, as topo_get_profile).
+ * Finest level of the V-cycle, in the V-cycle precision: 1 = the first plain smoothing sweep
+ * (z <- z + omega D^{-1} (b - A z) with z != 0), 2 = the residual b - A z before restriction,
+ * 3 = the restriction P^T r, 4 = the prolongation and correction z += P z_c.  Spans of several
+ * kernels: 5 = the whole V-cycle (preconditioner), 6 = its part on levels >= 1, 7 = its part on
+ * levels >= 2 (coarsest solve included).  A kind that the solver's V-cycle does not run has
+ * count 0.  kind outside 0..7 -> E_INVALID_ARG. */
+topo_status topo_get_profile_kernel(const topo_solver* s, int kind, double* ms_total,
+                                    long long* count);
 
 /* Set the densities x [device, m FP64] (copied) and rebuild the Galerkin hierarchy
  * A_{k-1} = P^T A_k P (Sec. 5.1) with the coarsest factorisation.  x must be finite, > 0. */
@@ -134,7 +159,10 @@ topo_status topo_apply_K(topo_solver* s, const double* v, double* y);
 topo_status topo_apply_vcycle(topo_solver* s, const double* r, double* y);
 
 /* Coarse-level data, for inspection: level 0 is the finest.  For 1 <= level < levels the
- * Galerkin element matrices [host out, m_level x ne x ne FP64 with ne = 8 (2D) or 24 (3D)]. */
+ * Galerkin element matrices [host out, m_level x ne x ne FP64 with ne = 8 (2D) or 24 (3D)].
+ * Mixed-precision solvers with fixed damping (Jacobi, omega_auto = 0) compute and keep the
+ * matrices below the coarsest level in FP32 only; those are returned widened.  The 2D mixed
+ * first coarse level is applied matrix-free and has none (E_INVALID_ARG). */
 topo_status topo_get_level_matrices(topo_solver* s, int level, double* out_host);
 /* Number of elements of a level (0 = finest). */
 int topo_level_elems(const topo_solver* s, int level);

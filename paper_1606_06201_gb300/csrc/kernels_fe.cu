@@ -30,11 +30,20 @@ __device__ __forceinline__ int loc_of(int lx, int ly, int lz) {
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
+// Load of a vector entry: through the read-only path (ldg), or, when COH, from L2 (ld.global.cg):
+// the fused coarse-level kernel reads vectors that other blocks of its cluster wrote earlier in
+// the same launch, which the non-coherent read-only path may not see.
+template <bool COH, typename T>
+__device__ __forceinline__ T vld(const T* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+
 // Sum over the elements around node (i,j,k) of rows (loc*DIM + c) of the element matrix times
 // the element's DOF values.  FINE: element matrix x_e K0; otherwise the Galerkin element matrices
 // stored entry-major, Ae[(row * NE + col) * m + e], so that a warp reading one entry of 32
 // consecutive elements reads contiguous memory.
-template <int DIM, typename T, bool FINE>
+template <int DIM, typename T, bool FINE, bool COH = false>
 __device__ __forceinline__ void node_apply(const Dims& d, int i, int j, int k,
                                            const T* __restrict__ K0, const T* __restrict__ x,
                                            const T* __restrict__ Ae, const T* __restrict__ v,
@@ -44,6 +53,43 @@ __device__ __forceinline__ void node_apply(const Dims& d, int i, int j, int k,
   const long long m = d.elems();
 #pragma unroll
   for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+  if constexpr (DIM == 2 && !FINE) {
+    // Coarse 2D levels are latency-bound: all 64 matrix entries and 32 vector entries of the
+    // four adjacent elements are loaded before any is used (a missing element reads element 0
+    // and node 0 and is not accumulated).
+    T a[4][16], ve[4][8];
+    bool ok[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int dx = s & 1, dy = s >> 1;
+      const int ex = i - 1 + dx, ey = j - 1 + dy;
+      ok[s] = ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny;
+      const int loc = loc_of(1 - dx, 1 - dy, 0);
+      const long long e = ok[s] ? ex + (long long)d.nx * ey : 0;
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          a[s][c * 8 + q] = ldg(Ae + (long long)((loc * 2 + c) * 8 + q) * m + e);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const long long nid = ok[s] ? (ex + loc_ox(b)) + (long long)nnx * (ey + loc_oy(b)) : 0;
+        ve[s][2 * b] = vld<COH>(v + 2 * nid);
+        ve[s][2 * b + 1] = vld<COH>(v + 2 * nid + 1);
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      if (!ok[s]) continue;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        T t = T(0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t = fma(a[s][c * 8 + q], ve[s][q], t);
+        acc[c] += t;
+      }
+    }
+  } else {
 #pragma unroll 1
   for (int s = 0; s < NN; ++s) {
     const int dx = s & 1, dy = (s >> 1) & 1, dz = (DIM == 3) ? (s >> 2) : 0;
@@ -58,7 +104,7 @@ __device__ __forceinline__ void node_apply(const Dims& d, int i, int j, int k,
       const long long nid = (ex + loc_ox(a)) + (long long)nnx * ((ey + loc_oy(a)) +
                                                                  (long long)nny * (ez + loc_oz(a)));
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) ve[a * DIM + c] = ldg(v + DIM * nid + c);
+      for (int c = 0; c < DIM; ++c) ve[a * DIM + c] = vld<COH>(v + DIM * nid + c);
     }
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
@@ -76,9 +122,50 @@ __device__ __forceinline__ void node_apply(const Dims& d, int i, int j, int k,
       }
     }
   }
+  }
 }
 
-// mode 0: y = A v;  1: y = b - A v;  2: y = v + omega invd (b - A v);  3: y = omega invd b.
+// mode 0: y = A v;  1: y = b - A v;  2: y = v + omega invd (b - A v);  3: y = omega invd b,
+// for the DIM entries of one node (v, b, y of the right-hand side at hand; w: arrow column).
+template <int DIM, typename T, int MODE, bool FINE, bool COH = false>
+__device__ __forceinline__ void apply_node(const Dims& d, long long node, const T* __restrict__ K0,
+                                           const T* __restrict__ x, const T* __restrict__ Ae,
+                                           const T* v, const T* b, T* y,
+                                           const T* __restrict__ invd, T omega,
+                                           const uint8_t* __restrict__ fixed,
+                                           const T* __restrict__ w) {
+  const long long n = d.nodes() * DIM;
+  const int nnx = d.nx + 1, nny = d.ny + 1;
+  int i, j, k;
+  node_coords(node, nnx, nny, DIM, i, j, k);
+  T acc[DIM];
+  if (MODE != 3) {
+    node_apply<DIM, T, FINE, COH>(d, i, j, k, K0, x, Ae, v, acc);
+    if (w) {
+      const T vl = v[n];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) acc[c] = fma(w[DIM * node + c], vl, acc[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const long long id = DIM * node + c;
+    T out;
+    if (fixed[id]) {
+      out = T(0);
+    } else if (MODE == 0) {
+      out = acc[c];
+    } else if (MODE == 1) {
+      out = vld<COH>(b + id) - acc[c];
+    } else if (MODE == 2) {
+      out = vld<COH>(v + id) + omega * invd[id] * (vld<COH>(b + id) - acc[c]);
+    } else {
+      out = omega * invd[id] * vld<COH>(b + id);
+    }
+    y[id] = out;
+  }
+}
+
 template <int DIM, typename T, int MODE, bool FINE>
 __global__ void __launch_bounds__(kThreads) k_apply(Dims d, const T* __restrict__ K0,
                                                     const T* __restrict__ x,
@@ -96,39 +183,8 @@ __global__ void __launch_bounds__(kThreads) k_apply(Dims d, const T* __restrict_
   const long long nodes = d.nodes();
   if (node >= nodes) return;
   const long long n = nodes * DIM;
-  const int nnx = d.nx + 1, nny = d.ny + 1;
-  const int i = (int)(node % nnx);
-  const int j = (int)((node / nnx) % nny);
-  const int k = (DIM == 3) ? (int)(node / ((long long)nnx * nny)) : 0;
-  v += rhs * n;
-  b += rhs * n;
-  y += rhs * n;
-  T acc[DIM];
-  if (MODE != 3) {
-    node_apply<DIM, T, FINE>(d, i, j, k, K0, x, Ae, v, acc);
-    if (w) {
-      const T vl = v[n];
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) acc[c] = fma(w[DIM * node + c], vl, acc[c]);
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < DIM; ++c) {
-    const long long id = DIM * node + c;
-    T out;
-    if (fixed[id]) {
-      out = T(0);
-    } else if (MODE == 0) {
-      out = acc[c];
-    } else if (MODE == 1) {
-      out = b[id] - acc[c];
-    } else if (MODE == 2) {
-      out = v[id] + omega * invd[id] * (b[id] - acc[c]);
-    } else {
-      out = omega * invd[id] * b[id];
-    }
-    y[id] = out;
-  }
+  apply_node<DIM, T, MODE, FINE>(d, node, K0, x, Ae, v + rhs * n, b + rhs * n, y + rhs * n, invd,
+                                 omega, fixed, w);
 }
 
 // First coarse level of the 2D grid without stored element matrices: the Galerkin element matrix
@@ -294,26 +350,14 @@ __global__ void __launch_bounds__(kThreads) k_apply_dot_fine(Dims d, const doubl
 
 // Restriction r_c = P^T r_f: each coarse node gathers the 3x3(x3) fine nodes around its
 // coincident fine node with weights prod_d w(offset), w(0) = 1, w(+-1) = 1/2.
-template <int DIM, typename T>
-__global__ void __launch_bounds__(kThreads) k_restrict(Dims df, const T* __restrict__ rf,
-                                                       T* __restrict__ rc,
-                                                       const uint8_t* __restrict__ fixed_c,
-                                                       const CgScalars* __restrict__ sc,
-                                                       int arrow) {
-  pdl_prologue();
-  const int rhs = blockIdx.y;
-  if (sc && sc[rhs].done) return;
-  Dims dc{df.nx / 2, df.ny / 2, DIM == 3 ? df.nz / 2 : 1, DIM};
-  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nodes_c = dc.nodes();
-  if (arrow && node == 0) rc[dc.dofs()] = rf[df.dofs()];
-  if (node >= nodes_c) return;
+template <int DIM, typename T, bool COH = false>
+__device__ __forceinline__ void restrict_node(const Dims& df, const Dims& dc, long long node,
+                                              const T* rf, T* rc,
+                                              const uint8_t* __restrict__ fixed_c) {
   const int cnx = dc.nx + 1, cny = dc.ny + 1;
-  const int I = (int)(node % cnx), J = (int)((node / cnx) % cny);
-  const int K = (DIM == 3) ? (int)(node / ((long long)cnx * cny)) : 0;
+  int I, J, K;
+  node_coords(node, cnx, cny, DIM, I, J, K);
   const int fnx = df.nx + 1, fny = df.ny + 1;
-  rf += rhs * df.dofs();
-  rc += rhs * dc.dofs();
   T acc[DIM];
 #pragma unroll
   for (int c = 0; c < DIM; ++c) acc[c] = T(0);
@@ -332,7 +376,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict(Dims df, const T* __restr
         const T w = (ox == 0) ? wy : wy * T(0.5);
         const long long fid = fi + (long long)fnx * (fj + (long long)fny * (DIM == 3 ? fk : 0));
 #pragma unroll
-        for (int c = 0; c < DIM; ++c) acc[c] = fma(w, rf[DIM * fid + c], acc[c]);
+        for (int c = 0; c < DIM; ++c) acc[c] = fma(w, vld<COH>(rf + DIM * fid + c), acc[c]);
       }
     }
   }
@@ -343,27 +387,31 @@ __global__ void __launch_bounds__(kThreads) k_restrict(Dims df, const T* __restr
   }
 }
 
-// Prolongation and correction z_f += P z_c (bilinear / trilinear interpolation).
 template <int DIM, typename T>
-__global__ void __launch_bounds__(kThreads) k_prolong_add(Dims df, const T* __restrict__ zc,
-                                                          T* __restrict__ zf,
-                                                          const uint8_t* __restrict__ fixed_f,
-                                                          const CgScalars* __restrict__ sc,
-                                                          int arrow) {
+__global__ void __launch_bounds__(kThreads) k_restrict(Dims df, const T* __restrict__ rf,
+                                                       T* __restrict__ rc,
+                                                       const uint8_t* __restrict__ fixed_c,
+                                                       const CgScalars* __restrict__ sc,
+                                                       int arrow) {
   pdl_prologue();
   const int rhs = blockIdx.y;
   if (sc && sc[rhs].done) return;
   Dims dc{df.nx / 2, df.ny / 2, DIM == 3 ? df.nz / 2 : 1, DIM};
   const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nodes_f = df.nodes();
-  if (arrow && node == 0) zf[df.dofs()] += zc[dc.dofs()];
-  if (node >= nodes_f) return;
+  if (arrow && node == 0) rc[dc.dofs()] = rf[df.dofs()];
+  if (node >= dc.nodes()) return;
+  restrict_node<DIM, T>(df, dc, node, rf + rhs * df.dofs(), rc + rhs * dc.dofs(), fixed_c);
+}
+
+// Prolongation and correction z_f += P z_c (bilinear / trilinear interpolation).
+template <int DIM, typename T, bool COH = false>
+__device__ __forceinline__ void prolong_node(const Dims& df, const Dims& dc, long long node,
+                                             const T* zc, T* zf,
+                                             const uint8_t* __restrict__ fixed_f) {
   const int fnx = df.nx + 1, fny = df.ny + 1;
-  const int i = (int)(node % fnx), j = (int)((node / fnx) % fny);
-  const int k = (DIM == 3) ? (int)(node / ((long long)fnx * fny)) : 0;
+  int i, j, k;
+  node_coords(node, fnx, fny, DIM, i, j, k);
   const int cnx = dc.nx + 1, cny = dc.ny + 1;
-  zc += rhs * dc.dofs();
-  zf += rhs * df.dofs();
   T acc[DIM];
 #pragma unroll
   for (int c = 0; c < DIM; ++c) acc[c] = T(0);
@@ -384,14 +432,127 @@ __global__ void __launch_bounds__(kThreads) k_prolong_add(Dims df, const T* __re
         const T w = wxh * wyh * wzh;
         const long long cid = I + (long long)cnx * (J + (long long)cny * (DIM == 3 ? K : 0));
 #pragma unroll
-        for (int c = 0; c < DIM; ++c) acc[c] = fma(w, zc[DIM * cid + c], acc[c]);
+        for (int c = 0; c < DIM; ++c) acc[c] = fma(w, vld<COH>(zc + DIM * cid + c), acc[c]);
       }
     }
   }
 #pragma unroll
   for (int c = 0; c < DIM; ++c) {
     const long long id = DIM * node + c;
-    if (!fixed_f[id]) zf[id] += acc[c];
+    if (!fixed_f[id]) zf[id] = (COH ? __ldcg(zf + id) : zf[id]) + acc[c];
+  }
+}
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(kThreads) k_prolong_add(Dims df, const T* __restrict__ zc,
+                                                          T* __restrict__ zf,
+                                                          const uint8_t* __restrict__ fixed_f,
+                                                          const CgScalars* __restrict__ sc,
+                                                          int arrow) {
+  pdl_prologue();
+  const int rhs = blockIdx.y;
+  if (sc && sc[rhs].done) return;
+  Dims dc{df.nx / 2, df.ny / 2, DIM == 3 ? df.nz / 2 : 1, DIM};
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (arrow && node == 0) zf[df.dofs()] += zc[dc.dofs()];
+  if (node >= df.nodes()) return;
+  prolong_node<DIM, T>(df, dc, node, zc + rhs * dc.dofs(), zf + rhs * df.dofs(), fixed_f);
+}
+
+// ---- Fused deep levels of the 2D V-cycle ----------------------------------------------------
+// The levels below a few thousand nodes cost a launch per smoothing sweep, residual, restriction
+// and prolongation while their work is a few microseconds of L2 traffic.  One cluster of
+// kTailCluster blocks per right-hand side runs all of them, phase by phase, with the cluster
+// barrier (hardware, release/acquire at cluster scope) between phases; the per-node arithmetic is
+// the same device code as the unfused kernels, so the results are the same bits.  Vectors written
+// within the launch are read from L2 (COH loads), never through the read-only cache.
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+               ::: "memory");
+}
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads, 1) k_vcycle_tail(const __grid_constant__ TailArgs<T> A,
+                                                                 const CgScalars* __restrict__ sc) {
+  pdl_prologue();
+  const int rhs = blockIdx.y;
+  if (sc && sc[rhs].done) return;  // the same for every block of the cluster
+  const long long t0 = (long long)cluster_rank() * blockDim.x + threadIdx.x;
+  const long long ts = (long long)kTailCluster * blockDim.x;
+  T* res[kTailMax];
+  for (int k = 0; k < A.nl - 1; ++k) {
+    const Dims d = A.d[k];
+    const long long n = d.dofs(), nodes = d.nodes();
+    const T* b = A.b[k] + rhs * n;
+    T* c = A.z[k] + rhs * n;
+    T* o = A.t[k] + rhs * n;
+    if (A.nu1 >= 1) {
+      for (long long nd = t0; nd < nodes; nd += ts)
+        apply_node<2, T, 3, false, true>(d, nd, nullptr, nullptr, A.Ae[k], c, b, c, A.invd[k],
+                                         A.omega, A.fixed[k], nullptr);
+      cluster_barrier();
+      for (int it = 1; it < A.nu1; ++it) {
+        for (long long nd = t0; nd < nodes; nd += ts)
+          apply_node<2, T, 2, false, true>(d, nd, nullptr, nullptr, A.Ae[k], c, b, o, A.invd[k],
+                                           A.omega, A.fixed[k], nullptr);
+        cluster_barrier();
+        T* tmp = c;
+        c = o;
+        o = tmp;
+      }
+    } else {
+      for (long long q = t0; q < n; q += ts) c[q] = T(0);
+      cluster_barrier();
+    }
+    for (long long nd = t0; nd < nodes; nd += ts)
+      apply_node<2, T, 1, false, true>(d, nd, nullptr, nullptr, A.Ae[k], c, b, o, A.invd[k],
+                                       A.omega, A.fixed[k], nullptr);
+    cluster_barrier();
+    const Dims dc = A.d[k + 1];
+    T* bc = A.b[k + 1] + rhs * dc.dofs();
+    for (long long nd = t0; nd < dc.nodes(); nd += ts)
+      restrict_node<2, T, true>(d, dc, nd, o, bc, A.fixed[k + 1]);
+    cluster_barrier();
+    res[k] = c;
+  }
+  {  // coarsest level: z = Ainv b, one warp per row
+    const int L = A.nl - 1;
+    const T* b = A.b[L] + (long long)rhs * A.nc;
+    T* z = A.z[L] + (long long)rhs * A.nc;
+    const int lane = threadIdx.x & 31;
+    for (long long row = t0 >> 5; row < A.nc; row += ts >> 5) {
+      const double v = dense_row_dot<true>(A.nc, A.Ainv + row * A.nc, b, lane);
+      if (lane == 0) z[row] = (T)v;
+    }
+    cluster_barrier();
+    res[L] = z;
+  }
+  for (int k = A.nl - 2; k >= 0; --k) {
+    const Dims d = A.d[k], dc = A.d[k + 1];
+    const long long n = d.dofs(), nodes = d.nodes();
+    const T* b = A.b[k] + rhs * n;
+    T* c = res[k];
+    T* zb = A.z[k] + rhs * n;
+    T* o = (c == zb) ? A.t[k] + rhs * n : zb;
+    for (long long nd = t0; nd < nodes; nd += ts)
+      prolong_node<2, T, true>(d, dc, nd, res[k + 1], c, A.fixed[k]);
+    cluster_barrier();
+    for (int it = 0; it < A.nu2; ++it) {
+      for (long long nd = t0; nd < nodes; nd += ts)
+        apply_node<2, T, 2, false, true>(d, nd, nullptr, nullptr, A.Ae[k], c, b, o, A.invd[k],
+                                         A.omega, A.fixed[k], nullptr);
+      cluster_barrier();
+      T* tmp = c;
+      c = o;
+      o = tmp;
+    }
+    res[k] = c;
   }
 }
 
@@ -423,6 +584,36 @@ __global__ void k_inv_diag(Dims d, const double* __restrict__ K0, const double* 
   for (int c = 0; c < DIM; ++c) {
     const long long id = DIM * node + c;
     invd[id] = (fixed[id] || !(acc[c] > 0.0)) ? 1.0 : 1.0 / acc[c];
+  }
+}
+
+// FP32 variant for coarse levels whose element matrices are stored in FP32 only.
+template <int DIM>
+__global__ void k_inv_diag32(Dims d, const float* __restrict__ Ae,
+                             const uint8_t* __restrict__ fixed, float* __restrict__ invd) {
+  pdl_prologue();
+  constexpr int NN = Elem<DIM>::NN, NE = Elem<DIM>::NE;
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= d.nodes()) return;
+  const int nnx = d.nx + 1, nny = d.ny + 1;
+  const int i = (int)(node % nnx), j = (int)((node / nnx) % nny);
+  const int k = (DIM == 3) ? (int)(node / ((long long)nnx * nny)) : 0;
+  float acc[DIM] = {};
+  for (int s = 0; s < NN; ++s) {
+    const int dx = s & 1, dy = (s >> 1) & 1, dz = (DIM == 3) ? (s >> 2) : 0;
+    const int ex = i - 1 + dx, ey = j - 1 + dy, ez = (DIM == 3) ? k - 1 + dz : 0;
+    if (ex < 0 || ex >= d.nx || ey < 0 || ey >= d.ny) continue;
+    if (DIM == 3 && (ez < 0 || ez >= d.nz)) continue;
+    const int loc = loc_of(1 - dx, 1 - dy, DIM == 3 ? 1 - dz : 0);
+    const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
+    for (int c = 0; c < DIM; ++c) {
+      const int r = loc * DIM + c;
+      acc[c] += Ae[(long long)(r * NE + r) * d.elems() + e];
+    }
+  }
+  for (int c = 0; c < DIM; ++c) {
+    const long long id = DIM * node + c;
+    invd[id] = (fixed[id] || !(acc[c] > 0.0f)) ? 1.0f : 1.0f / acc[c];
   }
 }
 
@@ -591,12 +782,74 @@ template cudaError_t launch_prolong_add<double>(const Dims&, const double*, doub
 template cudaError_t launch_prolong_add<float>(const Dims&, const float*, float*, const uint8_t*,
                                                int, const CgScalars*, cudaStream_t, int);
 
+template <typename T>
+cudaError_t launch_vcycle_tail(const TailArgs<T>& a, int nrhs, const CgScalars* sc,
+                               cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kTailCluster, nrhs);
+  cfg.blockDim = dim3(kTailThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kTailCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, k_vcycle_tail<T>, a, sc);
+}
+template cudaError_t launch_vcycle_tail<float>(const TailArgs<float>&, int, const CgScalars*,
+                                               cudaStream_t);
+template cudaError_t launch_vcycle_tail<double>(const TailArgs<double>&, int, const CgScalars*,
+                                                cudaStream_t);
+
+// Whether a cluster of kTailCluster blocks of the fused kernel fits on this device.
+cudaError_t prepare_tail_kernels() {
+  if (kTailCluster > 8) {
+    cudaError_t e = cudaFuncSetAttribute(k_vcycle_tail<float>,
+                                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_vcycle_tail<double>,
+                               cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  for (int p = 0; p < 2; ++p) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kTailCluster);
+    cfg.blockDim = dim3(kTailThreads);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kTailCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    cudaError_t e = p == 0 ? cudaOccupancyMaxActiveClusters(&clusters, k_vcycle_tail<float>, &cfg)
+                           : cudaOccupancyMaxActiveClusters(&clusters, k_vcycle_tail<double>, &cfg);
+    if (e != cudaSuccess) return e;
+    if (clusters < 1) return cudaErrorNotSupported;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_inv_diag(const Dims& d, const double* K0, const double* x, const double* Ae,
                             const uint8_t* fixed, double* invd, cudaStream_t st) {
   if (d.dim == 2)
     topo::launch(k_inv_diag<2>, blocks_for(d.nodes()), kThreads, 0, st, d, K0, x, Ae, fixed, invd);
   else
     topo::launch(k_inv_diag<3>, blocks_for(d.nodes()), kThreads, 0, st, d, K0, x, Ae, fixed, invd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inv_diag32(const Dims& d, const float* Ae, const uint8_t* fixed, float* invd,
+                              cudaStream_t st) {
+  if (d.dim == 2)
+    topo::launch(k_inv_diag32<2>, blocks_for(d.nodes()), kThreads, 0, st, d, Ae, fixed, invd);
+  else
+    topo::launch(k_inv_diag32<3>, blocks_for(d.nodes()), kThreads, 0, st, d, Ae, fixed, invd);
   return cudaGetLastError();
 }
 

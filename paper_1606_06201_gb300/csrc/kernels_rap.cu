@@ -39,10 +39,10 @@ __device__ __forceinline__ double wchild(int c, int a, int A) {
 
 // Output layout: entry-major, Ac[entry * mc + E]; thread t -> (entry = t / mc, E = t % mc), so
 // the entry (and the constants it reads) is uniform within a warp.
-template <int DIM>
-__global__ void k_rap_from_fine(Dims df, const double* __restrict__ C,
-                                const double* __restrict__ x, double* __restrict__ Ac,
-                                const double* __restrict__ g, const double* __restrict__ Dinv) {
+template <int DIM, typename T>
+__global__ void k_rap_from_fine(Dims df, const T* __restrict__ C, const T* __restrict__ x,
+                                T* __restrict__ Ac, const double* __restrict__ g,
+                                const double* __restrict__ Dinv) {
   pdl_prologue();
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM, NE2 = NE * NE;
   const int cnx = df.nx / 2, cny = df.ny / 2, cnz = DIM == 3 ? df.nz / 2 : 1;
@@ -52,13 +52,13 @@ __global__ void k_rap_from_fine(Dims df, const double* __restrict__ C,
   const int entry = (int)(t / mc);
   const long long E = t % mc;
   const int EX = (int)(E % cnx), EY = (int)((E / cnx) % cny), EZ = (int)(E / ((long long)cnx * cny));
-  double acc = 0.0;
+  T acc = T(0);
 #pragma unroll
   for (int c = 0; c < NN; ++c) {
     const int fx = 2 * EX + (c & 1), fy = 2 * EY + ((c >> 1) & 1), fz = 2 * EZ + (c >> 2);
     const long long fe = fx + (long long)df.nx * (fy + (long long)df.ny * (DIM == 3 ? fz : 0));
     acc = fma(x[fe], __ldg(C + c * NE2 + entry), acc);
-    if (g) {  // rank-one term (P_c^T g_c)_I (P_c^T g_c)_J / D_c
+    if (g) {  // FP64 solvers only (T = double)  // rank-one term (P_c^T g_c)_I (P_c^T g_c)_J / D_c
       const int I = entry / NE, J = entry % NE;
       const int A = I / DIM, al = I % DIM, B = J / DIM, be = J % DIM;
       double hI = 0.0, hJ = 0.0;
@@ -66,7 +66,7 @@ __global__ void k_rap_from_fine(Dims df, const double* __restrict__ C,
         hI = fma(wchild<DIM>(c, a, A), g[fe * NE + a * DIM + al], hI);
         hJ = fma(wchild<DIM>(c, a, B), g[fe * NE + a * DIM + be], hJ);
       }
-      acc = fma(hI * hJ, Dinv[fe], acc);
+      acc = (T)fma(hI * hJ, Dinv[fe], (double)acc);
     }
   }
   Ac[t] = acc;
@@ -75,9 +75,9 @@ __global__ void k_rap_from_fine(Dims df, const double* __restrict__ C,
 // Second coarse level straight from the finest densities: A_E = sum_f x_f C2_f over the 4^dim fine
 // elements f below E, with C2_f = W_f^T K0 W_f (W_f: composite interpolation from E's nodes to the
 // nodes of f).  Entry-major output; thread t -> (entry = t / mc, E = t % mc).
-template <int DIM>
-__global__ void k_rap2_from_fine(Dims df, const double* __restrict__ C2,
-                                 const double* __restrict__ x, double* __restrict__ Ac) {
+template <int DIM, typename T>
+__global__ void k_rap2_from_fine(Dims df, const T* __restrict__ C2, const T* __restrict__ x,
+                                 T* __restrict__ Ac) {
   pdl_prologue();
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM, NE2 = NE * NE, NF = NN * NN;
   const int cnx = df.nx / 4, cny = df.ny / 4, cnz = DIM == 3 ? df.nz / 4 : 1;
@@ -87,7 +87,7 @@ __global__ void k_rap2_from_fine(Dims df, const double* __restrict__ C2,
   const int entry = (int)(t / mc);
   const long long E = t % mc;
   const int EX = (int)(E % cnx), EY = (int)((E / cnx) % cny), EZ = (int)(E / ((long long)cnx * cny));
-  double acc = 0.0;
+  T acc = T(0);
 #pragma unroll 4
   for (int f = 0; f < NF; ++f) {
     const int c1 = f / NN, c2 = f % NN;
@@ -140,8 +140,8 @@ __global__ void k_inv_diag_l1(Dims dc, const double* __restrict__ C, const doubl
 // General Galerkin step from level matrices Af (entry-major, mf elements) to Ac (entry-major):
 // A_E = sum_c P_c^T A_c P_c with the interpolation weights W_c[a][A] tabulated in shared memory
 // (exact binary fractions) and their zeros skipped.
-template <int DIM>
-__global__ void k_rap_coarse(Dims df, const double* __restrict__ Af, double* __restrict__ Ac) {
+template <int DIM, typename TI, typename TO>
+__global__ void k_rap_coarse(Dims df, const TI* __restrict__ Af, TO* __restrict__ Ac) {
   pdl_prologue();
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM, NE2 = NE * NE;
   __shared__ float W[NN][NN][NN];  // [child][fine local node a][coarse local node A]
@@ -160,20 +160,20 @@ __global__ void k_rap_coarse(Dims df, const double* __restrict__ Af, double* __r
   const int I = entry / NE, J = entry % NE;
   const int A = I / DIM, al = I % DIM, B = J / DIM, be = J % DIM;
   const int EX = (int)(E % cnx), EY = (int)((E / cnx) % cny), EZ = (int)(E / ((long long)cnx * cny));
-  double acc = 0.0;
+  TO acc = TO(0);
   for (int c = 0; c < NN; ++c) {
     const int fx = 2 * EX + (c & 1), fy = 2 * EY + ((c >> 1) & 1), fz = 2 * EZ + (c >> 2);
     const long long fe = fx + (long long)df.nx * (fy + (long long)df.ny * (DIM == 3 ? fz : 0));
     for (int a = 0; a < NN; ++a) {
       const float wa = W[c][a][A];
       if (wa == 0.0f) continue;
-      double s = 0.0;
+      TO s = TO(0);
       for (int b = 0; b < NN; ++b) {
         const float wb = W[c][b][B];
         if (wb == 0.0f) continue;
-        s = fma(__ldg(Af + (long long)((a * DIM + al) * NE + b * DIM + be) * mf + fe), (double)wb, s);
+        s = fma((TO)__ldg(Af + (long long)((a * DIM + al) * NE + b * DIM + be) * mf + fe), (TO)wb, s);
       }
-      acc = fma((double)wa, s, acc);
+      acc = fma((TO)wa, s, acc);
     }
   }
   Ac[t] = acc;
@@ -238,8 +238,10 @@ constexpr double kPivotFloor = 1e-13;
 // In-place Cholesky A = L L^T of a dense SPD matrix in one block (right-looking), then L^T is
 // mirrored into the strict upper triangle.  info = 0, or k+1 if the k-th diagonal entry is not
 // positive or a pivot is not finite.
-__global__ void __launch_bounds__(1024) k_cholesky(int n, double* A, double* diag0, int* info) {
+__global__ void __launch_bounds__(1024) k_cholesky(int n, double* A, double* diag0, int* info,
+                                                  const int* only_if) {
   pdl_prologue();
+  if (only_if && !*only_if) return;  // Newton-Schulz inverse already accepted
   __shared__ int bad;
   if (threadIdx.x == 0) bad = 0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) diag0[k] = A[(long long)k * n + k];
@@ -282,10 +284,11 @@ inline int inv_warps(int n) {
 }
 
 __global__ void __launch_bounds__(kInvWarps * 32) k_chol_inverse(int n, const double* __restrict__ LU,
-                                                                 double* Ainv, const int* info) {
+                                                                 double* Ainv, const int* info,
+                                                                 const int* only_if) {
   pdl_prologue();
   extern __shared__ double wsh[];  // [warps per block][n]
-  if (*info) return;
+  if (*info || (only_if && !*only_if)) return;
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int j = blockIdx.x * (blockDim.x >> 5) + wib;
   if (j >= n) return;
@@ -315,8 +318,10 @@ __global__ void __launch_bounds__(kInvWarps * 32) k_chol_inverse(int n, const do
 }
 
 // Cholesky in shared memory for small n (n * n doubles fit in one block's shared memory).
-__global__ void __launch_bounds__(1024) k_cholesky_smem(int n, double* A, double* diag0, int* info) {
+__global__ void __launch_bounds__(1024) k_cholesky_smem(int n, double* A, double* diag0, int* info,
+                                                       const int* only_if) {
   pdl_prologue();
+  if (only_if && !*only_if) return;  // Newton-Schulz inverse already accepted
   extern __shared__ double S[];
   __shared__ int bad;
   const long long nn = (long long)n * n;
@@ -351,6 +356,100 @@ __global__ void __launch_bounds__(1024) k_cholesky_smem(int n, double* A, double
   }
 }
 
+// Small coarsest matrices (n <= kGjMaxN) are inverted without an FP64 factorisation, whose n
+// dependent steps run at the FP64 rate of a single SM: a Gauss-Jordan inverse in FP32 in one
+// block gives X0, and Newton-Schulz steps X <- X (2I - A X) in FP64, each two n x n products
+// spread over n blocks, square the error ||I - A X|| until it is at FP64 rounding.  The last
+// step checks ||I - A X||_max <= kNsTol before its product; above it (or not finite) the flag
+// is set and the Cholesky path below recomputes the inverse from A.
+constexpr int kGjMaxN = 128;
+constexpr int kNsSteps = 4;
+constexpr double kNsTol = 1e-7;
+
+// Gauss-Jordan step k with pivot p maps a_kk -> 1/p, a_kj -> a_kj/p, a_ik -> -a_ik/p and
+// a_ij -> a_ij - a_ik a_kj / p (old values on the right); after n steps the array holds A^{-1}.
+// No pivoting: the pivots of an SPD matrix are its Schur-complement diagonals.  Thread (warp w,
+// lane l) keeps the 4 x 4 entries (w + 32a, l + 32b) in registers; the pivot row and column of
+// the next step are written to double-buffered shared arrays during a step, so one barrier per
+// step suffices.  Also clears info[0] and the Newton-Schulz flag.
+__global__ void __launch_bounds__(1024) k_gj32_start(int n, const double* __restrict__ A,
+                                                     double* __restrict__ X, int* info,
+                                                     int* ns_bad) {
+  pdl_prologue();
+  __shared__ float Pb[2][kGjMaxN];  // pivot row (values before the step), by step parity
+  __shared__ float Cb[2][kGjMaxN];  // pivot column (values before the step), by step parity
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    *info = 0;
+    *ns_bad = 0;
+  }
+  float r[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = w + 32 * a, j = l + 32 * b;
+      const bool in = i < n && j < n;
+      r[a][b] = in ? (float)A[(long long)i * n + j] : 0.0f;
+      if (in && j == 0) Cb[0][i] = r[a][b];
+      if (in && i == 0) Pb[0][j] = r[a][b];
+    }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    const int cur = k & 1;
+    float* Pn = Pb[cur ^ 1];
+    float* Cn = Cb[cur ^ 1];
+    const float rp = 1.0f / Pb[cur][k];
+    float pj[4], fi[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) pj[b] = (l + 32 * b < n) ? Pb[cur][l + 32 * b] : 0.0f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) fi[a] = (w + 32 * a < n) ? Cb[cur][w + 32 * a] * rp : 0.0f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = w + 32 * a, j = l + 32 * b;
+        if (i < n && j < n) {
+          float v;
+          if (i == k) v = (j == k) ? rp : r[a][b] * rp;
+          else if (j == k) v = -fi[a];
+          else v = fmaf(-fi[a], pj[b], r[a][b]);
+          r[a][b] = v;
+          if (j == k + 1) Cn[i] = v;
+          if (i == k + 1) Pn[j] = v;
+        }
+      }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = w + 32 * a, j = l + 32 * b;
+      if (i < n && j < n) X[(long long)i * n + j] = (double)r[a][b];
+    }
+}
+
+// C = alpha I + beta L R for n x n matrices: block i computes row i, thread j column j.  check:
+// set *bad if some |C_ij - delta_ij| > kNsTol or is not finite (C = 2I - A X gives I - A X).
+__global__ void __launch_bounds__(kGjMaxN) k_ns_gemm(int n, const double* __restrict__ L,
+                                                     const double* __restrict__ R,
+                                                     double* __restrict__ C, double alpha,
+                                                     double beta, int check, int* bad) {
+  pdl_prologue();
+  __shared__ double Li[kGjMaxN];
+  const int i = blockIdx.x, j = threadIdx.x;
+  for (int k = j; k < n; k += blockDim.x) Li[k] = L[(long long)i * n + k];
+  __syncthreads();
+  if (j >= n) return;
+  double acc = 0.0;
+  for (int k = 0; k < n; ++k) acc = fma(Li[k], R[(long long)k * n + j], acc);
+  const double c = fma(beta, acc, i == j ? alpha : 0.0);
+  C[(long long)i * n + j] = c;
+  if (check && !(fabs(c - (i == j ? 1.0 : 0.0)) <= kNsTol)) atomicOr(bad, 1);
+}
+
 // z = A^{-1} b: one warp per row, FP64 accumulation whatever the vector type.
 template <typename T>
 __global__ void k_dense_solve(int n, const double* __restrict__ Ainv, const T* __restrict__ b,
@@ -363,39 +462,46 @@ __global__ void k_dense_solve(int n, const double* __restrict__ Ainv, const T* _
   if (warp >= n) return;
   b += (long long)rhs * n;
   z += (long long)rhs * n;
-  const double* row = Ainv + (long long)warp * n;
-  double s = 0.0;
-  for (int k = lane; k < n; k += 32) s = fma(row[k], (double)b[k], s);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const double s = dense_row_dot<false>(n, Ainv + (long long)warp * n, b, lane);
   if (lane == 0) z[warp] = (T)s;
 }
 
 }  // namespace
 
-cudaError_t launch_rap_from_fine(const Dims& fine, const double* C, const double* x, double* Ac,
-                                 cudaStream_t st, const double* g, const double* Dinv) {
+template <typename T>
+cudaError_t launch_rap_from_fine(const Dims& fine, const T* C, const T* x, T* Ac, cudaStream_t st,
+                                 const double* g, const double* Dinv) {
   const int ne = fine.dim == 2 ? 8 : 24;
   const long long mc = fine.elems() / (fine.dim == 2 ? 4 : 8);
   const long long total = mc * ne * ne;
   if (fine.dim == 2)
-    topo::launch(k_rap_from_fine<2>, blocks_for(total), kThreads, 0, st, fine, C, x, Ac, g, Dinv);
+    topo::launch(k_rap_from_fine<2, T>, blocks_for(total), kThreads, 0, st, fine, C, x, Ac, g, Dinv);
   else
-    topo::launch(k_rap_from_fine<3>, blocks_for(total), kThreads, 0, st, fine, C, x, Ac, g, Dinv);
+    topo::launch(k_rap_from_fine<3, T>, blocks_for(total), kThreads, 0, st, fine, C, x, Ac, g, Dinv);
   return cudaGetLastError();
 }
+template cudaError_t launch_rap_from_fine<double>(const Dims&, const double*, const double*,
+                                                  double*, cudaStream_t, const double*,
+                                                  const double*);
+template cudaError_t launch_rap_from_fine<float>(const Dims&, const float*, const float*, float*,
+                                                 cudaStream_t, const double*, const double*);
 
-cudaError_t launch_rap2_from_fine(const Dims& fine, const double* C2, const double* x, double* Ac,
+template <typename T>
+cudaError_t launch_rap2_from_fine(const Dims& fine, const T* C2, const T* x, T* Ac,
                                   cudaStream_t st) {
   const int ne = fine.dim == 2 ? 8 : 24;
   const long long mc = fine.elems() / (fine.dim == 2 ? 16 : 64);
   const long long total = mc * ne * ne;
   if (fine.dim == 2)
-    topo::launch(k_rap2_from_fine<2>, blocks_for(total), kThreads, 0, st, fine, C2, x, Ac);
+    topo::launch(k_rap2_from_fine<2, T>, blocks_for(total), kThreads, 0, st, fine, C2, x, Ac);
   else
-    topo::launch(k_rap2_from_fine<3>, blocks_for(total), kThreads, 0, st, fine, C2, x, Ac);
+    topo::launch(k_rap2_from_fine<3, T>, blocks_for(total), kThreads, 0, st, fine, C2, x, Ac);
   return cudaGetLastError();
 }
+template cudaError_t launch_rap2_from_fine<double>(const Dims&, const double*, const double*,
+                                                   double*, cudaStream_t);
+template cudaError_t launch_rap2_from_fine<float>(const Dims&, const float*, const float*, float*,
+                                                  cudaStream_t);
 
 cudaError_t launch_inv_diag_l1(const Dims& coarse1, const double* C, const double* xf,
                                const uint8_t* fixed, double* invd, cudaStream_t st) {
@@ -406,16 +512,23 @@ cudaError_t launch_inv_diag_l1(const Dims& coarse1, const double* C, const doubl
   return cudaGetLastError();
 }
 
-cudaError_t launch_rap_coarse(const Dims& fine, const double* Af, double* Ac, cudaStream_t st) {
+template <typename TI, typename TO>
+cudaError_t launch_rap_coarse(const Dims& fine, const TI* Af, TO* Ac, cudaStream_t st) {
   const int ne = fine.dim == 2 ? 8 : 24;
   const long long mc = fine.elems() / (fine.dim == 2 ? 4 : 8);
   const long long total = mc * ne * ne;
   if (fine.dim == 2)
-    topo::launch(k_rap_coarse<2>, blocks_for(total), kThreads, 0, st, fine, Af, Ac);
+    topo::launch(k_rap_coarse<2, TI, TO>, blocks_for(total), kThreads, 0, st, fine, Af, Ac);
   else
-    topo::launch(k_rap_coarse<3>, blocks_for(total), kThreads, 0, st, fine, Af, Ac);
+    topo::launch(k_rap_coarse<3, TI, TO>, blocks_for(total), kThreads, 0, st, fine, Af, Ac);
   return cudaGetLastError();
 }
+template cudaError_t launch_rap_coarse<double, double>(const Dims&, const double*, double*,
+                                                       cudaStream_t);
+template cudaError_t launch_rap_coarse<float, float>(const Dims&, const float*, float*,
+                                                     cudaStream_t);
+template cudaError_t launch_rap_coarse<float, double>(const Dims&, const float*, double*,
+                                                      cudaStream_t);
 
 cudaError_t launch_assemble_dense(const Dims& d, const double* K0, const double* x,
                                   const double* Ae, const uint8_t* fixed, double* A,
@@ -434,28 +547,55 @@ cudaError_t launch_assemble_dense(const Dims& d, const double* K0, const double*
 }
 
 cudaError_t prepare_coarse_kernels(int n) {
-  const size_t smem = (size_t)n * n * sizeof(double);
-  if (smem <= 200 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_cholesky_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024);
-    if (e != cudaSuccess) return e;
-  }
+  // the largest sizes, so that solvers of other sizes keep working
+  (void)n;
+  cudaError_t e =
+      cudaFuncSetAttribute(k_cholesky_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_chol_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               200 * 1024);
 }
 
-cudaError_t launch_cholesky_inverse(int n, double* A, double* Ainv, int* info, cudaStream_t st) {
+size_t coarse_scratch_doubles(int n) { return n <= kGjMaxN ? 2 * (size_t)n * n : 0; }
+
+cudaError_t launch_cholesky_inverse(int n, double* A, double* Ainv, int* info, cudaStream_t st,
+                                    double* scratch, int* ns_bad, bool allow_ns) {
+  const int* only_if = nullptr;
+  if (allow_ns && n <= kGjMaxN && scratch && ns_bad) {
+    // X ping-pongs between Ainv and T so that the last product lands in Ainv (kNsSteps even)
+    static_assert(kNsSteps % 2 == 0, "Newton-Schulz ping-pong ends in Ainv");
+    double* R = scratch;
+    double* T = scratch + (size_t)n * n;
+    topo::launch(k_gj32_start, 1, 1024, 0, st, n, (const double*)A, Ainv, info, ns_bad);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    double* X = Ainv;
+    double* Xn = T;
+    for (int it = 0; it < kNsSteps; ++it) {
+      const int last = (it == kNsSteps - 1) ? 1 : 0;
+      topo::launch(k_ns_gemm, n, kGjMaxN, 0, st, n, (const double*)A, (const double*)X, R, 2.0,
+                   -1.0, last, ns_bad);
+      topo::launch(k_ns_gemm, n, kGjMaxN, 0, st, n, (const double*)X, (const double*)R, Xn, 0.0,
+                   1.0, 0, ns_bad);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      double* t = X;
+      X = Xn;
+      Xn = t;
+    }
+    only_if = ns_bad;  // the Cholesky kernels below run only if the check failed
+  }
   const size_t smem = (size_t)n * n * sizeof(double);
   // row 0 of Ainv holds the original diagonal until the inverse overwrites it
   if (smem <= 200 * 1024)
-    topo::launch(k_cholesky_smem, 1, 1024, smem, st, n, A, Ainv, info);
+    topo::launch(k_cholesky_smem, 1, 1024, smem, st, n, A, Ainv, info, only_if);
   else
-    topo::launch(k_cholesky, 1, 1024, 0, st, n, A, Ainv, info);
+    topo::launch(k_cholesky, 1, 1024, 0, st, n, A, Ainv, info, only_if);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int wpb = inv_warps(n);
   const size_t wsm = (size_t)wpb * n * sizeof(double);
-  topo::launch(k_chol_inverse, (n + wpb - 1) / wpb, wpb * 32, wsm, st, n, A, Ainv, info);
+  topo::launch(k_chol_inverse, (n + wpb - 1) / wpb, wpb * 32, wsm, st, n, A, Ainv, info, only_if);
   return cudaGetLastError();
 }
 

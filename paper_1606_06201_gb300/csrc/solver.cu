@@ -5,11 +5,11 @@
 // The library runs on a private non-blocking stream.  Each call orders itself after the caller's
 // stream (topo_set_stream, default the legacy stream) with an event and makes the caller's stream
 // wait for its work on exit, so device pointers from the caller may be used on either side.
-// One CG iteration is captured once per solver as the body of a conditional while node; a
-// one-thread kernel at the end of the body clears the condition when every right-hand side has
-// stopped, so a whole solve is one graph launch and one read-back of the scalars.  The kernels
-// of a right-hand side whose recurrence has stopped return at once.  Profiling runs (and
-// TOPO_NO_LOOP=1) use a graph of a block of iterations that the host replays instead.
+// A block of CG iterations is captured once per solver into a CUDA graph that the host replays,
+// reading the scalars back once per block.  The kernels of a right-hand side whose recurrence has
+// stopped return at once.  With topo_set_graph_mode(s, 1) one iteration is instead the body of a
+// conditional while node, and a one-thread kernel at the end of the body clears the condition when
+// every right-hand side has stopped: a whole solve is then one graph launch and one read-back.
 #include <cmath>
 #include <cstdlib>
 #include <cstdio>
@@ -36,14 +36,6 @@ bool pdl_enabled() {
     return v && v[0] == '1';
   }();
   return on;
-}
-
-bool loop_disabled() {
-  static const bool off = [] {
-    const char* v = std::getenv("TOPO_NO_LOOP");
-    return v && v[0] == '1';
-  }();
-  return off;
 }
 
 topo_status cuda_status(cudaError_t e, const char* what) {
@@ -217,8 +209,7 @@ struct Prec<float> {
   static const float* invd(const Level& l) { return l.invd32; }
 };
 
-// Operator application on level k (mode as launch_apply): the warp-sweep Q1 kernels on the 2D
-// finest level, the generic element-matrix kernels elsewhere.
+// Arrow vector w of a level and the fine-level rank-one data in the V-cycle precision.
 template <typename TV>
 const TV* arrow_w(const Level& l);
 template <>
@@ -240,6 +231,15 @@ struct ArrowFine<float> {
   static const float* Dinv(topo_solver* s) { return s->Dinv32; }
   static float* se(topo_solver* s) { return s->se32; }
 };
+
+// External event-record node around a profiled kernel (kind, slot of the captured iteration); a
+// plain record during capture would only track dependencies.
+topo_status prof_mark(topo_solver* s, int kind, int end) {
+  if (!s->profiling || s->prof_slot < 0 || !((s->prof_mask >> kind) & 1u)) return TOPO_OK;
+  const size_t i = ((size_t)kind * s->graph_iters + s->prof_slot) * 2 + end;
+  TOPO_CUDA(cudaEventRecordWithFlags(s->prof_ev[i], s->st, cudaEventRecordExternal));
+  return TOPO_OK;
+}
 
 // Operator application on level k (mode as launch_apply): the warp-sweep Q1 kernels on the 2D
 // finest level, the matrix-free first coarse level in mixed precision, the Z operator (element
@@ -302,6 +302,22 @@ topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* 
 }
 
 // One V-cycle at level k with right-hand side b (Algorithm MG, function mgm, from z = 0).
+// First level of the fused deep part of the V-cycle in precision TV, or -1: 2D K systems with
+// Jacobi smoothing, element matrices in TV on every fused level above the coarsest, at most
+// kTailNodes nodes on the first fused level and kTailMax fused levels.
+template <typename TV>
+int tail_level(const topo_solver* s) {
+  if (!s->tail_on || s->dim != 2 || s->arrow || s->desc.smoother != 0) return -1;
+  const int last = s->nlev - 1;
+  for (int k = 1; k < last; ++k) {
+    if (s->L[k].d.nodes() > kTailNodes || s->nlev - k > kTailMax) continue;
+    bool ok = true;
+    for (int j = k; j < last; ++j) ok = ok && Prec<TV>::Ae(s->L[j]) && Prec<TV>::invd(s->L[j]);
+    if (ok) return k;
+  }
+  return -1;
+}
+
 // fuse_beta: the last smoothing sweep of the finest level also forms r~^T y~ and beta (the CG
 // direction update then needs only the p kernel).
 template <typename TV>
@@ -318,6 +334,30 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
   TV* cur = zk;
   TV* oth = (TV*)lv.t;
   const int nu1 = s->desc.nu1, nu2 = s->desc.nu2;
+  if (k == tail_level<TV>(s)) {  // this level and all below in one cluster launch
+    TailArgs<TV> a = {};
+    a.nl = s->nlev - k;
+    a.nu1 = nu1;
+    a.nu2 = nu2;
+    a.nc = s->nc;
+    a.omega = (TV)s->desc.omega;
+    a.Ainv = s->Ainv;
+    for (int j = 0; j < a.nl; ++j) {
+      Level& l = s->L[k + j];
+      a.d[j] = l.d;
+      a.Ae[j] = Prec<TV>::Ae(l);
+      a.invd[j] = Prec<TV>::invd(l);
+      a.fixed[j] = l.fixed;
+      a.b[j] = j == 0 ? const_cast<TV*>(b) : (TV*)l.b;
+      a.z[j] = (TV*)l.z;
+      a.t[j] = (TV*)l.t;
+    }
+    TOPO_CUDA(launch_vcycle_tail<TV>(a, nrhs, sc, s->st));
+    // the iterate ends where the unfused cycle leaves it: one swap per plain sweep
+    const int swaps = (nu1 >= 1 ? nu1 - 1 : 0) + nu2;
+    *result = (swaps % 2 == 0) ? cur : oth;
+    return TOPO_OK;
+  }
   if (lv.lam_dev) {  // Chebyshev smoothing, the same polynomial before and after the correction
     const long long nv = lv.n;
     const TV* inv = Prec<TV>::invd(lv);
@@ -345,28 +385,48 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
     *result = cur;
     return TOPO_OK;
   }
+  const bool fine = (k == 0);
+  bool sweep_timed = false;  // profiling: the first plain sweep of the finest level
   if (nu1 >= 1) {
     TOPO_TRY(apply_level<TV>(s, k, 3, cur, b, cur, sc));
     for (int it = 1; it < nu1; ++it) {
+      const bool t = fine && !sweep_timed;
+      if (t) TOPO_TRY(prof_mark(s, 1, 0));
       TOPO_TRY(apply_level<TV>(s, k, 2, cur, b, oth, sc));
+      if (t) TOPO_TRY(prof_mark(s, 1, 1));
+      sweep_timed = sweep_timed || t;
       std::swap(cur, oth);
     }
   } else {
     TOPO_CUDA(cudaMemsetAsync(cur, 0, sizeof(TV) * s->vlen(k) * nrhs, s->st));
   }
+  if (fine) TOPO_TRY(prof_mark(s, 2, 0));
   TOPO_TRY(apply_level<TV>(s, k, 1, cur, b, oth, sc));
+  if (fine) TOPO_TRY(prof_mark(s, 2, 1));
   Level& lc = s->L[k + 1];
+  if (fine) TOPO_TRY(prof_mark(s, 3, 0));
   TOPO_CUDA(launch_restrict<TV>(lv.d, oth, (TV*)lc.b, lc.fixed, nrhs, sc, s->st, s->arrow));
+  if (fine) TOPO_TRY(prof_mark(s, 3, 1));
   TV* zc = nullptr;
+  const int sub_kind = (k == 0) ? 6 : (k == 1 ? 7 : -1);  // levels >= 1, levels >= 2
+  if (sub_kind > 0) TOPO_TRY(prof_mark(s, sub_kind, 0));
   TOPO_TRY(vcycle<TV>(s, k + 1, (const TV*)lc.b, &zc, sc, false));
+  if (sub_kind > 0) TOPO_TRY(prof_mark(s, sub_kind, 1));
+  if (fine) TOPO_TRY(prof_mark(s, 4, 0));
   TOPO_CUDA(launch_prolong_add<TV>(lv.d, zc, cur, lv.fixed, nrhs, sc, s->st, s->arrow));
+  if (fine) TOPO_TRY(prof_mark(s, 4, 1));
   for (int it = 0; it < nu2; ++it) {
-    if (fuse_beta && k == 0 && it == nu2 - 1)
+    if (fuse_beta && k == 0 && it == nu2 - 1) {
       TOPO_CUDA(launch_q1_smooth_beta<TV>(lv.d.nx, lv.d.ny, s->q1, Prec<TV>::x(s), cur, b, oth,
                                           (TV)s->desc.omega, lv.fixed, nrhs, s->r, s->partials,
                                           s->counters, const_cast<CgScalars*>(sc), s->st));
-    else
+    } else {
+      const bool t = fine && !sweep_timed;
+      if (t) TOPO_TRY(prof_mark(s, 1, 0));
       TOPO_TRY(apply_level<TV>(s, k, 2, cur, b, oth, sc));
+      if (t) TOPO_TRY(prof_mark(s, 1, 1));
+      sweep_timed = sweep_timed || t;
+    }
     std::swap(cur, oth);
   }
   *result = cur;
@@ -388,9 +448,8 @@ template <typename TV>
 topo_status cg_iteration(topo_solver* s, int slot, double tol, int max_iter) {
   Level& l0 = s->L[0];
   const long long n = s->ncg();
-  // external event-record nodes: a plain record during capture only tracks dependencies
-  if (s->profiling)
-    TOPO_CUDA(cudaEventRecordWithFlags(s->prof_ev[2 * slot], s->st, cudaEventRecordExternal));
+  s->prof_slot = s->profiling ? slot : -1;
+  TOPO_TRY(prof_mark(s, 0, 0));
   if (s->arrow) {
     TOPO_TRY(apply_level<double>(s, 0, 0, s->p, nullptr, s->q, s->sc));
     TOPO_CUDA(launch_cg_alpha(n, 1, s->p, s->q, s->partials, s->counters, s->sc, s->st));
@@ -401,21 +460,23 @@ topo_status cg_iteration(topo_solver* s, int slot, double tol, int max_iter) {
     TOPO_CUDA(launch_apply_dot_fine(l0.d, s->K0, s->x, s->p, s->q, l0.fixed, s->nrhs, s->partials,
                                     s->counters, s->sc, s->st));
   }
-  if (s->profiling)
-    TOPO_CUDA(cudaEventRecordWithFlags(s->prof_ev[2 * slot + 1], s->st, cudaEventRecordExternal));
+  TOPO_TRY(prof_mark(s, 0, 1));
   TV* rv = std::is_same<TV, double>::value ? nullptr : (TV*)s->rv;
   TOPO_CUDA(launch_cg_update<TV>(n, s->nrhs, s->z, s->r, s->p, s->q, rv, s->partials, s->counters,
                                  s->sc, tol, max_iter, s->st));
   void* y = nullptr;
   const bool fuse = s->q1_ok && !s->arrow && s->desc.nu2 >= 1 && !s->desc.flexible &&
                     s->nlev >= 2 && s->desc.smoother == 0;
+  TOPO_TRY(prof_mark(s, 5, 0));
   TOPO_TRY(precondition<TV>(s, s->sc, &y, fuse));
+  TOPO_TRY(prof_mark(s, 5, 1));
   s->yv = y;
   if (fuse)
     TOPO_CUDA(launch_cg_p<TV>(n, s->nrhs, (const TV*)y, s->p, (TV*)s->yold, 0, s->sc, s->st));
   else
     TOPO_CUDA(launch_cg_direction<TV>(n, s->nrhs, s->r, (const TV*)y, s->p, (TV*)s->yold,
                                       s->desc.flexible, s->partials, s->counters, s->sc, s->st));
+  s->prof_slot = -1;
   return TOPO_OK;
 }
 
@@ -559,7 +620,7 @@ topo_status solve_impl(topo_solver* s, const double* b, double* u, double tol, i
     s->setup_tol[ux] = tol;
   }
   // Programmatic-launch attributes stay out of conditional bodies.
-  const bool use_loop = !s->profiling && !s->no_loop && !pdl_enabled() && !loop_disabled();
+  const bool use_loop = s->graph_mode == 1 && !s->profiling && !s->no_loop && !pdl_enabled();
   if (use_loop && (!s->loop || s->loop_tol != tol)) {
     topo_status ls = capture_loop<TV>(s, tol, max_iter);
     if (ls != TOPO_OK) {  // conditional graphs unavailable: fall back to blocks of iterations
@@ -608,16 +669,17 @@ topo_status solve_impl(topo_solver* s, const double* b, double* u, double tol, i
     }
     if (s->profiling) {
       const int ran = std::min(iter_after - iter_before, s->graph_iters);
-      for (int slot = 0; slot < ran; ++slot) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, s->prof_ev[2 * slot], s->prof_ev[2 * slot + 1]) ==
-            cudaSuccess) {
-          s->prof_ms += ms;
-          s->prof_count += 1;
-        } else {
-          cudaGetLastError();  // timing unavailable: leave no sticky error behind
+      for (int kind = 0; kind < topo_solver::kProfKinds; ++kind)
+        for (int slot = 0; slot < ran; ++slot) {
+          const size_t i = ((size_t)kind * s->graph_iters + slot) * 2;
+          float ms = 0.f;
+          if (cudaEventElapsedTime(&ms, s->prof_ev[i], s->prof_ev[i + 1]) == cudaSuccess) {
+            s->prof_ms[kind] += ms;
+            s->prof_count[kind] += 1;
+          } else {
+            cudaGetLastError();  // kind not in this graph or timing unavailable: no sticky error
+          }
         }
-      }
     }
     iter_before = iter_after;
   }
@@ -652,6 +714,7 @@ topo_status enqueue_build(topo_solver* s) {
   cudaStream_t st = s->st;
   const long long m = s->L[0].m;
   const int ne2 = s->ne * s->ne;
+  TOPO_CUDA(cudaMemsetAsync(s->info, 0, 4 * sizeof(int), st));
   TOPO_CUDA(launch_check_positive(s->x, m, s->info + 1, st));
   if (mixed) TOPO_CUDA(launch_convert_d2f(s->x, s->x32, m, st));
   if (s->arrow && mixed) {
@@ -659,14 +722,28 @@ topo_status enqueue_build(topo_solver* s) {
     TOPO_CUDA(launch_convert_d2f(s->Dinv, s->Dinv32, m, st));
   }
   for (int k = 1; k < nl; ++k) {
+    Level& lk = s->L[k];
+    // FP32 hierarchy: FP32 products into Ae32 below the coarsest level, FP64 into Ae on it
+    const bool f32 = s->h32 && !lk.Ae;
     if (k == 1) {
-      if (s->L[1].Ae)  // stored unless the first coarse level is applied matrix-free
-        TOPO_CUDA(launch_rap_from_fine(s->L[0].d, s->C, s->x, s->L[1].Ae, st,
-                                       s->arrow ? s->g : nullptr, s->arrow ? s->Dinv : nullptr));
+      if (f32 && lk.Ae32)
+        TOPO_CUDA(launch_rap_from_fine<float>(s->L[0].d, s->C32, s->x32, lk.Ae32, st));
+      else if (lk.Ae)  // stored unless the first coarse level is applied matrix-free
+        TOPO_CUDA(launch_rap_from_fine<double>(s->L[0].d, s->C, s->x, lk.Ae, st,
+                                               s->arrow ? s->g : nullptr,
+                                               s->arrow ? s->Dinv : nullptr));
     } else if (k == 2 && s->C2) {
-      TOPO_CUDA(launch_rap2_from_fine(s->L[0].d, s->C2, s->x, s->L[2].Ae, st));
+      if (f32)
+        TOPO_CUDA(launch_rap2_from_fine<float>(s->L[0].d, s->C2f, s->x32, lk.Ae32, st));
+      else
+        TOPO_CUDA(launch_rap2_from_fine<double>(s->L[0].d, s->C2, s->x, lk.Ae, st));
+    } else if (s->h32) {
+      if (f32)
+        TOPO_CUDA((launch_rap_coarse<float, float>(s->L[k - 1].d, s->L[k - 1].Ae32, lk.Ae32, st)));
+      else
+        TOPO_CUDA((launch_rap_coarse<float, double>(s->L[k - 1].d, s->L[k - 1].Ae32, lk.Ae, st)));
     } else {
-      TOPO_CUDA(launch_rap_coarse(s->L[k - 1].d, s->L[k - 1].Ae, s->L[k].Ae, st));
+      TOPO_CUDA((launch_rap_coarse<double, double>(s->L[k - 1].d, s->L[k - 1].Ae, lk.Ae, st)));
     }
     if (s->arrow)
       TOPO_CUDA(launch_restrict<double>(s->L[k - 1].d, s->L[k - 1].w, s->L[k].w, s->L[k].fixed, 1,
@@ -674,6 +751,10 @@ topo_status enqueue_build(topo_solver* s) {
   }
   for (int k = 0; k < nl - 1; ++k) {
     Level& lv = s->L[k];
+    if (k >= 1 && !lv.Ae && lv.Ae32) {  // FP32 hierarchy level: FP32 diagonal only
+      TOPO_CUDA(launch_inv_diag32(lv.d, lv.Ae32, lv.fixed, lv.invd32, st));
+      continue;
+    }
     if (k == 1 && !lv.Ae)
       TOPO_CUDA(launch_inv_diag_l1(lv.d, s->C, s->x, lv.fixed, lv.invd, st));
     else if (!(s->arrow && k == 0))  // the IP driver writes the finest diagonal of Z
@@ -705,7 +786,10 @@ topo_status enqueue_build(topo_solver* s) {
                                   s->Adense, st, 0, s->arrow ? lc.w : nullptr, s->zll,
                                   (s->arrow && fine_coarsest) ? s->g : nullptr,
                                   (s->arrow && fine_coarsest) ? s->Dinv : nullptr));
-  TOPO_CUDA(launch_cholesky_inverse(s->nc + (s->arrow ? 1 : 0), s->Adense, s->Ainv, s->info, st));
+  // K systems: Newton-Schulz inverse for small coarsest levels; IP systems keep the modified
+  // Cholesky, whose pivot floor guards the nearly singular Schur complement of the multiplier.
+  TOPO_CUDA(launch_cholesky_inverse(s->nc + (s->arrow ? 1 : 0), s->Adense, s->Ainv, s->info, st,
+                                    s->Ascratch, s->info + 2, !s->arrow && s->Ascratch));
   return TOPO_OK;
 }
 
@@ -784,6 +868,10 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   s->q1_ok = (s->dim == 2) && q1_coefficients(d->E, d->nu, K0.data(), s->q1) && !d->generic_kernels;
   s->l1_free = (s->dim == 2) && !arrow && s->prec == TOPO_MIXED && s->nlev >= 3 &&
                !d->generic_kernels;
+  // The V-cycle of a mixed solver reads FP32 coarse matrices only, so they are computed in FP32
+  // (Galerkin products of FP32 inputs) unless a build-time power iteration needs FP64 operators;
+  // the coarsest matrix is still accumulated and factored in FP64.
+  s->h32 = !arrow && s->prec == TOPO_MIXED && d->smoother == 0 && !d->omega_auto;
   std::vector<float> K0f(K0.begin(), K0.end()), C32(C.begin(), C.end());
   TOPO_TRY(s->alloc(&s->K0, ne * ne));
   TOPO_TRY(s->alloc(&s->K0f, ne * ne));
@@ -792,6 +880,11 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   if (!C2.empty()) {
     TOPO_TRY(s->alloc(&s->C2, C2.size()));
     TOPO_CUDA(cudaMemcpy(s->C2, C2.data(), sizeof(double) * C2.size(), cudaMemcpyHostToDevice));
+    if (s->h32) {
+      std::vector<float> C2f(C2.begin(), C2.end());
+      TOPO_TRY(s->alloc(&s->C2f, C2f.size()));
+      TOPO_CUDA(cudaMemcpy(s->C2f, C2f.data(), sizeof(float) * C2f.size(), cudaMemcpyHostToDevice));
+    }
   }
   TOPO_CUDA(cudaMemcpy(s->K0, K0.data(), sizeof(double) * ne * ne, cudaMemcpyHostToDevice));
   TOPO_CUDA(cudaMemcpy(s->K0f, K0f.data(), sizeof(float) * ne * ne, cudaMemcpyHostToDevice));
@@ -816,7 +909,8 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
     const long long vl = lv.n + (arrow ? 2 : 0);
     if (k >= 1) {
       const bool l1_matrix_free = (k == 1 && s->l1_free);
-      if (!l1_matrix_free) TOPO_TRY(s->alloc(&lv.Ae, lv.m * ne * ne));
+      // FP32 hierarchy: FP64 matrices on the coarsest level only
+      if (!l1_matrix_free && (!s->h32 || coarsest)) TOPO_TRY(s->alloc(&lv.Ae, lv.m * ne * ne));
       if (s->prec == TOPO_MIXED && !coarsest && !l1_matrix_free)
         TOPO_TRY(s->alloc(&lv.Ae32, lv.m * ne * ne));
     }
@@ -852,9 +946,14 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   s->nc = (int)lc.n;
   const size_t na = (size_t)s->nc + (arrow ? 1 : 0);
   TOPO_CUDA(prepare_coarse_kernels((int)na));
+  s->tail_ok = prepare_tail_kernels() == cudaSuccess;  // a cluster of the fused kernel fits
+  cudaGetLastError();
+  s->tail_on = s->tail_ok;
   TOPO_TRY(s->alloc(&s->Adense, na * na));
   TOPO_TRY(s->alloc(&s->Ainv, na * na));
-  TOPO_TRY(s->alloc(&s->info, 2));
+  TOPO_TRY(s->alloc(&s->info, 4));
+  if (!arrow && coarse_scratch_doubles((int)na))
+    TOPO_TRY(s->alloc(&s->Ascratch, coarse_scratch_doubles((int)na)));
   TOPO_TRY(s->alloc(&s->pw_est, 2));
   // densities and CG vectors (IP systems: trailing lambda entry, padded to an even length)
   const long long m = s->L[0].m;
@@ -890,7 +989,7 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   TOPO_TRY(s->alloc(&s->dots, nrhs));
   TOPO_CUDA(cudaMallocHost((void**)&s->sc_host, sizeof(CgScalars) * nrhs));
   TOPO_CUDA(cudaMallocHost((void**)&s->dots_host, sizeof(double) * nrhs));
-  s->prof_ev.resize(2 * s->graph_iters);
+  s->prof_ev.resize(2 * s->graph_iters * topo_solver::kProfKinds);
   for (auto& e : s->prof_ev) TOPO_CUDA(cudaEventCreate(&e));
   TOPO_CUDA(cudaDeviceSynchronize());
   return TOPO_OK;
@@ -908,6 +1007,11 @@ topo_status topo_solver_create(const topo_solver_desc* d, topo_solver** out) {
       d->nrhs < 1 || d->nrhs > kMaxRhs || !(d->E > 0.0) || !(d->nu > -1.0 && d->nu < 0.5) ||
       (d->smoother != 0 && d->smoother != 1)) {
     set_error("topo_solver_create: invalid descriptor field");
+    return TOPO_E_INVALID_ARG;
+  }
+  const Dims dfine{d->nx, d->ny, d->dim == 3 ? d->nz : 1, d->dim};
+  if (dfine.dofs() >= (1LL << 31)) {  // kernels index nodes and DOFs with 32-bit arithmetic
+    set_error("topo_solver_create: grid has 2^31 or more DOFs");
     return TOPO_E_INVALID_ARG;
   }
   const int f = 1 << (d->levels - 1);
@@ -932,6 +1036,40 @@ topo_status topo_solver_create(const topo_solver_desc* d, topo_solver** out) {
   return TOPO_OK;
 }
 
+topo_status topo_set_vcycle_fusion(topo_solver* s, int on) {
+  if (!s) {
+    set_error("topo_set_vcycle_fusion: null solver");
+    return TOPO_E_INVALID_ARG;
+  }
+  const bool want = on != 0 && s->tail_ok;
+  if (want != s->tail_on) {
+    s->tail_on = want;
+    for (int u = 0; u < 2; ++u)  // captured graphs hold the old V-cycle
+      if (s->setup[u]) {
+        cudaGraphExecDestroy(s->setup[u]);
+        s->setup[u] = nullptr;
+      }
+    if (s->graph) {
+      cudaGraphExecDestroy(s->graph);
+      s->graph = nullptr;
+    }
+    if (s->loop) {
+      cudaGraphExecDestroy(s->loop);
+      s->loop = nullptr;
+    }
+  }
+  return TOPO_OK;
+}
+
+topo_status topo_set_graph_mode(topo_solver* s, int mode) {
+  if (!s || (mode != 0 && mode != 1)) {
+    set_error("topo_set_graph_mode: null solver or mode not 0/1");
+    return TOPO_E_INVALID_ARG;
+  }
+  s->graph_mode = mode;
+  return TOPO_OK;
+}
+
 topo_status topo_set_stream(topo_solver* s, void* stream) {
   if (!s) return TOPO_E_INVALID_ARG;
   s->user = (cudaStream_t)stream;
@@ -943,23 +1081,41 @@ size_t topo_solver_device_bytes(const topo_solver* s) { return s ? s->bytes : 0;
 unsigned long long topo_solver_launch_count(const topo_solver* s) { return s ? s->launches : 0; }
 
 topo_status topo_set_profiling(topo_solver* s, int on) {
-  if (!s) return TOPO_E_INVALID_ARG;
-  if ((bool)on != s->profiling) {
-    s->profiling = on != 0;
-    if (s->graph) {  // the iteration graph gains or loses its event nodes
+  return topo_set_profiling_mask(s, on ? 1u : 0u);
+}
+
+topo_status topo_set_profiling_mask(topo_solver* s, unsigned mask) {
+  if (!s || mask >= (1u << topo_solver::kProfKinds)) {
+    set_error("topo_set_profiling_mask: null solver or mask beyond the profiled kinds");
+    return TOPO_E_INVALID_ARG;
+  }
+  if (mask != s->prof_mask) {
+    s->prof_mask = mask;
+    s->profiling = mask != 0;
+    if (s->graph) {  // the iteration graph gains or loses event nodes
       cudaGraphExecDestroy(s->graph);
       s->graph = nullptr;
     }
   }
-  s->prof_ms = 0.0;
-  s->prof_count = 0;
+  for (int k = 0; k < topo_solver::kProfKinds; ++k) {
+    s->prof_ms[k] = 0.0;
+    s->prof_count[k] = 0;
+  }
   return TOPO_OK;
 }
 
 topo_status topo_get_profile(const topo_solver* s, double* operator_ms_total, long long* count) {
-  if (!s || !operator_ms_total || !count) return TOPO_E_INVALID_ARG;
-  *operator_ms_total = s->prof_ms;
-  *count = s->prof_count;
+  return topo_get_profile_kernel(s, 0, operator_ms_total, count);
+}
+
+topo_status topo_get_profile_kernel(const topo_solver* s, int kind, double* ms_total,
+                                    long long* count) {
+  if (!s || !ms_total || !count || kind < 0 || kind >= topo_solver::kProfKinds) {
+    set_error("topo_get_profile_kernel: null argument or kind outside 0..7");
+    return TOPO_E_INVALID_ARG;
+  }
+  *ms_total = s->prof_ms[kind];
+  *count = s->prof_count[kind];
   return TOPO_OK;
 }
 
@@ -1031,7 +1187,7 @@ topo_status topo_get_level_matrices(topo_solver* s, int level, double* out_host)
     set_error("topo_get_level_matrices: level must be in [1, levels) after topo_set_density");
     return TOPO_E_INVALID_ARG;
   }
-  if (!s->L[level].Ae) {
+  if (!s->L[level].Ae && !s->L[level].Ae32) {
     set_error("topo_get_level_matrices: this level is applied matrix-free (mixed precision)");
     return TOPO_E_INVALID_ARG;
   }
@@ -1039,9 +1195,17 @@ topo_status topo_get_level_matrices(topo_solver* s, int level, double* out_host)
   const Level& lv = s->L[level];
   const long long ne2 = (long long)s->ne * s->ne;
   std::vector<double> tmp(lv.m * ne2);
-  TOPO_CUDA(cudaMemcpyAsync(tmp.data(), lv.Ae, sizeof(double) * tmp.size(), cudaMemcpyDeviceToHost,
-                            s->st));
-  TOPO_CUDA(cudaStreamSynchronize(s->st));
+  if (lv.Ae) {
+    TOPO_CUDA(cudaMemcpyAsync(tmp.data(), lv.Ae, sizeof(double) * tmp.size(),
+                              cudaMemcpyDeviceToHost, s->st));
+    TOPO_CUDA(cudaStreamSynchronize(s->st));
+  } else {  // FP32 hierarchy: the stored FP32 matrices, widened
+    std::vector<float> t32(tmp.size());
+    TOPO_CUDA(cudaMemcpyAsync(t32.data(), lv.Ae32, sizeof(float) * t32.size(),
+                              cudaMemcpyDeviceToHost, s->st));
+    TOPO_CUDA(cudaStreamSynchronize(s->st));
+    for (size_t q = 0; q < tmp.size(); ++q) tmp[q] = t32[q];
+  }
   for (long long e = 0; e < lv.m; ++e)
     for (long long q = 0; q < ne2; ++q) out_host[e * ne2 + q] = tmp[q * lv.m + e];
   return TOPO_OK;

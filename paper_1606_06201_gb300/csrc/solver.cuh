@@ -30,6 +30,8 @@ struct topo_solver {
   float* x32 = nullptr;
   float* C32 = nullptr;          // FP32 copy of C (matrix-free first coarse level)
   double* C2 = nullptr;          // composite matrices two levels down (second coarse level)
+  float* C2f = nullptr;          // FP32 copy of C2 (FP32 hierarchy)
+  bool h32 = false;              // mixed K solver with fixed damping: coarse matrices built in FP32
   bool l1_free = false;          // mixed 2D K systems: level 1 applied matrix-free in FP32
   // Arrow (IP) systems Z = [K 0; 0 0] + [B; e^T] D^{-1} [B^T e] (Eq. (nwtr2Z)): vectors carry a
   // trailing lambda entry; g_e = K0 u_e and Dinv = 1/D on the finest level are owned by the IP
@@ -46,7 +48,8 @@ struct topo_solver {
   int nc = 0;                    // DOFs of the coarsest level
   double* Adense = nullptr;
   double* Ainv = nullptr;
-  int* info = nullptr;
+  double* Ascratch = nullptr;    // Newton-Schulz products of the coarsest inverse (small n)
+  int* info = nullptr;           // [0] coarsest pivot failure, [1] bad density, [2] Newton-Schulz flag
   double *z = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
   void* yold = nullptr;          // previous preconditioned residual (flexible beta)
   void* rv = nullptr;            // residual in V-cycle precision (mixed)
@@ -61,7 +64,10 @@ struct topo_solver {
   cudaGraphExec_t loop = nullptr;         // persistent CG: while-node over one iteration
   int loop_kernels = 0;                   // kernels per loop iteration
   double loop_tol = -1.0;
-  bool no_loop = false;                   // conditional graphs unavailable (or TOPO_NO_LOOP=1)
+  int graph_mode = 0;                     // 0 replayed blocks of iterations, 1 while-node loop
+  bool tail_ok = false;                   // the fused deep-level kernel can run on this device
+  bool tail_on = false;                   // and is used (topo_set_vcycle_fusion)
+  bool no_loop = false;                   // conditional graphs unavailable on this device
   cudaGraphExec_t graph = nullptr;        // graph_iters CG iterations (profiling runs)
   int graph_kernels = 0;
   double graph_tol = -1.0;                // tolerance baked into the captured graphs
@@ -73,9 +79,14 @@ struct topo_solver {
   int graph_iters = 4;
   unsigned long long launches = 0;        // kernels launched by this solver
   bool profiling = false;
-  std::vector<cudaEvent_t> prof_ev;       // event pairs around the outer operator per slot
-  double prof_ms = 0.0;
-  long long prof_count = 0;
+  unsigned prof_mask = 0;                 // profiled kinds (bit k = kind k)
+  // Profiling: event pairs per (kind, iteration slot) of the block graph; kinds as
+  // topo_get_profile_kernel (0 outer operator, 1-4 finest-level V-cycle kernels, 5-7 V-cycle parts).
+  static constexpr int kProfKinds = 8;
+  std::vector<cudaEvent_t> prof_ev;
+  double prof_ms[kProfKinds] = {};
+  long long prof_count[kProfKinds] = {};
+  int prof_slot = -1;                     // slot of the iteration being captured, -1 outside
   bool have_density = false;
   size_t bytes = 0;
   std::vector<void*> allocs;

@@ -134,6 +134,76 @@ inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
   cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// Node coordinates from a linear node index with 32-bit division (grids hold < 2^31 nodes; the
+// solver checks this at creation): i fastest, then j, then k.
+__device__ __forceinline__ void node_coords(long long node, int nnx, int nny, int dim, int& i,
+                                            int& j, int& k) {
+  const unsigned nd = (unsigned)node;
+  const unsigned q = nd / (unsigned)nnx;
+  i = (int)(nd - q * (unsigned)nnx);
+  if (dim == 3) {
+    const unsigned r = q / (unsigned)nny;
+    j = (int)(q - r * (unsigned)nny);
+    k = (int)r;
+  } else {
+    j = (int)q;
+    k = 0;
+  }
+}
+
+// z_row = sum_k Ainv[row][k] b[k] by one warp: lane-strided FP64 sums, then a butterfly
+// (COH: b read from L2, for data written earlier in the same launch by other blocks).
+template <bool COH, typename T>
+__device__ __forceinline__ double dense_row_dot(int n, const double* __restrict__ row, const T* b,
+                                                int lane) {
+  double s = 0.0;
+  for (int k = lane; k < n; k += 32) {
+    T bk;
+    if constexpr (COH) bk = __ldcg(b + k);
+    else bk = b[k];
+    s = fma(row[k], (double)bk, s);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// Deep levels of the 2D V-cycle fused into one launch (kernels_fe.cu): levels tail_from ..
+// coarsest, run by one thread-block cluster per right-hand side.
+#ifndef TOPO_TAIL_CLUSTER
+#define TOPO_TAIL_CLUSTER 8
+#endif
+#ifndef TOPO_TAIL_THREADS
+#define TOPO_TAIL_THREADS 256
+#endif
+// Measured on the 2048 x 1024 solve (9 levels, ms per hierarchy build + solve): unfused 7.95;
+// fused from the level of 2145 nodes 7.93-8.02, from 8385 nodes 8.18-8.28, from 561 nodes 7.92.
+// Graph launches of the small kernels cost about as much as the L2 round trips of a fused phase,
+// so the fused part starts where a level fits in one pass of the cluster's threads.
+#ifndef TOPO_TAIL_NODES
+#define TOPO_TAIL_NODES 1024
+#endif
+constexpr int kTailMax = 8;                      // levels in the fused part, coarsest included
+constexpr int kTailCluster = TOPO_TAIL_CLUSTER;  // blocks per cluster (above 8: non-portable)
+constexpr int kTailThreads = TOPO_TAIL_THREADS;
+constexpr long long kTailNodes = TOPO_TAIL_NODES;  // most nodes of the first fused level
+
+template <typename T>
+struct TailArgs {
+  int nl;        // fused levels, the last one the coarsest
+  int nu1, nu2;
+  int nc;        // coarsest DOFs (Ainv is nc x nc)
+  T omega;
+  const double* Ainv;
+  Dims d[kTailMax];
+  const T* Ae[kTailMax];
+  const T* invd[kTailMax];
+  const uint8_t* fixed[kTailMax];
+  T* b[kTailMax];  // b[0]: the restricted residual from the level above
+  T* z[kTailMax];
+  T* t[kTailMax];
+};
+
 inline unsigned blocks_for(long long n, int threads = kThreads) {
   return (unsigned)((n + threads - 1) / threads);
 }
@@ -151,6 +221,13 @@ cudaError_t launch_apply(const Dims& d, int mode, const T* K0, const T* x, const
                          const T* b,
                          T* y, const T* invd, T omega, const uint8_t* fixed, int nrhs,
                          const CgScalars* sc, cudaStream_t st, const T* w = nullptr);
+// Fused deep part of the V-cycle (Jacobi smoothing, element matrices on every fused level but
+// the coarsest): the result of the first fused level ends in z[0] or t[0] as in the unfused
+// cycle (tail_result).
+template <typename T>
+cudaError_t launch_vcycle_tail(const TailArgs<T>& a, int nrhs, const CgScalars* sc,
+                               cudaStream_t st);
+cudaError_t prepare_tail_kernels();
 // First coarse level of a 2D grid, matrix-free from the finest densities xf and the four child
 // matrices C (same modes as launch_apply).
 template <typename T>
@@ -172,6 +249,9 @@ cudaError_t launch_prolong_add(const Dims& fine, const T* zc, T* zf, const uint8
                                int nrhs, const CgScalars* sc, cudaStream_t st, int arrow = 0);
 cudaError_t launch_inv_diag(const Dims& d, const double* K0, const double* x, const double* Ae,
                             const uint8_t* fixed, double* invd, cudaStream_t st);
+// FP32 inverse diagonal of a coarse level from its FP32 element matrices.
+cudaError_t launch_inv_diag32(const Dims& d, const float* Ae, const uint8_t* fixed, float* invd,
+                              cudaStream_t st);
 cudaError_t launch_element_energy(const Dims& d, const double* K0, const double* u,
                                   const double* lam, double* out, double scale, cudaStream_t st);
 
@@ -213,12 +293,17 @@ cudaError_t launch_q1g_apply(int nx, int ny, int mode, const Q1Coef& coef, const
 
 // Hierarchy construction (kernels_rap.cu).
 // g, Dinv != nullptr: add the rank-one terms (P_c^T g_c)(P_c^T g_c)^T Dinv_c of Z.
-cudaError_t launch_rap_from_fine(const Dims& fine, const double* C, const double* x, double* Ac,
-                                 cudaStream_t st, const double* g = nullptr,
-                                 const double* Dinv = nullptr);
-cudaError_t launch_rap_coarse(const Dims& fine, const double* Af, double* Ac, cudaStream_t st);
+// T = double or float (arithmetic and storage); the rank-one terms g, Dinv need T = double.
+template <typename T>
+cudaError_t launch_rap_from_fine(const Dims& fine, const T* C, const T* x, T* Ac, cudaStream_t st,
+                                 const double* g = nullptr, const double* Dinv = nullptr);
+// TI: stored type of the finer level's matrices; TO: arithmetic and stored type of the result
+// (double/double, float/float, float/double).
+template <typename TI, typename TO>
+cudaError_t launch_rap_coarse(const Dims& fine, const TI* Af, TO* Ac, cudaStream_t st);
 // Second coarse level from the finest densities with the 4^dim composite matrices C2.
-cudaError_t launch_rap2_from_fine(const Dims& fine, const double* C2, const double* x, double* Ac,
+template <typename T>
+cudaError_t launch_rap2_from_fine(const Dims& fine, const T* C2, const T* x, T* Ac,
                                   cudaStream_t st);
 // Inverse diagonal of the first coarse level from the finest densities and the child matrices.
 cudaError_t launch_inv_diag_l1(const Dims& coarse1, const double* C, const double* xf,
@@ -231,7 +316,15 @@ cudaError_t launch_assemble_dense(const Dims& d, const double* K0, const double*
                                   long long ld = 0, const double* w = nullptr,
                                   const double* zll = nullptr, const double* g = nullptr,
                                   const double* Dinv = nullptr);
-cudaError_t launch_cholesky_inverse(int n, double* A, double* Ainv, int* info, cudaStream_t st);
+// Ainv = A^{-1} for the dense SPD coarsest matrix; info[0] = 0 or k+1 (pivot k failed).  With
+// allow_ns and n small enough: FP32 Gauss-Jordan + FP64 Newton-Schulz in scratch
+// (coarse_scratch_doubles(n) doubles), *ns_bad set if that did not reach FP64 accuracy, in which
+// case the Cholesky kernels (always enqueued) recompute it; otherwise Cholesky (with the pivot
+// floor) + triangular inverse.
+cudaError_t launch_cholesky_inverse(int n, double* A, double* Ainv, int* info, cudaStream_t st,
+                                    double* scratch = nullptr, int* ns_bad = nullptr,
+                                    bool allow_ns = false);
+size_t coarse_scratch_doubles(int n);
 // Shared-memory limits of the coarsest-level kernels (call once, outside stream capture).
 cudaError_t prepare_coarse_kernels(int n);
 template <typename T>

@@ -75,6 +75,11 @@ _SIGS = {
     "topo_solver_create": (ctypes.c_int, [ctypes.POINTER(SolverDesc), ctypes.POINTER(_vp)]),
     "topo_solver_destroy": (ctypes.c_int, [_vp]),
     "topo_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "topo_set_graph_mode": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "topo_set_vcycle_fusion": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "topo_set_profiling_mask": (ctypes.c_int, [_vp, ctypes.c_uint]),
+    "topo_get_profile_kernel": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_longlong)]),
     "topo_solver_device_bytes": (ctypes.c_size_t, [_vp]),
     "topo_solver_launch_count": (ctypes.c_ulonglong, [_vp]),
     "topo_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
@@ -358,13 +363,36 @@ class Solver:
     def launch_count(self):
         return int(_lib.topo_solver_launch_count(self._h))
 
+    def set_graph_mode(self, mode):
+        """0: replayed graph of 4 CG iterations (default); 1: one conditional-while graph per solve."""
+        _check(_lib.topo_set_graph_mode(self._h, int(mode)), "topo_set_graph_mode")
+
     def set_profiling(self, on):
         _check(_lib.topo_set_profiling(self._h, int(bool(on))), "topo_set_profiling")
+
+    def set_vcycle_fusion(self, on):
+        """Fuse the deep levels of the 2D V-cycle into one cluster launch (default on)."""
+        _check(_lib.topo_set_vcycle_fusion(self._h, int(bool(on))), "topo_set_vcycle_fusion")
+
+    def set_profiling_mask(self, mask):
+        """Profile the kinds in mask (bit k = PROFILE_KINDS[k]); 0 turns profiling off."""
+        _check(_lib.topo_set_profiling_mask(self._h, int(mask)), "topo_set_profiling_mask")
 
     def profile(self):
         """(summed ms, launches) of the outer operator kernel since set_profiling."""
         ms, cnt = ctypes.c_double(), ctypes.c_longlong()
         _check(_lib.topo_get_profile(self._h, ctypes.byref(ms), ctypes.byref(cnt)), "topo_get_profile")
+        return ms.value, cnt.value
+
+    PROFILE_KINDS = ("outer_operator", "fine_smoothing_sweep", "fine_residual",
+                     "fine_restriction", "fine_prolongation", "vcycle", "vcycle_levels_ge1",
+                     "vcycle_levels_ge2")
+
+    def profile_kernel(self, kind):
+        """(summed ms, launches) of one profiled kernel kind (index into PROFILE_KINDS)."""
+        ms, cnt = ctypes.c_double(), ctypes.c_longlong()
+        _check(_lib.topo_get_profile_kernel(self._h, int(kind), ctypes.byref(ms), ctypes.byref(cnt)),
+               "topo_get_profile_kernel")
         return ms.value, cnt.value
 
     def set_density(self, x):

@@ -58,7 +58,9 @@ def test_descriptor_validation_needs_no_device():
     from paper_1606_06201_gb300 import topo
     fixed = np.zeros(2 * 9 * 5, dtype=np.uint8)
     bad = [dict(levels=5), dict(levels=0), dict(nu1=-1), dict(omega=1.5), dict(nrhs=0),
-           dict(precision=7), dict(smoother=2)]
+           dict(precision=7), dict(smoother=2),
+           # 2^31 or more DOFs (rejected before the mask is read)
+           dict(dim=3, nx=1024, ny=1024, nz=1024, levels=9)]
     for kw in bad:
         args = dict(dim=2, nx=8, ny=4, nz=0, E=1.0, nu=0.3, levels=2, precision=0, nu1=2, nu2=2,
                     omega=0.6, max_iter=10, nrhs=1, flexible=0, generic_kernels=0, smoother=0, omega_auto=0)

@@ -63,6 +63,38 @@ def test_galerkin_level_matrices_match_sparse_rap(shape):
         np.testing.assert_allclose(A, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("shape", [(64, 32, 0, 5), (8, 4, 4, 3)])
+@pytest.mark.parametrize("generic", [False, True])
+def test_fp32_hierarchy_matrices_match_sparse_rap(shape, generic):
+    """Mixed solvers with fixed damping build the coarse matrices below the coarsest level in FP32
+    (from FP32 densities and FP32 child tables) and the coarsest in FP64 from FP32 inputs: each
+    level against the oracle's FP64 Galerkin product to FP32 accuracy."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny, nz, levels = shape
+    fixed = W.clamp_xmin(nx, ny, nz)
+    x = _x(nx, ny, nz, 15)
+    s = topo.Solver(nx, ny, nz, fixed=fixed, levels=levels, precision=topo.MIXED,
+                    generic_kernels=generic)
+    s.set_density(dev(torch, x))
+    levs, _, _, _ = oracle_hierarchy(nx, ny, nz, x, fixed, levels)
+    from oracle.mg import coarse_fixed
+    g = fe.Grid(nx, ny, nz)
+    fx = fixed.astype(bool)
+    checked = 0
+    for k in range(1, levels):
+        g, fx = coarse_fixed(g, fx)
+        if k == 1 and not nz and not generic:
+            continue  # matrix-free in mixed precision
+        Ae = s.level_matrices(k)
+        free = fe.free_dofs(fx)
+        A = fe.assemble_elementwise(g, Ae)[free][:, free].toarray()
+        ref = levs[k].A.toarray()
+        np.testing.assert_allclose(A, ref, rtol=0, atol=2e-6 * np.abs(ref).max())
+        checked += 1
+    assert checked >= 2
+
+
 @pytest.mark.parametrize("generic", [False, True])
 @pytest.mark.parametrize("shape", [(16, 8, 0, 3), (64, 32, 0, 3), (96, 40, 0, 4), (8, 4, 4, 3)])
 @pytest.mark.parametrize("nu", [(2, 2), (1, 1), (0, 1)])
@@ -82,6 +114,29 @@ def test_vcycle_fp64_matches_oracle(shape, nu, generic):
     ref = np.zeros(s.n)
     ref[free] = mg.vcycle(levs, r[free], nu[0], nu[1], omega)
     assert rel_err(y, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("contrast", [1e-3, 1e-9])
+def test_small_coarsest_inverse_newton_schulz_and_fallback(contrast):
+    """Coarsest level of 90 DOFs (32 x 16 grid, 3 levels): inverted by FP32 Gauss-Jordan and FP64
+    Newton-Schulz steps; with a 1e-9 density block the coarsest matrix is too ill-conditioned for
+    the FP32 start, the accuracy check fails and the Cholesky kernels recompute the inverse.  Both
+    V-cycles against the oracle's (tolerance: the conditioning of the extreme case)."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny, levels = 32, 16, 3
+    fixed = W.clamp_xmin(nx, ny)
+    x = np.ones(nx * ny)
+    xe = x.reshape(ny, nx)
+    xe[4:12, 8:24] = contrast
+    s = topo.Solver(nx, ny, fixed=fixed, levels=levels, omega=0.6)
+    s.set_density(dev(torch, x))
+    levs, free, _, _ = oracle_hierarchy(nx, ny, 0, x, fixed, levels)
+    r = W.random_vector(s.n, 9, fixed)
+    y = host(s.apply_vcycle(dev(torch, r)))
+    ref = np.zeros(s.n)
+    ref[free] = mg.vcycle(levs, r[free], 2, 2, 0.6)
+    assert rel_err(y, ref) <= (1e-12 if contrast > 1e-6 else 1e-6)
 
 
 @pytest.mark.parametrize("shape", [(64, 32, 0, 3), (128, 64, 0, 5), (8, 4, 4, 2)])
@@ -158,6 +213,95 @@ def test_batched_rhs_equal_individual_solves():
     for k in range(3):
         u, _ = s1.solve(dev(torch, F[k]), tol=1e-12)
         np.testing.assert_allclose(host(U)[k], host(u), rtol=0, atol=1e-14 * np.abs(host(u)).max())
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_modes_give_identical_bits(precision):
+    """The replayed 4-iteration graph and the one-launch conditional-while graph run the same
+    kernels in the same order: same iterates bit for bit, same counts, also when one right-hand
+    side (zero) stops at once and another hits max_iter."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny = 64, 32
+    fixed = W.clamp_xmin(nx, ny)
+    x = dev(torch, _x(nx, ny, 0, 33))
+    F = np.stack([W.normal_load(fixed, 50), np.zeros(fixed.size), W.normal_load(fixed, 51)])
+    out = []
+    for mode in (0, 1):
+        s = topo.Solver(nx, ny, fixed=fixed, levels=3, nrhs=3, precision=precision, max_iter=30)
+        s.set_graph_mode(mode)
+        s.set_density(x)
+        U, info = s.solve(dev(torch, F), tol=1e-10)
+        U2, info2 = s.solve(dev(torch, F), tol=1e-30, allow_not_converged=True)
+        out.append((host(U), info.iterations, host(U2), info2.iterations, info2.status))
+        s.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][2], out[1][2])
+    assert out[0][1] == out[1][1] and out[0][3] == out[1][3] and out[0][4] == out[1][4]
+    with pytest.raises(topo.TopoError):
+        topo.Solver(nx, ny, fixed=fixed, levels=3).set_graph_mode(2)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("shape,nu,nrhs", [((256, 128, 0, 6), (2, 2), 1),
+                                           ((128, 64, 0, 5), (1, 1), 2),
+                                           ((96, 40, 0, 4), (0, 1), 1),
+                                           ((256, 64, 0, 6), (2, 3), 3)])
+def test_fused_deep_levels_give_identical_bits(precision, shape, nu, nrhs):
+    """The deep levels of the V-cycle in one cluster launch run the same per-node arithmetic as
+    the per-sweep launches: V-cycle outputs and whole solves agree bit for bit."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny, nz, levels = shape
+    fixed = W.clamp_xmin(nx, ny)
+    x = dev(torch, _x(nx, ny, 0, 37))
+    R = np.stack([W.random_vector(fixed.size, 60 + k, fixed) for k in range(nrhs)])
+    F = np.stack([W.normal_load(fixed, 70 + k) for k in range(nrhs)])
+    out = []
+    for fused in (False, True):
+        s = topo.Solver(nx, ny, fixed=fixed, levels=levels, precision=precision, nu1=nu[0],
+                        nu2=nu[1], nrhs=nrhs, max_iter=200)
+        s.set_vcycle_fusion(fused)
+        s.set_density(x)
+        y = host(s.apply_vcycle(dev(torch, R)))
+        # (nu1, nu2) = (0, 1) is not a symmetric preconditioner: CG may stall, the bits still agree
+        u, info = s.solve(dev(torch, F), tol=1e-9, allow_not_converged=True)
+        out.append((y, host(u), info.iterations))
+        s.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+
+
+def test_profiling_times_every_kernel_kind_and_keeps_results():
+    """Profiling inserts event nodes only: the iterate is bit-identical to an unprofiled solve,
+    and every kernel kind of the iteration is timed once per CG iteration."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny = 128, 64
+    fixed = W.clamp_xmin(nx, ny)
+    x = dev(torch, _x(nx, ny, 0, 35))
+    f = dev(torch, W.normal_load(fixed, 36))
+    s = topo.Solver(nx, ny, fixed=fixed, levels=4, precision=topo.MIXED)
+    s.set_density(x)
+    u0, info0 = s.solve(f, tol=1e-9)
+    s.set_profiling(True)  # the outer operator only
+    u1, info1 = s.solve(f, tol=1e-9)
+    assert torch.equal(u0, u1) and info0.iterations == info1.iterations
+    assert s.profile()[1] == info1.iterations
+    assert all(s.profile_kernel(k)[1] == 0 for k in range(1, len(topo.Solver.PROFILE_KINDS)))
+    s.set_profiling_mask((1 << len(topo.Solver.PROFILE_KINDS)) - 1)
+    u2, info2 = s.solve(f, tol=1e-9)
+    assert torch.equal(u0, u2) and info0.iterations == info2.iterations
+    for k in range(len(topo.Solver.PROFILE_KINDS)):
+        ms, cnt = s.profile_kernel(k)
+        assert cnt == info2.iterations and ms > 0.0, (k, ms, cnt)
+    assert s.profile() == s.profile_kernel(0)
+    with pytest.raises(topo.TopoError):
+        s.set_profiling_mask(1 << len(topo.Solver.PROFILE_KINDS))
+    with pytest.raises(topo.TopoError):
+        s.profile_kernel(len(topo.Solver.PROFILE_KINDS))
+    s.close()
 
 
 def test_energy_gradient_and_compliance():
