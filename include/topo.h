@@ -115,6 +115,13 @@ topo_status topo_set_graph_mode(topo_solver* s, int mode);
  * coarsest run in one launch of a thread-block cluster per right-hand side; off, one launch per
  * sweep, residual and transfer.  Both give the same bits.  Other systems ignore the setting. */
 topo_status topo_set_vcycle_fusion(topo_solver* s, int on);
+/* Arithmetic of the outer operator q = K(x) p of Algorithm PCG on the 2D finest level of K
+ * systems: 0 = FP64; 1 = pairs of FP32 values (hi + lo, about 48 significant bits, FP64 in and
+ * out, p^T q accumulated in pairs), which GB300 runs several times faster than FP64.  Default: 1
+ * for mixed-precision solvers, 0 for FP64 solvers; other systems always use FP64.  Inputs of
+ * magnitude below 2^-100 lose their low part and values beyond float range give a breakdown.
+ * Other modes -> E_INVALID_ARG. */
+topo_status topo_set_outer_precision(topo_solver* s, int mode);
 /* Device bytes held by the solver. */
 size_t topo_solver_device_bytes(const topo_solver* s);
 /* Number of CUDA kernels this solver has launched since its creation (graph kernel nodes

@@ -253,6 +253,231 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, int 
   }
 }
 
+// ---- Outer operator in pair-of-FP32 arithmetic ------------------------------------------------
+// GB300 issues about 2 FP64 operations per clock per SM against 128 FP32 ones, so the FP64 outer
+// operator of the mixed solver is ALU-bound at ~40 FP64 operations per element.  This variant
+// computes the same butterfly with each value held as an unevaluated sum hi + lo of two floats
+// (Dekker's double-float arithmetic with error-free TwoSum and FMA-based TwoProd, about 48
+// significant bits): p is split into float pairs with integer operations, q is rebuilt as
+// double(hi) + double(lo) (one FP64 add per DOF), and p^T q is accumulated in pairs.  Values
+// below 2^-100 in magnitude lose their low part (float range); 48 bits keep the CG recurrences of
+// the mixed solver far below its 1e-8 tolerance.  All adds and multiplies use the _rn intrinsics
+// so that the compiler cannot contract them into fused operations that break the error terms.
+struct f2 {
+  float h, l;
+};
+
+__device__ __forceinline__ f2 fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ f2 df_add(f2 a, f2 b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  return fast_two_sum(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
+}
+
+__device__ __forceinline__ f2 df_neg(f2 a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ f2 df_sub(f2 a, f2 b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ f2 df_mul(f2 a, f2 b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+  return fast_two_sum(p, e);
+}
+
+// double -> float pair with integer operations only: hi = d truncated to 24 significant bits,
+// lo = the remaining 29 bits rounded to float.  |d| < 2^-126 gives 0; the finite range of the
+// outer operator's inputs is well inside float's.
+__device__ __forceinline__ f2 df_from_double(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7ff);
+  const int ef = e - 1023 + 127;
+  if (ef <= 0) return {0.0f, 0.0f};
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  if (ef >= 255)  // beyond float range, infinities and NaNs: an infinity or a NaN
+    return {__uint_as_float(sign | 0x7f800000u | (unsigned)((b >> 29) & 0x7fffffu) |
+                            (e == 2047 && (b & 0xfffffffffffffull) ? 1u : 0u)),
+            0.0f};
+  const float hi = __uint_as_float(sign | ((unsigned)ef << 23) |
+                                   (unsigned)((b >> 29) & 0x7fffffu));
+  const unsigned rem = (unsigned)(b & ((1ull << 29) - 1));
+  // rem * 2^(e - 1075) = rem * 2^-52 * 2^(e - 1023); both factors are normal floats here
+  float lo = __fmul_rn(__fmul_rn(__uint2float_rn(rem), 0x1p-52f),
+                       __uint_as_float((unsigned)ef << 23));
+  return {hi, sign ? -lo : lo};
+}
+
+// float -> double exactly, with integer operations (normal floats; zero and subnormals give 0).
+__device__ __forceinline__ double double_from_float(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ef = (u >> 23) & 0xff;
+  if (ef == 0) return 0.0;
+  if (ef == 255)  // infinities and NaNs stay what they are (breakdown tests see them)
+    return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
+                                            (0x7ffull << 52) |
+                                            ((unsigned long long)(u & 0x7fffffu) << 29)));
+  const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
+                               ((unsigned long long)(ef + 896) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)b);
+}
+
+struct Q1KD {
+  f2 c11, c12, c22, c33, cH, cHp;
+};
+
+// The butterfly of q1_element in pair arithmetic (the density applied after Khat).
+__device__ __forceinline__ void q1_element_df(const Q1KD& k, f2 xe, const f2 u[4], const f2 v[4],
+                                              f2 ru[4], f2 rv[4]) {
+  const f2 d1 = df_sub(u[2], u[0]), d2 = df_sub(u[1], u[3]);
+  const f2 s1 = df_add(u[0], u[2]), s2 = df_add(u[1], u[3]);
+  const f2 X = df_add(d2, d1), Y = df_sub(d1, d2), H = df_sub(s1, s2);
+  const f2 e1 = df_sub(v[2], v[0]), e2 = df_sub(v[1], v[3]);
+  const f2 t1 = df_add(v[0], v[2]), t2 = df_add(v[1], v[3]);
+  const f2 Xp = df_add(e2, e1), Yp = df_sub(e1, e2), Hp = df_sub(t1, t2);
+  const f2 G = df_add(Y, Xp);
+  const f2 gX = df_mul(xe, df_add(df_mul(k.c11, X), df_mul(k.c12, Yp)));
+  const f2 gYp = df_mul(xe, df_add(df_mul(k.c12, X), df_mul(k.c22, Yp)));
+  const f2 gG = df_mul(xe, df_mul(k.c33, G));
+  const f2 gH = df_mul(xe, df_mul(k.cH, H));
+  const f2 gHp = df_mul(xe, df_mul(k.cHp, Hp));
+  const f2 A = df_add(gX, gG), B = df_sub(gX, gG);
+  ru[0] = df_sub(gH, A);
+  ru[1] = df_sub(B, gH);
+  ru[2] = df_add(A, gH);
+  ru[3] = df_sub(df_neg(B), gH);
+  const f2 C = df_add(gYp, gG), Dd = df_sub(gYp, gG);
+  rv[0] = df_sub(gHp, C);
+  rv[1] = df_sub(df_neg(Dd), gHp);
+  rv[2] = df_add(C, gHp);
+  rv[3] = df_sub(Dd, gHp);
+}
+
+__device__ __forceinline__ f2 shfl_dn_df(f2 a) { return {shfl_dn(a.h), shfl_dn(a.l)}; }
+__device__ __forceinline__ f2 shfl_up1_df(f2 a) { return {shfl_up1(a.h), shfl_up1(a.l)}; }
+
+// q = K(x) p with p^T q and alpha (as k_q1_sweep<double, 0, 1>), in pair arithmetic.  xdf: the
+// densities as float pairs.
+__global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep_df(int nx, int ny, int rows, Q1KD k,
+                                                                const float2* __restrict__ xdf,
+                                                                const double* __restrict__ v,
+                                                                double* __restrict__ y,
+                                                                const uint8_t* __restrict__ fixed,
+                                                                CgScalars* sc, double* partials,
+                                                                unsigned* counters) {
+  pdl_prologue();
+  const int rhs = blockIdx.y;
+  if (sc && sc[rhs].done) return;
+  const long long n = 2LL * (nx + 1) * (ny + 1);
+  v += rhs * n;
+  y += rhs * n;
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kQ1Warps + (threadIdx.x >> 5);
+  const int ncolw = (nx + 1 + kQ1Cols - 1) / kQ1Cols;
+  const int nstrip = (ny + 1 + rows - 1) / rows;
+  const int wc = gw % ncolw, ws = gw / ncolw;
+  f2 part = {0.0f, 0.0f};
+  if (ws < nstrip) {
+    const int c = wc * kQ1Cols - 1 + lane;
+    const bool col_ok = (c >= 0 && c <= nx);
+    const bool out_lane = (lane >= 1 && lane <= kQ1Cols && col_ok);
+    const bool el_col = (lane <= kQ1Cols && c >= 0 && c < nx);
+    const int j0 = ws * rows;
+    const int j1 = min(j0 + rows, ny + 1);
+    const double2* v2 = reinterpret_cast<const double2*>(v);
+    const long long rs = nx + 1;
+    const f2 z = {0.0f, 0.0f};
+    f2 pbu = z, pbv = z;
+    if (col_ok && j0 >= 1) {
+      const double2 t = v2[c + rs * (j0 - 1)];
+      pbu = df_from_double(t.x);
+      pbv = df_from_double(t.y);
+    }
+    double2 pt_n = make_double2(0.0, 0.0);
+    float2 xe_n = make_float2(0.0f, 0.0f);
+    {
+      const int ey = j0 - 1;
+      if (col_ok && ey + 1 <= ny) pt_n = v2[c + rs * (ey + 1)];
+      if (el_col && ey >= 0 && ey < ny) xe_n = xdf[c + (long long)nx * ey];
+    }
+    uint16_t fx_n = 0;
+    f2 cu = z, cv = z;
+    for (int ey = j0 - 1; ey < j1; ++ey) {
+      const f2 ptu = df_from_double(pt_n.x), ptv = df_from_double(pt_n.y);
+      const f2 xe = {xe_n.x, xe_n.y};
+      const uint16_t fx = fx_n;
+      pt_n = make_double2(0.0, 0.0);
+      xe_n = make_float2(0.0f, 0.0f);
+      if (ey + 1 < j1) {
+        if (col_ok && ey + 2 <= ny) pt_n = v2[c + rs * (ey + 2)];
+        if (el_col && ey + 1 < ny) xe_n = xdf[c + (long long)nx * (ey + 1)];
+        if (out_lane && ey + 1 >= j0)
+          fx_n = *reinterpret_cast<const uint16_t*>(fixed + 2 * (c + rs * (ey + 1)));
+      }
+      const f2 uu[4] = {pbu, shfl_dn_df(pbu), shfl_dn_df(ptu), ptu};
+      const f2 vv[4] = {pbv, shfl_dn_df(pbv), shfl_dn_df(ptv), ptv};
+      f2 ru[4], rv[4];
+      q1_element_df(k, xe, uu, vv, ru, rv);
+      const f2 l1u = shfl_up1_df(ru[1]), l1v = shfl_up1_df(rv[1]);
+      const f2 l2u = shfl_up1_df(ru[2]), l2v = shfl_up1_df(rv[2]);
+      if (ey >= j0 && out_lane) {
+        f2 qu = df_add(df_add(cu, ru[0]), l1u), qv = df_add(df_add(cv, rv[0]), l1v);
+        if (fx & 0xff) qu = z;
+        if (fx >> 8) qv = z;
+        double2 out;
+        out.x = double_from_float(qu.h) + double_from_float(qu.l);
+        out.y = double_from_float(qv.h) + double_from_float(qv.l);
+        reinterpret_cast<double2*>(y)[c + rs * ey] = out;
+        part = df_add(part, df_add(df_mul(pbu, qu), df_mul(pbv, qv)));
+      }
+      cu = df_add(ru[3], l2u);
+      cv = df_add(rv[3], l2v);
+      pbu = ptu;
+      pbv = ptv;
+    }
+  }
+  const double bs = block_sum_q1(double_from_float(part.h) + double_from_float(part.l));
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[(long long)rhs * gridDim.x + blockIdx.x] = bs;
+    __threadfence();
+    last = (atomicAdd(&counters[rhs], 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  double s = 0.0;
+  for (unsigned t = threadIdx.x; t < gridDim.x; t += blockDim.x)
+    s += __ldcg(partials + (long long)rhs * gridDim.x + t);
+  s = block_sum_q1(s);
+  if (threadIdx.x == 0) {
+    CgScalars& S = sc[rhs];
+    S.pq = s;
+    const double alpha = S.ry / s;
+    if (!(s > 0.0) || !isfinite(alpha)) {
+      S.status = TOPO_E_BREAKDOWN;
+      S.done = 1;
+      S.alpha = 0.0;
+    } else {
+      S.alpha = alpha;
+    }
+    counters[rhs] = 0;
+  }
+}
+
+// Densities as float pairs (hi + lo) for k_q1_sweep_df.
+__global__ void k_split_df(const double* __restrict__ x, float2* __restrict__ out, long long m) {
+  pdl_prologue();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) {
+    const f2 t = df_from_double(x[i]);
+    out[i] = make_float2(t.h, t.l);
+  }
+}
+
 // First coarse level, matrix-free Galerkin operator A_1 = P^T K(x) P applied element by element:
 // the coarse element's four nodal values are interpolated bilinearly to the 3 x 3 fine nodes of
 // its four children, each child's x_c K0 is applied in the butterfly form, and the 3 x 3 fine
@@ -477,6 +702,30 @@ template cudaError_t launch_q1_smooth_beta<float>(int, int, const Q1Coef&, const
                                                   const float*, const float*, float*, float,
                                                   const uint8_t*, int, const double*, double*,
                                                   unsigned*, CgScalars*, cudaStream_t);
+
+namespace {
+f2 df_const(double c) {
+  const float h = (float)c;
+  return {h, (float)(c - (double)h)};
+}
+}  // namespace
+
+cudaError_t launch_q1_apply_dot_df(int nx, int ny, const Q1Coef& coef, const float2* xdf,
+                                   const double* v, double* y, const uint8_t* fixed, int nrhs,
+                                   double* partials, unsigned* counters, CgScalars* sc,
+                                   cudaStream_t st) {
+  const Q1KD k{df_const(coef.c11), df_const(coef.c12), df_const(coef.c22), df_const(coef.c33),
+               df_const(coef.cH), df_const(coef.cHp)};
+  dim3 grid(q1_blocks(nx, ny), nrhs);
+  topo::launch(k_q1_sweep_df, grid, kQ1Warps * 32, 0, st, nx, ny, q1_rows(nx, ny), k, xdf, v, y,
+               fixed, sc, partials, counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_df(const double* x, float2* out, long long m, cudaStream_t st) {
+  topo::launch(k_split_df, blocks_for(m), kThreads, 0, st, x, out, m);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_q1_apply_dot(int nx, int ny, const Q1Coef& coef, const double* x,
                                 const double* v, double* y, const uint8_t* fixed, int nrhs,

@@ -453,6 +453,9 @@ topo_status cg_iteration(topo_solver* s, int slot, double tol, int max_iter) {
   if (s->arrow) {
     TOPO_TRY(apply_level<double>(s, 0, 0, s->p, nullptr, s->q, s->sc));
     TOPO_CUDA(launch_cg_alpha(n, 1, s->p, s->q, s->partials, s->counters, s->sc, s->st));
+  } else if (s->q1_ok && s->outer_df && s->xdf) {
+    TOPO_CUDA(launch_q1_apply_dot_df(l0.d.nx, l0.d.ny, s->q1, s->xdf, s->p, s->q, l0.fixed,
+                                     s->nrhs, s->partials, s->counters, s->sc, s->st));
   } else if (s->q1_ok) {
     TOPO_CUDA(launch_q1_apply_dot(l0.d.nx, l0.d.ny, s->q1, s->x, s->p, s->q, l0.fixed, s->nrhs,
                                   s->partials, s->counters, s->sc, s->st));
@@ -716,6 +719,7 @@ topo_status enqueue_build(topo_solver* s) {
   const int ne2 = s->ne * s->ne;
   TOPO_CUDA(cudaMemsetAsync(s->info, 0, 4 * sizeof(int), st));
   TOPO_CUDA(launch_check_positive(s->x, m, s->info + 1, st));
+  if (s->xdf) TOPO_CUDA(launch_split_df(s->x, s->xdf, m, st));
   if (mixed) TOPO_CUDA(launch_convert_d2f(s->x, s->x32, m, st));
   if (s->arrow && mixed) {
     TOPO_CUDA(launch_convert_d2f(s->g, s->g32, m * s->ne, st));
@@ -959,6 +963,10 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   const long long m = s->L[0].m;
   const long long n = s->L[0].n + (arrow ? 2 : 0);
   TOPO_TRY(s->alloc(&s->x, m));
+  if (s->q1_ok && !arrow) {  // pair-arithmetic outer operator: default for mixed solvers
+    TOPO_TRY(s->alloc(&s->xdf, m));
+    s->outer_df = s->prec == TOPO_MIXED ? 1 : 0;
+  }
   if (s->prec == TOPO_MIXED) {
     TOPO_TRY(s->alloc(&s->x32, m));
     TOPO_TRY(s->alloc((float**)&s->rv, n * nrhs));
@@ -1033,6 +1041,26 @@ topo_status topo_solver_create(const topo_solver_desc* d, topo_solver** out) {
     return st;
   }
   *out = s;
+  return TOPO_OK;
+}
+
+topo_status topo_set_outer_precision(topo_solver* s, int mode) {
+  if (!s || (mode != 0 && mode != 1)) {
+    set_error("topo_set_outer_precision: null solver or mode not 0/1");
+    return TOPO_E_INVALID_ARG;
+  }
+  const int want = (mode == 1 && s->xdf) ? 1 : 0;
+  if (want != s->outer_df) {
+    s->outer_df = want;
+    if (s->graph) {  // captured iterations hold the old kernel
+      cudaGraphExecDestroy(s->graph);
+      s->graph = nullptr;
+    }
+    if (s->loop) {
+      cudaGraphExecDestroy(s->loop);
+      s->loop = nullptr;
+    }
+  }
   return TOPO_OK;
 }
 

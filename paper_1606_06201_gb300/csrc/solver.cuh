@@ -65,6 +65,8 @@ struct topo_solver {
   int loop_kernels = 0;                   // kernels per loop iteration
   double loop_tol = -1.0;
   int graph_mode = 0;                     // 0 replayed blocks of iterations, 1 while-node loop
+  float2* xdf = nullptr;                  // densities as float pairs (pair-arithmetic operator)
+  int outer_df = 0;                       // outer operator in float-pair arithmetic (1) or FP64
   bool tail_ok = false;                   // the fused deep-level kernel can run on this device
   bool tail_on = false;                   // and is used (topo_set_vcycle_fusion)
   bool no_loop = false;                   // conditional graphs unavailable on this device

@@ -265,6 +265,13 @@ cudaError_t launch_q1_apply_dot(int nx, int ny, const Q1Coef& coef, const double
                                 double* partials, unsigned* counters, CgScalars* sc,
                                 cudaStream_t st);
 long long q1_partial_blocks(int nx, int ny);
+// The same q = K(x) p with p^T q and alpha in pair-of-FP32 arithmetic (about 48 bits), with the
+// densities split once per hierarchy build (launch_split_df).
+cudaError_t launch_q1_apply_dot_df(int nx, int ny, const Q1Coef& coef, const float2* xdf,
+                                   const double* v, double* y, const uint8_t* fixed, int nrhs,
+                                   double* partials, unsigned* counters, CgScalars* sc,
+                                   cudaStream_t st);
+cudaError_t launch_split_df(const double* x, float2* out, long long m, cudaStream_t st);
 // Jacobi sweep (mode 2) on the 2D finest level fused with r^T y against the FP64 CG residual r and
 // the beta of Algorithm PCG (last smoothing sweep of the preconditioner).
 template <typename T>

@@ -77,6 +77,7 @@ _SIGS = {
     "topo_set_stream": (ctypes.c_int, [_vp, _vp]),
     "topo_set_graph_mode": (ctypes.c_int, [_vp, ctypes.c_int]),
     "topo_set_vcycle_fusion": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "topo_set_outer_precision": (ctypes.c_int, [_vp, ctypes.c_int]),
     "topo_set_profiling_mask": (ctypes.c_int, [_vp, ctypes.c_uint]),
     "topo_get_profile_kernel": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                                ctypes.POINTER(ctypes.c_longlong)]),
@@ -369,6 +370,10 @@ class Solver:
 
     def set_profiling(self, on):
         _check(_lib.topo_set_profiling(self._h, int(bool(on))), "topo_set_profiling")
+
+    def set_outer_precision(self, mode):
+        """Outer CG operator on the 2D finest level: 0 FP64, 1 float pairs (mixed default)."""
+        _check(_lib.topo_set_outer_precision(self._h, int(mode)), "topo_set_outer_precision")
 
     def set_vcycle_fusion(self, on):
         """Fuse the deep levels of the 2D V-cycle into one cluster launch (default on)."""

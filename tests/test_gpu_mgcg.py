@@ -273,6 +273,33 @@ def test_fused_deep_levels_give_identical_bits(precision, shape, nu, nrhs):
     assert out[0][2] == out[1][2]
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pair_arithmetic_outer_operator_reaches_tight_tolerances(precision):
+    """The outer operator in float pairs (about 48 bits): solves to 1e-11 whose true residual, by
+    the oracle's sparse matrix, is at that level; and the same iteration count (within one) and
+    solution (to the conditioning of the solve) as the FP64 operator."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny, levels = 256, 128, 6
+    fixed = W.clamp_xmin(nx, ny)
+    x = _x(nx, ny, 0, 39)
+    f = W.normal_load(fixed, 40)
+    K, free, _ = oracle_K_free(nx, ny, 0, x, fixed.astype(bool))
+    res = {}
+    for mode in (0, 1):
+        s = topo.Solver(nx, ny, fixed=fixed, levels=levels, precision=precision)
+        s.set_outer_precision(mode)
+        s.set_density(dev(torch, x))
+        u, info = s.solve(dev(torch, f), tol=1e-11)
+        uh = host(u)
+        r = np.linalg.norm(f[free] - K @ uh[free]) / np.linalg.norm(f[free])
+        assert r <= 3e-11, (mode, r)
+        res[mode] = (uh, info.iterations)
+        s.close()
+    assert abs(res[0][1] - res[1][1]) <= 1
+    assert rel_err(res[1][0], res[0][0]) <= 1e-9
+
+
 def test_profiling_times_every_kernel_kind_and_keeps_results():
     """Profiling inserts event nodes only: the iterate is bit-identical to an unprofiled solve,
     and every kernel kind of the iteration is timed once per CG iteration."""
