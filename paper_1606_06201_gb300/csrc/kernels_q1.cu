@@ -135,14 +135,28 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, int 
     zero.y = T(0);
     V2 pb = zero;
     if (MODE != 3 && col_ok && j0 >= 1) pb = v2[c + rs * (j0 - 1)];
-    // the loads of row ey + 1 are issued one iteration ahead of their use
-    V2 pt_n = zero, bb_n = zero;
-    T xe_n = T(0);
-    uint16_t fx_n = 0;
+    // Loads run two element rows ahead of their use (a strip is walked row by row, so one row of
+    // lookahead leaves each row waiting for its own loads): *_n is used at the next iteration,
+    // *_nn at the one after.  Element row e needs v of node row e + 1, x of element row e, and b,
+    // the mask (and the FP64 residual for DOT 2) of node row e, the row it outputs.
+    V2 pt_n = zero, pt_nn = zero, bb_n = zero, bb_nn = zero;
+    T xe_n = T(0), xe_nn = T(0);
+    uint16_t fx_n = 0, fx_nn = 0;
+    double2 rr_n = make_double2(0.0, 0.0), rr_nn = make_double2(0.0, 0.0);
     {
-      const int ey = j0 - 1;
+      const int ey = j0 - 1;  // first iteration: element row j0 - 1, no output
       if (MODE != 3 && col_ok && ey + 1 <= ny) pt_n = v2[c + rs * (ey + 1)];
       if (el_col && ey >= 0 && ey < ny) xe_n = x[c + (long long)nx * ey];
+      if (ey + 1 < j1) {  // second iteration: element row j0, output node row j0
+        if (MODE != 3 && col_ok && ey + 2 <= ny) pt_nn = v2[c + rs * (ey + 2)];
+        if (el_col && ey + 1 < ny) xe_nn = x[c + (long long)nx * (ey + 1)];
+        if (out_lane) {
+          const long long nn = c + rs * (ey + 1);
+          fx_nn = *reinterpret_cast<const uint16_t*>(fixed + 2 * nn);
+          if (MODE != 0) bb_nn = b2[nn];
+          if (DOT == 2) rr_nn = reinterpret_cast<const double2*>(rdot)[nn];
+        }
+      }
     }
     T cu = T(0), cv = T(0), xcarry = T(0);
     for (int ey = j0 - 1; ey < j1; ++ey) {
@@ -150,16 +164,22 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, int 
       const T xe = xe_n;
       const V2 bb = bb_n;
       const uint16_t fx = fx_n;
-      // prefetch: v of node row ey + 2, x of element row ey + 1, b and mask of node row ey + 1
-      pt_n = zero;
-      xe_n = T(0);
-      if (ey + 1 < j1) {
-        if (MODE != 3 && col_ok && ey + 2 <= ny) pt_n = v2[c + rs * (ey + 2)];
-        if (el_col && ey + 1 < ny) xe_n = x[c + (long long)nx * (ey + 1)];
-        if (out_lane && ey + 1 >= j0) {
-          const long long nn = c + rs * (ey + 1);
-          fx_n = *reinterpret_cast<const uint16_t*>(fixed + 2 * nn);
-          if (MODE != 0) bb_n = b2[nn];
+      const double2 rr = rr_n;
+      pt_n = pt_nn;
+      xe_n = xe_nn;
+      bb_n = bb_nn;
+      fx_n = fx_nn;
+      rr_n = rr_nn;
+      pt_nn = zero;
+      xe_nn = T(0);
+      if (ey + 2 < j1) {  // loads of the iteration after next: element row ey + 2
+        if (MODE != 3 && col_ok && ey + 3 <= ny) pt_nn = v2[c + rs * (ey + 3)];
+        if (el_col && ey + 2 < ny) xe_nn = x[c + (long long)nx * (ey + 2)];
+        if (out_lane) {
+          const long long nn = c + rs * (ey + 2);
+          fx_nn = *reinterpret_cast<const uint16_t*>(fixed + 2 * nn);
+          if (MODE != 0) bb_nn = b2[nn];
+          if (DOT == 2) rr_nn = reinterpret_cast<const double2*>(rdot)[nn];
         }
       }
       const T pbr_u = shfl_dn(pb.x), pbr_v = shfl_dn(pb.y);
@@ -202,10 +222,7 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, int 
         if (fx >> 8) out.y = T(0);
         reinterpret_cast<V2*>(y)[node] = out;
         if (DOT == 1) part = fma((double)pb.x, (double)out.x, fma((double)pb.y, (double)out.y, part));
-        if (DOT == 2) {
-          const double2 rr = reinterpret_cast<const double2*>(rdot)[node];
-          part = fma(rr.x, (double)out.x, fma(rr.y, (double)out.y, part));
-        }
+        if (DOT == 2) part = fma(rr.x, (double)out.x, fma(rr.y, (double)out.y, part));
       }
       cu = ru[3] + l2u;
       cv = rv[3] + l2v;
@@ -397,26 +414,34 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep_df(int nx, int ny, i
       pbu = df_from_double(t.x);
       pbv = df_from_double(t.y);
     }
-    double2 pt_n = make_double2(0.0, 0.0);
-    float2 xe_n = make_float2(0.0f, 0.0f);
+    // two element rows of lookahead, as in k_q1_sweep
+    double2 pt_n = make_double2(0.0, 0.0), pt_nn = make_double2(0.0, 0.0);
+    float2 xe_n = make_float2(0.0f, 0.0f), xe_nn = make_float2(0.0f, 0.0f);
+    uint16_t fx_n = 0, fx_nn = 0;
     {
       const int ey = j0 - 1;
       if (col_ok && ey + 1 <= ny) pt_n = v2[c + rs * (ey + 1)];
       if (el_col && ey >= 0 && ey < ny) xe_n = xdf[c + (long long)nx * ey];
+      if (ey + 1 < j1) {
+        if (col_ok && ey + 2 <= ny) pt_nn = v2[c + rs * (ey + 2)];
+        if (el_col && ey + 1 < ny) xe_nn = xdf[c + (long long)nx * (ey + 1)];
+        if (out_lane) fx_nn = *reinterpret_cast<const uint16_t*>(fixed + 2 * (c + rs * (ey + 1)));
+      }
     }
-    uint16_t fx_n = 0;
     f2 cu = z, cv = z;
     for (int ey = j0 - 1; ey < j1; ++ey) {
       const f2 ptu = df_from_double(pt_n.x), ptv = df_from_double(pt_n.y);
       const f2 xe = {xe_n.x, xe_n.y};
       const uint16_t fx = fx_n;
-      pt_n = make_double2(0.0, 0.0);
-      xe_n = make_float2(0.0f, 0.0f);
-      if (ey + 1 < j1) {
-        if (col_ok && ey + 2 <= ny) pt_n = v2[c + rs * (ey + 2)];
-        if (el_col && ey + 1 < ny) xe_n = xdf[c + (long long)nx * (ey + 1)];
-        if (out_lane && ey + 1 >= j0)
-          fx_n = *reinterpret_cast<const uint16_t*>(fixed + 2 * (c + rs * (ey + 1)));
+      pt_n = pt_nn;
+      xe_n = xe_nn;
+      fx_n = fx_nn;
+      pt_nn = make_double2(0.0, 0.0);
+      xe_nn = make_float2(0.0f, 0.0f);
+      if (ey + 2 < j1) {
+        if (col_ok && ey + 3 <= ny) pt_nn = v2[c + rs * (ey + 3)];
+        if (el_col && ey + 2 < ny) xe_nn = xdf[c + (long long)nx * (ey + 2)];
+        if (out_lane) fx_nn = *reinterpret_cast<const uint16_t*>(fixed + 2 * (c + rs * (ey + 2)));
       }
       const f2 uu[4] = {pbu, shfl_dn_df(pbu), shfl_dn_df(ptu), ptu};
       const f2 vv[4] = {pbv, shfl_dn_df(pbv), shfl_dn_df(ptv), ptv};
@@ -517,16 +542,43 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, int
   const float2* v2 = reinterpret_cast<const float2*>(v);
   float2 pb = make_float2(0.f, 0.f);
   if (MODE != 3 && col_ok && j0 >= 1) pb = v2[c + (long long)(nx + 1) * (j0 - 1)];
+  // Two element rows of lookahead (see k_q1_sweep): iteration e reads v of node row e + 1, the
+  // four child densities of coarse element row e, and b, invd and the mask of node row e.
+  const long long rs = nx + 1;
+  const float2 z2 = make_float2(0.f, 0.f);
+  float2 pt_n = z2, pt_nn = z2, xb_n = z2, xb_nn = z2, xt_n = z2, xt_nn = z2;
+  float2 bb_n = z2, bb_nn = z2, di_n = z2, di_nn = z2;
+  uint16_t fx_n = 0, fx_nn = 0;
+  auto load_row = [&](int e, float2& pt, float2& xb, float2& xt, float2& bb, float2& di,
+                      uint16_t& fx) {
+    pt = z2;
+    xb = z2;
+    xt = z2;
+    if (MODE != 3 && col_ok && e + 1 <= ny) pt = v2[c + rs * (e + 1)];
+    if (MODE != 3 && el_col && e >= 0 && e < ny) {
+      xb = *reinterpret_cast<const float2*>(xf + 2 * c + (long long)fnx * (2 * e));
+      xt = *reinterpret_cast<const float2*>(xf + 2 * c + (long long)fnx * (2 * e + 1));
+    }
+    if (e >= j0 && out_lane) {
+      const long long node = c + rs * e;
+      fx = *reinterpret_cast<const uint16_t*>(fixed + 2 * node);
+      if (MODE != 0) bb = reinterpret_cast<const float2*>(b)[node];
+      if (MODE == 2 || MODE == 3) di = reinterpret_cast<const float2*>(invd)[node];
+    }
+  };
+  load_row(j0 - 1, pt_n, xb_n, xt_n, bb_n, di_n, fx_n);
+  if (j0 < j1) load_row(j0, pt_nn, xb_nn, xt_nn, bb_nn, di_nn, fx_nn);
   float cu = 0.f, cv = 0.f;
   for (int ey = j0 - 1; ey < j1; ++ey) {
-    float2 pt = make_float2(0.f, 0.f);
-    if (MODE != 3 && col_ok && ey + 1 <= ny) pt = v2[c + (long long)(nx + 1) * (ey + 1)];
-    const bool el_ok = el_col && ey >= 0 && ey < ny;
-    float2 xb = make_float2(0.f, 0.f), xt = make_float2(0.f, 0.f);
-    if (MODE != 3 && el_ok) {
-      xb = *reinterpret_cast<const float2*>(xf + 2 * c + (long long)fnx * (2 * ey));
-      xt = *reinterpret_cast<const float2*>(xf + 2 * c + (long long)fnx * (2 * ey + 1));
-    }
+    const float2 pt = pt_n, xb = xb_n, xt = xt_n, bb = bb_n, di = di_n;
+    const uint16_t fx = fx_n;
+    pt_n = pt_nn;
+    xb_n = xb_nn;
+    xt_n = xt_nn;
+    bb_n = bb_nn;
+    di_n = di_nn;
+    fx_n = fx_nn;
+    if (ey + 2 < j1) load_row(ey + 2, pt_nn, xb_nn, xt_nn, bb_nn, di_nn, fx_nn);
     const float pbr_u = shfl_dn(pb.x), pbr_v = shfl_dn(pb.y);
     const float ptr_u = shfl_dn(pt.x), ptr_v = shfl_dn(pt.y);
     float R[4][2] = {};  // coarse local nodes (0,0) (1,0) (1,1) (0,1), components u, v
@@ -569,19 +621,16 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, int
     const float l2u = shfl_up1(R[2][0]), l2v = shfl_up1(R[2][1]);
     if (ey >= j0 && out_lane) {
       const float qu = cu + R[0][0] + l1u, qv = cv + R[0][1] + l1v;
-      const long long node = c + (long long)(nx + 1) * ey;
-      const uint16_t fx = *reinterpret_cast<const uint16_t*>(fixed + 2 * node);
+      const long long node = c + rs * ey;
       float2 out;
       if (MODE == 0) {
         out.x = qu;
         out.y = qv;
       } else {
-        const float2 bb = reinterpret_cast<const float2*>(b)[node];
         if (MODE == 1) {
           out.x = bb.x - qu;
           out.y = bb.y - qv;
         } else {
-          const float2 di = reinterpret_cast<const float2*>(invd)[node];
           if (MODE == 2) {
             out.x = fmaf(omega * di.x, bb.x - qu, pb.x);
             out.y = fmaf(omega * di.y, bb.y - qv, pb.y);

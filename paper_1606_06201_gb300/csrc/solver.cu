@@ -755,6 +755,9 @@ topo_status enqueue_build(topo_solver* s) {
   }
   for (int k = 0; k < nl - 1; ++k) {
     Level& lv = s->L[k];
+    // the 2D Q1 sweeps form the finest diagonal from x on the fly; only the power iteration and
+    // the Chebyshev smoother read it from invd
+    if (k == 0 && s->q1_ok && !s->arrow && !lv.omega_dev && !lv.lam_dev) continue;
     if (k >= 1 && !lv.Ae && lv.Ae32) {  // FP32 hierarchy level: FP32 diagonal only
       TOPO_CUDA(launch_inv_diag32(lv.d, lv.Ae32, lv.fixed, lv.invd32, st));
       continue;
