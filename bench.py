@@ -38,13 +38,26 @@ WORKLOAD = "mgcg_2d_q1_2048x1024_9lev_logunif_box5_normal_load"
 # (add, multiply and fused multiply-add each occupy one issue slot; a probe on this part measured
 # 0.60e12 FP64 FMA/s = 1.20 TFLOP/s).
 FP64_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
-# FP64 operations of the butterfly operator kernel: 40 per element (two 4-point butterflies per
-# displacement component, 13 scalings, two inverse butterflies) + 6 node-assembly adds + 2 FMA of
-# the fused p^T q per node.
+# FP32 pipe peak the same way: 152 SMs x 128 FP32 lanes x 2.07 GHz, one operation per lane and
+# clock (an FMA counts as one).
+FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+# FP64 operations of the FP64 butterfly operator kernel: 40 per element (two 4-point butterflies
+# per displacement component, 13 scalings, two inverse butterflies) + 6 node-assembly adds + 2 FMA
+# of the fused p^T q per node.
 OPS_PER_ELEM, OPS_PER_NODE = 40.0, 8.0
-# DRAM bytes of one launch of that kernel on this workload from an ncu capture
+# FP32 operations of the same operator in float pairs: per element 29 pair additions (11 FP32
+# operations each: TwoSum, the low parts, a renormalising FastTwoSum) and 12 pair products (7:
+# product, FMA error term, two cross FMAs, FastTwoSum), plus the 2 pair additions of the carried
+# node sums; per output node 4 pair additions of the node sums and 2 products + 2 additions of
+# p^T q, and 2 FP32 multiplies of each of the two input splits.
+DF_OPS_PER_ELEM = 29 * 11 + 12 * 7 + 2 * 11
+DF_OPS_PER_NODE = 4 * 11 + 2 * 7 + 2 * 11 + 4
+# DRAM bytes of one launch of the FP64 operator on this workload from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum = 55.21 MB + 3.51 MB).
 OPERATOR_DRAM_BYTES = 58712320.0
+# The same for the float-pair operator (ncu capture of k_q1_sweep_df on this workload:
+# 54.94 MB read + 2.53 MB write).
+DF_OPERATOR_DRAM_BYTES = 57463808.0
 
 
 def _measured_hbm_gbs():
@@ -174,6 +187,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ip", action="store_true", help="skip the 512x256 IP/OC wall-time runs")
+    ap.add_argument("--outer-fp64", action="store_true",
+                    help="mixed solver with the FP64 outer operator instead of float pairs")
     ap.add_argument("--only", choices=["mixed", "fp64"], default=None,
                     help="run one solver configuration only (for profiler launch lists); no JSON line")
     args = ap.parse_args()
@@ -207,6 +222,8 @@ def main():
 
     def run(precision, steps, warmup, profile_mask=0, host_io=False):
         s = topo.Solver(NX, NY, fixed=cfg["fixed"], levels=LEVELS, precision=precision)
+        if args.outer_fp64:
+            s.set_outer_precision(0)
         u_d = torch.zeros_like(f_d)
         if host_io:
             x_h = torch.as_tensor(cfg["x"]).pin_memory()
@@ -261,7 +278,7 @@ def main():
     with ClockSampler(dev.index) as clk:
         # headline: event pairs around the outer operator only (one pair adds ~nothing)
         mixed = run(topo.MIXED, args.steps, args.warmup, profile_mask=1)
-        fp64 = run(topo.FP64, args.steps, args.warmup)
+        fp64 = run(topo.FP64, args.steps, args.warmup, profile_mask=1)
         e2e = run(topo.MIXED, args.steps, args.warmup, host_io=True)
         # separate run with every kind profiled, for the per-kernel and per-part times (its own
         # step time is longer by the extra event nodes and is not reported)
@@ -309,30 +326,53 @@ def main():
     if rank == 0:
         m, n = NX * NY, cfg["f"].size
         nodes = (NX + 1) * (NY + 1)
-        ops_per_launch = OPS_PER_ELEM * m + OPS_PER_NODE * nodes
         op_ms, op_cnt = mixed["prof"]
         op_avg_ms = op_ms / op_cnt if op_cnt else float("nan")
-        achieved = ops_per_launch / (op_avg_ms * 1e-3) / 1e12
-        roof = {"kernel": "k_q1_sweep<double,0,1> (outer FP64 operator q = K(x) p, fused p^T q)",
-                "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TOPS,
-                "unit": "T FP64-op/s", "frac": achieved / FP64_PEAK_TOPS,
-                "traffic": OPERATOR_DRAM_BYTES,
-                "peak_source": "derived: 152 SMs x 2 FP64 issue slots/clk x 2.07 GHz",
-                "algorithmic_ops_per_launch": ops_per_launch,
-                "algorithmic_bytes_per_launch": 8.0 * m + 16.0 * n + 1.0 * n,
-                "dense_form_tflops": (144.0 * m + 2.0 * n) / (op_avg_ms * 1e-3) / 1e12,
-                "avg_launch_ms": op_avg_ms, "launches_timed": op_cnt}
+        alg_bytes = 8.0 * m + 16.0 * n + 1.0 * n  # densities (FP64 or float pair), p, q, mask
+        if args.outer_fp64:
+            ops_per_launch = OPS_PER_ELEM * m + OPS_PER_NODE * nodes
+            achieved = ops_per_launch / (op_avg_ms * 1e-3) / 1e12
+            roof = {"kernel": "k_q1_sweep<double,0,1> (outer FP64 operator q = K(x) p, fused p^T q)",
+                    "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TOPS,
+                    "unit": "T FP64-op/s", "frac": achieved / FP64_PEAK_TOPS,
+                    "traffic": OPERATOR_DRAM_BYTES,
+                    "peak_source": "derived: 152 SMs x 2 FP64 issue slots/clk x 2.07 GHz"}
+        else:
+            ops_per_launch = DF_OPS_PER_ELEM * m + DF_OPS_PER_NODE * nodes
+            achieved = ops_per_launch / (op_avg_ms * 1e-3) / 1e12
+            roof = {"kernel": "k_q1_sweep_df (outer operator q = K(x) p in float pairs, fused p^T q)",
+                    "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TOPS,
+                    "unit": "T FP32-op/s", "frac": achieved / FP32_PEAK_TOPS,
+                    "traffic": DF_OPERATOR_DRAM_BYTES,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"}
+        roof.update({"algorithmic_ops_per_launch": ops_per_launch,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "hbm_gbs_at_algorithmic_bytes": alg_bytes / (op_avg_ms * 1e-3) / 1e9,
+                     "avg_launch_ms": op_avg_ms, "launches_timed": op_cnt})
+        f_ms, f_cnt = fp64["prof"]
+        fp64_op = None
+        if f_cnt:
+            f_avg = f_ms / f_cnt
+            f_ops = OPS_PER_ELEM * m + OPS_PER_NODE * nodes
+            fp64_op = {"kernel": "k_q1_sweep<double,0,1> (FP64 solver's outer operator)",
+                       "bound": "alu", "achieved": f_ops / (f_avg * 1e-3) / 1e12,
+                       "peak": FP64_PEAK_TOPS, "unit": "T FP64-op/s",
+                       "frac": f_ops / (f_avg * 1e-3) / 1e12 / FP64_PEAK_TOPS,
+                       "traffic": OPERATOR_DRAM_BYTES, "avg_launch_ms": f_avg,
+                       "launches_timed": f_cnt}
         # HBM-bound kernels of the FP32 V-cycle on the finest level, timed live like the operator:
         # algorithmic bytes per launch (FP32 vectors of n DOFs, FP32 densities of m elements, the
         # byte mask) / average launch time, against the measured copy bandwidth.
         hbm_peak = _measured_hbm_gbs()
         nc = ((NX // 2) + 1) * ((NY // 2) + 1) * 2
         hbm_bytes = {
-            "fine_smoothing_sweep": ("k_q1_sweep<float,2,0>: z' = z + omega D^-1 (b - K(x) z), "
-                                     "diag from x", 4.0 * m + 13.0 * n),
+            "fine_smoothing_sweep": ("k_q1_fused<float,4>: first two Jacobi sweeps from zero, "
+                                     "z = omega D^-1 b formed on the fly, diag from x",
+                                     4.0 * m + 9.0 * n),
             "fine_residual": ("k_q1_sweep<float,1,0>: r = b - K(x) z", 4.0 * m + 13.0 * n),
             "fine_restriction": ("k_restrict<2,float>: b_c = P^T r", 4.0 * n + 5.0 * nc),
-            "fine_prolongation": ("k_prolong_add<2,float>: z += P z_c", 9.0 * n + 4.0 * nc),
+            "fine_prolongation": ("k_q1_fused<float,5>: v = z + P z_c formed on the fly, then "
+                                  "one Jacobi sweep", 4.0 * m + 13.0 * n + 4.0 * nc),
         }
         hbm_kernels = []
         for k, key in enumerate(topo.Solver.PROFILE_KINDS):
@@ -372,7 +412,8 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycle + f64 CG",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycle + f64 CG" + (" (f64 outer operator)" if args.outer_fp64 else
+                                                 " (outer operator in f32 pairs, ~48-bit)"),
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "levels": LEVELS, "tol": TOL,
                        "free_dofs": nfree, "smoother": "damped Jacobi omega=0.6 nu1=nu2=2",
@@ -380,7 +421,8 @@ def main():
                        "l2": "working set > L2 (vectors 33.6 MB each, ~0.5 GB resident)"},
             "iterations_per_solve": mixed["iters"] / args.steps, "final_rel_residual": mixed["res"],
             "fp64": {"value": ws * nfree * fp64["iters"] / (ms_fp64 * 1e-3), "unit": UNIT,
-                     "ms_per_step": ms_fp64 / args.steps, "iterations_per_solve": fp64["iters"] / args.steps},
+                     "ms_per_step": ms_fp64 / args.steps, "iterations_per_solve": fp64["iters"] / args.steps,
+                     "operator_roofline": fp64_op},
             "roofline": roof,
             "hbm_kernels": hbm_kernels,
             "iteration_breakdown": breakdown,

@@ -110,10 +110,12 @@ topo_status topo_set_stream(topo_solver* s, void* cuda_stream);
  * (falls back to mode 0 where conditional graph nodes are unavailable, and while profiling).
  * Other modes -> E_INVALID_ARG. */
 topo_status topo_set_graph_mode(topo_solver* s, int mode);
-/* Algorithm MG on the deep levels of a 2D K system with Jacobi smoothing: on (default, where the
- * device can run it) the levels from the first one of at most a few thousand nodes down to the
- * coarsest run in one launch of a thread-block cluster per right-hand side; off, one launch per
- * sweep, residual and transfer.  Both give the same bits.  Other systems ignore the setting. */
+/* Fused kernels in Algorithm MG for 2D K systems with Jacobi smoothing (default on; off: one
+ * launch per sweep, residual and transfer).  On the finest level the first two sweeps from zero
+ * are one kernel, and so are the prolongation with the first post-smoothing sweep; the levels
+ * from the first one of at most 1024 nodes down to the coarsest run in one launch of a
+ * thread-block cluster per right-hand side (where the device can run it).  Both settings give
+ * the same bits.  Other systems ignore the setting. */
 topo_status topo_set_vcycle_fusion(topo_solver* s, int on);
 /* Arithmetic of the outer operator q = K(x) p of Algorithm PCG on the 2D finest level of K
  * systems: 0 = FP64; 1 = pairs of FP32 values (hi + lo, about 48 significant bits, FP64 in and
@@ -138,9 +140,10 @@ topo_status topo_set_profiling(topo_solver* s, int on);
 topo_status topo_set_profiling_mask(topo_solver* s, unsigned mask);
 topo_status topo_get_profile(const topo_solver* s, double* operator_ms_total, long long* count);
 /* The same for other parts of the iteration (kind 0 = the outer operator, as topo_get_profile).
- * Finest level of the V-cycle, in the V-cycle precision: 1 = the first plain smoothing sweep
- * (z <- z + omega D^{-1} (b - A z) with z != 0), 2 = the residual b - A z before restriction,
- * 3 = the restriction P^T r, 4 = the prolongation and correction z += P z_c.  Spans of several
+ * Finest level of the V-cycle, in the V-cycle precision: 1 = the first smoothing kernel with a
+ * matrix product (the fused first two sweeps, or the first sweep from z != 0), 2 = the residual
+ * b - A z before restriction, 3 = the restriction P^T r, 4 = the prolongation and correction
+ * z += P z_c (fused with the first post-smoothing sweep where the V-cycle fuses).  Spans of several
  * kernels: 5 = the whole V-cycle (preconditioner), 6 = its part on levels >= 1, 7 = its part on
  * levels >= 2 (coarsest solve included).  A kind that the solver's V-cycle does not run has
  * count 0.  kind outside 0..7 -> E_INVALID_ARG. */

@@ -270,6 +270,180 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, int 
   }
 }
 
+// ---- Fused pairs of V-cycle steps on the finest level ----------------------------------------
+// MODE 4: the first two damped-Jacobi sweeps from zero, z = omega D^{-1} b then
+//         y = z + omega D^{-1} (b - K z), with z formed on the fly from b and x (no z pass).
+// MODE 5: the prolongation and correction t + P zc followed by one sweep on the corrected
+//         iterate, y = v + omega D^{-1} (b - K v) with v = t + P zc formed on the fly (zc: the
+//         level-1 correction, (nx/2 + 1) x (ny/2 + 1) nodes).
+// The per-node arithmetic and its order are those of k_q1_sweep (modes 3 and 2) and k_prolong_add,
+// so the results are the same bits as the unfused steps.  Loads run one element row ahead.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kQ1Warps * 32) k_q1_fused(int nx, int ny, int rows, Q1K<T> k,
+                                                             const T* __restrict__ x,
+                                                             const T* __restrict__ t,
+                                                             const T* __restrict__ zc,
+                                                             const T* __restrict__ b,
+                                                             T* __restrict__ y, T omega,
+                                                             const uint8_t* __restrict__ fixed,
+                                                             const CgScalars* sc) {
+  static_assert(MODE == 4 || MODE == 5, "fused modes");
+  pdl_prologue();
+  using V2 = typename Vec2<T>::type;
+  const int rhs = blockIdx.y;
+  if (sc && sc[rhs].done) return;
+  const long long n = 2LL * (nx + 1) * (ny + 1);
+  const long long ncn = (long long)(nx / 2 + 1) * (ny / 2 + 1);
+  b += rhs * n;
+  y += rhs * n;
+  if (MODE == 5) {
+    t += rhs * n;
+    zc += rhs * 2 * ncn;
+  }
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kQ1Warps + (threadIdx.x >> 5);
+  const int ncolw = (nx + 1 + kQ1Cols - 1) / kQ1Cols;
+  const int nstrip = (ny + 1 + rows - 1) / rows;
+  const int wc = gw % ncolw, ws = gw / ncolw;
+  if (ws >= nstrip) return;
+  const int c = wc * kQ1Cols - 1 + lane;
+  const bool col_ok = (c >= 0 && c <= nx);
+  const bool out_lane = (lane >= 1 && lane <= kQ1Cols && col_ok);
+  const bool el_col = (lane <= kQ1Cols && c >= 0 && c < nx);
+  // MODE 4 forms D^{-1} on every lane's node: every lane needs its own element column's density
+  // and lane 0 also the one to its left (the other lanes get it by a shuffle)
+  const bool xcol = MODE == 4 ? (c >= 0 && c < nx) : el_col;
+  const bool xleft0 = MODE == 4 && lane == 0 && c - 1 >= 0 && c - 1 < nx;
+  const int j0 = ws * rows;
+  const int j1 = min(j0 + rows, ny + 1);
+  const long long rs = nx + 1;
+  const long long crs = nx / 2 + 1;
+  const V2* b2 = reinterpret_cast<const V2*>(b);
+  const V2* t2 = reinterpret_cast<const V2*>(t);
+  const V2* zc2 = reinterpret_cast<const V2*>(zc);
+  V2 zero;
+  zero.x = T(0);
+  zero.y = T(0);
+  // raw data of node row r (element row r for the densities)
+  struct Raw {
+    V2 b, t, z00, z10, z01, z11;
+    T xe, xl0;
+    uint16_t fx;
+  };
+  auto load = [&](int r, Raw& R) {
+    R.b = zero;
+    R.t = zero;
+    R.z00 = R.z10 = R.z01 = R.z11 = zero;
+    R.xe = T(0);
+    R.xl0 = T(0);
+    R.fx = 0;
+    if (r < 0 || r > ny) return;
+    if (xcol && r < ny) R.xe = x[c + (long long)nx * r];
+    if (xleft0 && r < ny) R.xl0 = x[c - 1 + (long long)nx * r];
+    if (!col_ok) return;
+    const long long nd = c + rs * r;
+    R.fx = *reinterpret_cast<const uint16_t*>(fixed + 2 * nd);
+    R.b = b2[nd];
+    if (MODE == 5) {
+      R.t = t2[nd];
+      const int i0 = c >> 1, i1 = (c + 1) >> 1, q0 = r >> 1, q1 = (r + 1) >> 1;
+      R.z00 = zc2[i0 + crs * q0];
+      R.z10 = zc2[i1 + crs * q0];
+      R.z01 = zc2[i0 + crs * q1];
+      R.z11 = zc2[i1 + crs * q1];
+    }
+  };
+  // xpair(r) = x(c, r) + x(c - 1, r), the left density by a shuffle (lane 0: its own load)
+  auto xpair_of = [&](const Raw& R) {
+    const T xl = shfl_up1(R.xe);
+    return R.xe + (lane >= 1 ? xl : (MODE == 4 ? R.xl0 : T(0)));
+  };
+  auto dinv_of = [&](T xs) { return xs > T(0) ? T(1) / (k.kd * xs) : T(1); };
+  // the input node value v(r) of the sweep
+  auto input = [&](int r, const Raw& R, T xpair_prev, T xpair_r) {
+    V2 v = zero;
+    if (MODE == 4) {
+      const T dinv = dinv_of(xpair_prev + xpair_r);
+      v.x = omega * dinv * R.b.x;
+      v.y = omega * dinv * R.b.y;
+      if (R.fx & 0xff) v.x = T(0);
+      if (R.fx >> 8) v.y = T(0);
+    } else {
+      const T wxh = (c & 1) ? T(0.5) : T(1);
+      const T wyh = (r & 1) ? T(0.5) : T(1);
+      const T w = wxh * wyh * T(1);
+      T ax = T(0), ay = T(0);
+      ax = fma(w, R.z00.x, ax);
+      ay = fma(w, R.z00.y, ay);
+      if (c & 1) {
+        ax = fma(w, R.z10.x, ax);
+        ay = fma(w, R.z10.y, ay);
+      }
+      if (r & 1) {
+        ax = fma(w, R.z01.x, ax);
+        ay = fma(w, R.z01.y, ay);
+        if (c & 1) {
+          ax = fma(w, R.z11.x, ax);
+          ay = fma(w, R.z11.y, ay);
+        }
+      }
+      v = R.t;
+      if (!(R.fx & 0xff)) v.x = R.t.x + ax;
+      if (!(R.fx >> 8)) v.y = R.t.y + ay;
+    }
+    return v;
+  };
+  // start: rows j0 - 2 (densities only), j0 - 1 (the first element row) and j0 (its top nodes)
+  Raw Rm, Rc, Rn;
+  load(j0 - 2, Rm);
+  load(j0 - 1, Rc);
+  load(j0, Rn);
+  T xpair_m = xpair_of(Rm);
+  if (j0 - 2 < 0) xpair_m = T(0);
+  T xpair_c = xpair_of(Rc);
+  V2 pb = (j0 - 1 >= 0 && col_ok) ? input(j0 - 1, Rc, xpair_m, xpair_c) : zero;
+  T xcarry = T(0);
+  T cu = T(0), cv = T(0);
+  for (int ey = j0 - 1; ey < j1; ++ey) {
+    const Raw R = Rc;   // node row ey: b, mask; element row ey: density
+    const Raw N = Rn;   // node row ey + 1
+    if (ey + 2 <= ny && ey + 1 < j1) load(ey + 2, Rn);
+    else Rn = Raw{zero, zero, zero, zero, zero, zero, T(0), T(0), 0};
+    Rc = N;
+    const T xpair_n = xpair_of(N);
+    const V2 pt = (ey + 1 <= ny && col_ok) ? input(ey + 1, N, xpair_c, xpair_n) : zero;
+    const T xe = el_col ? R.xe : T(0);
+    const T pbr_u = shfl_dn(pb.x), pbr_v = shfl_dn(pb.y);
+    const T ptr_u = shfl_dn(pt.x), ptr_v = shfl_dn(pt.y);
+    T ru[4], rv[4];
+    {
+      const T uu[4] = {pb.x, pbr_u, ptr_u, pt.x};
+      const T vv[4] = {pb.y, pbr_v, ptr_v, pt.y};
+      q1_element<T>(k, xe, uu, vv, ru, rv);
+    }
+    const T l1u = shfl_up1(ru[1]), l1v = shfl_up1(rv[1]);
+    const T l2u = shfl_up1(ru[2]), l2v = shfl_up1(rv[2]);
+    const T xl = shfl_up1(xe);
+    const T xpair = xe + (lane >= 1 ? xl : T(0));
+    if (ey >= j0 && out_lane) {
+      const T qu = cu + ru[0] + l1u, qv = cv + rv[0] + l1v;
+      const T xs = xcarry + xpair;
+      const T dinv = dinv_of(xs);
+      V2 out;
+      out.x = fma(omega * dinv, R.b.x - qu, pb.x);
+      out.y = fma(omega * dinv, R.b.y - qv, pb.y);
+      if (R.fx & 0xff) out.x = T(0);
+      if (R.fx >> 8) out.y = T(0);
+      reinterpret_cast<V2*>(y)[c + rs * ey] = out;
+    }
+    cu = ru[3] + l2u;
+    cv = rv[3] + l2v;
+    xcarry = xpair;
+    xpair_c = xpair_n;
+    pb = pt;
+  }
+}
+
 // ---- Outer operator in pair-of-FP32 arithmetic ------------------------------------------------
 // GB300 issues about 2 FP64 operations per clock per SM against 128 FP32 ones, so the FP64 outer
 // operator of the mixed solver is ALU-bound at ~40 FP64 operations per element.  This variant
@@ -751,6 +925,29 @@ template cudaError_t launch_q1_smooth_beta<float>(int, int, const Q1Coef&, const
                                                   const float*, const float*, float*, float,
                                                   const uint8_t*, int, const double*, double*,
                                                   unsigned*, CgScalars*, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_q1_fused(int nx, int ny, int mode, const Q1Coef& coef, const T* x, const T* t,
+                            const T* zc, const T* b, T* y, T omega, const uint8_t* fixed,
+                            int nrhs, const CgScalars* sc, cudaStream_t st) {
+  dim3 grid(q1_blocks(nx, ny), nrhs);
+  const Q1K<T> k = coef_cast<T>(coef);
+  if (mode == 4)
+    topo::launch(k_q1_fused<T, 4>, grid, kQ1Warps * 32, 0, st, nx, ny, q1_rows(nx, ny), k, x, t,
+                 zc, b, y, omega, fixed, sc);
+  else
+    topo::launch(k_q1_fused<T, 5>, grid, kQ1Warps * 32, 0, st, nx, ny, q1_rows(nx, ny), k, x, t,
+                 zc, b, y, omega, fixed, sc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_q1_fused<double>(int, int, int, const Q1Coef&, const double*,
+                                             const double*, const double*, const double*, double*,
+                                             double, const uint8_t*, int, const CgScalars*,
+                                             cudaStream_t);
+template cudaError_t launch_q1_fused<float>(int, int, int, const Q1Coef&, const float*,
+                                            const float*, const float*, const float*, float*,
+                                            float, const uint8_t*, int, const CgScalars*,
+                                            cudaStream_t);
 
 namespace {
 f2 df_const(double c) {

@@ -307,7 +307,7 @@ topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* 
 // kTailNodes nodes on the first fused level and kTailMax fused levels.
 template <typename TV>
 int tail_level(const topo_solver* s) {
-  if (!s->tail_on || s->dim != 2 || s->arrow || s->desc.smoother != 0) return -1;
+  if (!s->fuse_on || !s->tail_ok || s->dim != 2 || s->arrow || s->desc.smoother != 0) return -1;
   const int last = s->nlev - 1;
   for (int k = 1; k < last; ++k) {
     if (s->L[k].d.nodes() > kTailNodes || s->nlev - k > kTailMax) continue;
@@ -386,8 +386,22 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
     return TOPO_OK;
   }
   const bool fine = (k == 0);
-  bool sweep_timed = false;  // profiling: the first plain sweep of the finest level
-  if (nu1 >= 1) {
+  // finest 2D Q1 level: the first two sweeps, and the prolongation with the first post-sweep, as
+  // single fused kernels (the same bits)
+  const bool fine_fused = fine && s->fuse_on && s->q1_ok && !s->arrow;
+  bool sweep_timed = false;  // profiling: the first smoothing kernel of the finest level
+  if (nu1 >= 2 && fine_fused) {
+    TOPO_TRY(prof_mark(s, 1, 0));
+    TOPO_CUDA(launch_q1_fused<TV>(lv.d.nx, lv.d.ny, 4, s->q1, Prec<TV>::x(s), nullptr, nullptr, b,
+                                  oth, (TV)s->desc.omega, lv.fixed, nrhs, sc, s->st));
+    TOPO_TRY(prof_mark(s, 1, 1));
+    sweep_timed = true;
+    std::swap(cur, oth);
+    for (int it = 2; it < nu1; ++it) {
+      TOPO_TRY(apply_level<TV>(s, k, 2, cur, b, oth, sc));
+      std::swap(cur, oth);
+    }
+  } else if (nu1 >= 1) {
     TOPO_TRY(apply_level<TV>(s, k, 3, cur, b, cur, sc));
     for (int it = 1; it < nu1; ++it) {
       const bool t = fine && !sweep_timed;
@@ -412,10 +426,20 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
   if (sub_kind > 0) TOPO_TRY(prof_mark(s, sub_kind, 0));
   TOPO_TRY(vcycle<TV>(s, k + 1, (const TV*)lc.b, &zc, sc, false));
   if (sub_kind > 0) TOPO_TRY(prof_mark(s, sub_kind, 1));
-  if (fine) TOPO_TRY(prof_mark(s, 4, 0));
-  TOPO_CUDA(launch_prolong_add<TV>(lv.d, zc, cur, lv.fixed, nrhs, sc, s->st, s->arrow));
-  if (fine) TOPO_TRY(prof_mark(s, 4, 1));
-  for (int it = 0; it < nu2; ++it) {
+  int it0 = 0;
+  if (fine_fused && nu2 >= 1 && !(fuse_beta && nu2 == 1)) {
+    TOPO_TRY(prof_mark(s, 4, 0));
+    TOPO_CUDA(launch_q1_fused<TV>(lv.d.nx, lv.d.ny, 5, s->q1, Prec<TV>::x(s), cur, zc, b, oth,
+                                  (TV)s->desc.omega, lv.fixed, nrhs, sc, s->st));
+    TOPO_TRY(prof_mark(s, 4, 1));
+    std::swap(cur, oth);
+    it0 = 1;
+  } else {
+    if (fine) TOPO_TRY(prof_mark(s, 4, 0));
+    TOPO_CUDA(launch_prolong_add<TV>(lv.d, zc, cur, lv.fixed, nrhs, sc, s->st, s->arrow));
+    if (fine) TOPO_TRY(prof_mark(s, 4, 1));
+  }
+  for (int it = it0; it < nu2; ++it) {
     if (fuse_beta && k == 0 && it == nu2 - 1) {
       TOPO_CUDA(launch_q1_smooth_beta<TV>(lv.d.nx, lv.d.ny, s->q1, Prec<TV>::x(s), cur, b, oth,
                                           (TV)s->desc.omega, lv.fixed, nrhs, s->r, s->partials,
@@ -955,7 +979,6 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   TOPO_CUDA(prepare_coarse_kernels((int)na));
   s->tail_ok = prepare_tail_kernels() == cudaSuccess;  // a cluster of the fused kernel fits
   cudaGetLastError();
-  s->tail_on = s->tail_ok;
   TOPO_TRY(s->alloc(&s->Adense, na * na));
   TOPO_TRY(s->alloc(&s->Ainv, na * na));
   TOPO_TRY(s->alloc(&s->info, 4));
@@ -1072,9 +1095,9 @@ topo_status topo_set_vcycle_fusion(topo_solver* s, int on) {
     set_error("topo_set_vcycle_fusion: null solver");
     return TOPO_E_INVALID_ARG;
   }
-  const bool want = on != 0 && s->tail_ok;
-  if (want != s->tail_on) {
-    s->tail_on = want;
+  const bool want = on != 0;
+  if (want != s->fuse_on) {
+    s->fuse_on = want;
     for (int u = 0; u < 2; ++u)  // captured graphs hold the old V-cycle
       if (s->setup[u]) {
         cudaGraphExecDestroy(s->setup[u]);

@@ -68,7 +68,7 @@ struct topo_solver {
   float2* xdf = nullptr;                  // densities as float pairs (pair-arithmetic operator)
   int outer_df = 0;                       // outer operator in float-pair arithmetic (1) or FP64
   bool tail_ok = false;                   // the fused deep-level kernel can run on this device
-  bool tail_on = false;                   // and is used (topo_set_vcycle_fusion)
+  bool fuse_on = true;                    // fused V-cycle kernels in use (topo_set_vcycle_fusion)
   bool no_loop = false;                   // conditional graphs unavailable on this device
   cudaGraphExec_t graph = nullptr;        // graph_iters CG iterations (profiling runs)
   int graph_kernels = 0;

@@ -265,6 +265,13 @@ cudaError_t launch_q1_apply_dot(int nx, int ny, const Q1Coef& coef, const double
                                 double* partials, unsigned* counters, CgScalars* sc,
                                 cudaStream_t st);
 long long q1_partial_blocks(int nx, int ny);
+// Fused pairs of finest-level V-cycle steps (same bits as the separate steps): mode 4 = the first
+// two Jacobi sweeps from zero (b -> y); mode 5 = prolongation and correction t + P zc followed by
+// one Jacobi sweep (t, zc -> y).  zc: the first coarse level's vector.
+template <typename T>
+cudaError_t launch_q1_fused(int nx, int ny, int mode, const Q1Coef& coef, const T* x, const T* t,
+                            const T* zc, const T* b, T* y, T omega, const uint8_t* fixed,
+                            int nrhs, const CgScalars* sc, cudaStream_t st);
 // The same q = K(x) p with p^T q and alpha in pair-of-FP32 arithmetic (about 48 bits), with the
 // densities split once per hierarchy build (launch_split_df).
 cudaError_t launch_q1_apply_dot_df(int nx, int ny, const Q1Coef& coef, const float2* xdf,
