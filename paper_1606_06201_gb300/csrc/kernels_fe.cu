@@ -39,14 +39,34 @@ __device__ __forceinline__ T vld(const T* p) {
   else return __ldg(p);
 }
 
+// Entries of the vector a sweep multiplies, by DOF index.  VLoad reads a stored vector; VJac0 forms
+// the first Jacobi sweep from zero, omega D^{-1} b (as apply_node MODE 3), so that the fused mode 4
+// of apply_node sweeps on it without storing it: the same arithmetic in the same order.
+template <bool COH, typename T>
+struct VLoad {
+  const T* v;
+  __device__ __forceinline__ T operator()(long long i) const { return vld<COH>(v + i); }
+};
+
+template <bool COH, typename T>
+struct VJac0 {
+  const T* b;
+  const T* invd;
+  const uint8_t* fixed;
+  T omega;
+  __device__ __forceinline__ T operator()(long long i) const {
+    return fixed[i] ? T(0) : mul_rn(mul_rn(omega, invd[i]), vld<COH>(b + i));
+  }
+};
+
 // Sum over the elements around node (i,j,k) of rows (loc*DIM + c) of the element matrix times
 // the element's DOF values.  FINE: element matrix x_e K0; otherwise the Galerkin element matrices
 // stored entry-major, Ae[(row * NE + col) * m + e], so that a warp reading one entry of 32
 // consecutive elements reads contiguous memory.
-template <int DIM, typename T, bool FINE, bool COH = false>
+template <int DIM, typename T, bool FINE, typename VIn>
 __device__ __forceinline__ void node_apply(const Dims& d, int i, int j, int k,
                                            const T* __restrict__ K0, const T* __restrict__ x,
-                                           const T* __restrict__ Ae, const T* __restrict__ v,
+                                           const T* __restrict__ Ae, const VIn& vin,
                                            T acc[DIM]) {
   constexpr int NN = Elem<DIM>::NN, NE = Elem<DIM>::NE;
   const int nnx = d.nx + 1, nny = d.ny + 1;
@@ -74,8 +94,8 @@ __device__ __forceinline__ void node_apply(const Dims& d, int i, int j, int k,
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const long long nid = ok[s] ? (ex + loc_ox(b)) + (long long)nnx * (ey + loc_oy(b)) : 0;
-        ve[s][2 * b] = vld<COH>(v + 2 * nid);
-        ve[s][2 * b + 1] = vld<COH>(v + 2 * nid + 1);
+        ve[s][2 * b] = vin(2 * nid);
+        ve[s][2 * b + 1] = vin(2 * nid + 1);
       }
     }
 #pragma unroll
@@ -104,7 +124,7 @@ __device__ __forceinline__ void node_apply(const Dims& d, int i, int j, int k,
       const long long nid = (ex + loc_ox(a)) + (long long)nnx * ((ey + loc_oy(a)) +
                                                                  (long long)nny * (ez + loc_oz(a)));
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) ve[a * DIM + c] = vld<COH>(v + DIM * nid + c);
+      for (int c = 0; c < DIM; ++c) ve[a * DIM + c] = vin(DIM * nid + c);
     }
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
@@ -127,10 +147,11 @@ __device__ __forceinline__ void node_apply(const Dims& d, int i, int j, int k,
 
 // mode 0: y = A v;  1: y = b - A v;  2: y = v + omega invd (b - A v);  3: y = omega invd b,
 // for the DIM entries of one node (v, b, y of the right-hand side at hand; w: arrow column).
-template <int DIM, typename T, int MODE, bool FINE, bool COH = false>
+// MODE 4: the sweep on VJac0 (the first two sweeps from zero).  vin supplies the swept vector.
+template <int DIM, typename T, int MODE, bool FINE, bool COH, typename VIn>
 __device__ __forceinline__ void apply_node(const Dims& d, long long node, const T* __restrict__ K0,
                                            const T* __restrict__ x, const T* __restrict__ Ae,
-                                           const T* v, const T* b, T* y,
+                                           const VIn& vin, const T* b, T* y,
                                            const T* __restrict__ invd, T omega,
                                            const uint8_t* __restrict__ fixed,
                                            const T* __restrict__ w) {
@@ -140,9 +161,9 @@ __device__ __forceinline__ void apply_node(const Dims& d, long long node, const 
   node_coords(node, nnx, nny, DIM, i, j, k);
   T acc[DIM];
   if (MODE != 3) {
-    node_apply<DIM, T, FINE, COH>(d, i, j, k, K0, x, Ae, v, acc);
+    node_apply<DIM, T, FINE>(d, i, j, k, K0, x, Ae, vin, acc);
     if (w) {
-      const T vl = v[n];
+      const T vl = vin(n);
 #pragma unroll
       for (int c = 0; c < DIM; ++c) acc[c] = fma(w[DIM * node + c], vl, acc[c]);
     }
@@ -157,8 +178,8 @@ __device__ __forceinline__ void apply_node(const Dims& d, long long node, const 
       out = acc[c];
     } else if (MODE == 1) {
       out = vld<COH>(b + id) - acc[c];
-    } else if (MODE == 2) {
-      out = vld<COH>(v + id) + omega * invd[id] * (vld<COH>(b + id) - acc[c]);
+    } else if (MODE == 2 || MODE == 4) {
+      out = vin(id) + omega * invd[id] * (vld<COH>(b + id) - acc[c]);
     } else {
       out = omega * invd[id] * vld<COH>(b + id);
     }
@@ -183,8 +204,15 @@ __global__ void __launch_bounds__(kThreads) k_apply(Dims d, const T* __restrict_
   const long long nodes = d.nodes();
   if (node >= nodes) return;
   const long long n = nodes * DIM;
-  apply_node<DIM, T, MODE, FINE>(d, node, K0, x, Ae, v + rhs * n, b + rhs * n, y + rhs * n, invd,
-                                 omega, fixed, w);
+  if constexpr (MODE == 4) {
+    const VJac0<false, T> vin{b + rhs * n, invd, fixed, omega};
+    apply_node<DIM, T, MODE, FINE, false>(d, node, K0, x, Ae, vin, b + rhs * n, y + rhs * n,
+                                          invd, omega, fixed, w);
+  } else {
+    const VLoad<false, T> vin{v + rhs * n};
+    apply_node<DIM, T, MODE, FINE, false>(d, node, K0, x, Ae, vin, b + rhs * n, y + rhs * n,
+                                          invd, omega, fixed, w);
+  }
 }
 
 // First coarse level of the 2D grid without stored element matrices: the Galerkin element matrix
@@ -260,12 +288,15 @@ void apply_dispatch(const Dims& d, const T* K0, const T* x, const T* Ae, const T
                     T* y, const T* invd, T omega, const uint8_t* fixed, int nrhs,
                     const CgScalars* sc, cudaStream_t st, const T* w) {
   dim3 grid(blocks_for(d.nodes()), nrhs);
-  if (x)
-    topo::launch(k_apply<DIM, T, MODE, true>, grid, kThreads, 0, st, d, K0, x, Ae, v, b, y, invd, omega,
-                                                           fixed, sc, w);
-  else
-    topo::launch(k_apply<DIM, T, MODE, false>, grid, kThreads, 0, st, d, K0, x, Ae, v, b, y, invd, omega,
-                                                            fixed, sc, w);
+  if constexpr (MODE <= 3) {
+    if (x) {
+      topo::launch(k_apply<DIM, T, MODE, true>, grid, kThreads, 0, st, d, K0, x, Ae, v, b, y, invd,
+                   omega, fixed, sc, w);
+      return;
+    }
+  }
+  topo::launch(k_apply<DIM, T, MODE, false>, grid, kThreads, 0, st, d, K0, x, Ae, v, b, y, invd,
+               omega, fixed, sc, w);
 }
 
 // Block sum of one double per thread (deterministic tree), result valid in thread 0.
@@ -311,7 +342,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_dot_fine(Dims d, const doubl
     const int j = (int)((node / nnx) % nny);
     const int k = (DIM == 3) ? (int)(node / ((long long)nnx * nny)) : 0;
     double acc[DIM];
-    node_apply<DIM, double, true>(d, i, j, k, K0, x, nullptr, v, acc);
+    node_apply<DIM, double, true>(d, i, j, k, K0, x, nullptr, VLoad<false, double>{v}, acc);
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
       const long long id = DIM * node + c;
@@ -492,27 +523,36 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_vcycle_tail(const __grid_co
     const T* b = A.b[k] + rhs * n;
     T* c = A.z[k] + rhs * n;
     T* o = A.t[k] + rhs * n;
-    if (A.nu1 >= 1) {
+    if (A.nu1 >= 2) {  // the first two sweeps in one phase
+      const VJac0<true, T> vj{b, A.invd[k], A.fixed[k], A.omega};
       for (long long nd = t0; nd < nodes; nd += ts)
-        apply_node<2, T, 3, false, true>(d, nd, nullptr, nullptr, A.Ae[k], c, b, c, A.invd[k],
+        apply_node<2, T, 4, false, true>(d, nd, nullptr, nullptr, A.Ae[k], vj, b, o, A.invd[k],
                                          A.omega, A.fixed[k], nullptr);
       cluster_barrier();
-      for (int it = 1; it < A.nu1; ++it) {
+      T* tmp = c;
+      c = o;
+      o = tmp;
+      for (int it = 2; it < A.nu1; ++it) {
         for (long long nd = t0; nd < nodes; nd += ts)
-          apply_node<2, T, 2, false, true>(d, nd, nullptr, nullptr, A.Ae[k], c, b, o, A.invd[k],
-                                           A.omega, A.fixed[k], nullptr);
+          apply_node<2, T, 2, false, true>(d, nd, nullptr, nullptr, A.Ae[k], VLoad<true, T>{c}, b,
+                                           o, A.invd[k], A.omega, A.fixed[k], nullptr);
         cluster_barrier();
-        T* tmp = c;
+        tmp = c;
         c = o;
         o = tmp;
       }
+    } else if (A.nu1 == 1) {
+      for (long long nd = t0; nd < nodes; nd += ts)
+        apply_node<2, T, 3, false, true>(d, nd, nullptr, nullptr, A.Ae[k], VLoad<true, T>{c}, b, c,
+                                         A.invd[k], A.omega, A.fixed[k], nullptr);
+      cluster_barrier();
     } else {
       for (long long q = t0; q < n; q += ts) c[q] = T(0);
       cluster_barrier();
     }
     for (long long nd = t0; nd < nodes; nd += ts)
-      apply_node<2, T, 1, false, true>(d, nd, nullptr, nullptr, A.Ae[k], c, b, o, A.invd[k],
-                                       A.omega, A.fixed[k], nullptr);
+      apply_node<2, T, 1, false, true>(d, nd, nullptr, nullptr, A.Ae[k], VLoad<true, T>{c}, b, o,
+                                       A.invd[k], A.omega, A.fixed[k], nullptr);
     cluster_barrier();
     const Dims dc = A.d[k + 1];
     T* bc = A.b[k + 1] + rhs * dc.dofs();
@@ -540,13 +580,15 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_vcycle_tail(const __grid_co
     T* c = res[k];
     T* zb = A.z[k] + rhs * n;
     T* o = (c == zb) ? A.t[k] + rhs * n : zb;
+    // (the prolongation stays a phase of its own: a sweep that formed P z_c on the fly would do
+    // so once per element entry it reads, and measured slower)
     for (long long nd = t0; nd < nodes; nd += ts)
       prolong_node<2, T, true>(d, dc, nd, res[k + 1], c, A.fixed[k]);
     cluster_barrier();
     for (int it = 0; it < A.nu2; ++it) {
       for (long long nd = t0; nd < nodes; nd += ts)
-        apply_node<2, T, 2, false, true>(d, nd, nullptr, nullptr, A.Ae[k], c, b, o, A.invd[k],
-                                         A.omega, A.fixed[k], nullptr);
+        apply_node<2, T, 2, false, true>(d, nd, nullptr, nullptr, A.Ae[k], VLoad<true, T>{c}, b, o,
+                                         A.invd[k], A.omega, A.fixed[k], nullptr);
       cluster_barrier();
       T* tmp = c;
       c = o;
@@ -678,23 +720,30 @@ template <typename T>
 cudaError_t launch_apply(const Dims& d, int mode, const T* K0, const T* x, const T* Ae, const T* v,
                          const T* b, T* y, const T* invd, T omega, const uint8_t* fixed, int nrhs,
                          const CgScalars* sc, cudaStream_t st, const T* w) {
-#define TOPO_APPLY_CASE(DIM)                                                                    \
-  switch (mode) {                                                                               \
-    case 0:                                                                                     \
-      apply_dispatch<DIM, T, 0>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st, w);    \
-      break;                                                                                    \
-    case 1:                                                                                     \
-      apply_dispatch<DIM, T, 1>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st, w);    \
-      break;                                                                                    \
-    case 2:                                                                                     \
-      apply_dispatch<DIM, T, 2>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st, w);    \
-      break;                                                                                    \
-    default:                                                                                    \
-      apply_dispatch<DIM, T, 3>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st, w);    \
+#define TOPO_APPLY_CASE(DIM)                                                                     \
+  switch (mode) {                                                                                \
+    case 0:                                                                                      \
+      apply_dispatch<DIM, T, 0>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st, w); \
+      break;                                                                                     \
+    case 1:                                                                                      \
+      apply_dispatch<DIM, T, 1>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st, w); \
+      break;                                                                                     \
+    case 2:                                                                                      \
+      apply_dispatch<DIM, T, 2>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st, w); \
+      break;                                                                                     \
+    default:                                                                                     \
+      apply_dispatch<DIM, T, 3>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st, w); \
   }
   if (d.dim == 2) {
-    TOPO_APPLY_CASE(2)
+    if (mode == 4 && !x && !w) {
+      apply_dispatch<2, T, 4>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st, w);
+    } else if (mode >= 4) {
+      return cudaErrorInvalidValue;  // the fused mode: 2D stored element matrices, no arrow
+    } else {
+      TOPO_APPLY_CASE(2)
+    }
   } else {
+    if (mode >= 4) return cudaErrorInvalidValue;
     TOPO_APPLY_CASE(3)
   }
 #undef TOPO_APPLY_CASE

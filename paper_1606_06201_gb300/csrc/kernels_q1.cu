@@ -364,8 +364,8 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_fused(int nx, int ny, int 
     V2 v = zero;
     if (MODE == 4) {
       const T dinv = dinv_of(xpair_prev + xpair_r);
-      v.x = omega * dinv * R.b.x;
-      v.y = omega * dinv * R.b.y;
+      v.x = mul_rn(mul_rn(omega, dinv), R.b.x);
+      v.y = mul_rn(mul_rn(omega, dinv), R.b.y);
       if (R.fx & 0xff) v.x = T(0);
       if (R.fx >> 8) v.y = T(0);
     } else {
@@ -683,6 +683,10 @@ __global__ void k_split_df(const double* __restrict__ x, float2* __restrict__ ou
 // forces are restricted back to the four coarse nodes (weights 1, 1/2, 1/4).  Same warp-sweep
 // data movement as k_q1_sweep on the coarse grid (nx, ny = coarse elements); xf holds the finest
 // densities (2nx x 2ny), invd the level's inverse diagonal (modes 2, 3).
+// MODE 4 and 5 fuse pairs of steps as k_q1_fused does on the finest level: 4 = the first two sweeps
+// from zero (z = omega invd b formed on the fly), 5 = the prolongation and correction t + P zc
+// (zc: the second coarse level's vector) formed on the fly, then one sweep; the same bits as the
+// separate steps.
 template <int MODE>
 __global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, int rows,
                                                               Q1K<float> k,
@@ -692,14 +696,19 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, int
                                                               float* __restrict__ y, float omega,
                                                               const float* __restrict__ invd,
                                                               const uint8_t* __restrict__ fixed,
-                                                              const CgScalars* sc) {
+                                                              const CgScalars* sc,
+                                                              const float* __restrict__ zc) {
+  constexpr bool FUSED = MODE == 4 || MODE == 5;
+  constexpr bool SWEEP = MODE == 2 || FUSED;  // output y = v + omega invd (b - A v)
   pdl_prologue();
   const int rhs = blockIdx.y;
   if (sc && sc[rhs].done) return;
   const long long n = 2LL * (nx + 1) * (ny + 1);
+  const long long ncn = (long long)(nx / 2 + 1) * (ny / 2 + 1);
   v += rhs * n;
   y += rhs * n;
   b += rhs * n;
+  if (MODE == 5) zc += rhs * 2 * ncn;
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * kQ1Warps + (threadIdx.x >> 5);
   const int ncolw = (nx + 1 + kQ1Cols - 1) / kQ1Cols;
@@ -713,46 +722,96 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, int
   const int j0 = ws * rows;
   const int j1 = min(j0 + rows, ny + 1);
   const int fnx = 2 * nx;
-  const float2* v2 = reinterpret_cast<const float2*>(v);
-  float2 pb = make_float2(0.f, 0.f);
-  if (MODE != 3 && col_ok && j0 >= 1) pb = v2[c + (long long)(nx + 1) * (j0 - 1)];
-  // Two element rows of lookahead (see k_q1_sweep): iteration e reads v of node row e + 1, the
-  // four child densities of coarse element row e, and b, invd and the mask of node row e.
   const long long rs = nx + 1;
+  const long long crs = nx / 2 + 1;
+  const float2* v2 = reinterpret_cast<const float2*>(v);
+  const float2* zc2 = reinterpret_cast<const float2*>(zc);
   const float2 z2 = make_float2(0.f, 0.f);
-  float2 pt_n = z2, pt_nn = z2, xb_n = z2, xb_nn = z2, xt_n = z2, xt_nn = z2;
-  float2 bb_n = z2, bb_nn = z2, di_n = z2, di_nn = z2;
-  uint16_t fx_n = 0, fx_nn = 0;
-  auto load_row = [&](int e, float2& pt, float2& xb, float2& xt, float2& bb, float2& di,
-                      uint16_t& fx) {
-    pt = z2;
-    xb = z2;
-    xt = z2;
-    if (MODE != 3 && col_ok && e + 1 <= ny) pt = v2[c + rs * (e + 1)];
-    if (MODE != 3 && el_col && e >= 0 && e < ny) {
-      xb = *reinterpret_cast<const float2*>(xf + 2 * c + (long long)fnx * (2 * e));
-      xt = *reinterpret_cast<const float2*>(xf + 2 * c + (long long)fnx * (2 * e + 1));
+  // the fused modes form the swept vector on every lane's node (node data of all rows)
+  const bool node_data = FUSED ? col_ok : out_lane;
+  // Two element rows of lookahead (see k_q1_sweep): iteration e reads v of node row e + 1 (the
+  // stored iterate; MODE 5: t and the four zc values around node row e + 1), the four child
+  // densities of coarse element row e, and b, invd and the mask of node row e.
+  struct Raw {
+    float2 pt, xb, xt, bb, di, z00, z10, z01, z11;
+    uint16_t fx;
+  };
+  auto load_row = [&](int e, Raw& R) {
+    R.pt = R.xb = R.xt = R.bb = R.di = z2;
+    R.fx = 0;
+    R.z00 = R.z10 = R.z01 = R.z11 = z2;
+    if (MODE != 3 && MODE != 4 && col_ok && e + 1 <= ny) R.pt = v2[c + rs * (e + 1)];
+    if (MODE == 5 && col_ok && e + 1 <= ny) {
+      const int r = e + 1, i0 = c >> 1, i1 = (c + 1) >> 1, q0 = r >> 1, q1 = (r + 1) >> 1;
+      R.z00 = zc2[i0 + crs * q0];
+      R.z10 = zc2[i1 + crs * q0];
+      R.z01 = zc2[i0 + crs * q1];
+      R.z11 = zc2[i1 + crs * q1];
     }
-    if (e >= j0 && out_lane) {
+    if (MODE != 3 && el_col && e >= 0 && e < ny) {
+      R.xb = *reinterpret_cast<const float2*>(xf + 2 * c + (long long)fnx * (2 * e));
+      R.xt = *reinterpret_cast<const float2*>(xf + 2 * c + (long long)fnx * (2 * e + 1));
+    }
+    if (e >= (FUSED ? 0 : j0) && e <= ny && node_data) {
       const long long node = c + rs * e;
-      fx = *reinterpret_cast<const uint16_t*>(fixed + 2 * node);
-      if (MODE != 0) bb = reinterpret_cast<const float2*>(b)[node];
-      if (MODE == 2 || MODE == 3) di = reinterpret_cast<const float2*>(invd)[node];
+      R.fx = *reinterpret_cast<const uint16_t*>(fixed + 2 * node);
+      if (MODE != 0) R.bb = reinterpret_cast<const float2*>(b)[node];
+      if (MODE != 0 && MODE != 1) R.di = reinterpret_cast<const float2*>(invd)[node];
     }
   };
-  load_row(j0 - 1, pt_n, xb_n, xt_n, bb_n, di_n, fx_n);
-  if (j0 < j1) load_row(j0, pt_nn, xb_nn, xt_nn, bb_nn, di_nn, fx_nn);
+  // the swept vector at node row r of this lane: MODE 4 from the row's own b, invd and mask (as
+  // MODE 3 writes it), MODE 5 from t (tv) and the zc values around the node (as k_prolong_add)
+  auto fused_input = [&](int r, float2 tv, const Raw& nodeR, const Raw& zR) {
+    float2 out = z2;
+    if (MODE == 4) {
+      out.x = mul_rn(mul_rn(omega, nodeR.di.x), nodeR.bb.x);
+      out.y = mul_rn(mul_rn(omega, nodeR.di.y), nodeR.bb.y);
+      if (nodeR.fx & 0xff) out.x = 0.f;
+      if (nodeR.fx >> 8) out.y = 0.f;
+    } else if (MODE == 5) {
+      const float wxh = (c & 1) ? 0.5f : 1.f;
+      const float wyh = (r & 1) ? 0.5f : 1.f;
+      const float w = wxh * wyh * 1.f;
+      float ax = 0.f, ay = 0.f;
+      ax = fmaf(w, zR.z00.x, ax);
+      ay = fmaf(w, zR.z00.y, ay);
+      if (c & 1) {
+        ax = fmaf(w, zR.z10.x, ax);
+        ay = fmaf(w, zR.z10.y, ay);
+      }
+      if (r & 1) {
+        ax = fmaf(w, zR.z01.x, ax);
+        ay = fmaf(w, zR.z01.y, ay);
+        if (c & 1) {
+          ax = fmaf(w, zR.z11.x, ax);
+          ay = fmaf(w, zR.z11.y, ay);
+        }
+      }
+      out = tv;
+      if (!(nodeR.fx & 0xff)) out.x = tv.x + ax;
+      if (!(nodeR.fx >> 8)) out.y = tv.y + ay;
+    }
+    return out;
+  };
+  Raw Rn{}, Rnn{};
+  load_row(j0 - 1, Rn);
+  if (j0 < j1) load_row(j0, Rnn);
+  float2 pb = z2;
+  if (MODE != 3 && MODE != 4 && col_ok && j0 >= 1) pb = v2[c + rs * (j0 - 1)];
+  if (FUSED && col_ok && j0 >= 1) {
+    Raw Rm{};
+    load_row(j0 - 2, Rm);  // MODE 5: zc around node row j0 - 1
+    pb = fused_input(j0 - 1, pb, Rn, Rm);
+  }
   float cu = 0.f, cv = 0.f;
   for (int ey = j0 - 1; ey < j1; ++ey) {
-    const float2 pt = pt_n, xb = xb_n, xt = xt_n, bb = bb_n, di = di_n;
-    const uint16_t fx = fx_n;
-    pt_n = pt_nn;
-    xb_n = xb_nn;
-    xt_n = xt_nn;
-    bb_n = bb_nn;
-    di_n = di_nn;
-    fx_n = fx_nn;
-    if (ey + 2 < j1) load_row(ey + 2, pt_nn, xb_nn, xt_nn, bb_nn, di_nn, fx_nn);
+    const Raw Cur = Rn;  // iteration ey: t of node row ey + 1, densities of row ey, node row ey
+    Rn = Rnn;            // iteration ey + 1: node row ey + 1
+    if (ey + 2 < j1) load_row(ey + 2, Rnn);
+    const float2 xb = Cur.xb, xt = Cur.xt, bb = Cur.bb, di = Cur.di;
+    const uint16_t fx = Cur.fx;
+    float2 pt = Cur.pt;
+    if (FUSED) pt = (col_ok && ey + 1 <= ny) ? fused_input(ey + 1, Cur.pt, Rn, Cur) : z2;
     const float pbr_u = shfl_dn(pb.x), pbr_v = shfl_dn(pb.y);
     const float ptr_u = shfl_dn(pt.x), ptr_v = shfl_dn(pt.y);
     float R[4][2] = {};  // coarse local nodes (0,0) (1,0) (1,1) (0,1), components u, v
@@ -805,7 +864,7 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, int
           out.x = bb.x - qu;
           out.y = bb.y - qv;
         } else {
-          if (MODE == 2) {
+          if (SWEEP) {
             out.x = fmaf(omega * di.x, bb.x - qu, pb.x);
             out.y = fmaf(omega * di.y, bb.y - qv, pb.y);
           } else {
@@ -887,21 +946,28 @@ template cudaError_t launch_q1_apply<float>(int, int, int, const Q1Coef&, const 
 cudaError_t launch_q1g_apply(int nx, int ny, int mode, const Q1Coef& coef, const float* xf,
                              const float* v, const float* b, float* y, float omega,
                              const float* invd, const uint8_t* fixed, int nrhs,
-                             const CgScalars* sc, cudaStream_t st) {
+                             const CgScalars* sc, cudaStream_t st, const float* zc) {
   dim3 grid(q1_blocks(nx, ny), nrhs);
   const Q1K<float> k = coef_cast<float>(coef);
+  const int rows = q1_rows(nx, ny);
   switch (mode) {
     case 0:
-      topo::launch(k_q1g_sweep<0>, grid, kQ1Warps * 32, 0, st, nx, ny, q1_rows(nx, ny), k, xf, v, b, y, omega, invd, fixed, sc);
+      topo::launch(k_q1g_sweep<0>, grid, kQ1Warps * 32, 0, st, nx, ny, rows, k, xf, v, b, y, omega, invd, fixed, sc, zc);
       break;
     case 1:
-      topo::launch(k_q1g_sweep<1>, grid, kQ1Warps * 32, 0, st, nx, ny, q1_rows(nx, ny), k, xf, v, b, y, omega, invd, fixed, sc);
+      topo::launch(k_q1g_sweep<1>, grid, kQ1Warps * 32, 0, st, nx, ny, rows, k, xf, v, b, y, omega, invd, fixed, sc, zc);
       break;
     case 2:
-      topo::launch(k_q1g_sweep<2>, grid, kQ1Warps * 32, 0, st, nx, ny, q1_rows(nx, ny), k, xf, v, b, y, omega, invd, fixed, sc);
+      topo::launch(k_q1g_sweep<2>, grid, kQ1Warps * 32, 0, st, nx, ny, rows, k, xf, v, b, y, omega, invd, fixed, sc, zc);
+      break;
+    case 4:
+      topo::launch(k_q1g_sweep<4>, grid, kQ1Warps * 32, 0, st, nx, ny, rows, k, xf, v, b, y, omega, invd, fixed, sc, zc);
+      break;
+    case 5:
+      topo::launch(k_q1g_sweep<5>, grid, kQ1Warps * 32, 0, st, nx, ny, rows, k, xf, v, b, y, omega, invd, fixed, sc, zc);
       break;
     default:
-      topo::launch(k_q1g_sweep<3>, grid, kQ1Warps * 32, 0, st, nx, ny, q1_rows(nx, ny), k, xf, v, b, y, omega, invd, fixed, sc);
+      topo::launch(k_q1g_sweep<3>, grid, kQ1Warps * 32, 0, st, nx, ny, rows, k, xf, v, b, y, omega, invd, fixed, sc, zc);
   }
   return cudaGetLastError();
 }

@@ -389,6 +389,11 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
   // finest 2D Q1 level: the first two sweeps, and the prolongation with the first post-sweep, as
   // single fused kernels (the same bits)
   const bool fine_fused = fine && s->fuse_on && s->q1_ok && !s->arrow;
+  // coarse 2D levels with stored element matrices: the first two sweeps as one kernel (mode 4).
+  // (Prolongation with the first post-sweep measured slower there: a node-parallel kernel forms
+  // P z_c once per element entry it reads, 32 times per node.)
+  const bool coarse_fused = !fine && s->fuse_on && s->dim == 2 && !s->arrow &&
+                            !(k == 1 && s->l1_free) && Prec<TV>::Ae(lv) != nullptr;
   bool sweep_timed = false;  // profiling: the first smoothing kernel of the finest level
   if (nu1 >= 2 && fine_fused) {
     TOPO_TRY(prof_mark(s, 1, 0));
@@ -396,6 +401,13 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
                                   oth, (TV)s->desc.omega, lv.fixed, nrhs, sc, s->st));
     TOPO_TRY(prof_mark(s, 1, 1));
     sweep_timed = true;
+    std::swap(cur, oth);
+    for (int it = 2; it < nu1; ++it) {
+      TOPO_TRY(apply_level<TV>(s, k, 2, cur, b, oth, sc));
+      std::swap(cur, oth);
+    }
+  } else if (nu1 >= 2 && coarse_fused) {
+    TOPO_TRY(apply_level<TV>(s, k, 4, cur, b, oth, sc));
     std::swap(cur, oth);
     for (int it = 2; it < nu1; ++it) {
       TOPO_TRY(apply_level<TV>(s, k, 2, cur, b, oth, sc));

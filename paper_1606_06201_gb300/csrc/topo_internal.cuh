@@ -151,6 +151,11 @@ __device__ __forceinline__ void node_coords(long long node, int nnx, int nny, in
   }
 }
 
+// Rounded products that the compiler may not contract into a later addition: the fused V-cycle
+// kernels form values that the unfused ones store to memory, and must round them the same way.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // z_row = sum_k Ainv[row][k] b[k] by one warp: lane-strided FP64 sums, then a butterfly
 // (COH: b read from L2, for data written earlier in the same launch by other blocks).
 template <bool COH, typename T>
@@ -213,8 +218,10 @@ inline unsigned blocks_for(long long n, int threads = kThreads) {
 void element_stiffness_host(int dim, double E, double nu, double* K0);
 
 // Operator application on one level.  mode: 0 y = A v; 1 y = b - A v; 2 y = v + omega invd (b - A v);
-// 3 y = omega invd b (first Jacobi sweep from zero, v unused).  x != nullptr: finest level with
-// element matrices x_e K0; otherwise Ae holds element matrices.  nrhs vectors of length n.
+// 3 y = omega invd b (first Jacobi sweep from zero, v unused); 2D stored element matrices only:
+// 4 = mode 2 on v = omega invd b (the first two sweeps from zero, v unused).
+// x != nullptr: finest level with element matrices x_e K0; otherwise Ae holds element matrices.
+// nrhs vectors of length n.
 // w != nullptr adds the arrow column: y_u += w v_lambda with v_lambda = v[n] (nrhs = 1).
 template <typename T>
 cudaError_t launch_apply(const Dims& d, int mode, const T* K0, const T* x, const T* Ae, const T* v,
@@ -300,10 +307,12 @@ cudaError_t launch_ae_sweep(int nx, int ny, int mode, const T* Ae, const T* v, c
                             const CgScalars* sc, cudaStream_t st);
 // First coarse level of the 2D Q1 hierarchy, matrix-free in FP32 (P^T K(x) P element by element);
 // nx, ny = coarse elements, xf = finest densities.
+// mode 4, 5: the fused pairs of steps of launch_q1_fused on this level (zc: the next coarser
+// level's vector for mode 5).
 cudaError_t launch_q1g_apply(int nx, int ny, int mode, const Q1Coef& coef, const float* xf,
                              const float* v, const float* b, float* y, float omega,
                              const float* invd, const uint8_t* fixed, int nrhs,
-                             const CgScalars* sc, cudaStream_t st);
+                             const CgScalars* sc, cudaStream_t st, const float* zc = nullptr);
 
 // Hierarchy construction (kernels_rap.cu).
 // g, Dinv != nullptr: add the rank-one terms (P_c^T g_c)(P_c^T g_c)^T Dinv_c of Z.
