@@ -795,7 +795,7 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, int
   };
   Raw Rn{}, Rnn{};
   load_row(j0 - 1, Rn);
-  if (j0 < j1) load_row(j0, Rnn);
+  if (j0 < j1 || FUSED) load_row(j0, Rnn);
   float2 pb = z2;
   if (MODE != 3 && MODE != 4 && col_ok && j0 >= 1) pb = v2[c + rs * (j0 - 1)];
   if (FUSED && col_ok && j0 >= 1) {
@@ -807,7 +807,9 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, int
   for (int ey = j0 - 1; ey < j1; ++ey) {
     const Raw Cur = Rn;  // iteration ey: t of node row ey + 1, densities of row ey, node row ey
     Rn = Rnn;            // iteration ey + 1: node row ey + 1
-    if (ey + 2 < j1) load_row(ey + 2, Rnn);
+    // the fused modes read the node data of row ey + 1 from the item of iteration ey + 1, so the
+    // item of iteration j1 (node row j1, the top of the strip) is loaded too
+    if (ey + 2 < j1 || (FUSED && ey + 2 == j1)) load_row(ey + 2, Rnn);
     const float2 xb = Cur.xb, xt = Cur.xt, bb = Cur.bb, di = Cur.di;
     const uint16_t fx = Cur.fx;
     float2 pt = Cur.pt;

@@ -246,7 +246,7 @@ topo_status prof_mark(topo_solver* s, int kind, int end) {
 // rank-one terms and lambda row) for IP systems, the generic element-matrix kernels elsewhere.
 template <typename TV>
 topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* b, TV* y,
-                        const CgScalars* sc) {
+                        const CgScalars* sc, const TV* zc = nullptr) {
   Level& lv = s->L[k];
   // adaptive damping: omega_k is folded into invd at build time (and read from the device for the
   // lambda entry), so the kernels take omega = 1
@@ -277,7 +277,7 @@ topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* 
     if (s->q1_ok)
       TOPO_CUDA(launch_q1g_apply(lv.d.nx, lv.d.ny, mode, s->q1, s->x32, (const float*)v,
                                  (const float*)b, (float*)y, (float)omega, s->L[1].invd32,
-                                 lv.fixed, s->nrhs, sc, s->st));
+                                 lv.fixed, s->nrhs, sc, s->st, (const float*)zc));
     else
       TOPO_CUDA(launch_apply_l1<float>(lv.d, mode, s->C32, s->x32, (const float*)v,
                                        (const float*)b, (float*)y, s->L[1].invd32, (float)omega,
@@ -389,6 +389,9 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
   // finest 2D Q1 level: the first two sweeps, and the prolongation with the first post-sweep, as
   // single fused kernels (the same bits)
   const bool fine_fused = fine && s->fuse_on && s->q1_ok && !s->arrow;
+  // the matrix-free first coarse level (2D mixed): both fusions in its warp sweep
+  const bool l1_fused = k == 1 && s->fuse_on && s->l1_free && s->q1_ok && !s->arrow &&
+                        std::is_same<TV, float>::value;
   // coarse 2D levels with stored element matrices: the first two sweeps as one kernel (mode 4).
   // (Prolongation with the first post-sweep measured slower there: a node-parallel kernel forms
   // P z_c once per element entry it reads, 32 times per node.)
@@ -406,7 +409,7 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
       TOPO_TRY(apply_level<TV>(s, k, 2, cur, b, oth, sc));
       std::swap(cur, oth);
     }
-  } else if (nu1 >= 2 && coarse_fused) {
+  } else if (nu1 >= 2 && (coarse_fused || l1_fused)) {
     TOPO_TRY(apply_level<TV>(s, k, 4, cur, b, oth, sc));
     std::swap(cur, oth);
     for (int it = 2; it < nu1; ++it) {
@@ -444,6 +447,10 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
     TOPO_CUDA(launch_q1_fused<TV>(lv.d.nx, lv.d.ny, 5, s->q1, Prec<TV>::x(s), cur, zc, b, oth,
                                   (TV)s->desc.omega, lv.fixed, nrhs, sc, s->st));
     TOPO_TRY(prof_mark(s, 4, 1));
+    std::swap(cur, oth);
+    it0 = 1;
+  } else if (l1_fused && nu2 >= 1) {
+    TOPO_TRY(apply_level<TV>(s, k, 5, cur, b, oth, sc, zc));
     std::swap(cur, oth);
     it0 = 1;
   } else {
