@@ -181,6 +181,21 @@ def element_energy(grid, K0, u):
     return np.einsum("ei,ij,ej->e", ue, K0, ue)
 
 
+def apply_K(grid, K0, x, u, chunk=1 << 20):
+    """K(x) u = sum_e x_e L_e^T K0 L_e u (Eq. (to)) without assembling K, for grids too large for
+    a sparse matrix: element gathers, the element product, and a weighted bincount as the scatter,
+    in chunks of elements."""
+    edofs = grid.element_dofs()
+    x = np.asarray(x, dtype=float)
+    u = np.asarray(u, dtype=float)
+    out = np.zeros(grid.n_dofs)
+    for e0 in range(0, edofs.shape[0], chunk):
+        ed = edofs[e0:e0 + chunk]
+        ve = (u[ed] @ K0.T) * x[e0:e0 + chunk, None]
+        out += np.bincount(ed.ravel(), weights=ve.ravel(), minlength=grid.n_dofs)
+    return out
+
+
 def scatter_add(grid, ve):
     """sum_e L_e^T ve[e]: element vectors (m, ne) to a full-length vector."""
     out = np.zeros(grid.n_dofs)

@@ -146,6 +146,19 @@ def test_assembly_matches_dense_loops(shape):
                                rtol=0, atol=1e-14)
 
 
+@pytest.mark.parametrize("shape", [(1, 1, 0), (3, 2, 0), (2, 2, 2), (5, 3, 2)])
+def test_matrix_free_apply_matches_dense_loops(shape):
+    """apply_K (chunked gathers and a weighted bincount) against the dense assembly by loops,
+    with chunks smaller than the element count so that the chunk seams are crossed."""
+    grid = fe.Grid(*shape)
+    K0 = fe.element_stiffness(grid.dim)
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0.1, 1.0, grid.n_elems)
+    u = rng.standard_normal(grid.n_dofs)
+    np.testing.assert_allclose(fe.apply_K(grid, K0, x, u, chunk=2), _dense_assembly(grid, K0, x) @ u,
+                               rtol=0, atol=1e-13 * np.abs(u).max())
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_patch_test_uniform_strain(dim):
     grid = fe.Grid(4, 3) if dim == 2 else fe.Grid(3, 3, 2)
