@@ -1,0 +1,357 @@
+// Finest-level operator of the 3D trilinear hex grid in the element's Walsh-Hadamard basis
+// (Eq. (to), Sec. 7): q = K(x) p with p^T q and alpha of Algorithm PCG.
+//
+// Element product.  For each displacement component the eight nodal values of an element are
+// mapped to the coefficients of the modes (1, xi, eta, zeta, xi eta, eta zeta, xi zeta,
+// xi eta zeta) by a three-stage Walsh-Hadamard butterfly (H, with H H^T = 8 I).  In that basis
+// the cube element's stiffness Khat = T^-T K0 T^-1 has 45 nonzeros in five kinds of blocks:
+//   normal strains (u_xi, v_eta, w_zeta): a on the diagonal, b off it;
+//   the three shear pairs (u_eta, v_xi), (u_zeta, w_xi), (v_zeta, w_eta): s in every entry;
+//   three bilinear pairs (u_xieta, w_etazeta), (u_xizeta, v_etazeta), (v_xieta, w_xizeta): p, q;
+//   the triple (u_etazeta, v_xizeta, w_xieta): d on the diagonal, e off it;
+//   the trilinear modes: h on the diagonal;
+// and zero rows for the constant modes (rigid translations).  So K0 v_e costs two butterflies of
+// 23 and 22 additions per component and about 43 scalings and additions: about 178 operations
+// instead of 576 multiply-adds.  The host rebuilds T^T Khat T from the eight numbers and checks it
+// against the quadrature K0 before enabling this path.
+//
+// Data movement.  One thread per element writes its 24 local forces to a buffer (entry-major, so
+// that a warp writes contiguous memory); one thread per node then sums the contributions of its
+// eight elements in a fixed order (deterministic, no atomics), masks fixed DOFs, and accumulates
+// p^T q with the last-block finalisation of the other CG kernels.
+#include <cmath>
+#include <vector>
+
+#include "topo_internal.cuh"
+
+namespace topo {
+
+namespace {
+
+__device__ __forceinline__ int hx_ox(int a) { return ((a & 3) == 1 || (a & 3) == 2) ? 1 : 0; }
+__device__ __forceinline__ int hx_oy(int a) { return ((a & 3) >= 2) ? 1 : 0; }
+__device__ __forceinline__ int hx_oz(int a) { return a >> 2; }
+
+// Mode coefficients of one component: n[k][j][i] nodal values -> t = (xi, eta, zeta, xieta,
+// etazeta, xizeta, xietazeta) (the constant mode is not needed).
+template <typename T>
+__device__ __forceinline__ void wht_fwd(const T n[2][2][2], T t[7]) {
+  T Sx[2][2], Dx[2][2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      Sx[k][j] = n[k][j][1] + n[k][j][0];
+      Dx[k][j] = n[k][j][1] - n[k][j][0];
+    }
+  T SS[2], SD[2], DS[2], DD[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    SS[k] = Sx[k][1] + Sx[k][0];
+    SD[k] = Sx[k][1] - Sx[k][0];
+    DS[k] = Dx[k][1] + Dx[k][0];
+    DD[k] = Dx[k][1] - Dx[k][0];
+  }
+  t[0] = DS[1] + DS[0];  // xi
+  t[1] = SD[1] + SD[0];  // eta
+  t[2] = SS[1] - SS[0];  // zeta
+  t[3] = DD[1] + DD[0];  // xi eta
+  t[4] = SD[1] - SD[0];  // eta zeta
+  t[5] = DS[1] - DS[0];  // xi zeta
+  t[6] = DD[1] - DD[0];  // xi eta zeta
+}
+
+// Nodal forces r[k][j][i] = sum_m H[m][node] g_m of one component (g of the constant mode = 0).
+template <typename T>
+__device__ __forceinline__ void wht_inv(const T g[7], T r[2][2][2]) {
+  // z stage: A[mx][my][k]
+  T A[2][2][2];
+  A[0][0][0] = -g[2];
+  A[0][0][1] = g[2];
+  A[0][1][0] = g[1] - g[4];
+  A[0][1][1] = g[1] + g[4];
+  A[1][0][0] = g[0] - g[5];
+  A[1][0][1] = g[0] + g[5];
+  A[1][1][0] = g[3] - g[6];
+  A[1][1][1] = g[3] + g[6];
+  // y stage: B[mx][j][k]
+  T B[2][2][2];
+#pragma unroll
+  for (int mx = 0; mx < 2; ++mx)
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      B[mx][0][k] = A[mx][0][k] - A[mx][1][k];
+      B[mx][1][k] = A[mx][0][k] + A[mx][1][k];
+    }
+  // x stage
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      r[k][j][0] = B[0][j][k] - B[1][j][k];
+      r[k][j][1] = B[0][j][k] + B[1][j][k];
+    }
+}
+
+template <typename T>
+struct HexK {
+  T a, b, s, p, q, d, e, h;
+};
+
+// Element forces of x_e K0 v_e: u, v, w mode coefficients in, forces out (in place).
+template <typename T>
+__device__ __forceinline__ void hex_khat(const HexK<T>& k, T xe, T tu[7], T tv[7], T tw[7]) {
+  const T a = xe * k.a, b = xe * k.b, s = xe * k.s, p = xe * k.p, q = xe * k.q, d = xe * k.d,
+          e = xe * k.e, h = xe * k.h;
+  // normal strains
+  const T S = tu[0] + tv[1] + tw[2];
+  const T bS = b * S, ab = a - b;
+  const T gux = fma(ab, tu[0], bS), gvy = fma(ab, tv[1], bS), gwz = fma(ab, tw[2], bS);
+  // shears
+  const T gxy = s * (tu[1] + tv[0]);
+  const T gxz = s * (tu[2] + tw[0]);
+  const T gyz = s * (tv[2] + tw[1]);
+  // bilinear pairs
+  const T guxy = fma(p, tu[3], q * tw[4]), gwyz = fma(q, tu[3], p * tw[4]);
+  const T guxz = fma(p, tu[5], q * tv[4]), gvyz = fma(q, tu[5], p * tv[4]);
+  const T gvxy = fma(p, tv[3], q * tw[5]), gwxz = fma(q, tv[3], p * tw[5]);
+  // the triple
+  const T Sd = tu[4] + tv[5] + tw[3];
+  const T eS = e * Sd, de = d - e;
+  const T guyz = fma(de, tu[4], eS), gvxz = fma(de, tv[5], eS), gwxy = fma(de, tw[3], eS);
+  // trilinear
+  const T guxyz = h * tu[6], gvxyz = h * tv[6], gwxyz = h * tw[6];
+  tu[0] = gux; tu[1] = gxy; tu[2] = gxz; tu[3] = guxy; tu[4] = guyz; tu[5] = guxz; tu[6] = guxyz;
+  tv[0] = gxy; tv[1] = gvy; tv[2] = gyz; tv[3] = gvxy; tv[4] = gvyz; tv[5] = gvxz; tv[6] = gvxyz;
+  tw[0] = gxz; tw[1] = gyz; tw[2] = gwz; tw[3] = gwxy; tw[4] = gwyz; tw[5] = gwxz; tw[6] = gwxyz;
+}
+
+// One thread per element: R[(a * 3 + c) * m + e] = (x_e K0 v_e)_{a,c}.
+__global__ void __launch_bounds__(kThreads) k_hex_elem(Dims d, HexK<double> k,
+                                                       const double* __restrict__ x,
+                                                       const double* __restrict__ v,
+                                                       double* __restrict__ R,
+                                                       const CgScalars* __restrict__ sc) {
+  pdl_prologue();
+  const int rhs = blockIdx.y;
+  if (sc && sc[rhs].done) return;
+  const long long m = d.elems();
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  const long long n = d.dofs();
+  v += rhs * n;
+  R += rhs * 24 * m;
+  int ex, ey, ez;
+  node_coords(e, d.nx, d.ny, 3, ex, ey, ez);
+  const int nnx = d.nx + 1, nny = d.ny + 1;
+  double nu[2][2][2], nv[2][2][2], nw[2][2][2];
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const long long nid = (ex + i) + (long long)nnx * ((ey + j) + (long long)nny * (ez + kk));
+        nu[kk][j][i] = __ldg(v + 3 * nid);
+        nv[kk][j][i] = __ldg(v + 3 * nid + 1);
+        nw[kk][j][i] = __ldg(v + 3 * nid + 2);
+      }
+  double tu[7], tv[7], tw[7];
+  wht_fwd(nu, tu);
+  wht_fwd(nv, tv);
+  wht_fwd(nw, tw);
+  hex_khat(k, __ldg(x + e), tu, tv, tw);
+  wht_inv(tu, nu);
+  wht_inv(tv, nv);
+  wht_inv(tw, nw);
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int i = hx_ox(a), j = hx_oy(a), kk = hx_oz(a);
+    R[(long long)(a * 3 + 0) * m + e] = nu[kk][j][i];
+    R[(long long)(a * 3 + 1) * m + e] = nv[kk][j][i];
+    R[(long long)(a * 3 + 2) * m + e] = nw[kk][j][i];
+  }
+}
+
+// Block sum of one double per thread (deterministic tree), result valid in thread 0.
+__device__ __forceinline__ double block_sum_hex(double v) {
+  __shared__ double warp_sums[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) warp_sums[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (wid == 0) {
+    s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  return s;
+}
+
+// One thread per node: q = sum of the node's element forces (elements in the fixed order of
+// node_apply), masked; p^T q and alpha = r^T y / p^T q by the last block.
+__global__ void __launch_bounds__(kThreads) k_hex_gather_dot(Dims d, const double* __restrict__ R,
+                                                             const double* __restrict__ p,
+                                                             double* __restrict__ q,
+                                                             const uint8_t* __restrict__ fixed,
+                                                             double* partials, unsigned* counters,
+                                                             CgScalars* sc) {
+  pdl_prologue();
+  const int rhs = blockIdx.y;
+  if (sc[rhs].done) return;
+  const long long m = d.elems();
+  const long long nodes = d.nodes();
+  const long long n = nodes * 3;
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  p += rhs * n;
+  q += rhs * n;
+  R += rhs * 24 * m;
+  double part = 0.0;
+  if (node < nodes) {
+    int i, j, kk;
+    node_coords(node, d.nx + 1, d.ny + 1, 3, i, j, kk);
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int s = 0; s < 8; ++s) {
+      const int dx = s & 1, dy = (s >> 1) & 1, dz = s >> 2;
+      const int ex = i - 1 + dx, ey = j - 1 + dy, ez = kk - 1 + dz;
+      if (ex < 0 || ex >= d.nx || ey < 0 || ey >= d.ny || ez < 0 || ez >= d.nz) continue;
+      const int lx = 1 - dx, ly = 1 - dy, lz = 1 - dz;
+      const int loc = (ly ? (lx ? 2 : 3) : (lx ? 1 : 0)) + 4 * lz;
+      const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[c] += __ldg(R + (long long)(loc * 3 + c) * m + e);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long id = 3 * node + c;
+      const double out = fixed[id] ? 0.0 : acc[c];
+      q[id] = out;
+      part = fma(p[id], out, part);
+    }
+  }
+  const double bs = block_sum_hex(part);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[(long long)rhs * gridDim.x + blockIdx.x] = bs;
+    __threadfence();
+    last = (atomicAdd(&counters[rhs], 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  double s = 0.0;
+  for (unsigned t = threadIdx.x; t < gridDim.x; t += blockDim.x)
+    s += __ldcg(partials + (long long)rhs * gridDim.x + t);
+  s = block_sum_hex(s);
+  if (threadIdx.x == 0) {
+    CgScalars& S = sc[rhs];
+    S.pq = s;
+    const double alpha = S.ry / s;
+    if (!(s > 0.0) || !isfinite(alpha)) {
+      S.status = TOPO_E_BREAKDOWN;
+      S.done = 1;
+      S.alpha = 0.0;
+    } else {
+      S.alpha = alpha;
+    }
+    counters[rhs] = 0;
+  }
+}
+
+}  // namespace
+
+bool hex_coefficients(const double* K0, HexCoef& c) {
+  // T: row (comp * 8 + mode), column (node * 3 + comp); modes 1, xi, eta, zeta, xieta, etazeta,
+  // xizeta, xietazeta
+  const int ox[8] = {0, 1, 1, 0, 0, 1, 1, 0}, oy[8] = {0, 0, 1, 1, 0, 0, 1, 1},
+            oz[8] = {0, 0, 0, 0, 1, 1, 1, 1};
+  double H[8][8];
+  for (int a = 0; a < 8; ++a) {
+    const double xi = 2 * ox[a] - 1, eta = 2 * oy[a] - 1, zeta = 2 * oz[a] - 1;
+    const double md[8] = {1, xi, eta, zeta, xi * eta, eta * zeta, xi * zeta, xi * eta * zeta};
+    for (int mm = 0; mm < 8; ++mm) H[mm][a] = md[mm];
+  }
+  std::vector<double> T(24 * 24, 0.0);
+  for (int cc = 0; cc < 3; ++cc)
+    for (int mm = 0; mm < 8; ++mm)
+      for (int a = 0; a < 8; ++a) T[(cc * 8 + mm) * 24 + a * 3 + cc] = H[mm][a];
+  // Khat = T K0 T^T / 64 (T^-1 = T^T / 8)
+  std::vector<double> TK(24 * 24, 0.0), Kh(24 * 24, 0.0);
+  for (int i = 0; i < 24; ++i)
+    for (int j = 0; j < 24; ++j) {
+      double acc = 0.0;
+      for (int l = 0; l < 24; ++l) acc += T[i * 24 + l] * K0[l * 24 + j];
+      TK[i * 24 + j] = acc;
+    }
+  for (int i = 0; i < 24; ++i)
+    for (int j = 0; j < 24; ++j) {
+      double acc = 0.0;
+      for (int l = 0; l < 24; ++l) acc += TK[i * 24 + l] * T[j * 24 + l];
+      Kh[i * 24 + j] = acc / 64.0;
+    }
+  auto at = [&](int c1, int m1, int c2, int m2) { return Kh[(c1 * 8 + m1) * 24 + c2 * 8 + m2]; };
+  c.a = at(0, 1, 0, 1);
+  c.b = at(0, 1, 1, 2);
+  c.s = at(0, 2, 0, 2);
+  c.p = at(0, 4, 0, 4);
+  c.q = at(0, 4, 2, 5);
+  c.d = at(0, 5, 0, 5);
+  c.e = at(0, 5, 1, 6);
+  c.h = at(0, 7, 0, 7);
+  // the structured Khat from the eight numbers, then T^T Khat T against K0
+  std::vector<double> Ks(24 * 24, 0.0);
+  auto set = [&](int c1, int m1, int c2, int m2, double val) {
+    Ks[(c1 * 8 + m1) * 24 + c2 * 8 + m2] = val;
+    Ks[(c2 * 8 + m2) * 24 + c1 * 8 + m1] = val;
+  };
+  for (int cc = 0; cc < 3; ++cc) set(cc, 1 + cc, cc, 1 + cc, c.a);
+  set(0, 1, 1, 2, c.b);
+  set(0, 1, 2, 3, c.b);
+  set(1, 2, 2, 3, c.b);
+  const int sh[3][4] = {{0, 2, 1, 1}, {0, 3, 2, 1}, {1, 3, 2, 2}};  // (u,eta)(v,xi) etc.
+  for (auto& z : sh) {
+    set(z[0], z[1], z[0], z[1], c.s);
+    set(z[2], z[3], z[2], z[3], c.s);
+    set(z[0], z[1], z[2], z[3], c.s);
+  }
+  const int pr[3][4] = {{0, 4, 2, 5}, {0, 6, 1, 5}, {1, 4, 2, 6}};  // bilinear pairs
+  for (auto& z : pr) {
+    set(z[0], z[1], z[0], z[1], c.p);
+    set(z[2], z[3], z[2], z[3], c.p);
+    set(z[0], z[1], z[2], z[3], c.q);
+  }
+  const int tr[3][2] = {{0, 5}, {1, 6}, {2, 4}};  // (u,etazeta) (v,xizeta) (w,xieta)
+  for (int i = 0; i < 3; ++i) {
+    set(tr[i][0], tr[i][1], tr[i][0], tr[i][1], c.d);
+    for (int j = i + 1; j < 3; ++j) set(tr[i][0], tr[i][1], tr[j][0], tr[j][1], c.e);
+  }
+  for (int cc = 0; cc < 3; ++cc) set(cc, 7, cc, 7, c.h);
+  double err = 0.0, scale = 0.0;
+  for (int i = 0; i < 24; ++i)
+    for (int j = 0; j < 24; ++j) {
+      double acc = 0.0;
+      for (int l = 0; l < 24; ++l)
+        for (int r = 0; r < 24; ++r) acc += T[l * 24 + i] * Ks[l * 24 + r] * T[r * 24 + j];
+      err = std::max(err, std::fabs(acc - K0[i * 24 + j]));
+      scale = std::max(scale, std::fabs(K0[i * 24 + j]));
+    }
+  return err <= 1e-13 * scale;
+}
+
+cudaError_t launch_hex_apply_dot(const Dims& d, const HexCoef& c, const double* x, const double* v,
+                                 double* y, const uint8_t* fixed, int nrhs, double* R,
+                                 double* partials, unsigned* counters, CgScalars* sc,
+                                 cudaStream_t st) {
+  const HexK<double> k{c.a, c.b, c.s, c.p, c.q, c.d, c.e, c.h};
+  topo::launch(k_hex_elem, dim3(blocks_for(d.elems()), nrhs), kThreads, 0, st, d, k, x, v, R,
+               (const CgScalars*)sc);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  topo::launch(k_hex_gather_dot, dim3(blocks_for(d.nodes()), nrhs), kThreads, 0, st, d,
+               (const double*)R, v, y, fixed, partials, counters, sc);
+  return cudaGetLastError();
+}
+
+}  // namespace topo

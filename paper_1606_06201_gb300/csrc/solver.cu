@@ -502,6 +502,9 @@ topo_status cg_iteration(topo_solver* s, int slot, double tol, int max_iter) {
   } else if (s->q1_ok) {
     TOPO_CUDA(launch_q1_apply_dot(l0.d.nx, l0.d.ny, s->q1, s->x, s->p, s->q, l0.fixed, s->nrhs,
                                   s->partials, s->counters, s->sc, s->st));
+  } else if (s->hex_ok) {
+    TOPO_CUDA(launch_hex_apply_dot(l0.d, s->hex, s->x, s->p, s->q, l0.fixed, s->nrhs, s->hexR,
+                                   s->partials, s->counters, s->sc, s->st));
   } else {
     TOPO_CUDA(launch_apply_dot_fine(l0.d, s->K0, s->x, s->p, s->q, l0.fixed, s->nrhs, s->partials,
                                     s->counters, s->sc, s->st));
@@ -916,6 +919,7 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   std::vector<double> C2;
   if (!arrow && s->nlev >= 3) grandchild_matrices(s->dim, K0.data(), C2);
   s->q1_ok = (s->dim == 2) && q1_coefficients(d->E, d->nu, K0.data(), s->q1) && !d->generic_kernels;
+  s->hex_ok = (s->dim == 3) && !arrow && !d->generic_kernels && hex_coefficients(K0.data(), s->hex);
   s->l1_free = (s->dim == 2) && !arrow && s->prec == TOPO_MIXED && s->nlev >= 3 &&
                !d->generic_kernels;
   // The V-cycle of a mixed solver reads FP32 coarse matrices only, so they are computed in FP32
@@ -1008,6 +1012,7 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   const long long m = s->L[0].m;
   const long long n = s->L[0].n + (arrow ? 2 : 0);
   TOPO_TRY(s->alloc(&s->x, m));
+  if (s->hex_ok) TOPO_TRY(s->alloc(&s->hexR, (size_t)m * 24 * nrhs));
   if (s->q1_ok && !arrow) {  // pair-arithmetic outer operator: default for mixed solvers
     TOPO_TRY(s->alloc(&s->xdf, m));
     s->outer_df = s->prec == TOPO_MIXED ? 1 : 0;

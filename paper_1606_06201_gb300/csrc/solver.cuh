@@ -66,6 +66,9 @@ struct topo_solver {
   double loop_tol = -1.0;
   int graph_mode = 0;                     // 0 replayed blocks of iterations, 1 while-node loop
   float2* xdf = nullptr;                  // densities as float pairs (pair-arithmetic operator)
+  bool hex_ok = false;                    // 3D outer operator in the Walsh-Hadamard basis
+  HexCoef hex{};
+  double* hexR = nullptr;                 // its element forces (24 x elems x nrhs)
   int outer_df = 0;                       // outer operator in float-pair arithmetic (1) or FP64
   bool tail_ok = false;                   // the fused deep-level kernel can run on this device
   bool fuse_on = true;                    // fused V-cycle kernels in use (topo_set_vcycle_fusion)

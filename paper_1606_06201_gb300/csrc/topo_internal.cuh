@@ -92,6 +92,12 @@ struct Q1Coef {
   double c11, c12, c22, c33, cH, cHp, kd;
 };
 
+// Coefficients of the 3D hex K0 in the element's Walsh-Hadamard basis (kernels_hex.cu): normal
+// block a (diagonal) and b, shear s, bilinear pairs p and q, the triple d and e, trilinear h.
+struct HexCoef {
+  double a, b, s, p, q, d, e, h;
+};
+
 // Host-side error reporting.
 void set_error(const std::string& msg);
 topo_status cuda_status(cudaError_t e, const char* what);
@@ -272,6 +278,14 @@ cudaError_t launch_q1_apply_dot(int nx, int ny, const Q1Coef& coef, const double
                                 double* partials, unsigned* counters, CgScalars* sc,
                                 cudaStream_t st);
 long long q1_partial_blocks(int nx, int ny);
+// 3D finest-level outer operator in the Walsh-Hadamard basis (kernels_hex.cu): element forces into
+// R (24 x elems per right-hand side), then a node gather with p^T q and alpha.  hex_coefficients
+// returns false when T^T Khat T does not reproduce K0 (the generic kernel is then used).
+bool hex_coefficients(const double* K0, HexCoef& c);
+cudaError_t launch_hex_apply_dot(const Dims& d, const HexCoef& c, const double* x, const double* v,
+                                 double* y, const uint8_t* fixed, int nrhs, double* R,
+                                 double* partials, unsigned* counters, CgScalars* sc,
+                                 cudaStream_t st);
 // Fused pairs of finest-level V-cycle steps (same bits as the separate steps): mode 4 = the first
 // two Jacobi sweeps from zero (b -> y); mode 5 = prolongation and correction t + P zc followed by
 // one Jacobi sweep (t, zc -> y).  zc: the first coarse level's vector.
