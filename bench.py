@@ -189,7 +189,7 @@ def main():
     ap.add_argument("--no-ip", action="store_true", help="skip the 512x256 IP/OC wall-time runs")
     ap.add_argument("--outer-fp64", action="store_true",
                     help="mixed solver with the FP64 outer operator instead of float pairs")
-    ap.add_argument("--only", choices=["mixed", "fp64"], default=None,
+    ap.add_argument("--only", choices=["mixed", "fp64", "batched3d"], default=None,
                     help="run one solver configuration only (for profiler launch lists); no JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -269,6 +269,43 @@ def main():
         s.close()
         return dict(ms=ms, iters=iters, res=res, launches=launches, prof=prof, kinds=kinds)
 
+    def batched_3d_run(steps=3, warmup=3):
+        """128x64x64 hex grid (1.6M DOFs, 5 levels), 8 unit point loads on the x = max face as one
+        batched mixed solve per step (hierarchy build + PCG to 1e-8 for all 8); DOF*iterations
+        summed over the load cases."""
+        c4 = W.random_field_3d(128, 64, 64, n_rhs=8)
+        nfree4 = int(np.count_nonzero(c4["fixed"] == 0))
+        x4 = torch.as_tensor(c4["x"], device=dev)
+        f4 = torch.as_tensor(c4["f"], device=dev)
+        s4 = topo.Solver(128, 64, 64, fixed=c4["fixed"], levels=5, precision=topo.MIXED, nrhs=8)
+        u4 = torch.zeros_like(f4)
+        for _ in range(warmup):
+            s4.set_density(x4)
+            s4.solve(f4, u4, tol=TOL)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        iters = 0
+        e0.record()
+        for _ in range(steps):
+            s4.set_density(x4)
+            _, info4 = s4.solve(f4, u4, tol=TOL)
+            iters += info4.iterations
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        s4.close()
+        return {"workload": "3d_hex_128x64x64_5lev_8_point_loads_batched", "free_dofs": nfree4,
+                "nrhs": 8, "steps": steps, "ms_per_step": ms / steps,
+                "iterations_per_solve": iters / steps,
+                "value": 8 * nfree4 * iters / (ms * 1e-3), "unit": UNIT,
+                "smoother": "damped Jacobi omega=0.5 nu1=nu2=2",
+                "precision": "FP32 V-cycle, FP64 CG and outer operator"}
+
+    if args.only == "batched3d":
+        r = batched_3d_run(args.steps, args.warmup)
+        print("only=batched3d ms_per_step=%.3f iterations=%.1f" % (r["ms_per_step"],
+                                                                  r["iterations_per_solve"]))
+        return 0
     if args.only:
         r = run(topo.MIXED if args.only == "mixed" else topo.FP64, args.steps, args.warmup)
         print("only=%s ms_per_step=%.3f iterations=%d launches=%d" % (
@@ -310,38 +347,6 @@ def main():
                                   "compliance": oinfo.compliance}
             oc.close()
         return out
-
-    def batched_3d_run(steps=3, warmup=3):
-        """128x64x64 hex grid (1.6M DOFs, 5 levels), 8 unit point loads on the x = max face as one
-        batched mixed solve per step (hierarchy build + PCG to 1e-8 for all 8); DOF*iterations
-        summed over the load cases."""
-        c4 = W.random_field_3d(128, 64, 64, n_rhs=8)
-        nfree4 = int(np.count_nonzero(c4["fixed"] == 0))
-        x4 = torch.as_tensor(c4["x"], device=dev)
-        f4 = torch.as_tensor(c4["f"], device=dev)
-        s4 = topo.Solver(128, 64, 64, fixed=c4["fixed"], levels=5, precision=topo.MIXED, nrhs=8)
-        u4 = torch.zeros_like(f4)
-        for _ in range(warmup):
-            s4.set_density(x4)
-            s4.solve(f4, u4, tol=TOL)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        iters = 0
-        e0.record()
-        for _ in range(steps):
-            s4.set_density(x4)
-            _, info4 = s4.solve(f4, u4, tol=TOL)
-            iters += info4.iterations
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        s4.close()
-        return {"workload": "3d_hex_128x64x64_5lev_8_point_loads_batched", "free_dofs": nfree4,
-                "nrhs": 8, "steps": steps, "ms_per_step": ms / steps,
-                "iterations_per_solve": iters / steps,
-                "value": 8 * nfree4 * iters / (ms * 1e-3), "unit": UNIT,
-                "smoother": "damped Jacobi omega=0.5 nu1=nu2=2",
-                "precision": "FP32 V-cycle, FP64 CG and outer operator"}
 
     def gather_max(v):
         if ws == 1:

@@ -450,6 +450,187 @@ __global__ void __launch_bounds__(kGjMaxN) k_ns_gemm(int n, const double* __rest
   if (check && !(fabs(c - (i == j ? 1.0 : 0.0)) <= kNsTol)) atomicOr(bad, 1);
 }
 
+// Larger coarsest matrices (n > kGjMaxN: 3D grids, the IP systems' 2D coarsest levels) are
+// inverted by block Gauss-Jordan in FP64 on tiles of kBg x kBg over many blocks: an n-step
+// factorisation on one SM runs at the FP64 rate of that SM alone (21 ms for n = 675).  The matrix
+// is padded with the identity to a multiple of kBg.  Block step K, with P = W_KK^{-1} formed by
+// scalar Gauss-Jordan (the pivots are the same Schur-complement diagonals as in the scalar
+// elimination, so the same floor and failure test apply):
+//   Z_J = P W_KJ (J != K);  W_IJ -= W_IK Z_J (I, J != K);  W_IK <- -W_IK P, W_KJ <- Z_J, W_KK <- P.
+// After the last step W holds the inverse.
+constexpr int kBg = 32;
+
+// W (npad x npad) = [A 0; 0 I], a0 = diagonal of A (1 on the padding).
+__global__ void k_bgj_setup(int n, int npad, const double* __restrict__ A, double* __restrict__ W,
+                            double* __restrict__ a0, int* info) {
+  pdl_prologue();
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) *info = 0;
+  if (t >= (long long)npad * npad) return;
+  const int i = (int)(t / npad), j = (int)(t % npad);
+  const double v = (i < n && j < n) ? A[(long long)i * n + j] : (i == j ? 1.0 : 0.0);
+  W[t] = v;
+  if (i == j) a0[i] = v;
+}
+
+// P = W_KK^{-1} by scalar Gauss-Jordan in shared memory (one block of kBg * 8 threads, each
+// thread 4 entries of the tile); pivot floor and failure test as in the Cholesky kernels.
+__global__ void __launch_bounds__(kBg * 8) k_bgj_pivot(int npad, int K, const double* __restrict__ W,
+                                                       const double* __restrict__ a0,
+                                                       double* __restrict__ P, int* info) {
+  pdl_prologue();
+  __shared__ double S[kBg][kBg + 1];
+  __shared__ double piv;
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  const long long base = (long long)K * kBg;
+  for (int t = tid; t < kBg * kBg; t += blockDim.x)
+    S[t / kBg][t % kBg] = W[(base + t / kBg) * npad + base + t % kBg];
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < kBg; ++k) {
+    if (tid == 0) {
+      const double akk = S[k][k];
+      const double d0 = a0[base + k];
+      if (!(d0 > 0.0) || !isfinite(akk)) bad = 1;
+      piv = fmax(akk, kPivotFloor * d0);
+    }
+    __syncthreads();
+    if (bad) break;
+    const double rp = 1.0 / piv;
+    double nv[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int t = tid + r * blockDim.x;
+      const int i = t / kBg, j = t % kBg;
+      const double aij = S[i][j];
+      if (i == k) nv[r] = (j == k) ? rp : aij * rp;
+      else if (j == k) nv[r] = -aij * rp;
+      else nv[r] = fma(-S[i][k] * rp, S[k][j], aij);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int t = tid + r * blockDim.x;
+      S[t / kBg][t % kBg] = nv[r];
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (tid == 0 && *info == 0) {
+      int k = 0;  // first failing pivot of this block, for the report
+      while (k < kBg && a0[base + k] > 0.0) ++k;
+      *info = (int)(base + (k < kBg ? k : 0)) + 1;
+    }
+    return;
+  }
+  for (int t = tid; t < kBg * kBg; t += blockDim.x) P[t] = S[t / kBg][t % kBg];
+}
+
+// C = X Y for kBg x kBg tiles in shared memory; each of the kBg * 8 threads forms 4 outputs.
+__device__ __forceinline__ void tile_mm(const double (*X)[kBg + 1], const double (*Y)[kBg + 1],
+                                        double out[4]) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int t = tid + r * blockDim.x;
+    const int i = t / kBg, j = t % kBg;
+    double acc = 0.0;
+#pragma unroll 8
+    for (int l = 0; l < kBg; ++l) acc = fma(X[i][l], Y[l][j], acc);
+    out[r] = acc;
+  }
+}
+
+// Z_J = P W_KJ for every tile column J != K (block J).
+__global__ void __launch_bounds__(kBg * 8) k_bgj_zrow(int npad, int K, const double* __restrict__ W,
+                                                      const double* __restrict__ P,
+                                                      double* __restrict__ Z, const int* info) {
+  pdl_prologue();
+  if (*info) return;
+  const int J = blockIdx.x;
+  if (J == K) return;
+  __shared__ double Ps[kBg][kBg + 1], Bs[kBg][kBg + 1];
+  const long long rb = (long long)K * kBg, cb = (long long)J * kBg;
+  for (int t = threadIdx.x; t < kBg * kBg; t += blockDim.x) {
+    Ps[t / kBg][t % kBg] = P[t];
+    Bs[t / kBg][t % kBg] = W[(rb + t / kBg) * npad + cb + t % kBg];
+  }
+  __syncthreads();
+  double out[4];
+  tile_mm(Ps, Bs, out);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int t = threadIdx.x + r * blockDim.x;
+    Z[(long long)(t / kBg) * npad + cb + t % kBg] = out[r];
+  }
+}
+
+// W_IJ -= W_IK Z_J for I, J != K (block (J, I)).
+__global__ void __launch_bounds__(kBg * 8) k_bgj_update(int npad, int K, double* __restrict__ W,
+                                                        const double* __restrict__ Z,
+                                                        const int* info) {
+  pdl_prologue();
+  if (*info) return;
+  const int J = blockIdx.x, I = blockIdx.y;
+  if (I == K || J == K) return;
+  __shared__ double As[kBg][kBg + 1], Zs[kBg][kBg + 1];
+  const long long ib = (long long)I * kBg, jb = (long long)J * kBg, kb = (long long)K * kBg;
+  for (int t = threadIdx.x; t < kBg * kBg; t += blockDim.x) {
+    As[t / kBg][t % kBg] = W[(ib + t / kBg) * npad + kb + t % kBg];
+    Zs[t / kBg][t % kBg] = Z[(long long)(t / kBg) * npad + jb + t % kBg];
+  }
+  __syncthreads();
+  double out[4];
+  tile_mm(As, Zs, out);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int t = threadIdx.x + r * blockDim.x;
+    double* w = W + (ib + t / kBg) * npad + jb + t % kBg;
+    *w = *w - out[r];
+  }
+}
+
+// W_IK <- -W_IK P, W_KI <- Z_I (block I != K); W_KK <- P (block K).
+__global__ void __launch_bounds__(kBg * 8) k_bgj_final(int npad, int K, double* __restrict__ W,
+                                                       const double* __restrict__ P,
+                                                       const double* __restrict__ Z,
+                                                       const int* info) {
+  pdl_prologue();
+  if (*info) return;
+  const int I = blockIdx.x;
+  const long long ib = (long long)I * kBg, kb = (long long)K * kBg;
+  if (I == K) {
+    for (int t = threadIdx.x; t < kBg * kBg; t += blockDim.x)
+      W[(kb + t / kBg) * npad + kb + t % kBg] = P[t];
+    return;
+  }
+  __shared__ double As[kBg][kBg + 1], Ps[kBg][kBg + 1];
+  for (int t = threadIdx.x; t < kBg * kBg; t += blockDim.x) {
+    As[t / kBg][t % kBg] = W[(ib + t / kBg) * npad + kb + t % kBg];
+    Ps[t / kBg][t % kBg] = P[t];
+  }
+  __syncthreads();
+  double out[4];
+  tile_mm(As, Ps, out);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int t = threadIdx.x + r * blockDim.x;
+    W[(ib + t / kBg) * npad + kb + t % kBg] = -out[r];
+    W[(kb + t / kBg) * npad + ib + t % kBg] = Z[(long long)(t / kBg) * npad + ib + t % kBg];
+  }
+}
+
+// Ainv (n x n) = the leading block of W.
+__global__ void k_bgj_copy(int n, int npad, const double* __restrict__ W, double* __restrict__ Ainv,
+                           const int* info) {
+  pdl_prologue();
+  if (*info) return;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  Ainv[t] = W[(t / n) * npad + t % n];
+}
+
 // z = A^{-1} b: one warp per row, FP64 accumulation whatever the vector type.
 template <typename T>
 __global__ void k_dense_solve(int n, const double* __restrict__ Ainv, const T* __restrict__ b,
@@ -556,10 +737,40 @@ cudaError_t prepare_coarse_kernels(int n) {
                               200 * 1024);
 }
 
-size_t coarse_scratch_doubles(int n) { return n <= kGjMaxN ? 2 * (size_t)n * n : 0; }
+// Newton-Schulz products (n <= kGjMaxN) or the block Gauss-Jordan workspace: W, the original
+// diagonal, the row of Z tiles and P.
+size_t coarse_scratch_doubles(int n) {
+  if (n <= kGjMaxN) return 2 * (size_t)n * n;
+  const size_t npad = ((size_t)n + kBg - 1) / kBg * kBg;
+  return npad * npad + npad + (size_t)kBg * npad + (size_t)kBg * kBg;
+}
 
 cudaError_t launch_cholesky_inverse(int n, double* A, double* Ainv, int* info, cudaStream_t st,
                                     double* scratch, int* ns_bad, bool allow_ns) {
+  if (n > kGjMaxN && scratch) {  // block Gauss-Jordan over many blocks
+    const int npad = (n + kBg - 1) / kBg * kBg, nb = npad / kBg;
+    double* W = scratch;
+    double* a0 = W + (size_t)npad * npad;
+    double* Z = a0 + npad;
+    double* P = Z + (size_t)kBg * npad;
+    topo::launch(k_bgj_setup, blocks_for((long long)npad * npad), kThreads, 0, st, n, npad,
+                 (const double*)A, W, a0, info);
+    for (int K = 0; K < nb; ++K) {
+      topo::launch(k_bgj_pivot, 1, kBg * 8, 0, st, npad, K, (const double*)W, (const double*)a0,
+                   P, info);
+      topo::launch(k_bgj_zrow, nb, kBg * 8, 0, st, npad, K, (const double*)W, (const double*)P, Z,
+                   (const int*)info);
+      topo::launch(k_bgj_update, dim3(nb, nb), kBg * 8, 0, st, npad, K, W, (const double*)Z,
+                   (const int*)info);
+      topo::launch(k_bgj_final, nb, kBg * 8, 0, st, npad, K, W, (const double*)P,
+                   (const double*)Z, (const int*)info);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    topo::launch(k_bgj_copy, blocks_for((long long)n * n), kThreads, 0, st, n, npad,
+                 (const double*)W, Ainv, (const int*)info);
+    return cudaGetLastError();
+  }
   const int* only_if = nullptr;
   if (allow_ns && n <= kGjMaxN && scratch && ns_bad) {
     // X ping-pongs between Ainv and T so that the last product lands in Ainv (kNsSteps even)

@@ -842,7 +842,7 @@ topo_status enqueue_build(topo_solver* s) {
   // K systems: Newton-Schulz inverse for small coarsest levels; IP systems keep the modified
   // Cholesky, whose pivot floor guards the nearly singular Schur complement of the multiplier.
   TOPO_CUDA(launch_cholesky_inverse(s->nc + (s->arrow ? 1 : 0), s->Adense, s->Ainv, s->info, st,
-                                    s->Ascratch, s->info + 2, !s->arrow && s->Ascratch));
+                                    s->Ascratch, s->info + 2, !s->arrow && s->Ascratch != nullptr));
   return TOPO_OK;
 }
 
@@ -1005,7 +1005,8 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   TOPO_TRY(s->alloc(&s->Adense, na * na));
   TOPO_TRY(s->alloc(&s->Ainv, na * na));
   TOPO_TRY(s->alloc(&s->info, 4));
-  if (!arrow && coarse_scratch_doubles((int)na))
+  // Newton-Schulz products (small K systems) or the block Gauss-Jordan workspace (larger ones)
+  if ((!arrow || na > 128) && coarse_scratch_doubles((int)na))
     TOPO_TRY(s->alloc(&s->Ascratch, coarse_scratch_doubles((int)na)));
   TOPO_TRY(s->alloc(&s->pw_est, 2));
   // densities and CG vectors (IP systems: trailing lambda entry, padded to an even length)
