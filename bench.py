@@ -189,7 +189,7 @@ def main():
     ap.add_argument("--no-ip", action="store_true", help="skip the 512x256 IP/OC wall-time runs")
     ap.add_argument("--outer-fp64", action="store_true",
                     help="mixed solver with the FP64 outer operator instead of float pairs")
-    ap.add_argument("--only", choices=["mixed", "fp64", "batched3d"], default=None,
+    ap.add_argument("--only", choices=["mixed", "fp64", "batched3d", "ip"], default=None,
                     help="run one solver configuration only (for profiler launch lists); no JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -301,27 +301,6 @@ def main():
                 "smoother": "damped Jacobi omega=0.5 nu1=nu2=2",
                 "precision": "FP32 V-cycle, FP64 CG and outer operator"}
 
-    if args.only == "batched3d":
-        r = batched_3d_run(args.steps, args.warmup)
-        print("only=batched3d ms_per_step=%.3f iterations=%.1f" % (r["ms_per_step"],
-                                                                  r["iterations_per_solve"]))
-        return 0
-    if args.only:
-        r = run(topo.MIXED if args.only == "mixed" else topo.FP64, args.steps, args.warmup)
-        print("only=%s ms_per_step=%.3f iterations=%d launches=%d" % (
-            args.only, r["ms"] / args.steps, r["iters"], r["launches"]), flush=True)
-        return 0
-    # warm-up + timed steps: mixed (headline, with live operator timing), FP64, end-to-end
-    with ClockSampler(dev.index) as clk:
-        # headline: event pairs around the outer operator only (one pair adds ~nothing)
-        mixed = run(topo.MIXED, args.steps, args.warmup, profile_mask=1)
-        fp64 = run(topo.FP64, args.steps, args.warmup, profile_mask=1)
-        e2e = run(topo.MIXED, args.steps, args.warmup, host_io=True)
-        # separate run with every kind profiled, for the per-kernel and per-part times (its own
-        # step time is longer by the extra event nodes and is not reported)
-        kinds_run = run(topo.MIXED, max(1, min(args.steps, 5)), 3,
-                        profile_mask=(1 << len(topo.Solver.PROFILE_KINDS)) - 1)
-
     def ip_oc_runs():
         """512x256 cantilever (Example 2 shape 428, V = 0.4 m, 6 levels): IP and AOC with 50 outer
         iterations each (linear solves to 1e-8), FP64 and mixed."""
@@ -347,6 +326,37 @@ def main():
                                   "compliance": oinfo.compliance}
             oc.close()
         return out
+
+    if args.only == "ip":  # profiling aid: the mixed IP run on 512x256, steps = Newton budget
+        c2 = W.cantilever_2d(512, 256, 0.4)
+        f2 = torch.as_tensor(c2["f"], device=dev)
+        ip = topo.IP(512, 256, fixed=c2["fixed"], f=f2, V=c2["V"], xbar=1.0, levels=6,
+                     precision=topo.MIXED, max_iter=1000)
+        info = ip.run(topo.ip_options(cg_tol=1e-8, max_newton=args.steps))
+        print("only=ip wall_ms=%.3f newton=%d cg_iters=%d" % (info.wall_ms, info.newton,
+                                                              info.cg_iters))
+        ip.close()
+        return 0
+    if args.only == "batched3d":
+        r = batched_3d_run(args.steps, args.warmup)
+        print("only=batched3d ms_per_step=%.3f iterations=%.1f" % (r["ms_per_step"],
+                                                                  r["iterations_per_solve"]))
+        return 0
+    if args.only:
+        r = run(topo.MIXED if args.only == "mixed" else topo.FP64, args.steps, args.warmup)
+        print("only=%s ms_per_step=%.3f iterations=%d launches=%d" % (
+            args.only, r["ms"] / args.steps, r["iters"], r["launches"]), flush=True)
+        return 0
+    # warm-up + timed steps: mixed (headline, with live operator timing), FP64, end-to-end
+    with ClockSampler(dev.index) as clk:
+        # headline: event pairs around the outer operator only (one pair adds ~nothing)
+        mixed = run(topo.MIXED, args.steps, args.warmup, profile_mask=1)
+        fp64 = run(topo.FP64, args.steps, args.warmup, profile_mask=1)
+        e2e = run(topo.MIXED, args.steps, args.warmup, host_io=True)
+        # separate run with every kind profiled, for the per-kernel and per-part times (its own
+        # step time is longer by the extra event nodes and is not reported)
+        kinds_run = run(topo.MIXED, max(1, min(args.steps, 5)), 3,
+                        profile_mask=(1 << len(topo.Solver.PROFILE_KINDS)) - 1)
 
     def gather_max(v):
         if ws == 1:

@@ -253,6 +253,17 @@ topo_status topo_ip_get_state(topo_ip* ip, double* u, double* x, double* phi, do
                               double* scal);
 topo_status topo_ip_set_state(topo_ip* ip, const double* u, const double* x, const double* phi,
                               const double* psi, const double* scal);
+/* The rest of the state a bitwise resume needs: the power-iteration vectors of the
+ * augmented-system solver.  Its damping omega_k = min(omega, 4/(3 * 1.05 lambda_k)) takes
+ * lambda_k ~ lambda_max(D_k^{-1} Z_k) from a power iteration on every level (Sec. 5); the first
+ * build runs 15 steps from a fixed start vector, each later build 5 steps from the previous
+ * build's vectors.  len [host] receives the number of doubles (0 when no level iterates).
+ * get: v [device, len] receives the vectors, ready [host] = 1 if they come from a successful
+ * build (else the next build starts from the fixed vector).  set: v [device, len] is copied
+ * when ready = 1 (v may be null when ready = 0).  Both synchronize the IP's stream. */
+topo_status topo_ip_power_state_size(topo_ip* ip, long long* len);
+topo_status topo_ip_get_power_state(topo_ip* ip, double* v, int* ready);
+topo_status topo_ip_set_power_state(topo_ip* ip, const double* v, int ready);
 
 /* ---- Optimality Conditions methods (Sec. 4) ----------------------------------------------
  * OC: u = K(x)^{-1} f, E_i = u^T K_i u, bisection on lambda in [0, lam_hi] until the interval is

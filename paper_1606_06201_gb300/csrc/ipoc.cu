@@ -372,6 +372,39 @@ topo_status topo_ip_set_state(topo_ip* a, const double* u, const double* x, cons
   return TOPO_OK;
 }
 
+// Power-iteration vectors of the augmented-system solver (start vectors of the next build's
+// lambda_max estimates); device copies on the solver's stream.
+topo_status topo_ip_power_state_size(topo_ip* a, long long* len) {
+  if (!a || !len) return TOPO_E_INVALID_ARG;
+  *len = (long long)a->Z->pw_len;
+  return TOPO_OK;
+}
+
+topo_status topo_ip_get_power_state(topo_ip* a, double* v, int* ready) {
+  if (!a || !ready || (a->Z->pw_len && !v)) return TOPO_E_INVALID_ARG;
+  StreamGuard gd(a->Z);
+  cudaStream_t st = a->Z->st;
+  if (a->Z->pw_len)
+    TOPO_CUDA(cudaMemcpyAsync(v, a->Z->pw_vec, sizeof(double) * a->Z->pw_len,
+                              cudaMemcpyDeviceToDevice, st));
+  TOPO_CUDA(cudaStreamSynchronize(st));
+  *ready = a->Z->pw_ready ? 1 : 0;
+  return TOPO_OK;
+}
+
+topo_status topo_ip_set_power_state(topo_ip* a, const double* v, int ready) {
+  if (!a || (ready && a->Z->pw_len && !v)) return TOPO_E_INVALID_ARG;
+  StreamGuard gd(a->Z);
+  cudaStream_t st = a->Z->st;
+  if (ready && a->Z->pw_len) {
+    TOPO_CUDA(cudaMemcpyAsync(a->Z->pw_vec, v, sizeof(double) * a->Z->pw_len,
+                              cudaMemcpyDeviceToDevice, st));
+    TOPO_CUDA(cudaStreamSynchronize(st));
+  }
+  a->Z->pw_ready = ready && a->Z->pw_len;
+  return TOPO_OK;
+}
+
 // ---- OC -----------------------------------------------------------------------------------
 
 topo_status topo_oc_create(const topo_solver_desc* desc, const double* f, double V, double xbar,

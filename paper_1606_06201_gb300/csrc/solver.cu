@@ -757,7 +757,13 @@ topo_status solve_impl(topo_solver* s, const double* b, double* u, double tol, i
   return worst;
 }
 
-topo_status enqueue_build(topo_solver* s) {
+// Power iterations for lambda_max(D^{-1} A_k): from the fixed start vector on the first build, and
+// from the previous build's vector afterwards (the matrices of consecutive IP Newton steps or OC
+// iterations are close, so a few steps refine the estimate).
+constexpr int kPowerCold = 15;
+constexpr int kPowerWarm = 5;
+
+topo_status enqueue_build(topo_solver* s, bool warm = false) {
   const int nl = s->nlev;
   const bool mixed = s->prec == TOPO_MIXED;
   cudaStream_t st = s->st;
@@ -814,10 +820,12 @@ topo_status enqueue_build(topo_solver* s) {
       TOPO_CUDA(launch_inv_diag(lv.d, s->K0, k == 0 ? s->x : nullptr, lv.Ae, lv.fixed, lv.invd, st));
     if (lv.omega_dev || lv.lam_dev) {  // lambda_max(D^{-1} A_k) by power iteration
       const int ar = s->arrow ? 1 : 0;
-      TOPO_CUDA(launch_power_init(lv.n, ar, s->p, lv.fixed, st));
-      for (int it = 0; it < 15; ++it) {
-        TOPO_TRY(apply_level<double>(s, k, 0, s->p, nullptr, s->q, nullptr));
-        TOPO_CUDA(launch_power_step(lv.n, ar, s->p, s->q, lv.invd, s->zll, s->r, s->partials,
+      double* pv = s->pw_vec + s->pw_off[k];
+      if (!warm) TOPO_CUDA(launch_power_init(lv.n, ar, pv, lv.fixed, st));
+      const int steps = warm ? kPowerWarm : kPowerCold;
+      for (int it = 0; it < steps; ++it) {
+        TOPO_TRY(apply_level<double>(s, k, 0, pv, nullptr, s->q, nullptr));
+        TOPO_CUDA(launch_power_step(lv.n, ar, pv, s->q, lv.invd, s->zll, s->r, s->partials,
                                     s->counters, s->pw_est, st));
       }
       if (lv.lam_dev)
@@ -847,8 +855,18 @@ topo_status enqueue_build(topo_solver* s) {
 }
 
 topo_status build_hierarchy(topo_solver* s) {
-  if (!s->build) TOPO_TRY(capture(s, &s->build, &s->build_kernels, [&]() { return enqueue_build(s); }));
-  TOPO_TRY(launch_graph(s, s->build, s->build_kernels));
+  const bool warm = s->pw_vec && s->pw_ready;
+  s->pw_ready = false;  // a failed build leaves no vectors to start from
+  if (warm) {
+    if (!s->build_warm)
+      TOPO_TRY(capture(s, &s->build_warm, &s->build_warm_kernels,
+                       [&]() { return enqueue_build(s, true); }));
+    TOPO_TRY(launch_graph(s, s->build_warm, s->build_warm_kernels));
+  } else {
+    if (!s->build)
+      TOPO_TRY(capture(s, &s->build, &s->build_kernels, [&]() { return enqueue_build(s); }));
+    TOPO_TRY(launch_graph(s, s->build, s->build_kernels));
+  }
   int info_h[2] = {0, 0};
   TOPO_CUDA(cudaMemcpyAsync(info_h, s->info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s->st));
   TOPO_CUDA(cudaStreamSynchronize(s->st));
@@ -860,6 +878,7 @@ topo_status build_hierarchy(topo_solver* s) {
     set_error("coarsest operator is not positive definite (pivot " + std::to_string(info_h[0]) + ")");
     return TOPO_E_BREAKDOWN;
   }
+  s->pw_ready = s->pw_vec != nullptr;
   return TOPO_OK;
 }
 
@@ -885,6 +904,7 @@ topo_status topo_solver_destroy(topo_solver* s) {
   for (int k = 0; k < 2; ++k)
     if (s->setup[k]) cudaGraphExecDestroy(s->setup[k]);
   if (s->build) cudaGraphExecDestroy(s->build);
+  if (s->build_warm) cudaGraphExecDestroy(s->build_warm);
   for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
   for (void* p : s->allocs) cudaFree(p);
   if (s->sc_host) cudaFreeHost(s->sc_host);
@@ -1009,6 +1029,16 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   if ((!arrow || na > 128) && coarse_scratch_doubles((int)na))
     TOPO_TRY(s->alloc(&s->Ascratch, coarse_scratch_doubles((int)na)));
   TOPO_TRY(s->alloc(&s->pw_est, 2));
+  {  // power-iteration vectors (with the trailing lambda entry of IP systems, padded to even)
+    size_t tot = 0;
+    s->pw_off.assign(s->nlev, 0);
+    for (int k = 0; k < s->nlev; ++k) {
+      s->pw_off[k] = tot;
+      if (s->L[k].omega_dev || s->L[k].lam_dev) tot += (size_t)s->L[k].n + 2;
+    }
+    s->pw_len = tot;
+    if (tot) TOPO_TRY(s->alloc(&s->pw_vec, tot));
+  }
   // densities and CG vectors (IP systems: trailing lambda entry, padded to an even length)
   const long long m = s->L[0].m;
   const long long n = s->L[0].n + (arrow ? 2 : 0);

@@ -81,6 +81,12 @@ struct topo_solver {
   double setup_tol[2] = {-1.0, -1.0};
   cudaGraphExec_t build = nullptr;        // Galerkin hierarchy and coarsest factorisation
   int build_kernels = 0;
+  cudaGraphExec_t build_warm = nullptr;   // the same with warm-started power iterations
+  int build_warm_kernels = 0;
+  double* pw_vec = nullptr;               // power-iteration vectors of the levels, kept
+  std::vector<size_t> pw_off;             // between builds (offsets into pw_vec)
+  size_t pw_len = 0;                      // doubles in pw_vec
+  bool pw_ready = false;                  // pw_vec holds the last build's vectors
   int graph_iters = 4;
   unsigned long long launches = 0;        // kernels launched by this solver
   bool profiling = false;

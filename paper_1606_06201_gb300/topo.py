@@ -107,6 +107,9 @@ _SIGS = {
     "topo_ip_run": (ctypes.c_int, [_vp, ctypes.POINTER(IpOpts), ctypes.POINTER(IpInfo)]),
     "topo_ip_get_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "topo_ip_set_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "topo_ip_power_state_size": (ctypes.c_int, [_vp, _vp]),
+    "topo_ip_get_power_state": (ctypes.c_int, [_vp, _vp, _vp]),
+    "topo_ip_set_power_state": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "topo_oc_create": (ctypes.c_int, [ctypes.POINTER(SolverDesc), _vp, ctypes.c_double,
                                       ctypes.c_double, ctypes.POINTER(_vp)]),
     "topo_oc_destroy": (ctypes.c_int, [_vp]),
@@ -247,18 +250,38 @@ class IP:
         return info
 
     def state(self):
+        """(u, x, phi, psi, scal, pw): the iterate, scal = (lambda, s, r) on the host, and pw the
+        augmented solver's power-iteration vectors with a trailing 1.0 when the next build starts
+        from them (0.0: from the fixed start vector)."""
         import torch
         u = torch.empty(self.n, dtype=torch.float64, device="cuda")
         x, phi, psi = (torch.empty(self.m, dtype=torch.float64, device="cuda") for _ in range(3))
         scal = np.zeros(3)
         _check(_lib.topo_ip_get_state(self._h, _ptr(u), _ptr(x), _ptr(phi), _ptr(psi),
                                       scal.ctypes.data_as(_vp)), "topo_ip_get_state")
-        return u, x, phi, psi, scal
+        ln = ctypes.c_longlong(0)
+        _check(_lib.topo_ip_power_state_size(self._h, ctypes.byref(ln)), "topo_ip_power_state_size")
+        pw = torch.zeros(ln.value + 1, dtype=torch.float64, device="cuda")
+        ready = ctypes.c_int(0)
+        _check(_lib.topo_ip_get_power_state(self._h, _ptr(pw), ctypes.byref(ready)),
+               "topo_ip_get_power_state")
+        pw[ln.value] = float(ready.value)
+        return u, x, phi, psi, scal, pw
 
-    def set_state(self, u, x, phi, psi, scal):
+    def set_state(self, u, x, phi, psi, scal, pw=None):
         scal = np.ascontiguousarray(scal, dtype=np.float64)
         _check(_lib.topo_ip_set_state(self._h, _ptr(u), _ptr(x), _ptr(phi), _ptr(psi),
                                       scal.ctypes.data_as(_vp)), "topo_ip_set_state")
+        ln = ctypes.c_longlong(0)
+        _check(_lib.topo_ip_power_state_size(self._h, ctypes.byref(ln)), "topo_ip_power_state_size")
+        if pw is None:
+            _check(_lib.topo_ip_set_power_state(self._h, None, 0), "topo_ip_set_power_state")
+            return
+        if pw.numel() != ln.value + 1:
+            raise ValueError("set_state: power state has %d entries, expected %d"
+                             % (pw.numel(), ln.value + 1))
+        ready = int(float(pw[ln.value]) != 0.0)
+        _check(_lib.topo_ip_set_power_state(self._h, _ptr(pw), ready), "topo_ip_set_power_state")
 
 
 class OC:

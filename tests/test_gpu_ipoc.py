@@ -38,7 +38,7 @@ def test_ip_trajectory_fp64_matches_oracle(shape, levels):
     worst_x = worst_u = 0.0
     for k, st in enumerate(traj):
         info = solver.step(opts)
-        u, x, phi, psi, scal = solver.state()
+        u, x, phi, psi, scal, _ = solver.state()
         worst_x = max(worst_x, _rel(host(x), st["x"]))
         worst_u = max(worst_u, _rel(host(u), st["u"]))
         assert abs(scal[0] - st["lam"]) <= 1e-9 * max(1.0, abs(st["lam"])), k
@@ -58,7 +58,7 @@ def test_ip_mixed_run_matches_oracle():
     solver = topo.IP(64, 32, fixed=cfg["fixed"], f=dev(torch, cfg["f"]), V=cfg["V"],
                      xbar=cfg["xbar"], levels=3, precision=topo.MIXED, max_iter=5000)
     info = solver.run(topo.ip_options(cg_tol=1e-10))
-    u, x, phi, psi, scal = solver.state()
+    u, x, phi, psi, scal, _ = solver.state()
     assert info.done == 1 and info.ip_iters == 12
     assert _rel(host(x), z[2]) <= 1e-6
     c = float(cfg["f"] @ host(u))
@@ -68,6 +68,8 @@ def test_ip_mixed_run_matches_oracle():
 
 
 def test_ip_checkpoint_resume_is_bitwise():
+    """Resuming from a snapshot (iterate, scalars and the augmented solver's power-iteration
+    vectors) reproduces the uninterrupted run bit for bit."""
     torch = torch_cuda()
     topo = topo_lib()
     cfg, _ = _problem(32, 16)
@@ -77,6 +79,7 @@ def test_ip_checkpoint_resume_is_bitwise():
     for _ in range(5):
         a.step(opts)
     snap = [t.clone() if hasattr(t, "clone") else t.copy() for t in a.state()]
+    assert snap[5].numel() > 1 and float(snap[5][-1]) == 1.0  # warm vectors from the last build
     for _ in range(4):
         a.step(opts)
     ref = [host(t) if hasattr(t, "cpu") else t for t in a.state()]
@@ -154,7 +157,7 @@ def test_ip_512x256_scalars_stay_consistent():
         ip.init(opts)
         for _ in range(4):
             info = ip.step(opts)
-            u, x, phi, psi, scal = ip.state()
+            u, x, phi, psi, scal, _ = ip.state()
             assert scal[1] == 0.2 ** info.ip_iters and scal[2] == 0.2 ** info.ip_iters
             assert np.isfinite(scal[0]) and abs(scal[0]) < 10.0
             xh = host(x)

@@ -442,6 +442,15 @@ def test_chebyshev_smoother_solves_and_is_symmetric(precision):
         Mc = host(s.apply_vcycle(dev(torch, c)))
         assert abs(Ma @ c - a @ Mc) <= 1e-11 * abs(Ma @ c)
         assert a @ Ma > 0
+    # a second density: the power iterations start from the first build's vectors
+    x2 = _x(nx, ny, 0, 45)
+    s.set_density(dev(torch, x2))
+    u2, info2 = s.solve(dev(torch, f), tol=tol)
+    K2, _, _ = oracle_K_free(nx, ny, 0, x2, fixed.astype(bool))
+    exact2 = np.zeros(s.n)
+    exact2[free] = SPDSolver(K2, grid, free).solve(f[free])
+    assert info2.status == topo.OK
+    assert rel_err(host(u2), exact2) <= (1e-10 if precision == 0 else 1e-6)
 
 
 def test_autotuner_picks_a_converging_setting(tmp_path):
