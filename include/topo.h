@@ -242,6 +242,8 @@ topo_status topo_ip_create(const topo_solver_desc* desc, const double* f, double
                            topo_ip** out);
 topo_status topo_ip_destroy(topo_ip* ip);
 topo_status topo_ip_set_stream(topo_ip* ip, void* cuda_stream);
+/* topo_set_vcycle_fusion on both solvers of the IP (the same bits either way). */
+topo_status topo_ip_set_vcycle_fusion(topo_ip* ip, int on);
 /* x = V/m, u = K(x)^{-1} f, lambda = 1, phi = psi = e, s = r = 1 (Sec. 3.1). */
 topo_status topo_ip_init(topo_ip* ip, const topo_ip_opts* opts);
 /* One Newton step (Sec. 3.1 steps 1-4); info after the step. */

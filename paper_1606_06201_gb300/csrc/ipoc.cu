@@ -231,6 +231,12 @@ topo_status topo_ip_set_stream(topo_ip* a, void* stream) {
   return topo_set_stream(a->Z, stream);
 }
 
+topo_status topo_ip_set_vcycle_fusion(topo_ip* a, int on) {
+  if (!a) return TOPO_E_INVALID_ARG;
+  TOPO_TRY(topo_set_vcycle_fusion(a->K, on));
+  return topo_set_vcycle_fusion(a->Z, on);
+}
+
 topo_status topo_ip_init(topo_ip* a, const topo_ip_opts* o) {
   if (!a || !o) return TOPO_E_INVALID_ARG;
   StreamGuard gd(a->Z);

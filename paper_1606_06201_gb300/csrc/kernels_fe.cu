@@ -215,6 +215,118 @@ __global__ void __launch_bounds__(kThreads) k_apply(Dims d, const T* __restrict_
   }
 }
 
+// Block sum of one double per thread (deterministic tree), result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double warp_sums[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) warp_sums[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (wid == 0) {
+    s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  return s;
+}
+
+// The swept vector of the first two sweeps from zero on a coarse level of an IP system: VJac0 for
+// the node entries and yl = omega_l b_lambda / Z_ll for the lambda entry (index n).
+template <typename T>
+struct VJac0Arrow {
+  VJac0<false, T> u;
+  long long n;
+  T yl;
+  __device__ __forceinline__ T operator()(long long i) const { return i == n ? yl : u(i); }
+};
+
+// Node rows of one coarse IP level over a grid-stride range of nodes; returns this thread's
+// partial sum of w_i v_i (v as vin supplies it).
+template <int DIM, typename T, int MODE, typename VIn>
+__device__ __forceinline__ double arrow_node_rows(const Dims& d, const T* __restrict__ Ae,
+                                                  const VIn& vin, const T* __restrict__ b,
+                                                  T* __restrict__ y, const T* __restrict__ invd,
+                                                  T omega, const uint8_t* __restrict__ fixed,
+                                                  const T* __restrict__ w) {
+  const long long nodes = d.nodes();
+  double part = 0.0;
+  for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < nodes;
+       node += (long long)gridDim.x * blockDim.x) {
+    apply_node<DIM, T, MODE, false, false>(d, node, nullptr, nullptr, Ae, vin, b, y, invd, omega,
+                                           fixed, MODE == 3 ? nullptr : w);
+    if (MODE != 3)
+#pragma unroll
+      for (int c = 0; c < DIM; ++c)
+        part = fma((double)w[DIM * node + c], (double)vin(DIM * node + c), part);
+  }
+  return part;
+}
+
+// Coarse level of an IP system (the arrow matrix of Eq. (nwtr2) after Galerkin coarsening): the
+// node rows of apply_node with the arrow column w, and in the same pass the lambda row
+// (Z v)_lambda = w^T v_u + Z_ll v_lambda.  Each block sums w_i v_i over its nodes; the last block
+// to finish adds the block sums in block order and writes y[n] per MODE, with the lambda entry's
+// damping omega_l (or *wdev when the damping comes from the power iteration).  MODE 4 is the
+// first two sweeps from zero in one pass (the swept vector formed on the fly by VJac0Arrow; the
+// same bits as modes 3 then 2).  Grid-stride over nodes with at most kRedBlocks blocks, one
+// partial sum each.
+template <int DIM, typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) k_apply_arrow(Dims d, const T* __restrict__ Ae,
+                                                          const T* __restrict__ v,
+                                                          const T* __restrict__ b,
+                                                          T* __restrict__ y,
+                                                          const T* __restrict__ invd, T omega,
+                                                          const uint8_t* __restrict__ fixed,
+                                                          const CgScalars* __restrict__ sc,
+                                                          const T* __restrict__ w,
+                                                          const double* zll, double omega_l,
+                                                          const double* wdev, double* partials,
+                                                          unsigned* counter) {
+  pdl_prologue();
+  if (sc && sc[0].done) return;
+  const long long n = d.nodes() * DIM;
+  const double z = *zll, om = wdev ? *wdev : omega_l;
+  T yl = T(0);
+  double part;
+  if constexpr (MODE == 4) {
+    yl = (T)(om * (double)b[n] / z);
+    const VJac0Arrow<T> vin{VJac0<false, T>{b, invd, fixed, omega}, n, yl};
+    part = arrow_node_rows<DIM, T, MODE>(d, Ae, vin, b, y, invd, omega, fixed, w);
+  } else {
+    const VLoad<false, T> vin{v};
+    part = arrow_node_rows<DIM, T, MODE>(d, Ae, vin, b, y, invd, omega, fixed, w);
+  }
+  __shared__ bool last;
+  const double bs = block_sum(part);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = bs;
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  double acc = 0.0;
+  for (unsigned t = threadIdx.x; t < gridDim.x; t += blockDim.x) acc += __ldcg(partials + t);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) {
+    *counter = 0;
+    double out;
+    if (MODE == 3) {
+      out = om * (double)b[n] / z;
+    } else {
+      const double vl = MODE == 4 ? (double)yl : (double)v[n];
+      const double q = acc + z * vl;
+      if (MODE == 0) out = q;
+      else if (MODE == 1) out = (double)b[n] - q;
+      else out = vl + om * ((double)b[n] - q) / z;
+    }
+    y[n] = (T)out;
+  }
+}
+
 // First coarse level of the 2D grid without stored element matrices: the Galerkin element matrix
 // of coarse element E is sum_c x_c C_c over its four children (C_c = P_c^T K0 P_c), so
 // (A v)_node = sum_{E at node} sum_c x_c (C_c v_E)_row.  xf: densities of the finest level.
@@ -299,23 +411,6 @@ void apply_dispatch(const Dims& d, const T* K0, const T* x, const T* Ae, const T
                omega, fixed, sc, w);
 }
 
-// Block sum of one double per thread (deterministic tree), result valid in thread 0.
-__device__ __forceinline__ double block_sum(double v) {
-  __shared__ double warp_sums[32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) warp_sums[wid] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (wid == 0) {
-    s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  }
-  return s;
-}
 
 // q = A p (FP64, finest level) with the partial sums of p^T q; the last block to finish adds the
 // partials in block order and forms alpha = r^T y / p^T A p (Algorithm PCG).
@@ -758,6 +853,47 @@ template cudaError_t launch_apply<float>(const Dims&, int, const float*, const f
                                          const float*, const float*, float*, const float*, float,
                                          const uint8_t*, int, const CgScalars*, cudaStream_t,
                                          const float*);
+
+template <typename T>
+cudaError_t launch_apply_arrow(const Dims& d, int mode, const T* Ae, const T* v, const T* b, T* y,
+                               const T* invd, T omega, const uint8_t* fixed, const T* w,
+                               const double* zll, double omega_l, const double* wdev,
+                               double* partials, unsigned* counter, const CgScalars* sc,
+                               cudaStream_t st) {
+  const long long nb = blocks_for(d.nodes());
+  const unsigned grid = (unsigned)(nb < kRedBlocks ? nb : kRedBlocks);
+#define TOPO_ARROW(DIM, MODE)                                                                  \
+  topo::launch(k_apply_arrow<DIM, T, MODE>, grid, kThreads, 0, st, d, Ae, v, b, y, invd, omega, \
+               fixed, sc, w, zll, omega_l, wdev, partials, counter)
+#define TOPO_ARROW_MODES(DIM)          \
+  switch (mode) {                      \
+    case 0: TOPO_ARROW(DIM, 0); break; \
+    case 1: TOPO_ARROW(DIM, 1); break; \
+    case 2: TOPO_ARROW(DIM, 2); break; \
+    case 3: TOPO_ARROW(DIM, 3); break; \
+    default: return cudaErrorInvalidValue; \
+  }
+  if (d.dim == 2 && mode == 4) {
+    TOPO_ARROW(2, 4);
+  } else if (d.dim == 2) {
+    TOPO_ARROW_MODES(2)
+  } else {
+    TOPO_ARROW_MODES(3)
+  }
+#undef TOPO_ARROW_MODES
+#undef TOPO_ARROW
+  return cudaGetLastError();
+}
+template cudaError_t launch_apply_arrow<double>(const Dims&, int, const double*, const double*,
+                                                const double*, double*, const double*, double,
+                                                const uint8_t*, const double*, const double*,
+                                                double, const double*, double*, unsigned*,
+                                                const CgScalars*, cudaStream_t);
+template cudaError_t launch_apply_arrow<float>(const Dims&, int, const float*, const float*,
+                                               const float*, float*, const float*, float,
+                                               const uint8_t*, const float*, const double*, double,
+                                               const double*, double*, unsigned*, const CgScalars*,
+                                               cudaStream_t);
 
 template <typename T>
 cudaError_t launch_apply_l1(const Dims& d, int mode, const T* C, const T* xf, const T* v,

@@ -223,37 +223,6 @@ __global__ void __launch_bounds__(kThreads) k_z_node(Dims d, const T* __restrict
   }
 }
 
-// Lambda row on a coarse level: (Z v)_lambda = w^T v_u + Z_ll v_lambda, written per MODE.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreads) k_arrow_row(long long n, const T* __restrict__ w,
-                                                        const T* __restrict__ v,
-                                                        const T* __restrict__ b,
-                                                        T* __restrict__ y, const double* zll,
-                                                        double omega, double* partials,
-                                                        unsigned* counter, const CgScalars* sc,
-                                                        const double* wdev) {
-  pdl_prologue();
-  if (sc && sc[0].done) return;
-  if (wdev) omega = *wdev;
-  double part[1] = {0.0};
-  if (MODE != 3)
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-      part[0] = fma((double)w[i], (double)v[i], part[0]);
-  double tot[1];
-  if (!last_block<1>(part, 0, partials, counter, tot)) return;
-  if (threadIdx.x == 0) {
-    const double z = *zll;
-    const double q = tot[0] + z * (double)v[n];
-    double out;
-    if (MODE == 0) out = q;
-    else if (MODE == 1) out = (double)b[n] - q;
-    else if (MODE == 2) out = (double)v[n] + omega * ((double)b[n] - q) / z;
-    else out = omega * (double)b[n] / z;
-    y[n] = (T)out;
-  }
-}
-
 // ---- IP element and node kernels ---------------------------------------------------------
 // Per element at z = (u, lambda, x, phi, psi) and barrier (s, r):
 //   g_e = K0 u_e, F3 = -1/2 u_e^T g_e - lambda - phi + psi, Res4 = s - phi x,
@@ -612,38 +581,6 @@ template cudaError_t launch_z_apply_fine<float>(const Dims&, int, const float*, 
                                                 const uint8_t*, const double*, double*, unsigned*,
                                                 const CgScalars*, cudaStream_t, const double*);
 
-template <typename T>
-cudaError_t launch_arrow_row(long long n, int mode, const T* w, const T* v, const T* b, T* y,
-                             const double* zll, double omega, double* partials, unsigned* counter,
-                             const CgScalars* sc, cudaStream_t st, const double* wdev) {
-  const unsigned gr = red_grid(n);
-  switch (mode) {
-    case 0:
-      topo::launch(k_arrow_row<T, 0>, gr, kThreads, 0, st, n, w, v, b, y, zll, omega, partials, counter, sc,
-                                                 wdev);
-      break;
-    case 1:
-      topo::launch(k_arrow_row<T, 1>, gr, kThreads, 0, st, n, w, v, b, y, zll, omega, partials, counter, sc,
-                                                 wdev);
-      break;
-    case 2:
-      topo::launch(k_arrow_row<T, 2>, gr, kThreads, 0, st, n, w, v, b, y, zll, omega, partials, counter, sc,
-                                                 wdev);
-      break;
-    default:
-      topo::launch(k_arrow_row<T, 3>, gr, kThreads, 0, st, n, w, v, b, y, zll, omega, partials, counter, sc,
-                                                 wdev);
-  }
-  return cudaGetLastError();
-}
-template cudaError_t launch_arrow_row<double>(long long, int, const double*, const double*,
-                                              const double*, double*, const double*, double,
-                                              double*, unsigned*, const CgScalars*, cudaStream_t,
-                                              const double*);
-template cudaError_t launch_arrow_row<float>(long long, int, const float*, const float*,
-                                             const float*, float*, const double*, double, double*,
-                                             unsigned*, const CgScalars*, cudaStream_t,
-                                             const double*);
 
 cudaError_t launch_ip_residuals(const Dims& d, const double* K0, const double* u, const double* x,
                                 const double* phi, const double* psi, const double* f,

@@ -260,12 +260,10 @@ topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* 
                                         lv.omega_dev));
       return TOPO_OK;
     }
-    TOPO_CUDA(launch_apply<TV>(lv.d, mode, Prec<TV>::K0(s), nullptr, Prec<TV>::Ae(lv), v, b, y,
-                               Prec<TV>::invd(lv), omega, lv.fixed, 1, sc, s->st,
-                               mode == 3 ? nullptr : arrow_w<TV>(lv)));
-    TOPO_CUDA(launch_arrow_row<TV>(lv.n, mode, arrow_w<TV>(lv), v, b, y, s->zll,
-                                   (double)s->desc.omega, s->partials, s->counters, sc, s->st,
-                                   lv.omega_dev));
+    TOPO_CUDA(launch_apply_arrow<TV>(lv.d, mode, Prec<TV>::Ae(lv), v, b, y, Prec<TV>::invd(lv),
+                                     omega, lv.fixed, arrow_w<TV>(lv), s->zll,
+                                     (double)s->desc.omega, lv.omega_dev, s->partials,
+                                     s->counters, sc, s->st));
     return TOPO_OK;
   }
   if (k == 0 && s->q1_ok) {
@@ -395,8 +393,9 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
   // coarse 2D levels with stored element matrices: the first two sweeps as one kernel (mode 4).
   // (Prolongation with the first post-sweep measured slower there: a node-parallel kernel forms
   // P z_c once per element entry it reads, 32 times per node.)
-  const bool coarse_fused = !fine && s->fuse_on && s->dim == 2 && !s->arrow &&
-                            !(k == 1 && s->l1_free) && Prec<TV>::Ae(lv) != nullptr;
+  // IP systems: the same, with the lambda row in the kernel (k_apply_arrow).
+  const bool coarse_fused = !fine && s->fuse_on && s->dim == 2 && !(k == 1 && s->l1_free) &&
+                            Prec<TV>::Ae(lv) != nullptr;
   bool sweep_timed = false;  // profiling: the first smoothing kernel of the finest level
   if (nu1 >= 2 && fine_fused) {
     TOPO_TRY(prof_mark(s, 1, 0));

@@ -429,10 +429,16 @@ cudaError_t launch_z_apply_fine(const Dims& d, int mode, const T* K0, const T* x
                                 T omega, const uint8_t* fixed, const double* zll, double* partials,
                                 unsigned* counter, const CgScalars* sc, cudaStream_t st,
                                 const double* wdev = nullptr);
+// Coarse level of an IP system in one launch: node rows with the arrow column w, and the lambda
+// row w^T v_u + Z_ll v_lambda from a fixed-grid reduction in the same kernel (y[n] per mode, with
+// omega_l or *wdev for the lambda entry).  Modes 0-3 as launch_apply; mode 4 (2D only) the first
+// two sweeps from zero.  nrhs = 1.
 template <typename T>
-cudaError_t launch_arrow_row(long long n, int mode, const T* w, const T* v, const T* b, T* y,
-                             const double* zll, double omega, double* partials, unsigned* counter,
-                             const CgScalars* sc, cudaStream_t st, const double* wdev = nullptr);
+cudaError_t launch_apply_arrow(const Dims& d, int mode, const T* Ae, const T* v, const T* b, T* y,
+                               const T* invd, T omega, const uint8_t* fixed, const T* w,
+                               const double* zll, double omega_l, const double* wdev,
+                               double* partials, unsigned* counter, const CgScalars* sc,
+                               cudaStream_t st);
 cudaError_t launch_ip_residuals(const Dims& d, const double* K0, const double* u, const double* x,
                                 const double* phi, const double* psi, const double* f,
                                 const uint8_t* fixed, IpScalars* ip, double* g, double* tR3,

@@ -108,6 +108,7 @@ _SIGS = {
     "topo_ip_get_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "topo_ip_set_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "topo_ip_power_state_size": (ctypes.c_int, [_vp, _vp]),
+    "topo_ip_set_vcycle_fusion": (ctypes.c_int, [_vp, ctypes.c_int]),
     "topo_ip_get_power_state": (ctypes.c_int, [_vp, _vp, _vp]),
     "topo_ip_set_power_state": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "topo_oc_create": (ctypes.c_int, [ctypes.POINTER(SolverDesc), _vp, ctypes.c_double,
@@ -248,6 +249,9 @@ class IP:
         info = IpInfo()
         _check(_lib.topo_ip_run(self._h, ctypes.byref(opts), ctypes.byref(info)), "topo_ip_run")
         return info
+
+    def set_vcycle_fusion(self, on):
+        _check(_lib.topo_ip_set_vcycle_fusion(self._h, int(bool(on))), "topo_ip_set_vcycle_fusion")
 
     def state(self):
         """(u, x, phi, psi, scal, pw): the iterate, scal = (lambda, s, r) on the host, and pw the
