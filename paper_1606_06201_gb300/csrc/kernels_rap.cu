@@ -179,6 +179,154 @@ __global__ void k_rap_coarse(Dims df, const TI* __restrict__ Af, TO* __restrict_
   Ac[t] = acc;
 }
 
+// ---- 2D Galerkin products, one thread per coarse element ----------------------------------
+// The entry-parallel kernels above re-read each fine value once per output entry that uses it
+// (16 to 64 times) and spend most of their instructions on index arithmetic and zero-weight
+// tests.  In 2D one thread can hold all 64 outputs of its coarse element; the weights are then
+// compile-time constants (the zero ones vanish from the code), every fine value is read once,
+// and the constant tables travel in the kernel's parameter space, so each multiply-add reads its
+// table operand from the constant bank.  Every output is accumulated in the same order as in the
+// entry-parallel kernels (the same bits).
+
+template <typename T, int N>
+struct ConstTable {
+  T v[N];
+};
+
+__host__ __device__ constexpr float w1c(int p, int q) {
+  return (p - 2 * q == 0) ? 1.0f : ((p - 2 * q == 1 || p - 2 * q == -1) ? 0.5f : 0.0f);
+}
+__host__ __device__ constexpr int lox(int a) { return ((a & 3) == 1 || (a & 3) == 2) ? 1 : 0; }
+__host__ __device__ constexpr int loy(int a) { return ((a & 3) >= 2) ? 1 : 0; }
+// wchild<2>(c, a, A) as a constant expression
+__host__ __device__ constexpr float w2c(int c, int a, int A) {
+  return w1c((c & 1) + lox(a), lox(A)) * w1c(((c >> 1) & 1) + loy(a), loy(A));
+}
+
+constexpr int kRapElemThreads = 128;
+
+// First coarse level (k_rap_from_fine, 2D): A_E = sum_c x_c C_c (+ rank-one terms of Z).
+template <typename T>
+__global__ void __launch_bounds__(kRapElemThreads)
+    k_rap1_elem2d(Dims df, const __grid_constant__ ConstTable<T, 256> C, const T* __restrict__ x,
+                  T* __restrict__ Ac, const double* __restrict__ g,
+                  const double* __restrict__ Dinv) {
+  pdl_prologue();
+  const int cnx = df.nx / 2, cny = df.ny / 2;
+  const long long mc = (long long)cnx * cny;
+  const long long E = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (E >= mc) return;
+  const int EX = (int)(E % cnx), EY = (int)(E / cnx);
+  T acc[64];
+#pragma unroll
+  for (int q = 0; q < 64; ++q) acc[q] = T(0);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const long long fe = (2 * EX + (c & 1)) + (long long)df.nx * (2 * EY + ((c >> 1) & 1));
+    const T xc = x[fe];
+#pragma unroll
+    for (int q = 0; q < 64; ++q) acc[q] = fma(xc, C.v[c * 64 + q], acc[q]);
+    if (g) {
+      double gc[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) gc[q] = g[fe * 8 + q];
+      const double dc = Dinv[fe];
+      double h[8];
+#pragma unroll
+      for (int I = 0; I < 8; ++I) {
+        double hv = 0.0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) hv = fma((double)w2c(c, a, I / 2), gc[a * 2 + I % 2], hv);
+        h[I] = hv;
+      }
+#pragma unroll
+      for (int q = 0; q < 64; ++q) acc[q] = (T)fma(h[q / 8] * h[q % 8], dc, (double)acc[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 64; ++q) Ac[q * mc + E] = acc[q];
+}
+
+// Second coarse level from the finest densities (k_rap2_from_fine, 2D): A_E = sum_f x_f C2_f.
+template <typename T>
+__global__ void __launch_bounds__(kRapElemThreads)
+    k_rap2_elem2d(Dims df, const __grid_constant__ ConstTable<T, 1024> C2,
+                  const T* __restrict__ x, T* __restrict__ Ac) {
+  pdl_prologue();
+  const int cnx = df.nx / 4, cny = df.ny / 4;
+  const long long mc = (long long)cnx * cny;
+  const long long E = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (E >= mc) return;
+  const int EX = (int)(E % cnx), EY = (int)(E / cnx);
+  T xf[16];
+#pragma unroll
+  for (int f = 0; f < 16; ++f) {
+    const int c1 = f / 4, c2 = f % 4;
+    const int fx = 4 * EX + 2 * (c1 & 1) + (c2 & 1);
+    const int fy = 4 * EY + 2 * ((c1 >> 1) & 1) + ((c2 >> 1) & 1);
+    xf[f] = x[fx + (long long)df.nx * fy];
+  }
+#pragma unroll
+  for (int q = 0; q < 64; ++q) {
+    T acc = T(0);
+#pragma unroll
+    for (int f = 0; f < 16; ++f) acc = fma(xf[f], C2.v[f * 64 + q], acc);
+    Ac[q * mc + E] = acc;
+  }
+}
+
+// Deeper levels (k_rap_coarse, 2D): A_E = sum_c P_c^T A_c P_c, row pair (a, 0..1) of each child
+// read once and applied to every output it feeds.
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(kRapElemThreads)
+    k_rap_coarse_elem2d(Dims df, const TI* __restrict__ Af, TO* __restrict__ Ac) {
+  pdl_prologue();
+  const int cnx = df.nx / 2, cny = df.ny / 2;
+  const long long mc = (long long)cnx * cny;
+  const long long mf = df.elems();
+  const long long E = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (E >= mc) return;
+  const int EX = (int)(E % cnx), EY = (int)(E / cnx);
+  TO acc[64];
+#pragma unroll
+  for (int q = 0; q < 64; ++q) acc[q] = TO(0);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const long long fe = (2 * EX + (c & 1)) + (long long)df.nx * (2 * EY + ((c >> 1) & 1));
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      TO row[2][8];
+#pragma unroll
+      for (int al = 0; al < 2; ++al)
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          row[al][q] = (TO)__ldg(Af + (long long)((a * 2 + al) * 8 + q) * mf + fe);
+#pragma unroll
+      for (int A = 0; A < 4; ++A) {
+        constexpr float kZero = 0.0f;
+        const float wa = w2c(c, a, A);
+        if (wa == kZero) continue;
+#pragma unroll
+        for (int al = 0; al < 2; ++al)
+#pragma unroll
+          for (int J = 0; J < 8; ++J) {
+            const int B = J / 2, be = J % 2;
+            TO sv = TO(0);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              const float wb = w2c(c, b, B);
+              if (wb == kZero) continue;
+              sv = fma(row[al][b * 2 + be], (TO)wb, sv);
+            }
+            acc[(A * 2 + al) * 8 + J] = fma((TO)wa, sv, acc[(A * 2 + al) * 8 + J]);
+          }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 64; ++q) Ac[q * mc + E] = acc[q];
+}
+
 // Dense operator of a level (used for the coarsest level): entry (i, j) gathers the elements that
 // hold both DOFs' nodes.  Fixed DOFs get identity rows and columns.
 template <int DIM>
@@ -651,11 +799,16 @@ __global__ void k_dense_solve(int n, const double* __restrict__ Ainv, const T* _
 
 template <typename T>
 cudaError_t launch_rap_from_fine(const Dims& fine, const T* C, const T* x, T* Ac, cudaStream_t st,
-                                 const double* g, const double* Dinv) {
+                                 const double* g, const double* Dinv, const double* Ch) {
   const int ne = fine.dim == 2 ? 8 : 24;
   const long long mc = fine.elems() / (fine.dim == 2 ? 4 : 8);
   const long long total = mc * ne * ne;
-  if (fine.dim == 2)
+  if (fine.dim == 2 && Ch) {
+    ConstTable<T, 256> tab;
+    for (int i = 0; i < 256; ++i) tab.v[i] = (T)Ch[i];
+    topo::launch(k_rap1_elem2d<T>, (unsigned)((mc + kRapElemThreads - 1) / kRapElemThreads),
+                 kRapElemThreads, 0, st, fine, tab, x, Ac, g, Dinv);
+  } else if (fine.dim == 2)
     topo::launch(k_rap_from_fine<2, T>, blocks_for(total), kThreads, 0, st, fine, C, x, Ac, g, Dinv);
   else
     topo::launch(k_rap_from_fine<3, T>, blocks_for(total), kThreads, 0, st, fine, C, x, Ac, g, Dinv);
@@ -663,26 +816,32 @@ cudaError_t launch_rap_from_fine(const Dims& fine, const T* C, const T* x, T* Ac
 }
 template cudaError_t launch_rap_from_fine<double>(const Dims&, const double*, const double*,
                                                   double*, cudaStream_t, const double*,
-                                                  const double*);
+                                                  const double*, const double*);
 template cudaError_t launch_rap_from_fine<float>(const Dims&, const float*, const float*, float*,
-                                                 cudaStream_t, const double*, const double*);
+                                                 cudaStream_t, const double*, const double*,
+                                                 const double*);
 
 template <typename T>
 cudaError_t launch_rap2_from_fine(const Dims& fine, const T* C2, const T* x, T* Ac,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, const double* C2h) {
   const int ne = fine.dim == 2 ? 8 : 24;
   const long long mc = fine.elems() / (fine.dim == 2 ? 16 : 64);
   const long long total = mc * ne * ne;
-  if (fine.dim == 2)
+  if (fine.dim == 2 && C2h) {
+    ConstTable<T, 1024> tab;
+    for (int i = 0; i < 1024; ++i) tab.v[i] = (T)C2h[i];
+    topo::launch(k_rap2_elem2d<T>, (unsigned)((mc + kRapElemThreads - 1) / kRapElemThreads),
+                 kRapElemThreads, 0, st, fine, tab, x, Ac);
+  } else if (fine.dim == 2)
     topo::launch(k_rap2_from_fine<2, T>, blocks_for(total), kThreads, 0, st, fine, C2, x, Ac);
   else
     topo::launch(k_rap2_from_fine<3, T>, blocks_for(total), kThreads, 0, st, fine, C2, x, Ac);
   return cudaGetLastError();
 }
 template cudaError_t launch_rap2_from_fine<double>(const Dims&, const double*, const double*,
-                                                   double*, cudaStream_t);
+                                                   double*, cudaStream_t, const double*);
 template cudaError_t launch_rap2_from_fine<float>(const Dims&, const float*, const float*, float*,
-                                                  cudaStream_t);
+                                                  cudaStream_t, const double*);
 
 cudaError_t launch_inv_diag_l1(const Dims& coarse1, const double* C, const double* xf,
                                const uint8_t* fixed, double* invd, cudaStream_t st) {
@@ -699,7 +858,9 @@ cudaError_t launch_rap_coarse(const Dims& fine, const TI* Af, TO* Ac, cudaStream
   const long long mc = fine.elems() / (fine.dim == 2 ? 4 : 8);
   const long long total = mc * ne * ne;
   if (fine.dim == 2)
-    topo::launch(k_rap_coarse<2, TI, TO>, blocks_for(total), kThreads, 0, st, fine, Af, Ac);
+    topo::launch(k_rap_coarse_elem2d<TI, TO>,
+                 (unsigned)((mc + kRapElemThreads - 1) / kRapElemThreads), kRapElemThreads, 0, st,
+                 fine, Af, Ac);
   else
     topo::launch(k_rap_coarse<3, TI, TO>, blocks_for(total), kThreads, 0, st, fine, Af, Ac);
   return cudaGetLastError();

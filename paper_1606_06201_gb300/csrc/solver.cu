@@ -782,16 +782,19 @@ topo_status enqueue_build(topo_solver* s, bool warm = false) {
     const bool f32 = s->h32 && !lk.Ae;
     if (k == 1) {
       if (f32 && lk.Ae32)
-        TOPO_CUDA(launch_rap_from_fine<float>(s->L[0].d, s->C32, s->x32, lk.Ae32, st));
+        TOPO_CUDA(launch_rap_from_fine<float>(s->L[0].d, s->C32, s->x32, lk.Ae32, st, nullptr,
+                                              nullptr, s->C_host.data()));
       else if (lk.Ae)  // stored unless the first coarse level is applied matrix-free
         TOPO_CUDA(launch_rap_from_fine<double>(s->L[0].d, s->C, s->x, lk.Ae, st,
                                                s->arrow ? s->g : nullptr,
-                                               s->arrow ? s->Dinv : nullptr));
+                                               s->arrow ? s->Dinv : nullptr, s->C_host.data()));
     } else if (k == 2 && s->C2) {
       if (f32)
-        TOPO_CUDA(launch_rap2_from_fine<float>(s->L[0].d, s->C2f, s->x32, lk.Ae32, st));
+        TOPO_CUDA(launch_rap2_from_fine<float>(s->L[0].d, s->C2f, s->x32, lk.Ae32, st,
+                                               s->C2_host.data()));
       else
-        TOPO_CUDA(launch_rap2_from_fine<double>(s->L[0].d, s->C2, s->x, lk.Ae, st));
+        TOPO_CUDA(launch_rap2_from_fine<double>(s->L[0].d, s->C2, s->x, lk.Ae, st,
+                                                s->C2_host.data()));
     } else if (s->h32) {
       if (f32)
         TOPO_CUDA((launch_rap_coarse<float, float>(s->L[k - 1].d, s->L[k - 1].Ae32, lk.Ae32, st)));
@@ -945,6 +948,10 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   // (Galerkin products of FP32 inputs) unless a build-time power iteration needs FP64 operators;
   // the coarsest matrix is still accumulated and factored in FP64.
   s->h32 = !arrow && s->prec == TOPO_MIXED && d->smoother == 0 && !d->omega_auto;
+  if (s->dim == 2) {
+    s->C_host = C;
+    s->C2_host = C2;
+  }
   std::vector<float> K0f(K0.begin(), K0.end()), C32(C.begin(), C.end());
   TOPO_TRY(s->alloc(&s->K0, ne * ne));
   TOPO_TRY(s->alloc(&s->K0f, ne * ne));

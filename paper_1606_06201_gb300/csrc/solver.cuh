@@ -24,6 +24,7 @@ struct topo_solver {
   double* K0 = nullptr;
   float* K0f = nullptr;
   double* C = nullptr;           // constant child matrices P_c^T K0 P_c
+  std::vector<double> C_host, C2_host;  // host copies of C and C2 (kernel-parameter tables)
   Q1Coef q1{};                   // butterfly coefficients of the 2D K0
   bool q1_ok = false;            // 2D and T^T Khat T reproduces K0: use the warp-sweep kernels
   double* x = nullptr;

@@ -331,9 +331,12 @@ cudaError_t launch_q1g_apply(int nx, int ny, int mode, const Q1Coef& coef, const
 // Hierarchy construction (kernels_rap.cu).
 // g, Dinv != nullptr: add the rank-one terms (P_c^T g_c)(P_c^T g_c)^T Dinv_c of Z.
 // T = double or float (arithmetic and storage); the rank-one terms g, Dinv need T = double.
+// Ch / C2h [host, FP64]: the same tables as C / C2; given in 2D, one thread per coarse element
+// takes them as kernel parameters (the same bits as the entry-parallel kernels).
 template <typename T>
 cudaError_t launch_rap_from_fine(const Dims& fine, const T* C, const T* x, T* Ac, cudaStream_t st,
-                                 const double* g = nullptr, const double* Dinv = nullptr);
+                                 const double* g = nullptr, const double* Dinv = nullptr,
+                                 const double* Ch = nullptr);
 // TI: stored type of the finer level's matrices; TO: arithmetic and stored type of the result
 // (double/double, float/float, float/double).
 template <typename TI, typename TO>
@@ -341,7 +344,7 @@ cudaError_t launch_rap_coarse(const Dims& fine, const TI* Af, TO* Ac, cudaStream
 // Second coarse level from the finest densities with the 4^dim composite matrices C2.
 template <typename T>
 cudaError_t launch_rap2_from_fine(const Dims& fine, const T* C2, const T* x, T* Ac,
-                                  cudaStream_t st);
+                                  cudaStream_t st, const double* C2h = nullptr);
 // Inverse diagonal of the first coarse level from the finest densities and the child matrices.
 cudaError_t launch_inv_diag_l1(const Dims& coarse1, const double* C, const double* xf,
                                const uint8_t* fixed, double* invd, cudaStream_t st);

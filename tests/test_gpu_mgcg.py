@@ -41,7 +41,7 @@ def test_apply_K_matches_assembled(shape, generic):
     np.testing.assert_allclose(y, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("shape", [(16, 8, 0, 3), (64, 32, 0, 4), (8, 4, 4, 3)])
+@pytest.mark.parametrize("shape", [(16, 8, 0, 3), (64, 32, 0, 4), (200, 48, 0, 4), (8, 4, 4, 3)])
 def test_galerkin_level_matrices_match_sparse_rap(shape):
     torch = torch_cuda()
     topo = topo_lib()
@@ -63,7 +63,7 @@ def test_galerkin_level_matrices_match_sparse_rap(shape):
         np.testing.assert_allclose(A, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("shape", [(64, 32, 0, 5), (8, 4, 4, 3)])
+@pytest.mark.parametrize("shape", [(64, 32, 0, 5), (200, 48, 0, 4), (8, 4, 4, 3)])
 @pytest.mark.parametrize("generic", [False, True])
 def test_fp32_hierarchy_matrices_match_sparse_rap(shape, generic):
     """Mixed solvers with fixed damping build the coarse matrices below the coarsest level in FP32
