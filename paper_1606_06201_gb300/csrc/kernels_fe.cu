@@ -177,11 +177,11 @@ __device__ __forceinline__ void apply_node(const Dims& d, long long node, const 
     } else if (MODE == 0) {
       out = acc[c];
     } else if (MODE == 1) {
-      out = vld<COH>(b + id) - acc[c];
+      out = node_out<1, T>(acc[c], T(0), vld<COH>(b + id), T(0), omega);
     } else if (MODE == 2 || MODE == 4) {
-      out = vin(id) + omega * invd[id] * (vld<COH>(b + id) - acc[c]);
+      out = node_out<2, T>(acc[c], vin(id), vld<COH>(b + id), invd[id], omega);
     } else {
-      out = omega * invd[id] * vld<COH>(b + id);
+      out = node_out<3, T>(T(0), T(0), vld<COH>(b + id), invd[id], omega);
     }
     y[id] = out;
   }

@@ -309,8 +309,9 @@ int tail_level(const topo_solver* s) {
   const int last = s->nlev - 1;
   for (int k = 1; k < last; ++k) {
     if (s->L[k].d.nodes() > kTailNodes || s->nlev - k > kTailMax) continue;
-    bool ok = true;
-    for (int j = k; j < last; ++j) ok = ok && Prec<TV>::Ae(s->L[j]) && Prec<TV>::invd(s->L[j]);
+    bool ok = true;  // (the fused kernel takes one damping for all its levels)
+    for (int j = k; j < last; ++j)
+      ok = ok && Prec<TV>::Ae(s->L[j]) && Prec<TV>::invd(s->L[j]) && !s->L[j].omega_dev;
     if (ok) return k;
   }
   return -1;

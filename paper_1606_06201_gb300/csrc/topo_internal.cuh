@@ -162,6 +162,18 @@ __device__ __forceinline__ void node_coords(long long node, int nnx, int nny, in
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
+// Output of one DOF row of the node-parallel operator kernels: mode 1 b - A v; modes 2 and 4 one
+// Jacobi sweep v + omega invd (b - A v); mode 3 the first sweep from zero omega invd b.  The
+// roundings are spelled out (no contraction left to the compiler), so that every kernel that
+// forms these rows gives the same bits.
+template <int MODE, typename T>
+__device__ __forceinline__ T node_out(T acc, T v, T b, T invd, T omega) {
+  if constexpr (MODE == 1) return b - acc;
+  else if constexpr (MODE == 2 || MODE == 4) return fma(mul_rn(omega, invd), b - acc, v);
+  else if constexpr (MODE == 3) return mul_rn(mul_rn(omega, invd), b);
+  else return acc;
+}
+
 // z_row = sum_k Ainv[row][k] b[k] by one warp: lane-strided FP64 sums, then a butterfly
 // (COH: b read from L2, for data written earlier in the same launch by other blocks).
 template <bool COH, typename T>

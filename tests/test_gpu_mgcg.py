@@ -274,6 +274,32 @@ def test_fused_deep_levels_give_identical_bits(precision, shape, nu, nrhs):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+def test_fused_levels_with_power_iteration_damping_give_identical_bits(precision):
+    """Per-level damping from the power iteration (omega folded into the inverse diagonals):
+    the fused kernels take each level's own damping, so fused and unfused V-cycles and solves
+    agree bit for bit."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny, levels = 256, 128, 6
+    fixed = W.clamp_xmin(nx, ny)
+    x = dev(torch, _x(nx, ny, 0, 38))
+    r = W.random_vector(fixed.size, 61, fixed)
+    f = W.normal_load(fixed, 71)
+    out = []
+    for fused in (False, True):
+        s = topo.Solver(nx, ny, fixed=fixed, levels=levels, precision=precision, omega_auto=True)
+        s.set_vcycle_fusion(fused)
+        s.set_density(x)
+        y = host(s.apply_vcycle(dev(torch, r)))
+        u, info = s.solve(dev(torch, f), tol=1e-9)
+        out.append((y, host(u), info.iterations))
+        s.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 def test_pair_arithmetic_outer_operator_reaches_tight_tolerances(precision):
     """The outer operator in float pairs (about 48 bits): solves to 1e-11 whose true residual, by
     the oracle's sparse matrix, is at that level; and the same iteration count (within one) and
