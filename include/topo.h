@@ -73,8 +73,10 @@ typedef struct {
                            (pre) / nu2 (post) on D^{-1} A_k over [lambda_k / 4, 1.05 lambda_k],
                            lambda_k from the power iteration (K systems only) */
   int omega_auto;       /* 1: per-level damping omega_k = min(omega, 4 / (3 lambda_k)) with
-                           lambda_k ~ lambda_max(D^{-1} A_k) from 15 power iterations at every
-                           hierarchy build (all levels of IP systems; levels >= 1 otherwise).
+                           lambda_k ~ lambda_max(D^{-1} A_k) from a power iteration at every
+                           hierarchy build: 15 steps from a fixed vector on the first build, 5
+                           steps from the previous build's vector afterwards (all levels of IP
+                           systems; levels >= 1 otherwise).
                            IP drivers always use it: the element rank-one terms of Z push
                            lambda_max(D^{-1} Z) well above the value for K(x). */
 } topo_solver_desc;
