@@ -51,8 +51,8 @@ typedef enum { TOPO_FP64 = 0, TOPO_MIXED = 1 } topo_precision;
 /* Solver description.  levels >= 1 (1 = coarsest level only: exact dense solve); every
  * coarsening halves nx, ny (, nz), which must stay integers.  The smoother is damped Jacobi
  * (Algorithm MG's opt(), Sec. 5.1: the paper names Gauss-Seidel only as an example) with nu1
- * pre- and nu2 post-sweeps and damping omega; the coarsest level is solved exactly (dense FP64
- * Cholesky).  precision TOPO_MIXED runs the V-cycle (smoother, transfers, coarse operators) in
+ * pre- and nu2 post-sweeps and damping omega; the coarsest level is solved exactly (an explicit
+ * FP64 inverse of the dense coarsest matrix, formed at every hierarchy build).  precision TOPO_MIXED runs the V-cycle (smoother, transfers, coarse operators) in
  * FP32 and keeps the CG recurrences, dot products, the outer operator and the coarsest solve
  * in FP64.  nrhs > 1 batches right-hand sides (vectors [nrhs][n], one CG per right-hand side). */
 typedef struct {
@@ -116,8 +116,9 @@ topo_status topo_set_graph_mode(topo_solver* s, int mode);
  * launch per sweep, residual and transfer).  On the finest level the first two sweeps from zero
  * are one kernel, and so are the prolongation with the first post-smoothing sweep; the levels
  * from the first one of at most 1024 nodes down to the coarsest run in one launch of a
- * thread-block cluster per right-hand side (where the device can run it).  Both settings give
- * the same bits.  Other systems ignore the setting. */
+ * thread-block cluster per right-hand side (where the device can run it).  2D IP systems: the
+ * first two sweeps of every coarse level in one kernel.  Both settings give the same bits.  3D
+ * and Chebyshev systems ignore the setting. */
 topo_status topo_set_vcycle_fusion(topo_solver* s, int on);
 /* Arithmetic of the outer operator q = K(x) p of Algorithm PCG on the 2D finest level of K
  * systems: 0 = FP64; 1 = pairs of FP32 values (hi + lo, about 48 significant bits, FP64 in and
