@@ -416,7 +416,10 @@ def main():
             "fine_smoothing_sweep": ("k_q1_fused<float,4>: first two Jacobi sweeps from zero, "
                                      "z = omega D^-1 b formed on the fly, diag from x",
                                      4.0 * m + 9.0 * n),
-            "fine_residual": ("k_q1_sweep<float,1,0>: r = b - K(x) z", 4.0 * m + 13.0 * n),
+            "fine_residual": (("k_q1_resrestrict<float>: b_c = P^T (b - K(x) z) in one pass, the "
+                               "residual not stored", 4.0 * m + 9.0 * n + 5.0 * nc)
+                              if kinds_run["kinds"] and not kinds_run["kinds"][3][1] else
+                              ("k_q1_sweep<float,1,0>: r = b - K(x) z", 4.0 * m + 13.0 * n)),
             "fine_restriction": ("k_restrict<2,float>: b_c = P^T r", 4.0 * n + 5.0 * nc),
             "fine_prolongation": ("k_q1_fused<float,5>: v = z + P z_c formed on the fly, then "
                                   "one Jacobi sweep", 4.0 * m + 13.0 * n + 4.0 * nc),

@@ -114,7 +114,8 @@ topo_status topo_set_stream(topo_solver* s, void* cuda_stream);
 topo_status topo_set_graph_mode(topo_solver* s, int mode);
 /* Fused kernels in Algorithm MG for 2D K systems with Jacobi smoothing (default on; off: one
  * launch per sweep, residual and transfer).  On the finest level the first two sweeps from zero
- * are one kernel, and so are the prolongation with the first post-smoothing sweep; the levels
+ * are one kernel, and so are the residual with the restriction, and the prolongation with the
+ * first post-smoothing sweep; the levels
  * from the first one of at most 1024 nodes down to the coarsest run in one launch of a
  * thread-block cluster per right-hand side (where the device can run it).  2D IP systems: the
  * first two sweeps of every coarse level in one kernel.  Both settings give the same bits.  3D
@@ -145,7 +146,8 @@ topo_status topo_get_profile(const topo_solver* s, double* operator_ms_total, lo
 /* The same for other parts of the iteration (kind 0 = the outer operator, as topo_get_profile).
  * Finest level of the V-cycle, in the V-cycle precision: 1 = the first smoothing kernel with a
  * matrix product (the fused first two sweeps, or the first sweep from z != 0), 2 = the residual
- * b - A z before restriction, 3 = the restriction P^T r, 4 = the prolongation and correction
+ * b - A z before restriction (with the restriction, where the V-cycle fuses the two), 3 = the
+ * restriction P^T r (count 0 where fused into kind 2), 4 = the prolongation and correction
  * z += P z_c (fused with the first post-smoothing sweep where the V-cycle fuses).  Spans of several
  * kernels: 5 = the whole V-cycle (preconditioner), 6 = its part on levels >= 1, 7 = its part on
  * levels >= 2 (coarsest solve included).  A kind that the solver's V-cycle does not run has

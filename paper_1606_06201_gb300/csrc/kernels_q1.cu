@@ -270,6 +270,165 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, int 
   }
 }
 
+// ---- Residual and restriction in one pass --------------------------------------------------
+// b_c = P^T (b - K(x) v) on the finest level: the residual rows of k_q1_sweep<T, 1, 0> (the same
+// arithmetic), never stored, are combined into the coarse right-hand side by the 9-point full
+// weighting in the order of k_restrict (per coarse node: fine rows 2J - 1, 2J, 2J + 1, and in
+// each row the columns 2I - 1, 2I, 2I + 1), so the coarse values are the same bits as those of
+// the two separate kernels.  A warp owns kRRCols coarse columns, I = kRRCols wc + 1 ..
+// kRRCols (wc + 1) (and I = 0 in the first warp), and a strip of coarse rows; its lanes cover the
+// fine columns 2 kRRCols wc - 1 .. 2 kRRCols wc + 30, residuals on lanes 1..30, so that each owned
+// 3-column stencil lies on them, and it walks the fine rows 2 J0 - 1 .. 2 J1 - 1 (the row below
+// the strip is recomputed).  Loads run two element rows ahead, as in k_q1_sweep.
+constexpr int kRRCols = 14;
+
+template <typename T>
+__global__ void __launch_bounds__(kQ1Warps * 32) k_q1_resrestrict(int nx, int ny, int crows,
+                                                                   Q1K<T> k,
+                                                                   const T* __restrict__ x,
+                                                                   const T* __restrict__ v,
+                                                                   const T* __restrict__ b,
+                                                                   T* __restrict__ bc,
+                                                                   const uint8_t* __restrict__ fixed,
+                                                                   const uint8_t* __restrict__ fixed_c,
+                                                                   const CgScalars* sc) {
+  pdl_prologue();
+  using V2 = typename Vec2<T>::type;
+  const int rhs = blockIdx.y;
+  if (sc && sc[rhs].done) return;
+  const long long n = 2LL * (nx + 1) * (ny + 1);
+  const int cnx = nx / 2, cny = ny / 2;
+  v += rhs * n;
+  b += rhs * n;
+  bc += rhs * 2LL * (cnx + 1) * (cny + 1);
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kQ1Warps + (threadIdx.x >> 5);
+  const int ncolw = (cnx + kRRCols - 1) / kRRCols;
+  const int nstrip = (cny + 1 + crows - 1) / crows;
+  const int wc = gw % ncolw, ws = gw / ncolw;
+  if (ws >= nstrip) return;
+  const int c = wc * 2 * kRRCols - 1 + lane;  // fine node column and element column of the lane
+  const bool col_ok = (c >= 0 && c <= nx);
+  const bool out_lane = (lane >= 1 && lane <= 30 && col_ok);
+  const bool el_col = (lane <= 30 && c >= 0 && c < nx);
+  const bool own = col_ok && (c & 1) == 0 && ((lane >= 3 && lane <= 2 * kRRCols + 1) ||
+                                              (wc == 0 && lane == 1));
+  const int I = c >> 1;
+  const int J0 = ws * crows, J1 = min(J0 + crows, cny + 1);
+  const int j0 = max(2 * J0 - 1, 0), j1 = min(2 * J1 - 1, ny) + 1;  // fine rows [j0, j1)
+  const V2* v2 = reinterpret_cast<const V2*>(v);
+  const V2* b2 = reinterpret_cast<const V2*>(b);
+  const long long rs = nx + 1;
+  V2 zero;
+  zero.x = T(0);
+  zero.y = T(0);
+  V2 pb = zero;
+  if (col_ok && j0 >= 1) pb = v2[c + rs * (j0 - 1)];
+  V2 pt_n = zero, pt_nn = zero, bb_n = zero, bb_nn = zero;
+  T xe_n = T(0), xe_nn = T(0);
+  uint16_t fx_n = 0, fx_nn = 0;
+  {
+    const int ey = j0 - 1;
+    if (col_ok && ey + 1 <= ny) pt_n = v2[c + rs * (ey + 1)];
+    if (el_col && ey >= 0 && ey < ny) xe_n = x[c + (long long)nx * ey];
+    if (ey + 1 < j1) {
+      if (col_ok && ey + 2 <= ny) pt_nn = v2[c + rs * (ey + 2)];
+      if (el_col && ey + 1 < ny) xe_nn = x[c + (long long)nx * (ey + 1)];
+      if (out_lane) {
+        const long long nn = c + rs * (ey + 1);
+        fx_nn = *reinterpret_cast<const uint16_t*>(fixed + 2 * nn);
+        bb_nn = b2[nn];
+      }
+    }
+  }
+  T cu = T(0), cv = T(0);
+  T ax = T(0), ay = T(0);  // the full-weighting sums of the coarse row in progress
+  for (int ey = j0 - 1; ey < j1; ++ey) {
+    const V2 pt = pt_n;
+    const T xe = xe_n;
+    const V2 bb = bb_n;
+    const uint16_t fx = fx_n;
+    pt_n = pt_nn;
+    xe_n = xe_nn;
+    bb_n = bb_nn;
+    fx_n = fx_nn;
+    pt_nn = zero;
+    xe_nn = T(0);
+    if (ey + 2 < j1) {
+      if (col_ok && ey + 3 <= ny) pt_nn = v2[c + rs * (ey + 3)];
+      if (el_col && ey + 2 < ny) xe_nn = x[c + (long long)nx * (ey + 2)];
+      if (out_lane) {
+        const long long nn = c + rs * (ey + 2);
+        fx_nn = *reinterpret_cast<const uint16_t*>(fixed + 2 * nn);
+        bb_nn = b2[nn];
+      }
+    }
+    const T pbr_u = shfl_dn(pb.x), pbr_v = shfl_dn(pb.y);
+    const T ptr_u = shfl_dn(pt.x), ptr_v = shfl_dn(pt.y);
+    T ru[4], rv[4];
+    {
+      const T uu[4] = {pb.x, pbr_u, ptr_u, pt.x};
+      const T vv[4] = {pb.y, pbr_v, ptr_v, pt.y};
+      q1_element<T>(k, xe, uu, vv, ru, rv);
+    }
+    const T l1u = shfl_up1(ru[1]), l1v = shfl_up1(rv[1]);
+    const T l2u = shfl_up1(ru[2]), l2v = shfl_up1(rv[2]);
+    if (ey >= j0) {  // residual of node row ey (warp-uniform), then its share of P^T r
+      V2 r = zero;
+      if (out_lane) {
+        const T qu = cu + ru[0] + l1u, qv = cv + rv[0] + l1v;
+        r.x = bb.x - qu;
+        r.y = bb.y - qv;
+        if (fx & 0xff) r.x = T(0);
+        if (fx >> 8) r.y = T(0);
+      }
+      const T rlx = shfl_up1(r.x), rly = shfl_up1(r.y);
+      const T rrx = shfl_dn(r.x), rry = shfl_dn(r.y);
+      // one fine row of the weighting, with the row weight wy (k_restrict's order)
+      auto row_terms = [&](T wy, T& sx, T& sy) {
+        if (c - 1 >= 0) {
+          const T w = wy * T(0.5);
+          sx = fma(w, rlx, sx);
+          sy = fma(w, rly, sy);
+        }
+        sx = fma(wy, r.x, sx);
+        sy = fma(wy, r.y, sy);
+        if (c + 1 <= nx) {
+          const T w = wy * T(0.5);
+          sx = fma(w, rrx, sx);
+          sy = fma(w, rry, sy);
+        }
+      };
+      auto write = [&](int J, T sx, T sy) {
+        const long long cid = 2LL * (I + (long long)(cnx + 1) * J);
+        V2 o;
+        o.x = fixed_c[cid] ? T(0) : sx;
+        o.y = fixed_c[cid + 1] ? T(0) : sy;
+        reinterpret_cast<V2*>(bc)[cid >> 1] = o;
+      };
+      if (own) {
+        if ((ey & 1) == 0) {  // fine row 2J: the middle row of coarse row J
+          const int J = ey >> 1;
+          row_terms(T(1), ax, ay);
+          if (ey == ny && J >= J0 && J < J1) write(J, ax, ay);
+        } else {  // fine row 2J + 1: the last row of coarse row J, the first of J + 1
+          const int J = ey >> 1;
+          if (J >= J0) {
+            row_terms(T(1) * T(0.5), ax, ay);
+            write(J, ax, ay);
+          }
+          ax = T(0);
+          ay = T(0);
+          row_terms(T(1) * T(0.5), ax, ay);
+        }
+      }
+    }
+    cu = ru[3] + l2u;
+    cv = rv[3] + l2v;
+    pb = pt;
+  }
+}
+
 // ---- Fused pairs of V-cycle steps on the finest level ----------------------------------------
 // MODE 4: the first two damped-Jacobi sweeps from zero, z = omega D^{-1} b then
 //         y = z + omega D^{-1} (b - K z), with z formed on the fly from b and x (no z pass).
@@ -938,6 +1097,32 @@ cudaError_t launch_q1_apply(int nx, int ny, int mode, const Q1Coef& coef, const 
   }
   return cudaGetLastError();
 }
+template <typename T>
+cudaError_t launch_q1_resrestrict(int nx, int ny, const Q1Coef& coef, const T* x, const T* v,
+                                  const T* b, T* bc, const uint8_t* fixed,
+                                  const uint8_t* fixed_c, int nrhs, const CgScalars* sc,
+                                  cudaStream_t st) {
+  const int cnx = nx / 2, cny = ny / 2;
+  const long long ncolw = (cnx + kRRCols - 1) / kRRCols;
+  const long long target = 152LL * 32;  // warps for about one per SM scheduler slot
+  long long crows = (ncolw * (cny + 1) + target - 1) / target;
+  if (crows < 1) crows = 1;
+  if (crows > kQ1MaxRows / 2) crows = kQ1MaxRows / 2;
+  const long long warps = ncolw * ((cny + 1 + crows - 1) / crows);
+  dim3 grid((unsigned)((warps + kQ1Warps - 1) / kQ1Warps), nrhs);
+  topo::launch(k_q1_resrestrict<T>, grid, kQ1Warps * 32, 0, st, nx, ny, (int)crows,
+               coef_cast<T>(coef), x, v, b, bc, fixed, fixed_c, sc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_q1_resrestrict<double>(int, int, const Q1Coef&, const double*,
+                                                   const double*, const double*, double*,
+                                                   const uint8_t*, const uint8_t*, int,
+                                                   const CgScalars*, cudaStream_t);
+template cudaError_t launch_q1_resrestrict<float>(int, int, const Q1Coef&, const float*,
+                                                  const float*, const float*, float*,
+                                                  const uint8_t*, const uint8_t*, int,
+                                                  const CgScalars*, cudaStream_t);
+
 template cudaError_t launch_q1_apply<double>(int, int, int, const Q1Coef&, const double*,
                                              const double*, const double*, double*, double,
                                              const uint8_t*, int, const CgScalars*, cudaStream_t);

@@ -429,13 +429,20 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
   } else {
     TOPO_CUDA(cudaMemsetAsync(cur, 0, sizeof(TV) * s->vlen(k) * nrhs, s->st));
   }
-  if (fine) TOPO_TRY(prof_mark(s, 2, 0));
-  TOPO_TRY(apply_level<TV>(s, k, 1, cur, b, oth, sc));
-  if (fine) TOPO_TRY(prof_mark(s, 2, 1));
   Level& lc = s->L[k + 1];
-  if (fine) TOPO_TRY(prof_mark(s, 3, 0));
-  TOPO_CUDA(launch_restrict<TV>(lv.d, oth, (TV*)lc.b, lc.fixed, nrhs, sc, s->st, s->arrow));
-  if (fine) TOPO_TRY(prof_mark(s, 3, 1));
+  if (fine_fused) {  // residual and restriction in one pass (the residual is not stored)
+    TOPO_TRY(prof_mark(s, 2, 0));
+    TOPO_CUDA(launch_q1_resrestrict<TV>(lv.d.nx, lv.d.ny, s->q1, Prec<TV>::x(s), cur, b,
+                                        (TV*)lc.b, lv.fixed, lc.fixed, nrhs, sc, s->st));
+    TOPO_TRY(prof_mark(s, 2, 1));
+  } else {
+    if (fine) TOPO_TRY(prof_mark(s, 2, 0));
+    TOPO_TRY(apply_level<TV>(s, k, 1, cur, b, oth, sc));
+    if (fine) TOPO_TRY(prof_mark(s, 2, 1));
+    if (fine) TOPO_TRY(prof_mark(s, 3, 0));
+    TOPO_CUDA(launch_restrict<TV>(lv.d, oth, (TV*)lc.b, lc.fixed, nrhs, sc, s->st, s->arrow));
+    if (fine) TOPO_TRY(prof_mark(s, 3, 1));
+  }
   TV* zc = nullptr;
   const int sub_kind = (k == 0) ? 6 : (k == 1 ? 7 : -1);  // levels >= 1, levels >= 2
   if (sub_kind > 0) TOPO_TRY(prof_mark(s, sub_kind, 0));

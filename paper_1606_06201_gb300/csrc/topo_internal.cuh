@@ -281,6 +281,14 @@ cudaError_t launch_element_energy(const Dims& d, const double* K0, const double*
                                   const double* lam, double* out, double scale, cudaStream_t st);
 
 // Finest-level 2D Q1 operator, warp-sweep kernels (kernels_q1.cu); same modes as launch_apply.
+// b_c = P^T (b - K(x) v) on the finest level in one pass (the residual is not stored): the same
+// bits as launch_q1_apply mode 1 followed by launch_restrict.  bc, fixed_c: the first coarse
+// level's right-hand sides [nrhs][n_c] and mask.
+template <typename T>
+cudaError_t launch_q1_resrestrict(int nx, int ny, const Q1Coef& coef, const T* x, const T* v,
+                                  const T* b, T* bc, const uint8_t* fixed,
+                                  const uint8_t* fixed_c, int nrhs, const CgScalars* sc,
+                                  cudaStream_t st);
 template <typename T>
 cudaError_t launch_q1_apply(int nx, int ny, int mode, const Q1Coef& coef, const T* x, const T* v,
                             const T* b, T* y, T omega, const uint8_t* fixed, int nrhs,

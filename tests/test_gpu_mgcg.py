@@ -346,10 +346,21 @@ def test_profiling_times_every_kernel_kind_and_keeps_results():
     s.set_profiling_mask((1 << len(topo.Solver.PROFILE_KINDS)) - 1)
     u2, info2 = s.solve(f, tol=1e-9)
     assert torch.equal(u0, u2) and info0.iterations == info2.iterations
+    fused_restriction = topo.Solver.PROFILE_KINDS.index("fine_restriction")
     for k in range(len(topo.Solver.PROFILE_KINDS)):
         ms, cnt = s.profile_kernel(k)
-        assert cnt == info2.iterations and ms > 0.0, (k, ms, cnt)
+        if k == fused_restriction:  # one kernel with the residual (timed as fine_residual)
+            assert cnt == 0, (k, ms, cnt)
+        else:
+            assert cnt == info2.iterations and ms > 0.0, (k, ms, cnt)
     assert s.profile() == s.profile_kernel(0)
+    s.set_vcycle_fusion(False)  # separate kernels: every kind timed
+    s.set_profiling_mask((1 << len(topo.Solver.PROFILE_KINDS)) - 1)  # (resets the sums)
+    u3, info3 = s.solve(f, tol=1e-9)
+    assert torch.equal(u0, u3) and info0.iterations == info3.iterations
+    for k in range(len(topo.Solver.PROFILE_KINDS)):
+        ms, cnt = s.profile_kernel(k)
+        assert cnt == info3.iterations and ms > 0.0, (k, ms, cnt)
     with pytest.raises(topo.TopoError):
         s.set_profiling_mask(1 << len(topo.Solver.PROFILE_KINDS))
     with pytest.raises(topo.TopoError):
