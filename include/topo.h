@@ -229,6 +229,9 @@ typedef struct {
   int max_newton;      /* Newton step budget */
   double cg_tol;       /* relative residual for the Z systems (Sec. 6.1 uses 1e-2) */
   double cg_tol_init;  /* relative residual of the initial K(x) u = f solve (<= 0: cg_tol) */
+  double cg_tol_factor; /* the Z systems of major iteration k (k barrier reductions so far) are
+                           solved to cg_tol * cg_tol_factor^k: 1 keeps cg_tol fixed, 0.5 is the
+                           "CG tol decreasing" variant of Sec. 9.1 (tab:IP); in (0, 1] */
 } topo_ip_opts;
 
 typedef struct {
@@ -255,7 +258,8 @@ topo_status topo_ip_init(topo_ip* ip, const topo_ip_opts* opts);
 topo_status topo_ip_step(topo_ip* ip, const topo_ip_opts* opts, topo_ip_info* info);
 /* init + steps until max(s, r) <= tau_IP or max_newton steps. */
 topo_status topo_ip_run(topo_ip* ip, const topo_ip_opts* opts, topo_ip_info* info);
-/* Checkpoint / resume: u [device, n], x, phi, psi [device, m], scal [host, 3] = lambda, s, r. */
+/* Checkpoint / resume: u [device, n], x, phi, psi [device, m], scal [host, 4] = lambda, s, r and
+ * the number of barrier reductions so far (as a double). */
 topo_status topo_ip_get_state(topo_ip* ip, double* u, double* x, double* phi, double* psi,
                               double* scal);
 topo_status topo_ip_set_state(topo_ip* ip, const double* u, const double* x, const double* phi,

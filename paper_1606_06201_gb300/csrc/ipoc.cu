@@ -237,8 +237,20 @@ topo_status topo_ip_set_vcycle_fusion(topo_ip* a, int on) {
   return topo_set_vcycle_fusion(a->Z, on);
 }
 
+// The options the IP driver cannot run with.
+topo_status check_ip_opts(const topo_ip_opts* o, const char* where) {
+  if (!(o->cg_tol > 0.0) || !(o->cg_tol_factor > 0.0 && o->cg_tol_factor <= 1.0) ||
+      !(o->sigma > 0.0 && o->sigma < 1.0)) {
+    topo::set_error(std::string(where) +
+                    ": cg_tol must be > 0, cg_tol_factor in (0, 1] and sigma in (0, 1)");
+    return TOPO_E_INVALID_ARG;
+  }
+  return TOPO_OK;
+}
+
 topo_status topo_ip_init(topo_ip* a, const topo_ip_opts* o) {
   if (!a || !o) return TOPO_E_INVALID_ARG;
+  TOPO_TRY(check_ip_opts(o, "topo_ip_init"));
   StreamGuard gd(a->Z);
   cudaStream_t st = a->Z->st;
   const double V = a->ip_host->V;
@@ -273,6 +285,7 @@ topo_status topo_ip_init(topo_ip* a, const topo_ip_opts* o) {
 
 topo_status topo_ip_step(topo_ip* a, const topo_ip_opts* o, topo_ip_info* info) {
   if (!a || !o) return TOPO_E_INVALID_ARG;
+  TOPO_TRY(check_ip_opts(o, "topo_ip_step"));
   if (a->done) {
     fill_ip_info(a, 0.0, info, TOPO_OK);
     return TOPO_OK;
@@ -285,7 +298,8 @@ topo_status topo_ip_step(topo_ip* a, const topo_ip_opts* o, topo_ip_info* info) 
   TOPO_CUDA(cudaMemcpyAsync(Z->x, a->x, sizeof(double) * a->m, cudaMemcpyDeviceToDevice, st));
   TOPO_TRY(topo::solver_build(Z));
   topo_solve_info si{};
-  topo_status ss = topo::solver_solve(Z, a->rhs, a->du, o->cg_tol, 0, &si);
+  const double tol = o->cg_tol * std::pow(o->cg_tol_factor, (double)a->ip_iters);
+  topo_status ss = topo::solver_solve(Z, a->rhs, a->du, tol, 0, &si);
   a->cg_iters += si.iterations;
   a->feval += 1;
   if (ss != TOPO_OK && ss != TOPO_E_NOT_CONVERGED) {
@@ -342,7 +356,8 @@ topo_status topo_ip_run(topo_ip* a, const topo_ip_opts* o, topo_ip_info* info) {
   return st;
 }
 
-// State for checkpointing: u [n], x, phi, psi [m] device; scal[0..2] = lambda, s, r (host).
+// State for checkpointing: u [n], x, phi, psi [m] device; scal[0..3] = lambda, s, r and the
+// barrier reductions so far (host).
 topo_status topo_ip_get_state(topo_ip* a, double* u, double* x, double* phi, double* psi,
                               double* scal) {
   if (!a || !u || !x || !phi || !psi || !scal) return TOPO_E_INVALID_ARG;
@@ -356,6 +371,7 @@ topo_status topo_ip_get_state(topo_ip* a, double* u, double* x, double* phi, dou
   scal[0] = a->ip_host->lam;
   scal[1] = a->ip_host->s;
   scal[2] = a->ip_host->r;
+  scal[3] = (double)a->ip_iters;
   return TOPO_OK;
 }
 
@@ -372,6 +388,7 @@ topo_status topo_ip_set_state(topo_ip* a, const double* u, const double* x, cons
   a->ip_host->lam = scal[0];
   a->ip_host->s = scal[1];
   a->ip_host->r = scal[2];
+  a->ip_iters = (int)scal[3];
   TOPO_CUDA(cudaMemcpyAsync(a->ip, a->ip_host, sizeof(IpScalars), cudaMemcpyHostToDevice, st));
   TOPO_CUDA(cudaStreamSynchronize(st));
   a->done = false;

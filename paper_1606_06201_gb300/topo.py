@@ -42,7 +42,8 @@ class IpOpts(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("tau_nwt", ctypes.c_double),
                 ("tau_ip", ctypes.c_double), ("frac", ctypes.c_double),
                 ("step_x_only", ctypes.c_int), ("max_newton", ctypes.c_int),
-                ("cg_tol", ctypes.c_double), ("cg_tol_init", ctypes.c_double)]
+                ("cg_tol", ctypes.c_double), ("cg_tol_init", ctypes.c_double),
+                ("cg_tol_factor", ctypes.c_double)]
 
 
 class IpInfo(ctypes.Structure):
@@ -178,10 +179,12 @@ def _desc(nx, ny, nz, fixed, levels, precision, nu1, nu2, omega, max_iter, nrhs,
 
 
 def ip_options(sigma=0.2, tau_nwt=0.1, tau_ip=1e-8, frac=0.9, step_x_only=False, max_newton=500,
-               cg_tol=1e-8, cg_tol_init=None):
-    """Sec. 3 defaults; cg_tol is the relative residual of every Z solve."""
+               cg_tol=1e-8, cg_tol_init=None, cg_tol_factor=1.0):
+    """Sec. 3 defaults; cg_tol is the relative residual of the Z solves of the first major
+    iteration, multiplied by cg_tol_factor at every barrier reduction (Sec. 9.1: 1e-2 with factor
+    1 or 0.5)."""
     return IpOpts(sigma, tau_nwt, tau_ip, frac, int(step_x_only), max_newton, cg_tol,
-                  cg_tol if cg_tol_init is None else cg_tol_init)
+                  cg_tol if cg_tol_init is None else cg_tol_init, cg_tol_factor)
 
 
 def oc_options(variant=OC_AOC, q=0.5, xlow=1e-6, lam_hi=1e4, tau_lambda=1e-11, tau_oc=1e-5,
@@ -254,13 +257,14 @@ class IP:
         _check(_lib.topo_ip_set_vcycle_fusion(self._h, int(bool(on))), "topo_ip_set_vcycle_fusion")
 
     def state(self):
-        """(u, x, phi, psi, scal, pw): the iterate, scal = (lambda, s, r) on the host, and pw the
+        """(u, x, phi, psi, scal, pw): the iterate, scal = (lambda, s, r, barrier reductions so
+        far) on the host, and pw the
         augmented solver's power-iteration vectors with a trailing 1.0 when the next build starts
         from them (0.0: from the fixed start vector)."""
         import torch
         u = torch.empty(self.n, dtype=torch.float64, device="cuda")
         x, phi, psi = (torch.empty(self.m, dtype=torch.float64, device="cuda") for _ in range(3))
-        scal = np.zeros(3)
+        scal = np.zeros(4)
         _check(_lib.topo_ip_get_state(self._h, _ptr(u), _ptr(x), _ptr(phi), _ptr(psi),
                                       scal.ctypes.data_as(_vp)), "topo_ip_get_state")
         ln = ctypes.c_longlong(0)

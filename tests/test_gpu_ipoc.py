@@ -116,6 +116,51 @@ def test_ip_fused_coarse_sweeps_give_identical_bits(precision):
         np.testing.assert_array_equal(g_, r_)
 
 
+def test_inexact_newton_settings_of_tab_ip():
+    """Sec. 9.1 (tab:IP) on the square cantilever of Example 1 with 6 refinements (64 x 64): Z
+    systems solved to 1e-10 ("exact"), to a fixed 1e-2, and to 1e-2 halved at every barrier
+    reduction.  As in the paper at tau_IP = 1e-8: all three need the same 12 major iterations and
+    about the same Newton steps; the fixed tolerance needs the fewest CG iterations, the
+    decreasing one more, the exact one most; the solutions agree (x_min of the same order)."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    cfg = W.cantilever_2d(64, 64, 0.5)
+    f = dev(torch, cfg["f"])
+    res = {}
+    for name, tol, fac in (("exact", 1e-10, 1.0), ("fixed", 1e-2, 1.0), ("decreasing", 1e-2, 0.5)):
+        ip = topo.IP(64, 64, fixed=cfg["fixed"], f=f, V=cfg["V"], xbar=1.0, levels=4,
+                     precision=topo.MIXED)
+        info = ip.run(topo.ip_options(cg_tol=tol, cg_tol_factor=fac, max_newton=500))
+        u, x = ip.state()[:2]
+        res[name] = (info, float(cfg["f"] @ host(u)), host(x))
+        ip.close()
+    ex, fx, dc = res["exact"][0], res["fixed"][0], res["decreasing"][0]
+    assert ex.done and fx.done and dc.done
+    assert ex.ip_iters == fx.ip_iters == dc.ip_iters == 12
+    assert fx.newton <= ex.newton + 5 and dc.newton <= ex.newton + 2
+    assert fx.cg_iters < dc.cg_iters < ex.cg_iters
+    c_ex = res["exact"][1]
+    assert abs(res["fixed"][1] - c_ex) <= 1e-4 * c_ex
+    assert abs(res["decreasing"][1] - c_ex) <= 1e-6 * c_ex
+    x_ex = res["exact"][2]
+    assert np.max(np.abs(res["fixed"][2] - x_ex)) <= 0.05
+    assert np.max(np.abs(res["decreasing"][2] - x_ex)) <= 1e-3
+    for name in ("fixed", "decreasing"):
+        assert 0.5 * x_ex.min() <= res[name][2].min() <= 2.0 * x_ex.min()
+
+
+def test_ip_rejects_bad_tolerance_options():
+    torch = torch_cuda()
+    topo = topo_lib()
+    cfg, _ = _problem(16, 8)
+    ip = topo.IP(16, 8, fixed=cfg["fixed"], f=dev(torch, cfg["f"]), V=cfg["V"], xbar=1.0, levels=2)
+    for kw in (dict(cg_tol_factor=0.0), dict(cg_tol_factor=1.5), dict(cg_tol=0.0)):
+        with pytest.raises(topo.TopoError) as e:
+            ip.init(topo.ip_options(**kw))
+        assert e.value.status == topo.E_INVALID_ARG
+    ip.close()
+
+
 def test_ip_rejects_infeasible_volume():
     torch = torch_cuda()
     topo = topo_lib()
