@@ -8,6 +8,8 @@
 // identity on components) and  P^T A P = sum_E L_E^T ( sum_{c in E} P_c^T A_c P_c ) L_E.
 // For the first coarsening A_c = x_c K0, so sum_c x_c (P_c^T K0 P_c) with four (eight) constant
 // matrices C_c = P_c^T K0 P_c prepared on the host.
+#include <type_traits>
+
 #include "topo_internal.cuh"
 
 namespace topo {
@@ -204,6 +206,15 @@ __host__ __device__ constexpr float w2c(int c, int a, int A) {
 }
 
 constexpr int kRapElemThreads = 128;
+
+// One thread per coarse element pays where its outputs are FP32, or where the coarse level has
+// enough elements to fill the GPU; FP64 outputs of a small level (a few thousand elements or
+// fewer: the coarsest levels, the small IP hierarchies) are FP64-bound and want one thread per
+// output entry.
+template <typename TO>
+bool rap_elem_parallel(long long mc) {
+  return std::is_same<TO, float>::value || mc >= 152LL * kRapElemThreads;
+}
 
 // First coarse level (k_rap_from_fine, 2D): A_E = sum_c x_c C_c (+ rank-one terms of Z).
 template <typename T>
@@ -627,41 +638,49 @@ __global__ void __launch_bounds__(kBg * 8) k_bgj_pivot(int npad, int K, const do
                                                        const double* __restrict__ a0,
                                                        double* __restrict__ P, int* info) {
   pdl_prologue();
-  __shared__ double S[kBg][kBg + 1];
-  __shared__ double piv;
-  __shared__ int bad;
+  // Two copies of the tile (step k reads one and writes the other) and the pivot reciprocal of
+  // each step, formed by the thread that writes the next pivot entry: one barrier per step.
+  __shared__ double S[2][kBg][kBg + 1];
+  __shared__ double D0[kBg];
+  __shared__ double rp_s[2];
+  __shared__ int bad_s[2];
   const int tid = threadIdx.x;
   const long long base = (long long)K * kBg;
   for (int t = tid; t < kBg * kBg; t += blockDim.x)
-    S[t / kBg][t % kBg] = W[(base + t / kBg) * npad + base + t % kBg];
-  if (tid == 0) bad = 0;
+    S[0][t / kBg][t % kBg] = W[(base + t / kBg) * npad + base + t % kBg];
+  if (tid < kBg) D0[tid] = a0[base + tid];
   __syncthreads();
+  // pivot k: floored at kPivotFloor times the original diagonal (a non-positive original
+  // diagonal or a non-finite entry marks the matrix as not positive definite).  Slot k & 1 is
+  // written during step k - 1 and read after its barrier; step k - 1 read the other slot.
+  auto pivot = [&](int k, double akk) {
+    const double d0 = D0[k];
+    bad_s[k & 1] = (!(d0 > 0.0) || !isfinite(akk)) ? 1 : 0;
+    rp_s[k & 1] = 1.0 / fmax(akk, kPivotFloor * d0);
+  };
+  if (tid == 0) pivot(0, S[0][0][0]);
+  __syncthreads();
+  int cur = 0;
+  bool bad = false;
   for (int k = 0; k < kBg; ++k) {
-    if (tid == 0) {
-      const double akk = S[k][k];
-      const double d0 = a0[base + k];
-      if (!(d0 > 0.0) || !isfinite(akk)) bad = 1;
-      piv = fmax(akk, kPivotFloor * d0);
+    if (bad_s[k & 1]) {  // the same value in every thread
+      bad = true;
+      break;
     }
-    __syncthreads();
-    if (bad) break;
-    const double rp = 1.0 / piv;
-    double nv[4];
+    const double rp = rp_s[k & 1];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int t = tid + r * blockDim.x;
       const int i = t / kBg, j = t % kBg;
-      const double aij = S[i][j];
-      if (i == k) nv[r] = (j == k) ? rp : aij * rp;
-      else if (j == k) nv[r] = -aij * rp;
-      else nv[r] = fma(-S[i][k] * rp, S[k][j], aij);
+      const double aij = S[cur][i][j];
+      double nv;
+      if (i == k) nv = (j == k) ? rp : aij * rp;
+      else if (j == k) nv = -aij * rp;
+      else nv = fma(-S[cur][i][k] * rp, S[cur][k][j], aij);
+      S[cur ^ 1][i][j] = nv;
+      if (k + 1 < kBg && i == k + 1 && j == k + 1) pivot(k + 1, nv);
     }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int t = tid + r * blockDim.x;
-      S[t / kBg][t % kBg] = nv[r];
-    }
+    cur ^= 1;
     __syncthreads();
   }
   if (bad) {
@@ -672,7 +691,7 @@ __global__ void __launch_bounds__(kBg * 8) k_bgj_pivot(int npad, int K, const do
     }
     return;
   }
-  for (int t = tid; t < kBg * kBg; t += blockDim.x) P[t] = S[t / kBg][t % kBg];
+  for (int t = tid; t < kBg * kBg; t += blockDim.x) P[t] = S[cur][t / kBg][t % kBg];
 }
 
 // C = X Y for kBg x kBg tiles in shared memory; each of the kBg * 8 threads forms 4 outputs.
@@ -803,7 +822,7 @@ cudaError_t launch_rap_from_fine(const Dims& fine, const T* C, const T* x, T* Ac
   const int ne = fine.dim == 2 ? 8 : 24;
   const long long mc = fine.elems() / (fine.dim == 2 ? 4 : 8);
   const long long total = mc * ne * ne;
-  if (fine.dim == 2 && Ch) {
+  if (fine.dim == 2 && Ch && rap_elem_parallel<T>(mc)) {
     ConstTable<T, 256> tab;
     for (int i = 0; i < 256; ++i) tab.v[i] = (T)Ch[i];
     topo::launch(k_rap1_elem2d<T>, (unsigned)((mc + kRapElemThreads - 1) / kRapElemThreads),
@@ -827,7 +846,7 @@ cudaError_t launch_rap2_from_fine(const Dims& fine, const T* C2, const T* x, T* 
   const int ne = fine.dim == 2 ? 8 : 24;
   const long long mc = fine.elems() / (fine.dim == 2 ? 16 : 64);
   const long long total = mc * ne * ne;
-  if (fine.dim == 2 && C2h) {
+  if (fine.dim == 2 && C2h && rap_elem_parallel<T>(mc)) {
     ConstTable<T, 1024> tab;
     for (int i = 0; i < 1024; ++i) tab.v[i] = (T)C2h[i];
     topo::launch(k_rap2_elem2d<T>, (unsigned)((mc + kRapElemThreads - 1) / kRapElemThreads),
@@ -857,10 +876,12 @@ cudaError_t launch_rap_coarse(const Dims& fine, const TI* Af, TO* Ac, cudaStream
   const int ne = fine.dim == 2 ? 8 : 24;
   const long long mc = fine.elems() / (fine.dim == 2 ? 4 : 8);
   const long long total = mc * ne * ne;
-  if (fine.dim == 2)
+  if (fine.dim == 2 && rap_elem_parallel<TO>(mc))
     topo::launch(k_rap_coarse_elem2d<TI, TO>,
                  (unsigned)((mc + kRapElemThreads - 1) / kRapElemThreads), kRapElemThreads, 0, st,
                  fine, Af, Ac);
+  else if (fine.dim == 2)
+    topo::launch(k_rap_coarse<2, TI, TO>, blocks_for(total), kThreads, 0, st, fine, Af, Ac);
   else
     topo::launch(k_rap_coarse<3, TI, TO>, blocks_for(total), kThreads, 0, st, fine, Af, Ac);
   return cudaGetLastError();

@@ -63,6 +63,33 @@ def test_galerkin_level_matrices_match_sparse_rap(shape):
         np.testing.assert_allclose(A, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
 
 
+def test_galerkin_level_matrices_large_2d_fp64():
+    """FP64 levels of a 512 x 256 hierarchy, where the first coarse level (32768 elements) is
+    built with one thread per coarse element and the deeper ones (8192 elements and fewer) with
+    one per entry: the assembled operators against the oracle's sparse P^T A P, compared as
+    sparse matrices."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny, levels = 512, 256, 5
+    fixed = W.clamp_xmin(nx, ny)
+    x = _x(nx, ny, 0, 16)
+    s = topo.Solver(nx, ny, fixed=fixed, levels=levels)
+    s.set_density(dev(torch, x))
+    levs, _, _, _ = oracle_hierarchy(nx, ny, 0, x, fixed, levels)
+    from oracle.mg import coarse_fixed
+    g = fe.Grid(nx, ny)
+    fx = fixed.astype(bool)
+    for k in range(1, levels):
+        g, fx = coarse_fixed(g, fx)
+        free = fe.free_dofs(fx)
+        A = fe.assemble_elementwise(g, s.level_matrices(k))[free][:, free].tocsr()
+        ref = levs[k].A.tocsr()
+        diff = (A - ref).tocoo()
+        scale = np.abs(ref.data).max()
+        assert diff.nnz == 0 or np.abs(diff.data).max() <= 1e-13 * scale, k
+    s.close()
+
+
 @pytest.mark.parametrize("shape", [(64, 32, 0, 5), (200, 48, 0, 4), (8, 4, 4, 3)])
 @pytest.mark.parametrize("generic", [False, True])
 def test_fp32_hierarchy_matrices_match_sparse_rap(shape, generic):
