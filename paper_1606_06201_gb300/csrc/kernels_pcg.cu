@@ -66,6 +66,28 @@ __device__ bool last_block_sums(const double (&part)[NV], double* partials, unsi
 }
 
 // r = A z0 - b (use_x0) or r = -b, z = 0; ||b||, ||r|| -> initial scalars and stop test.
+// CG scalars at the start: ||b||, r^T r and the stop test of Algorithm PCG on them.
+__device__ __forceinline__ CgScalars cg_start_scalars(double bb, double rr, double tol,
+                                                      int max_iter) {
+  CgScalars S = {};
+  S.bnorm = sqrt(bb);
+  S.rr = rr;
+  S.rel = S.bnorm > 0.0 ? sqrt(rr) / S.bnorm : 0.0;
+  S.iter = 0;
+  S.status = TOPO_OK;
+  if (!isfinite(S.rel)) {
+    S.status = TOPO_E_BREAKDOWN;
+    S.done = 1;
+  } else {
+    S.done = (S.bnorm == 0.0 || S.rel <= tol) ? 1 : 0;
+    if (!S.done && max_iter <= 0) {
+      S.done = 1;
+      S.status = TOPO_E_NOT_CONVERGED;
+    }
+  }
+  return S;
+}
+
 __global__ void __launch_bounds__(kThreads) k_cg_init(long long n, const double* __restrict__ b,
                                                       double* __restrict__ z,
                                                       double* __restrict__ r,
@@ -90,25 +112,41 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(long long n, const double*
   }
   double tot[2];
   if (!last_block_sums<2>(part, partials, counters, rhs, tot)) return;
-  if (threadIdx.x == 0) {
-    CgScalars S = {};
-    S.bnorm = sqrt(tot[0]);
-    S.rr = tot[1];
-    S.rel = S.bnorm > 0.0 ? sqrt(tot[1]) / S.bnorm : 0.0;
-    S.iter = 0;
-    S.status = TOPO_OK;
-    if (!isfinite(S.rel)) {
-      S.status = TOPO_E_BREAKDOWN;
-      S.done = 1;
-    } else {
-      S.done = (S.bnorm == 0.0 || S.rel <= tol) ? 1 : 0;
-      if (!S.done && max_iter <= 0) {
-        S.done = 1;
-        S.status = TOPO_E_NOT_CONVERGED;
-      }
-    }
-    sc[rhs] = S;
+  if (threadIdx.x == 0) sc[rhs] = cg_start_scalars(tot[0], tot[1], tol, max_iter);
+}
+
+// The same from the caller's right-hand side with zero start (use_x0 = 0) in one pass: b masked
+// on fixed DOFs (index < n_mask), z = 0, r = -b, and the FP32 copy of r for the V-cycle (rv, or
+// none): the values of k_mask_copy, k_cg_init and k_d2f in sequence.
+template <typename TV>
+__global__ void __launch_bounds__(kThreads) k_cg_init_zero(long long n, long long n_mask,
+                                                           const double* __restrict__ b,
+                                                           const uint8_t* __restrict__ fixed,
+                                                           double* __restrict__ z,
+                                                           double* __restrict__ r,
+                                                           TV* __restrict__ rv, double* partials,
+                                                           unsigned* counters, CgScalars* sc,
+                                                           double tol, int max_iter) {
+  pdl_prologue();
+  const int rhs = blockIdx.y;
+  b += rhs * n;
+  z += rhs * n;
+  r += rhs * n;
+  if (rv) rv += rhs * n;
+  double part[2] = {0.0, 0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double bi = (i < n_mask && fixed[i]) ? 0.0 : b[i];
+    const double ri = -bi;
+    z[i] = 0.0;
+    r[i] = ri;
+    if (rv) rv[i] = (TV)ri;
+    part[0] = fma(bi, bi, part[0]);
+    part[1] = fma(ri, ri, part[1]);
   }
+  double tot[2];
+  if (!last_block_sums<2>(part, partials, counters, rhs, tot)) return;
+  if (threadIdx.x == 0) sc[rhs] = cg_start_scalars(tot[0], tot[1], tol, max_iter);
 }
 
 // p = -y (first direction), y_old = y, and r^T y.
@@ -444,6 +482,23 @@ cudaError_t launch_cg_init(long long n, int nrhs, const double* b, double* z, do
                                                             counters, sc, tol, max_iter);
   return cudaGetLastError();
 }
+
+template <typename TV>
+cudaError_t launch_cg_init_zero(long long n, long long n_mask, int nrhs, const double* b,
+                                const uint8_t* fixed, double* z, double* r, TV* rv,
+                                double* partials, unsigned* counters, CgScalars* sc, double tol,
+                                int max_iter, cudaStream_t st) {
+  topo::launch(k_cg_init_zero<TV>, dim3(red_blocks(n), nrhs), kThreads, 0, st, n, n_mask, b, fixed,
+               z, r, rv, partials, counters, sc, tol, max_iter);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cg_init_zero<float>(long long, long long, int, const double*,
+                                                const uint8_t*, double*, double*, float*, double*,
+                                                unsigned*, CgScalars*, double, int, cudaStream_t);
+template cudaError_t launch_cg_init_zero<double>(long long, long long, int, const double*,
+                                                 const uint8_t*, double*, double*, double*,
+                                                 double*, unsigned*, CgScalars*, double, int,
+                                                 cudaStream_t);
 
 template <typename TV>
 cudaError_t launch_cg_start_p(long long n, int nrhs, const double* r, const TV* y, double* p,

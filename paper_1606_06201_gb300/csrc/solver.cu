@@ -646,15 +646,13 @@ template <typename TV>
 topo_status cg_setup(topo_solver* s, int use_x0, double tol, int max_iter) {
   const long long n = s->ncg();
   const int nrhs = s->nrhs;
-  const double* Az = nullptr;
-  if (use_x0) {
+  if (use_x0) {  // (from z = 0 the start vectors come from launch_cg_init_zero before the graph)
     TOPO_TRY(apply_level<double>(s, 0, 0, s->z, nullptr, s->q, nullptr));
-    Az = s->q;
+    TOPO_CUDA(launch_cg_init(n, nrhs, s->bbuf, s->z, s->r, s->q, use_x0, s->partials,
+                             s->counters, s->sc, tol, max_iter, s->st));
+    if (!std::is_same<TV, double>::value)
+      TOPO_CUDA(launch_convert_d2f(s->r, (float*)s->rv, n * nrhs, s->st));
   }
-  TOPO_CUDA(launch_cg_init(n, nrhs, s->bbuf, s->z, s->r, Az, use_x0, s->partials, s->counters,
-                           s->sc, tol, max_iter, s->st));
-  if (!std::is_same<TV, double>::value)
-    TOPO_CUDA(launch_convert_d2f(s->r, (float*)s->rv, n * nrhs, s->st));
   void* y = nullptr;
   TOPO_TRY(precondition<TV>(s, s->sc, &y));
   TOPO_CUDA(launch_cg_start_p<TV>(n, nrhs, s->r, (const TV*)y, s->p, (TV*)s->yold,
@@ -695,8 +693,16 @@ topo_status solve_impl(topo_solver* s, const double* b, double* u, double tol, i
   }
   TOPO_CUDA(cudaEventRecord(s->ev_t0, s->st));
   // entries on fixed DOFs are ignored: the eliminated system has no equations there
-  TOPO_CUDA(launch_mask_copy(n, s->L[0].n, nrhs, b, s->bbuf, s->L[0].fixed, s->st));
-  if (use_x0) TOPO_CUDA(launch_mask_copy(n, s->L[0].n, nrhs, u, s->z, s->L[0].fixed, s->st));
+  if (use_x0) {
+    TOPO_CUDA(launch_mask_copy(n, s->L[0].n, nrhs, b, s->bbuf, s->L[0].fixed, s->st));
+    TOPO_CUDA(launch_mask_copy(n, s->L[0].n, nrhs, u, s->z, s->L[0].fixed, s->st));
+    s->launches += 2;
+  } else {
+    TOPO_CUDA(launch_cg_init_zero<TV>(n, s->L[0].n, nrhs, b, s->L[0].fixed, s->z, s->r,
+                                      std::is_same<TV, double>::value ? nullptr : (TV*)s->rv,
+                                      s->partials, s->counters, s->sc, tol, max_iter, s->st));
+    s->launches += 1;
+  }
   TOPO_TRY(launch_graph(s, s->setup[ux], s->setup_kernels[ux]));
   if (use_loop && !s->no_loop) {
     TOPO_CUDA(cudaGraphLaunch(s->loop, s->st));

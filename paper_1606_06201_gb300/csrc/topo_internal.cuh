@@ -395,6 +395,13 @@ cudaError_t launch_convert_f2d(const float* a, double* b, long long n, cudaStrea
 cudaError_t launch_check_positive(const double* x, long long m, int* flag, cudaStream_t st);
 
 // CG vector kernels (kernels_pcg.cu).
+// z = 0, r = -b (b masked on the fixed DOFs below n_mask), rv = (TV) r (rv may be null) and the
+// start scalars, in one pass over the caller's b.
+template <typename TV>
+cudaError_t launch_cg_init_zero(long long n, long long n_mask, int nrhs, const double* b,
+                                const uint8_t* fixed, double* z, double* r, TV* rv,
+                                double* partials, unsigned* counters, CgScalars* sc, double tol,
+                                int max_iter, cudaStream_t st);
 cudaError_t launch_cg_init(long long n, int nrhs, const double* b, double* z, double* r,
                            const double* Az, int use_x0, double* partials, unsigned* counters,
                            CgScalars* sc, double tol, int max_iter, cudaStream_t st);
