@@ -693,6 +693,277 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_vcycle_tail(const __grid_co
   }
 }
 
+// ---- Deep levels of the 2D V-cycle in one block's shared memory ----------------------------
+// The cluster form above spends most of its time at the cluster barrier (a phase costs about as
+// much as a launch).  From the first level of at most kTailNodes nodes down, the element matrices,
+// inverse diagonals, masks and vectors of all the fused levels fit in the shared memory of one
+// block (about 185 KB for the 32 x 16, 16 x 8 and 8 x 4 levels in FP32).  One block per
+// right-hand side copies them in once per V-cycle and runs every phase on shared memory with
+// __syncthreads between phases; only the coarsest inverse is read from global memory.  The
+// per-node arithmetic and its order are those of the unfused kernels (node_apply's coarse 2D
+// branch, node_out, restrict_node, prolong_node, dense_row_dot), so the bits are the same.
+template <typename T>
+struct SmVec {
+  const T* v;
+  __device__ __forceinline__ T operator()(long long i) const { return v[i]; }
+};
+template <typename T>
+struct SmJac0 {  // omega invd b, as VJac0 forms it
+  const T* b;
+  const T* invd;
+  const uint8_t* fixed;
+  T omega;
+  __device__ __forceinline__ T operator()(long long i) const {
+    return fixed[i] ? T(0) : mul_rn(mul_rn(omega, invd[i]), b[i]);
+  }
+};
+
+// 16-byte asynchronous copy global -> shared (no register staging; the thread waits for its own
+// copies with cp_async_wait_all, a hardware wait).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+template <int MODE, typename T, typename VIn>
+__device__ __forceinline__ void sm_apply(const Dims& d, int node, const T* M, const VIn& vin,
+                                         const T* B, const T* D, const uint8_t* F, T* Y,
+                                         T omega) {
+  const int nnx = d.nx + 1;
+  const int m = d.nx * d.ny;
+  const int i = node % nnx, j = node / nnx;
+  T acc[2] = {T(0), T(0)};
+  if (MODE != 3) {
+    T a[4][16], ve[4][8];
+    bool ok[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int dx = s & 1, dy = s >> 1;
+      const int ex = i - 1 + dx, ey = j - 1 + dy;
+      ok[s] = ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny;
+      const int loc = loc_of(1 - dx, 1 - dy, 0);
+      const int e = ok[s] ? ex + d.nx * ey : 0;
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[s][c * 8 + q] = M[((loc * 2 + c) * 8 + q) * m + e];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int nid = ok[s] ? (ex + loc_ox(b)) + nnx * (ey + loc_oy(b)) : 0;
+        ve[s][2 * b] = vin(2 * nid);
+        ve[s][2 * b + 1] = vin(2 * nid + 1);
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      if (!ok[s]) continue;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        T t = T(0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t = fma(a[s][c * 8 + q], ve[s][q], t);
+        acc[c] += t;
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int id = 2 * node + c;
+    T out;
+    if (F[id]) out = T(0);
+    else if (MODE == 1) out = node_out<1, T>(acc[c], T(0), B[id], T(0), omega);
+    else if (MODE == 2 || MODE == 4) out = node_out<2, T>(acc[c], vin(id), B[id], D[id], omega);
+    else out = node_out<3, T>(T(0), T(0), B[id], D[id], omega);
+    Y[id] = out;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void sm_restrict(const Dims& df, const Dims& dc, int node, const T* rf,
+                                            T* rc, const uint8_t* fixed_c) {
+  const int cnx = dc.nx + 1;
+  const int I = node % cnx, J = node / cnx;
+  T acc[2] = {T(0), T(0)};
+  for (int oy = -1; oy <= 1; ++oy) {
+    const int fj = 2 * J + oy;
+    if (fj < 0 || fj > df.ny) continue;
+    const T wy = (oy == 0) ? T(1) : T(1) * T(0.5);
+    for (int ox = -1; ox <= 1; ++ox) {
+      const int fi = 2 * I + ox;
+      if (fi < 0 || fi > df.nx) continue;
+      const T w = (ox == 0) ? wy : wy * T(0.5);
+      const int fid = fi + (df.nx + 1) * fj;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) acc[c] = fma(w, rf[2 * fid + c], acc[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 2; ++c) rc[2 * node + c] = fixed_c[2 * node + c] ? T(0) : acc[c];
+}
+
+template <typename T>
+__device__ __forceinline__ void sm_prolong(const Dims& df, const Dims& dc, int node, const T* zc,
+                                           T* zf, const uint8_t* fixed_f) {
+  const int fnx = df.nx + 1, cnx = dc.nx + 1;
+  const int i = node % fnx, j = node / fnx;
+  T acc[2] = {T(0), T(0)};
+  const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1;
+  const T wxh = (i & 1) ? T(0.5) : T(1);
+  const T wyh = (j & 1) ? T(0.5) : T(1);
+  const T wzh = T(1);
+  const int nyi = (j & 1) ? 2 : 1, nxi = (i & 1) ? 2 : 1;
+  for (int bq = 0; bq < nyi; ++bq) {
+    const int J = bq ? j1 : j0;
+    for (int cq = 0; cq < nxi; ++cq) {
+      const int I = cq ? i1 : i0;
+      const T w = wxh * wyh * wzh;
+      const int cid = I + cnx * J;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) acc[c] = fma(w, zc[2 * cid + c], acc[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int id = 2 * node + c;
+    if (!fixed_f[id]) zf[id] = zf[id] + acc[c];
+  }
+}
+
+// (FP64: half the threads, so that the 96 values a node gathers stay in registers)
+template <typename T>
+constexpr int tail1_threads() { return sizeof(T) == 8 ? kTail1Threads / 2 : kTail1Threads; }
+
+template <typename T>
+__global__ void __launch_bounds__(tail1_threads<T>(), 1)
+    k_vcycle_tail1(const __grid_constant__ TailArgs<T> A, const CgScalars* __restrict__ sc) {
+  pdl_prologue();
+  const int rhs = blockIdx.x;
+  if (sc && sc[rhs].done) return;
+  extern __shared__ float4 tail1_raw[];
+  char* sm = reinterpret_cast<char*>(tail1_raw);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int L = A.nl - 1;  // the coarsest, relative
+  // the coarsest inverse is read once per cycle from global memory: bring it to L2 now
+  for (long long q = (long long)tid * 16; q < (long long)A.nc * A.nc; q += (long long)nt * 16)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(A.Ainv + q));
+  // every fused level's matrices (16-byte asynchronous copies, all in flight together), inverse
+  // diagonal and mask, and the first level's b
+#pragma unroll 1
+  for (int k = 0; k < L; ++k) {
+    const int chunks = (int)(64 * A.d[k].elems() * sizeof(T) / 16);
+    char* M = sm + A.off_m[k];
+    const char* src = reinterpret_cast<const char*>(A.Ae[k]);
+    for (int i = tid; i < chunks; i += nt) cp_async16(M + 16 * i, src + 16 * (long long)i);
+  }
+#pragma unroll 1
+  for (int k = 0; k < A.nl; ++k) {
+    const int n = (int)A.d[k].dofs();
+    uint8_t* F = reinterpret_cast<uint8_t*>(sm + A.off_f[k]);
+    for (int i = tid; i < n; i += nt) F[i] = A.fixed[k][i];
+    if (k == L) continue;
+    T* D = reinterpret_cast<T*>(sm + A.off_d[k]);
+    for (int i = tid; i < n; i += nt) D[i] = __ldg(A.invd[k] + i);
+    if (k == 0) {
+      T* B = reinterpret_cast<T*>(sm + A.off_b[k]);
+      const T* b = A.b[0] + (long long)rhs * n;
+      for (int i = tid; i < n; i += nt) B[i] = b[i];
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  T* res[kTailMax];
+#pragma unroll 1
+  for (int k = 0; k < L; ++k) {
+    const Dims d = A.d[k];
+    const int n = (int)d.dofs(), nodes = (int)d.nodes();
+    const T* M = reinterpret_cast<const T*>(sm + A.off_m[k]);
+    const T* B = reinterpret_cast<const T*>(sm + A.off_b[k]);
+    const T* D = reinterpret_cast<const T*>(sm + A.off_d[k]);
+    const uint8_t* F = reinterpret_cast<const uint8_t*>(sm + A.off_f[k]);
+    T* c = reinterpret_cast<T*>(sm + A.off_z[k]);
+    T* o = reinterpret_cast<T*>(sm + A.off_t[k]);
+    if (A.nu1 >= 2) {  // the first two sweeps in one phase
+      for (int nd = tid; nd < nodes; nd += nt)
+        sm_apply<4>(d, nd, M, SmJac0<T>{B, D, F, A.omega}, B, D, F, o, A.omega);
+      __syncthreads();
+      T* tmp = c;
+      c = o;
+      o = tmp;
+      for (int it = 2; it < A.nu1; ++it) {
+        for (int nd = tid; nd < nodes; nd += nt)
+          sm_apply<2>(d, nd, M, SmVec<T>{c}, B, D, F, o, A.omega);
+        __syncthreads();
+        tmp = c;
+        c = o;
+        o = tmp;
+      }
+    } else if (A.nu1 == 1) {
+      for (int nd = tid; nd < nodes; nd += nt)
+        sm_apply<3>(d, nd, M, SmVec<T>{c}, B, D, F, c, A.omega);
+      __syncthreads();
+    } else {
+      for (int q = tid; q < n; q += nt) c[q] = T(0);
+      __syncthreads();
+    }
+    for (int nd = tid; nd < nodes; nd += nt)
+      sm_apply<1>(d, nd, M, SmVec<T>{c}, B, D, F, o, A.omega);
+    __syncthreads();
+    const Dims dc = A.d[k + 1];
+    T* bc = reinterpret_cast<T*>(sm + A.off_b[k + 1]);
+    const uint8_t* Fc = reinterpret_cast<const uint8_t*>(sm + A.off_f[k + 1]);
+    for (int nd = tid; nd < (int)dc.nodes(); nd += nt) sm_restrict<T>(d, dc, nd, o, bc, Fc);
+    __syncthreads();
+    res[k] = c;
+  }
+  {  // coarsest level: z = Ainv b, one warp per row
+    const T* b = reinterpret_cast<const T*>(sm + A.off_b[L]);
+    T* z = reinterpret_cast<T*>(sm + A.off_z[L]);
+    const int lane = tid & 31, nw = nt >> 5;
+    for (int row = tid >> 5; row < A.nc; row += 2 * nw) {  // two rows in flight per warp
+      const int row2 = row + nw;
+      const double v = dense_row_dot<false>(A.nc, A.Ainv + (long long)row * A.nc, b, lane);
+      const double v2 = row2 < A.nc
+                            ? dense_row_dot<false>(A.nc, A.Ainv + (long long)row2 * A.nc, b, lane)
+                            : 0.0;
+      if (lane == 0) {
+        z[row] = (T)v;
+        if (row2 < A.nc) z[row2] = (T)v2;
+      }
+    }
+    __syncthreads();
+    res[L] = z;
+  }
+#pragma unroll 1
+  for (int k = L - 1; k >= 0; --k) {
+    const Dims d = A.d[k], dc = A.d[k + 1];
+    const int nodes = (int)d.nodes();
+    const T* M = reinterpret_cast<const T*>(sm + A.off_m[k]);
+    const T* B = reinterpret_cast<const T*>(sm + A.off_b[k]);
+    const T* D = reinterpret_cast<const T*>(sm + A.off_d[k]);
+    const uint8_t* F = reinterpret_cast<const uint8_t*>(sm + A.off_f[k]);
+    T* zs = reinterpret_cast<T*>(sm + A.off_z[k]);
+    T* c = res[k];
+    T* o = (c == zs) ? reinterpret_cast<T*>(sm + A.off_t[k]) : zs;
+    for (int nd = tid; nd < nodes; nd += nt) sm_prolong<T>(d, dc, nd, res[k + 1], c, F);
+    __syncthreads();
+    for (int it = 0; it < A.nu2; ++it) {
+      for (int nd = tid; nd < nodes; nd += nt)
+        sm_apply<2>(d, nd, M, SmVec<T>{c}, B, D, F, o, A.omega);
+      __syncthreads();
+      T* tmp = c;
+      c = o;
+      o = tmp;
+    }
+    res[k] = c;
+  }
+  const int n0 = (int)A.d[0].dofs();
+  T* out = A.z[0] + (long long)rhs * n0;
+  for (int i = tid; i < n0; i += nt) out[i] = res[0][i];
+}
+
 // 1 / diag(A) per DOF (1 on fixed DOFs).
 template <int DIM>
 __global__ void k_inv_diag(Dims d, const double* __restrict__ K0, const double* __restrict__ x,
@@ -990,8 +1261,69 @@ template cudaError_t launch_vcycle_tail<float>(const TailArgs<float>&, int, cons
 template cudaError_t launch_vcycle_tail<double>(const TailArgs<double>&, int, const CgScalars*,
                                                 cudaStream_t);
 
-// Whether a cluster of kTailCluster blocks of the fused kernel fits on this device.
+namespace {
+int tail1_smem_limit() {
+  static int lim = -1;
+  if (lim < 0) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_vcycle_tail1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin) != cudaSuccess ||
+        cudaFuncSetAttribute(k_vcycle_tail1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin) != cudaSuccess) {
+      cudaGetLastError();
+      optin = 0;
+    }
+    lim = optin;
+  }
+  return lim;
+}
+unsigned align16u(unsigned long long x) { return (unsigned)((x + 15ull) & ~15ull); }
+}  // namespace
+
+template <typename T>
+bool tail1_layout(TailArgs<T>& a) {
+  unsigned long long off = 0;
+  for (int k = 0; k < a.nl; ++k) {
+    const unsigned long long n = (unsigned long long)a.d[k].dofs();
+    const unsigned long long m = (unsigned long long)a.d[k].elems();
+    const bool coarsest = (k == a.nl - 1);
+    a.off_m[k] = (unsigned)off;
+    if (!coarsest) off += align16u(64ull * m * sizeof(T));
+    a.off_z[k] = (unsigned)off;
+    off += align16u(n * sizeof(T));
+    a.off_t[k] = (unsigned)off;
+    if (!coarsest) off += align16u(n * sizeof(T));
+    a.off_b[k] = (unsigned)off;
+    off += align16u(n * sizeof(T));
+    a.off_d[k] = (unsigned)off;
+    if (!coarsest) off += align16u(n * sizeof(T));
+    a.off_f[k] = (unsigned)off;
+    off += align16u(n);
+  }
+  a.smem = (unsigned)off;
+  return off > 0 && off <= (unsigned long long)tail1_smem_limit();
+}
+template bool tail1_layout<float>(TailArgs<float>&);
+template bool tail1_layout<double>(TailArgs<double>&);
+
+template <typename T>
+cudaError_t launch_vcycle_tail1(const TailArgs<T>& a, int nrhs, const CgScalars* sc,
+                                cudaStream_t st) {
+  topo::launch(k_vcycle_tail1<T>, dim3(nrhs), tail1_threads<T>(), a.smem, st, a, sc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_vcycle_tail1<float>(const TailArgs<float>&, int, const CgScalars*,
+                                                cudaStream_t);
+template cudaError_t launch_vcycle_tail1<double>(const TailArgs<double>&, int, const CgScalars*,
+                                                 cudaStream_t);
+
+// Whether a cluster of kTailCluster blocks of the fused kernel fits on this device (and the
+// shared-memory limit of the single-block form, set here, outside any stream capture).
 cudaError_t prepare_tail_kernels() {
+  tail1_smem_limit();
   if (kTailCluster > 8) {
     cudaError_t e = cudaFuncSetAttribute(k_vcycle_tail<float>,
                                          cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

@@ -351,6 +351,11 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
       a.z[j] = (TV*)l.z;
       a.t[j] = (TV*)l.t;
     }
+    if (tail1_layout<TV>(a)) {  // all fused levels in one block's shared memory
+      TOPO_CUDA(launch_vcycle_tail1<TV>(a, nrhs, sc, s->st));
+      *result = zk;
+      return TOPO_OK;
+    }
     TOPO_CUDA(launch_vcycle_tail<TV>(a, nrhs, sc, s->st));
     // the iterate ends where the unfused cycle leaves it: one swap per plain sweep
     const int swaps = (nu1 >= 1 ? nu1 - 1 : 0) + nu2;

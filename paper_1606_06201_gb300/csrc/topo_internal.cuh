@@ -225,7 +225,13 @@ struct TailArgs {
   T* b[kTailMax];  // b[0]: the restricted residual from the level above
   T* z[kTailMax];
   T* t[kTailMax];
+  // single-block form (k_vcycle_tail1): byte offsets of each level's element matrices, vectors
+  // and mask in shared memory, and the bytes in all
+  unsigned off_m[kTailMax], off_z[kTailMax], off_t[kTailMax], off_b[kTailMax], off_d[kTailMax],
+      off_f[kTailMax];
+  unsigned smem;
 };
+constexpr int kTail1Threads = 512;
 
 inline unsigned blocks_for(long long n, int threads = kThreads) {
   return (unsigned)((n + threads - 1) / threads);
@@ -253,6 +259,14 @@ template <typename T>
 cudaError_t launch_vcycle_tail(const TailArgs<T>& a, int nrhs, const CgScalars* sc,
                                cudaStream_t st);
 cudaError_t prepare_tail_kernels();
+// The same levels in the shared memory of one block per right-hand side (no cluster barrier, no
+// L2 round trip between phases).  tail1_layout fills a.off_* and a.smem and returns whether they
+// fit in a block's shared memory; launch_vcycle_tail1 leaves the first level's result in z[0].
+template <typename T>
+bool tail1_layout(TailArgs<T>& a);
+template <typename T>
+cudaError_t launch_vcycle_tail1(const TailArgs<T>& a, int nrhs, const CgScalars* sc,
+                                cudaStream_t st);
 // First coarse level of a 2D grid, matrix-free from the finest densities xf and the four child
 // matrices C (same modes as launch_apply).
 template <typename T>
