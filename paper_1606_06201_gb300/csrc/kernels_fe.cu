@@ -718,14 +718,47 @@ struct SmJac0 {  // omega invd b, as VJac0 forms it
   }
 };
 
-// 16-byte asynchronous copy global -> shared (no register staging; the thread waits for its own
-// copies with cp_async_wait_all, a hardware wait).
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+// Bulk copies global -> shared by the tensor memory accelerator, completing on an mbarrier.
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;" ::: "memory");
+__device__ __forceinline__ void mbar_init(unsigned bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes,
+                                         unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+// Waits for phase 0 of the barrier for at most kBulkWaitNs of the global timer (each poll may
+// suspend the thread for up to 1 us); false if it gave up.
+constexpr unsigned long long kBulkWaitNs = 1000000000ull;
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_wait0(unsigned bar) {
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0, 1000;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar)
+        : "memory");
+    if (ok) return true;
+    if (global_ns() - t0 > kBulkWaitNs) return false;
+  }
 }
 
 template <int MODE, typename T, typename VIn>
@@ -849,14 +882,18 @@ __global__ void __launch_bounds__(tail1_threads<T>(), 1)
   // the coarsest inverse is read once per cycle from global memory: bring it to L2 now
   for (long long q = (long long)tid * 16; q < (long long)A.nc * A.nc; q += (long long)nt * 16)
     asm volatile("prefetch.global.L2 [%0];" ::"l"(A.Ainv + q));
-  // every fused level's matrices (16-byte asynchronous copies, all in flight together), inverse
-  // diagonal and mask, and the first level's b
-#pragma unroll 1
-  for (int k = 0; k < L; ++k) {
-    const int chunks = (int)(64 * A.d[k].elems() * sizeof(T) / 16);
-    char* M = sm + A.off_m[k];
-    const char* src = reinterpret_cast<const char*>(A.Ae[k]);
-    for (int i = tid; i < chunks; i += nt) cp_async16(M + 16 * i, src + 16 * (long long)i);
+  // every fused level's matrices by bulk copies on one barrier, the inverse diagonals, masks and
+  // the first level's b by plain loads meanwhile
+  uint64_t* bar_p = reinterpret_cast<uint64_t*>(sm + A.off_bar);
+  const unsigned bar = smem_addr(bar_p);
+  if (tid == 0) {
+    mbar_init(bar);
+    unsigned bytes = 0;
+    for (int k = 0; k < L; ++k) bytes += (unsigned)(64 * A.d[k].elems() * sizeof(T));
+    mbar_expect_tx(bar, bytes);
+    for (int k = 0; k < L; ++k)
+      bulk_g2s(smem_addr(sm + A.off_m[k]), A.Ae[k], (unsigned)(64 * A.d[k].elems() * sizeof(T)),
+               bar);
   }
 #pragma unroll 1
   for (int k = 0; k < A.nl; ++k) {
@@ -872,8 +909,21 @@ __global__ void __launch_bounds__(tail1_threads<T>(), 1)
       for (int i = tid; i < n; i += nt) B[i] = b[i];
     }
   }
-  cp_async_wait_all();
-  __syncthreads();
+  __syncthreads();  // (the barrier is initialised before anyone polls it)
+  // every thread polls; the block decides together, so that all or none continue
+  if (!__syncthreads_and(mbar_wait0(bar) ? 1 : 0)) {
+    // the copies did not land in time: give them a second bounded wait before the block's shared
+    // memory is released, and stop this right-hand side's CG with a timeout
+    if (tid == 0) {
+      mbar_wait0(bar);
+      if (sc) {
+        CgScalars* w = const_cast<CgScalars*>(sc) + rhs;
+        w->status = TOPO_E_TIMEOUT;
+        w->done = 1;
+      }
+    }
+    return;
+  }
   T* res[kTailMax];
 #pragma unroll 1
   for (int k = 0; k < L; ++k) {
@@ -1303,6 +1353,8 @@ bool tail1_layout(TailArgs<T>& a) {
     a.off_f[k] = (unsigned)off;
     off += align16u(n);
   }
+  a.off_bar = (unsigned)off;
+  off += 16;
   a.smem = (unsigned)off;
   return off > 0 && off <= (unsigned long long)tail1_smem_limit();
 }

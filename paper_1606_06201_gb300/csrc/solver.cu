@@ -772,6 +772,7 @@ topo_status solve_impl(topo_solver* s, const double* b, double* u, double tol, i
   }
   if (worst == TOPO_E_NOT_CONVERGED) set_error("CG reached max_iter before the tolerance");
   if (worst == TOPO_E_BREAKDOWN) set_error("CG breakdown (p^T A p <= 0 or a non-finite scalar)");
+  if (worst == TOPO_E_TIMEOUT) set_error("a bounded device-side wait expired (V-cycle data copy)");
   return worst;
 }
 

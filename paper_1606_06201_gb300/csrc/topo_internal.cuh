@@ -229,6 +229,7 @@ struct TailArgs {
   // and mask in shared memory, and the bytes in all
   unsigned off_m[kTailMax], off_z[kTailMax], off_t[kTailMax], off_b[kTailMax], off_d[kTailMax],
       off_f[kTailMax];
+  unsigned off_bar;  // the mbarrier of the bulk copies
   unsigned smem;
 };
 constexpr int kTail1Threads = 512;
