@@ -226,18 +226,13 @@ def main():
             s.set_outer_precision(0)
         u_d = torch.zeros_like(f_d)
         if host_io:
-            x_h = torch.as_tensor(cfg["x"]).pin_memory()
-            f_h = torch.as_tensor(cfg["f"]).pin_memory()
+            x_h = torch.as_tensor(cfg["x"]).contiguous().pin_memory()
+            f_h = torch.as_tensor(cfg["f"]).contiguous().pin_memory()
             u_h = torch.empty_like(f_h).pin_memory()
-            x_in, f_in = torch.empty_like(x_d), torch.empty_like(f_d)
 
         def step():
-            if host_io:
-                x_in.copy_(x_h, non_blocking=True)
-                f_in.copy_(f_h, non_blocking=True)
-                s.set_density(x_in)
-                _, info = s.solve(f_in, u_d, tol=TOL)
-                u_h.copy_(u_d, non_blocking=True)
+            if host_io:  # the C-ABI call with host buffers: copies inside the call
+                info = s.solve_host(x_h, f_h, u_h, tol=TOL)
             else:
                 s.set_density(x_d)
                 _, info = s.solve(f_d, u_d, tol=TOL)

@@ -166,6 +166,13 @@ topo_status topo_set_density(topo_solver* s, const double* x);
 topo_status topo_solve(topo_solver* s, const double* b, double* u, double tol, int use_x0,
                        topo_solve_info* info);
 
+/* topo_set_density and topo_solve (from the zero guess) from host memory: x [host, m], b [host,
+ * nrhs x n], u [host, nrhs x n, out].  x is copied and the hierarchy built while b is copied on a
+ * second stream; u is copied back before the call returns.  Page-locked host buffers let the
+ * copies run asynchronously (pageable ones work, with staged copies).  K systems only. */
+topo_status topo_solve_host(topo_solver* s, const double* x, const double* b, double* u,
+                            double tol, topo_solve_info* info);
+
 /* y = K(x) v on the finest level in FP64 (masked), v, y [device, nrhs x n]. */
 topo_status topo_apply_K(topo_solver* s, const double* v, double* y);
 

@@ -750,7 +750,8 @@ topo_status solve_impl(topo_solver* s, const double* b, double* u, double tol, i
     }
     iter_before = iter_after;
   }
-  TOPO_CUDA(cudaMemcpyAsync(u, s->z, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s->st));
+  if (u != s->z)
+    TOPO_CUDA(cudaMemcpyAsync(u, s->z, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s->st));
   TOPO_CUDA(cudaEventRecord(s->ev_t1, s->st));
   TOPO_CUDA(cudaEventSynchronize(s->ev_t1));
   topo_status worst = TOPO_OK;
@@ -935,6 +936,9 @@ topo_status topo_solver_destroy(topo_solver* s) {
   if (s->ev_out) cudaEventDestroy(s->ev_out);
   if (s->ev_t0) cudaEventDestroy(s->ev_t0);
   if (s->ev_t1) cudaEventDestroy(s->ev_t1);
+  if (s->ev_copy_in) cudaEventDestroy(s->ev_copy_in);
+  if (s->ev_copy) cudaEventDestroy(s->ev_copy);
+  if (s->st_copy) cudaStreamDestroy(s->st_copy);
   if (s->st) cudaStreamDestroy(s->st);
   delete s;
   return TOPO_OK;
@@ -953,6 +957,9 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   TOPO_CUDA(cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming));
   TOPO_CUDA(cudaEventCreate(&s->ev_t0));
   TOPO_CUDA(cudaEventCreate(&s->ev_t1));
+  TOPO_CUDA(cudaStreamCreateWithFlags(&s->st_copy, cudaStreamNonBlocking));
+  TOPO_CUDA(cudaEventCreateWithFlags(&s->ev_copy_in, cudaEventDisableTiming));
+  TOPO_CUDA(cudaEventCreateWithFlags(&s->ev_copy, cudaEventDisableTiming));
   const int ne = s->ne, nrhs = s->nrhs;
   // element data
   std::vector<double> K0(ne * ne), C;
@@ -1285,6 +1292,40 @@ topo_status topo_solve(topo_solver* s, const double* b, double* u, double tol, i
   StreamGuard g(s);
   if (s->prec == TOPO_MIXED) return solve_impl<float>(s, b, u, tol, use_x0, info);
   return solve_impl<double>(s, b, u, tol, use_x0, info);
+}
+
+topo_status topo_solve_host(topo_solver* s, const double* x, const double* b, double* u,
+                            double tol, topo_solve_info* info) {
+  if (!s || !x || !b || !u || !(tol >= 0.0)) {
+    set_error("topo_solve_host: invalid argument");
+    return TOPO_E_INVALID_ARG;
+  }
+  if (s->arrow) {
+    set_error("topo_solve_host: K systems only");
+    return TOPO_E_INVALID_ARG;
+  }
+  StreamGuard g(s);
+  const long long m = s->L[0].m, n = s->L[0].n * s->nrhs;
+  // b travels on the copy stream (after the solver's earlier work on its buffer) while the
+  // hierarchy is built from x
+  TOPO_CUDA(cudaEventRecord(s->ev_copy_in, s->st));
+  TOPO_CUDA(cudaStreamWaitEvent(s->st_copy, s->ev_copy_in, 0));
+  TOPO_CUDA(cudaMemcpyAsync(s->bbuf, b, sizeof(double) * n, cudaMemcpyHostToDevice, s->st_copy));
+  TOPO_CUDA(cudaEventRecord(s->ev_copy, s->st_copy));
+  TOPO_CUDA(cudaMemcpyAsync(s->x, x, sizeof(double) * m, cudaMemcpyHostToDevice, s->st));
+  topo_status st = build_hierarchy(s);
+  s->have_density = (st == TOPO_OK);
+  if (st != TOPO_OK) {
+    cudaStreamSynchronize(s->st_copy);
+    return st;
+  }
+  TOPO_CUDA(cudaStreamWaitEvent(s->st, s->ev_copy, 0));
+  st = s->prec == TOPO_MIXED ? solve_impl<float>(s, s->bbuf, s->z, tol, 0, info)
+                             : solve_impl<double>(s, s->bbuf, s->z, tol, 0, info);
+  if (st != TOPO_OK && st != TOPO_E_NOT_CONVERGED) return st;
+  TOPO_CUDA(cudaMemcpyAsync(u, s->z, sizeof(double) * n, cudaMemcpyDeviceToHost, s->st));
+  TOPO_CUDA(cudaStreamSynchronize(s->st));
+  return st;
 }
 
 topo_status topo_apply_K(topo_solver* s, const double* v, double* y) {

@@ -19,6 +19,8 @@ struct topo_solver {
   cudaStream_t st = nullptr;     // private stream
   cudaStream_t user = nullptr;   // caller's stream (nullptr = legacy default stream)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+  cudaStream_t st_copy = nullptr;  // host-to-device copies that overlap the hierarchy build
+  cudaEvent_t ev_copy_in = nullptr, ev_copy = nullptr;
   std::vector<Level> L;
   std::vector<uint8_t> fixed_host;
   double* K0 = nullptr;

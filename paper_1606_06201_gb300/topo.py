@@ -88,6 +88,7 @@ _SIGS = {
     "topo_get_profile": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_longlong)]),
     "topo_set_density": (ctypes.c_int, [_vp, _vp]),
+    "topo_solve_host": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, _vp]),
     "topo_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int,
                                   ctypes.POINTER(SolveInfo)]),
     "topo_apply_K": (ctypes.c_int, [_vp, _vp, _vp]),
@@ -139,6 +140,11 @@ def _check(status, where, allow=()):
     if status != OK and status not in allow:
         raise TopoError(status, where)
     return status
+
+
+def _torch_f64():
+    import torch
+    return torch.float64
 
 
 def _ptr(t):
@@ -443,6 +449,19 @@ class Solver:
         _check(_lib.topo_solve(self._h, _ptr(b), _ptr(u), float(tol), int(bool(use_x0)),
                                ctypes.byref(info)), "topo_solve", allow)
         return u, info
+
+    def solve_host(self, x, b, u, tol=1e-8, allow_not_converged=False):
+        """topo_solve_host: densities x, right-hand sides b and the solution u in host memory
+        (contiguous FP64 CPU tensors, best page-locked)."""
+        for t in (x, b, u):
+            if t.is_cuda or t.dtype != _torch_f64() or not t.is_contiguous():
+                raise ValueError("expected contiguous float64 CPU tensors")
+        info = SolveInfo()
+        allow = (E_NOT_CONVERGED,) if allow_not_converged else ()
+        _check(_lib.topo_solve_host(self._h, _vp(x.data_ptr()), _vp(b.data_ptr()),
+                                    _vp(u.data_ptr()), float(tol), ctypes.byref(info)),
+               "topo_solve_host", allow)
+        return info
 
     def apply_K(self, v, y=None):
         import torch

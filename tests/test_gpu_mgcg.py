@@ -353,6 +353,32 @@ def test_pair_arithmetic_outer_operator_reaches_tight_tolerances(precision):
     assert rel_err(res[1][0], res[0][0]) <= 1e-9
 
 
+@pytest.mark.parametrize("precision,nrhs", [(0, 1), (1, 1), (1, 3)])
+def test_solve_from_host_buffers_matches_device_solve(precision, nrhs):
+    """topo_solve_host (copies in and out inside the call, b copied while the hierarchy is built)
+    gives the bits of topo_set_density + topo_solve on device buffers."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny = 128, 64
+    fixed = W.clamp_xmin(nx, ny)
+    x = _x(nx, ny, 0, 17)
+    F = np.stack([W.normal_load(fixed, 80 + k) for k in range(nrhs)])
+    s = topo.Solver(nx, ny, fixed=fixed, levels=4, precision=precision, nrhs=nrhs)
+    s.set_density(dev(torch, x))
+    u_dev, info_dev = s.solve(dev(torch, F), tol=1e-9)
+    xh = torch.as_tensor(x).contiguous().pin_memory()
+    fh = torch.as_tensor(F).contiguous().pin_memory()
+    uh = torch.full_like(fh, float("nan")).pin_memory()
+    info = s.solve_host(xh, fh, uh, tol=1e-9)
+    assert info.status == topo.OK and info.iterations == info_dev.iterations
+    np.testing.assert_array_equal(uh.numpy(), host(u_dev))
+    # pageable host memory works too
+    uh2 = torch.zeros_like(fh)
+    s.solve_host(torch.as_tensor(x).contiguous(), torch.as_tensor(F).contiguous(), uh2, tol=1e-9)
+    np.testing.assert_array_equal(uh2.numpy(), host(u_dev))
+    s.close()
+
+
 def test_profiling_times_every_kernel_kind_and_keeps_results():
     """Profiling inserts event nodes only: the iterate is bit-identical to an unprofiled solve,
     and every kernel kind of the iteration is timed once per CG iteration."""
