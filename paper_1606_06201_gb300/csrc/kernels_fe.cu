@@ -327,6 +327,118 @@ __global__ void __launch_bounds__(kThreads) k_apply_arrow(Dims d, const T* __res
   }
 }
 
+// 3D node-parallel operator with the right-hand sides of a node in one thread (NR of them per
+// thread, grid.y chunks beyond): the element rows - x_e K0 on the finest level, K0 staged in
+// shared memory; the stored Galerkin matrices below - are read once per node and applied to every
+// right-hand side, where the per-right-hand-side launches read them once each.  Per right-hand
+// side the arithmetic and its order are those of node_apply and apply_node (same bits).
+constexpr int kApply3Threads = 128;
+
+template <typename T, int MODE, bool FINE, int NR>
+__global__ void __launch_bounds__(kApply3Threads) k_apply3_rhs(
+    Dims d, const T* __restrict__ K0, const T* __restrict__ x, const T* __restrict__ Ae,
+    const T* __restrict__ v, const T* __restrict__ b, T* __restrict__ y, const T* __restrict__ invd,
+    T omega, const uint8_t* __restrict__ fixed, const CgScalars* __restrict__ sc, int nrhs) {
+  pdl_prologue();
+  constexpr int NE = 24;
+  __shared__ T k0s[FINE ? NE * NE : 1];
+  if (FINE) {
+    for (int t = threadIdx.x; t < NE * NE; t += blockDim.x) k0s[t] = K0[t];
+    __syncthreads();
+  }
+  const int r0 = blockIdx.y * NR;
+  bool live[NR];
+  bool any = false;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    live[r] = (r0 + r < nrhs) && !(sc && sc[r0 + r].done);
+    any = any || live[r];
+  }
+  const long long nodes = d.nodes();
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= nodes || !any) return;
+  const long long n = nodes * 3;
+  const int nnx = d.nx + 1, nny = d.ny + 1;
+  const long long m = d.elems();
+  int i, j, k;
+  node_coords(node, nnx, nny, 3, i, j, k);
+  T acc[NR][3];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) acc[r][0] = acc[r][1] = acc[r][2] = T(0);
+  if (MODE != 3) {
+#pragma unroll 1
+    for (int s = 0; s < 8; ++s) {
+      const int dx = s & 1, dy = (s >> 1) & 1, dz = s >> 2;
+      const int ex = i - 1 + dx, ey = j - 1 + dy, ez = k - 1 + dz;
+      if (ex < 0 || ex >= d.nx || ey < 0 || ey >= d.ny || ez < 0 || ez >= d.nz) continue;
+      const int loc = loc_of(1 - dx, 1 - dy, 1 - dz);
+      const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
+      T row[3][NE];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int q = 0; q < NE; ++q)
+          row[c][q] = FINE ? k0s[(loc * 3 + c) * NE + q]
+                           : ldg(Ae + (long long)((loc * 3 + c) * NE + q) * m + e);
+      const T xe = FINE ? ldg(x + e) : T(0);
+      long long nid[8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+        nid[a] = (ex + loc_ox(a)) + (long long)nnx * ((ey + loc_oy(a)) + (long long)nny * (ez + loc_oz(a)));
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (!live[r]) continue;
+        const T* vr = v + (long long)(r0 + r) * n;
+        T ve[NE];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) ve[a * 3 + c] = ldg(vr + 3 * nid[a] + c);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          T t = T(0);
+#pragma unroll
+          for (int q = 0; q < NE; ++q) t = fma(row[c][q], ve[q], t);
+          if (FINE) acc[r][c] = fma(xe, t, acc[r][c]);
+          else acc[r][c] += t;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    if (!live[r]) continue;
+    const long long off = (long long)(r0 + r) * n;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long id = 3 * node + c;
+      T out;
+      if (fixed[id]) out = T(0);
+      else if (MODE == 0) out = acc[r][c];
+      else if (MODE == 1) out = node_out<1, T>(acc[r][c], T(0), ldg(b + off + id), T(0), omega);
+      else if (MODE == 2)
+        out = node_out<2, T>(acc[r][c], ldg(v + off + id), ldg(b + off + id), invd[id], omega);
+      else out = node_out<3, T>(T(0), T(0), ldg(b + off + id), invd[id], omega);
+      y[off + id] = out;
+    }
+  }
+}
+
+template <typename T, int MODE, bool FINE>
+void apply3_rhs_dispatch(const Dims& d, const T* K0, const T* x, const T* Ae, const T* v,
+                         const T* b, T* y, const T* invd, T omega, const uint8_t* fixed, int nrhs,
+                         const CgScalars* sc, cudaStream_t st) {
+  const unsigned gx = blocks_for(d.nodes(), kApply3Threads);
+#define TOPO_A3(NR)                                                                          \
+  topo::launch(k_apply3_rhs<T, MODE, FINE, NR>, dim3(gx, (nrhs + NR - 1) / NR), kApply3Threads, \
+               0, st, d, K0, x, Ae, v, b, y, invd, omega, fixed, sc, nrhs)
+  if (nrhs >= 5) TOPO_A3(8);
+  else if (nrhs >= 3) TOPO_A3(4);
+  else if (nrhs == 2) TOPO_A3(2);
+  else TOPO_A3(1);
+#undef TOPO_A3
+}
+
 // First coarse level of the 2D grid without stored element matrices: the Galerkin element matrix
 // of coarse element E is sum_c x_c C_c over its four children (C_c = P_c^T K0 P_c), so
 // (A v)_node = sum_{E at node} sum_c x_c (C_c v_E)_row.  xf: densities of the finest level.
@@ -1160,7 +1272,20 @@ cudaError_t launch_apply(const Dims& d, int mode, const T* K0, const T* x, const
     }
   } else {
     if (mode >= 4) return cudaErrorInvalidValue;
-    TOPO_APPLY_CASE(3)
+    if (!w) {  // every right-hand side of a node in one thread
+#define TOPO_A3_MODE(MODE)                                                                    \
+  if (x) apply3_rhs_dispatch<T, MODE, true>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st); \
+  else apply3_rhs_dispatch<T, MODE, false>(d, K0, x, Ae, v, b, y, invd, omega, fixed, nrhs, sc, st)
+      switch (mode) {
+        case 0: TOPO_A3_MODE(0); break;
+        case 1: TOPO_A3_MODE(1); break;
+        case 2: TOPO_A3_MODE(2); break;
+        default: TOPO_A3_MODE(3);
+      }
+#undef TOPO_A3_MODE
+    } else {
+      TOPO_APPLY_CASE(3)
+    }
   }
 #undef TOPO_APPLY_CASE
   return cudaGetLastError();
