@@ -826,6 +826,22 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep_df(int nx, int ny, i
   }
 }
 
+// The densities checked (flag set if one is not finite and > 0) and converted for the FP32
+// V-cycle (x32) and the pair-arithmetic operator (xdf) in one pass; x32, xdf may be null.
+__global__ void k_prepare_x(const double* __restrict__ x, long long m, int* flag,
+                            float* __restrict__ x32, float2* __restrict__ xdf) {
+  pdl_prologue();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const double v = x[i];
+  if (!(v > 0.0) || !isfinite(v)) *flag = 1;
+  if (x32) x32[i] = (float)v;
+  if (xdf) {
+    const f2 t = df_from_double(v);
+    xdf[i] = make_float2(t.h, t.l);
+  }
+}
+
 // Densities as float pairs (hi + lo) for k_q1_sweep_df.
 __global__ void k_split_df(const double* __restrict__ x, float2* __restrict__ out, long long m) {
   pdl_prologue();
@@ -1218,6 +1234,13 @@ cudaError_t launch_q1_apply_dot_df(int nx, int ny, const Q1Coef& coef, const flo
   dim3 grid(q1_blocks(nx, ny), nrhs);
   topo::launch(k_q1_sweep_df, grid, kQ1Warps * 32, 0, st, nx, ny, q1_rows(nx, ny), k, xdf, v, y,
                fixed, sc, partials, counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prepare_x(const double* x, long long m, int* flag, float* x32, float2* xdf,
+                             cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  topo::launch(k_prepare_x, blocks_for(m), kThreads, 0, st, x, m, flag, x32, xdf);
   return cudaGetLastError();
 }
 

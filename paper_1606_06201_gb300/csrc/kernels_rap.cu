@@ -104,9 +104,9 @@ __global__ void k_rap2_from_fine(Dims df, const T* __restrict__ C2, const T* __r
 
 // 1 / diag of the first coarse level straight from the finest densities:
 // diag(A_1)_i = sum_{E at node} sum_c x_c (C_c)_{ii}.
-template <int DIM>
-__global__ void k_inv_diag_l1(Dims dc, const double* __restrict__ C, const double* __restrict__ xf,
-                              const uint8_t* __restrict__ fixed, double* __restrict__ invd) {
+template <int DIM, typename T>
+__global__ void k_inv_diag_l1(Dims dc, const T* __restrict__ C, const T* __restrict__ xf,
+                              const uint8_t* __restrict__ fixed, T* __restrict__ invd) {
   pdl_prologue();
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM, NE2 = NE * NE;
   const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -115,7 +115,7 @@ __global__ void k_inv_diag_l1(Dims dc, const double* __restrict__ C, const doubl
   const int i = (int)(node % nnx), j = (int)((node / nnx) % nny);
   const int k = (DIM == 3) ? (int)(node / ((long long)nnx * nny)) : 0;
   const int fnx = 2 * dc.nx, fny = 2 * dc.ny;
-  double acc[DIM] = {};
+  T acc[DIM] = {};
   for (int s = 0; s < NN; ++s) {
     const int dx = s & 1, dy = (s >> 1) & 1, dz = (DIM == 3) ? (s >> 2) : 0;
     const int ex = i - 1 + dx, ey = j - 1 + dy, ez = (DIM == 3) ? k - 1 + dz : 0;
@@ -126,7 +126,7 @@ __global__ void k_inv_diag_l1(Dims dc, const double* __restrict__ C, const doubl
       const long long fe = (2 * ex + (c & 1)) +
                            (long long)fnx * ((2 * ey + ((c >> 1) & 1)) +
                                              (long long)fny * (DIM == 3 ? 2 * ez + (c >> 2) : 0));
-      const double xc = xf[fe];
+      const T xc = xf[fe];
       for (int cc = 0; cc < DIM; ++cc) {
         const int r = loc * DIM + cc;
         acc[cc] = fma(xc, C[c * NE2 + r * NE + r], acc[cc]);
@@ -135,7 +135,7 @@ __global__ void k_inv_diag_l1(Dims dc, const double* __restrict__ C, const doubl
   }
   for (int cc = 0; cc < DIM; ++cc) {
     const long long id = DIM * node + cc;
-    invd[id] = (fixed[id] || !(acc[cc] > 0.0)) ? 1.0 : 1.0 / acc[cc];
+    invd[id] = (fixed[id] || !(acc[cc] > T(0))) ? T(1) : T(1) / acc[cc];
   }
 }
 
@@ -862,14 +862,21 @@ template cudaError_t launch_rap2_from_fine<double>(const Dims&, const double*, c
 template cudaError_t launch_rap2_from_fine<float>(const Dims&, const float*, const float*, float*,
                                                   cudaStream_t, const double*);
 
-cudaError_t launch_inv_diag_l1(const Dims& coarse1, const double* C, const double* xf,
-                               const uint8_t* fixed, double* invd, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_inv_diag_l1(const Dims& coarse1, const T* C, const T* xf,
+                               const uint8_t* fixed, T* invd, cudaStream_t st) {
   if (coarse1.dim == 2)
-    topo::launch(k_inv_diag_l1<2>, blocks_for(coarse1.nodes()), kThreads, 0, st, coarse1, C, xf, fixed, invd);
+    topo::launch(k_inv_diag_l1<2, T>, blocks_for(coarse1.nodes()), kThreads, 0, st, coarse1, C, xf,
+                 fixed, invd);
   else
-    topo::launch(k_inv_diag_l1<3>, blocks_for(coarse1.nodes()), kThreads, 0, st, coarse1, C, xf, fixed, invd);
+    topo::launch(k_inv_diag_l1<3, T>, blocks_for(coarse1.nodes()), kThreads, 0, st, coarse1, C, xf,
+                 fixed, invd);
   return cudaGetLastError();
 }
+template cudaError_t launch_inv_diag_l1<double>(const Dims&, const double*, const double*,
+                                                const uint8_t*, double*, cudaStream_t);
+template cudaError_t launch_inv_diag_l1<float>(const Dims&, const float*, const float*,
+                                               const uint8_t*, float*, cudaStream_t);
 
 template <typename TI, typename TO>
 cudaError_t launch_rap_coarse(const Dims& fine, const TI* Af, TO* Ac, cudaStream_t st) {

@@ -790,9 +790,7 @@ topo_status enqueue_build(topo_solver* s, bool warm = false) {
   const long long m = s->L[0].m;
   const int ne2 = s->ne * s->ne;
   TOPO_CUDA(cudaMemsetAsync(s->info, 0, 4 * sizeof(int), st));
-  TOPO_CUDA(launch_check_positive(s->x, m, s->info + 1, st));
-  if (s->xdf) TOPO_CUDA(launch_split_df(s->x, s->xdf, m, st));
-  if (mixed) TOPO_CUDA(launch_convert_d2f(s->x, s->x32, m, st));
+  TOPO_CUDA(launch_prepare_x(s->x, m, s->info + 1, mixed ? s->x32 : nullptr, s->xdf, st));
   if (s->arrow && mixed) {
     TOPO_CUDA(launch_convert_d2f(s->g, s->g32, m * s->ne, st));
     TOPO_CUDA(launch_convert_d2f(s->Dinv, s->Dinv32, m, st));
@@ -837,8 +835,13 @@ topo_status enqueue_build(topo_solver* s, bool warm = false) {
       TOPO_CUDA(launch_inv_diag32(lv.d, lv.Ae32, lv.fixed, lv.invd32, st));
       continue;
     }
+    if (k == 1 && !lv.Ae && mixed && !lv.omega_dev && !lv.lam_dev) {
+      // the matrix-free first coarse level of an FP32 V-cycle: only its FP32 diagonal is read
+      TOPO_CUDA(launch_inv_diag_l1<float>(lv.d, s->C32, s->x32, lv.fixed, lv.invd32, st));
+      continue;
+    }
     if (k == 1 && !lv.Ae)
-      TOPO_CUDA(launch_inv_diag_l1(lv.d, s->C, s->x, lv.fixed, lv.invd, st));
+      TOPO_CUDA(launch_inv_diag_l1<double>(lv.d, s->C, s->x, lv.fixed, lv.invd, st));
     else if (!(s->arrow && k == 0))  // the IP driver writes the finest diagonal of Z
       TOPO_CUDA(launch_inv_diag(lv.d, s->K0, k == 0 ? s->x : nullptr, lv.Ae, lv.fixed, lv.invd, st));
     if (lv.omega_dev || lv.lam_dev) {  // lambda_max(D^{-1} A_k) by power iteration

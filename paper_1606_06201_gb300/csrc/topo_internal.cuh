@@ -335,6 +335,10 @@ cudaError_t launch_q1_apply_dot_df(int nx, int ny, const Q1Coef& coef, const flo
                                    double* partials, unsigned* counters, CgScalars* sc,
                                    cudaStream_t st);
 cudaError_t launch_split_df(const double* x, float2* out, long long m, cudaStream_t st);
+// flag = 1 if some x_i is not finite and > 0 (flag zeroed by the caller); x32 = (float) x and
+// xdf = x as float pairs where not null.
+cudaError_t launch_prepare_x(const double* x, long long m, int* flag, float* x32, float2* xdf,
+                             cudaStream_t st);
 // Jacobi sweep (mode 2) on the 2D finest level fused with r^T y against the FP64 CG residual r and
 // the beta of Algorithm PCG (last smoothing sweep of the preconditioner).
 template <typename T>
@@ -381,8 +385,9 @@ template <typename T>
 cudaError_t launch_rap2_from_fine(const Dims& fine, const T* C2, const T* x, T* Ac,
                                   cudaStream_t st, const double* C2h = nullptr);
 // Inverse diagonal of the first coarse level from the finest densities and the child matrices.
-cudaError_t launch_inv_diag_l1(const Dims& coarse1, const double* C, const double* xf,
-                               const uint8_t* fixed, double* invd, cudaStream_t st);
+template <typename T>
+cudaError_t launch_inv_diag_l1(const Dims& coarse1, const T* C, const T* xf,
+                               const uint8_t* fixed, T* invd, cudaStream_t st);
 // Dense operator of a level with leading dimension ld; with an arrow (w != nullptr) the row and
 // column n hold w (zero on fixed DOFs) and A[n][n] = *zll.  g, Dinv: rank-one terms (finest level).
 cudaError_t launch_assemble_dense(const Dims& d, const double* K0, const double* x,
