@@ -69,6 +69,11 @@ __device__ __forceinline__ void q1_element(const Q1K<T>& k, T xe, const T u[4], 
   rv[3] = Dd - gHp;
 }
 
+// 1 / v rounded to nearest: the value of the IEEE division 1 / v, by the reciprocal intrinsic
+// (fewer instructions than the general division sequence).
+__device__ __forceinline__ float recip_rn(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double recip_rn(double v) { return __drcp_rn(v); }
+
 template <typename T>
 __device__ __forceinline__ T shfl_dn(T v) { return __shfl_down_sync(0xffffffffu, v, 1); }
 template <typename T>
@@ -209,7 +214,7 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, int 
           out.y = bb.y - qv;
         } else {
           const T xs = xcarry + xpair;
-          const T dinv = xs > T(0) ? T(1) / (k.kd * xs) : T(1);
+          const T dinv = xs > T(0) ? recip_rn(k.kd * xs) : T(1);
           if (MODE == 2) {
             out.x = fma(omega * dinv, bb.x - qu, pb.x);
             out.y = fma(omega * dinv, bb.y - qv, pb.y);
@@ -517,12 +522,14 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_fused(int nx, int ny, int 
     const T xl = shfl_up1(R.xe);
     return R.xe + (lane >= 1 ? xl : (MODE == 4 ? R.xl0 : T(0)));
   };
-  auto dinv_of = [&](T xs) { return xs > T(0) ? T(1) / (k.kd * xs) : T(1); };
+  auto dinv_of = [&](T xs) { return xs > T(0) ? recip_rn(k.kd * xs) : T(1); };
   // the input node value v(r) of the sweep
+  T dinv_in = T(0);  // MODE 4: the diagonal of the last input row, reused at its output
   auto input = [&](int r, const Raw& R, T xpair_prev, T xpair_r) {
     V2 v = zero;
     if (MODE == 4) {
       const T dinv = dinv_of(xpair_prev + xpair_r);
+      dinv_in = dinv;
       v.x = mul_rn(mul_rn(omega, dinv), R.b.x);
       v.y = mul_rn(mul_rn(omega, dinv), R.b.y);
       if (R.fx & 0xff) v.x = T(0);
@@ -569,6 +576,7 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_fused(int nx, int ny, int 
     if (ey + 2 <= ny && ey + 1 < j1) load(ey + 2, Rn);
     else Rn = Raw{zero, zero, zero, zero, zero, zero, T(0), T(0), 0};
     Rc = N;
+    const T dinv_row = dinv_in;  // (MODE 4: node row ey's, formed when it was the input row)
     const T xpair_n = xpair_of(N);
     const V2 pt = (ey + 1 <= ny && col_ok) ? input(ey + 1, N, xpair_c, xpair_n) : zero;
     const T xe = el_col ? R.xe : T(0);
@@ -586,8 +594,7 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_fused(int nx, int ny, int 
     const T xpair = xe + (lane >= 1 ? xl : T(0));
     if (ey >= j0 && out_lane) {
       const T qu = cu + ru[0] + l1u, qv = cv + rv[0] + l1v;
-      const T xs = xcarry + xpair;
-      const T dinv = dinv_of(xs);
+      const T dinv = MODE == 4 ? dinv_row : dinv_of(xcarry + xpair);
       V2 out;
       out.x = fma(omega * dinv, R.b.x - qu, pb.x);
       out.y = fma(omega * dinv, R.b.y - qv, pb.y);
