@@ -185,6 +185,8 @@ __global__ void __launch_bounds__(kThreads) k_cg_start_p(long long n, const doub
 
 // z += alpha p, r += alpha q, rv = r (V-cycle input precision), ||r||^2 and the stop test.
 template <typename TV>
+// (z += alpha p of this iteration is applied by k_cg_p, which reads p anyway, or by
+// k_cg_finish_z when the iteration ends the solve.)
 __global__ void __launch_bounds__(kThreads) k_cg_update(long long n, double* __restrict__ z,
                                                         double* __restrict__ r,
                                                         const double* __restrict__ p,
@@ -204,7 +206,6 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(long long n, double* __r
   double part[1] = {0.0};
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    z[i] = fma(alpha, p[i], z[i]);
     const double ri = fma(alpha, q[i], r[i]);
     r[i] = ri;
     if (rv) rv[i] = (TV)ri;
@@ -266,24 +267,45 @@ __global__ void __launch_bounds__(kThreads) k_cg_beta(long long n, const double*
   }
 }
 
-// p = -y + beta p, y_old = y.
+// z += alpha p (the iterate update of the iteration now ending), then p = -y + beta p, y_old = y.
 template <typename TV>
 __global__ void __launch_bounds__(kThreads) k_cg_p(long long n, const TV* __restrict__ y,
                                                    double* __restrict__ p, TV* __restrict__ y_old,
-                                                   int flexible, const CgScalars* sc) {
+                                                   int flexible, const CgScalars* sc,
+                                                   double* __restrict__ z) {
   pdl_prologue();
   const int rhs = blockIdx.y;
   if (sc[rhs].done) return;
-  const double beta = sc[rhs].beta;
+  const double beta = sc[rhs].beta, alpha = sc[rhs].alpha;
   y += rhs * n;
   p += rhs * n;
+  z += rhs * n;
   if (flexible) y_old += rhs * n;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const TV yi = y[i];
-    p[i] = fma(beta, p[i], -(double)yi);
+    const double pi = p[i];
+    z[i] = fma(alpha, pi, z[i]);
+    p[i] = fma(beta, pi, -(double)yi);
     if (flexible) y_old[i] = yi;
   }
+}
+
+// The iterate update of the iteration that ended the solve (its direction update did not run):
+// z += alpha p for every right-hand side with alpha != 0 (alpha = 0: stopped before an update,
+// or a breakdown in the operator).
+__global__ void __launch_bounds__(kThreads) k_cg_finish_z(long long n, const double* __restrict__ p,
+                                                          double* __restrict__ z,
+                                                          const CgScalars* sc) {
+  pdl_prologue();
+  const int rhs = blockIdx.y;
+  const double alpha = sc[rhs].alpha;
+  if (alpha == 0.0) return;
+  p += rhs * n;
+  z += rhs * n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    z[i] = fma(alpha, p[i], z[i]);
 }
 
 __global__ void __launch_bounds__(kThreads) k_dot(long long n, const double* __restrict__ a,
@@ -521,12 +543,19 @@ cudaError_t launch_cg_update(long long n, int nrhs, double* z, double* r, const 
 template <typename TV>
 cudaError_t launch_cg_direction(long long n, int nrhs, const double* r, const TV* y, double* p,
                                 TV* y_old, int flexible, double* partials, unsigned* counters,
-                                CgScalars* sc, cudaStream_t st) {
+                                CgScalars* sc, cudaStream_t st, double* z) {
   topo::launch(k_cg_beta<TV>, dim3(red_blocks(n), nrhs), kThreads, 0, st, n, r, y, y_old, flexible,
                                                                 partials, counters, sc);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  topo::launch(k_cg_p<TV>, dim3(red_blocks(n), nrhs), kThreads, 0, st, n, y, p, y_old, flexible, sc);
+  topo::launch(k_cg_p<TV>, dim3(red_blocks(n), nrhs), kThreads, 0, st, n, y, p, y_old, flexible, sc,
+               z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_finish_z(long long n, int nrhs, const double* p, double* z,
+                               const CgScalars* sc, cudaStream_t st) {
+  topo::launch(k_cg_finish_z, dim3(red_blocks(n), nrhs), kThreads, 0, st, n, p, z, sc);
   return cudaGetLastError();
 }
 
@@ -595,14 +624,15 @@ cudaError_t launch_cg_alpha(long long n, int nrhs, const double* p, const double
 
 template <typename TV>
 cudaError_t launch_cg_p(long long n, int nrhs, const TV* y, double* p, TV* y_old, int flexible,
-                        CgScalars* sc, cudaStream_t st) {
-  topo::launch(k_cg_p<TV>, dim3(red_blocks(n), nrhs), kThreads, 0, st, n, y, p, y_old, flexible, sc);
+                        CgScalars* sc, cudaStream_t st, double* z) {
+  topo::launch(k_cg_p<TV>, dim3(red_blocks(n), nrhs), kThreads, 0, st, n, y, p, y_old, flexible, sc,
+               z);
   return cudaGetLastError();
 }
 template cudaError_t launch_cg_p<double>(long long, int, const double*, double*, double*, int,
-                                         CgScalars*, cudaStream_t);
+                                         CgScalars*, cudaStream_t, double*);
 template cudaError_t launch_cg_p<float>(long long, int, const float*, double*, float*, int,
-                                        CgScalars*, cudaStream_t);
+                                        CgScalars*, cudaStream_t, double*);
 
 cudaError_t launch_dot(long long n, int nrhs, const double* a, const double* b, double* partials,
                        unsigned* counters, double* out, cudaStream_t st) {
@@ -619,7 +649,7 @@ cudaError_t launch_dot(long long n, int nrhs, const double* a, const double* b, 
                                             double, int, cudaStream_t);                          \
   template cudaError_t launch_cg_direction<TV>(long long, int, const double*, const TV*,         \
                                                double*, TV*, int, double*, unsigned*,            \
-                                               CgScalars*, cudaStream_t);
+                                               CgScalars*, cudaStream_t, double*);
 TOPO_INST(double)
 TOPO_INST(float)
 #undef TOPO_INST

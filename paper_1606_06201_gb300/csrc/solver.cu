@@ -532,11 +532,14 @@ topo_status cg_iteration(topo_solver* s, int slot, double tol, int max_iter) {
   TOPO_TRY(precondition<TV>(s, s->sc, &y, fuse));
   TOPO_TRY(prof_mark(s, 5, 1));
   s->yv = y;
+  // (the direction kernel also applies this iteration's z += alpha p)
   if (fuse)
-    TOPO_CUDA(launch_cg_p<TV>(n, s->nrhs, (const TV*)y, s->p, (TV*)s->yold, 0, s->sc, s->st));
+    TOPO_CUDA(launch_cg_p<TV>(n, s->nrhs, (const TV*)y, s->p, (TV*)s->yold, 0, s->sc, s->st,
+                              s->z));
   else
     TOPO_CUDA(launch_cg_direction<TV>(n, s->nrhs, s->r, (const TV*)y, s->p, (TV*)s->yold,
-                                      s->desc.flexible, s->partials, s->counters, s->sc, s->st));
+                                      s->desc.flexible, s->partials, s->counters, s->sc, s->st,
+                                      s->z));
   s->prof_slot = -1;
   return TOPO_OK;
 }
@@ -750,6 +753,9 @@ topo_status solve_impl(topo_solver* s, const double* b, double* u, double tol, i
     }
     iter_before = iter_after;
   }
+  // the iterate update of the last iteration (its direction kernel did not run)
+  TOPO_CUDA(launch_cg_finish_z(n, nrhs, s->p, s->z, s->sc, s->st));
+  s->launches += 1;
   if (u != s->z)
     TOPO_CUDA(cudaMemcpyAsync(u, s->z, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s->st));
   TOPO_CUDA(cudaEventRecord(s->ev_t1, s->st));

@@ -422,6 +422,10 @@ cudaError_t launch_cg_init_zero(long long n, long long n_mask, int nrhs, const d
                                 const uint8_t* fixed, double* z, double* r, TV* rv,
                                 double* partials, unsigned* counters, CgScalars* sc, double tol,
                                 int max_iter, cudaStream_t st);
+// z += alpha p per right-hand side with alpha != 0: the iterate update of the iteration that
+// ended the solve (k_cg_p applies it otherwise).
+cudaError_t launch_cg_finish_z(long long n, int nrhs, const double* p, double* z,
+                               const CgScalars* sc, cudaStream_t st);
 cudaError_t launch_cg_init(long long n, int nrhs, const double* b, double* z, double* r,
                            const double* Az, int use_x0, double* partials, unsigned* counters,
                            CgScalars* sc, double tol, int max_iter, cudaStream_t st);
@@ -436,11 +440,11 @@ cudaError_t launch_cg_update(long long n, int nrhs, double* z, double* r, const 
 template <typename TV>
 cudaError_t launch_cg_direction(long long n, int nrhs, const double* r, const TV* y, double* p,
                                 TV* y_old, int flexible, double* partials, unsigned* counters,
-                                CgScalars* sc, cudaStream_t st);
+                                CgScalars* sc, cudaStream_t st, double* z);
 // p = -y + beta p (beta already in the scalars), y_old = y if flexible.
 template <typename TV>
 cudaError_t launch_cg_p(long long n, int nrhs, const TV* y, double* p, TV* y_old, int flexible,
-                        CgScalars* sc, cudaStream_t st);
+                        CgScalars* sc, cudaStream_t st, double* z);
 cudaError_t launch_dot(long long n, int nrhs, const double* a, const double* b, double* partials,
                        unsigned* counters, double* out, cudaStream_t st);
 // Power iteration for lambda_max(D^{-1} A): v <- D^{-1} A v / ||.||_D (y = A v supplied by the
