@@ -122,10 +122,28 @@ def newton_criterion(prob, z, s, r):
             + np.linalg.norm(rt3) / (np.linalg.norm(phi) + np.linalg.norm(psi)))
 
 
+def kkt_criterion(prob, z, s, r):
+    """The scaled KKT residual of the Remark in Sec. 3.4:
+    ||Res1|| / ||f|| + ||tilde Res3|| / (||phi|| + ||psi||) + phi^T x / (||phi|| ||x||)
+    + psi^T (xbar - x) / (||psi|| ||xbar - x||).  (The printed last denominator repeats
+    ||phi|| ||x||; the reading here scales each complementarity term by its own factors.)"""
+    u, lam, x, phi, psi = z
+    res1, _, _, _, _, rt3, _, _ = kkt_residuals(prob, prob.K0, u, lam, x, phi, psi, s, r)
+    xu = prob.xbar - x
+    nphi, npsi = np.linalg.norm(phi), np.linalg.norm(psi)
+    return (np.linalg.norm(res1) / np.linalg.norm(prob.f) + np.linalg.norm(rt3) / (nphi + npsi)
+            + float(phi @ x) / (nphi * np.linalg.norm(x))
+            + float(psi @ xu) / (npsi * np.linalg.norm(xu)))
+
+
 def ip_run(prob, sigma=0.2, tau_nwt=0.1, tau_ip=1e-8, frac=0.9, step_rule="all",
-           max_newton=500, record=False):
+           max_newton=500, record=False, stop_rule="barrier", tau_kkt=1e-6):
     """Sec. 3.1 algorithm.  Returns (z, info); info counts IP iterations (barrier reductions),
-    Newton steps and linear solves (feval), and optionally the per-step trajectory."""
+    Newton steps and linear solves (feval), and optionally the per-step trajectory.
+    stop_rule "barrier": stop once max(s, r) <= tau_IP (Eq. (crit:ip)); "kkt": stop once the
+    scaled KKT residual of the Remark in Sec. 3.4 (kkt_criterion, after each Newton step) is
+    <= tau_kkt.  (The Remark names no tolerance of its own; at tau_IP = 1e-8 the tilde Res3
+    term stalls near 1e-7, from the rounding of Res4 / x at tiny x, so the test takes its own.)"""
     m = prob.m
     x = np.full(m, prob.V / m)
     u = prob.solve_u(x)
@@ -143,11 +161,13 @@ def ip_run(prob, sigma=0.2, tau_nwt=0.1, tau_ip=1e-8, frac=0.9, step_rule="all",
         if record:
             info["traj"].append(dict(u=z[0].copy(), lam=z[1], x=z[2].copy(), phi=z[3].copy(),
                                      psi=z[4].copy(), s=s, r=r, alpha=alpha, crit=crit))
+        if stop_rule == "kkt" and kkt_criterion(prob, z, s, r) <= tau_kkt:
+            break
         if crit <= tau_nwt:
             s *= sigma
             r *= sigma
             info["ip"] += 1
-            if max(s, r) <= tau_ip:
+            if stop_rule == "barrier" and max(s, r) <= tau_ip:
                 break
     info["s"], info["r"] = s, r
     info["compliance"] = float(prob.f @ z[0])

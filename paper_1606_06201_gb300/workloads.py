@@ -104,6 +104,19 @@ def cantilever_2d(nx, ny, volfrac):
                 V=V, xbar=1.0, x0=np.full(m, V / m))
 
 
+def corner_supported_2d(nx, ny, volfrac):
+    """Example-3-shaped beam: both components fixed at the two lower corner nodes (0, 0) and
+    (nx, 0), f_y = -1 at the lower edge's middle node (nx/2, 0), V = volfrac * m, xbar = 1,
+    x0 = V/m."""
+    m = nx * ny
+    V = volfrac * m
+    fixed = np.zeros(n_dofs(nx, ny), dtype=np.uint8)
+    for node in (0, nx):
+        fixed[2 * node] = fixed[2 * node + 1] = 1
+    return dict(nx=nx, ny=ny, nz=0, fixed=fixed, f=point_load(nx, ny, 0, (nx // 2, 0), 1, -1.0),
+                V=V, xbar=1.0, x0=np.full(m, V / m))
+
+
 def random_field_2d(nx, ny, seed_x=0, seed_f=1):
     """Standalone-solve workload: log-uniform smoothed densities, N(0,1) load on free DOFs."""
     fixed = clamp_xmin(nx, ny)

@@ -122,3 +122,54 @@ def test_ip_and_long_run_oc_agree():
     _, info = ip.ip_run(prob)
     _, oinfo = oc.oc_run(prob, variant="aoc", tau_oc=0.0, max_feval=3000, xlow=1e-10)
     np.testing.assert_allclose(oinfo["compliance"][-1], info["compliance"], rtol=2e-5)
+
+
+def test_kkt_stop_rule_gives_almost_the_same_solution():
+    """Remark in Sec. 3.4: stopping once the scaled KKT residual is small leads to almost the same
+    results as the barrier rule max(s, r) <= tau_IP.  With tau_kkt = 1e-4 the run stops at the
+    first Newton step whose residual meets it, and x agrees with the barrier rule's to 1e-3."""
+    for shape in ((16, 8), (32, 16)):
+        prob = _problem(*shape)
+        zb, ib = ip.ip_run(prob)
+        zk, ik = ip.ip_run(prob, stop_rule="kkt", tau_kkt=1e-4, record=True)
+        kkt = [ip.kkt_criterion(prob, [t["u"], t["lam"], t["x"], t["phi"], t["psi"]], t["s"],
+                                t["r"]) for t in ik["traj"]]
+        assert kkt[-1] <= 1e-4 and all(k > 1e-4 for k in kkt[:-1]), shape
+        assert np.max(np.abs(zb[2] - zk[2])) <= 1e-3, shape
+        assert abs(ib["compliance"] - ik["compliance"]) <= 1e-6 * ib["compliance"], shape
+
+
+def test_kkt_criterion_vanishes_at_a_kkt_point_and_sums_its_terms():
+    """The scaled KKT residual is the sum of its four non-negative terms: zero residuals and zero
+    complementarity give 0; a complementarity product alone gives exactly its scaled value."""
+    prob = _problem(8, 4)
+    m = prob.m
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0.1, 0.9, m)
+    u = prob.solve_u(x)
+    # phi = psi = 0 would divide by zero: one entry each, on elements where the bound is apart
+    phi = np.zeros(m)
+    psi = np.zeros(m)
+    phi[0], psi[1] = 2.0, 3.0
+    z = [u, 0.0, x, phi, psi]
+    # with s = phi x and r = psi (xbar - x) elementwise the barrier residuals vanish; Res3 does not
+    val = ip.kkt_criterion(prob, z, 0.0, 0.0)
+    comp = phi[0] * x[0] / (2.0 * np.linalg.norm(x)) + psi[1] * (1 - x[1]) / (3.0 * np.linalg.norm(1 - x))
+    res1, _, _, _, _, rt3, _, _ = ip.kkt_residuals(prob, prob.K0, u, 0.0, x, phi, psi, 0.0, 0.0)
+    expect = (np.linalg.norm(res1) / np.linalg.norm(prob.f) + np.linalg.norm(rt3) / 5.0 + comp)
+    assert abs(val - expect) <= 1e-12 * expect
+
+
+def test_example3_corner_supported_solution_is_mirror_symmetric():
+    """Example 3's setting (two lower corners fixed, load at the lower edge's middle node) is
+    symmetric about the vertical centre line, and so is the IP solution of the convex problem."""
+    nx, ny = 16, 4
+    cfg = W.corner_supported_2d(nx, ny, 0.5)
+    prob = ip.Problem(fe.Grid(nx, ny), fe.element_stiffness(2), cfg["fixed"], cfg["f"], cfg["V"],
+                      cfg["xbar"])
+    z, info = ip.ip_run(prob)
+    assert info["ip"] == 12 and max(info["s"], info["r"]) <= 1e-8
+    x = z[2].reshape(ny, nx)
+    assert np.max(np.abs(x - x[:, ::-1])) <= 1e-9
+    assert abs(x.sum() - cfg["V"]) <= 1e-9 * cfg["V"]
+
