@@ -239,6 +239,11 @@ typedef struct {
   double cg_tol_factor; /* the Z systems of major iteration k (k barrier reductions so far) are
                            solved to cg_tol * cg_tol_factor^k: 1 keeps cg_tol fixed, 0.5 is the
                            "CG tol decreasing" variant of Sec. 9.1 (tab:IP); in (0, 1] */
+  int stop_rule;       /* 0: stop once max(s, r) <= tau_ip (Eq. (crit:ip)); 1: stop once the scaled
+                          KKT residual of the Remark in Sec. 3.4 is <= tau_kkt after a Newton step:
+                          ||Res1||/||f|| + ||tilde Res3||/(||phi|| + ||psi||)
+                          + phi^T x/(||phi|| ||x||) + psi^T (xbar - x)/(||psi|| ||xbar - x||) */
+  double tau_kkt;      /* tolerance of stop_rule 1 (> 0) */
 } topo_ip_opts;
 
 typedef struct {
@@ -247,9 +252,10 @@ typedef struct {
   int feval;           /* linear systems solved (initial solve included) */
   int cg_iters;        /* CG iterations over all systems */
   double s, r, lam, alpha, crit; /* barrier parameters, multiplier, last step, Newton test value */
-  int done;            /* 1 once max(s, r) <= tau_IP */
+  int done;            /* 1 once the stop rule holds */
   int status;
   double wall_ms;      /* topo_ip_run: elapsed time of the run */
+  double kkt;          /* scaled KKT residual after the last Newton step (stop_rule 1's value) */
 } topo_ip_info;
 
 /* f [device, n], copied.  Returns TOPO_E_INFEASIBLE unless 0 < V < m xbar. */

@@ -28,6 +28,7 @@ struct topo_ip {
   double* partials = nullptr;
   unsigned* counter = nullptr;
   double fnorm = 0.0;
+  double kkt = NAN;  // scaled KKT residual after the last Newton step
   int newton = 0, ip_iters = 0, feval = 0, cg_iters = 0;
   bool done = false;
   std::vector<void*> allocs;
@@ -121,6 +122,7 @@ void fill_ip_info(topo_ip* a, double crit, topo_ip_info* info, int status) {
   info->lam = h.lam;
   info->alpha = h.alpha;
   info->crit = crit;
+  info->kkt = a->kkt;
   info->done = a->done ? 1 : 0;
   info->status = status;
 }
@@ -173,7 +175,7 @@ topo_status topo_ip_create(const topo_solver_desc* desc, const double* f, double
   s2 = s2 ? s2 : a->alloc(&a->dphi, m);
   s2 = s2 ? s2 : a->alloc(&a->dpsi, m);
   s2 = s2 ? s2 : a->alloc(&a->ip, 1);
-  s2 = s2 ? s2 : a->alloc(&a->partials, 8 * (size_t)kRedBlocks + 8 * blocks_for(a->d.nodes()));
+  s2 = s2 ? s2 : a->alloc(&a->partials, 12 * (size_t)kRedBlocks + 8 * blocks_for(a->d.nodes()));
   s2 = s2 ? s2 : a->alloc(&a->counter, 1);
   if (s2 != TOPO_OK) return fail(s2);
   if (cudaMallocHost((void**)&a->ip_host, sizeof(IpScalars)) != cudaSuccess)
@@ -240,9 +242,11 @@ topo_status topo_ip_set_vcycle_fusion(topo_ip* a, int on) {
 // The options the IP driver cannot run with.
 topo_status check_ip_opts(const topo_ip_opts* o, const char* where) {
   if (!(o->cg_tol > 0.0) || !(o->cg_tol_factor > 0.0 && o->cg_tol_factor <= 1.0) ||
-      !(o->sigma > 0.0 && o->sigma < 1.0)) {
+      !(o->sigma > 0.0 && o->sigma < 1.0) || (o->stop_rule != 0 && o->stop_rule != 1) ||
+      (o->stop_rule == 1 && !(o->tau_kkt > 0.0))) {
     topo::set_error(std::string(where) +
-                    ": cg_tol must be > 0, cg_tol_factor in (0, 1] and sigma in (0, 1)");
+                    ": cg_tol must be > 0, cg_tol_factor in (0, 1], sigma in (0, 1), stop_rule 0 "
+                    "or 1 (with tau_kkt > 0)");
     return TOPO_E_INVALID_ARG;
   }
   return TOPO_OK;
@@ -319,6 +323,13 @@ topo_status topo_ip_step(topo_ip* a, const topo_ip_opts* o, topo_ip_info* info) 
     fill_ip_info(a, crit, info, TOPO_E_BREAKDOWN);
     return TOPO_E_BREAKDOWN;
   }
+  // the scaled KKT residual of the Remark in Sec. 3.4, at the new iterate with the current (s, r)
+  a->kkt = crit + h.comp_phi / (h.nrm_phi * h.nrm_x) + h.comp_psi / (h.nrm_psi * h.nrm_xu);
+  if (o->stop_rule == 1 && a->kkt <= o->tau_kkt) {
+    a->done = true;
+    fill_ip_info(a, crit, info, ss);
+    return TOPO_OK;
+  }
   if (crit <= o->tau_nwt) {
     h.s *= o->sigma;
     h.r *= o->sigma;
@@ -326,7 +337,7 @@ topo_status topo_ip_step(topo_ip* a, const topo_ip_opts* o, topo_ip_info* info) 
     TOPO_CUDA(cudaMemcpyAsync(&a->ip->s, &h.s, sizeof(double), cudaMemcpyHostToDevice, st));
     TOPO_CUDA(cudaMemcpyAsync(&a->ip->r, &h.r, sizeof(double), cudaMemcpyHostToDevice, st));
     TOPO_CUDA(cudaStreamSynchronize(st));
-    if (std::max(h.s, h.r) <= o->tau_ip) a->done = true;
+    if (o->stop_rule == 0 && std::max(h.s, h.r) <= o->tau_ip) a->done = true;
   }
   fill_ip_info(a, crit, info, ss);
   return TOPO_OK;

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kThreads) k_ip_elem(Dims d, const double* __re
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM;
   const long long m = d.elems();
   const double lam = ip->lam, s = ip->s, r = ip->r, xbar = ip->xbar;
-  double part[6] = {0, 0, 0, 0, 0, 0};
+  double part[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < m;
        e += (long long)gridDim.x * blockDim.x) {
     double ue[NE];
@@ -277,9 +277,13 @@ __global__ void __launch_bounds__(kThreads) k_ip_elem(Dims d, const double* __re
     part[3] = fma(ph, ph, part[3]);
     part[4] = fma(ps, ps, part[4]);
     part[5] += di;
+    part[6] = fma(ph, xe, part[6]);  // the complementarity terms of the scaled KKT residual
+    part[7] = fma(ps, xu, part[7]);
+    part[8] = fma(xe, xe, part[8]);
+    part[9] = fma(xu, xu, part[9]);
   }
-  double tot[6];
-  if (!last_block<6>(part, 0, partials, counter, tot)) return;
+  double tot[10];
+  if (!last_block<10>(part, 0, partials, counter, tot)) return;
   if (threadIdx.x == 0) {
     ip->sum_x = tot[0];
     ip->sum_t = tot[1];
@@ -287,6 +291,10 @@ __global__ void __launch_bounds__(kThreads) k_ip_elem(Dims d, const double* __re
     ip->nrm_phi = sqrt(tot[3]);
     ip->nrm_psi = sqrt(tot[4]);
     ip->zll = tot[5];
+    ip->comp_phi = tot[6];
+    ip->comp_psi = tot[7];
+    ip->nrm_x = sqrt(tot[8]);
+    ip->nrm_xu = sqrt(tot[9]);
   }
 }
 

@@ -54,6 +54,8 @@ struct IpScalars {
   double sum_x, sum_t, res2;     // sum x, sum tilde Res3 / D, V - sum x
   double nrm_tr3, nrm_phi, nrm_psi, nrm_res1;
   double zll;                    // Z_ll = sum 1 / D
+  double comp_phi, comp_psi;     // phi^T x, psi^T (xbar - x)
+  double nrm_x, nrm_xu;          // ||x||, ||xbar - x||
   double alpha, dlam;            // step length, lambda direction
   int step_all;                  // 1: 0.9 rule also on phi and psi
   int pad;

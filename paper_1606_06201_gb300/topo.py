@@ -43,14 +43,16 @@ class IpOpts(ctypes.Structure):
                 ("tau_ip", ctypes.c_double), ("frac", ctypes.c_double),
                 ("step_x_only", ctypes.c_int), ("max_newton", ctypes.c_int),
                 ("cg_tol", ctypes.c_double), ("cg_tol_init", ctypes.c_double),
-                ("cg_tol_factor", ctypes.c_double)]
+                ("cg_tol_factor", ctypes.c_double), ("stop_rule", ctypes.c_int),
+                ("tau_kkt", ctypes.c_double)]
 
 
 class IpInfo(ctypes.Structure):
     _fields_ = [("newton", ctypes.c_int), ("ip_iters", ctypes.c_int), ("feval", ctypes.c_int),
                 ("cg_iters", ctypes.c_int), ("s", ctypes.c_double), ("r", ctypes.c_double),
                 ("lam", ctypes.c_double), ("alpha", ctypes.c_double), ("crit", ctypes.c_double),
-                ("done", ctypes.c_int), ("status", ctypes.c_int), ("wall_ms", ctypes.c_double)]
+                ("done", ctypes.c_int), ("status", ctypes.c_int), ("wall_ms", ctypes.c_double),
+                ("kkt", ctypes.c_double)]
 
 
 class OcOpts(ctypes.Structure):
@@ -185,12 +187,17 @@ def _desc(nx, ny, nz, fixed, levels, precision, nu1, nu2, omega, max_iter, nrhs,
 
 
 def ip_options(sigma=0.2, tau_nwt=0.1, tau_ip=1e-8, frac=0.9, step_x_only=False, max_newton=500,
-               cg_tol=1e-8, cg_tol_init=None, cg_tol_factor=1.0):
+               cg_tol=1e-8, cg_tol_init=None, cg_tol_factor=1.0, stop_rule="barrier",
+               tau_kkt=1e-6):
     """Sec. 3 defaults; cg_tol is the relative residual of the Z solves of the first major
     iteration, multiplied by cg_tol_factor at every barrier reduction (Sec. 9.1: 1e-2 with factor
-    1 or 0.5)."""
+    1 or 0.5).  stop_rule "barrier" (max(s, r) <= tau_ip) or "kkt" (the scaled KKT residual of
+    the Remark in Sec. 3.4 <= tau_kkt)."""
+    if stop_rule not in ("barrier", "kkt"):
+        raise ValueError("stop_rule must be 'barrier' or 'kkt'")
     return IpOpts(sigma, tau_nwt, tau_ip, frac, int(step_x_only), max_newton, cg_tol,
-                  cg_tol if cg_tol_init is None else cg_tol_init, cg_tol_factor)
+                  cg_tol if cg_tol_init is None else cg_tol_init, cg_tol_factor,
+                  0 if stop_rule == "barrier" else 1, tau_kkt)
 
 
 def oc_options(variant=OC_AOC, q=0.5, xlow=1e-6, lam_hi=1e4, tau_lambda=1e-11, tau_oc=1e-5,

@@ -161,6 +161,42 @@ def test_ip_rejects_bad_tolerance_options():
     ip.close()
 
 
+def test_ip_kkt_stop_rule_matches_oracle():
+    """The scaled-KKT-residual stop (Remark in Sec. 3.4, tau_kkt = 1e-4): the GPU IP (FP64)
+    stops at the oracle's Newton step with the oracle's x."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    cfg, prob = _problem(32, 16)
+    z, oinfo = oip.ip_run(prob, stop_rule="kkt", tau_kkt=1e-4)
+    ip_ = topo.IP(32, 16, fixed=cfg["fixed"], f=dev(torch, cfg["f"]), V=cfg["V"], xbar=1.0,
+                  levels=3, max_iter=5000)
+    info = ip_.run(topo.ip_options(cg_tol=1e-12, cg_tol_init=1e-13, stop_rule="kkt",
+                                   tau_kkt=1e-4))
+    assert info.done == 1 and info.newton == oinfo["newton"] and info.kkt <= 1e-4
+    assert _rel(host(ip_.state()[1]), z[2]) <= 1e-8
+    ip_.close()
+
+
+def test_ip_example3_corner_supported_matches_oracle():
+    """Example 3's setting (lower corners fixed, load at the lower edge's middle node) on a 32 x 8
+    grid, FP64: the same Newton steps and barrier reductions as the oracle, x to 1e-8."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    cfg = W.corner_supported_2d(32, 8, 0.5)
+    prob = oip.Problem(fe.Grid(32, 8), fe.element_stiffness(2), cfg["fixed"], cfg["f"], cfg["V"],
+                       cfg["xbar"])
+    z, oinfo = oip.ip_run(prob)
+    ip_ = topo.IP(32, 8, fixed=cfg["fixed"], f=dev(torch, cfg["f"]), V=cfg["V"], xbar=1.0,
+                  levels=3, max_iter=5000)
+    info = ip_.run(topo.ip_options(cg_tol=1e-12, cg_tol_init=1e-13))
+    assert info.done == 1 and info.newton == oinfo["newton"] and info.ip_iters == oinfo["ip"]
+    x = host(ip_.state()[1])
+    assert _rel(x, z[2]) <= 1e-8
+    xr = x.reshape(8, 32)
+    assert np.max(np.abs(xr - xr[:, ::-1])) <= 1e-8
+    ip_.close()
+
+
 def test_ip_rejects_infeasible_volume():
     torch = torch_cuda()
     topo = topo_lib()
