@@ -1458,8 +1458,13 @@ int tail1_smem_limit() {
 unsigned align16u(unsigned long long x) { return (unsigned)((x + 15ull) & ~15ull); }
 }  // namespace
 
+// (A coarsest system above kTail1MaxNc DOFs keeps the cluster form: its dense solve, nc^2 FP64
+// multiply-adds, is FP64-bound on one SM - 306 DOFs took 78 us in one block.)
+constexpr int kTail1MaxNc = 128;
+
 template <typename T>
 bool tail1_layout(TailArgs<T>& a) {
+  if (a.nc > kTail1MaxNc) return false;
   unsigned long long off = 0;
   for (int k = 0; k < a.nl; ++k) {
     const unsigned long long n = (unsigned long long)a.d[k].dofs();
