@@ -121,10 +121,10 @@ topo_status topo_set_graph_mode(topo_solver* s, int mode);
  * first two sweeps of every coarse level in one kernel.  Both settings give the same bits.  3D
  * and Chebyshev systems ignore the setting. */
 topo_status topo_set_vcycle_fusion(topo_solver* s, int on);
-/* Arithmetic of the outer operator q = K(x) p of Algorithm PCG on the 2D finest level of K
- * systems: 0 = FP64; 1 = pairs of FP32 values (hi + lo, about 48 significant bits, FP64 in and
- * out, p^T q accumulated in pairs), which GB300 runs several times faster than FP64.  Default: 1
- * for mixed-precision solvers, 0 for FP64 solvers; other systems always use FP64.  Inputs of
+/* Arithmetic of the outer operator q = K(x) p of Algorithm PCG on the finest level of K systems
+ * (2D Q1 and 3D hex): 0 = FP64; 1 = pairs of FP32 values (hi + lo, about 48 significant bits,
+ * FP64 in and out, p^T q accumulated in pairs), which GB300 runs several times faster than FP64.
+ * Default: 1 for mixed-precision solvers, 0 for FP64 solvers; IP systems always use FP64.  Inputs of
  * magnitude below 2^-100 lose their low part and values beyond float range give a breakdown.
  * Other modes -> E_INVALID_ARG. */
 topo_status topo_set_outer_precision(topo_solver* s, int mode);

@@ -22,6 +22,7 @@
 #include <cmath>
 #include <vector>
 
+#include "pairs.cuh"
 #include "topo_internal.cuh"
 
 namespace topo {
@@ -260,6 +261,130 @@ __global__ void __launch_bounds__(kThreads) k_hex_gather_dot(Dims d, const doubl
   }
 }
 
+// ---- The same operator in pair-of-FP32 arithmetic (the mixed solver's outer operator) -------
+// FP64 runs at about 2 operations per clock per SM on this part, so k_hex_elem is FP64-bound at
+// ~178 operations per element.  Here every value is a float pair (about 48 bits): the three
+// butterflies and the Khat blocks are the templates above on PairNum, p is split with integer
+// operations, the element forces are stored as pairs (8 bytes, as the FP64 ones), the node sums
+// run in pairs and q is rebuilt in FP64 with one add per DOF; p^T q is accumulated in pairs.
+__global__ void __launch_bounds__(kThreads) k_hex_elem_df(Dims d, HexK<PairNum> k,
+                                                          const float2* __restrict__ xdf,
+                                                          const double* __restrict__ v,
+                                                          float2* __restrict__ R,
+                                                          const CgScalars* __restrict__ sc) {
+  pdl_prologue();
+  const int rhs = blockIdx.y;
+  if (sc && sc[rhs].done) return;
+  const long long m = d.elems();
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  const long long n = d.dofs();
+  v += rhs * n;
+  R += rhs * 24 * m;
+  int ex, ey, ez;
+  node_coords(e, d.nx, d.ny, 3, ex, ey, ez);
+  const int nnx = d.nx + 1, nny = d.ny + 1;
+  PairNum nu[2][2][2], nv[2][2][2], nw[2][2][2];
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const long long nid = (ex + i) + (long long)nnx * ((ey + j) + (long long)nny * (ez + kk));
+        nu[kk][j][i] = {df_from_double(__ldg(v + 3 * nid))};
+        nv[kk][j][i] = {df_from_double(__ldg(v + 3 * nid + 1))};
+        nw[kk][j][i] = {df_from_double(__ldg(v + 3 * nid + 2))};
+      }
+  PairNum tu[7], tv[7], tw[7];
+  wht_fwd(nu, tu);
+  wht_fwd(nv, tv);
+  wht_fwd(nw, tw);
+  const float2 xe = __ldg(xdf + e);
+  hex_khat(k, PairNum{{xe.x, xe.y}}, tu, tv, tw);
+  wht_inv(tu, nu);
+  wht_inv(tv, nv);
+  wht_inv(tw, nw);
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int i = hx_ox(a), j = hx_oy(a), kk = hx_oz(a);
+    R[(long long)(a * 3 + 0) * m + e] = make_float2(nu[kk][j][i].v.h, nu[kk][j][i].v.l);
+    R[(long long)(a * 3 + 1) * m + e] = make_float2(nv[kk][j][i].v.h, nv[kk][j][i].v.l);
+    R[(long long)(a * 3 + 2) * m + e] = make_float2(nw[kk][j][i].v.h, nw[kk][j][i].v.l);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_hex_gather_dot_df(Dims d, const float2* __restrict__ R,
+                                                                const double* __restrict__ p,
+                                                                double* __restrict__ q,
+                                                                const uint8_t* __restrict__ fixed,
+                                                                double* partials,
+                                                                unsigned* counters,
+                                                                CgScalars* sc) {
+  pdl_prologue();
+  const int rhs = blockIdx.y;
+  if (sc[rhs].done) return;
+  const long long m = d.elems();
+  const long long nodes = d.nodes();
+  const long long n = nodes * 3;
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  p += rhs * n;
+  q += rhs * n;
+  R += rhs * 24 * m;
+  f2 part = {0.0f, 0.0f};
+  if (node < nodes) {
+    int i, j, kk;
+    node_coords(node, d.nx + 1, d.ny + 1, 3, i, j, kk);
+    f2 acc[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+    for (int s = 0; s < 8; ++s) {
+      const int dx = s & 1, dy = (s >> 1) & 1, dz = s >> 2;
+      const int ex = i - 1 + dx, ey = j - 1 + dy, ez = kk - 1 + dz;
+      if (ex < 0 || ex >= d.nx || ey < 0 || ey >= d.ny || ez < 0 || ez >= d.nz) continue;
+      const int lx = 1 - dx, ly = 1 - dy, lz = 1 - dz;
+      const int loc = (ly ? (lx ? 2 : 3) : (lx ? 1 : 0)) + 4 * lz;
+      const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float2 r = __ldg(R + (long long)(loc * 3 + c) * m + e);
+        acc[c] = df_add(acc[c], f2{r.x, r.y});
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long id = 3 * node + c;
+      if (fixed[id]) acc[c] = f2{0.0f, 0.0f};
+      q[id] = double_from_float(acc[c].h) + double_from_float(acc[c].l);
+      part = df_add(part, df_mul(df_from_double(p[id]), acc[c]));
+    }
+  }
+  const double bs = block_sum_hex(double_from_float(part.h) + double_from_float(part.l));
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[(long long)rhs * gridDim.x + blockIdx.x] = bs;
+    __threadfence();
+    last = (atomicAdd(&counters[rhs], 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  double s = 0.0;
+  for (unsigned t = threadIdx.x; t < gridDim.x; t += blockDim.x)
+    s += __ldcg(partials + (long long)rhs * gridDim.x + t);
+  s = block_sum_hex(s);
+  if (threadIdx.x == 0) {
+    CgScalars& S = sc[rhs];
+    S.pq = s;
+    const double alpha = S.ry / s;
+    if (!(s > 0.0) || !isfinite(alpha)) {
+      S.status = TOPO_E_BREAKDOWN;
+      S.done = 1;
+      S.alpha = 0.0;
+    } else {
+      S.alpha = alpha;
+    }
+    counters[rhs] = 0;
+  }
+}
+
 }  // namespace
 
 bool hex_coefficients(const double* K0, HexCoef& c) {
@@ -351,6 +476,22 @@ cudaError_t launch_hex_apply_dot(const Dims& d, const HexCoef& c, const double* 
   if (e != cudaSuccess) return e;
   topo::launch(k_hex_gather_dot, dim3(blocks_for(d.nodes()), nrhs), kThreads, 0, st, d,
                (const double*)R, v, y, fixed, partials, counters, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hex_apply_dot_df(const Dims& d, const HexCoef& c, const float2* xdf,
+                                    const double* v, double* y, const uint8_t* fixed, int nrhs,
+                                    double* R, double* partials, unsigned* counters, CgScalars* sc,
+                                    cudaStream_t st) {
+  const HexK<PairNum> k{{df_const(c.a)}, {df_const(c.b)}, {df_const(c.s)}, {df_const(c.p)},
+                        {df_const(c.q)}, {df_const(c.d)}, {df_const(c.e)}, {df_const(c.h)}};
+  float2* Rp = reinterpret_cast<float2*>(R);  // (pairs in the FP64 buffer: the same bytes)
+  topo::launch(k_hex_elem_df, dim3(blocks_for(d.elems()), nrhs), kThreads, 0, st, d, k, xdf, v,
+               Rp, (const CgScalars*)sc);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  topo::launch(k_hex_gather_dot_df, dim3(blocks_for(d.nodes()), nrhs), kThreads, 0, st, d,
+               (const float2*)Rp, v, y, fixed, partials, counters, sc);
   return cudaGetLastError();
 }
 

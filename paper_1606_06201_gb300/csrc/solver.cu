@@ -514,6 +514,9 @@ topo_status cg_iteration(topo_solver* s, int slot, double tol, int max_iter) {
   } else if (s->q1_ok) {
     TOPO_CUDA(launch_q1_apply_dot(l0.d.nx, l0.d.ny, s->q1, s->x, s->p, s->q, l0.fixed, s->nrhs,
                                   s->partials, s->counters, s->sc, s->st));
+  } else if (s->hex_ok && s->outer_df && s->xdf) {
+    TOPO_CUDA(launch_hex_apply_dot_df(l0.d, s->hex, s->xdf, s->p, s->q, l0.fixed, s->nrhs,
+                                      s->hexR, s->partials, s->counters, s->sc, s->st));
   } else if (s->hex_ok) {
     TOPO_CUDA(launch_hex_apply_dot(l0.d, s->hex, s->x, s->p, s->q, l0.fixed, s->nrhs, s->hexR,
                                    s->partials, s->counters, s->sc, s->st));
@@ -1086,7 +1089,7 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   const long long n = s->L[0].n + (arrow ? 2 : 0);
   TOPO_TRY(s->alloc(&s->x, m));
   if (s->hex_ok) TOPO_TRY(s->alloc(&s->hexR, (size_t)m * 24 * nrhs));
-  if (s->q1_ok && !arrow) {  // pair-arithmetic outer operator: default for mixed solvers
+  if ((s->q1_ok || s->hex_ok) && !arrow) {  // pair-arithmetic outer operator: default for mixed
     TOPO_TRY(s->alloc(&s->xdf, m));
     s->outer_df = s->prec == TOPO_MIXED ? 1 : 0;
   }

@@ -323,6 +323,11 @@ cudaError_t launch_hex_apply_dot(const Dims& d, const HexCoef& c, const double* 
                                  double* y, const uint8_t* fixed, int nrhs, double* R,
                                  double* partials, unsigned* counters, CgScalars* sc,
                                  cudaStream_t st);
+// The same in pair-of-FP32 arithmetic (about 48 bits; xdf: the densities as float pairs).
+cudaError_t launch_hex_apply_dot_df(const Dims& d, const HexCoef& c, const float2* xdf,
+                                    const double* v, double* y, const uint8_t* fixed, int nrhs,
+                                    double* R, double* partials, unsigned* counters, CgScalars* sc,
+                                    cudaStream_t st);
 // Fused pairs of finest-level V-cycle steps (same bits as the separate steps): mode 4 = the first
 // two Jacobi sweeps from zero (b -> y); mode 5 = prolongation and correction t + P zc followed by
 // one Jacobi sweep (t, zc -> y).  zc: the first coarse level's vector.

@@ -353,6 +353,33 @@ def test_pair_arithmetic_outer_operator_reaches_tight_tolerances(precision):
     assert rel_err(res[1][0], res[0][0]) <= 1e-9
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pair_arithmetic_hex_outer_operator(precision):
+    """The 3D Walsh-Hadamard outer operator in float pairs, batched (3 load cases): solves to
+    1e-11 whose true residual by the oracle's sparse matrix is at that level, and the FP64
+    operator's iteration counts (within one) and solutions (to 1e-9)."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny, nz, levels = 16, 8, 8, 3
+    cfg = W.random_field_3d(nx, ny, nz, n_rhs=3)
+    K, free, _ = oracle_K_free(nx, ny, nz, cfg["x"], cfg["fixed"].astype(bool))
+    res = {}
+    for mode in (0, 1):
+        s = topo.Solver(nx, ny, nz, fixed=cfg["fixed"], levels=levels, precision=precision, nrhs=3)
+        s.set_outer_precision(mode)
+        s.set_density(dev(torch, cfg["x"]))
+        U, info = s.solve(dev(torch, cfg["f"]), tol=1e-11)
+        Uh = host(U)
+        for r in range(3):
+            f = cfg["f"][r]
+            rr = np.linalg.norm(f[free] - K @ Uh[r][free]) / np.linalg.norm(f[free])
+            assert rr <= 3e-11, (mode, r, rr)
+        res[mode] = (Uh, info.iterations)
+        s.close()
+    assert abs(res[0][1] - res[1][1]) <= 1
+    assert rel_err(res[1][0], res[0][0]) <= 1e-9
+
+
 @pytest.mark.parametrize("precision,nrhs", [(0, 1), (1, 1), (1, 3)])
 def test_solve_from_host_buffers_matches_device_solve(precision, nrhs):
     """topo_solve_host (copies in and out inside the call, b copied while the hierarchy is built)
