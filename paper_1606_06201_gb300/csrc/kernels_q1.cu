@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, int 
     const int j1 = min(j0 + rows, ny + 1);
     const V2* v2 = reinterpret_cast<const V2*>(v);
     const V2* b2 = reinterpret_cast<const V2*>(b);
-    const long long rs = nx + 1;  // node row stride
+    const int rs = nx + 1;  // node row stride (grids hold < 2^31 DOFs: 32-bit indices)
     V2 zero;
     zero.x = T(0);
     zero.y = T(0);
@@ -152,12 +152,12 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, int 
     {
       const int ey = j0 - 1;  // first iteration: element row j0 - 1, no output
       if (MODE != 3 && col_ok && ey + 1 <= ny) pt_n = v2[c + rs * (ey + 1)];
-      if (el_col && ey >= 0 && ey < ny) xe_n = x[c + (long long)nx * ey];
+      if (el_col && ey >= 0 && ey < ny) xe_n = x[c + nx * ey];
       if (ey + 1 < j1) {  // second iteration: element row j0, output node row j0
         if (MODE != 3 && col_ok && ey + 2 <= ny) pt_nn = v2[c + rs * (ey + 2)];
-        if (el_col && ey + 1 < ny) xe_nn = x[c + (long long)nx * (ey + 1)];
+        if (el_col && ey + 1 < ny) xe_nn = x[c + nx * (ey + 1)];
         if (out_lane) {
-          const long long nn = c + rs * (ey + 1);
+          const int nn = c + rs * (ey + 1);
           fx_nn = *reinterpret_cast<const uint16_t*>(fixed + 2 * nn);
           if (MODE != 0) bb_nn = b2[nn];
           if (DOT == 2) rr_nn = reinterpret_cast<const double2*>(rdot)[nn];
@@ -180,9 +180,9 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, int 
       xe_nn = T(0);
       if (ey + 2 < j1) {  // loads of the iteration after next: element row ey + 2
         if (MODE != 3 && col_ok && ey + 3 <= ny) pt_nn = v2[c + rs * (ey + 3)];
-        if (el_col && ey + 2 < ny) xe_nn = x[c + (long long)nx * (ey + 2)];
+        if (el_col && ey + 2 < ny) xe_nn = x[c + nx * (ey + 2)];
         if (out_lane) {
-          const long long nn = c + rs * (ey + 2);
+          const int nn = c + rs * (ey + 2);
           fx_nn = *reinterpret_cast<const uint16_t*>(fixed + 2 * nn);
           if (MODE != 0) bb_nn = b2[nn];
           if (DOT == 2) rr_nn = reinterpret_cast<const double2*>(rdot)[nn];
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, int 
       const T xpair = xe + (lane >= 1 ? xl : T(0));
       if (ey >= j0 && out_lane) {
         const T qu = cu + ru[0] + l1u, qv = cv + rv[0] + l1v;
-        const long long node = c + rs * ey;
+        const int node = c + rs * ey;
         V2 out;
         if (MODE == 0) {
           out.x = qu;
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_resrestrict(int nx, int ny
   const int j0 = max(2 * J0 - 1, 0), j1 = min(2 * J1 - 1, ny) + 1;  // fine rows [j0, j1)
   const V2* v2 = reinterpret_cast<const V2*>(v);
   const V2* b2 = reinterpret_cast<const V2*>(b);
-  const long long rs = nx + 1;
+  const int rs = nx + 1;
   V2 zero;
   zero.x = T(0);
   zero.y = T(0);
@@ -336,12 +336,12 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_resrestrict(int nx, int ny
   {
     const int ey = j0 - 1;
     if (col_ok && ey + 1 <= ny) pt_n = v2[c + rs * (ey + 1)];
-    if (el_col && ey >= 0 && ey < ny) xe_n = x[c + (long long)nx * ey];
+    if (el_col && ey >= 0 && ey < ny) xe_n = x[c + nx * ey];
     if (ey + 1 < j1) {
       if (col_ok && ey + 2 <= ny) pt_nn = v2[c + rs * (ey + 2)];
-      if (el_col && ey + 1 < ny) xe_nn = x[c + (long long)nx * (ey + 1)];
+      if (el_col && ey + 1 < ny) xe_nn = x[c + nx * (ey + 1)];
       if (out_lane) {
-        const long long nn = c + rs * (ey + 1);
+        const int nn = c + rs * (ey + 1);
         fx_nn = *reinterpret_cast<const uint16_t*>(fixed + 2 * nn);
         bb_nn = b2[nn];
       }
@@ -362,9 +362,9 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_resrestrict(int nx, int ny
     xe_nn = T(0);
     if (ey + 2 < j1) {
       if (col_ok && ey + 3 <= ny) pt_nn = v2[c + rs * (ey + 3)];
-      if (el_col && ey + 2 < ny) xe_nn = x[c + (long long)nx * (ey + 2)];
+      if (el_col && ey + 2 < ny) xe_nn = x[c + nx * (ey + 2)];
       if (out_lane) {
-        const long long nn = c + rs * (ey + 2);
+        const int nn = c + rs * (ey + 2);
         fx_nn = *reinterpret_cast<const uint16_t*>(fixed + 2 * nn);
         bb_nn = b2[nn];
       }
@@ -481,8 +481,8 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_fused(int nx, int ny, int 
   const bool xleft0 = MODE == 4 && lane == 0 && c - 1 >= 0 && c - 1 < nx;
   const int j0 = ws * rows;
   const int j1 = min(j0 + rows, ny + 1);
-  const long long rs = nx + 1;
-  const long long crs = nx / 2 + 1;
+  const int rs = nx + 1;
+  const int crs = nx / 2 + 1;
   const V2* b2 = reinterpret_cast<const V2*>(b);
   const V2* t2 = reinterpret_cast<const V2*>(t);
   const V2* zc2 = reinterpret_cast<const V2*>(zc);
@@ -503,10 +503,10 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_fused(int nx, int ny, int 
     R.xl0 = T(0);
     R.fx = 0;
     if (r < 0 || r > ny) return;
-    if (xcol && r < ny) R.xe = x[c + (long long)nx * r];
-    if (xleft0 && r < ny) R.xl0 = x[c - 1 + (long long)nx * r];
+    if (xcol && r < ny) R.xe = x[c + nx * r];
+    if (xleft0 && r < ny) R.xl0 = x[c - 1 + nx * r];
     if (!col_ok) return;
-    const long long nd = c + rs * r;
+    const int nd = c + rs * r;
     R.fx = *reinterpret_cast<const uint16_t*>(fixed + 2 * nd);
     R.b = b2[nd];
     if (MODE == 5) {
@@ -684,7 +684,7 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep_df(int nx, int ny, i
     const int j0 = ws * rows;
     const int j1 = min(j0 + rows, ny + 1);
     const double2* v2 = reinterpret_cast<const double2*>(v);
-    const long long rs = nx + 1;
+    const int rs = nx + 1;
     const f2 z = {0.0f, 0.0f};
     f2 pbu = z, pbv = z;
     if (col_ok && j0 >= 1) {
@@ -699,10 +699,10 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep_df(int nx, int ny, i
     {
       const int ey = j0 - 1;
       if (col_ok && ey + 1 <= ny) pt_n = v2[c + rs * (ey + 1)];
-      if (el_col && ey >= 0 && ey < ny) xe_n = xdf[c + (long long)nx * ey];
+      if (el_col && ey >= 0 && ey < ny) xe_n = xdf[c + nx * ey];
       if (ey + 1 < j1) {
         if (col_ok && ey + 2 <= ny) pt_nn = v2[c + rs * (ey + 2)];
-        if (el_col && ey + 1 < ny) xe_nn = xdf[c + (long long)nx * (ey + 1)];
+        if (el_col && ey + 1 < ny) xe_nn = xdf[c + nx * (ey + 1)];
         if (out_lane) fx_nn = *reinterpret_cast<const uint16_t*>(fixed + 2 * (c + rs * (ey + 1)));
       }
     }
@@ -718,7 +718,7 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep_df(int nx, int ny, i
       xe_nn = make_float2(0.0f, 0.0f);
       if (ey + 2 < j1) {
         if (col_ok && ey + 3 <= ny) pt_nn = v2[c + rs * (ey + 3)];
-        if (el_col && ey + 2 < ny) xe_nn = xdf[c + (long long)nx * (ey + 2)];
+        if (el_col && ey + 2 < ny) xe_nn = xdf[c + nx * (ey + 2)];
         if (out_lane) fx_nn = *reinterpret_cast<const uint16_t*>(fixed + 2 * (c + rs * (ey + 2)));
       }
       const f2 uu[4] = {pbu, shfl_dn_df(pbu), shfl_dn_df(ptu), ptu};
@@ -842,8 +842,8 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, int
   const int j0 = ws * rows;
   const int j1 = min(j0 + rows, ny + 1);
   const int fnx = 2 * nx;
-  const long long rs = nx + 1;
-  const long long crs = nx / 2 + 1;
+  const int rs = nx + 1;
+  const int crs = nx / 2 + 1;
   const float2* v2 = reinterpret_cast<const float2*>(v);
   const float2* zc2 = reinterpret_cast<const float2*>(zc);
   const float2 z2 = make_float2(0.f, 0.f);
@@ -869,11 +869,11 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, int
       R.z11 = zc2[i1 + crs * q1];
     }
     if (MODE != 3 && el_col && e >= 0 && e < ny) {
-      R.xb = *reinterpret_cast<const float2*>(xf + 2 * c + (long long)fnx * (2 * e));
-      R.xt = *reinterpret_cast<const float2*>(xf + 2 * c + (long long)fnx * (2 * e + 1));
+      R.xb = *reinterpret_cast<const float2*>(xf + 2 * c + fnx * (2 * e));
+      R.xt = *reinterpret_cast<const float2*>(xf + 2 * c + fnx * (2 * e + 1));
     }
     if (e >= (FUSED ? 0 : j0) && e <= ny && node_data) {
-      const long long node = c + rs * e;
+      const int node = c + rs * e;
       R.fx = *reinterpret_cast<const uint16_t*>(fixed + 2 * node);
       if (MODE != 0) R.bb = reinterpret_cast<const float2*>(b)[node];
       if (MODE != 0 && MODE != 1) R.di = reinterpret_cast<const float2*>(invd)[node];
@@ -976,7 +976,7 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, int
     const float l2u = shfl_up1(R[2][0]), l2v = shfl_up1(R[2][1]);
     if (ey >= j0 && out_lane) {
       const float qu = cu + R[0][0] + l1u, qv = cv + R[0][1] + l1v;
-      const long long node = c + rs * ey;
+      const int node = c + rs * ey;
       float2 out;
       if (MODE == 0) {
         out.x = qu;
