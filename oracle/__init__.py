@@ -17,6 +17,7 @@ fe        grid numbering, element stiffness K0 (2D Q1 plane stress, 3D trilinear
 linsolve  exact SPD solves: banded Cholesky, bordering for the arrow matrix Z
 mg        explicit prolongation, Galerkin coarse operators, Algorithm MG, Algorithm PCG
 ip        primal-dual interior-point method (Sec. 2-3, Eq. (nwt), (nwtr), (nwtr2))
+simp      SIMP model with the density filter and its IP method (Sec. 9)
 oc        OC / damped OC / averaged OC (Sec. 4)
 grad      adjoint gradient of a linear functional of u
 

@@ -137,13 +137,16 @@ def kkt_criterion(prob, z, s, r):
 
 
 def ip_run(prob, sigma=0.2, tau_nwt=0.1, tau_ip=1e-8, frac=0.9, step_rule="all",
-           max_newton=500, record=False, stop_rule="barrier", tau_kkt=1e-6):
+           max_newton=500, record=False, stop_rule="barrier", tau_kkt=1e-6, methods=None):
     """Sec. 3.1 algorithm.  Returns (z, info); info counts IP iterations (barrier reductions),
     Newton steps and linear solves (feval), and optionally the per-step trajectory.
     stop_rule "barrier": stop once max(s, r) <= tau_IP (Eq. (crit:ip)); "kkt": stop once the
     scaled KKT residual of the Remark in Sec. 3.4 (kkt_criterion, after each Newton step) is
     <= tau_kkt.  (The Remark names no tolerance of its own; at tau_IP = 1e-8 the tilde Res3
-    term stalls near 1e-7, from the rounding of Res4 / x at tiny x, so the test takes its own.)"""
+    term stalls near 1e-7, from the rounding of Res4 / x at tiny x, so the test takes its own.)
+    ``methods`` = (direction, Newton criterion, KKT criterion) of another model of the same
+    form (the SIMP model of Sec. 9); the default is this module's VTS functions."""
+    direction, criterion, kkt = methods or (newton_direction, newton_criterion, kkt_criterion)
     m = prob.m
     x = np.full(m, prob.V / m)
     u = prob.solve_u(x)
@@ -151,17 +154,17 @@ def ip_run(prob, sigma=0.2, tau_nwt=0.1, tau_ip=1e-8, frac=0.9, step_rule="all",
     s = r = 1.0
     info = dict(newton=0, ip=0, feval=1, traj=[])
     while info["newton"] < max_newton:
-        d, _ = newton_direction(prob, z, s, r)
+        d, _ = direction(prob, z, s, r)
         info["feval"] += 1
         alpha = step_length(prob, z, d, frac, step_rule)
         z = [z[0] + alpha * d[0], z[1] + alpha * d[1], z[2] + alpha * d[2],
              z[3] + alpha * d[3], z[4] + alpha * d[4]]
         info["newton"] += 1
-        crit = newton_criterion(prob, z, s, r)
+        crit = criterion(prob, z, s, r)
         if record:
             info["traj"].append(dict(u=z[0].copy(), lam=z[1], x=z[2].copy(), phi=z[3].copy(),
                                      psi=z[4].copy(), s=s, r=r, alpha=alpha, crit=crit))
-        if stop_rule == "kkt" and kkt_criterion(prob, z, s, r) <= tau_kkt:
+        if stop_rule == "kkt" and kkt(prob, z, s, r) <= tau_kkt:
             break
         if crit <= tau_nwt:
             s *= sigma
