@@ -64,7 +64,7 @@ typedef struct {
   int precision;        /* topo_precision */
   int nu1, nu2;         /* pre/post smoothing sweeps (>= 0) */
   double omega;         /* Jacobi damping, (0, 1] */
-  int max_iter;         /* CG iteration cap (the paper uses 1000, Sec. 9.1) */
+  int max_iter;         /* CG iteration cap (the paper uses 1000, Sec. 8.1) */
   int nrhs;             /* right-hand sides solved together (>= 1) */
   int flexible;         /* 1: Polak-Ribiere beta (safeguard for the FP32 V-cycle) */
   int generic_kernels;  /* 1: use the generic element-matrix kernels on the 2D finest level
@@ -238,7 +238,7 @@ typedef struct {
   double cg_tol_init;  /* relative residual of the initial K(x) u = f solve (<= 0: cg_tol) */
   double cg_tol_factor; /* the Z systems of major iteration k (k barrier reductions so far) are
                            solved to cg_tol * cg_tol_factor^k: 1 keeps cg_tol fixed, 0.5 is the
-                           "CG tol decreasing" variant of Sec. 9.1 (tab:IP); in (0, 1] */
+                           "CG tol decreasing" variant of Sec. 8.1 (tab:IP); in (0, 1] */
   int stop_rule;       /* 0: stop once max(s, r) <= tau_ip (Eq. (crit:ip)); 1: stop once the scaled
                           KKT residual of the Remark in Sec. 3.4 is <= tau_kkt after a Newton step:
                           ||Res1||/||f|| + ||tilde Res3||/(||phi|| + ||psi||)
@@ -265,6 +265,21 @@ topo_status topo_ip_destroy(topo_ip* ip);
 topo_status topo_ip_set_stream(topo_ip* ip, void* cuda_stream);
 /* topo_set_vcycle_fusion on both solvers of the IP (the same bits either way). */
 topo_status topo_ip_set_vcycle_fusion(topo_ip* ip, int on);
+/* Switches the problem to the SIMP model with the density filter (Sec. 9).  The equilibrium is
+   hat K(x~) u = f with hat K(x~) = sum_i x~_i^p K_i and x~ = W x.  hat W_ij = max(0, rmin - dist(i, j)),
+   with dist the Manhattan distance of the element centres in element widths.  Each column of W is
+   hat W's column divided by its sum, as Sec. 9 prints it, so sum x~ = sum x.  The volume
+   constraint and the bounds act on x.  The Newton systems are Eq. (nwtr)/(nwtr2) with B(u)
+   replaced by hat B(u) = B(u) diag(p x~^(p-1)) W; the x-x second derivative of the non-convex
+   problem is left out, as in the paper's method.  The outer CG applies that Z exactly (two filter
+   passes per product).  The V-cycle's hierarchy is built from its element-local approximation,
+   which keeps the row sums of W D^{-1} W^T (= W D^{-1} e) as element weights in place of the matrix:
+   exact on the lambda row and column.  Call once, before topo_ip_init.
+   p in [1, 8], rmin in [1, 9] (the stencil reaches |o|_1 <= ceil(rmin) - 1); otherwise
+   TOPO_E_INVALID_ARG.  p = 1 and rmin = 1 (W = I) is the convex problem. */
+topo_status topo_ip_set_simp(topo_ip* ip, double p, double rmin);
+/* xt [device, m]: x~ = W x at the current iterate (x itself without topo_ip_set_simp).  Synchronous. */
+topo_status topo_ip_filtered_density(topo_ip* ip, double* xt);
 /* x = V/m, u = K(x)^{-1} f, lambda = 1, phi = psi = e, s = r = 1 (Sec. 3.1). */
 topo_status topo_ip_init(topo_ip* ip, const topo_ip_opts* opts);
 /* One Newton step (Sec. 3.1 steps 1-4); info after the step. */
@@ -302,7 +317,7 @@ enum { TOPO_OC_PLAIN = 0, TOPO_OC_DOC = 1, TOPO_OC_AOC = 2 };
 typedef struct {
   int variant;         /* TOPO_OC_PLAIN, TOPO_OC_DOC or TOPO_OC_AOC */
   double q;            /* DOC damping exponent (Sec. 4.2: 1/2) */
-  double xlow;         /* lower bound keeping K(x) nonsingular (Sec. 9.2: 1e-6) */
+  double xlow;         /* lower bound keeping K(x) nonsingular (Sec. 8.2: 1e-6) */
   double lam_hi;       /* initial upper end of the bisection (Sec. 4.1: 1e4) */
   double tau_lambda;   /* bisection tolerance (Sec. 4.1: 1e-11) */
   double tau_oc;       /* stop when |f^T u_k - f^T u_{k-1}| <= tau_oc (Eq. (OCstop): 1e-5) */

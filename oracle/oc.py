@@ -5,7 +5,7 @@ with the overall stopping rule Eq. (OCstop), each linear system solved exactly.
 Readings of the paper used here:
   * Algorithm OC step 3(c) writes "x = x^NEW" inside the bisection loop; the old x stays fixed
     during the bisection and x becomes x^NEW(lambda) of the last midpoint evaluated.
-  * A lower bound xlow > 0 keeps K(x) nonsingular (Sec. 9.2): x^NEW = min(max(x E / lambda,
+  * A lower bound xlow > 0 keeps K(x) nonsingular (Sec. 8.2): x^NEW = min(max(x E / lambda,
     xlow), xbar) with the element energy E_i = u^T K_i u (no factor 1/2, Sec. 4.1).
   * Bisection decisions compare the correctly rounded sum of x^NEW (math.fsum) with V:
     "sum > V" raises the lower end, otherwise the upper end is lowered, exactly as printed.

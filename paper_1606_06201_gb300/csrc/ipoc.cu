@@ -29,6 +29,8 @@ struct topo_ip {
   unsigned* counter = nullptr;
   double fnorm = 0.0;
   double kkt = NAN;  // scaled KKT residual after the last Newton step
+  bool simp_on = false;  // SIMP model with the density filter (Sec. 9)
+  SimpArgs sa{};
   int newton = 0, ip_iters = 0, feval = 0, cg_iters = 0;
   bool done = false;
   std::vector<void*> allocs;
@@ -100,7 +102,19 @@ topo_status ip_residuals(topo_ip* a) {
   topo_solver* Z = a->Z;
   TOPO_CUDA(launch_ip_residuals(a->d, Z->K0, a->u, a->x, a->phi, a->psi, a->f, Z->L[0].fixed,
                                 a->ip, a->g, a->tR3, a->Dinv, a->t, a->rhs, Z->L[0].w,
-                                Z->L[0].invd, a->partials, a->counter, Z->st));
+                                Z->L[0].invd, a->partials, a->counter, Z->st,
+                                a->simp_on ? &a->sa : nullptr));
+  return TOPO_OK;
+}
+
+// The stiffness coefficients of the current design: x, or rho = (W x)^p for the SIMP model.
+topo_status stiffness_coefficients(topo_ip* a, double* dst, cudaStream_t st) {
+  const double* src = a->x;
+  if (a->simp_on) {
+    TOPO_CUDA(launch_simp_density(a->d, a->sa, a->x, st));
+    src = a->sa.rho;
+  }
+  TOPO_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * a->m, cudaMemcpyDeviceToDevice, st));
   return TOPO_OK;
 }
 
@@ -239,6 +253,70 @@ topo_status topo_ip_set_vcycle_fusion(topo_ip* a, int on) {
   return topo_set_vcycle_fusion(a->Z, on);
 }
 
+topo_status topo_ip_set_simp(topo_ip* a, double p, double rmin) {
+  if (!a) return TOPO_E_INVALID_ARG;
+  if (!(p >= 1.0 && p <= 8.0) || !(rmin >= 1.0 && rmin <= (double)(kSimpMaxR + 1))) {
+    topo::set_error("topo_ip_set_simp: p must lie in [1, 8] and rmin in [1, " +
+                    std::to_string(kSimpMaxR + 1) + "]");
+    return TOPO_E_INVALID_ARG;
+  }
+  if (a->simp_on) {
+    topo::set_error("topo_ip_set_simp: the SIMP model is already set on this problem");
+    return TOPO_E_INVALID_ARG;
+  }
+  StreamGuard gd(a->Z);
+  const long long m = a->m;
+  SimpArgs& sa = a->sa;
+  double* invS = nullptr;
+  topo_status s2 = TOPO_OK;
+  s2 = s2 ? s2 : a->alloc(&invS, m);
+  s2 = s2 ? s2 : a->alloc(&sa.xt, m);
+  s2 = s2 ? s2 : a->alloc(&sa.rho, m);
+  s2 = s2 ? s2 : a->alloc(&sa.c, m);
+  s2 = s2 ? s2 : a->alloc(&sa.E, m);
+  s2 = s2 ? s2 : a->alloc(&sa.e3, m);
+  s2 = s2 ? s2 : a->alloc(&sa.gh, m * a->ne);
+  s2 = s2 ? s2 : a->alloc(&sa.th, m);
+  s2 = s2 ? s2 : a->alloc(&sa.Dm, m);
+  s2 = s2 ? s2 : a->alloc(&sa.ea, m);
+  s2 = s2 ? s2 : a->alloc(&sa.eb, m);
+  if (s2 != TOPO_OK) return s2;
+  sa.p = p;
+  sa.rmin = rmin;
+  sa.R = (int)std::ceil(rmin) - 1;
+  sa.invS = invS;
+  TOPO_CUDA(launch_filter_colsum(a->d, rmin, sa.R, invS, a->Z->st));
+  TOPO_CUDA(cudaStreamSynchronize(a->Z->st));
+  // the hierarchy of Z takes the element-local columns c_e g_e and the row sums of W D^-1 W^T as
+  // weights; the outer CG applies the exact Z
+  topo_solver* Z = a->Z;
+  Z->g = sa.gh;
+  Z->Dinv = sa.Dm;
+  Z->simp.on = true;
+  Z->simp.rmin = rmin;
+  Z->simp.R = sa.R;
+  Z->simp.invS = invS;
+  Z->simp.Dinv = a->Dinv;
+  Z->simp.ea = sa.ea;
+  Z->simp.eb = sa.eb;
+  a->simp_on = true;
+  return TOPO_OK;
+}
+
+topo_status topo_ip_filtered_density(topo_ip* a, double* xt) {
+  if (!a || !xt) return TOPO_E_INVALID_ARG;
+  StreamGuard gd(a->Z);
+  cudaStream_t st = a->Z->st;
+  if (a->simp_on) {
+    TOPO_CUDA(launch_simp_density(a->d, a->sa, a->x, st));
+    TOPO_CUDA(cudaMemcpyAsync(xt, a->sa.xt, sizeof(double) * a->m, cudaMemcpyDeviceToDevice, st));
+  } else {
+    TOPO_CUDA(cudaMemcpyAsync(xt, a->x, sizeof(double) * a->m, cudaMemcpyDeviceToDevice, st));
+  }
+  TOPO_CUDA(cudaStreamSynchronize(st));
+  return TOPO_OK;
+}
+
 // The options the IP driver cannot run with.
 topo_status check_ip_opts(const topo_ip_opts* o, const char* where) {
   if (!(o->cg_tol > 0.0) || !(o->cg_tol_factor > 0.0 && o->cg_tol_factor <= 1.0) ||
@@ -273,7 +351,7 @@ topo_status topo_ip_init(topo_ip* a, const topo_ip_opts* o) {
   topo_solver* K = a->K;
   {
     StreamGuard gk(K->st, st, K->ev_in, K->ev_out);
-    TOPO_CUDA(cudaMemcpyAsync(K->x, a->x, sizeof(double) * a->m, cudaMemcpyDeviceToDevice, K->st));
+    TOPO_TRY(stiffness_coefficients(a, K->x, K->st));
     TOPO_TRY(topo::solver_build(K));
     topo_solve_info si{};
     topo_status s = topo::solver_solve(K, a->f, a->u, o->cg_tol_init > 0 ? o->cg_tol_init : o->cg_tol,
@@ -299,7 +377,8 @@ topo_status topo_ip_step(topo_ip* a, const topo_ip_opts* o, topo_ip_info* info) 
   cudaStream_t st = Z->st;
   // residuals, Z data and right-hand side at z with the current (s, r)
   TOPO_TRY(ip_residuals(a));
-  TOPO_CUDA(cudaMemcpyAsync(Z->x, a->x, sizeof(double) * a->m, cudaMemcpyDeviceToDevice, st));
+  TOPO_CUDA(cudaMemcpyAsync(Z->x, a->simp_on ? a->sa.rho : a->x, sizeof(double) * a->m,
+                            cudaMemcpyDeviceToDevice, st));
   TOPO_TRY(topo::solver_build(Z));
   topo_solve_info si{};
   const double tol = o->cg_tol * std::pow(o->cg_tol_factor, (double)a->ip_iters);
@@ -311,7 +390,8 @@ topo_status topo_ip_step(topo_ip* a, const topo_ip_opts* o, topo_ip_info* info) 
     return ss;
   }
   TOPO_CUDA(launch_ip_recover_update(a->d, a->g, a->du, a->tR3, a->Dinv, a->u, a->x, a->phi, a->psi,
-                                     a->dx, a->dphi, a->dpsi, a->ip, a->partials, a->counter, st));
+                                     a->dx, a->dphi, a->dpsi, a->ip, a->partials, a->counter, st,
+                                     a->simp_on ? &a->sa : nullptr));
   a->newton += 1;
   // Newton test at the new iterate with the current (s, r)
   TOPO_TRY(ip_residuals(a));

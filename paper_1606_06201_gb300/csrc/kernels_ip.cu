@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(kThreads) k_z_node(Dims d, const T* __restrict
 //   g_e = K0 u_e, F3 = -1/2 u_e^T g_e - lambda - phi + psi, Res4 = s - phi x,
 //   Res5 = r - psi (xbar - x), tR3 = F3 - Res4/x + Res5/(xbar - x), D = phi/x + psi/(xbar - x),
 //   Dinv = 1/D, t = tR3 Dinv.  Sums: sum x, sum t, ||tR3||^2, ||phi||^2, ||psi||^2, sum Dinv.
+// e3 != null (SIMP, Sec. 9): F3 takes the filtered energy term -e3_e in place of -1/2 u_e^T g_e.
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_ip_elem(Dims d, const double* __restrict__ K0,
                                                       const double* __restrict__ u,
@@ -238,7 +239,8 @@ __global__ void __launch_bounds__(kThreads) k_ip_elem(Dims d, const double* __re
                                                       double* __restrict__ tR3,
                                                       double* __restrict__ Dinv,
                                                       double* __restrict__ t, double* partials,
-                                                      unsigned* counter) {
+                                                      unsigned* counter,
+                                                      const double* __restrict__ e3) {
   pdl_prologue();
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM;
   const long long m = d.elems();
@@ -263,7 +265,7 @@ __global__ void __launch_bounds__(kThreads) k_ip_elem(Dims d, const double* __re
     }
     const double xe = x[e], ph = phi[e], ps = psi[e];
     const double xu = xbar - xe;
-    const double F3 = -0.5 * en - lam - ph + ps;
+    const double F3 = (e3 ? -e3[e] : -0.5 * en) - lam - ph + ps;
     const double R4 = s - ph * xe, R5 = r - ps * xu;
     const double tr = F3 - R4 / xe + R5 / xu;
     const double De = ph / xe + ps / xu;
@@ -300,11 +302,13 @@ __global__ void __launch_bounds__(kThreads) k_ip_elem(Dims d, const double* __re
 
 // Per node: Res1 = f - K(x) u; rhs_u = Res1 + sum_e g_e t_e; w = sum_e g_e Dinv_e (the Z_ul
 // column); invd = 1 / (sum_e x_e K0_ii + g_e,i^2 Dinv_e); ||Res1||^2.  Last block: rhs_lambda.
+// gk: the K0 u_e used for K(x) u (SIMP: the unscaled columns, while g holds c_e K0 u_e).
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_ip_node(Dims d, const double* __restrict__ K0,
                                                       const double* __restrict__ x,
                                                       const double* __restrict__ u,
                                                       const double* __restrict__ f,
+                                                      const double* __restrict__ gk,
                                                       const double* __restrict__ g,
                                                       const double* __restrict__ t,
                                                       const double* __restrict__ Dinv,
@@ -334,8 +338,8 @@ __global__ void __launch_bounds__(kThreads) k_ip_node(Dims d, const double* __re
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
         const double gi = g[e * NE + loc * DIM + c];
-        // K(x) u row = x_e (K0 u_e)_row = x_e g_e,row
-        ku[c] = fma(xe, gi, ku[c]);
+        // K(x) u row = x_e (K0 u_e)_row
+        ku[c] = fma(xe, gk[e * NE + loc * DIM + c], ku[c]);
         gt[c] = fma(gi, te, gt[c]);
         gw[c] = fma(gi, de, gw[c]);
         dg[c] = fma(xe, K0[(loc * DIM + c) * NE + loc * DIM + c], dg[c]);
@@ -370,7 +374,8 @@ __global__ void __launch_bounds__(kThreads) k_ip_node(Dims d, const double* __re
 
 // Direction completion and step length: d_x = (g_e^T d_u,e + d_lambda - tR3) Dinv,
 // d_phi = (Res4 - phi d_x)/x, d_psi = (Res5 + psi d_x)/(xbar - x); minima of the ratios of the
-// 0.9 rule over x (both bounds), phi and psi.
+// 0.9 rule over x (both bounds), phi and psi.  bt != null (SIMP): bt_e = (hat B^T d_u)_e replaces
+// g_e^T d_u,e.
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_ip_recover(Dims d, const double* __restrict__ g,
                                                          const double* __restrict__ du,
@@ -383,7 +388,8 @@ __global__ void __launch_bounds__(kThreads) k_ip_recover(Dims d, const double* _
                                                          double* __restrict__ dphi,
                                                          double* __restrict__ dpsi,
                                                          IpScalars* ip, double* partials,
-                                                         unsigned* counter) {
+                                                         unsigned* counter,
+                                                         const double* __restrict__ bt) {
   pdl_prologue();
   constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM;
   const long long m = d.elems();
@@ -394,11 +400,15 @@ __global__ void __launch_bounds__(kThreads) k_ip_recover(Dims d, const double* _
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < m;
        e += (long long)gridDim.x * blockDim.x) {
     double acc = dl - tR3[e];
+    if (bt) {
+      acc += bt[e];
+    } else {
 #pragma unroll
-    for (int a = 0; a < NN; ++a) {
-      const long long nid = elem_node<DIM>(d, e, a);
+      for (int a = 0; a < NN; ++a) {
+        const long long nid = elem_node<DIM>(d, e, a);
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) acc = fma(g[e * NE + a * DIM + c], du[DIM * nid + c], acc);
+        for (int c = 0; c < DIM; ++c) acc = fma(g[e * NE + a * DIM + c], du[DIM * nid + c], acc);
+      }
     }
     const double ddx = acc * Dinv[e];
     const double xe = x[e], ph = phi[e], ps = psi[e], xu = xbar - xe;
@@ -444,6 +454,162 @@ __global__ void k_axpy_alpha(long long n, double* u, const double* du, const IpS
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     u[i] = fma(a, du[i], u[i]);
+}
+
+// ---- SIMP density filter (Sec. 9) ---------------------------------------------------------
+// The stencil of element (ex, ey, ez): in-grid offsets o with |o|_1 <= R, weight hat W = rmin -
+// |o|_1 (> 0 since R = ceil(rmin) - 1 < rmin); hat W is symmetric, so row and column sums agree.
+// Each sum runs over the offsets in a fixed order (z, y, x ascending): results do not depend on
+// the launch.
+template <int DIM>
+__device__ __forceinline__ void elem_coords(const Dims& d, long long e, int& ex, int& ey, int& ez) {
+  ex = (int)(e % d.nx);
+  ey = (int)((e / d.nx) % d.ny);
+  ez = (DIM == 3) ? (int)(e / ((long long)d.nx * d.ny)) : 0;
+}
+
+// sum over the stencil of w * a_j * b_j (a or b may be null = 1).
+template <int DIM>
+__device__ double stencil_sum(const Dims& d, long long e, double rmin, int R,
+                              const double* __restrict__ a, const double* __restrict__ b) {
+  int ex, ey, ez;
+  elem_coords<DIM>(d, e, ex, ey, ez);
+  const int zr = DIM == 3 ? R : 0;
+  double acc = 0.0;
+  for (int dz = -zr; dz <= zr; ++dz) {
+    const int jz = ez + dz;
+    if (DIM == 3 && (jz < 0 || jz >= d.nz)) continue;
+    const int rz = R - abs(dz);
+    for (int dy = -rz; dy <= rz; ++dy) {
+      const int jy = ey + dy;
+      if (jy < 0 || jy >= d.ny) continue;
+      const int ry = rz - abs(dy);
+      for (int dx = -ry; dx <= ry; ++dx) {
+        const int jx = ex + dx;
+        if (jx < 0 || jx >= d.nx) continue;
+        const double w = rmin - (double)(abs(dx) + abs(dy) + abs(dz));
+        const long long j = jx + (long long)d.nx * (jy + (long long)d.ny * jz);
+        const double v = a ? (b ? a[j] * b[j] : a[j]) : (b ? b[j] : 1.0);
+        acc = fma(w, v, acc);
+      }
+    }
+  }
+  return acc;
+}
+
+template <int DIM>
+__global__ void k_filter_colsum(Dims d, double rmin, int R, double* __restrict__ invS) {
+  pdl_prologue();
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.elems()) return;
+  invS[e] = 1.0 / stencil_sum<DIM>(d, e, rmin, R, nullptr, nullptr);
+}
+
+// x~ = W x (x~_k = sum_i hat W_ki x_i / S_i), rho = x~^p, c = p x~^(p-1).
+template <int DIM>
+__global__ void k_simp_density(Dims d, double rmin, int R, const double* __restrict__ invS,
+                               const double* __restrict__ x, double p, double* __restrict__ xt,
+                               double* __restrict__ rho, double* __restrict__ c) {
+  pdl_prologue();
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.elems()) return;
+  const double v = stencil_sum<DIM>(d, e, rmin, R, x, invS);
+  xt[e] = v;
+  rho[e] = p == 1.0 ? v : pow(v, p);
+  c[e] = p == 1.0 ? 1.0 : p * pow(v, p - 1.0);
+}
+
+// out_i = post (W^T (pre a))_i = post / S_i sum_k hat W_ik pre_k a_k  (pre may be null = 1).
+template <int DIM>
+__global__ void k_filter_t(Dims d, double rmin, int R, const double* __restrict__ invS,
+                           const double* __restrict__ a, const double* __restrict__ pre,
+                           double post, double* __restrict__ out, const CgScalars* sc) {
+  pdl_prologue();
+  if (sc && sc[0].done) return;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.elems()) return;
+  out[e] = post * invS[e] * stencil_sum<DIM>(d, e, rmin, R, a, pre);
+}
+
+// out_k = (W a)_k = sum_j hat W_kj a_j / S_j.
+template <int DIM>
+__global__ void k_filter_w(Dims d, double rmin, int R, const double* __restrict__ invS,
+                           const double* __restrict__ a, double* __restrict__ out,
+                           const CgScalars* sc) {
+  pdl_prologue();
+  if (sc && sc[0].done) return;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.elems()) return;
+  out[e] = stencil_sum<DIM>(d, e, rmin, R, a, invS);
+}
+
+// Between the element and node passes of the SIMP residuals: th = W t (the right-hand side's
+// element weights), Dm = W Dinv = (W D^{-1} W^T) e, the row sums of W D^{-1} W^T (every column of W
+// sums to 1, so W^T e = e), and gh_e = c_e g_e.  The hierarchy's element-local Z keeps
+// diag(Dm) in place of W D^{-1} W^T: exact on the lambda row and column and on constant element
+// fields, and above Z in the Loewner order (diag(Dm) - W D^{-1} W^T is a weighted graph
+// Laplacian).
+template <int DIM>
+__global__ void k_simp_mid(Dims d, double rmin, int R, const double* __restrict__ invS,
+                           const double* __restrict__ t, const double* __restrict__ Dinv,
+                           const double* __restrict__ g, const double* __restrict__ c,
+                           double* __restrict__ th, double* __restrict__ Dm,
+                           double* __restrict__ gh) {
+  pdl_prologue();
+  constexpr int NE = (DIM == 2 ? 4 : 8) * DIM;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.elems()) return;
+  th[e] = stencil_sum<DIM>(d, e, rmin, R, t, invS);
+  Dm[e] = stencil_sum<DIM>(d, e, rmin, R, Dinv, invS);
+  const double ce = c[e];
+#pragma unroll
+  for (int q = 0; q < NE; ++q) gh[e * NE + q] = ce * g[e * NE + q];
+}
+
+// a_e = g_e^T v_e.
+template <int DIM>
+__global__ void k_elem_gdot(Dims d, const double* __restrict__ g, const double* __restrict__ v,
+                            double* __restrict__ a, const CgScalars* sc) {
+  pdl_prologue();
+  constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM;
+  if (sc && sc[0].done) return;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.elems()) return;
+  double acc = 0.0;
+#pragma unroll
+  for (int q = 0; q < NN; ++q) {
+    const long long nid = elem_node<DIM>(d, e, q);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) acc = fma(g[e * NE + q * DIM + c], v[DIM * nid + c], acc);
+  }
+  a[e] = acc;
+}
+
+// sb_i = Dinv_i ((W^T a)_i + v_lambda) and the lambda row y_lambda = sum_i sb_i
+// (= e^T W sb, since every column of W sums to 1).
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_simp_zt(Dims d, double rmin, int R,
+                                                      const double* __restrict__ invS,
+                                                      const double* __restrict__ a,
+                                                      const double* __restrict__ Dinv,
+                                                      const double* __restrict__ v,
+                                                      double* __restrict__ y,
+                                                      double* __restrict__ sb, double* partials,
+                                                      unsigned* counter, const CgScalars* sc) {
+  pdl_prologue();
+  if (sc && sc[0].done) return;
+  const long long m = d.elems();
+  const double vl = v[d.dofs()];
+  double part[1] = {0.0};
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double s = Dinv[e] * fma(invS[e], stencil_sum<DIM>(d, e, rmin, R, a, nullptr), vl);
+    sb[e] = s;
+    part[0] += s;
+  }
+  double tot[1];
+  if (!last_block<1>(part, 0, partials, counter, tot)) return;
+  if (threadIdx.x == 0) y[d.dofs()] = tot[0];
 }
 
 // ---- OC kernels --------------------------------------------------------------------------
@@ -594,23 +760,59 @@ cudaError_t launch_ip_residuals(const Dims& d, const double* K0, const double* u
                                 const double* phi, const double* psi, const double* f,
                                 const uint8_t* fixed, IpScalars* ip, double* g, double* tR3,
                                 double* Dinv, double* t, double* rhs, double* w, double* invd,
-                                double* partials, unsigned* counter, cudaStream_t st) {
+                                double* partials, unsigned* counter, cudaStream_t st,
+                                const SimpArgs* sa) {
   const unsigned ge = red_grid(d.elems());
+  const unsigned gm = blocks_for(d.elems());
+  const double* e3 = nullptr;
+  if (sa) {  // x~, rho, c; E = u_e^T K0 u_e; e3 = 1/2 W^T (c E)
+    cudaError_t e = launch_simp_density(d, *sa, x, st);
+    if (e != cudaSuccess) return e;
+    e = launch_element_energy(d, K0, u, u, sa->E, 1.0, st);
+    if (e != cudaSuccess) return e;
+    if (d.dim == 2)
+      topo::launch(k_filter_t<2>, gm, kThreads, 0, st, d, sa->rmin, sa->R, sa->invS,
+                   (const double*)sa->E, (const double*)sa->c, 0.5, sa->e3, (const CgScalars*)nullptr);
+    else
+      topo::launch(k_filter_t<3>, gm, kThreads, 0, st, d, sa->rmin, sa->R, sa->invS,
+                   (const double*)sa->E, (const double*)sa->c, 0.5, sa->e3, (const CgScalars*)nullptr);
+    e3 = sa->e3;
+  }
   if (d.dim == 2)
-    topo::launch(k_ip_elem<2>, ge, kThreads, 0, st, d, K0, u, x, phi, psi, ip, g, tR3, Dinv, t, partials,
-                                          counter);
+    topo::launch(k_ip_elem<2>, ge, kThreads, 0, st, d, K0, u, x, phi, psi, ip, g, tR3, Dinv, t,
+                 partials, counter, e3);
   else
-    topo::launch(k_ip_elem<3>, ge, kThreads, 0, st, d, K0, u, x, phi, psi, ip, g, tR3, Dinv, t, partials,
-                                          counter);
+    topo::launch(k_ip_elem<3>, ge, kThreads, 0, st, d, K0, u, x, phi, psi, ip, g, tR3, Dinv, t,
+                 partials, counter, e3);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  // node pass: K(x) u with the unscaled g; Z's right-hand side, column and diagonal with the
+  // hierarchy's element data
+  const double* xk = x;
+  const double* gz = g;
+  const double* tz = t;
+  const double* dz = Dinv;
+  if (sa) {
+    if (d.dim == 2)
+      topo::launch(k_simp_mid<2>, gm, kThreads, 0, st, d, sa->rmin, sa->R, sa->invS,
+                   (const double*)t, (const double*)Dinv, (const double*)g, (const double*)sa->c,
+                   sa->th, sa->Dm, sa->gh);
+    else
+      topo::launch(k_simp_mid<3>, gm, kThreads, 0, st, d, sa->rmin, sa->R, sa->invS,
+                   (const double*)t, (const double*)Dinv, (const double*)g, (const double*)sa->c,
+                   sa->th, sa->Dm, sa->gh);
+    xk = sa->rho;
+    gz = sa->gh;
+    tz = sa->th;
+    dz = sa->Dm;
+  }
   const unsigned gn = blocks_for(d.nodes());
   if (d.dim == 2)
-    topo::launch(k_ip_node<2>, gn, kThreads, 0, st, d, K0, x, u, f, g, t, Dinv, fixed, rhs, w, invd, ip,
-                                          partials, counter);
+    topo::launch(k_ip_node<2>, gn, kThreads, 0, st, d, K0, xk, u, f, (const double*)g, gz, tz, dz,
+                 fixed, rhs, w, invd, ip, partials, counter);
   else
-    topo::launch(k_ip_node<3>, gn, kThreads, 0, st, d, K0, x, u, f, g, t, Dinv, fixed, rhs, w, invd, ip,
-                                          partials, counter);
+    topo::launch(k_ip_node<3>, gn, kThreads, 0, st, d, K0, xk, u, f, (const double*)g, gz, tz, dz,
+                 fixed, rhs, w, invd, ip, partials, counter);
   return cudaGetLastError();
 }
 
@@ -618,19 +820,87 @@ cudaError_t launch_ip_recover_update(const Dims& d, const double* g, const doubl
                                      const double* tR3, const double* Dinv, double* u, double* x,
                                      double* phi, double* psi, double* dx, double* dphi,
                                      double* dpsi, IpScalars* ip, double* partials,
-                                     unsigned* counter, cudaStream_t st) {
+                                     unsigned* counter, cudaStream_t st, const SimpArgs* sa) {
   const unsigned ge = red_grid(d.elems());
+  const double* bt = nullptr;
+  if (sa) {  // bt = hat B^T d_u = W^T (gh^T d_u)
+    const unsigned gm = blocks_for(d.elems());
+    if (d.dim == 2) {
+      topo::launch(k_elem_gdot<2>, gm, kThreads, 0, st, d, (const double*)sa->gh, du, sa->ea,
+                   (const CgScalars*)nullptr);
+      topo::launch(k_filter_t<2>, gm, kThreads, 0, st, d, sa->rmin, sa->R, sa->invS,
+                   (const double*)sa->ea, (const double*)nullptr, 1.0, sa->eb,
+                   (const CgScalars*)nullptr);
+    } else {
+      topo::launch(k_elem_gdot<3>, gm, kThreads, 0, st, d, (const double*)sa->gh, du, sa->ea,
+                   (const CgScalars*)nullptr);
+      topo::launch(k_filter_t<3>, gm, kThreads, 0, st, d, sa->rmin, sa->R, sa->invS,
+                   (const double*)sa->ea, (const double*)nullptr, 1.0, sa->eb,
+                   (const CgScalars*)nullptr);
+    }
+    bt = sa->eb;
+  }
   if (d.dim == 2)
-    topo::launch(k_ip_recover<2>, ge, kThreads, 0, st, d, g, du, tR3, Dinv, x, phi, psi, dx, dphi, dpsi, ip,
-                                             partials, counter);
+    topo::launch(k_ip_recover<2>, ge, kThreads, 0, st, d, g, du, tR3, Dinv, x, phi, psi, dx, dphi,
+                 dpsi, ip, partials, counter, bt);
   else
-    topo::launch(k_ip_recover<3>, ge, kThreads, 0, st, d, g, du, tR3, Dinv, x, phi, psi, dx, dphi, dpsi, ip,
-                                             partials, counter);
+    topo::launch(k_ip_recover<3>, ge, kThreads, 0, st, d, g, du, tR3, Dinv, x, phi, psi, dx, dphi,
+                 dpsi, ip, partials, counter, bt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long m = d.elems(), n = d.dofs();
   topo::launch(k_ip_update_elem, blocks_for(m), kThreads, 0, st, m, x, phi, psi, dx, dphi, dpsi, ip);
   topo::launch(k_axpy_alpha, red_grid(n), kThreads, 0, st, n, u, du, ip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_filter_colsum(const Dims& d, double rmin, int R, double* invS,
+                                 cudaStream_t st) {
+  const long long m = d.elems();
+  if (d.dim == 2)
+    topo::launch(k_filter_colsum<2>, blocks_for(m), kThreads, 0, st, d, rmin, R, invS);
+  else
+    topo::launch(k_filter_colsum<3>, blocks_for(m), kThreads, 0, st, d, rmin, R, invS);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_simp_density(const Dims& d, const SimpArgs& sa, const double* x,
+                                cudaStream_t st) {
+  const unsigned gm = blocks_for(d.elems());
+  if (d.dim == 2)
+    topo::launch(k_simp_density<2>, gm, kThreads, 0, st, d, sa.rmin, sa.R, sa.invS, x, sa.p,
+                 sa.xt, sa.rho, sa.c);
+  else
+    topo::launch(k_simp_density<3>, gm, kThreads, 0, st, d, sa.rmin, sa.R, sa.invS, x, sa.p,
+                 sa.xt, sa.rho, sa.c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_simp_z_apply(const Dims& d, const double* K0, const double* rho,
+                                const double* gh, const double* Dinv, const double* invS,
+                                double rmin, int R, double* ea, double* eb, double* se,
+                                const double* v, double* y, const uint8_t* fixed,
+                                double* partials, unsigned* counter, const CgScalars* sc,
+                                cudaStream_t st) {
+  const unsigned gm = blocks_for(d.elems());
+  const unsigned ge = red_grid(d.elems());
+  const unsigned gn = blocks_for(d.nodes());
+#define TOPO_SZ(DIM)                                                                            \
+  do {                                                                                          \
+    topo::launch(k_elem_gdot<DIM>, gm, kThreads, 0, st, d, gh, v, ea, sc);                      \
+    topo::launch(k_simp_zt<DIM>, ge, kThreads, 0, st, d, rmin, R, invS, (const double*)ea,      \
+                 Dinv, v, y, eb, partials, counter, sc);                                        \
+    topo::launch(k_filter_w<DIM>, gm, kThreads, 0, st, d, rmin, R, invS, (const double*)eb, se, \
+                 sc);                                                                           \
+    topo::launch(k_z_node<DIM, double, 0>, gn, kThreads, 0, st, d, K0, rho, gh,                 \
+                 (const double*)se, v, (const double*)nullptr, y, (const double*)nullptr, 1.0,  \
+                 fixed, (const double*)nullptr, sc, (const double*)nullptr);                    \
+  } while (0)
+  if (d.dim == 2)
+    TOPO_SZ(2);
+  else
+    TOPO_SZ(3);
+#undef TOPO_SZ
   return cudaGetLastError();
 }
 

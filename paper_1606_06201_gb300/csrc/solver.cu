@@ -498,6 +498,19 @@ topo_status precondition(topo_solver* s, const CgScalars* sc, void** y, bool fus
   return TOPO_OK;
 }
 
+// The outer CG's operator y = A v: the level-0 operator, or for the SIMP model (Sec. 9) the exact Z
+// with the filter, whose element-local approximation the hierarchy holds.
+topo_status apply_outer(topo_solver* s, const double* v, double* y, const CgScalars* sc) {
+  if (s->simp.on) {
+    const Level& l0 = s->L[0];
+    TOPO_CUDA(launch_simp_z_apply(l0.d, s->K0, s->x, s->g, s->simp.Dinv, s->simp.invS,
+                                  s->simp.rmin, s->simp.R, s->simp.ea, s->simp.eb, s->se, v, y,
+                                  l0.fixed, s->partials, s->counters, sc, s->st));
+    return TOPO_OK;
+  }
+  return apply_level<double>(s, 0, 0, v, nullptr, y, sc);
+}
+
 // One PCG iteration (q = A p, update, precondition, new direction), enqueued on s->st.
 template <typename TV>
 topo_status cg_iteration(topo_solver* s, int slot, double tol, int max_iter) {
@@ -506,7 +519,7 @@ topo_status cg_iteration(topo_solver* s, int slot, double tol, int max_iter) {
   s->prof_slot = s->profiling ? slot : -1;
   TOPO_TRY(prof_mark(s, 0, 0));
   if (s->arrow) {
-    TOPO_TRY(apply_level<double>(s, 0, 0, s->p, nullptr, s->q, s->sc));
+    TOPO_TRY(apply_outer(s, s->p, s->q, s->sc));
     TOPO_CUDA(launch_cg_alpha(n, 1, s->p, s->q, s->partials, s->counters, s->sc, s->st));
   } else if (s->q1_ok && s->outer_df && s->xdf) {
     TOPO_CUDA(launch_q1_apply_dot_df(l0.d.nx, l0.d.ny, s->q1, s->xdf, s->p, s->q, l0.fixed,
@@ -658,7 +671,7 @@ topo_status cg_setup(topo_solver* s, int use_x0, double tol, int max_iter) {
   const long long n = s->ncg();
   const int nrhs = s->nrhs;
   if (use_x0) {  // (from z = 0 the start vectors come from launch_cg_init_zero before the graph)
-    TOPO_TRY(apply_level<double>(s, 0, 0, s->z, nullptr, s->q, nullptr));
+    TOPO_TRY(apply_outer(s, s->z, s->q, nullptr));
     TOPO_CUDA(launch_cg_init(n, nrhs, s->bbuf, s->z, s->r, s->q, use_x0, s->partials,
                              s->counters, s->sc, tol, max_iter, s->st));
     if (!std::is_same<TV, double>::value)
@@ -1346,7 +1359,7 @@ topo_status topo_apply_K(topo_solver* s, const double* v, double* y) {
     return TOPO_E_INVALID_ARG;
   }
   StreamGuard g(s);
-  return apply_level<double>(s, 0, 0, v, nullptr, y, nullptr);
+  return apply_outer(s, v, y, nullptr);
 }
 
 topo_status topo_apply_vcycle(topo_solver* s, const double* r, double* y) {

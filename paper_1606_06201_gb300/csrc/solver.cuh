@@ -47,6 +47,17 @@ struct topo_solver {
   float* g32 = nullptr;
   float* Dinv32 = nullptr;
   double* se = nullptr;          // element scalars s_e of the Z operator
+  // SIMP model (Sec. 9): the outer CG applies the exact Z with the filter (launch_simp_z_apply);
+  // g and Dinv above then hold the hierarchy's element-local columns and weights.
+  struct {
+    bool on = false;
+    double rmin = 0.0;
+    int R = 0;
+    const double* invS = nullptr;
+    const double* Dinv = nullptr;  // exact 1 / D
+    double* ea = nullptr;
+    double* eb = nullptr;
+  } simp;
   float* se32 = nullptr;
   int nc = 0;                    // DOFs of the coarsest level
   double* Adense = nullptr;

@@ -61,6 +61,27 @@ struct IpScalars {
   int pad;
 };
 
+// The SIMP model with the density filter (Sec. 9).  hat W_ij = max(0, rmin - dist(i, j)) with the
+// Manhattan distance of element centres (element widths), so the stencil holds the offsets o with
+// |o|_1 <= R = ceil(rmin) - 1; W = hat W diag(invS) (columns normalised, as printed).  Per-element
+// buffers [m] unless noted.
+constexpr int kSimpMaxR = 8;  // largest stencil half-width (rmin <= 9)
+struct SimpArgs {
+  double rmin = 0.0, p = 1.0;
+  int R = 0;
+  const double* invS = nullptr;  // 1 / (column sums of hat W)
+  double* xt = nullptr;          // x~ = W x
+  double* rho = nullptr;         // x~^p, the stiffness coefficients of hat K(x~)
+  double* c = nullptr;           // p x~^(p-1)
+  double* E = nullptr;           // u_e^T K0 u_e
+  double* e3 = nullptr;          // 1/2 W^T (c E), the energy term of the modified row 3
+  double* gh = nullptr;          // [m * ne] c_e g_e, the element columns of hat B = G diag(c) W
+  double* th = nullptr;          // W (tilde Res3 / D)
+  double* Dm = nullptr;          // W D^{-1} e, the row sums of W D^{-1} W^T: the hierarchy's weights
+  double* ea = nullptr;          // scratch
+  double* eb = nullptr;          // scratch
+};
+
 // Device-resident scalars of the OC bisection.
 struct OcScalars {
   double lo, hi, tau, lam_last;
@@ -500,16 +521,34 @@ cudaError_t launch_apply_arrow(const Dims& d, int mode, const T* Ae, const T* v,
                                const double* zll, double omega_l, const double* wdev,
                                double* partials, unsigned* counter, const CgScalars* sc,
                                cudaStream_t st);
+// sa != nullptr: the SIMP residuals (Sec. 9): x~, rho, c from x; F3 with the filtered energy
+// term; rhs, w, invd of Z with hat B = G diag(c) W, whose element-local hierarchy takes the
+// row sums of W D^{-1} W^T (sa->Dm) as weights and the columns sa->gh.  Dinv keeps the exact 1/D.
 cudaError_t launch_ip_residuals(const Dims& d, const double* K0, const double* u, const double* x,
                                 const double* phi, const double* psi, const double* f,
                                 const uint8_t* fixed, IpScalars* ip, double* g, double* tR3,
                                 double* Dinv, double* t, double* rhs, double* w, double* invd,
-                                double* partials, unsigned* counter, cudaStream_t st);
+                                double* partials, unsigned* counter, cudaStream_t st,
+                                const SimpArgs* sa = nullptr);
 cudaError_t launch_ip_recover_update(const Dims& d, const double* g, const double* du,
                                      const double* tR3, const double* Dinv, double* u, double* x,
                                      double* phi, double* psi, double* dx, double* dphi,
                                      double* dpsi, IpScalars* ip, double* partials,
-                                     unsigned* counter, cudaStream_t st);
+                                     unsigned* counter, cudaStream_t st,
+                                     const SimpArgs* sa = nullptr);
+// 1 / column sums of hat W (SIMP filter).
+cudaError_t launch_filter_colsum(const Dims& d, double rmin, int R, double* invS, cudaStream_t st);
+// x~ = W x, rho = x~^p, c = p x~^(p-1).
+cudaError_t launch_simp_density(const Dims& d, const SimpArgs& sa, const double* x,
+                                cudaStream_t st);
+// The exact SIMP augmented operator y = Z v (MODE 0):  a_e = gh_e^T v_e;
+// sb = Dinv (W^T a + v_lambda), y_lambda = sum sb;  se = W sb;  y_u = hat K v + sum_e gh_e se_e.
+cudaError_t launch_simp_z_apply(const Dims& d, const double* K0, const double* rho,
+                                const double* gh, const double* Dinv, const double* invS,
+                                double rmin, int R, double* ea, double* eb, double* se,
+                                const double* v, double* y, const uint8_t* fixed,
+                                double* partials, unsigned* counter, const CgScalars* sc,
+                                cudaStream_t st);
 cudaError_t launch_oc_bisection(long long m, const double* x, const double* E, OcScalars* oc,
                                 int steps, double* xout, double* partials, unsigned* counter,
                                 cudaStream_t st);

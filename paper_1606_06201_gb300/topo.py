@@ -113,6 +113,8 @@ _SIGS = {
     "topo_ip_set_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "topo_ip_power_state_size": (ctypes.c_int, [_vp, _vp]),
     "topo_ip_set_vcycle_fusion": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "topo_ip_set_simp": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
+    "topo_ip_filtered_density": (ctypes.c_int, [_vp, _vp]),
     "topo_ip_get_power_state": (ctypes.c_int, [_vp, _vp, _vp]),
     "topo_ip_set_power_state": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "topo_oc_create": (ctypes.c_int, [ctypes.POINTER(SolverDesc), _vp, ctypes.c_double,
@@ -190,7 +192,7 @@ def ip_options(sigma=0.2, tau_nwt=0.1, tau_ip=1e-8, frac=0.9, step_x_only=False,
                cg_tol=1e-8, cg_tol_init=None, cg_tol_factor=1.0, stop_rule="barrier",
                tau_kkt=1e-6):
     """Sec. 3 defaults; cg_tol is the relative residual of the Z solves of the first major
-    iteration, multiplied by cg_tol_factor at every barrier reduction (Sec. 9.1: 1e-2 with factor
+    iteration, multiplied by cg_tol_factor at every barrier reduction (Sec. 8.1: 1e-2 with factor
     1 or 0.5).  stop_rule "barrier" (max(s, r) <= tau_ip) or "kkt" (the scaled KKT residual of
     the Remark in Sec. 3.4 <= tau_kkt)."""
     if stop_rule not in ("barrier", "kkt"):
@@ -229,7 +231,9 @@ class IP:
     """Primal-dual interior-point method on the GPU (see include/topo.h)."""
 
     def __init__(self, nx, ny, nz=0, fixed=None, f=None, V=None, xbar=1.0, levels=3,
-                 precision=FP64, nu1=2, nu2=2, omega=None, max_iter=1000, E=1.0, nu=0.3):
+                 precision=FP64, nu1=2, nu2=2, omega=None, max_iter=1000, E=1.0, nu=0.3,
+                 simp=None):
+        """simp = (p, rmin): the SIMP model with the density filter (topo_ip_set_simp)."""
         import torch
         d, self._fixed, self.dim, self.n = _desc(nx, ny, nz, fixed, levels, precision, nu1, nu2,
                                                  omega, max_iter, 1, None, E, nu, False)
@@ -241,6 +245,18 @@ class IP:
         self._h = h
         _check(_lib.topo_ip_set_stream(h, _vp(torch.cuda.current_stream().cuda_stream)),
                "topo_ip_set_stream")
+        if simp is not None:
+            self.set_simp(*simp)
+
+    def set_simp(self, p, rmin):
+        _check(_lib.topo_ip_set_simp(self._h, float(p), float(rmin)), "topo_ip_set_simp")
+
+    def filtered_density(self):
+        """x~ = W x at the current iterate (x without the SIMP model), a device tensor."""
+        import torch
+        xt = torch.empty(self.m, dtype=torch.float64, device="cuda")
+        _check(_lib.topo_ip_filtered_density(self._h, _ptr(xt)), "topo_ip_filtered_density")
+        return xt
 
     def close(self):
         if getattr(self, "_h", None):

@@ -117,7 +117,7 @@ def test_ip_fused_coarse_sweeps_give_identical_bits(precision):
 
 
 def test_inexact_newton_settings_of_tab_ip():
-    """Sec. 9.1 (tab:IP) on the square cantilever of Example 1 with 6 refinements (64 x 64): Z
+    """Sec. 8.1 (tab:IP) on the square cantilever of Example 1 with 6 refinements (64 x 64): Z
     systems solved to 1e-10 ("exact"), to a fixed 1e-2, and to 1e-2 halved at every barrier
     reduction.  As in the paper at tau_IP = 1e-8: all three need the same 12 major iterations and
     about the same Newton steps; the fixed tolerance needs the fewest CG iterations, the

@@ -1,4 +1,4 @@
-"""The IP iteration counts printed in tab:IP (Sec. 9.1) against the oracle's barrier schedule."""
+"""The IP iteration counts printed in tab:IP (Sec. 8.1) against the oracle's barrier schedule."""
 import json
 import os
 
