@@ -30,6 +30,7 @@ struct topo_ip {
   double fnorm = 0.0;
   double kkt = NAN;  // scaled KKT residual after the last Newton step
   bool simp_on = false;  // SIMP model with the density filter (Sec. 9)
+  bool started = false;  // topo_ip_init or topo_ip_set_state has run
   SimpArgs sa{};
   int newton = 0, ip_iters = 0, feval = 0, cg_iters = 0;
   bool done = false;
@@ -260,8 +261,8 @@ topo_status topo_ip_set_simp(topo_ip* a, double p, double rmin) {
                     std::to_string(kSimpMaxR + 1) + "]");
     return TOPO_E_INVALID_ARG;
   }
-  if (a->simp_on) {
-    topo::set_error("topo_ip_set_simp: the SIMP model is already set on this problem");
+  if (a->simp_on || a->started) {
+    topo::set_error("topo_ip_set_simp: call once, before topo_ip_init and topo_ip_set_state");
     return TOPO_E_INVALID_ARG;
   }
   StreamGuard gd(a->Z);
@@ -362,6 +363,7 @@ topo_status topo_ip_init(topo_ip* a, const topo_ip_opts* o) {
   a->newton = a->ip_iters = 0;
   a->feval = 1;
   a->done = false;
+  a->started = true;
   return TOPO_OK;
 }
 
@@ -483,6 +485,7 @@ topo_status topo_ip_set_state(topo_ip* a, const double* u, const double* x, cons
   TOPO_CUDA(cudaMemcpyAsync(a->ip, a->ip_host, sizeof(IpScalars), cudaMemcpyHostToDevice, st));
   TOPO_CUDA(cudaStreamSynchronize(st));
   a->done = false;
+  a->started = true;
   return TOPO_OK;
 }
 

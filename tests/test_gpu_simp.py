@@ -153,3 +153,27 @@ def test_simp_mixed_run_reaches_the_oracle_objective():
     c = float(cfg["f"] @ u)
     assert abs(c - oinfo["compliance"]) <= 1e-5 * oinfo["compliance"], (c, oinfo["compliance"])
     assert abs(info.newton - oinfo["newton"]) <= 0.1 * oinfo["newton"], (info.newton, oinfo["newton"])
+
+
+def test_simp_rejects_bad_arguments_and_late_calls():
+    """p outside [1, 8], rmin outside [1, 9], a second call, or a call after topo_ip_init: each
+    returns an error and changes nothing."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    shape = (16, 8)
+    cfg = W.cantilever_2d(*shape, 0.4)
+    for p, rmin in ((0.5, 2.0), (9.0, 2.0), (3.0, 0.5), (3.0, 10.0), (float("nan"), 2.0)):
+        ip = _gpu_ip(topo, torch, shape, cfg, 3.0, 2, None)
+        with pytest.raises(topo.TopoError):
+            ip.set_simp(p, rmin)
+        ip.close()
+    ip = _gpu_ip(topo, torch, shape, cfg, 3.0, 2, (3.0, 2.0))
+    with pytest.raises(topo.TopoError):
+        ip.set_simp(3.0, 2.0)
+    ip.close()
+    ip = _gpu_ip(topo, torch, shape, cfg, 3.0, 2, None)
+    ip.init(topo.ip_options())
+    with pytest.raises(topo.TopoError):
+        ip.set_simp(3.0, 2.0)
+    np.testing.assert_array_equal(host(ip.filtered_density()), host(ip.state()[1]))
+    ip.close()
