@@ -148,5 +148,6 @@ def test_3d_scale_run_256x128x128_forward_backward():
     assert _true_residual(grid, K0, cfg["x"], cfg["fixed"].astype(bool), cfg["f"], uh) <= 2e-8
     g_ref = -fe.element_energy(grid, K0, uh)
     assert np.all(np.abs(host(xt.grad) - g_ref) <= _energy_bound(grid, K0, uh, uh))
-    assert abs(float(c) - float(cfg["f"] @ uh)) <= 1e-12 * abs(float(c))
+    cv = float(c.detach())
+    assert abs(cv - float(cfg["f"] @ uh)) <= 1e-12 * abs(cv)
     s.close()
