@@ -52,9 +52,11 @@ typedef enum { TOPO_FP64 = 0, TOPO_MIXED = 1 } topo_precision;
  * coarsening halves nx, ny (, nz), which must stay integers.  The smoother is damped Jacobi
  * (Algorithm MG's opt(), Sec. 5.1: the paper names Gauss-Seidel only as an example) with nu1
  * pre- and nu2 post-sweeps and damping omega; the coarsest level is solved exactly (an explicit
- * FP64 inverse of the dense coarsest matrix, formed at every hierarchy build).  precision TOPO_MIXED runs the V-cycle (smoother, transfers, coarse operators) in
- * FP32 and keeps the CG recurrences, dot products, the outer operator and the coarsest solve
- * in FP64.  nrhs > 1 batches right-hand sides (vectors [nrhs][n], one CG per right-hand side). */
+ * FP64 inverse of the dense coarsest matrix, formed at every hierarchy build).  precision
+ * TOPO_MIXED runs the V-cycle (smoother, transfers, coarse operators) in FP32 and keeps the CG
+ * recurrences, dot products and the coarsest solve in FP64; the outer operator runs in float
+ * pairs (topo_set_outer_precision).  nrhs > 1 batches right-hand sides (vectors [nrhs][n], one
+ * CG per right-hand side). */
 typedef struct {
   int dim;              /* 2 or 3 */
   int nx, ny, nz;       /* elements per direction (nz ignored in 2D) */
@@ -124,7 +126,9 @@ topo_status topo_set_vcycle_fusion(topo_solver* s, int on);
 /* Arithmetic of the outer operator q = K(x) p of Algorithm PCG on the finest level of K systems
  * (2D Q1 and 3D hex): 0 = FP64; 1 = pairs of FP32 values (hi + lo, about 48 significant bits,
  * FP64 in and out, p^T q accumulated in pairs), which GB300 runs several times faster than FP64.
- * Default: 1 for mixed-precision solvers, 0 for FP64 solvers; IP systems always use FP64.  Inputs of
+ * Default: 1 for mixed-precision solvers, 0 for FP64 solvers.  The augmented systems of a
+ * mixed-precision IP (topo_ip_*) run the node pass of their outer Z operator in pairs as well, and
+ * FP64 IPs keep FP64.  Inputs of
  * magnitude below 2^-100 lose their low part and values beyond float range give a breakdown.
  * Other modes -> E_INVALID_ARG. */
 topo_status topo_set_outer_precision(topo_solver* s, int mode);

@@ -18,6 +18,7 @@
 //
 // All reductions write one partial per block; the last block to finish combines them in block
 // order and updates the device-resident scalars.
+#include "pairs.cuh"
 #include "topo_internal.cuh"
 
 namespace topo {
@@ -220,6 +221,68 @@ __global__ void __launch_bounds__(kThreads) k_z_node(Dims d, const T* __restrict
     else if (MODE == 2) out = v[id] + omega * invd[id] * (b[id] - acc[c]);
     else out = omega * invd[id] * b[id];
     y[id] = out;
+  }
+}
+
+// (Z v)_u on the finest level in float pairs, for mixed-precision IP systems: k_z_node's MODE 0
+// with K0 staged in shared memory as pairs and x, g, s_e and v converted from FP64 as they load.
+// The FP64 pipe of this GPU runs at a sixtieth of the FP32 rate, and the node pass is 80 FP64
+// multiply-adds per node.  The result hi + lo goes to FP64 (about 48 significant bits, as the
+// K systems' pair operator).
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_z_node_df(Dims d, const double* __restrict__ K0,
+                                                        const double* __restrict__ x,
+                                                        const double* __restrict__ g,
+                                                        const double* __restrict__ se,
+                                                        const double* __restrict__ v,
+                                                        double* __restrict__ y,
+                                                        const uint8_t* __restrict__ fixed,
+                                                        const CgScalars* sc) {
+  pdl_prologue();
+  constexpr int NN = DIM == 2 ? 4 : 8, NE = NN * DIM;
+  __shared__ f2 k0s[NE * NE];
+  if (sc && sc[0].done) return;  // the same for the whole block
+  for (int t = threadIdx.x; t < NE * NE; t += blockDim.x) k0s[t] = df_from_double(K0[t]);
+  __syncthreads();
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nodes = d.nodes();
+  if (node >= nodes) return;
+  const int nnx = d.nx + 1, nny = d.ny + 1;
+  const int i = (int)(node % nnx), j = (int)((node / nnx) % nny);
+  const int k = (DIM == 3) ? (int)(node / ((long long)nnx * nny)) : 0;
+  PairNum acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = PairNum{{0.0f, 0.0f}};
+  for (int s = 0; s < NN; ++s) {
+    const int dx = s & 1, dy = (s >> 1) & 1, dz = (DIM == 3) ? (s >> 2) : 0;
+    const int ex = i - 1 + dx, ey = j - 1 + dy, ez = (DIM == 3) ? k - 1 + dz : 0;
+    if (ex < 0 || ex >= d.nx || ey < 0 || ey >= d.ny) continue;
+    if (DIM == 3 && (ez < 0 || ez >= d.nz)) continue;
+    const int loc = loc_of(1 - dx, 1 - dy, DIM == 3 ? 1 - dz : 0);
+    const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
+    PairNum ve[NE];
+#pragma unroll
+    for (int a = 0; a < NN; ++a) {
+      const long long nid = elem_node<DIM>(d, e, a);
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) ve[a * DIM + c] = PairNum{df_from_double(v[DIM * nid + c])};
+    }
+    const PairNum xe{df_from_double(x[e])}, s_e{df_from_double(se[e])};
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      const f2* row = k0s + (loc * DIM + c) * NE;
+      PairNum t{{0.0f, 0.0f}};
+#pragma unroll
+      for (int q = 0; q < NE; ++q) t = fma(PairNum{row[q]}, ve[q], t);
+      acc[c] = fma(xe, t, acc[c]);
+      acc[c] = fma(PairNum{df_from_double(g[e * NE + loc * DIM + c])}, s_e, acc[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const long long id = DIM * node + c;
+    y[id] = fixed[id] ? 0.0
+                      : __dadd_rn(double_from_float(acc[c].v.h), double_from_float(acc[c].v.l));
   }
 }
 
@@ -756,6 +819,29 @@ template cudaError_t launch_z_apply_fine<float>(const Dims&, int, const float*, 
                                                 const CgScalars*, cudaStream_t, const double*);
 
 
+cudaError_t launch_z_apply_fine_df(const Dims& d, const double* K0, const double* x,
+                                   const double* g, const double* Dinv, double* se,
+                                   const double* v, double* y, const uint8_t* fixed,
+                                   const double* zll, double* partials, unsigned* counter,
+                                   const CgScalars* sc, cudaStream_t st) {
+  const unsigned ge = red_grid(d.elems());
+  const unsigned gn = blocks_for(d.nodes());
+  if (d.dim == 2) {
+    topo::launch(k_z_elem<2, double, 0>, ge, kThreads, 0, st, d, g, Dinv, v,
+                 (const double*)nullptr, y, se, zll, 1.0, partials, counter, sc,
+                 (const double*)nullptr);
+    topo::launch(k_z_node_df<2>, gn, kThreads, 0, st, d, K0, x, g, (const double*)se, v, y, fixed,
+                 sc);
+  } else {
+    topo::launch(k_z_elem<3, double, 0>, ge, kThreads, 0, st, d, g, Dinv, v,
+                 (const double*)nullptr, y, se, zll, 1.0, partials, counter, sc,
+                 (const double*)nullptr);
+    topo::launch(k_z_node_df<3>, gn, kThreads, 0, st, d, K0, x, g, (const double*)se, v, y, fixed,
+                 sc);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ip_residuals(const Dims& d, const double* K0, const double* u, const double* x,
                                 const double* phi, const double* psi, const double* f,
                                 const uint8_t* fixed, IpScalars* ip, double* g, double* tR3,
@@ -881,7 +967,7 @@ cudaError_t launch_simp_z_apply(const Dims& d, const double* K0, const double* r
                                 double rmin, int R, double* ea, double* eb, double* se,
                                 const double* v, double* y, const uint8_t* fixed,
                                 double* partials, unsigned* counter, const CgScalars* sc,
-                                cudaStream_t st) {
+                                cudaStream_t st, bool df) {
   const unsigned gm = blocks_for(d.elems());
   const unsigned ge = red_grid(d.elems());
   const unsigned gn = blocks_for(d.nodes());
@@ -892,9 +978,13 @@ cudaError_t launch_simp_z_apply(const Dims& d, const double* K0, const double* r
                  Dinv, v, y, eb, partials, counter, sc);                                        \
     topo::launch(k_filter_w<DIM>, gm, kThreads, 0, st, d, rmin, R, invS, (const double*)eb, se, \
                  sc);                                                                           \
-    topo::launch(k_z_node<DIM, double, 0>, gn, kThreads, 0, st, d, K0, rho, gh,                 \
-                 (const double*)se, v, (const double*)nullptr, y, (const double*)nullptr, 1.0,  \
-                 fixed, (const double*)nullptr, sc, (const double*)nullptr);                    \
+    if (df)                                                                                     \
+      topo::launch(k_z_node_df<DIM>, gn, kThreads, 0, st, d, K0, rho, gh, (const double*)se, v, \
+                   y, fixed, sc);                                                               \
+    else                                                                                        \
+      topo::launch(k_z_node<DIM, double, 0>, gn, kThreads, 0, st, d, K0, rho, gh,               \
+                   (const double*)se, v, (const double*)nullptr, y, (const double*)nullptr,     \
+                   1.0, fixed, (const double*)nullptr, sc, (const double*)nullptr);             \
   } while (0)
   if (d.dim == 2)
     TOPO_SZ(2);

@@ -505,7 +505,14 @@ topo_status apply_outer(topo_solver* s, const double* v, double* y, const CgScal
     const Level& l0 = s->L[0];
     TOPO_CUDA(launch_simp_z_apply(l0.d, s->K0, s->x, s->g, s->simp.Dinv, s->simp.invS,
                                   s->simp.rmin, s->simp.R, s->simp.ea, s->simp.eb, s->se, v, y,
-                                  l0.fixed, s->partials, s->counters, sc, s->st));
+                                  l0.fixed, s->partials, s->counters, sc, s->st,
+                                  s->outer_df != 0));
+    return TOPO_OK;
+  }
+  if (s->arrow && s->outer_df) {
+    const Level& l0 = s->L[0];
+    TOPO_CUDA(launch_z_apply_fine_df(l0.d, s->K0, s->x, s->g, s->Dinv, s->se, v, y, l0.fixed,
+                                     s->zll, s->partials, s->counters, sc, s->st));
     return TOPO_OK;
   }
   return apply_level<double>(s, 0, 0, v, nullptr, y, sc);
@@ -1106,6 +1113,7 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
     TOPO_TRY(s->alloc(&s->xdf, m));
     s->outer_df = s->prec == TOPO_MIXED ? 1 : 0;
   }
+  if (arrow) s->outer_df = s->prec == TOPO_MIXED ? 1 : 0;  // the Z node pass in pairs
   if (s->prec == TOPO_MIXED) {
     TOPO_TRY(s->alloc(&s->x32, m));
     TOPO_TRY(s->alloc((float**)&s->rv, n * nrhs));

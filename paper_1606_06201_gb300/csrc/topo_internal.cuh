@@ -542,13 +542,21 @@ cudaError_t launch_filter_colsum(const Dims& d, double rmin, int R, double* invS
 cudaError_t launch_simp_density(const Dims& d, const SimpArgs& sa, const double* x,
                                 cudaStream_t st);
 // The exact SIMP augmented operator y = Z v (MODE 0):  a_e = gh_e^T v_e;
-// sb = Dinv (W^T a + v_lambda), y_lambda = sum sb;  se = W sb;  y_u = hat K v + sum_e gh_e se_e.
+// sb = Dinv (W^T a + v_lambda), y_lambda = sum sb;  se = W sb;  y_u = hat K v + sum_e gh_e se_e
+// (the node pass in float pairs when df).
 cudaError_t launch_simp_z_apply(const Dims& d, const double* K0, const double* rho,
                                 const double* gh, const double* Dinv, const double* invS,
                                 double rmin, int R, double* ea, double* eb, double* se,
                                 const double* v, double* y, const uint8_t* fixed,
                                 double* partials, unsigned* counter, const CgScalars* sc,
-                                cudaStream_t st);
+                                cudaStream_t st, bool df);
+// The finest-level Z operator y = Z v (MODE 0) of mixed-precision IP systems: the element pass in
+// FP64 (s_e and the lambda row), the node pass in float pairs (about 48 bits).
+cudaError_t launch_z_apply_fine_df(const Dims& d, const double* K0, const double* x,
+                                   const double* g, const double* Dinv, double* se,
+                                   const double* v, double* y, const uint8_t* fixed,
+                                   const double* zll, double* partials, unsigned* counter,
+                                   const CgScalars* sc, cudaStream_t st);
 cudaError_t launch_oc_bisection(long long m, const double* x, const double* E, OcScalars* oc,
                                 int steps, double* xout, double* partials, unsigned* counter,
                                 cudaStream_t st);
