@@ -344,7 +344,7 @@ def main():
         return out
 
     def simp_example4_runs():
-        """Sec. 9.1 Example 4 shape 427: the Example 2 beam on 256 x 128 (7 levels), xbar = 3,
+        """Sec. 9.1 Example 4 shape 427: the Example 2 beam on 256 x 128 (5 levels), xbar = 3,
         SIMP p = 3 with the Manhattan density filter r_min = 2, V = 0.4 m, mixed precision, CG
         capped at 1000 iterations (Sec. 8.1).  The paper's tau_CG = 1e-2 and a tight 1e-6, each
         bounded to 250 Newton steps; Newton steps per barrier value as in tab:202."""
@@ -352,7 +352,7 @@ def main():
         c4 = W.cantilever_2d(256, 128, 0.4)
         f4 = torch.as_tensor(c4["f"], device=dev)
         for tol in (1e-2, 1e-6):
-            ip = topo.IP(256, 128, fixed=c4["fixed"], f=f4, V=c4["V"], xbar=3.0, levels=7,
+            ip = topo.IP(256, 128, fixed=c4["fixed"], f=f4, V=c4["V"], xbar=3.0, levels=5,
                          precision=topo.MIXED, max_iter=1000, simp=(3.0, 2.0))
             opts = topo.ip_options(cg_tol=tol)
             torch.cuda.synchronize()
