@@ -6,7 +6,9 @@
 // the current iterate, a Galerkin hierarchy of Z with the lambda unknown carried by the identity
 // (Sec. 7), PCG on Z, the direction completed element-wise, the 0.9 step rule (Sec. 3.3), the
 // update, and the Newton test (Sec. 3.4) at the new iterate; when it holds, s and r are multiplied
-// by sigma (Sec. 3.2) and the method stops once max(s, r) <= tau_IP.
+// by sigma (Sec. 3.2) and the method stops once max(s, r) <= tau_IP.  With topo_ip_set_simp the same
+// loop runs the SIMP model with the density filter (Sec. 9): the stiffness coefficients are
+// (W x)^p and the residuals and the direction take hat B(u).
 #include <algorithm>
 #include <cmath>
 #include <string>

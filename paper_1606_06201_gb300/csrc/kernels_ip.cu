@@ -12,6 +12,12 @@
 // F3 = -1/2 u^T K_i u - lambda - phi_i + psi_i (the printed matrix with the sign that makes the
 // direction a Newton step of the KKT map).
 //
+// SIMP (Sec. 9).  hat B(u) = B(u) diag(c) W with c = p x~^(p-1) and the column-normalised density
+// filter W (so e^T W = e^T).  The augmented Z is then the matrix above with columns c_e g_e and with
+// D^{-1} replaced by M = W D^{-1} W^T: s = M (hat G^T v_u + e v_lambda), computed as one element pass,
+// a filtered pass with the lambda-row reduction, and a second filter pass.  The filter is a stencil
+// gather over the element grid (|o|_1 <= ceil(rmin) - 1) in a fixed order.
+//
 // OC.  The bisection on lambda of Algorithm OC compares sum_i x_i^NEW(lambda) with V using a
 // double-double (error-free TwoSum) reduction rounded once at the end, so the decision does not
 // depend on the summation order.
