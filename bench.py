@@ -189,7 +189,7 @@ def main():
     ap.add_argument("--no-ip", action="store_true", help="skip the 512x256 IP/OC wall-time runs")
     ap.add_argument("--outer-fp64", action="store_true",
                     help="mixed solver with the FP64 outer operator instead of float pairs")
-    ap.add_argument("--only", choices=["mixed", "fp64", "batched3d", "ip"], default=None,
+    ap.add_argument("--only", choices=["mixed", "fp64", "batched3d", "ip", "simp"], default=None,
                     help="run one solver configuration only (for profiler launch lists); no JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -386,6 +386,16 @@ def main():
         info = ip.run(topo.ip_options(cg_tol=1e-8, max_newton=args.steps))
         print("only=ip wall_ms=%.3f newton=%d cg_iters=%d" % (info.wall_ms, info.newton,
                                                               info.cg_iters))
+        ip.close()
+        return 0
+    if args.only == "simp":  # profiling aid: Example 4 shape 427 (SIMP), steps = Newton budget
+        c4 = W.cantilever_2d(256, 128, 0.4)
+        f4 = torch.as_tensor(c4["f"], device=dev)
+        ip = topo.IP(256, 128, fixed=c4["fixed"], f=f4, V=c4["V"], xbar=3.0, levels=5,
+                     precision=topo.MIXED, max_iter=1000, simp=(3.0, 2.0))
+        info = ip.run(topo.ip_options(cg_tol=1e-6, max_newton=args.steps))
+        print("only=simp wall_ms=%.3f newton=%d cg_iters=%d" % (info.wall_ms, info.newton,
+                                                                info.cg_iters))
         ip.close()
         return 0
     if args.only == "batched3d":
