@@ -74,3 +74,14 @@ def test_descriptor_validation_needs_no_device():
         st = topo._lib.topo_solver_create(ctypes.byref(d), ctypes.byref(h))
         assert st == topo.E_INVALID_ARG, kw
         assert not h.value
+
+
+def test_null_handles_are_rejected_without_a_device():
+    """Entry points given a null handle return TOPO_E_INVALID_ARG before any CUDA call."""
+    from paper_1606_06201_gb300 import topo
+    L = topo._lib
+    buf = (ctypes.c_double * 4)()
+    assert L.topo_ip_set_simp(None, ctypes.c_double(3.0), ctypes.c_double(2.0)) == topo.E_INVALID_ARG
+    assert L.topo_ip_filtered_density(None, buf) == topo.E_INVALID_ARG
+    assert L.topo_ip_set_vcycle_fusion(None, 1) == topo.E_INVALID_ARG
+    assert L.topo_set_outer_precision(None, 1) == topo.E_INVALID_ARG
