@@ -11,7 +11,12 @@ from oracle import fe, ip, simp
 from paper_1606_06201_gb300 import workloads as W
 
 
-def _problem(nx, ny, volfrac=0.4, xbar=3.0, p=3.0, rmin=2.0):
+def _problem(nx, ny, volfrac=0.4, xbar=3.0, p=3.0, rmin=2.0, nz=0):
+    if nz:
+        fixed = W.clamp_xmin(nx, ny, nz)
+        f = W.point_load(nx, ny, nz, (nx, ny // 2, nz // 2), 1)
+        return simp.SimpProblem(fe.Grid(nx, ny, nz), fe.element_stiffness(3), fixed, f,
+                                volfrac * nx * ny * nz, xbar, p=p, rmin=rmin)
     cfg = W.cantilever_2d(nx, ny, volfrac)
     return simp.SimpProblem(fe.Grid(nx, ny), fe.element_stiffness(2), cfg["fixed"], cfg["f"],
                             cfg["V"], xbar, p=p, rmin=rmin)
@@ -97,12 +102,12 @@ def _unpack(prob, v):
     return [u, v[nf], v[nf + 1:nf + 1 + m], v[nf + 1 + m:nf + 1 + 2 * m], v[nf + 1 + 2 * m:]]
 
 
-@pytest.mark.parametrize("shape,rmin", [((4, 2), 2.0), ((4, 4), 2.5)])
+@pytest.mark.parametrize("shape,rmin", [((4, 2), 2.0), ((4, 4), 2.5), ((2, 2, 2), 2.0)])
 def test_direction_solves_fd_jacobian_without_the_xx_block(shape, rmin):
     """The direction solves J d = -F for the finite-difference Jacobian J of the SIMP KKT map once
     its (row 3, x) block, the second derivative that the method leaves out, is set to zero.  Every
     other block (hat K, hat B in rows 1 and 3, the filter) comes from the map itself."""
-    prob = _problem(*shape, rmin=rmin)
+    prob = _problem(*shape[:2], rmin=rmin, nz=shape[2] if len(shape) == 3 else 0)
     s, r = 0.3, 0.2
     z = _interior_state(prob, 0)
     d, _ = simp.newton_direction(prob, z, s, r)
