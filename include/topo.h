@@ -218,7 +218,9 @@ topo_status topo_grad_x(topo_solver* s, const double* lam, const double* u, doub
  * are zero when the library loads and every call leaves them at zero.
  * The first call on a device looks the array up (cudaGetSymbolAddress) with that device
  * current; make it before any stream capture.  Calls that overlap on one device (other
- * streams or host threads) share the array and race: the caller orders them. */
+ * streams or host threads) share the array and race: the caller orders them.  The address is kept
+ * for the life of the process: after a device reset (cudaDeviceReset) the module may load at
+ * another address, so the entry point must not be called on that device again. */
 topo_status topo_compliance_noalloc(const double* f, const double* u, long long n, int nrhs,
                                     double* c, void* cuda_stream);
 

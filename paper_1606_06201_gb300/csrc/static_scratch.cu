@@ -13,6 +13,8 @@
 // one ticket counter per right-hand side, kMaxRhs right-hand sides at most (311,552 bytes).
 // Its address on a device is looked up once, by the first call made with that device current
 // (cudaGetSymbolAddress); that first call should therefore come before any stream capture.
+// The address is kept for the life of the process; after a device reset (cudaDeviceReset) the
+// module may load at another address, so the entry point must not be used on that device again.
 // The ticket counters must start at zero: the array is zero when the module loads, and every
 // reduction puts its counter back to zero when it finishes.  The partial sums need no start
 // value.  Calls whose kernels overlap on one device (other streams, other host threads) share
