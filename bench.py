@@ -31,20 +31,32 @@ sys.path.insert(0, ROOT)
 from paper_1606_06201_gb300 import workloads as W  # noqa: E402
 
 NX, NY, LEVELS, TOL = 2048, 1024, 9, 1e-8
+# the oracle's IP / AOC runs that give the errors against the oracle are collected at most this
+# long after the bench starts (on a GB300 host the 512 x 256 runs take about a minute each)
+ORACLE_DEADLINE_S = 420.0
+T_START = time.perf_counter()
 METRIC = "MGCG DOF·iterations/s at 1e-8 rel. residual (mixed: FP32 V-cycle, FP64 CG)"
 UNIT = "DOF·it/s"
 WORKLOAD = "mgcg_2d_q1_2048x1024_9lev_logunif_box5_normal_load"
-# FP64 pipe peak from unit counts and clock: 152 SMs x 2 FP64 instructions/clock x 2.07 GHz
-# (add, multiply and fused multiply-add each occupy one issue slot; a probe on this part measured
-# 0.60e12 FP64 FMA/s = 1.20 TFLOP/s).
-FP64_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
-# FP32 pipe peak the same way: 152 SMs x 128 FP32 lanes x 2.07 GHz, one operation per lane and
-# clock (an FMA counts as one).
-FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
-# FP64 operations of the FP64 butterfly operator kernel: 40 per element (two 4-point butterflies
-# per displacement component, 13 scalings, two inverse butterflies) + 6 node-assembly adds + 2 FMA
-# of the fused p^T q per node.
-OPS_PER_ELEM, OPS_PER_NODE = 40.0, 8.0
+# Derived issue peaks (not measured; MEASURED_PEAKS.json has the copy bandwidth and cuBLAS bf16
+# only): SMs x lanes x clock, with the SM count read from the device at run time
+# (cudaDeviceProp.multiProcessorCount: 152 on GB300) and the maximum SM clock of MEASURED_PEAKS.json
+# (2070 MHz).  FP64: 2 instructions per SM and clock (an add, multiply or fused multiply-add each
+# take one issue slot; a probe on this part measured 0.60e12 FP64 FMA/s); FP32: 128 lanes per SM,
+# one operation per lane and clock (an FMA counts as one).
+SM_COUNT_DEFAULT, SM_MHZ_DEFAULT = 152, 2070.0
+
+
+def derived_peaks(sm_count, sm_mhz):
+    """(FP64, FP32) issue rates in T operations/s from unit counts and clock."""
+    return sm_count * 2 * sm_mhz * 1e6 / 1e12, sm_count * 128 * sm_mhz * 1e6 / 1e12
+
+
+FP64_PEAK_TOPS, FP32_PEAK_TOPS = derived_peaks(SM_COUNT_DEFAULT, SM_MHZ_DEFAULT)
+# FP64 operations of the FP64 butterfly operator kernel: 37 per element (two 4-point butterflies
+# per displacement component: 15 adds; 8 products; 14 multiply-adds for the scalings and the inverse
+# butterflies) + 6 node-assembly adds + 2 FMA of the fused p^T q per node.
+OPS_PER_ELEM, OPS_PER_NODE = 37.0, 8.0
 # FP32 operations of the same operator in float pairs: per element 29 pair additions (11 FP32
 # operations each: TwoSum, the low parts, a renormalising FastTwoSum) and 12 pair products (7:
 # product, FMA error term, two cross FMAs, FastTwoSum), plus the 2 pair additions of the carried
@@ -52,9 +64,9 @@ OPS_PER_ELEM, OPS_PER_NODE = 40.0, 8.0
 # p^T q, and 2 FP32 multiplies of each of the two input splits.
 DF_OPS_PER_ELEM = 29 * 11 + 12 * 7 + 2 * 11
 DF_OPS_PER_NODE = 4 * 11 + 2 * 7 + 2 * 11 + 4
-# DRAM bytes of one launch of the FP64 operator on this workload from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum = 55.21 MB + 3.51 MB).
-OPERATOR_DRAM_BYTES = 58712320.0
+# DRAM bytes of one launch of the FP64 operator on this workload from an ncu capture; None until
+# the operator as built now (37-operation element product) has been captured.
+OPERATOR_DRAM_BYTES = None
 # The same for the float-pair operator (ncu capture of k_q1_sweep_df on this workload:
 # 54.94 MB read + 2.53 MB write).
 DF_OPERATOR_DRAM_BYTES = 57463808.0
@@ -67,6 +79,15 @@ def _measured_hbm_gbs():
             return float(json.load(fh)["hbm_gbs"])
     except (OSError, KeyError, ValueError):
         return 6800.0
+
+
+def _measured_sm_max_mhz():
+    """Maximum SM clock recorded with the measured peaks, else 2070 MHz."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["sm_max_mhz"])
+    except (OSError, KeyError, ValueError):
+        return SM_MHZ_DEFAULT
 
 
 def _dist():
@@ -189,14 +210,37 @@ def main():
     ap.add_argument("--no-ip", action="store_true", help="skip the 512x256 IP/OC wall-time runs")
     ap.add_argument("--outer-fp64", action="store_true",
                     help="mixed solver with the FP64 outer operator instead of float pairs")
-    ap.add_argument("--only", choices=["mixed", "fp64", "batched3d", "ip", "simp"], default=None,
-                    help="run one solver configuration only (for profiler launch lists); no JSON line")
+    ap.add_argument("--only", choices=["mixed", "fp64", "batched3d", "ip", "simp", "oc_accuracy"],
+                    default=None,
+                    help="run one solver configuration only (for profiler launch lists); no JSON "
+                         "line.  oc_accuracy: the Sec. 8.2-8.3 accuracy study (one JSON line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
 
-    import torch
     ws, rank = _dist()
+    # the CPU baseline first, on an idle host (the oracle processes below share its cores)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and not args.only:
+        v, t, runs, nf, it = oracle_mgcg_sample(1024, 512, 8, seconds=10.0)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "oracle MGCG (scipy sparse, FP64, single thread) on the same recipe at "
+                         "1024x512 (%d free DOFs, 8 levels), %d run(s), %.1f s" % (nf, runs, t)}
+    # the oracle's IP and AOC runs of the Example-2-shaped workloads (64 x 32 and 512 x 256), for
+    # the errors against the oracle beside the GPU runs: started now, in two spawned CPU
+    # processes that share the host's cores, and collected after the GPU work
+    oracle_jobs, oracle_pool = {}, None
+    if rank == 0 and not args.no_ip and not args.only:
+        from oracle import runs as oruns
+        oracle_pool, _ = oruns.spawn_pool(2)
+        oracle_jobs = {
+            "c1": (oracle_pool.apply_async(oruns.ip_run, (64, 32, 0.5)),
+                   oracle_pool.apply_async(oruns.aoc_run, (64, 32, 0.5, 50))),
+            "c2": (oracle_pool.apply_async(oruns.ip_run, (512, 256, 0.4)),
+                   oracle_pool.apply_async(oruns.aoc_run, (512, 256, 0.4, 50)))}
+        oracle_pool.close()
+
+    import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
@@ -269,13 +313,20 @@ def main():
 
     def batched_3d_run(steps=3, warmup=3):
         """128x64x64 hex grid (1.6M DOFs, 5 levels), 8 unit point loads on the x = max face as one
-        batched mixed solve per step (hierarchy build + PCG to 1e-8 for all 8); DOF*iterations
-        summed over the load cases."""
+        batched mixed solve per step (hierarchy build + PCG to 1e-8 for all 8) with the
+        autotuner's smoother (damped Jacobi omega x nu, Chebyshev degree); DOF*iterations summed
+        over the load cases."""
+        from paper_1606_06201_gb300 import autotune
         c4 = W.random_field_3d(128, 64, 64, n_rhs=8)
         nfree4 = int(np.count_nonzero(c4["fixed"] == 0))
         x4 = torch.as_tensor(c4["x"], device=dev)
         f4 = torch.as_tensor(c4["f"], device=dev)
-        s4 = topo.Solver(128, 64, 64, fixed=c4["fixed"], levels=5, precision=topo.MIXED, nrhs=8)
+        t_tune = time.perf_counter()
+        tuned = autotune.autotune(128, 64, 64, c4["fixed"], x4, f4, 5, precision=topo.MIXED,
+                                  nrhs=8, tol=TOL, sweeps=(1, 2, 3), cheb_degrees=(1, 2, 3),
+                                  reps=1)
+        t_tune = time.perf_counter() - t_tune
+        s4 = autotune.solver_for(tuned, 128, 64, 64, c4["fixed"], 5, precision=topo.MIXED, nrhs=8)
         u4 = torch.zeros_like(f4)
         for _ in range(warmup):
             s4.set_density(x4)
@@ -296,27 +347,40 @@ def main():
                 "nrhs": 8, "steps": steps, "ms_per_step": ms / steps,
                 "iterations_per_solve": iters / steps,
                 "value": 8 * nfree4 * iters / (ms * 1e-3), "unit": UNIT,
-                "smoother": "damped Jacobi omega=0.5 nu1=nu2=2",
-                "precision": "FP32 V-cycle, FP64 CG and outer operator"}
+                "smoother": ("%s omega=%g nu1=nu2=%d (autotuned over %d settings in %.1f s, "
+                             "outside the timed steps)" % (tuned["smoother"], tuned["omega"],
+                                                          tuned["nu"], tuned["tried"], t_tune)),
+                "precision": "FP32 V-cycle, FP64 CG recurrences and dots, outer operator in "
+                             "float pairs (~48-bit)"}
 
-    def ip_oc_runs():
-        """512x256 cantilever (Example 2 shape 428, V = 0.4 m, 6 levels): IP and AOC with 50 outer
-        iterations each (linear solves to 1e-8), FP64 and mixed."""
+    def err_vs_oracle(x, u, c, o):
+        """Errors of a GPU run against the oracle's (exact solves): x in the max norm relative to
+        max|x|, u in the 2-norm relative, compliance relative."""
+        return {"x_max_rel": float(np.max(np.abs(x - o["x"])) / np.max(np.abs(o["x"]))),
+                "u_rel": float(np.linalg.norm(u - o["u"]) / np.linalg.norm(o["u"])),
+                "compliance_rel": float(abs(c - o["compliance"]) / abs(o["compliance"]))}
+
+    def ip_oc_runs(nx, ny, volfrac, levels, jobs, with_inexact):
+        """Example-2-shaped cantilever (V = volfrac m): IP (to tau_IP) and AOC (50 linear solves),
+        FP64 and mixed, linear solves to 1e-8; each with its error against the oracle's run of
+        the same problem (exact solves, Cholesky), whose wall time and cores are reported."""
         out = {}
-        c2 = W.cantilever_2d(512, 256, 0.4)
+        c2 = W.cantilever_2d(nx, ny, volfrac)
         f2 = torch.as_tensor(c2["f"], device=dev)
+        gpu = {}
         for name, prec in (("fp64", topo.FP64), ("mixed", topo.MIXED)):
-            ip = topo.IP(512, 256, fixed=c2["fixed"], f=f2, V=c2["V"], xbar=1.0, levels=6,
+            ip = topo.IP(nx, ny, fixed=c2["fixed"], f=f2, V=c2["V"], xbar=1.0, levels=levels,
                          precision=prec, max_iter=1000)
             info = ip.run(topo.ip_options(cg_tol=1e-8, max_newton=50))
-            u = ip.state()[0]
-            if prec == topo.MIXED:
-                x_exact = ip.state()[1]
+            u, x = ip.state()[:2]
             out["ip_" + name] = {"wall_s": info.wall_ms * 1e-3, "newton": info.newton,
                                  "ip_iters": info.ip_iters, "cg_iters": info.cg_iters,
                                  "feval": info.feval, "compliance": float(f2 @ u), "done": info.done}
+            gpu["ip_" + name] = (x.cpu().numpy(), u.cpu().numpy(), float(f2 @ u))
+            if prec == topo.MIXED:
+                x_exact = x
             ip.close()
-            oc = topo.OC(512, 256, fixed=c2["fixed"], f=f2, V=c2["V"], xbar=1.0, levels=6,
+            oc = topo.OC(nx, ny, fixed=c2["fixed"], f=f2, V=c2["V"], xbar=1.0, levels=levels,
                          precision=prec)
             oc.init()
             oinfo = oc.run(topo.oc_options(max_feval=50, tau_oc=0.0, cg_tol0=1e-8,
@@ -324,24 +388,98 @@ def main():
             out["aoc_" + name] = {"wall_s": oinfo.wall_ms * 1e-3, "feval": oinfo.feval,
                                   "iters": oinfo.iters, "cg_iters": oinfo.cg_iters,
                                   "compliance": oinfo.compliance}
+            gpu["aoc_" + name] = oc.x().cpu().numpy()
             oc.close()
-        # Sec. 8.1 settings (tab:IP): every PCG stopped at 1e-2 ("CG tol fixed"), or at 1e-2
-        # halved at every barrier reduction ("CG tol decreasing"); mixed precision, to tau_IP
-        x_ref = x_exact
-        for name, fac in (("fixed", 1.0), ("decreasing", 0.5)):
-            ip = topo.IP(512, 256, fixed=c2["fixed"], f=f2, V=c2["V"], xbar=1.0, levels=6,
-                         precision=topo.MIXED, max_iter=1000)
-            info = ip.run(topo.ip_options(cg_tol=1e-2, cg_tol_factor=fac, max_newton=500))
-            u, x = ip.state()[:2]
-            out["ip_mixed_tau_cg_1e-2_" + name] = {
-                "wall_s": info.wall_ms * 1e-3, "newton": info.newton, "ip_iters": info.ip_iters,
-                "cg_iters": info.cg_iters, "feval": info.feval,
-                "cg_iters_per_system": info.cg_iters / max(info.feval, 1),
-                "compliance": float(f2 @ u), "x_min": float(x.min()),
-                "max_abs_x_diff_vs_cg_tol_1e-8": float((x - x_ref).abs().max()),
-                "done": info.done}
-            ip.close()
+        if with_inexact:
+            # Sec. 8.1 settings (tab:IP): every PCG stopped at 1e-2 ("CG tol fixed"), or at 1e-2
+            # halved at every barrier reduction ("CG tol decreasing"); mixed precision, to tau_IP
+            x_ref = x_exact
+            for name, fac in (("fixed", 1.0), ("decreasing", 0.5)):
+                ip = topo.IP(nx, ny, fixed=c2["fixed"], f=f2, V=c2["V"], xbar=1.0, levels=levels,
+                             precision=topo.MIXED, max_iter=1000)
+                info = ip.run(topo.ip_options(cg_tol=1e-2, cg_tol_factor=fac, max_newton=500))
+                u, x = ip.state()[:2]
+                out["ip_mixed_tau_cg_1e-2_" + name] = {
+                    "wall_s": info.wall_ms * 1e-3, "newton": info.newton, "ip_iters": info.ip_iters,
+                    "cg_iters": info.cg_iters, "feval": info.feval,
+                    "cg_iters_per_system": info.cg_iters / max(info.feval, 1),
+                    "compliance": float(f2 @ u), "x_min": float(x.min()),
+                    "max_abs_x_diff_vs_cg_tol_1e-8": float((x - x_ref).abs().max()),
+                    "done": info.done}
+                ip.close()
+        # the oracle's runs (started before the GPU work, in spawned CPU processes)
+        try:
+            o_ip = jobs[0].get(timeout=max(1.0, ORACLE_DEADLINE_S - (time.perf_counter() - T_START)))
+            o_oc = jobs[1].get(timeout=max(1.0, ORACLE_DEADLINE_S - (time.perf_counter() - T_START)))
+        except Exception as exc:  # reported, not fatal for the GPU numbers
+            out["oracle"] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+            return out
+        for name in ("fp64", "mixed"):
+            x, u, c = gpu["ip_" + name]
+            out["ip_" + name]["err_vs_oracle"] = err_vs_oracle(x, u, c, o_ip)
+            xo = gpu["aoc_" + name]
+            out["aoc_" + name]["err_vs_oracle"] = {
+                "x_max_rel": float(np.max(np.abs(xo - o_oc["x"])) / np.max(np.abs(o_oc["x"]))),
+                "compliance_rel": float(abs(out["aoc_" + name]["compliance"] - o_oc["compliance"][-1])
+                                        / abs(o_oc["compliance"][-1]))}
+        out["oracle"] = {"kind": "oracle (scipy sparse assembly, banded Cholesky: exact solves)",
+                         "cores": o_ip["cores"], "ip_wall_s": o_ip["wall_s"],
+                         "ip_newton": o_ip["newton"], "ip_compliance": o_ip["compliance"],
+                         "aoc_wall_s": o_oc["wall_s"], "aoc_feval": o_oc["feval"],
+                         "aoc_compliance": o_oc["compliance"][-1]}
         return out
+
+    def oc_accuracy_study(n_inf=5000):
+        """Sec. 8.2-8.3 (tab:exact1, tab:exact2) on Example 1's problem 226 (the 64 x 64 square,
+        left edge clamped, unit load at the right-edge midpoint, V = 0.5 m, xbar = 1): AOC runs
+        stopped by Eq. (OCstop) at tau_OC = 1e-5, 1e-7, 1e-9 and after n_inf iterations (the
+        paper's "-inf"), for the lower bounds 1e-7 and 1e-17; the pairwise 2-norm and max-norm
+        differences of their x; and the IP at tau_IP = 1e-8 ... 1e-14 against the "-inf" OC
+        solution with lower bound 1e-17.  FP64, linear solves to 1e-12 (the paper uses a direct
+        solver here)."""
+        cfg = W.cantilever_2d(64, 64, 0.5)
+        f1 = torch.as_tensor(cfg["f"], device=dev)
+        sols, meta = {}, {}
+        for xlow in (1e-7, 1e-17):
+            for tau in (1e-5, 1e-7, 1e-9, None):
+                oc = topo.OC(64, 64, fixed=cfg["fixed"], f=f1, V=cfg["V"], xbar=1.0, levels=5,
+                             precision=topo.FP64, max_iter=2000)
+                oc.init()
+                opts = topo.oc_options(variant=topo.OC_AOC, xlow=xlow,
+                                       tau_oc=tau if tau else 0.0,
+                                       max_feval=2 * n_inf,
+                                       cg_tol0=1e-12, adaptive_tol=False)
+                try:
+                    info = oc.run(opts)
+                    key = "%g/%s" % (xlow, "-inf" if tau is None else "%g" % tau)
+                    sols[key] = oc.x().cpu().numpy()
+                    meta[key] = {"iters": info.iters, "feval": info.feval, "cg_iters": info.cg_iters,
+                                 "compliance": info.compliance, "wall_s": info.wall_ms * 1e-3,
+                                 "status": info.status}
+                except topo.TopoError as exc:
+                    meta["%g/%s" % (xlow, tau)] = {"error": str(exc)}
+                oc.close()
+        keys = list(sols)
+        pair = {a: {b: [float(np.linalg.norm(sols[a] - sols[b])),
+                        float(np.max(np.abs(sols[a] - sols[b])))] for b in keys} for a in keys}
+        ipres = {}
+        ref = sols.get("1e-17/-inf")
+        for tau_ip in (1e-8, 1e-10, 1e-12, 1e-14):
+            ip = topo.IP(64, 64, fixed=cfg["fixed"], f=f1, V=cfg["V"], xbar=1.0, levels=5,
+                         precision=topo.FP64, max_iter=5000)
+            try:
+                info = ip.run(topo.ip_options(tau_ip=tau_ip, cg_tol=1e-12, max_newton=500))
+                x = ip.state()[1].cpu().numpy()
+                ipres["%g" % tau_ip] = {"newton": info.newton, "ip_iters": info.ip_iters,
+                                        "done": info.done}
+                if ref is not None:
+                    ipres["%g" % tau_ip].update(err_2=float(np.linalg.norm(x - ref)),
+                                                err_max=float(np.max(np.abs(x - ref))))
+            except topo.TopoError as exc:
+                ipres["%g" % tau_ip] = {"error": str(exc)}
+            ip.close()
+        return {"study": "Sec. 8.2 tab:exact1 / Sec. 8.3 tab:exact2 on problem 226 (64 x 64)",
+                "oc_runs": meta, "oc_pairwise_2norm_maxnorm": pair, "ip_vs_oc_inf": ipres}
 
     def simp_example4_runs():
         """Sec. 9.1 Example 4 shape 427: the Example 2 beam on 256 x 128 (5 levels), xbar = 3,
@@ -398,6 +536,9 @@ def main():
                                                                 info.cg_iters))
         ip.close()
         return 0
+    if args.only == "oc_accuracy":
+        print(json.dumps(oc_accuracy_study()), flush=True)
+        return 0
     if args.only == "batched3d":
         r = batched_3d_run(args.steps, args.warmup)
         print("only=batched3d ms_per_step=%.3f iterations=%.1f" % (r["ms_per_step"],
@@ -436,27 +577,42 @@ def main():
         nodes = (NX + 1) * (NY + 1)
         op_ms, op_cnt = mixed["prof"]
         op_avg_ms = op_ms / op_cnt if op_cnt else float("nan")
-        alg_bytes = 8.0 * m + 16.0 * n + 1.0 * n  # densities (FP64 or float pair), p, q, mask
+        # the method's bytes of one K(x) p (Sec. 8(d): p and q at 16 B per node each, x at 8 B per
+        # element as a float pair, the fixed-DOF mask at 1 B per DOF)
+        alg_bytes = 8.0 * m + 16.0 * n + 1.0 * n
+        hbm_peak = _measured_hbm_gbs()
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        sm_mhz = _measured_sm_max_mhz()
+        fp64_peak, fp32_peak = derived_peaks(sm_count, sm_mhz)
+        peak_src = ("derived, not measured: %d SMs (cudaDeviceProp.multiProcessorCount) x %s x "
+                    "%.0f MHz (maximum SM clock)")
         if args.outer_fp64:
             ops_per_launch = OPS_PER_ELEM * m + OPS_PER_NODE * nodes
-            achieved = ops_per_launch / (op_avg_ms * 1e-3) / 1e12
-            roof = {"kernel": "k_q1_sweep<double,0,1> (outer FP64 operator q = K(x) p, fused p^T q)",
-                    "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TOPS,
-                    "unit": "T FP64-op/s", "frac": achieved / FP64_PEAK_TOPS,
-                    "traffic": OPERATOR_DRAM_BYTES,
-                    "peak_source": "derived: 152 SMs x 2 FP64 issue slots/clk x 2.07 GHz"}
+            kname = "k_q1_sweep<double,0,1> (outer FP64 operator q = K(x) p, fused p^T q)"
+            issue = {"bound": "alu", "achieved": ops_per_launch / (op_avg_ms * 1e-3) / 1e12,
+                     "peak": fp64_peak, "unit": "T FP64-op/s",
+                     "peak_source": peak_src % (sm_count, "2 FP64 issue slots", sm_mhz),
+                     "algorithmic_ops_per_launch": ops_per_launch}
+            traffic = OPERATOR_DRAM_BYTES
         else:
             ops_per_launch = DF_OPS_PER_ELEM * m + DF_OPS_PER_NODE * nodes
-            achieved = ops_per_launch / (op_avg_ms * 1e-3) / 1e12
-            roof = {"kernel": "k_q1_sweep_df (outer operator q = K(x) p in float pairs, fused p^T q)",
-                    "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TOPS,
-                    "unit": "T FP32-op/s", "frac": achieved / FP32_PEAK_TOPS,
-                    "traffic": DF_OPERATOR_DRAM_BYTES,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"}
-        roof.update({"algorithmic_ops_per_launch": ops_per_launch,
-                     "algorithmic_bytes_per_launch": alg_bytes,
-                     "hbm_gbs_at_algorithmic_bytes": alg_bytes / (op_avg_ms * 1e-3) / 1e9,
-                     "avg_launch_ms": op_avg_ms, "launches_timed": op_cnt})
+            kname = "k_q1_sweep_df (outer operator q = K(x) p in float pairs, fused p^T q)"
+            issue = {"bound": "alu", "achieved": ops_per_launch / (op_avg_ms * 1e-3) / 1e12,
+                     "peak": fp32_peak, "unit": "T FP32-op/s",
+                     "peak_source": peak_src % (sm_count, "128 FP32 lanes", sm_mhz),
+                     "algorithmic_ops_per_launch": ops_per_launch,
+                     "note": "operations of the pair arithmetic as written (425 FP32 ops per "
+                             "element + 84 per node), against the derived FP32 issue rate"}
+            traffic = DF_OPERATOR_DRAM_BYTES
+        issue["frac"] = issue["achieved"] / issue["peak"]
+        achieved = alg_bytes / (op_avg_ms * 1e-3) / 1e9
+        roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "bytes_model": "8 B per element (x) + 16 B per DOF (p, q) + 1 B per DOF (mask)",
+                "avg_launch_ms": op_avg_ms, "launches_timed": op_cnt,
+                "issue_view": issue}
         f_ms, f_cnt = fp64["prof"]
         fp64_op = None
         if f_cnt:
@@ -464,25 +620,28 @@ def main():
             f_ops = OPS_PER_ELEM * m + OPS_PER_NODE * nodes
             fp64_op = {"kernel": "k_q1_sweep<double,0,1> (FP64 solver's outer operator)",
                        "bound": "alu", "achieved": f_ops / (f_avg * 1e-3) / 1e12,
-                       "peak": FP64_PEAK_TOPS, "unit": "T FP64-op/s",
-                       "frac": f_ops / (f_avg * 1e-3) / 1e12 / FP64_PEAK_TOPS,
+                       "peak": fp64_peak, "unit": "T FP64-op/s",
+                       "frac": f_ops / (f_avg * 1e-3) / 1e12 / fp64_peak,
+                       "peak_source": peak_src % (sm_count, "2 FP64 issue slots", sm_mhz),
                        "traffic": OPERATOR_DRAM_BYTES, "avg_launch_ms": f_avg,
-                       "launches_timed": f_cnt}
+                       "launches_timed": f_cnt,
+                       "hbm_view": {"achieved": alg_bytes / (f_avg * 1e-3) / 1e9,
+                                    "peak": hbm_peak, "unit": "GB/s",
+                                    "frac": alg_bytes / (f_avg * 1e-3) / 1e9 / hbm_peak}}
         # HBM-bound kernels of the FP32 V-cycle on the finest level, timed live like the operator:
         # algorithmic bytes per launch (FP32 vectors of n DOFs, FP32 densities of m elements, the
         # byte mask) / average launch time, against the measured copy bandwidth.
-        hbm_peak = _measured_hbm_gbs()
         nc = ((NX // 2) + 1) * ((NY // 2) + 1) * 2
         hbm_bytes = {
-            "fine_smoothing_sweep": ("k_q1_fused<float,4>: first two Jacobi sweeps from zero, "
+            "fine_smoothing_sweep": ("k_q1w<float,4,0>: first two Jacobi sweeps from zero, "
                                      "z = omega D^-1 b formed on the fly, diag from x",
                                      4.0 * m + 9.0 * n),
-            "fine_residual": (("k_q1_resrestrict<float>: b_c = P^T (b - K(x) z) in one pass, the "
+            "fine_residual": (("k_q1w_resrestrict<float>: b_c = P^T (b - K(x) z) in one pass, the "
                                "residual not stored", 4.0 * m + 9.0 * n + 5.0 * nc)
                               if kinds_run["kinds"] and not kinds_run["kinds"][3][1] else
-                              ("k_q1_sweep<float,1,0>: r = b - K(x) z", 4.0 * m + 13.0 * n)),
+                              ("k_q1w<float,1,0>: r = b - K(x) z", 4.0 * m + 13.0 * n)),
             "fine_restriction": ("k_restrict<2,float>: b_c = P^T r", 4.0 * n + 5.0 * nc),
-            "fine_prolongation": ("k_q1_fused<float,5>: v = z + P z_c formed on the fly, then "
+            "fine_prolongation": ("k_q1w<float,5,0>: v = z + P z_c formed on the fly, then "
                                   "one Jacobi sweep", 4.0 * m + 13.0 * n + 4.0 * nc),
         }
         hbm_kernels = []
@@ -512,12 +671,6 @@ def main():
                          "unit": "us per CG iteration (live CUDA events, mixed solver, separate fully "
                                  "profiled run)",
                          "step_us": step_us}
-        cpu = None
-        if not args.no_cpu_baseline:
-            v, t, runs, nf, it = oracle_mgcg_sample(1024, 512, 8, seconds=10.0)
-            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": "oracle MGCG (scipy sparse, FP64, single thread) on the same recipe at "
-                             "1024x512 (%d free DOFs, 8 levels), %d run(s), %.1f s" % (nf, runs, t)}
         bi = 8 * (m + n)
         bo = 8 * n
         line = {
@@ -555,14 +708,21 @@ def main():
             except topo.TopoError as exc:
                 line["batched_3d_128x64x64"] = {"error": str(exc)}
             try:
-                line["ip_oc_512x256"] = ip_oc_runs()
+                line["ip_oc_64x32"] = ip_oc_runs(64, 32, 0.5, 3, oracle_jobs["c1"], False)
             except topo.TopoError as exc:  # reported, not fatal for the headline measurement
+                line["ip_oc_64x32"] = {"error": str(exc)}
+            try:
+                line["ip_oc_512x256"] = ip_oc_runs(512, 256, 0.4, 6, oracle_jobs["c2"], True)
+            except topo.TopoError as exc:
                 line["ip_oc_512x256"] = {"error": str(exc)}
             try:
                 line["simp_example4_256x128"] = simp_example4_runs()
             except topo.TopoError as exc:
                 line["simp_example4_256x128"] = {"error": str(exc)}
         print(json.dumps(line), flush=True)
+    if oracle_pool is not None:
+        oracle_pool.terminate()
+        oracle_pool.join()
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0

@@ -81,6 +81,15 @@ typedef struct {
                            systems; levels >= 1 otherwise).
                            IP drivers always use it: the element rank-one terms of Z push
                            lambda_max(D^{-1} Z) well above the value for K(x). */
+  const double* K0;     /* [host] the element stiffness K_i of Eq. (to) for a unit element, ne x ne
+                           row-major (ne = 8 in 2D, 24 in 3D; local node-major DOF order), read
+                           during topo_solver_create only; NULL: the analytic K0 of
+                           topo_element_stiffness(dim, E, nu), and E, nu are used for nothing
+                           else.  It must be finite and symmetric (|K0_ij - K0_ji| <= 1e-12
+                           max|K0|), else TOPO_E_INVALID_ARG.  The specialised finest-level
+                           kernels (2D butterfly, 3D Walsh-Hadamard basis) are used when K0 has
+                           their structure (checked to 1e-14), the generic element-matrix
+                           kernels otherwise. */
 } topo_solver_desc;
 
 typedef struct {
@@ -105,8 +114,20 @@ topo_status topo_element_stiffness(int dim, double E, double nu, double* K0_out)
  * current CUDA device.  Returns TOPO_E_INVALID_ARG if the masks are not compatible with
  * geometric coarsening (a fixed fine DOF must interpolate only from fixed coarse DOFs). */
 topo_status topo_solver_create(const topo_solver_desc* desc, topo_solver** out);
+/* Device bytes that topo_solver_create(desc) would allocate (the hierarchy, the coarsest dense
+ * matrices, the CG vectors and scratch), computed on the host without a device or an allocation;
+ * the same value topo_solver_device_bytes reports after the create.  Descriptor errors as
+ * topo_solver_create.  bytes [host]. */
+topo_status topo_solver_workspace_bytes(const topo_solver_desc* desc, size_t* bytes);
 topo_status topo_solver_destroy(topo_solver* s);
 topo_status topo_set_stream(topo_solver* s, void* cuda_stream);
+/* Per-solve records: with path [host] non-NULL every solve of this solver (topo_solve, and the
+ * linear solves inside the IP and OC drivers that own it) appends one JSON line to the file:
+ * the system ("K" or "Z"), grid, levels, precision, smoother, nrhs, free DOFs, tolerance,
+ * iterations, final relative residual, wall time, DOF-iterations per second and status.  NULL
+ * stops recording.  A file that cannot be opened is skipped silently (recording never fails a
+ * solve). */
+topo_status topo_set_record_file(topo_solver* s, const char* path);
 /* How topo_solve drives the CG iterations of Algorithm PCG (Sec. 5.2); both give the same bits.
  * mode 0 (default): a captured graph of 4 iterations that the host replays, reading the scalars
  * back after each replay.  mode 1: one graph launch per solve, whose conditional while node
@@ -114,6 +135,12 @@ topo_status topo_set_stream(topo_solver* s, void* cuda_stream);
  * (falls back to mode 0 where conditional graph nodes are unavailable, and while profiling).
  * Other modes -> E_INVALID_ARG. */
 topo_status topo_set_graph_mode(topo_solver* s, int mode);
+/* Strip height of the 2D finest-level FP32 warp sweeps (Algorithm MG's smoother, residual and
+ * transfers on the finest level of mixed solvers): each warp walks rows node rows of its column
+ * tile, recomputing one element row at the strip's lower edge.  0 (default) picks the height that
+ * fills about one wave of warps; 2..32 fixes it (a tuning parameter: the outputs do not depend on
+ * it, except for the summation order of the fused r~^T y~).  Other values -> E_INVALID_ARG. */
+topo_status topo_set_sweep_rows(topo_solver* s, int rows);
 /* Fused kernels in Algorithm MG for 2D K systems with Jacobi smoothing (default on; off: one
  * launch per sweep, residual and transfer).  On the finest level the first two sweeps from zero
  * are one kernel, and so are the residual with the restriction, and the prolongation with the
@@ -352,6 +379,25 @@ topo_status topo_oc_step(topo_oc* oc, const topo_oc_opts* opts, topo_oc_info* in
 topo_status topo_oc_run(topo_oc* oc, const topo_oc_opts* opts, topo_oc_info* info);
 topo_status topo_oc_get_x(topo_oc* oc, double* x);
 topo_status topo_oc_get_u(topo_oc* oc, double* u);
+/* Checkpoint / resume of an OC run: x [device, m] (the iterate the next step starts from),
+ * u [device, n] (the last displacement, the warm start of the next solve), scal [host, 7] =
+ * the CG tolerance in force (Sec. 6.2), the compliance of the previous and of the last iteration
+ * (NaN before there is one), whether u holds a solve (1) or not (0), and the counts of linear
+ * solves, iterations and CG iterations so far (as doubles).  A run resumed from a snapshot repeats
+ * the uninterrupted run bit for bit (with power-iteration damping or Chebyshev smoothing, restore
+ * the solver's power-iteration vectors too: topo_oc_get_power_state).  Both synchronize the OC's
+ * stream; set returns TOPO_E_INVALID_ARG for a non-finite or negative tolerance or count. */
+topo_status topo_oc_get_state(topo_oc* oc, double* x, double* u, double* scal);
+/* Per-solve JSONL records of the linear solves inside the OC and IP drivers (as
+ * topo_set_record_file; the IP's records name the system "K" for the initial solve and "Z" for the
+ * Newton systems). */
+topo_status topo_oc_set_record_file(topo_oc* oc, const char* path);
+topo_status topo_ip_set_record_file(topo_ip* ip, const char* path);
+topo_status topo_oc_set_state(topo_oc* oc, const double* x, const double* u, const double* scal);
+/* The power-iteration vectors of the OC's solver (as topo_ip_power_state_size and friends). */
+topo_status topo_oc_power_state_size(topo_oc* oc, long long* len);
+topo_status topo_oc_get_power_state(topo_oc* oc, double* v, int* ready);
+topo_status topo_oc_set_power_state(topo_oc* oc, const double* v, int ready);
 
 #ifdef __cplusplus
 }

@@ -20,6 +20,7 @@ ip        primal-dual interior-point method (Sec. 2-3, Eq. (nwt), (nwtr), (nwtr2
 simp      SIMP model with the density filter and its IP method (Sec. 9)
 oc        OC / damped OC / averaged OC (Sec. 4)
 grad      adjoint gradient of a linear functional of u
+runs      whole IP / AOC runs with per-step records, and a process pool to run them beside a GPU
 
 Functions without an independent pin say so in their docstring ("parity unpinned").
 """

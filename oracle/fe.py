@@ -90,14 +90,15 @@ def elasticity_matrix(dim, E=1.0, nu=0.3):
     return D
 
 
-def element_stiffness(dim, E=1.0, nu=0.3, h=1.0):
+def element_stiffness(dim, E=1.0, nu=0.3, h=1.0, D=None):
     """Element stiffness K0 = int B^T D B over one square (cube) element of side h with unit
     thickness, by tensor Gauss quadrature (2 points per direction; exact for Q1/trilinear).
 
     Sec. 7: square elements, bilinear u, E = 1, nu = 0.3.  In 2D K0 does not depend on h;
-    in 3D it scales with h.
+    in 3D it scales with h.  D: another constitutive matrix (Voigt order as elasticity_matrix),
+    for an anisotropic material; default the isotropic one of E, nu.
     """
-    D = elasticity_matrix(dim, E, nu)
+    D = elasticity_matrix(dim, E, nu) if D is None else np.asarray(D, dtype=float)
     pts, wts = _gauss2()
     if dim == 2:
         corners = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], dtype=float)

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtopo_gb300.so")
-SOURCES = ["kernels_fe.cu", "kernels_q1.cu", "kernels_hex.cu", "kernels_rap.cu", "kernels_pcg.cu",
+SOURCES = ["kernels_fe.cu", "kernels_q1.cu", "kernels_q1w.cu", "kernels_hex.cu", "kernels_rap.cu", "kernels_pcg.cu",
            "kernels_ip.cu",
            "solver.cu", "ipoc.cu", "static_scratch.cu",
            "element.cpp"]

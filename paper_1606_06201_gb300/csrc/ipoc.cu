@@ -334,6 +334,7 @@ topo_status check_ip_opts(const topo_ip_opts* o, const char* where) {
 }
 
 topo_status topo_ip_init(topo_ip* a, const topo_ip_opts* o) {
+  NvtxRange nvtx("topo: IP init (Sec. 3.1)");
   if (!a || !o) return TOPO_E_INVALID_ARG;
   TOPO_TRY(check_ip_opts(o, "topo_ip_init"));
   StreamGuard gd(a->Z);
@@ -370,6 +371,7 @@ topo_status topo_ip_init(topo_ip* a, const topo_ip_opts* o) {
 }
 
 topo_status topo_ip_step(topo_ip* a, const topo_ip_opts* o, topo_ip_info* info) {
+  NvtxRange nvtx("topo: IP Newton step (Sec. 3.1)");
   if (!a || !o) return TOPO_E_INVALID_ARG;
   TOPO_TRY(check_ip_opts(o, "topo_ip_step"));
   if (a->done) {
@@ -640,6 +642,7 @@ topo_status oc_operator(topo_oc* a, const topo_oc_opts* o, const double* xin, do
 }  // namespace
 
 topo_status topo_oc_step(topo_oc* a, const topo_oc_opts* o, topo_oc_info* info) {
+  NvtxRange nvtx("topo: OC step (Sec. 4)");
   if (!a || !o) return TOPO_E_INVALID_ARG;
   StreamGuard gd(a->K);
   cudaStream_t st = a->K->st;
@@ -717,6 +720,99 @@ topo_status topo_oc_get_u(topo_oc* a, double* u) {
   if (!a || !u) return TOPO_E_INVALID_ARG;
   StreamGuard gd(a->K);
   TOPO_CUDA(cudaMemcpyAsync(u, a->u, sizeof(double) * a->n, cudaMemcpyDeviceToDevice, a->K->st));
+  return TOPO_OK;
+}
+
+topo_status topo_oc_set_record_file(topo_oc* a, const char* path) {
+  if (!a) return TOPO_E_INVALID_ARG;
+  return topo_set_record_file(a->K, path);
+}
+
+topo_status topo_ip_set_record_file(topo_ip* a, const char* path) {
+  if (!a) return TOPO_E_INVALID_ARG;
+  if (a->K) TOPO_TRY(topo_set_record_file(a->K, path));
+  return topo_set_record_file(a->Z, path);
+}
+
+// Checkpoint / resume: the iterate, the warm-start displacement and the host scalars of the run.
+topo_status topo_oc_get_state(topo_oc* a, double* x, double* u, double* scal) {
+  if (!a || !x || !u || !scal) {
+    set_error("topo_oc_get_state: null argument");
+    return TOPO_E_INVALID_ARG;
+  }
+  StreamGuard gd(a->K);
+  cudaStream_t st = a->K->st;
+  TOPO_CUDA(cudaMemcpyAsync(x, a->x, sizeof(double) * a->m, cudaMemcpyDeviceToDevice, st));
+  TOPO_CUDA(cudaMemcpyAsync(u, a->u, sizeof(double) * a->n, cudaMemcpyDeviceToDevice, st));
+  TOPO_CUDA(cudaStreamSynchronize(st));
+  scal[0] = a->cg_tol;
+  scal[1] = a->c_prev;
+  scal[2] = a->c_last;
+  scal[3] = a->have_u ? 1.0 : 0.0;
+  scal[4] = (double)a->feval;
+  scal[5] = (double)a->iters;
+  scal[6] = (double)a->cg_iters;
+  return TOPO_OK;
+}
+
+topo_status topo_oc_set_state(topo_oc* a, const double* x, const double* u, const double* scal) {
+  if (!a || !x || !u || !scal) {
+    set_error("topo_oc_set_state: null argument");
+    return TOPO_E_INVALID_ARG;
+  }
+  // a tolerance not yet set (negative: the next step takes cg_tol0) or a positive finite one
+  const bool tol_ok = scal[0] == -1.0 || (std::isfinite(scal[0]) && scal[0] > 0.0);
+  bool ok = tol_ok && (scal[3] == 0.0 || scal[3] == 1.0);
+  for (int k = 4; k < 7; ++k)
+    ok = ok && std::isfinite(scal[k]) && scal[k] >= 0.0 && scal[k] == std::floor(scal[k]) &&
+         scal[k] < 2147483647.0;
+  if (!ok) {
+    set_error("topo_oc_set_state: invalid tolerance, flag or count in scal");
+    return TOPO_E_INVALID_ARG;
+  }
+  StreamGuard gd(a->K);
+  cudaStream_t st = a->K->st;
+  TOPO_CUDA(cudaMemcpyAsync(a->x, x, sizeof(double) * a->m, cudaMemcpyDeviceToDevice, st));
+  TOPO_CUDA(cudaMemcpyAsync(a->u, u, sizeof(double) * a->n, cudaMemcpyDeviceToDevice, st));
+  TOPO_CUDA(cudaStreamSynchronize(st));
+  a->cg_tol = scal[0];
+  a->c_prev = scal[1];
+  a->c_last = scal[2];
+  a->have_u = scal[3] == 1.0;
+  a->feval = (int)scal[4];
+  a->iters = (int)scal[5];
+  a->cg_iters = (int)scal[6];
+  return TOPO_OK;
+}
+
+topo_status topo_oc_power_state_size(topo_oc* a, long long* len) {
+  if (!a || !len) return TOPO_E_INVALID_ARG;
+  *len = (long long)a->K->pw_len;
+  return TOPO_OK;
+}
+
+topo_status topo_oc_get_power_state(topo_oc* a, double* v, int* ready) {
+  if (!a || !ready || (a->K->pw_len && !v)) return TOPO_E_INVALID_ARG;
+  StreamGuard gd(a->K);
+  cudaStream_t st = a->K->st;
+  if (a->K->pw_len)
+    TOPO_CUDA(cudaMemcpyAsync(v, a->K->pw_vec, sizeof(double) * a->K->pw_len,
+                              cudaMemcpyDeviceToDevice, st));
+  TOPO_CUDA(cudaStreamSynchronize(st));
+  *ready = a->K->pw_ready ? 1 : 0;
+  return TOPO_OK;
+}
+
+topo_status topo_oc_set_power_state(topo_oc* a, const double* v, int ready) {
+  if (!a || (ready && a->K->pw_len && !v)) return TOPO_E_INVALID_ARG;
+  StreamGuard gd(a->K);
+  cudaStream_t st = a->K->st;
+  if (ready && a->K->pw_len) {
+    TOPO_CUDA(cudaMemcpyAsync(a->K->pw_vec, v, sizeof(double) * a->K->pw_len,
+                              cudaMemcpyDeviceToDevice, st));
+    TOPO_CUDA(cudaStreamSynchronize(st));
+  }
+  a->K->pw_ready = ready && a->K->pw_len;
   return TOPO_OK;
 }
 

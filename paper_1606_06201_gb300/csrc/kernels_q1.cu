@@ -1,16 +1,7 @@
 // Finest-level operator of the 2D Q1 grid, K(x) v = sum_e x_e L_e^T K0 L_e v (Eq. (to), Sec. 7),
 // specialised for square plane-stress elements.
 //
-// Element product.  Writing the bilinear field of an element as
-//   u = 1/4 (S + X xi + Y eta + H xi eta),  v = 1/4 (S' + X' xi + Y' eta + H' xi eta)
-// with X = sum_a xi_a u_a, Y = sum_a eta_a u_a, H = sum_a xi_a eta_a u_a (xi_a, eta_a = +-1 at the
-// corners) and likewise for v, the strain energy of a unit square element is
-//   1/2 t^T Khat t,  t = (X, Y', G = Y + X', H, H'),
-//   Khat = diag-blocks [[D11, D12], [D12, D22]]/4 on (X, Y'), D33/4 on G,
-//          (D11 + D33)/12 on H, (D22 + D33)/12 on H'
-// (the cross terms between constant and linear parts integrate to zero).  So K0 = T^T Khat T and
-// K0 v_e costs two 4-point butterflies, 13 multiplies and two inverse butterflies: 40 operations
-// instead of 64 multiply-adds.  The host checks T^T Khat T == K0 before using this path.
+// The element product (two butterflies in the (1, xi, eta, xi eta) basis) is in q1_common.cuh.
 //
 // Data movement.  A warp owns 30 consecutive node columns and a strip of node rows.  Lane l holds
 // node column c = i0 - 1 + l and element column c; it walks the strip row by row, loading one node
@@ -20,6 +11,7 @@
 // elements in a fixed order (deterministic, no atomics); lanes 0 and 31 only supply halo values.
 // The Jacobi diagonal K0_ii sum_{e at node} x_e is formed on the fly from the same densities.
 #include "pairs.cuh"
+#include "q1_common.cuh"
 #include "topo_internal.cuh"
 
 namespace topo {
@@ -30,72 +22,7 @@ constexpr int kQ1Cols = 30;   // output node columns per warp
 constexpr int kQ1MaxRows = 16;  // output node rows per warp strip (at most)
 constexpr int kQ1Warps = 8;   // warps per block
 
-template <typename T>
-struct Vec2;
-template <>
-struct Vec2<double> {
-  using type = double2;
-};
-template <>
-struct Vec2<float> {
-  using type = float2;
-};
-
-template <typename T>
-struct Q1K {
-  T c11, c12, c22, c33, cH, cHp, kd;
-};
-
-template <typename T>
-__device__ __forceinline__ void q1_element(const Q1K<T>& k, T xe, const T u[4], const T v[4],
-                                           T ru[4], T rv[4]) {
-  const T d1 = u[2] - u[0], d2 = u[1] - u[3], s1 = u[0] + u[2], s2 = u[1] + u[3];
-  const T X = d2 + d1, Y = d1 - d2, H = s1 - s2;
-  const T e1 = v[2] - v[0], e2 = v[1] - v[3], t1 = v[0] + v[2], t2 = v[1] + v[3];
-  const T Xp = e2 + e1, Yp = e1 - e2, Hp = t1 - t2;
-  const T G = Y + Xp;
-  const T a11 = xe * k.c11, a12 = xe * k.c12, a22 = xe * k.c22;
-  const T gX = fma(a11, X, a12 * Yp);
-  const T gYp = fma(a12, X, a22 * Yp);
-  const T gG = (xe * k.c33) * G, gH = (xe * k.cH) * H, gHp = (xe * k.cHp) * Hp;
-  const T A = gX + gG, B = gX - gG;
-  ru[0] = gH - A;
-  ru[1] = B - gH;
-  ru[2] = A + gH;
-  ru[3] = -B - gH;
-  const T C = gYp + gG, Dd = gYp - gG;
-  rv[0] = gHp - C;
-  rv[1] = -Dd - gHp;
-  rv[2] = C + gHp;
-  rv[3] = Dd - gHp;
-}
-
-// 1 / v rounded to nearest: the value of the IEEE division 1 / v, by the reciprocal intrinsic
-// (fewer instructions than the general division sequence).
-__device__ __forceinline__ float recip_rn(float v) { return __frcp_rn(v); }
-__device__ __forceinline__ double recip_rn(double v) { return __drcp_rn(v); }
-
-template <typename T>
-__device__ __forceinline__ T shfl_dn(T v) { return __shfl_down_sync(0xffffffffu, v, 1); }
-template <typename T>
-__device__ __forceinline__ T shfl_up1(T v) { return __shfl_up_sync(0xffffffffu, v, 1); }
-
-__device__ __forceinline__ double block_sum_q1(double v) {
-  __shared__ double warp_sums[32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) warp_sums[wid] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (wid == 0) {
-    s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  }
-  return s;
-}
+using namespace q1;
 
 // MODE 0: y = K v; 1: y = b - K v; 2: y = v + omega D^{-1} (b - K v); 3: y = omega D^{-1} b.
 // DOT 1 (MODE 0, FP64): also p^T q with the last-block finalisation alpha = r^T y / p^T q.
@@ -1003,11 +930,6 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1g_sweep(int nx, int ny, int
     cv = R[3][1] + l2v;
     pb = pt;
   }
-}
-
-template <typename T>
-Q1K<T> coef_cast(const Q1Coef& c) {
-  return Q1K<T>{(T)c.c11, (T)c.c12, (T)c.c22, (T)c.c33, (T)c.cH, (T)c.cHp, (T)c.kd};
 }
 
 // Strip height: short enough that the grid has about one full wave of warps (152 SMs x 32),

@@ -160,6 +160,65 @@ bool q1_coefficients(double E, double nu, const double* K0, Q1Coef& q) {
   return err <= 1e-14 * scale;
 }
 
+// The butterfly coefficients of a caller's 8 x 8 K0: T has mutually orthogonal rows (squared norms
+// 4, 4, 8, 4, 4), so Khat_ab = T_a K0 T_b^T / (|T_a|^2 |T_b|^2) is the only candidate; the path is
+// taken when Khat has the butterfly's pattern (the normal block on (X, Y'), scalars on G, H, H'),
+// T^T Khat T reproduces K0 and the diagonal of K0 is constant (the on-the-fly Jacobi diagonal).
+bool q1_coefficients_from_K0(const double* K0, Q1Coef& q) {
+  const double xi[4] = {-1, 1, 1, -1}, eta[4] = {-1, -1, 1, 1};
+  double T[5][8] = {};
+  for (int a = 0; a < 4; ++a) {
+    T[0][2 * a] = xi[a];
+    T[1][2 * a + 1] = eta[a];
+    T[2][2 * a] = eta[a];
+    T[2][2 * a + 1] = xi[a];
+    T[3][2 * a] = xi[a] * eta[a];
+    T[4][2 * a + 1] = xi[a] * eta[a];
+  }
+  const double nrm[5] = {4, 4, 8, 4, 4};
+  double Kh[5][5] = {}, scale = 0.0;
+  for (int i = 0; i < 64; ++i) scale = std::max(scale, std::fabs(K0[i]));
+  if (!(scale > 0.0)) return false;
+  for (int a = 0; a < 5; ++a)
+    for (int b = 0; b < 5; ++b) {
+      double acc = 0.0;
+      for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) acc += T[a][i] * K0[i * 8 + j] * T[b][j];
+      Kh[a][b] = acc / (nrm[a] * nrm[b]);
+    }
+  for (int a = 0; a < 5; ++a)
+    for (int b = 0; b < 5; ++b) {
+      const bool allowed = (a == b) || (a < 2 && b < 2);
+      if (!allowed && std::fabs(Kh[a][b]) > 1e-14 * scale) return false;
+    }
+  double err = 0.0;
+  for (int i = 0; i < 8; ++i) {
+    if (std::fabs(K0[i * 8 + i] - K0[0]) > 1e-14 * scale) return false;
+    for (int j = 0; j < 8; ++j) {
+      double acc = 0.0;
+      for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 5; ++b) {
+          const bool allowed = (a == b) || (a < 2 && b < 2);
+          if (allowed) acc += T[a][i] * Kh[a][b] * T[b][j];
+        }
+      err = std::max(err, std::fabs(acc - K0[i * 8 + j]));
+    }
+  }
+  if (err > 1e-14 * scale) return false;
+  q = Q1Coef{Kh[0][0], 0.5 * (Kh[0][1] + Kh[1][0]), Kh[1][1], Kh[2][2], Kh[3][3], Kh[4][4], K0[0]};
+  return true;
+}
+
+// The element matrix of a descriptor: the caller's K0 or the analytic one.
+void descriptor_K0(const topo_solver_desc* d, std::vector<double>& K0) {
+  const int ne = d->dim == 2 ? 8 : 24;
+  K0.assign((size_t)ne * ne, 0.0);
+  if (d->K0)
+    std::copy(d->K0, d->K0 + ne * ne, K0.begin());
+  else
+    element_stiffness_host(d->dim, d->E, d->nu, K0.data());
+}
+
 // Coarse mask by injection; check that every fixed fine DOF interpolates only from fixed coarse
 // DOFs (then the element-local Galerkin product of the unmasked operators equals the masked one).
 bool coarsen_mask(const Dims& df, const std::vector<uint8_t>& ff, std::vector<uint8_t>& fc,
@@ -241,6 +300,54 @@ topo_status prof_mark(topo_solver* s, int kind, int end) {
   return TOPO_OK;
 }
 
+// The finest-level Q1 sweeps: two node columns per lane for FP32 vectors (kernels_q1w.cu, the
+// same outputs), one column per lane otherwise (kernels_q1.cu).
+template <typename TV>
+cudaError_t q1_apply(const topo_solver* s, int nx, int ny, int mode, const TV* x, const TV* v,
+                     const TV* b, TV* y, TV omega, const uint8_t* fixed, int nrhs,
+                     const CgScalars* sc) {
+  if constexpr (std::is_same<TV, float>::value) {
+    if (s->q1_wide && s->fixed_pad)
+      return launch_q1w_apply(nx, ny, mode, s->q1, x, v, b, y, omega, s->fixed_pad, nrhs, sc,
+                              s->st, s->sweep_rows);
+  }
+  return launch_q1_apply<TV>(nx, ny, mode, s->q1, x, v, b, y, omega, fixed, nrhs, sc, s->st);
+}
+template <typename TV>
+cudaError_t q1_fused(const topo_solver* s, int nx, int ny, int mode, const TV* x, const TV* t,
+                     const TV* zc, const TV* b, TV* y, TV omega, const uint8_t* fixed, int nrhs,
+                     const CgScalars* sc) {
+  if constexpr (std::is_same<TV, float>::value) {
+    if (s->q1_wide && s->fixed_pad)
+      return launch_q1w_fused(nx, ny, mode, s->q1, x, t, zc, b, y, omega, s->fixed_pad, nrhs, sc,
+                              s->st, s->sweep_rows);
+  }
+  return launch_q1_fused<TV>(nx, ny, mode, s->q1, x, t, zc, b, y, omega, fixed, nrhs, sc, s->st);
+}
+template <typename TV>
+cudaError_t q1_resrestrict(const topo_solver* s, int nx, int ny, const TV* x, const TV* v,
+                           const TV* b, TV* bc, const uint8_t* fixed, const uint8_t* fixed_c,
+                           int nrhs, const CgScalars* sc) {
+  if constexpr (std::is_same<TV, float>::value) {
+    if (s->q1_wide && s->fixed_pad)
+      return launch_q1w_resrestrict(nx, ny, s->q1, x, v, b, bc, s->fixed_pad, fixed_c, nrhs, sc,
+                                    s->st, s->sweep_rows);
+  }
+  return launch_q1_resrestrict<TV>(nx, ny, s->q1, x, v, b, bc, fixed, fixed_c, nrhs, sc, s->st);
+}
+template <typename TV>
+cudaError_t q1_smooth_beta(const topo_solver* s, int nx, int ny, const TV* x, const TV* v,
+                           const TV* b, TV* y, TV omega, const uint8_t* fixed, int nrhs,
+                           double* partials, unsigned* counters, CgScalars* sc) {
+  if constexpr (std::is_same<TV, float>::value) {
+    if (s->q1_wide && s->fixed_pad)
+      return launch_q1w_smooth_beta(nx, ny, s->q1, x, v, b, y, omega, s->fixed_pad, nrhs, s->r,
+                                    partials, counters, sc, s->st, s->sweep_rows);
+  }
+  return launch_q1_smooth_beta<TV>(nx, ny, s->q1, x, v, b, y, omega, fixed, nrhs, s->r, partials,
+                                   counters, sc, s->st);
+}
+
 // Operator application on level k (mode as launch_apply): the warp-sweep Q1 kernels on the 2D
 // finest level, the matrix-free first coarse level in mixed precision, the Z operator (element
 // rank-one terms and lambda row) for IP systems, the generic element-matrix kernels elsewhere.
@@ -267,8 +374,8 @@ topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* 
     return TOPO_OK;
   }
   if (k == 0 && s->q1_ok) {
-    TOPO_CUDA(launch_q1_apply<TV>(lv.d.nx, lv.d.ny, mode, s->q1, Prec<TV>::x(s), v, b, y, omega,
-                                  lv.fixed, s->nrhs, sc, s->st));
+    TOPO_CUDA(q1_apply<TV>(s, lv.d.nx, lv.d.ny, mode, Prec<TV>::x(s), v, b, y, omega, lv.fixed,
+                           s->nrhs, sc));
     return TOPO_OK;
   }
   if (k == 1 && s->l1_free && std::is_same<TV, float>::value) {
@@ -405,8 +512,8 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
   bool sweep_timed = false;  // profiling: the first smoothing kernel of the finest level
   if (nu1 >= 2 && fine_fused) {
     TOPO_TRY(prof_mark(s, 1, 0));
-    TOPO_CUDA(launch_q1_fused<TV>(lv.d.nx, lv.d.ny, 4, s->q1, Prec<TV>::x(s), nullptr, nullptr, b,
-                                  oth, (TV)s->desc.omega, lv.fixed, nrhs, sc, s->st));
+    TOPO_CUDA(q1_fused<TV>(s, lv.d.nx, lv.d.ny, 4, Prec<TV>::x(s), nullptr, nullptr, b, oth,
+                           (TV)s->desc.omega, lv.fixed, nrhs, sc));
     TOPO_TRY(prof_mark(s, 1, 1));
     sweep_timed = true;
     std::swap(cur, oth);
@@ -437,8 +544,8 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
   Level& lc = s->L[k + 1];
   if (fine_fused) {  // residual and restriction in one pass (the residual is not stored)
     TOPO_TRY(prof_mark(s, 2, 0));
-    TOPO_CUDA(launch_q1_resrestrict<TV>(lv.d.nx, lv.d.ny, s->q1, Prec<TV>::x(s), cur, b,
-                                        (TV*)lc.b, lv.fixed, lc.fixed, nrhs, sc, s->st));
+    TOPO_CUDA(q1_resrestrict<TV>(s, lv.d.nx, lv.d.ny, Prec<TV>::x(s), cur, b, (TV*)lc.b,
+                                 lv.fixed, lc.fixed, nrhs, sc));
     TOPO_TRY(prof_mark(s, 2, 1));
   } else {
     if (fine) TOPO_TRY(prof_mark(s, 2, 0));
@@ -456,8 +563,8 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
   int it0 = 0;
   if (fine_fused && nu2 >= 1 && !(fuse_beta && nu2 == 1)) {
     TOPO_TRY(prof_mark(s, 4, 0));
-    TOPO_CUDA(launch_q1_fused<TV>(lv.d.nx, lv.d.ny, 5, s->q1, Prec<TV>::x(s), cur, zc, b, oth,
-                                  (TV)s->desc.omega, lv.fixed, nrhs, sc, s->st));
+    TOPO_CUDA(q1_fused<TV>(s, lv.d.nx, lv.d.ny, 5, Prec<TV>::x(s), cur, zc, b, oth,
+                           (TV)s->desc.omega, lv.fixed, nrhs, sc));
     TOPO_TRY(prof_mark(s, 4, 1));
     std::swap(cur, oth);
     it0 = 1;
@@ -472,9 +579,9 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
   }
   for (int it = it0; it < nu2; ++it) {
     if (fuse_beta && k == 0 && it == nu2 - 1) {
-      TOPO_CUDA(launch_q1_smooth_beta<TV>(lv.d.nx, lv.d.ny, s->q1, Prec<TV>::x(s), cur, b, oth,
-                                          (TV)s->desc.omega, lv.fixed, nrhs, s->r, s->partials,
-                                          s->counters, const_cast<CgScalars*>(sc), s->st));
+      TOPO_CUDA(q1_smooth_beta<TV>(s, lv.d.nx, lv.d.ny, Prec<TV>::x(s), cur, b, oth,
+                                   (TV)s->desc.omega, lv.fixed, nrhs, s->partials, s->counters,
+                                   const_cast<CgScalars*>(sc)));
     } else {
       const bool t = fine && !sweep_timed;
       if (t) TOPO_TRY(prof_mark(s, 1, 0));
@@ -694,6 +801,7 @@ topo_status cg_setup(topo_solver* s, int use_x0, double tol, int max_iter) {
 template <typename TV>
 topo_status solve_impl(topo_solver* s, const double* b, double* u, double tol, int use_x0,
                        topo_solve_info* info) {
+  NvtxRange nvtx("topo: MGCG solve (Algorithm PCG)");
   const long long n = s->ncg();
   const int nrhs = s->nrhs;
   const int max_iter = s->desc.max_iter;
@@ -910,6 +1018,7 @@ topo_status enqueue_build(topo_solver* s, bool warm = false) {
 }
 
 topo_status build_hierarchy(topo_solver* s) {
+  NvtxRange nvtx("topo: hierarchy build (Galerkin, Sec. 5.1)");
   const bool warm = s->pw_vec && s->pw_ready;
   s->pw_ready = false;  // a failed build leaves no vectors to start from
   if (warm) {
@@ -994,12 +1103,20 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   TOPO_CUDA(cudaEventCreateWithFlags(&s->ev_copy, cudaEventDisableTiming));
   const int ne = s->ne, nrhs = s->nrhs;
   // element data
-  std::vector<double> K0(ne * ne), C;
-  element_stiffness_host(s->dim, d->E, d->nu, K0.data());
+  std::vector<double> K0, C;
+  descriptor_K0(d, K0);
   child_matrices(s->dim, K0.data(), C);
   std::vector<double> C2;
   if (!arrow && s->nlev >= 3) grandchild_matrices(s->dim, K0.data(), C2);
-  s->q1_ok = (s->dim == 2) && q1_coefficients(d->E, d->nu, K0.data(), s->q1) && !d->generic_kernels;
+  s->q1_ok = (s->dim == 2) && !d->generic_kernels &&
+             (d->K0 ? q1_coefficients_from_K0(K0.data(), s->q1)
+                    : q1_coefficients(d->E, d->nu, K0.data(), s->q1));
+  // TOPO_Q1_NARROW=1 keeps the one-column-per-lane FP32 sweeps (a reference for the two-column
+  // ones, which give the same outputs)
+  {
+    const char* nv = std::getenv("TOPO_Q1_NARROW");
+    s->q1_wide = !(nv && nv[0] == '1');
+  }
   s->hex_ok = (s->dim == 3) && !arrow && !d->generic_kernels && hex_coefficients(K0.data(), s->hex);
   s->l1_free = (s->dim == 2) && !arrow && s->prec == TOPO_MIXED && s->nlev >= 3 &&
                !d->generic_kernels;
@@ -1081,6 +1198,17 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
       dk = Dims{dk.nx / 2, dk.ny / 2, dk.dim == 3 ? dk.nz / 2 : 1, dk.dim};
     }
   }
+  if (s->dim == 2 && s->q1_ok && !arrow && s->prec == TOPO_MIXED) {
+    // the finest mask as node pairs with an even row stride, for the FP32 two-column sweeps
+    const int nx = d->nx, ny = d->ny, rsp = nx + 2;
+    std::vector<uint8_t> pad((size_t)(ny + 1) * rsp * 2, 0);
+    for (int j = 0; j <= ny; ++j)
+      for (int i = 0; i <= nx; ++i)
+        for (int c = 0; c < 2; ++c)
+          pad[((size_t)j * rsp + i) * 2 + c] = s->fixed_host[((size_t)j * (nx + 1) + i) * 2 + c];
+    TOPO_TRY(s->alloc(&s->fixed_pad, pad.size() / 4));
+    TOPO_CUDA(cudaMemcpy(s->fixed_pad, pad.data(), pad.size(), cudaMemcpyHostToDevice));
+  }
   Level& lc = s->L[s->nlev - 1];
   s->nc = (int)lc.n;
   const size_t na = (size_t)s->nc + (arrow ? 1 : 0);
@@ -1150,35 +1278,197 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   return TOPO_OK;
 }
 
-topo_status topo_solver_create(const topo_solver_desc* d, topo_solver** out) {
-  if (!d || !out || !d->fixed) {
-    set_error("topo_solver_create: null argument");
+// Descriptor checks shared by topo_solver_create, topo_solver_workspace_bytes and the IP / OC
+// drivers (what names the caller in the messages).
+topo_status validate_desc(const topo_solver_desc* d, const char* what) {
+  const std::string w(what);
+  if (!d || !d->fixed) {
+    set_error(w + ": null argument");
     return TOPO_E_INVALID_ARG;
   }
-  *out = nullptr;
   if ((d->dim != 2 && d->dim != 3) || d->nx < 1 || d->ny < 1 || (d->dim == 3 && d->nz < 1) ||
       d->levels < 1 || d->levels > 16 || (d->precision != TOPO_FP64 && d->precision != TOPO_MIXED) ||
       d->nu1 < 0 || d->nu2 < 0 || !(d->omega > 0.0 && d->omega <= 1.0) || d->max_iter < 0 ||
       d->nrhs < 1 || d->nrhs > kMaxRhs || !(d->E > 0.0) || !(d->nu > -1.0 && d->nu < 0.5) ||
       (d->smoother != 0 && d->smoother != 1)) {
-    set_error("topo_solver_create: invalid descriptor field");
+    set_error(w + ": invalid descriptor field");
     return TOPO_E_INVALID_ARG;
+  }
+  if (d->K0) {
+    const int ne = d->dim == 2 ? 8 : 24;
+    double mx = 0.0;
+    for (int i = 0; i < ne * ne; ++i) {
+      if (!std::isfinite(d->K0[i])) {
+        set_error(w + ": K0 has a non-finite entry");
+        return TOPO_E_INVALID_ARG;
+      }
+      mx = std::max(mx, std::fabs(d->K0[i]));
+    }
+    for (int i = 0; i < ne; ++i)
+      for (int j = 0; j < i; ++j)
+        if (std::fabs(d->K0[i * ne + j] - d->K0[j * ne + i]) > 1e-12 * mx) {
+          set_error(w + ": K0 is not symmetric");
+          return TOPO_E_INVALID_ARG;
+        }
+    if (!(mx > 0.0)) {
+      set_error(w + ": K0 is zero");
+      return TOPO_E_INVALID_ARG;
+    }
   }
   const Dims dfine{d->nx, d->ny, d->dim == 3 ? d->nz : 1, d->dim};
   if (dfine.dofs() >= (1LL << 31)) {  // kernels index nodes and DOFs with 32-bit arithmetic
-    set_error("topo_solver_create: grid has 2^31 or more DOFs");
+    set_error(w + ": grid has 2^31 or more DOFs");
     return TOPO_E_INVALID_ARG;
   }
   const int f = 1 << (d->levels - 1);
   if (d->nx % f || d->ny % f || (d->dim == 3 && d->nz % f)) {
-    set_error("topo_solver_create: grid not divisible by 2^(levels-1)");
+    set_error(w + ": grid not divisible by 2^(levels-1)");
     return TOPO_E_INVALID_ARG;
   }
   Dims dc{d->nx / f, d->ny / f, d->dim == 3 ? d->nz / f : 1, d->dim};
   if (dc.dofs() > 4096) {
-    set_error("topo_solver_create: coarsest level has more than 4096 DOFs; use more levels");
+    set_error(w + ": coarsest level has more than 4096 DOFs; use more levels");
     return TOPO_E_INVALID_ARG;
   }
+  return TOPO_OK;
+}
+
+// Device bytes create_impl allocates for d (the same decisions in the same order, counted on the
+// host).  Masks incompatible with coarsening are rejected as create_impl does.
+topo_status plan_bytes(const topo_solver_desc* d, bool arrow, size_t* out) {
+  const int dim = d->dim, ne = dim == 2 ? 8 : 24, nrhs = d->nrhs, nlev = d->levels;
+  const bool mixed = d->precision == TOPO_MIXED;
+  size_t bytes = 0;
+  auto add = [&](size_t count, size_t elem) { bytes += std::max<size_t>(count, 1) * elem; };
+  std::vector<double> K0, C, C2;
+  descriptor_K0(d, K0);
+  child_matrices(dim, K0.data(), C);
+  if (!arrow && nlev >= 3) grandchild_matrices(dim, K0.data(), C2);
+  Q1Coef q1;
+  HexCoef hex;
+  const bool q1_ok = dim == 2 && !d->generic_kernels &&
+                     (d->K0 ? q1_coefficients_from_K0(K0.data(), q1)
+                            : q1_coefficients(d->E, d->nu, K0.data(), q1));
+  const bool hex_ok = dim == 3 && !arrow && !d->generic_kernels && hex_coefficients(K0.data(), hex);
+  const bool l1_free = dim == 2 && !arrow && mixed && nlev >= 3 && !d->generic_kernels;
+  const bool h32 = !arrow && mixed && d->smoother == 0 && !d->omega_auto;
+  add(ne * ne, sizeof(double));
+  add(ne * ne, sizeof(float));
+  add(C.size(), sizeof(double));
+  add(C.size(), sizeof(float));
+  if (!C2.empty()) {
+    add(C2.size(), sizeof(double));
+    if (h32) add(C2.size(), sizeof(float));
+  }
+  Dims dk{d->nx, d->ny, dim == 3 ? d->nz : 1, dim};
+  std::vector<uint8_t> mask((size_t)dk.dofs());
+  for (size_t i = 0; i < mask.size(); ++i) mask[i] = d->fixed[i] ? 1 : 0;
+  const size_t vbytes = mixed ? sizeof(float) : sizeof(double);
+  std::vector<long long> lev_n(nlev);
+  std::vector<bool> pw_level(nlev, false);
+  long long nc = 0;
+  for (int k = 0; k < nlev; ++k) {
+    const long long n = dk.dofs(), m = dk.elems();
+    lev_n[k] = n;
+    add(n, 1);
+    const bool coarsest = k == nlev - 1;
+    const long long vl = n + (arrow ? 2 : 0);
+    if (k >= 1) {
+      const bool l1_matrix_free = k == 1 && l1_free;
+      if (!l1_matrix_free && (!h32 || coarsest)) add(m * ne * ne, sizeof(double));
+      if (mixed && !coarsest && !l1_matrix_free) add(m * ne * ne, sizeof(float));
+    }
+    if (arrow) {
+      add(n, sizeof(double));
+      if (mixed) add(n, sizeof(float));
+    }
+    if (!coarsest) {
+      add(n, sizeof(double));
+      if (mixed) add(n, sizeof(float));
+      if (d->smoother == 1 && !arrow) {
+        add(1, sizeof(double));
+        add(vbytes * vl * nrhs, 1);
+        pw_level[k] = true;
+      } else if (d->omega_auto && (arrow || k >= 1)) {
+        add(1, sizeof(double));
+        pw_level[k] = true;
+      }
+      add(vbytes * vl * nrhs, 1);
+    }
+    if (k >= 1) add(vbytes * vl * nrhs, 1);
+    add(vbytes * vl * nrhs, 1);
+    if (!coarsest) {
+      std::vector<uint8_t> next;
+      std::string why;
+      if (!coarsen_mask(dk, mask, next, why)) {
+        set_error(why);
+        return TOPO_E_INVALID_ARG;
+      }
+      mask.swap(next);
+      dk = Dims{dk.nx / 2, dk.ny / 2, dk.dim == 3 ? dk.nz / 2 : 1, dk.dim};
+    } else {
+      nc = n;
+    }
+  }
+  if (dim == 2 && q1_ok && !arrow && mixed)
+    add((size_t)(d->ny + 1) * (d->nx + 2) * 2 / 4, sizeof(unsigned));
+  const size_t na = (size_t)nc + (arrow ? 1 : 0);
+  add(na * na, sizeof(double));
+  add(na * na, sizeof(double));
+  add(4, sizeof(int));
+  if ((!arrow || na > 128) && coarse_scratch_doubles((int)na))
+    add(coarse_scratch_doubles((int)na), sizeof(double));
+  add(2, sizeof(double));
+  size_t tot = 0;
+  for (int k = 0; k < nlev; ++k)
+    if (pw_level[k]) tot += (size_t)lev_n[k] + 2;
+  if (tot) add(tot, sizeof(double));
+  const Dims d0{d->nx, d->ny, dim == 3 ? d->nz : 1, dim};
+  const long long m = d0.elems();
+  const long long n = d0.dofs() + (arrow ? 2 : 0);
+  add(m, sizeof(double));
+  if (hex_ok) add((size_t)m * 24 * nrhs, sizeof(double));
+  if ((q1_ok || hex_ok) && !arrow) add(m, sizeof(float2));
+  if (mixed) {
+    add(m, sizeof(float));
+    add(n * nrhs, sizeof(float));
+  }
+  if (arrow) {
+    add(m, sizeof(double));
+    if (mixed) {
+      add(m, sizeof(float));
+      add(m * ne, sizeof(float));
+      add(m, sizeof(float));
+    }
+  }
+  for (int v = 0; v < 5; ++v) add(n * nrhs, sizeof(double));
+  if (d->flexible) add(vbytes * n * nrhs, 1);
+  const long long pb = std::max<long long>((long long)kMaxRedValues * kRedBlocks,
+                                           blocks_for(d0.nodes()));
+  add(pb * nrhs, sizeof(double));
+  add(nrhs, sizeof(unsigned));
+  add(nrhs, sizeof(CgScalars));
+  add(nrhs, sizeof(double));
+  *out = bytes;
+  return TOPO_OK;
+}
+
+topo_status topo_solver_workspace_bytes(const topo_solver_desc* d, size_t* bytes) {
+  TOPO_TRY(validate_desc(d, "topo_solver_workspace_bytes"));
+  if (!bytes) {
+    set_error("topo_solver_workspace_bytes: null argument");
+    return TOPO_E_INVALID_ARG;
+  }
+  return plan_bytes(d, false, bytes);
+}
+
+topo_status topo_solver_create(const topo_solver_desc* d, topo_solver** out) {
+  if (!out) {
+    set_error("topo_solver_create: null argument");
+    return TOPO_E_INVALID_ARG;
+  }
+  *out = nullptr;
+  TOPO_TRY(validate_desc(d, "topo_solver_create"));
   topo_solver* s = new topo_solver();
   topo_status st = create_impl(d, s, false);
   if (st != TOPO_OK) {
@@ -1211,6 +1501,23 @@ topo_status topo_set_outer_precision(topo_solver* s, int mode) {
   return TOPO_OK;
 }
 
+// Captured graphs hold the V-cycle's kernels and launch shapes: drop them after a change.
+void drop_graphs(topo_solver* s) {
+  for (int u = 0; u < 2; ++u)
+    if (s->setup[u]) {
+      cudaGraphExecDestroy(s->setup[u]);
+      s->setup[u] = nullptr;
+    }
+  if (s->graph) {
+    cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+  }
+  if (s->loop) {
+    cudaGraphExecDestroy(s->loop);
+    s->loop = nullptr;
+  }
+}
+
 topo_status topo_set_vcycle_fusion(topo_solver* s, int on) {
   if (!s) {
     set_error("topo_set_vcycle_fusion: null solver");
@@ -1219,19 +1526,19 @@ topo_status topo_set_vcycle_fusion(topo_solver* s, int on) {
   const bool want = on != 0;
   if (want != s->fuse_on) {
     s->fuse_on = want;
-    for (int u = 0; u < 2; ++u)  // captured graphs hold the old V-cycle
-      if (s->setup[u]) {
-        cudaGraphExecDestroy(s->setup[u]);
-        s->setup[u] = nullptr;
-      }
-    if (s->graph) {
-      cudaGraphExecDestroy(s->graph);
-      s->graph = nullptr;
-    }
-    if (s->loop) {
-      cudaGraphExecDestroy(s->loop);
-      s->loop = nullptr;
-    }
+    drop_graphs(s);
+  }
+  return TOPO_OK;
+}
+
+topo_status topo_set_sweep_rows(topo_solver* s, int rows) {
+  if (!s || rows < 0 || rows > 32 || rows == 1) {
+    set_error("topo_set_sweep_rows: null solver or rows outside {0} and 2..32");
+    return TOPO_E_INVALID_ARG;
+  }
+  if (rows != s->sweep_rows) {
+    s->sweep_rows = rows;
+    drop_graphs(s);
   }
   return TOPO_OK;
 }
@@ -1312,6 +1619,28 @@ topo_status topo_set_density(topo_solver* s, const double* x) {
   return st;
 }
 
+// One JSON line per solve (topo_set_record_file): the configuration, the outcome and the rate.
+void append_record(const topo_solver* s, double tol, const topo_solve_info& in, topo_status st) {
+  if (s->record_path.empty()) return;
+  FILE* fp = std::fopen(s->record_path.c_str(), "a");
+  if (!fp) return;
+  long long nfree = 0;
+  for (uint8_t f : s->fixed_host) nfree += f ? 0 : 1;
+  const double rate = in.wall_ms > 0.0 ? (double)nfree * in.iterations / (in.wall_ms * 1e-3) : 0.0;
+  std::fprintf(fp,
+               "{\"call\": \"solve\", \"system\": \"%s\", \"dim\": %d, \"nx\": %d, \"ny\": %d, "
+               "\"nz\": %d, \"levels\": %d, \"precision\": \"%s\", \"smoother\": \"%s\", "
+               "\"nu1\": %d, \"nu2\": %d, \"omega\": %.17g, \"nrhs\": %d, \"free_dofs\": %lld, "
+               "\"tol\": %.17g, \"iterations\": %d, \"rel_residual\": %.17g, \"wall_ms\": %.6f, "
+               "\"dof_it_per_s\": %.6g, \"status\": %d}\n",
+               s->arrow ? "Z" : "K", s->dim, s->desc.nx, s->desc.ny, s->dim == 3 ? s->desc.nz : 0,
+               s->nlev, s->prec == TOPO_MIXED ? "mixed" : "fp64",
+               s->desc.smoother == 1 ? "chebyshev" : "jacobi", s->desc.nu1, s->desc.nu2,
+               s->desc.omega, s->nrhs, nfree, tol, in.iterations, in.rel_residual, in.wall_ms, rate,
+               (int)st);
+  std::fclose(fp);
+}
+
 topo_status topo_solve(topo_solver* s, const double* b, double* u, double tol, int use_x0,
                        topo_solve_info* info) {
   if (!s || !b || !u || !(tol >= 0.0)) {
@@ -1323,8 +1652,21 @@ topo_status topo_solve(topo_solver* s, const double* b, double* u, double tol, i
     return TOPO_E_INVALID_ARG;
   }
   StreamGuard g(s);
-  if (s->prec == TOPO_MIXED) return solve_impl<float>(s, b, u, tol, use_x0, info);
-  return solve_impl<double>(s, b, u, tol, use_x0, info);
+  topo_solve_info local{};
+  topo_solve_info* out = info ? info : &local;
+  const topo_status st = s->prec == TOPO_MIXED ? solve_impl<float>(s, b, u, tol, use_x0, out)
+                                               : solve_impl<double>(s, b, u, tol, use_x0, out);
+  append_record(s, tol, *out, st);
+  return st;
+}
+
+topo_status topo_set_record_file(topo_solver* s, const char* path) {
+  if (!s) {
+    set_error("topo_set_record_file: null solver");
+    return TOPO_E_INVALID_ARG;
+  }
+  s->record_path = path ? path : "";
+  return TOPO_OK;
 }
 
 topo_status topo_solve_host(topo_solver* s, const double* x, const double* b, double* u,
@@ -1459,10 +1801,11 @@ topo_status topo_grad_x(topo_solver* s, const double* lam, const double* u, doub
 namespace topo {
 
 topo_status solver_create_internal(const topo_solver_desc* d, bool arrow, topo_solver** out) {
-  topo_status st = topo_solver_create(d, out);  // validates the descriptor
-  if (st != TOPO_OK || !arrow) return st;
-  topo_solver_destroy(*out);
+  if (!arrow) return topo_solver_create(d, out);
+  if (!out) return TOPO_E_INVALID_ARG;
   *out = nullptr;
+  TOPO_TRY(validate_desc(d, "topo_solver_create"));
+  topo_status st;
   if (d->nrhs != 1) {
     set_error("IP systems are solved one right-hand side at a time");
     return TOPO_E_INVALID_ARG;
@@ -1487,8 +1830,12 @@ topo_status solver_build(topo_solver* s) {
 
 topo_status solver_solve(topo_solver* s, const double* b, double* u, double tol, int use_x0,
                          topo_solve_info* info) {
-  if (s->prec == TOPO_MIXED) return solve_impl<float>(s, b, u, tol, use_x0, info);
-  return solve_impl<double>(s, b, u, tol, use_x0, info);
+  topo_solve_info local{};
+  topo_solve_info* out = info ? info : &local;
+  const topo_status st = s->prec == TOPO_MIXED ? solve_impl<float>(s, b, u, tol, use_x0, out)
+                                               : solve_impl<double>(s, b, u, tol, use_x0, out);
+  append_record(s, tol, *out, st);
+  return st;
 }
 
 }  // namespace topo

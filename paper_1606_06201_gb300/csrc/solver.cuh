@@ -1,6 +1,7 @@
 // Solver object shared by the host translation units (solver.cu: MGCG; ipoc.cu: IP and OC).
 #pragma once
 
+#include <string>
 #include <vector>
 
 #include "topo_internal.cuh"
@@ -29,6 +30,9 @@ struct topo_solver {
   std::vector<double> C_host, C2_host;  // host copies of C and C2 (kernel-parameter tables)
   Q1Coef q1{};                   // butterfly coefficients of the 2D K0
   bool q1_ok = false;            // 2D and T^T Khat T reproduces K0: use the warp-sweep kernels
+  bool q1_wide = true;           // FP32 finest sweeps with two node columns per lane (kernels_q1w.cu)
+  int sweep_rows = 0;            // strip height of the 2D finest-level warp sweeps (0: automatic)
+  unsigned* fixed_pad = nullptr; // 2D finest mask as node pairs, row stride (nx + 2) / 2 words
   double* x = nullptr;
   float* x32 = nullptr;
   float* C32 = nullptr;          // FP32 copy of C (matrix-free first coarse level)
@@ -113,6 +117,7 @@ struct topo_solver {
   long long prof_count[kProfKinds] = {};
   int prof_slot = -1;                     // slot of the iteration being captured, -1 outside
   bool have_density = false;
+  std::string record_path;                // JSONL record of every solve appended here (empty: off)
   size_t bytes = 0;
   std::vector<void*> allocs;
 

@@ -10,6 +10,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/topo.h"
 
 namespace topo {
@@ -136,6 +138,16 @@ topo_status cuda_status(cudaError_t e, const char* what);
     cudaError_t _e = cudaGetLastError();                        \
     if (_e != cudaSuccess) return topo::cuda_status(_e, what);  \
   } while (0)
+
+// A named NVTX range for the duration of a scope: the phases of the method (hierarchy build, MGCG
+// solve, IP Newton step, OC step) show up as ranges in profilers (ncu --nvtx, Nsight Systems); with
+// no tool attached a push or pop costs a few nanoseconds.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Programmatic dependent launch (optional, TOPO_PDL=1): every kernel waits for its stream
 // predecessor's completion before touching memory (griddepcontrol.wait) and at once lets its own
@@ -336,6 +348,30 @@ cudaError_t launch_q1_apply_dot(int nx, int ny, const Q1Coef& coef, const double
                                 double* partials, unsigned* counters, CgScalars* sc,
                                 cudaStream_t st);
 long long q1_partial_blocks(int nx, int ny);
+// The FP32 finest-level sweeps with two node columns per lane (kernels_q1w.cu): the same outputs
+// as launch_q1_apply, launch_q1_fused, launch_q1_resrestrict and launch_q1_smooth_beta for T =
+// float (the fused dot of the last one summed in another order).  rows: the strip height of the
+// fine sweeps (0: about one wave of warps; the residual-restriction takes rows / 2 coarse rows).
+// fixed: the finest mask as node pairs with an even row stride ((nx + 2) / 2 words per node row,
+// the pad node zero; topo_solver::fixed_pad).
+cudaError_t launch_q1w_apply(int nx, int ny, int mode, const Q1Coef& coef, const float* x,
+                             const float* v, const float* b, float* y, float omega,
+                             const unsigned* fixed, int nrhs, const CgScalars* sc, cudaStream_t st,
+                             int rows = 0);
+cudaError_t launch_q1w_fused(int nx, int ny, int mode, const Q1Coef& coef, const float* x,
+                             const float* t, const float* zc, const float* b, float* y,
+                             float omega, const unsigned* fixed, int nrhs, const CgScalars* sc,
+                             cudaStream_t st, int rows = 0);
+cudaError_t launch_q1w_smooth_beta(int nx, int ny, const Q1Coef& coef, const float* x,
+                                   const float* v, const float* b, float* y, float omega,
+                                   const unsigned* fixed, int nrhs, const double* r,
+                                   double* partials, unsigned* counters, CgScalars* sc,
+                                   cudaStream_t st, int rows = 0);
+cudaError_t launch_q1w_resrestrict(int nx, int ny, const Q1Coef& coef, const float* x,
+                                   const float* v, const float* b, float* bc,
+                                   const unsigned* fixed, const uint8_t* fixed_c, int nrhs,
+                                   const CgScalars* sc, cudaStream_t st, int rows = 0);
+long long q1w_partial_blocks(int nx, int ny);
 // 3D finest-level outer operator in the Walsh-Hadamard basis (kernels_hex.cu): element forces into
 // R (24 x elems per right-hand side), then a node gather with p^T q and alpha.  hex_coefficients
 // returns false when T^T Khat T does not reproduce K0 (the generic kernel is then used).
@@ -367,13 +403,6 @@ cudaError_t launch_split_df(const double* x, float2* out, long long m, cudaStrea
 // xdf = x as float pairs where not null.
 cudaError_t launch_prepare_x(const double* x, long long m, int* flag, float* x32, float2* xdf,
                              cudaStream_t st);
-// Jacobi sweep (mode 2) on the 2D finest level fused with r^T y against the FP64 CG residual r and
-// the beta of Algorithm PCG (last smoothing sweep of the preconditioner).
-template <typename T>
-cudaError_t launch_q1_smooth_beta(int nx, int ny, const Q1Coef& coef, const T* x, const T* v,
-                                  const T* b, T* y, T omega, const uint8_t* fixed, int nrhs,
-                                  const double* r, double* partials, unsigned* counters,
-                                  CgScalars* sc, cudaStream_t st);
 // Jacobi sweep (mode 2) on the 2D finest level fused with r^T y against the FP64 CG residual r and
 // the beta of Algorithm PCG (last smoothing sweep of the preconditioner).
 template <typename T>

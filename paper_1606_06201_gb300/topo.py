@@ -30,7 +30,8 @@ class SolverDesc(ctypes.Structure):
                 ("precision", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("omega", ctypes.c_double), ("max_iter", ctypes.c_int), ("nrhs", ctypes.c_int),
                 ("flexible", ctypes.c_int), ("generic_kernels", ctypes.c_int),
-                ("smoother", ctypes.c_int), ("omega_auto", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("omega_auto", ctypes.c_int),
+                ("K0", ctypes.POINTER(ctypes.c_double))]
 
 
 class SolveInfo(ctypes.Structure):
@@ -126,6 +127,17 @@ _SIGS = {
     "topo_oc_run": (ctypes.c_int, [_vp, ctypes.POINTER(OcOpts), ctypes.POINTER(OcInfo)]),
     "topo_oc_get_x": (ctypes.c_int, [_vp, _vp]),
     "topo_oc_get_u": (ctypes.c_int, [_vp, _vp]),
+    "topo_oc_get_state": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "topo_oc_set_state": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "topo_oc_power_state_size": (ctypes.c_int, [_vp, _vp]),
+    "topo_oc_get_power_state": (ctypes.c_int, [_vp, _vp, _vp]),
+    "topo_oc_set_power_state": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "topo_solver_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(SolverDesc),
+                                                   ctypes.POINTER(ctypes.c_size_t)]),
+    "topo_set_record_file": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "topo_set_sweep_rows": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "topo_ip_set_record_file": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "topo_oc_set_record_file": (ctypes.c_int, [_vp, ctypes.c_char_p]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -169,8 +181,19 @@ def element_stiffness(dim, E=1.0, nu=0.3):
 JACOBI, CHEBYSHEV = 0, 1
 
 
+def _k0_array(dim, K0):
+    """The caller's element matrix as a contiguous FP64 host array (None: the analytic K0)."""
+    if K0 is None:
+        return None
+    ne = 8 if dim == 2 else 24
+    a = np.ascontiguousarray(np.asarray(K0, dtype=np.float64))
+    if a.size != ne * ne:
+        raise ValueError("K0 has %d entries, expected %d" % (a.size, ne * ne))
+    return a
+
+
 def _desc(nx, ny, nz, fixed, levels, precision, nu1, nu2, omega, max_iter, nrhs, flexible, E, nu,
-          generic_kernels, omega_auto=False, smoother=0):
+          generic_kernels, omega_auto=False, smoother=0, K0=None):
     dim = 3 if nz else 2
     n = dim * (nx + 1) * (ny + 1) * ((nz + 1) if nz else 1)
     if fixed is None:
@@ -182,10 +205,25 @@ def _desc(nx, ny, nz, fixed, levels, precision, nu1, nu2, omega, max_iter, nrhs,
         omega = 0.6 if dim == 2 else 0.5
     if flexible is None:
         flexible = 0
+    k0 = _k0_array(dim, K0)
     d = SolverDesc(dim, nx, ny, nz, E, nu, fixed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
                    levels, precision, nu1, nu2, omega, max_iter, nrhs, flexible,
-                   int(generic_kernels), int(smoother), int(omega_auto))
+                   int(generic_kernels), int(smoother), int(omega_auto),
+                   None if k0 is None else k0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    d._keep = (fixed, k0)  # the host arrays must outlive the create call
     return d, fixed, dim, n
+
+
+def workspace_bytes(nx, ny, nz=0, fixed=None, levels=3, precision=FP64, nu1=2, nu2=2, omega=None,
+                    max_iter=1000, nrhs=1, flexible=None, E=1.0, nu=0.3, generic_kernels=False,
+                    omega_auto=False, smoother=0, K0=None):
+    """Device bytes a Solver with these arguments allocates (topo_solver_workspace_bytes)."""
+    d, _, _, _ = _desc(nx, ny, nz, fixed, levels, precision, nu1, nu2, omega, max_iter, nrhs,
+                       flexible, E, nu, generic_kernels, omega_auto, smoother, K0)
+    out = ctypes.c_size_t(0)
+    _check(_lib.topo_solver_workspace_bytes(ctypes.byref(d), ctypes.byref(out)),
+           "topo_solver_workspace_bytes")
+    return int(out.value)
 
 
 def ip_options(sigma=0.2, tau_nwt=0.1, tau_ip=1e-8, frac=0.9, step_x_only=False, max_newton=500,
@@ -232,11 +270,12 @@ class IP:
 
     def __init__(self, nx, ny, nz=0, fixed=None, f=None, V=None, xbar=1.0, levels=3,
                  precision=FP64, nu1=2, nu2=2, omega=None, max_iter=1000, E=1.0, nu=0.3,
-                 simp=None):
-        """simp = (p, rmin): the SIMP model with the density filter (topo_ip_set_simp)."""
+                 simp=None, K0=None):
+        """simp = (p, rmin): the SIMP model with the density filter (topo_ip_set_simp).
+        K0: the caller's element matrix (None: the analytic one from E, nu)."""
         import torch
         d, self._fixed, self.dim, self.n = _desc(nx, ny, nz, fixed, levels, precision, nu1, nu2,
-                                                 omega, max_iter, 1, None, E, nu, False)
+                                                 omega, max_iter, 1, None, E, nu, False, K0=K0)
         self.m = nx * ny * (nz if nz else 1)
         self._f = f
         h = _vp()
@@ -247,6 +286,11 @@ class IP:
                "topo_ip_set_stream")
         if simp is not None:
             self.set_simp(*simp)
+
+    def set_record_file(self, path):
+        """Append one JSON line per linear solve to path (None: stop)."""
+        _check(_lib.topo_ip_set_record_file(self._h, None if path is None else str(path).encode()),
+               "topo_ip_set_record_file")
 
     def set_simp(self, p, rmin):
         _check(_lib.topo_ip_set_simp(self._h, float(p), float(rmin)), "topo_ip_set_simp")
@@ -325,10 +369,11 @@ class OC:
     """OC / DOC / AOC on the GPU (see include/topo.h)."""
 
     def __init__(self, nx, ny, nz=0, fixed=None, f=None, V=None, xbar=1.0, levels=3,
-                 precision=FP64, nu1=2, nu2=2, omega=None, max_iter=1000, E=1.0, nu=0.3):
+                 precision=FP64, nu1=2, nu2=2, omega=None, max_iter=1000, E=1.0, nu=0.3,
+                 K0=None):
         import torch
         d, self._fixed, self.dim, self.n = _desc(nx, ny, nz, fixed, levels, precision, nu1, nu2,
-                                                 omega, max_iter, 1, None, E, nu, False)
+                                                 omega, max_iter, 1, None, E, nu, False, K0=K0)
         self.m = nx * ny * (nz if nz else 1)
         h = _vp()
         _check(_lib.topo_oc_create(ctypes.byref(d), _ptr(f), float(V), float(xbar),
@@ -347,6 +392,11 @@ class OC:
             self.close()
         except Exception:
             pass
+
+    def set_record_file(self, path):
+        """Append one JSON line per linear solve to path (None: stop)."""
+        _check(_lib.topo_oc_set_record_file(self._h, None if path is None else str(path).encode()),
+               "topo_oc_set_record_file")
 
     def init(self, x0=None):
         _check(_lib.topo_oc_init(self._h, _ptr(x0) if x0 is not None else None), "topo_oc_init")
@@ -373,13 +423,47 @@ class OC:
         _check(_lib.topo_oc_get_u(self._h, _ptr(u)), "topo_oc_get_u")
         return u
 
+    def state(self):
+        """(x, u, scal, pw): the iterate, the warm-start displacement, scal = (CG tolerance,
+        previous and last compliance, u-valid flag, linear solves, iterations, CG iterations) on
+        the host, and the solver's power-iteration vectors with a trailing ready flag."""
+        import torch
+        x = torch.empty(self.m, dtype=torch.float64, device="cuda")
+        u = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        scal = np.zeros(7)
+        _check(_lib.topo_oc_get_state(self._h, _ptr(x), _ptr(u), scal.ctypes.data_as(_vp)),
+               "topo_oc_get_state")
+        ln = ctypes.c_longlong(0)
+        _check(_lib.topo_oc_power_state_size(self._h, ctypes.byref(ln)), "topo_oc_power_state_size")
+        pw = torch.zeros(ln.value + 1, dtype=torch.float64, device="cuda")
+        ready = ctypes.c_int(0)
+        _check(_lib.topo_oc_get_power_state(self._h, _ptr(pw), ctypes.byref(ready)),
+               "topo_oc_get_power_state")
+        pw[ln.value] = float(ready.value)
+        return x, u, scal, pw
+
+    def set_state(self, x, u, scal, pw=None):
+        scal = np.ascontiguousarray(scal, dtype=np.float64)
+        _check(_lib.topo_oc_set_state(self._h, _ptr(x), _ptr(u), scal.ctypes.data_as(_vp)),
+               "topo_oc_set_state")
+        ln = ctypes.c_longlong(0)
+        _check(_lib.topo_oc_power_state_size(self._h, ctypes.byref(ln)), "topo_oc_power_state_size")
+        if pw is None:
+            _check(_lib.topo_oc_set_power_state(self._h, None, 0), "topo_oc_set_power_state")
+            return
+        if pw.numel() != ln.value + 1:
+            raise ValueError("set_state: power state has %d entries, expected %d"
+                             % (pw.numel(), ln.value + 1))
+        ready = int(float(pw[ln.value]) != 0.0)
+        _check(_lib.topo_oc_set_power_state(self._h, _ptr(pw), ready), "topo_oc_set_power_state")
+
 
 class Solver:
     """MGCG solver for K(x) u = b on one structured grid (see include/topo.h)."""
 
     def __init__(self, nx, ny, nz=0, fixed=None, levels=3, precision=FP64, nu1=2, nu2=2,
                  omega=None, max_iter=1000, nrhs=1, flexible=None, E=1.0, nu=0.3,
-                 generic_kernels=False, omega_auto=False, smoother=0):
+                 generic_kernels=False, omega_auto=False, smoother=0, K0=None):
         dim = 3 if nz else 2
         n = dim * (nx + 1) * (ny + 1) * ((nz + 1) if nz else 1)
         if fixed is None:
@@ -391,10 +475,12 @@ class Solver:
             omega = 0.6 if dim == 2 else 0.5
         if flexible is None:
             flexible = 0
+        k0 = _k0_array(dim, K0)
         d = SolverDesc(dim, nx, ny, nz, E, nu,
                        self._fixed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), levels,
                        precision, nu1, nu2, omega, max_iter, nrhs, flexible, int(generic_kernels),
-                       int(smoother), int(omega_auto))
+                       int(smoother), int(omega_auto),
+                       None if k0 is None else k0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         h = _vp()
         _check(_lib.topo_solver_create(ctypes.byref(d), ctypes.byref(h)), "topo_solver_create")
         self._h = h
@@ -415,6 +501,15 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+    def set_sweep_rows(self, rows):
+        """Strip height of the 2D finest-level FP32 sweeps (topo_set_sweep_rows; 0: automatic)."""
+        _check(_lib.topo_set_sweep_rows(self._h, int(rows)), "topo_set_sweep_rows")
+
+    def set_record_file(self, path):
+        """Append one JSON line per solve to path (topo_set_record_file; None: stop)."""
+        _check(_lib.topo_set_record_file(self._h, None if path is None else str(path).encode()),
+               "topo_set_record_file")
 
     @property
     def device_bytes(self):

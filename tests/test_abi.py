@@ -85,3 +85,37 @@ def test_null_handles_are_rejected_without_a_device():
     assert L.topo_ip_filtered_density(None, buf) == topo.E_INVALID_ARG
     assert L.topo_ip_set_vcycle_fusion(None, 1) == topo.E_INVALID_ARG
     assert L.topo_set_outer_precision(None, 1) == topo.E_INVALID_ARG
+    assert L.topo_oc_get_state(None, buf, buf, buf) == topo.E_INVALID_ARG
+    assert L.topo_oc_set_state(None, buf, buf, buf) == topo.E_INVALID_ARG
+
+
+def test_workspace_query_needs_no_device():
+    """topo_solver_workspace_bytes is pure host arithmetic: it answers here, grows with the
+    number of right-hand sides and with mixed precision's FP32 copies dropped for FP64 vectors as
+    expected, and rejects what topo_solver_create rejects (including an asymmetric K0)."""
+    from oracle import fe
+    from paper_1606_06201_gb300 import topo
+    from paper_1606_06201_gb300 import workloads as W
+    f = W.clamp_xmin(64, 32)
+    b1 = topo.workspace_bytes(64, 32, fixed=f, levels=3)
+    b2 = topo.workspace_bytes(64, 32, fixed=f, levels=3, nrhs=2)
+    assert 0 < b1 < b2
+    # the FP64 solver's five CG vectors alone
+    assert b1 >= 5 * 8 * f.size
+    # the caller's analytic K0 costs the same
+    assert topo.workspace_bytes(64, 32, fixed=f, levels=3, K0=fe.element_stiffness(2)) == b1
+    with pytest.raises(topo.TopoError):
+        topo.workspace_bytes(64, 32, fixed=f, levels=7)       # not divisible by 2^(levels-1)
+    K0 = fe.element_stiffness(2)
+    K0[0, 1] += 1e-3
+    with pytest.raises(topo.TopoError):
+        topo.workspace_bytes(64, 32, fixed=f, levels=3, K0=K0)
+    K0 = fe.element_stiffness(2)
+    K0[3, 3] = np.nan
+    with pytest.raises(topo.TopoError):
+        topo.workspace_bytes(64, 32, fixed=f, levels=3, K0=K0)
+    # a mask that coarsening cannot keep (a fixed fine DOF between free coarse ones)
+    bad = np.zeros_like(f)
+    bad[2 * 1] = 1
+    with pytest.raises(topo.TopoError):
+        topo.workspace_bytes(64, 32, fixed=bad, levels=3)

@@ -1,0 +1,130 @@
+"""IP (Sec. 3) and AOC (Sec. 4.3) on the Example-2-shaped 512 x 256 cantilever (shape 428,
+V = 0.4 m, xbar = 1, 6 levels, 263,682 DOFs) on the GPU against the oracle's runs with exact
+(banded Cholesky) solves, in FP64 and in mixed precision.
+
+FP64: linear systems solved to a parity tolerance (1e-14); the same Newton and barrier counts, and x, u,
+lambda and f^T u at several Newton steps and at the end within 1e-10 (relative; lambda and the
+Newton criterion absolute), and the AOC compliance and lambda at every iteration with x and u at
+several iterations within 1e-10.  Mixed precision (FP32 V-cycle, FP64 recurrences): the final x
+and f^T u within 1e-6.
+
+The two oracle runs take a minute or two of CPU time; they run in two spawned CPU processes (the
+host's cores split between them) while the GPU runs its own part.
+"""
+import numpy as np
+import pytest
+
+from oracle import runs as oracle_runs
+from gpu_helpers import dev, host, topo_lib, torch_cuda
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+NX, NY, VOLFRAC, LEVELS = 512, 256, 0.4, 6
+IP_STEPS = (1, 5, 10, 20)
+AOC_FEVAL = 50
+AOC_ITERS = (1, 5, 10, 25)
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def oracle_c2():
+    pool, _ = oracle_runs.spawn_pool(2)
+    ip_job = pool.apply_async(oracle_runs.ip_run, (NX, NY, VOLFRAC, IP_STEPS))
+    oc_job = pool.apply_async(oracle_runs.aoc_run, (NX, NY, VOLFRAC, AOC_FEVAL, AOC_ITERS))
+    pool.close()
+    yield ip_job, oc_job
+    pool.terminate()
+    pool.join()
+
+
+def _cfg():
+    cfg, _ = oracle_runs.cantilever_problem(NX, NY, VOLFRAC)
+    return cfg
+
+
+def test_c2_ip_fp64_and_mixed_match_oracle(oracle_c2):
+    torch = torch_cuda()
+    topo = topo_lib()
+    cfg = _cfg()
+    f = dev(torch, cfg["f"])
+    # GPU runs first (the oracle works meanwhile)
+    # 64 times the condition number of the 64 x 32 case: the systems are solved to 1e-14 (or to
+    # stagnation) so that x, u stay within 1e-10 of the oracle's exact solves
+    ip64 = topo.IP(NX, NY, fixed=cfg["fixed"], f=f, V=cfg["V"], xbar=1.0, levels=LEVELS,
+                   max_iter=10000)
+    opts = topo.ip_options(cg_tol=1e-14, cg_tol_init=1e-15)
+    ip64.init(opts)
+    steps, kept = [], {}
+    while True:
+        info = ip64.step(opts)
+        u, x, phi, psi, scal, _ = ip64.state()
+        steps.append((info.crit, float(scal[0]), info.ip_iters))
+        if info.newton in IP_STEPS:
+            kept[info.newton] = (host(x), host(u))
+        if info.done or info.newton >= 200:
+            break
+    u64, x64 = host(ip64.state()[0]), host(ip64.state()[1])
+    ip64.close()
+    ipm = topo.IP(NX, NY, fixed=cfg["fixed"], f=f, V=cfg["V"], xbar=1.0, levels=LEVELS,
+                  precision=topo.MIXED, max_iter=5000)
+    infom = ipm.run(topo.ip_options(cg_tol=1e-10))
+    um, xm = host(ipm.state()[0]), host(ipm.state()[1])
+    ipm.close()
+
+    o = oracle_c2[0].get(timeout=3600)
+    assert info.done == 1 and info.newton == o["newton"] and info.ip_iters == o["ip"] == 12
+    for k, (crit, lam, _) in enumerate(steps):
+        assert abs(crit - o["crit"][k]) <= 1e-8, k
+        assert abs(lam - o["lam"][k]) <= 1e-9 * max(1.0, abs(o["lam"][k])), k
+    for k in IP_STEPS:
+        xo, uo = o["kept"][k]
+        assert _rel(kept[k][0], xo) <= 1e-10, (k, _rel(kept[k][0], xo))
+        assert _rel(kept[k][1], uo) <= 1e-10, (k, _rel(kept[k][1], uo))
+    assert _rel(x64, o["x"]) <= 1e-10 and _rel(u64, o["u"]) <= 1e-10
+    c_or = o["compliance"]
+    assert abs(float(cfg["f"] @ u64) - c_or) <= 1e-10 * c_or
+    # mixed precision
+    assert infom.done == 1 and infom.ip_iters == 12
+    assert _rel(xm, o["x"]) <= 1e-6, _rel(xm, o["x"])
+    assert abs(float(cfg["f"] @ um) - c_or) <= 1e-6 * c_or
+
+
+def test_c2_aoc_fp64_and_mixed_match_oracle(oracle_c2):
+    torch = torch_cuda()
+    topo = topo_lib()
+    cfg = _cfg()
+    f = dev(torch, cfg["f"])
+    results = {}
+    for prec, tol in ((topo.FP64, 1e-14), (topo.MIXED, 1e-10)):
+        oc = topo.OC(NX, NY, fixed=cfg["fixed"], f=f, V=cfg["V"], xbar=1.0, levels=LEVELS,
+                     precision=prec, max_iter=10000)
+        oc.init()
+        opts = topo.oc_options(variant=topo.OC_AOC, tau_oc=0.0, max_feval=AOC_FEVAL,
+                               cg_tol0=tol, adaptive_tol=False)
+        comps, lams, kept = [], [], {}
+        for it in range(1, AOC_FEVAL // 2 + 1):
+            if it in AOC_ITERS:
+                x_start = host(oc.x())
+            info = oc.step(opts)
+            comps.append(info.compliance)
+            lams.append(info.lam)
+            if it in AOC_ITERS:
+                kept[it] = x_start
+        results[prec] = (comps, lams, kept, host(oc.x()))
+        oc.close()
+
+    o = oracle_c2[1].get(timeout=3600)
+    assert o["iters"] == AOC_FEVAL // 2
+    comps, lams, kept, x_end = results[topo.FP64]
+    for k in range(o["iters"]):
+        assert abs(comps[k] - o["compliance"][k]) <= 1e-10 * o["compliance"][k], k
+        assert abs(lams[k] - o["lam"][k]) <= 1e-9 * o["lam"][k], k
+    for k in AOC_ITERS:
+        assert _rel(kept[k], o["kept"][k][0]) <= 1e-10, (k, _rel(kept[k], o["kept"][k][0]))
+    assert _rel(x_end, o["x"]) <= 1e-10
+    comps, lams, kept, x_end = results[topo.MIXED]
+    assert abs(comps[-1] - o["compliance"][-1]) <= 1e-6 * o["compliance"][-1]
+    assert _rel(x_end, o["x"]) <= 1e-6, _rel(x_end, o["x"])

@@ -39,15 +39,15 @@ def test_3d_128x64x64_eight_load_cases_batched_with_autotuned_smoother(tmp_path)
     in the true residual."""
     torch = torch_cuda()
     topo = topo_lib()
-    from paper_1606_06201_gb300.autotune import autotune
+    from paper_1606_06201_gb300.autotune import autotune, solver_for
     nx, ny, nz, levels = 128, 64, 64, 5
     cfg = W.random_field_3d(nx, ny, nz, n_rhs=8)
     x = dev(torch, cfg["x"])
     F = dev(torch, cfg["f"])
     best = autotune(nx, ny, nz, cfg["fixed"], x, F, levels, precision=topo.MIXED, nrhs=8,
-                    tol=1e-8, sweeps=(1, 2), reps=1, cache_path=str(tmp_path / "tune.json"))
-    s = topo.Solver(nx, ny, nz, fixed=cfg["fixed"], levels=levels, precision=topo.MIXED, nrhs=8,
-                    nu1=best["nu"], nu2=best["nu"], omega=best["omega"])
+                    tol=1e-8, sweeps=(1, 2), cheb_degrees=(1, 2), reps=1,
+                    cache_path=str(tmp_path / "tune.json"))
+    s = solver_for(best, nx, ny, nz, cfg["fixed"], levels, precision=topo.MIXED, nrhs=8)
     s.set_density(x)
     U, info = s.solve(F, tol=1e-8)
     assert info.status == topo.OK

@@ -269,3 +269,48 @@ def test_ip_512x256_scalars_stay_consistent():
             assert info.alpha > 0.5, info.alpha
         assert abs(xh.sum() - cfg["V"]) <= 1e-6 * cfg["V"]
         ip.close()
+
+
+@pytest.mark.parametrize("variant", ["aoc", "oc"])
+def test_oc_adaptive_cg_tolerance_matches_oracle(variant):
+    """Sec. 6.2: linear systems solved by MGCG to tau, tau starting at 0.1 and multiplied by 0.1
+    after an iteration whose compliance exceeds the previous one's, warm starts from the previous
+    u.  The oracle runs the same rule with its reference MGCG (the same hierarchy depth, smoother
+    and stopping test), so the GPU (FP64) takes the same tolerance at every iteration, the same
+    CG iteration counts and the same compliances."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    cfg, prob = _problem(64, 32)
+    feval = 40
+    sol = ooc.MGCGSolve(prob, levels=3, nu1=2, nu2=2, omega=0.6, tau=0.1)
+    _, oinfo = ooc.oc_run(prob, variant=variant, tau_oc=0.0, max_feval=feval, solve=sol,
+                          adaptive_tol=True)
+    taus = oinfo["tau"]
+    assert any(taus[k] < taus[k - 1] for k in range(1, len(taus)))  # the rule fired
+    comp = oinfo["compliance"]
+    # every decision c_k > c_{k-1} has a margin far above the solves' rounding (equal values come
+    # from solves that took no CG iteration and left u unchanged, on both sides)
+    assert all(comp[k] == comp[k - 1] or abs(comp[k] - comp[k - 1]) > 1e-9 * comp[k]
+               for k in range(1, len(comp)))
+    vmap = {"aoc": topo.OC_AOC, "oc": topo.OC_PLAIN}
+    solver = topo.OC(64, 32, fixed=cfg["fixed"], f=dev(torch, cfg["f"]), V=cfg["V"], xbar=1.0,
+                     levels=3, omega=0.6)
+    solver.init()
+    opts = topo.oc_options(variant=vmap[variant], tau_oc=0.0, max_feval=feval, cg_tol0=0.1,
+                           adaptive_tol=True)
+    info = solver.run(opts)
+    assert info.iters == oinfo["iters"] and info.feval == oinfo["feval"]
+    assert info.cg_iters == sol.iterations
+    assert abs(info.compliance - comp[-1]) <= 1e-10 * comp[-1]
+    assert info.cg_tol == pytest.approx(sol.tau, rel=1e-12)
+    solver.close()
+    # step by step: the tolerance in force and the compliance of every iteration
+    solver = topo.OC(64, 32, fixed=cfg["fixed"], f=dev(torch, cfg["f"]), V=cfg["V"], xbar=1.0,
+                     levels=3, omega=0.6)
+    solver.init()
+    for k in range(oinfo["iters"]):
+        info = solver.step(opts)
+        assert abs(info.compliance - comp[k]) <= 1e-10 * comp[k], k
+        if k + 1 < len(taus):
+            assert info.cg_tol == pytest.approx(taus[k + 1], rel=1e-12), k
+    solver.close()

@@ -570,22 +570,31 @@ def test_chebyshev_smoother_solves_and_is_symmetric(precision):
     assert rel_err(host(u2), exact2) <= (1e-10 if precision == 0 else 1e-6)
 
 
-def test_autotuner_picks_a_converging_setting(tmp_path):
-    """The smoother autotuner times full solves over (omega, nu), caches the fastest converging
-    setting per (grid, precision, batch) and that setting solves to the tolerance."""
+@pytest.mark.parametrize("shape", [(16, 8, 8, 3, 4), (256, 128, 0, 6, 1)])
+def test_autotuner_picks_a_converging_setting(tmp_path, shape):
+    """The autotuner times full solves over damped Jacobi (omega, nu), the Chebyshev degree and,
+    in 2D, the strip height of the finest-level sweeps; it caches the fastest converging setting
+    per (grid, precision, batch) and that setting solves to the tolerance."""
     torch = torch_cuda()
     topo = topo_lib()
     from paper_1606_06201_gb300 import autotune
-    cfg = W.random_field_3d(16, 8, 8, n_rhs=4)
+    nx, ny, nz, levels, nrhs = shape
+    if nz:
+        cfg = W.random_field_3d(nx, ny, nz, n_rhs=nrhs)
+    else:
+        cfg = W.random_field_2d(nx, ny)
     x, F = dev(torch, cfg["x"]), dev(torch, cfg["f"])
     path = str(tmp_path / "tune.json")
-    best = autotune.autotune(16, 8, 8, cfg["fixed"], x, F, levels=3, precision=topo.MIXED, nrhs=4,
-                             tol=1e-8, omegas=(0.3, 0.5), sweeps=(1, 2), cache_path=path)
-    assert best["omega"] in (0.3, 0.5) and best["nu"] in (1, 2) and best["ms"] > 0
+    best = autotune.autotune(nx, ny, nz, cfg["fixed"], x, F, levels=levels, precision=topo.MIXED,
+                             nrhs=nrhs, tol=1e-8, omegas=(0.3, 0.5), sweeps=(1, 2),
+                             cheb_degrees=(1, 2), rows=(0, 4, 8), cache_path=path)
+    assert best["smoother"] in ("jacobi", "chebyshev") and best["nu"] in (1, 2)
+    assert best["ms"] > 0 and best["tried"] == 6 + (0 if nz else 2)
+    assert best["rows"] in ((0,) if nz else (0, 4, 8))
     import json
     assert list(json.load(open(path)).values())[0] == best
-    s = topo.Solver(16, 8, 8, fixed=cfg["fixed"], levels=3, precision=topo.MIXED, nrhs=4,
-                    omega=best["omega"], nu1=best["nu"], nu2=best["nu"])
+    s = autotune.solver_for(best, nx, ny, nz, cfg["fixed"], levels, precision=topo.MIXED,
+                            nrhs=nrhs)
     s.set_density(x)
     _, info = s.solve(F, tol=1e-8)
     assert info.status == topo.OK and info.rel_residual <= 1e-8

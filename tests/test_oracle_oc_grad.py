@@ -67,3 +67,26 @@ def test_gradient_matches_central_differences(which):
         xm[e] -= h
         fd[k] = (w @ prob.solve_u(xp) - w @ prob.solve_u(xm)) / (2 * h)
     assert np.linalg.norm(g[idx] - fd) <= 1e-5 * np.linalg.norm(fd)
+
+
+def test_inexact_oc_adaptive_tolerance_rule():
+    """Sec. 6.2 in the oracle: with MGCG solves the tolerance of iteration k is tau_0 * 0.1^j, j
+    the number of earlier iterations whose compliance rose; with a tight tau_0 the inexact run
+    reproduces the exact-solve run."""
+    prob = _problem(32, 16)
+    sol = oc.MGCGSolve(prob, levels=3, tau=0.1)
+    _, info = oc.oc_run(prob, variant="oc", tau_oc=0.0, max_feval=30, solve=sol,
+                        adaptive_tol=True)
+    c, taus = info["compliance"], info["tau"]
+    rises = 0
+    for k in range(len(c)):
+        assert taus[k] == pytest.approx(0.1 * 0.1 ** rises, rel=1e-15), k
+        if k >= 1 and c[k] > c[k - 1]:
+            rises += 1
+    assert rises >= 1
+    tight = oc.MGCGSolve(prob, levels=3, tau=1e-12)
+    _, inexact = oc.oc_run(prob, variant="aoc", tau_oc=0.0, max_feval=20, solve=tight,
+                           adaptive_tol=True)
+    _, exact = oc.oc_run(prob, variant="aoc", tau_oc=0.0, max_feval=20)
+    np.testing.assert_allclose(inexact["compliance"], exact["compliance"], rtol=1e-9)
+    np.testing.assert_allclose(inexact["x"], exact["x"], rtol=0, atol=1e-8)
