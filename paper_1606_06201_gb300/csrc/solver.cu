@@ -353,8 +353,11 @@ cudaError_t q1_smooth_beta(const topo_solver* s, int nx, int ny, const TV* x, co
 // rank-one terms and lambda row) for IP systems, the generic element-matrix kernels elsewhere.
 template <typename TV>
 topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* b, TV* y,
-                        const CgScalars* sc, const TV* zc = nullptr) {
+                        const CgScalars* sc, const TV* zc = nullptr, int nrhs = 0) {
   Level& lv = s->L[k];
+  // nrhs: the vectors v, b, y hold this many right-hand sides (0: the solver's batch); the
+  // build-time power iteration applies the operator to a single vector
+  if (nrhs <= 0) nrhs = s->nrhs;
   // adaptive damping: omega_k is folded into invd at build time (and read from the device for the
   // lambda entry), so the kernels take omega = 1
   const TV omega = lv.omega_dev ? TV(1) : (TV)s->desc.omega;
@@ -375,23 +378,23 @@ topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* 
   }
   if (k == 0 && s->q1_ok) {
     TOPO_CUDA(q1_apply<TV>(s, lv.d.nx, lv.d.ny, mode, Prec<TV>::x(s), v, b, y, omega, lv.fixed,
-                           s->nrhs, sc));
+                           nrhs, sc));
     return TOPO_OK;
   }
   if (k == 1 && s->l1_free && std::is_same<TV, float>::value) {
     if (s->q1_ok)
       TOPO_CUDA(launch_q1g_apply(lv.d.nx, lv.d.ny, mode, s->q1, s->x32, (const float*)v,
                                  (const float*)b, (float*)y, (float)omega, s->L[1].invd32,
-                                 lv.fixed, s->nrhs, sc, s->st, (const float*)zc));
+                                 lv.fixed, nrhs, sc, s->st, (const float*)zc));
     else
       TOPO_CUDA(launch_apply_l1<float>(lv.d, mode, s->C32, s->x32, (const float*)v,
                                        (const float*)b, (float*)y, s->L[1].invd32, (float)omega,
-                                       lv.fixed, s->nrhs, sc, s->st));
+                                       lv.fixed, nrhs, sc, s->st));
     return TOPO_OK;
   }
   if (k == 1 && s->l1_free) {  // FP64 products on the matrix-free level (build-time power iteration)
     TOPO_CUDA(launch_apply_l1<double>(lv.d, mode, s->C, s->x, (const double*)v, (const double*)b,
-                                      (double*)y, lv.invd, (double)omega, lv.fixed, s->nrhs, sc,
+                                      (double*)y, lv.invd, (double)omega, lv.fixed, nrhs, sc,
                                       s->st));
     return TOPO_OK;
   }
@@ -402,7 +405,7 @@ topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* 
     return TOPO_E_INVALID_ARG;
   }
   TOPO_CUDA(launch_apply<TV>(lv.d, mode, Prec<TV>::K0(s), x, Ae, v, b, y, Prec<TV>::invd(lv), omega,
-                             lv.fixed, s->nrhs, sc, s->st));
+                             lv.fixed, nrhs, sc, s->st));
   return TOPO_OK;
 }
 
@@ -987,7 +990,7 @@ topo_status enqueue_build(topo_solver* s, bool warm = false) {
       if (!warm) TOPO_CUDA(launch_power_init(lv.n, ar, pv, lv.fixed, st));
       const int steps = warm ? kPowerWarm : kPowerCold;
       for (int it = 0; it < steps; ++it) {
-        TOPO_TRY(apply_level<double>(s, k, 0, pv, nullptr, s->q, nullptr));
+        TOPO_TRY(apply_level<double>(s, k, 0, pv, nullptr, s->q, nullptr, nullptr, 1));
         TOPO_CUDA(launch_power_step(lv.n, ar, pv, s->q, lv.invd, s->zll, s->r, s->partials,
                                     s->counters, s->pw_est, st));
       }

@@ -598,3 +598,29 @@ def test_autotuner_picks_a_converging_setting(tmp_path, shape):
     s.set_density(x)
     _, info = s.solve(F, tol=1e-8)
     assert info.status == topo.OK and info.rel_residual <= 1e-8
+
+
+@pytest.mark.parametrize("shape", [(64, 32, 0, 4), (16, 8, 8, 3)])
+@pytest.mark.parametrize("kind", ["chebyshev", "omega_auto"])
+def test_batched_power_iteration_smoothers_equal_individual_solves(shape, kind):
+    """Chebyshev smoothing and the adaptive damping take lambda_max from a build-time power
+    iteration on one vector per level: a batch of right-hand sides gets the same smoother as a
+    single solve, and the batched solutions equal the individual ones."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny, nz, levels = shape
+    fixed = W.clamp_xmin(nx, ny, nz)
+    x = dev(torch, _x(nx, ny, nz, 47))
+    F = np.stack([W.normal_load(fixed, 80 + k) for k in range(3)])
+    kw = dict(smoother=topo.CHEBYSHEV) if kind == "chebyshev" else dict(omega_auto=True)
+    sb = topo.Solver(nx, ny, nz, fixed=fixed, levels=levels, nrhs=3, **kw)
+    sb.set_density(x)
+    U, info = sb.solve(dev(torch, F), tol=1e-12)
+    assert info.status == topo.OK
+    s1 = topo.Solver(nx, ny, nz, fixed=fixed, levels=levels, **kw)
+    s1.set_density(x)
+    for k in range(3):
+        u, _ = s1.solve(dev(torch, F[k]), tol=1e-12)
+        np.testing.assert_allclose(host(U)[k], host(u), rtol=0, atol=1e-12 * np.abs(host(u)).max())
+    sb.close()
+    s1.close()
