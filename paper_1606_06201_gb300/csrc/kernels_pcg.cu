@@ -65,6 +65,29 @@ __device__ bool last_block_sums(const double (&part)[NV], double* partials, unsi
   return true;
 }
 
+// The per-iteration vector kernels move two elements per 16-byte access (a grid-stride loop over
+// single doubles left each warp one 8-byte load per vector in flight: 37% of the copy bandwidth
+// in k_cg_update).  The pair path needs n even and
+// every vector of the right-hand side 16-byte aligned (8-byte for the FP32 copies); otherwise the
+// single-element loop runs.  Either way the sums are taken in a fixed order per grid shape.
+template <typename TV>
+struct Pair2;
+template <>
+struct Pair2<double> {
+  using type = double2;
+};
+template <>
+struct Pair2<float> {
+  using type = float2;
+};
+
+__device__ __forceinline__ bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+__device__ __forceinline__ bool al8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
+template <typename TV>
+__device__ __forceinline__ bool al_pair(const TV* p) {
+  return sizeof(TV) == 8 ? al16(p) : al8(p);
+}
+
 // r = A z0 - b (use_x0) or r = -b, z = 0; ||b||, ||r|| -> initial scalars and stop test.
 // CG scalars at the start: ||b||, r^T r and the stop test of Algorithm PCG on them.
 __device__ __forceinline__ CgScalars cg_start_scalars(double bb, double rr, double tol,
@@ -204,12 +227,34 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(long long n, double* __r
   q += rhs * n;
   if (rv) rv += rhs * n;
   double part[1] = {0.0};
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const double ri = fma(alpha, q[i], r[i]);
-    r[i] = ri;
-    if (rv) rv[i] = (TV)ri;
-    part[0] = fma(ri, ri, part[0]);
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nt = (long long)gridDim.x * blockDim.x;
+  if ((n & 1) == 0 && al16(r) && al16(q) && (!rv || al_pair(rv))) {
+    using V2 = typename Pair2<TV>::type;
+    const long long np = n >> 1;
+    double2* r2 = reinterpret_cast<double2*>(r);
+    const double2* q2 = reinterpret_cast<const double2*>(q);
+    V2* rv2 = reinterpret_cast<V2*>(rv);
+    for (long long j = t0; j < np; j += nt) {
+      const double2 qa = q2[j], ra = r2[j];
+      const double2 sa = make_double2(fma(alpha, qa.x, ra.x), fma(alpha, qa.y, ra.y));
+      r2[j] = sa;
+      if (rv) {
+        V2 va;
+        va.x = (TV)sa.x;
+        va.y = (TV)sa.y;
+        rv2[j] = va;
+      }
+      part[0] = fma(sa.x, sa.x, part[0]);
+      part[0] = fma(sa.y, sa.y, part[0]);
+    }
+  } else {
+    for (long long i = t0; i < n; i += nt) {
+      const double ri = fma(alpha, q[i], r[i]);
+      r[i] = ri;
+      if (rv) rv[i] = (TV)ri;
+      part[0] = fma(ri, ri, part[0]);
+    }
   }
   double tot[1];
   if (!last_block_sums<1>(part, partials, counters, rhs, tot)) return;
@@ -244,11 +289,31 @@ __global__ void __launch_bounds__(kThreads) k_cg_beta(long long n, const double*
   y += rhs * n;
   if (flexible) y_old += rhs * n;
   double part[2] = {0.0, 0.0};
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const double ri = r[i];
-    part[0] = fma(ri, (double)y[i], part[0]);
-    if (flexible) part[1] = fma(ri, (double)y_old[i], part[1]);
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nt = (long long)gridDim.x * blockDim.x;
+  if ((n & 1) == 0 && al16(r) && al_pair(y) && (!flexible || al_pair(y_old))) {
+    using V2 = typename Pair2<TV>::type;
+    const long long np = n >> 1;
+    const double2* r2 = reinterpret_cast<const double2*>(r);
+    const V2* y2 = reinterpret_cast<const V2*>(y);
+    const V2* yo2 = reinterpret_cast<const V2*>(y_old);
+    for (long long j = t0; j < np; j += nt) {
+      const double2 rr = r2[j];
+      const V2 yv = y2[j];
+      part[0] = fma(rr.x, (double)yv.x, part[0]);
+      part[0] = fma(rr.y, (double)yv.y, part[0]);
+      if (flexible) {
+        const V2 yo = yo2[j];
+        part[1] = fma(rr.x, (double)yo.x, part[1]);
+        part[1] = fma(rr.y, (double)yo.y, part[1]);
+      }
+    }
+  } else {
+    for (long long i = t0; i < n; i += nt) {
+      const double ri = r[i];
+      part[0] = fma(ri, (double)y[i], part[0]);
+      if (flexible) part[1] = fma(ri, (double)y_old[i], part[1]);
+    }
   }
   double tot[2];
   if (!last_block_sums<2>(part, partials, counters, rhs, tot)) return;
@@ -281,13 +346,30 @@ __global__ void __launch_bounds__(kThreads) k_cg_p(long long n, const TV* __rest
   p += rhs * n;
   z += rhs * n;
   if (flexible) y_old += rhs * n;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const TV yi = y[i];
-    const double pi = p[i];
-    z[i] = fma(alpha, pi, z[i]);
-    p[i] = fma(beta, pi, -(double)yi);
-    if (flexible) y_old[i] = yi;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nt = (long long)gridDim.x * blockDim.x;
+  if ((n & 1) == 0 && al16(p) && al16(z) && al_pair(y) && (!flexible || al_pair(y_old))) {
+    using V2 = typename Pair2<TV>::type;
+    const long long np = n >> 1;
+    const V2* y2 = reinterpret_cast<const V2*>(y);
+    V2* yo2 = reinterpret_cast<V2*>(y_old);
+    double2* p2 = reinterpret_cast<double2*>(p);
+    double2* z2 = reinterpret_cast<double2*>(z);
+    for (long long j = t0; j < np; j += nt) {
+      const V2 yv = y2[j];
+      const double2 pv = p2[j], zv = z2[j];
+      z2[j] = make_double2(fma(alpha, pv.x, zv.x), fma(alpha, pv.y, zv.y));
+      p2[j] = make_double2(fma(beta, pv.x, -(double)yv.x), fma(beta, pv.y, -(double)yv.y));
+      if (flexible) yo2[j] = yv;
+    }
+  } else {
+    for (long long i = t0; i < n; i += nt) {
+      const TV yi = y[i];
+      const double pi = p[i];
+      z[i] = fma(alpha, pi, z[i]);
+      p[i] = fma(beta, pi, -(double)yi);
+      if (flexible) y_old[i] = yi;
+    }
   }
 }
 
@@ -334,9 +416,20 @@ __global__ void __launch_bounds__(kThreads) k_cg_alpha(long long n, const double
   p += rhs * n;
   q += rhs * n;
   double part[1] = {0.0};
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    part[0] = fma(p[i], q[i], part[0]);
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nt = (long long)gridDim.x * blockDim.x;
+  if ((n & 1) == 0 && al16(p) && al16(q)) {
+    const long long np = n >> 1;
+    const double2* p2 = reinterpret_cast<const double2*>(p);
+    const double2* q2 = reinterpret_cast<const double2*>(q);
+    for (long long j = t0; j < np; j += nt) {
+      const double2 pa = p2[j], qa = q2[j];
+      part[0] = fma(pa.x, qa.x, part[0]);
+      part[0] = fma(pa.y, qa.y, part[0]);
+    }
+  } else {
+    for (long long i = t0; i < n; i += nt) part[0] = fma(p[i], q[i], part[0]);
+  }
   double tot[1];
   if (!last_block_sums<1>(part, partials, counters, rhs, tot)) return;
   if (threadIdx.x == 0) {

@@ -4,8 +4,9 @@ V = 0.4 m, xbar = 1, 6 levels, 263,682 DOFs) on the GPU against the oracle's run
 
 FP64: linear systems solved to a parity tolerance (1e-14); the same Newton and barrier counts, and u,
 lambda and f^T u at several Newton steps and at the end within 1e-10 (relative; lambda and the
-Newton criterion absolute) with x within 1e-9, and the AOC compliance and lambda at every iteration
-with x at several iterations within 1e-10.  Mixed precision (FP32 V-cycle, FP64 recurrences): the final x
+Newton criterion absolute) with x within 1e-7 (the densities carry the solves' rounding amplified by
+D^{-1}), and the AOC compliance and lambda at every iteration within 1e-10 with x at several
+iterations within 1e-10 + 4 tau_lambda / lambda (the bisection's own resolution).  Mixed precision (FP32 V-cycle, FP64 recurrences): the final x
 and f^T u within 1e-6.
 
 The two oracle runs take a minute or two of CPU time; they run in two spawned CPU processes (the
@@ -79,18 +80,22 @@ def test_c2_ip_fp64_and_mixed_match_oracle(oracle_c2):
     for k, (crit, lam, _) in enumerate(steps):
         assert abs(crit - o["crit"][k]) <= 1e-8, k
         assert abs(lam - o["lam"][k]) <= 1e-9 * max(1.0, abs(o["lam"][k])), k
-    # the displacement and the compliance within 1e-10; the densities within 1e-9 (at step 10
-    # they reach 1.7e-10: both sides carry the rounding of a solve whose condition number is
-    # 64 times the 64 x 32 case's, where 1e-10 holds for x too)
+    # the displacement and the compliance within 1e-10.  The densities follow from the direction
+    # through d_x = D^{-1} (B^T d_u + d_lambda - tilde Res3) (Eq. (nwtr), row 3), and
+    # D = phi / x + psi / (xbar - x) falls with the barrier parameters (phi ~ s / x): near the
+    # optimum D^{-1} ~ x^2 / s reaches 1e8, and the rounding of the Z solves (1e-14 relative
+    # residual on the GPU, Cholesky in the oracle) reaches x amplified by it.  Measured on this
+    # grid: 6e-12 at Newton step 1, 2e-10 at step 10, 3e-9 at step 20, 1.6e-8 at the end, while u
+    # and f^T u agree to 1e-12 or better there.  x is held to 1e-7.
+    c_or = o["compliance"]
     errs = {k: (_rel(kept[k][0], o["kept"][k][0]), _rel(kept[k][1], o["kept"][k][1]),
                 abs(float(cfg["f"] @ kept[k][1]) - float(cfg["f"] @ o["kept"][k][1]))
                 / abs(float(cfg["f"] @ o["kept"][k][1])))
             for k in IP_STEPS}
+    errs["final"] = (_rel(x64, o["x"]), _rel(u64, o["u"]),
+                     abs(float(cfg["f"] @ u64) - c_or) / abs(c_or))
     for k, (ex, eu, ec) in errs.items():
-        assert ex <= 1e-9 and eu <= 1e-10 and ec <= 1e-10, (k, errs)
-    assert _rel(x64, o["x"]) <= 1e-9 and _rel(u64, o["u"]) <= 1e-10, errs
-    c_or = o["compliance"]
-    assert abs(float(cfg["f"] @ u64) - c_or) <= 1e-10 * c_or
+        assert ex <= 1e-7 and eu <= 1e-10 and ec <= 1e-10, (k, errs)
     # mixed precision
     assert infom.done == 1 and infom.ip_iters == 12
     assert _rel(xm, o["x"]) <= 1e-6, _rel(xm, o["x"])
@@ -127,9 +132,17 @@ def test_c2_aoc_fp64_and_mixed_match_oracle(oracle_c2):
     for k in range(o["iters"]):
         assert abs(comps[k] - o["compliance"][k]) <= 1e-10 * o["compliance"][k], k
         assert abs(lams[k] - o["lam"][k]) <= 1e-9 * o["lam"][k], k
+    # x^NEW = min(max(x E / lambda, xlow), xbar) with lambda from a bisection stopped at
+    # tau_lambda = 1e-11 (Algorithm OC): where E agrees to rounding, the two lambdas still differ
+    # by up to tau_lambda when a bisection decision near the root goes the other way, and x by
+    # the same relative amount.  Each x (the iterate an AOC iteration starts from, which is the
+    # average of two OC steps) is held to 1e-10 + 4 tau_lambda / lambda of the steps before it.
     for k in AOC_ITERS:
-        assert _rel(kept[k], o["kept"][k][0]) <= 1e-10, (k, _rel(kept[k], o["kept"][k][0]))
-    assert _rel(x_end, o["x"]) <= 1e-10
+        lam_min = min(o["lam"][:k]) if k > 1 else o["lam"][0]
+        tol = 1e-10 + 4e-11 / lam_min
+        assert _rel(kept[k], o["kept"][k][0]) <= tol, (k, _rel(kept[k], o["kept"][k][0]), tol)
+    tol = 1e-10 + 4e-11 / min(o["lam"])
+    assert _rel(x_end, o["x"]) <= tol, (_rel(x_end, o["x"]), tol)
     comps, lams, kept, x_end = results[topo.MIXED]
     assert abs(comps[-1] - o["compliance"][-1]) <= 1e-6 * o["compliance"][-1]
     assert _rel(x_end, o["x"]) <= 1e-6, _rel(x_end, o["x"])
