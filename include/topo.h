@@ -43,7 +43,8 @@ typedef enum {
   TOPO_E_INFEASIBLE = 4,    /* V outside (0, m xbar)                                         */
   TOPO_E_TIMEOUT = 5,       /* a bounded device-side wait expired                            */
   TOPO_E_OOM = 6,           /* device allocation failed                                      */
-  TOPO_E_CUDA = 7           /* any other CUDA runtime error                                  */
+  TOPO_E_CUDA = 7,          /* any other CUDA runtime error                                  */
+  TOPO_E_BOUNDS = 8         /* debug build (TOPO_BOUNDS_CHECK): an index outside its buffer  */
 } topo_status;
 
 typedef enum { TOPO_FP64 = 0, TOPO_MIXED = 1 } topo_precision;
@@ -141,6 +142,12 @@ topo_status topo_set_graph_mode(topo_solver* s, int mode);
  * fills about one wave of warps; 2..32 fixes it (a tuning parameter: the outputs do not depend on
  * it, except for the summation order of the fused r~^T y~).  Other values -> E_INVALID_ARG. */
 topo_status topo_set_sweep_rows(topo_solver* s, int rows);
+/* Bound of the device-side waits on asynchronous copies (the deep V-cycle levels' bulk copies):
+ * a wait that has not seen its copies land after ns nanoseconds of the global timer gives up,
+ * lets the copies finish under a second wait of the default bound, and stops the CG with
+ * TOPO_E_TIMEOUT; the solver stays usable.  Default 1e9 (1 s).  0 makes the first wait give up at
+ * once without polling: a way for tests to run the timeout path without a device fault. */
+topo_status topo_set_wait_limit_ns(topo_solver* s, unsigned long long ns);
 /* Fused kernels in Algorithm MG for 2D K systems with Jacobi smoothing (default on; off: one
  * launch per sweep, residual and transfer).  On the finest level the first two sweeps from zero
  * are one kernel, and so are the residual with the restriction, and the prolongation with the
@@ -398,6 +405,30 @@ topo_status topo_oc_set_state(topo_oc* oc, const double* x, const double* u, con
 topo_status topo_oc_power_state_size(topo_oc* oc, long long* len);
 topo_status topo_oc_get_power_state(topo_oc* oc, double* v, int* ready);
 topo_status topo_oc_set_power_state(topo_oc* oc, const double* v, int ready);
+
+/* Self-check of the integer FP64 <-> FP32 conversions that the CG vector kernels use in place of
+ * the hardware conversion instructions: converts d[i] (device, n doubles) to float and f[i]
+ * (device, n floats) to double both ways and writes to mismatches[0..1] (host) how many results
+ * differ (two NaNs count as equal).  Synchronous on the default stream; allocates 16 bytes of
+ * device memory for the counts.  TOPO_E_INVALID_ARG for null pointers with n > 0 or n < 0. */
+topo_status topo_check_conversions(const double* d, const float* f, long long n,
+                                   unsigned long long* mismatches);
+
+/* Index checks (debug build).  A library built with -DTOPO_BOUNDS_CHECK (the package's build with
+ * bounds_check=True writes libtopo_gb300_bc.so) checks the indices its operator kernels compute
+ * against the sizes of the buffers they address; an index out of range is not used (a load reads
+ * entry 0, a store is skipped) and is recorded, and topo_solve, topo_solve_host, topo_apply_K and
+ * topo_apply_vcycle then return TOPO_E_BOUNDS.  topo_bounds_check_enabled: 1 in that build, else
+ * 0.  topo_bounds_report (host pointers, each may be NULL): the number of indices found out of
+ * range since the last reset, the first one of them with the size it was checked against, its
+ * source file (NUL-terminated, at most file_len bytes) and line; reset = 1 clears the records.
+ * Synchronizes the device.  The release build reports 0.  topo_bounds_selftest (debug build; the
+ * release build returns TOPO_E_INVALID_ARG) evaluates one check of index i against size n in a
+ * kernel that addresses no buffer, so that a test can see a violation recorded. */
+int topo_bounds_check_enabled(void);
+topo_status topo_bounds_report(unsigned long long* count, long long* index, long long* size,
+                               char* file, int file_len, int* line, int reset);
+topo_status topo_bounds_selftest(long long i, long long n);
 
 #ifdef __cplusplus
 }

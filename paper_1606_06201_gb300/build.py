@@ -1,7 +1,9 @@
 """Build the CUDA library libtopo_gb300.so in-tree for sm_103a (nvcc, no cmake).
 
 Every translation unit is compiled in parallel to an object with -fPIC, then linked into one
-shared library next to this file.  ``python -m paper_1606_06201_gb300.build`` runs it.
+shared library next to this file.  ``python -m paper_1606_06201_gb300.build`` runs it;
+``--bounds-check`` builds the debug variant with index checks (-DTOPO_BOUNDS_CHECK) as
+libtopo_gb300_bc.so (load it by setting TOPO_LIBRARY to its path before importing the binding).
 """
 import concurrent.futures
 import os
@@ -12,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtopo_gb300.so")
+LIB_BC = os.path.join(HERE, "libtopo_gb300_bc.so")
 SOURCES = ["kernels_fe.cu", "kernels_q1.cu", "kernels_q1w.cu", "kernels_hex.cu", "kernels_rap.cu", "kernels_pcg.cu",
            "kernels_ip.cu",
            "solver.cu", "ipoc.cu", "static_scratch.cu",
@@ -24,8 +27,8 @@ def nvcc():
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def _compile(src, extra):
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+def _compile(src, extra, build_dir=BUILD):
+    obj = os.path.join(build_dir, os.path.splitext(src)[0] + ".o")
     path = os.path.join(CSRC, src)
     if src.endswith(".cu"):
         cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -38,22 +41,25 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
-def build(verbose=False, extra=()):
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose=False, extra=(), bounds_check=False):
+    build_dir, lib = (BUILD + "_bc", LIB_BC) if bounds_check else (BUILD, LIB)
+    extra = list(extra) + (["-DTOPO_BOUNDS_CHECK"] if bounds_check else [])
+    os.makedirs(build_dir, exist_ok=True)
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(lambda s: _compile(s, list(extra)), SOURCES))
+        results = list(ex.map(lambda s: _compile(s, extra, build_dir), SOURCES))
     objs = [o for o, _ in results]
     if verbose:
         for _, err in results:
             if err.strip():
                 sys.stderr.write(err)
-    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", lib, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    extra = sys.argv[1:]
-    print(build(verbose=True, extra=extra))
+    args = sys.argv[1:]
+    bc = "--bounds-check" in args
+    print(build(verbose=True, extra=[a for a in args if a != "--bounds-check"], bounds_check=bc))

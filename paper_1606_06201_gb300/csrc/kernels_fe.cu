@@ -85,7 +85,7 @@ __device__ __forceinline__ void node_apply(const Dims& d, int i, int j, int k,
       const int ex = i - 1 + dx, ey = j - 1 + dy;
       ok[s] = ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny;
       const int loc = loc_of(1 - dx, 1 - dy, 0);
-      const long long e = ok[s] ? ex + (long long)d.nx * ey : 0;
+      const long long e = ok[s] ? TOPO_IDX(ex + (long long)d.nx * ey, m) : 0;
 #pragma unroll
       for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -93,7 +93,8 @@ __device__ __forceinline__ void node_apply(const Dims& d, int i, int j, int k,
           a[s][c * 8 + q] = ldg(Ae + (long long)((loc * 2 + c) * 8 + q) * m + e);
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        const long long nid = ok[s] ? (ex + loc_ox(b)) + (long long)nnx * (ey + loc_oy(b)) : 0;
+        const long long nid =
+            ok[s] ? TOPO_IDX((ex + loc_ox(b)) + (long long)nnx * (ey + loc_oy(b)), d.nodes()) : 0;
         ve[s][2 * b] = vin(2 * nid);
         ve[s][2 * b + 1] = vin(2 * nid + 1);
       }
@@ -118,11 +119,13 @@ __device__ __forceinline__ void node_apply(const Dims& d, int i, int j, int k,
     if (DIM == 3 && (ez < 0 || ez >= d.nz)) continue;
     const int loc = loc_of(1 - dx, 1 - dy, DIM == 3 ? 1 - dz : 0);
     const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
+    if (!TOPO_IN(e, m)) continue;
     T ve[NE];
 #pragma unroll
     for (int a = 0; a < NN; ++a) {
-      const long long nid = (ex + loc_ox(a)) + (long long)nnx * ((ey + loc_oy(a)) +
-                                                                 (long long)nny * (ez + loc_oz(a)));
+      const long long nid = TOPO_IDX((ex + loc_ox(a)) + (long long)nnx * ((ey + loc_oy(a)) +
+                                                                          (long long)nny * (ez + loc_oz(a))),
+                                     d.nodes());
 #pragma unroll
       for (int c = 0; c < DIM; ++c) ve[a * DIM + c] = vin(DIM * nid + c);
     }
@@ -171,6 +174,7 @@ __device__ __forceinline__ void apply_node(const Dims& d, long long node, const 
 #pragma unroll
   for (int c = 0; c < DIM; ++c) {
     const long long id = DIM * node + c;
+    if (!TOPO_IN(id, n)) continue;
     T out;
     if (fixed[id]) {
       out = T(0);
@@ -373,6 +377,7 @@ __global__ void __launch_bounds__(kApply3Threads) k_apply3_rhs(
       if (ex < 0 || ex >= d.nx || ey < 0 || ey >= d.ny || ez < 0 || ez >= d.nz) continue;
       const int loc = loc_of(1 - dx, 1 - dy, 1 - dz);
       const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
+      if (!TOPO_IN(e, m)) continue;
       T row[3][NE];
 #pragma unroll
       for (int c = 0; c < 3; ++c)
@@ -384,7 +389,9 @@ __global__ void __launch_bounds__(kApply3Threads) k_apply3_rhs(
       long long nid[8];
 #pragma unroll
       for (int a = 0; a < 8; ++a)
-        nid[a] = (ex + loc_ox(a)) + (long long)nnx * ((ey + loc_oy(a)) + (long long)nny * (ez + loc_oz(a)));
+        nid[a] = TOPO_IDX((ex + loc_ox(a)) + (long long)nnx * ((ey + loc_oy(a)) +
+                                                               (long long)nny * (ez + loc_oz(a))),
+                          nodes);
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         if (!live[r]) continue;
@@ -412,6 +419,7 @@ __global__ void __launch_bounds__(kApply3Threads) k_apply3_rhs(
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long long id = 3 * node + c;
+      if (!TOPO_IN(id, n)) continue;
       T out;
       if (fixed[id]) out = T(0);
       else if (MODE == 0) out = acc[r][c];
@@ -612,7 +620,8 @@ __device__ __forceinline__ void restrict_node(const Dims& df, const Dims& dc, lo
         const int fi = 2 * I + ox;
         if (fi < 0 || fi > df.nx) continue;
         const T w = (ox == 0) ? wy : wy * T(0.5);
-        const long long fid = fi + (long long)fnx * (fj + (long long)fny * (DIM == 3 ? fk : 0));
+        const long long fid = TOPO_IDX(fi + (long long)fnx * (fj + (long long)fny * (DIM == 3 ? fk : 0)),
+                                       df.nodes());
 #pragma unroll
         for (int c = 0; c < DIM; ++c) acc[c] = fma(w, vld<COH>(rf + DIM * fid + c), acc[c]);
       }
@@ -621,7 +630,7 @@ __device__ __forceinline__ void restrict_node(const Dims& df, const Dims& dc, lo
 #pragma unroll
   for (int c = 0; c < DIM; ++c) {
     const long long id = DIM * node + c;
-    rc[id] = fixed_c[id] ? T(0) : acc[c];
+    if (TOPO_IN(id, dc.dofs())) rc[id] = fixed_c[id] ? T(0) : acc[c];
   }
 }
 
@@ -668,7 +677,8 @@ __device__ __forceinline__ void prolong_node(const Dims& df, const Dims& dc, lon
       for (int cq = 0; cq < nxi; ++cq) {
         const int I = cq ? i1 : i0;
         const T w = wxh * wyh * wzh;
-        const long long cid = I + (long long)cnx * (J + (long long)cny * (DIM == 3 ? K : 0));
+        const long long cid = TOPO_IDX(I + (long long)cnx * (J + (long long)cny * (DIM == 3 ? K : 0)),
+                                       dc.nodes());
 #pragma unroll
         for (int c = 0; c < DIM; ++c) acc[c] = fma(w, vld<COH>(zc + DIM * cid + c), acc[c]);
       }
@@ -677,7 +687,7 @@ __device__ __forceinline__ void prolong_node(const Dims& df, const Dims& dc, lon
 #pragma unroll
   for (int c = 0; c < DIM; ++c) {
     const long long id = DIM * node + c;
-    if (!fixed_f[id]) zf[id] = (COH ? __ldcg(zf + id) : zf[id]) + acc[c];
+    if (TOPO_IN(id, df.dofs()) && !fixed_f[id]) zf[id] = (COH ? __ldcg(zf + id) : zf[id]) + acc[c];
   }
 }
 
@@ -850,15 +860,18 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned
       ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
-// Waits for phase 0 of the barrier for at most kBulkWaitNs of the global timer (each poll may
-// suspend the thread for up to 1 us); false if it gave up.
+// Waits for phase 0 of the barrier for at most limit_ns of the global timer (each poll may
+// suspend the thread for up to 1 us); false if it gave up.  limit_ns = 0 gives up at once without
+// polling (topo_set_wait_limit_ns: the timeout path made to run, for tests).
 constexpr unsigned long long kBulkWaitNs = 1000000000ull;
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-__device__ __forceinline__ bool mbar_wait0(unsigned bar) {
+__device__ __forceinline__ bool mbar_wait0(unsigned bar,
+                                           unsigned long long limit_ns = kBulkWaitNs) {
+  if (limit_ns == 0) return false;
   const unsigned long long t0 = global_ns();
   for (;;) {
     unsigned ok;
@@ -869,7 +882,7 @@ __device__ __forceinline__ bool mbar_wait0(unsigned bar) {
         : "r"(bar)
         : "memory");
     if (ok) return true;
-    if (global_ns() - t0 > kBulkWaitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
 }
 
@@ -1023,11 +1036,11 @@ __global__ void __launch_bounds__(tail1_threads<T>(), 1)
   }
   __syncthreads();  // (the barrier is initialised before anyone polls it)
   // every thread polls; the block decides together, so that all or none continue
-  if (!__syncthreads_and(mbar_wait0(bar) ? 1 : 0)) {
-    // the copies did not land in time: give them a second bounded wait before the block's shared
-    // memory is released, and stop this right-hand side's CG with a timeout
+  if (!__syncthreads_and(mbar_wait0(bar, A.wait_ns) ? 1 : 0)) {
+    // the copies did not land in time: give them a second bounded wait (the full bound) before
+    // the block's shared memory is released, and stop this right-hand side's CG with a timeout
     if (tid == 0) {
-      mbar_wait0(bar);
+      mbar_wait0(bar, kBulkWaitNs);
       if (sc) {
         CgScalars* w = const_cast<CgScalars*>(sc) + rhs;
         w->status = TOPO_E_TIMEOUT;

@@ -19,7 +19,9 @@
 // that a warp writes contiguous memory); one thread per node then sums the contributions of its
 // eight elements in a fixed order (deterministic, no atomics), masks fixed DOFs, and accumulates
 // p^T q with the last-block finalisation of the other CG kernels.
+#include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "pairs.cuh"
@@ -152,7 +154,8 @@ __global__ void __launch_bounds__(kThreads) k_hex_elem(Dims d, HexK<double> k,
     for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
-        const long long nid = (ex + i) + (long long)nnx * ((ey + j) + (long long)nny * (ez + kk));
+        const long long nid =
+            TOPO_IDX((ex + i) + (long long)nnx * ((ey + j) + (long long)nny * (ez + kk)), d.nodes());
         nu[kk][j][i] = __ldg(v + 3 * nid);
         nv[kk][j][i] = __ldg(v + 3 * nid + 1);
         nw[kk][j][i] = __ldg(v + 3 * nid + 2);
@@ -222,12 +225,14 @@ __global__ void __launch_bounds__(kThreads) k_hex_gather_dot(Dims d, const doubl
       const int lx = 1 - dx, ly = 1 - dy, lz = 1 - dz;
       const int loc = (ly ? (lx ? 2 : 3) : (lx ? 1 : 0)) + 4 * lz;
       const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
+      if (!TOPO_IN(e, m)) continue;
 #pragma unroll
       for (int c = 0; c < 3; ++c) acc[c] += __ldg(R + (long long)(loc * 3 + c) * m + e);
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long long id = 3 * node + c;
+      if (!TOPO_IN(id, n)) continue;
       const double out = fixed[id] ? 0.0 : acc[c];
       q[id] = out;
       part = fma(p[id], out, part);
@@ -291,7 +296,8 @@ __global__ void __launch_bounds__(kThreads) k_hex_elem_df(Dims d, HexK<PairNum> 
     for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
-        const long long nid = (ex + i) + (long long)nnx * ((ey + j) + (long long)nny * (ez + kk));
+        const long long nid =
+            TOPO_IDX((ex + i) + (long long)nnx * ((ey + j) + (long long)nny * (ez + kk)), d.nodes());
         nu[kk][j][i] = {df_from_double(__ldg(v + 3 * nid))};
         nv[kk][j][i] = {df_from_double(__ldg(v + 3 * nid + 1))};
         nw[kk][j][i] = {df_from_double(__ldg(v + 3 * nid + 2))};
@@ -343,6 +349,7 @@ __global__ void __launch_bounds__(kThreads) k_hex_gather_dot_df(Dims d, const fl
       const int lx = 1 - dx, ly = 1 - dy, lz = 1 - dz;
       const int loc = (ly ? (lx ? 2 : 3) : (lx ? 1 : 0)) + 4 * lz;
       const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
+      if (!TOPO_IN(e, m)) continue;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const float2 r = __ldg(R + (long long)(loc * 3 + c) * m + e);
@@ -352,6 +359,7 @@ __global__ void __launch_bounds__(kThreads) k_hex_gather_dot_df(Dims d, const fl
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long long id = 3 * node + c;
+      if (!TOPO_IN(id, n)) continue;
       if (fixed[id]) acc[c] = f2{0.0f, 0.0f};
       q[id] = double_from_float(acc[c].h) + double_from_float(acc[c].l);
       part = df_add(part, df_mul(df_from_double(p[id]), acc[c]));
@@ -382,6 +390,349 @@ __global__ void __launch_bounds__(kThreads) k_hex_gather_dot_df(Dims d, const fl
       S.alpha = alpha;
     }
     counters[rhs] = 0;
+  }
+}
+
+
+// ---- Tile formulation: element forces through shared memory --------------------------------
+// A block owns a tile of (TX - 1) x (TY - 1) node columns and a range of cz node planes.  Its TX x
+// TY threads compute the elements of the tile plus one element row and column of halo (thread
+// (tx, ty) the element whose lower-left-front node is its node), one element layer at a time,
+// and write the 24 element forces to shared memory; after a barrier every thread with a node
+// in its tile adds the forces of the four elements of that layer around the node.  Marching up
+// the planes, a node plane is complete after the element layers below and above it: its forces
+// are added in the order of k_hex_gather_dot (layer below, then layer above; x fastest), so q
+// has the bits of the buffered form, without the 24 forces per element and right-hand side in
+// global memory (192 bytes written and read again per element in FP64).  The halo elements are
+// computed twice (in both tiles): the planner below picks the tile that minimises the element
+// work with enough blocks.  Two force buffers alternate, so one barrier per layer suffices.
+struct HexTile {
+  int tx, ty, cz;          // threads per row, rows, node planes per block
+  int tiles_x, tiles_y, zchunks;
+};
+
+__device__ __forceinline__ int tile_loc(int dx, int dy, int dz) {  // local node of the element
+  const int lx = 1 - dx, ly = 1 - dy, lz = 1 - dz;
+  return (ly ? (lx ? 2 : 3) : (lx ? 1 : 0)) + 4 * lz;
+}
+
+template <typename P>
+struct HexTileElem;  // the force type stored in shared memory and the density input
+template <>
+struct HexTileElem<double> {
+  using S = double;
+  __device__ static double from_v(double v) { return v; }
+  __device__ static double x_of(const void* x, long long e) {
+    return __ldg(static_cast<const double*>(x) + e);
+  }
+  __device__ static S store(double a) { return a; }
+  __device__ static double load(S a) { return a; }
+};
+template <>
+struct HexTileElem<PairNum> {
+  using S = float2;
+  __device__ static PairNum from_v(double v) { return {df_from_double(v)}; }
+  __device__ static PairNum x_of(const void* x, long long e) {
+    const float2 v = __ldg(static_cast<const float2*>(x) + e);
+    return {{v.x, v.y}};
+  }
+  __device__ static S store(PairNum a) { return make_float2(a.v.h, a.v.l); }
+  __device__ static f2 load(S a) { return {a.x, a.y}; }
+};
+
+// Outer operator q = K(x) p (FP64 or float pairs), p^T q per block and alpha by the last block.
+template <typename P>
+__global__ void __launch_bounds__(512) k_hex_tile_outer(Dims d, HexTile tl, HexK<P> k,
+                                                        const void* __restrict__ xin,
+                                                        const double* __restrict__ v,
+                                                        double* __restrict__ q,
+                                                        const uint8_t* __restrict__ fixed,
+                                                        double* partials, unsigned* counters,
+                                                        CgScalars* sc) {
+  using E = HexTileElem<P>;
+  using S = typename E::S;
+  pdl_prologue();
+  const int rhs = blockIdx.z;
+  if (sc[rhs].done) return;
+  extern __shared__ float4 hex_tile_raw[];
+  S* F = reinterpret_cast<S*>(hex_tile_raw);  // [2][24][TT]
+  const int TT = tl.tx * tl.ty;
+  const int t = threadIdx.x, tx = t % tl.tx, ty = t / tl.tx;
+  const int bx = blockIdx.x % tl.tiles_x, by = blockIdx.x / tl.tiles_x;
+  const int ex = bx * (tl.tx - 1) - 1 + tx, ey = by * (tl.ty - 1) - 1 + ty;
+  const int nnx = d.nx + 1, nny = d.ny + 1, nnz = d.nz + 1;
+  const int k0 = blockIdx.y * tl.cz, k1 = min(k0 + tl.cz, nnz);
+  const long long m = d.elems(), nodes = d.nodes(), n = nodes * 3;
+  v += rhs * n;
+  q += rhs * n;
+  const bool e_xy = ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny;
+  // the node of this thread: (ex, ey), when the four elements around it are in the tile
+  const bool own = tx >= 1 && ty >= 1 && ex < nnx && ey < nny;
+  using Acc = decltype(E::load(S()));
+  Acc acc[3];
+  double part_d = 0.0;
+  f2 part_f = {0.0f, 0.0f};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) acc[c] = Acc{};
+#pragma unroll 1
+  for (int ez = k0 - 1; ez < k1; ++ez) {
+    S* Fb = F + (size_t)((ez - k0 + 1) & 1) * 24 * TT;
+    if (e_xy && ez >= 0 && ez < d.nz) {
+      P nu[2][2][2], nv[2][2][2], nw[2][2][2];
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            const long long nid =
+            TOPO_IDX((ex + i) + (long long)nnx * ((ey + j) + (long long)nny * (ez + kk)), d.nodes());
+            nu[kk][j][i] = E::from_v(__ldg(v + 3 * nid));
+            nv[kk][j][i] = E::from_v(__ldg(v + 3 * nid + 1));
+            nw[kk][j][i] = E::from_v(__ldg(v + 3 * nid + 2));
+          }
+      P tu[7], tv[7], tw[7];
+      wht_fwd(nu, tu);
+      wht_fwd(nv, tv);
+      wht_fwd(nw, tw);
+      const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
+      hex_khat(k, E::x_of(xin, e), tu, tv, tw);
+      wht_inv(tu, nu);
+      wht_inv(tv, nv);
+      wht_inv(tw, nw);
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int i = hx_ox(a), j = hx_oy(a), kk = hx_oz(a);
+        Fb[(a * 3 + 0) * TT + t] = E::store(nu[kk][j][i]);
+        Fb[(a * 3 + 1) * TT + t] = E::store(nv[kk][j][i]);
+        Fb[(a * 3 + 2) * TT + t] = E::store(nw[kk][j][i]);
+      }
+    }
+    __syncthreads();
+    if (own) {
+      const bool lay = ez >= 0 && ez < d.nz;
+      // plane ez: the forces of layer ez (above it) complete its sums
+      if (ez >= k0) {
+        if (lay) {
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            const int dx = s & 1, dy = s >> 1;
+            const int gx = ex - 1 + dx, gy = ey - 1 + dy;
+            if (gx < 0 || gx >= d.nx || gy < 0 || gy >= d.ny) continue;
+            const int te = TOPO_IDX(t - (1 - dx) - (1 - dy) * tl.tx, TT);
+            const int loc = tile_loc(dx, dy, 1);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              if constexpr (std::is_same<P, double>::value) acc[c] += Fb[(loc * 3 + c) * TT + te];
+              else acc[c] = df_add(acc[c], E::load(Fb[(loc * 3 + c) * TT + te]));
+            }
+          }
+        }
+        const long long node = ex + (long long)nnx * (ey + (long long)nny * ez);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const long long id = 3 * node + c;
+          if (!TOPO_IN(id, n)) continue;
+          if constexpr (std::is_same<P, double>::value) {
+            const double out = fixed[id] ? 0.0 : acc[c];
+            q[id] = out;
+            part_d = fma(v[id], out, part_d);
+          } else {
+            if (fixed[id]) acc[c] = f2{0.0f, 0.0f};
+            q[id] = double_from_float(acc[c].h) + double_from_float(acc[c].l);
+            part_f = df_add(part_f, df_mul(df_from_double(v[id]), acc[c]));
+          }
+        }
+      }
+      // plane ez + 1: starts with the forces of layer ez (below it)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[c] = Acc{};
+      if (lay && ez + 1 < k1) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int dx = s & 1, dy = s >> 1;
+          const int gx = ex - 1 + dx, gy = ey - 1 + dy;
+          if (gx < 0 || gx >= d.nx || gy < 0 || gy >= d.ny) continue;
+          const int te = TOPO_IDX(t - (1 - dx) - (1 - dy) * tl.tx, TT);
+          const int loc = tile_loc(dx, dy, 0);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            if constexpr (std::is_same<P, double>::value) acc[c] += Fb[(loc * 3 + c) * TT + te];
+            else acc[c] = df_add(acc[c], E::load(Fb[(loc * 3 + c) * TT + te]));
+          }
+        }
+      }
+    }
+  }
+  double part;
+  if constexpr (std::is_same<P, double>::value) part = part_d;
+  else part = double_from_float(part_f.h) + double_from_float(part_f.l);
+  const double bs = block_sum_hex(part);
+  const unsigned nb = gridDim.x * gridDim.y, bid = blockIdx.x + gridDim.x * blockIdx.y;
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[(long long)rhs * nb + bid] = bs;
+    __threadfence();
+    last = (atomicAdd(&counters[rhs], 1u) == nb - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  double s = 0.0;
+  for (unsigned u = threadIdx.x; u < nb; u += blockDim.x) s += __ldcg(partials + (long long)rhs * nb + u);
+  s = block_sum_hex(s);
+  if (threadIdx.x == 0) {
+    CgScalars& Sc = sc[rhs];
+    Sc.pq = s;
+    const double alpha = Sc.ry / s;
+    if (!(s > 0.0) || !isfinite(alpha)) {
+      Sc.status = TOPO_E_BREAKDOWN;
+      Sc.done = 1;
+      Sc.alpha = 0.0;
+    } else {
+      Sc.alpha = alpha;
+    }
+    counters[rhs] = 0;
+  }
+  (void)m;
+}
+
+// V-cycle operator on the finest level: mode 0 y = A v, 1 y = b - A v, 2 y = v + omega invd
+// (b - A v).  DENSE: the element rows of K0 (shared memory) times the element's 24 values as
+// FMA chains, and the node adds x_e t with one FMA per element: the arithmetic, and its order,
+// of the node-parallel k_apply3_rhs, so the same bits.  Otherwise the Walsh-Hadamard form of
+// the element (about 180 operations instead of 576 multiply-adds) with x_e in the coefficients
+// and plain adds at the node (other roundings, the same operator).
+template <typename T, int MODE, bool DENSE>
+__global__ void __launch_bounds__(512) k_hex_tile_sweep(Dims d, HexTile tl, HexK<T> k,
+                                                        const T* __restrict__ K0,
+                                                        const T* __restrict__ x,
+                                                        const T* __restrict__ v,
+                                                        const T* __restrict__ b,
+                                                        T* __restrict__ y,
+                                                        const T* __restrict__ invd, T omega,
+                                                        const uint8_t* __restrict__ fixed,
+                                                        const CgScalars* __restrict__ sc) {
+  pdl_prologue();
+  const int rhs = blockIdx.z;
+  if (sc && sc[rhs].done) return;
+  extern __shared__ float4 hex_tile_raw[];
+  const int TT = tl.tx * tl.ty;
+  T* F = reinterpret_cast<T*>(hex_tile_raw);  // [2][24][TT]
+  T* X = F + 2 * 24 * TT;                      // [2][TT] (DENSE)
+  T* K0s = X + 2 * TT;                         // [576]  (DENSE)
+  if (DENSE) {
+    for (int u = threadIdx.x; u < 576; u += blockDim.x) K0s[u] = K0[u];
+    __syncthreads();
+  }
+  const int t = threadIdx.x, tx = t % tl.tx, ty = t / tl.tx;
+  const int bx = blockIdx.x % tl.tiles_x, by = blockIdx.x / tl.tiles_x;
+  const int ex = bx * (tl.tx - 1) - 1 + tx, ey = by * (tl.ty - 1) - 1 + ty;
+  const int nnx = d.nx + 1, nny = d.ny + 1, nnz = d.nz + 1;
+  const int k0 = blockIdx.y * tl.cz, k1 = min(k0 + tl.cz, nnz);
+  const long long n = d.nodes() * 3;
+  v += rhs * n;
+  y += rhs * n;
+  if (MODE != 0) b += rhs * n;
+  const bool e_xy = ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny;
+  const bool own = tx >= 1 && ty >= 1 && ex < nnx && ey < nny;
+  T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll 1
+  for (int ez = k0 - 1; ez < k1; ++ez) {
+    const int buf = (ez - k0 + 1) & 1;
+    T* Fb = F + (size_t)buf * 24 * TT;
+    if (e_xy && ez >= 0 && ez < d.nz) {
+      const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
+      if (DENSE) {
+        T ve[24];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          const long long nid = TOPO_IDX(
+              (ex + hx_ox(a)) + (long long)nnx * ((ey + hx_oy(a)) + (long long)nny * (ez + hx_oz(a))),
+              d.nodes());
+#pragma unroll
+          for (int c = 0; c < 3; ++c) ve[a * 3 + c] = __ldg(v + 3 * nid + c);
+        }
+#pragma unroll 4
+        for (int r = 0; r < 24; ++r) {
+          T s = T(0);
+#pragma unroll
+          for (int qq = 0; qq < 24; ++qq) s = fma(K0s[r * 24 + qq], ve[qq], s);
+          Fb[r * TT + t] = s;
+        }
+        X[buf * TT + t] = __ldg(x + e);
+      } else {
+        T nu[2][2][2], nv[2][2][2], nw[2][2][2];
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+          for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+              const long long nid =
+            TOPO_IDX((ex + i) + (long long)nnx * ((ey + j) + (long long)nny * (ez + kk)), d.nodes());
+              nu[kk][j][i] = __ldg(v + 3 * nid);
+              nv[kk][j][i] = __ldg(v + 3 * nid + 1);
+              nw[kk][j][i] = __ldg(v + 3 * nid + 2);
+            }
+        T tu[7], tv[7], tw[7];
+        wht_fwd(nu, tu);
+        wht_fwd(nv, tv);
+        wht_fwd(nw, tw);
+        hex_khat(k, __ldg(x + e), tu, tv, tw);
+        wht_inv(tu, nu);
+        wht_inv(tv, nv);
+        wht_inv(tw, nw);
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          const int i = hx_ox(a), j = hx_oy(a), kk = hx_oz(a);
+          Fb[(a * 3 + 0) * TT + t] = nu[kk][j][i];
+          Fb[(a * 3 + 1) * TT + t] = nv[kk][j][i];
+          Fb[(a * 3 + 2) * TT + t] = nw[kk][j][i];
+        }
+      }
+    }
+    __syncthreads();
+    if (own) {
+      const bool lay = ez >= 0 && ez < d.nz;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        // half 0: layer ez completes plane ez (dz = 1); half 1: it starts plane ez + 1 (dz = 0)
+        const int dz = 1 - half;
+        if (half == 0 && ez < k0) continue;
+        if (half == 1 && ez + 1 >= k1) continue;
+        if (lay) {
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            const int dx = s & 1, dy = s >> 1;
+            const int gx = ex - 1 + dx, gy = ey - 1 + dy;
+            if (gx < 0 || gx >= d.nx || gy < 0 || gy >= d.ny) continue;
+            const int te = TOPO_IDX(t - (1 - dx) - (1 - dy) * tl.tx, TT);
+            const int loc = tile_loc(dx, dy, dz);
+            const T xe = DENSE ? X[buf * TT + te] : T(0);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const T f = Fb[(loc * 3 + c) * TT + te];
+              acc[c] = DENSE ? fma(xe, f, acc[c]) : acc[c] + f;
+            }
+          }
+        }
+        if (half == 0) {
+          const long long node = ex + (long long)nnx * (ey + (long long)nny * ez);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const long long id = 3 * node + c;
+            if (!TOPO_IN(id, n)) continue;
+            T out;
+            if (fixed[id]) out = T(0);
+            else if (MODE == 0) out = acc[c];
+            else if (MODE == 1) out = node_out<1, T>(acc[c], T(0), __ldg(b + id), T(0), omega);
+            else out = node_out<2, T>(acc[c], __ldg(v + id), __ldg(b + id), invd[id], omega);
+            y[id] = out;
+            acc[c] = T(0);
+          }
+        }
+      }
+    }
   }
 }
 
@@ -494,5 +845,124 @@ cudaError_t launch_hex_apply_dot_df(const Dims& d, const HexCoef& c, const float
                (const float2*)Rp, v, y, fixed, partials, counters, sc);
   return cudaGetLastError();
 }
+
+
+// Tile plan: the (TX, TY) with at most max_threads threads (a multiple of 32) and the number of
+// z chunks that minimise the element work (halo included) with at least `target` blocks.
+HexTile hex_tile_plan(const Dims& d, int nrhs, int max_threads, int target) {
+  HexTile best = {};
+  double best_work = 0.0;
+  const int nnx = d.nx + 1, nny = d.ny + 1, nnz = d.nz + 1;
+  for (int ty = 2; ty <= 32; ++ty)
+    for (int tx = 4; tx <= 128; ++tx) {
+      const int th = tx * ty;
+      if (th % 32 || th > max_threads || th < 64) continue;
+      const int tiles_x = (nnx + tx - 2) / (tx - 1), tiles_y = (nny + ty - 2) / (ty - 1);
+      const long long tiles = (long long)tiles_x * tiles_y;
+      if (tiles > 65535) continue;
+      long long zc = (target + tiles * nrhs - 1) / (tiles * nrhs);
+      zc = std::max(1LL, std::min<long long>(zc, nnz));
+      const int cz = (int)((nnz + zc - 1) / zc);
+      zc = (nnz + cz - 1) / cz;
+      if (tiles * zc > (long long)kMaxRedValues * kRedBlocks) continue;
+      const double work = (double)tiles * th * (double)zc * (cz + 1);
+      if (best.tx == 0 || work < best_work * 0.999 ||
+          (work <= best_work * 1.001 && th > best.tx * best.ty)) {
+        best = {tx, ty, cz, tiles_x, tiles_y, (int)zc};
+        best_work = work;
+      }
+    }
+  return best;
+}
+
+template <typename K>
+static cudaError_t hex_tile_smem(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+constexpr int kHexTileOuterThreads = 256;  // (the pair element product keeps ~130 registers)
+constexpr int kHexTileSweepThreads = 512;
+
+cudaError_t prepare_hex_tile_kernels() {
+  cudaError_t e = hex_tile_smem(k_hex_tile_outer<double>, 2 * 24 * kHexTileOuterThreads * 8);
+  if (e == cudaSuccess) e = hex_tile_smem(k_hex_tile_outer<PairNum>, 2 * 24 * kHexTileOuterThreads * 8);
+#define TOPO_HT_PREP(T, MODE)                                                                      \
+  if (e == cudaSuccess)                                                                            \
+    e = hex_tile_smem(k_hex_tile_sweep<T, MODE, true>,                                             \
+                      (2 * 24 * kHexTileSweepThreads + 2 * kHexTileSweepThreads + 576) * sizeof(T)); \
+  if (e == cudaSuccess)                                                                            \
+    e = hex_tile_smem(k_hex_tile_sweep<T, MODE, false>,                                            \
+                      (2 * 24 * kHexTileSweepThreads + 2 * kHexTileSweepThreads + 576) * sizeof(T));
+  TOPO_HT_PREP(float, 0)
+  TOPO_HT_PREP(float, 1)
+  TOPO_HT_PREP(float, 2)
+  TOPO_HT_PREP(double, 0)
+  TOPO_HT_PREP(double, 1)
+  TOPO_HT_PREP(double, 2)
+#undef TOPO_HT_PREP
+  return e;
+}
+
+cudaError_t launch_hex_tile_apply_dot(const Dims& d, const HexCoef& c, const void* x, bool pairs,
+                                      const double* v, double* y, const uint8_t* fixed, int nrhs,
+                                      double* partials, unsigned* counters, CgScalars* sc,
+                                      cudaStream_t st) {
+  const HexTile tl = hex_tile_plan(d, nrhs, kHexTileOuterThreads, 152 * 6);
+  if (tl.tx == 0) return cudaErrorInvalidConfiguration;
+  const dim3 grid(tl.tiles_x * tl.tiles_y, tl.zchunks, nrhs);
+  const size_t smem = (size_t)2 * 24 * tl.tx * tl.ty * 8;
+  if (pairs) {
+    const HexK<PairNum> k{{df_const(c.a)}, {df_const(c.b)}, {df_const(c.s)}, {df_const(c.p)},
+                          {df_const(c.q)}, {df_const(c.d)}, {df_const(c.e)}, {df_const(c.h)}};
+    topo::launch(k_hex_tile_outer<PairNum>, grid, tl.tx * tl.ty, smem, st, d, tl, k, x, v, y,
+                 fixed, partials, counters, sc);
+  } else {
+    const HexK<double> k{c.a, c.b, c.s, c.p, c.q, c.d, c.e, c.h};
+    topo::launch(k_hex_tile_outer<double>, grid, tl.tx * tl.ty, smem, st, d, tl, k, x, v, y,
+                 fixed, partials, counters, sc);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_hex_tile_sweep(const Dims& d, int mode, bool dense, const HexCoef& c,
+                                  const T* K0, const T* x, const T* v, const T* b, T* y,
+                                  const T* invd, T omega, const uint8_t* fixed, int nrhs,
+                                  const CgScalars* sc, cudaStream_t st) {
+  const int maxt = sizeof(T) == 8 ? 256 : kHexTileSweepThreads;
+  const HexTile tl = hex_tile_plan(d, nrhs, maxt, 152 * 4);
+  if (tl.tx == 0) return cudaErrorInvalidConfiguration;
+  const dim3 grid(tl.tiles_x * tl.tiles_y, tl.zchunks, nrhs);
+  const int TT = tl.tx * tl.ty;
+  const size_t smem = (size_t)(2 * 24 * TT + (dense ? 2 * TT + 576 : 0)) * sizeof(T);
+  const HexK<T> k{(T)c.a, (T)c.b, (T)c.s, (T)c.p, (T)c.q, (T)c.d, (T)c.e, (T)c.h};
+#define TOPO_HT(MODE, DENSE)                                                                     \
+  topo::launch(k_hex_tile_sweep<T, MODE, DENSE>, grid, TT, smem, st, d, tl, k, K0, x, v, b, y, \
+               invd, omega, fixed, sc)
+  if (dense) {
+    if (mode == 0) TOPO_HT(0, true);
+    else if (mode == 1) TOPO_HT(1, true);
+    else if (mode == 2) TOPO_HT(2, true);
+    else return cudaErrorInvalidValue;
+  } else {
+    if (mode == 0) TOPO_HT(0, false);
+    else if (mode == 1) TOPO_HT(1, false);
+    else if (mode == 2) TOPO_HT(2, false);
+    else return cudaErrorInvalidValue;
+  }
+#undef TOPO_HT
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_hex_tile_sweep<float>(const Dims&, int, bool, const HexCoef&,
+                                                  const float*, const float*, const float*,
+                                                  const float*, float*, const float*, float,
+                                                  const uint8_t*, int, const CgScalars*,
+                                                  cudaStream_t);
+template cudaError_t launch_hex_tile_sweep<double>(const Dims&, int, bool, const HexCoef&,
+                                                   const double*, const double*, const double*,
+                                                   const double*, double*, const double*, double,
+                                                   const uint8_t*, int, const CgScalars*,
+                                                   cudaStream_t);
 
 }  // namespace topo

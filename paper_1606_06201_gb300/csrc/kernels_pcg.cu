@@ -7,6 +7,7 @@
 // and updates the device-resident scalars of its right-hand side.  Kernels return at once for a
 // right-hand side whose recurrence has stopped, which lets a captured graph of several
 // iterations run past convergence at the cost of empty launches.
+#include "pairs.cuh"
 #include "topo_internal.cuh"
 
 namespace topo {
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_init_zero(long long n, long lon
     const double ri = -bi;
     z[i] = 0.0;
     r[i] = ri;
-    if (rv) rv[i] = (TV)ri;
+    if (rv) rv[i] = tv_from_double<TV>(ri);
     part[0] = fma(bi, bi, part[0]);
     part[1] = fma(ri, ri, part[1]);
   }
@@ -191,9 +192,9 @@ __global__ void __launch_bounds__(kThreads) k_cg_start_p(long long n, const doub
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const TV yi = y[i];
-    p[i] = -(double)yi;
+    p[i] = -double_of(yi);
     if (flexible) y_old[i] = yi;
-    part[0] = fma(r[i], (double)yi, part[0]);
+    part[0] = fma(r[i], double_of(yi), part[0]);
   }
   double tot[1];
   if (!last_block_sums<1>(part, partials, counters, rhs, tot)) return;
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_start_p(long long n, const doub
 template <typename TV>
 // (z += alpha p of this iteration is applied by k_cg_p, which reads p anyway, or by
 // k_cg_finish_z when the iteration ends the solve.)
-__global__ void __launch_bounds__(kThreads) k_cg_update(long long n, double* __restrict__ z,
+__global__ void __launch_bounds__(kThreads, 4) k_cg_update(long long n, double* __restrict__ z,
                                                         double* __restrict__ r,
                                                         const double* __restrict__ p,
                                                         const double* __restrict__ q,
@@ -232,27 +233,36 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(long long n, double* __r
   if ((n & 1) == 0 && al16(r) && al16(q) && (!rv || al_pair(rv))) {
     using V2 = typename Pair2<TV>::type;
     const long long np = n >> 1;
-    double2* r2 = reinterpret_cast<double2*>(r);
-    const double2* q2 = reinterpret_cast<const double2*>(q);
-    V2* rv2 = reinterpret_cast<V2*>(rv);
-    for (long long j = t0; j < np; j += nt) {
-      const double2 qa = q2[j], ra = r2[j];
-      const double2 sa = make_double2(fma(alpha, qa.x, ra.x), fma(alpha, qa.y, ra.y));
+    double2* __restrict__ r2 = reinterpret_cast<double2*>(r);
+    const double2* __restrict__ q2 = reinterpret_cast<const double2*>(q);
+    V2* __restrict__ rv2 = reinterpret_cast<V2*>(rv);
+    auto put = [&](int j, double2 sa) {
       r2[j] = sa;
       if (rv) {
         V2 va;
-        va.x = (TV)sa.x;
-        va.y = (TV)sa.y;
+        va.x = tv_from_double<TV>(sa.x);
+        va.y = tv_from_double<TV>(sa.y);
         rv2[j] = va;
       }
       part[0] = fma(sa.x, sa.x, part[0]);
       part[0] = fma(sa.y, sa.y, part[0]);
+    };
+    const int npi = (int)np, nti = (int)nt;  // (fewer than 2^31 entries)
+    int j = (int)t0;
+    for (; j + nti < npi; j += 2 * nti) {  // both pairs' loads before either store
+      const double2 qa = q2[j], ra = r2[j], qb = q2[j + nti], rb = r2[j + nti];
+      put(j, make_double2(fma(alpha, qa.x, ra.x), fma(alpha, qa.y, ra.y)));
+      put(j + nti, make_double2(fma(alpha, qb.x, rb.x), fma(alpha, qb.y, rb.y)));
+    }
+    if (j < npi) {
+      const double2 qa = q2[j], ra = r2[j];
+      put(j, make_double2(fma(alpha, qa.x, ra.x), fma(alpha, qa.y, ra.y)));
     }
   } else {
     for (long long i = t0; i < n; i += nt) {
       const double ri = fma(alpha, q[i], r[i]);
       r[i] = ri;
-      if (rv) rv[i] = (TV)ri;
+      if (rv) rv[i] = tv_from_double<TV>(ri);
       part[0] = fma(ri, ri, part[0]);
     }
   }
@@ -294,25 +304,25 @@ __global__ void __launch_bounds__(kThreads) k_cg_beta(long long n, const double*
   if ((n & 1) == 0 && al16(r) && al_pair(y) && (!flexible || al_pair(y_old))) {
     using V2 = typename Pair2<TV>::type;
     const long long np = n >> 1;
-    const double2* r2 = reinterpret_cast<const double2*>(r);
-    const V2* y2 = reinterpret_cast<const V2*>(y);
-    const V2* yo2 = reinterpret_cast<const V2*>(y_old);
+    const double2* __restrict__ r2 = reinterpret_cast<const double2*>(r);
+    const V2* __restrict__ y2 = reinterpret_cast<const V2*>(y);
+    const V2* __restrict__ yo2 = reinterpret_cast<const V2*>(y_old);
     for (long long j = t0; j < np; j += nt) {
       const double2 rr = r2[j];
       const V2 yv = y2[j];
-      part[0] = fma(rr.x, (double)yv.x, part[0]);
-      part[0] = fma(rr.y, (double)yv.y, part[0]);
+      part[0] = fma(rr.x, double_of(yv.x), part[0]);
+      part[0] = fma(rr.y, double_of(yv.y), part[0]);
       if (flexible) {
         const V2 yo = yo2[j];
-        part[1] = fma(rr.x, (double)yo.x, part[1]);
-        part[1] = fma(rr.y, (double)yo.y, part[1]);
+        part[1] = fma(rr.x, double_of(yo.x), part[1]);
+        part[1] = fma(rr.y, double_of(yo.y), part[1]);
       }
     }
   } else {
     for (long long i = t0; i < n; i += nt) {
       const double ri = r[i];
-      part[0] = fma(ri, (double)y[i], part[0]);
-      if (flexible) part[1] = fma(ri, (double)y_old[i], part[1]);
+      part[0] = fma(ri, double_of(y[i]), part[0]);
+      if (flexible) part[1] = fma(ri, double_of(y_old[i]), part[1]);
     }
   }
   double tot[2];
@@ -333,6 +343,8 @@ __global__ void __launch_bounds__(kThreads) k_cg_beta(long long n, const double*
 }
 
 // z += alpha p (the iterate update of the iteration now ending), then p = -y + beta p, y_old = y.
+// (Scalar accesses: a version with 16-byte accesses, two pairs per iteration, measured 26.6 us
+// against 19.3 us at 4.2M DOFs.)
 template <typename TV>
 __global__ void __launch_bounds__(kThreads) k_cg_p(long long n, const TV* __restrict__ y,
                                                    double* __restrict__ p, TV* __restrict__ y_old,
@@ -346,30 +358,13 @@ __global__ void __launch_bounds__(kThreads) k_cg_p(long long n, const TV* __rest
   p += rhs * n;
   z += rhs * n;
   if (flexible) y_old += rhs * n;
-  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nt = (long long)gridDim.x * blockDim.x;
-  if ((n & 1) == 0 && al16(p) && al16(z) && al_pair(y) && (!flexible || al_pair(y_old))) {
-    using V2 = typename Pair2<TV>::type;
-    const long long np = n >> 1;
-    const V2* y2 = reinterpret_cast<const V2*>(y);
-    V2* yo2 = reinterpret_cast<V2*>(y_old);
-    double2* p2 = reinterpret_cast<double2*>(p);
-    double2* z2 = reinterpret_cast<double2*>(z);
-    for (long long j = t0; j < np; j += nt) {
-      const V2 yv = y2[j];
-      const double2 pv = p2[j], zv = z2[j];
-      z2[j] = make_double2(fma(alpha, pv.x, zv.x), fma(alpha, pv.y, zv.y));
-      p2[j] = make_double2(fma(beta, pv.x, -(double)yv.x), fma(beta, pv.y, -(double)yv.y));
-      if (flexible) yo2[j] = yv;
-    }
-  } else {
-    for (long long i = t0; i < n; i += nt) {
-      const TV yi = y[i];
-      const double pi = p[i];
-      z[i] = fma(alpha, pi, z[i]);
-      p[i] = fma(beta, pi, -(double)yi);
-      if (flexible) y_old[i] = yi;
-    }
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const TV yi = y[i];
+    const double pi = p[i];
+    z[i] = fma(alpha, pi, z[i]);
+    p[i] = fma(beta, pi, -double_of(yi));
+    if (flexible) y_old[i] = yi;
   }
 }
 
@@ -420,8 +415,8 @@ __global__ void __launch_bounds__(kThreads) k_cg_alpha(long long n, const double
   const long long nt = (long long)gridDim.x * blockDim.x;
   if ((n & 1) == 0 && al16(p) && al16(q)) {
     const long long np = n >> 1;
-    const double2* p2 = reinterpret_cast<const double2*>(p);
-    const double2* q2 = reinterpret_cast<const double2*>(q);
+    const double2* __restrict__ p2 = reinterpret_cast<const double2*>(p);
+    const double2* __restrict__ q2 = reinterpret_cast<const double2*>(q);
     for (long long j = t0; j < np; j += nt) {
       const double2 pa = p2[j], qa = q2[j];
       part[0] = fma(pa.x, qa.x, part[0]);
@@ -588,6 +583,23 @@ inline unsigned red_blocks(long long n) {
   return (unsigned)(b < kRedBlocks ? (b < 1 ? 1 : b) : kRedBlocks);
 }
 
+// Self-check of the integer conversions of pairs.cuh against the hardware conversions: counts
+// the inputs whose results differ (bad[0]: double -> float, bad[1]: float -> double; two NaNs
+// count as equal).
+__global__ void k_check_conversions(const double* __restrict__ d, const float* __restrict__ f,
+                                    long long n, unsigned long long* bad) {
+  unsigned long long b0 = 0, b1 = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float a = float_from_double_rn(d[i]), h = __double2float_rn(d[i]);
+    if (!((a != a && h != h) || __float_as_uint(a) == __float_as_uint(h))) ++b0;
+    const double c = double_from_float_exact(f[i]), e = (double)f[i];
+    if (!((c != c && e != e) || __double_as_longlong(c) == __double_as_longlong(e))) ++b1;
+  }
+  if (b0) atomicAdd(bad, b0);
+  if (b1) atomicAdd(bad + 1, b1);
+}
+
 }  // namespace
 
 cudaError_t launch_cg_init(long long n, int nrhs, const double* b, double* z, double* r,
@@ -746,5 +758,11 @@ cudaError_t launch_dot(long long n, int nrhs, const double* a, const double* b, 
 TOPO_INST(double)
 TOPO_INST(float)
 #undef TOPO_INST
+
+cudaError_t launch_check_conversions(const double* d, const float* f, long long n,
+                                     unsigned long long* bad, cudaStream_t st) {
+  topo::launch(k_check_conversions, dim3(kRedBlocks), kThreads, 0, st, d, f, n, bad);
+  return cudaGetLastError();
+}
 
 }  // namespace topo

@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, int 
     zero.x = T(0);
     zero.y = T(0);
     V2 pb = zero;
-    if (MODE != 3 && col_ok && j0 >= 1) pb = v2[c + rs * (j0 - 1)];
+    const long long NN = (long long)rs * (ny + 1), M = (long long)nx * ny;
+    if (MODE != 3 && col_ok && j0 >= 1) pb = v2[TOPO_IDX(c + rs * (j0 - 1), NN)];
     // Loads run two element rows ahead of their use (a strip is walked row by row, so one row of
     // lookahead leaves each row waiting for its own loads): *_n is used at the next iteration,
     // *_nn at the one after.  Element row e needs v of node row e + 1, x of element row e, and b,
@@ -78,13 +79,13 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, int 
     double2 rr_n = make_double2(0.0, 0.0), rr_nn = make_double2(0.0, 0.0);
     {
       const int ey = j0 - 1;  // first iteration: element row j0 - 1, no output
-      if (MODE != 3 && col_ok && ey + 1 <= ny) pt_n = v2[c + rs * (ey + 1)];
-      if (el_col && ey >= 0 && ey < ny) xe_n = x[c + nx * ey];
+      if (MODE != 3 && col_ok && ey + 1 <= ny) pt_n = v2[TOPO_IDX(c + rs * (ey + 1), NN)];
+      if (el_col && ey >= 0 && ey < ny) xe_n = x[TOPO_IDX(c + nx * ey, M)];
       if (ey + 1 < j1) {  // second iteration: element row j0, output node row j0
-        if (MODE != 3 && col_ok && ey + 2 <= ny) pt_nn = v2[c + rs * (ey + 2)];
-        if (el_col && ey + 1 < ny) xe_nn = x[c + nx * (ey + 1)];
+        if (MODE != 3 && col_ok && ey + 2 <= ny) pt_nn = v2[TOPO_IDX(c + rs * (ey + 2), NN)];
+        if (el_col && ey + 1 < ny) xe_nn = x[TOPO_IDX(c + nx * (ey + 1), M)];
         if (out_lane) {
-          const int nn = c + rs * (ey + 1);
+          const int nn = TOPO_IDX(c + rs * (ey + 1), NN);
           fx_nn = *reinterpret_cast<const uint16_t*>(fixed + 2 * nn);
           if (MODE != 0) bb_nn = b2[nn];
           if (DOT == 2) rr_nn = reinterpret_cast<const double2*>(rdot)[nn];
@@ -106,10 +107,10 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, int 
       pt_nn = zero;
       xe_nn = T(0);
       if (ey + 2 < j1) {  // loads of the iteration after next: element row ey + 2
-        if (MODE != 3 && col_ok && ey + 3 <= ny) pt_nn = v2[c + rs * (ey + 3)];
-        if (el_col && ey + 2 < ny) xe_nn = x[c + nx * (ey + 2)];
+        if (MODE != 3 && col_ok && ey + 3 <= ny) pt_nn = v2[TOPO_IDX(c + rs * (ey + 3), NN)];
+        if (el_col && ey + 2 < ny) xe_nn = x[TOPO_IDX(c + nx * (ey + 2), M)];
         if (out_lane) {
-          const int nn = c + rs * (ey + 2);
+          const int nn = TOPO_IDX(c + rs * (ey + 2), NN);
           fx_nn = *reinterpret_cast<const uint16_t*>(fixed + 2 * nn);
           if (MODE != 0) bb_nn = b2[nn];
           if (DOT == 2) rr_nn = reinterpret_cast<const double2*>(rdot)[nn];
@@ -153,9 +154,9 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep(int nx, int ny, int 
         }
         if (fx & 0xff) out.x = T(0);
         if (fx >> 8) out.y = T(0);
-        reinterpret_cast<V2*>(y)[node] = out;
-        if (DOT == 1) part = fma((double)pb.x, (double)out.x, fma((double)pb.y, (double)out.y, part));
-        if (DOT == 2) part = fma(rr.x, (double)out.x, fma(rr.y, (double)out.y, part));
+        if (TOPO_IN(node, NN)) reinterpret_cast<V2*>(y)[node] = out;
+        if (DOT == 1) part = fma(double_of(pb.x), double_of(out.x), fma(double_of(pb.y), double_of(out.y), part));
+        if (DOT == 2) part = fma(rr.x, double_of(out.x), fma(rr.y, double_of(out.y), part));
       }
       cu = ru[3] + l2u;
       cv = rv[3] + l2v;

@@ -105,7 +105,8 @@ struct WCtx {
     const bool row = want && r >= 0 && r <= ny, el = row && r < ny;
     const int rr = row ? r : 0, re = el ? r : 0;
     const int nd = a + rs * rr;
-    const bool k0 = row && n0, k1 = row && n1;
+    const long long NN = (long long)rs * (ny + 1), NC = (long long)crs * (ny / 2 + 1);
+    const bool k0 = row && n0 && TOPO_IN(nd, NN), k1 = row && n1 && TOPO_IN(nd + 1, NN);
     if (L::kV) {
       cp_async<sizeof(V2)>(sl + L::kOffV + lane * sizeof(V2), v2 + (k0 ? nd : 0), k0);
       cp_async<sizeof(V2)>(sl + L::kOffV + (32 + lane) * sizeof(V2), v2 + (k1 ? nd + 1 : 0), k1);
@@ -117,24 +118,30 @@ struct WCtx {
     if (L::kZ) {
       const int i0 = k0 ? a >> 1 : 0, q0 = rr >> 1, q1 = (rr + 1) >> 1;
       const bool odd = (r & 1) != 0;
-      cp_async<sizeof(V2)>(sl + L::kOffZ + lane * sizeof(V2), zc2 + (k0 ? i0 + crs * q0 : 0), k0);
+      const bool z0 = k0 && TOPO_IN(i0 + crs * q0, NC), z1 = k1 && TOPO_IN(i0 + 1 + crs * q0, NC);
+      const bool z2 = k0 && odd && TOPO_IN(i0 + crs * q1, NC);
+      const bool z3 = k1 && odd && TOPO_IN(i0 + 1 + crs * q1, NC);
+      cp_async<sizeof(V2)>(sl + L::kOffZ + lane * sizeof(V2), zc2 + (z0 ? i0 + crs * q0 : 0), z0);
       cp_async<sizeof(V2)>(sl + L::kOffZ + (32 + lane) * sizeof(V2),
-                           zc2 + (k1 ? i0 + 1 + crs * q0 : 0), k1);
+                           zc2 + (z1 ? i0 + 1 + crs * q0 : 0), z1);
       cp_async<sizeof(V2)>(sl + L::kOffZ + (64 + lane) * sizeof(V2),
-                           zc2 + (k0 && odd ? i0 + crs * q1 : 0), k0 && odd);
+                           zc2 + (z2 ? i0 + crs * q1 : 0), z2);
       cp_async<sizeof(V2)>(sl + L::kOffZ + (96 + lane) * sizeof(V2),
-                           zc2 + (k1 && odd ? i0 + 1 + crs * q1 : 0), k1 && odd);
+                           zc2 + (z3 ? i0 + 1 + crs * q1 : 0), z3);
     }
     if (L::kR) {
       cp_async<16>(sl + L::kOffR + lane * 16, rd2 + (k0 ? nd : 0), k0);
       cp_async<16>(sl + L::kOffR + (32 + lane) * 16, rd2 + (k1 ? nd + 1 : 0), k1);
     }
-    const bool xa = el && e0, xb = el && e1, xc = el && xl0;
+    const long long M = (long long)nx * ny, NF = (long long)((nx + 2) >> 1) * (ny + 1);
+    const bool xa = el && e0 && TOPO_IN(a + nx * re, M), xb = el && e1 && TOPO_IN(a + 1 + nx * re, M);
+    const bool xc = el && xl0 && (MODE != 4 || lane != 0 || TOPO_IN(a - 1 + nx * re, M));
     cp_async<sizeof(T)>(sl + L::kOffX + lane * sizeof(T), x + (xa ? a + nx * re : 0), xa);
     cp_async<sizeof(T)>(sl + L::kOffX + (32 + lane) * sizeof(T), x + (xb ? a + 1 + nx * re : 0), xb);
     if (MODE == 4 && lane == 0)
       cp_async<sizeof(T)>(sl + L::kOffX + 64 * sizeof(T), x + (xc ? a - 1 + nx * re : 0), xc);
-    cp_async<4>(sl + L::kOffF + lane * 4, fpad + (k0 ? (a >> 1) + ((nx + 2) >> 1) * rr : 0), k0);
+    const bool kf = k0 && TOPO_IN((a >> 1) + ((nx + 2) >> 1) * rr, NF);
+    cp_async<4>(sl + L::kOffF + lane * 4, fpad + (kf ? (a >> 1) + ((nx + 2) >> 1) * rr : 0), kf);
     cp_commit();
   }
 
@@ -382,9 +389,9 @@ __global__ void __launch_bounds__(kWWarps * 32) k_q1w(int nx, int ny, int rows, 
           o.y = w_out<T, MODE>(qv, R.b0.y, pb0.y, omega, dA);
           if (f & 0xffu) o.x = T(0);
           if (f & 0xff00u) o.y = T(0);
-          reinterpret_cast<V2*>(y)[node] = o;
-          if (DOT == 1) part = fma((double)pb0.x, (double)o.x, fma((double)pb0.y, (double)o.y, part));
-          if (DOT == 2) part = fma(R.r0.x, (double)o.x, fma(R.r0.y, (double)o.y, part));
+          if (TOPO_IN(node, (long long)C.rs * (C.ny + 1))) reinterpret_cast<V2*>(y)[node] = o;
+          if (DOT == 1) part = fma(double_of(pb0.x), double_of(o.x), fma(double_of(pb0.y), double_of(o.y), part));
+          if (DOT == 2) part = fma(R.r0.x, double_of(o.x), fma(R.r0.y, double_of(o.y), part));
         }
         if (out1) {
           const T qu = cuB + ruB[0] + ruA[1], qv = cvB + rvB[0] + rvA[1];
@@ -393,9 +400,9 @@ __global__ void __launch_bounds__(kWWarps * 32) k_q1w(int nx, int ny, int rows, 
           o.y = w_out<T, MODE>(qv, R.b1.y, pb1.y, omega, dB);
           if (f & 0xff0000u) o.x = T(0);
           if (f & 0xff000000u) o.y = T(0);
-          reinterpret_cast<V2*>(y)[node + 1] = o;
-          if (DOT == 1) part = fma((double)pb1.x, (double)o.x, fma((double)pb1.y, (double)o.y, part));
-          if (DOT == 2) part = fma(R.r1.x, (double)o.x, fma(R.r1.y, (double)o.y, part));
+          if (TOPO_IN(node + 1, (long long)C.rs * (C.ny + 1))) reinterpret_cast<V2*>(y)[node + 1] = o;
+          if (DOT == 1) part = fma(double_of(pb1.x), double_of(o.x), fma(double_of(pb1.y), double_of(o.y), part));
+          if (DOT == 2) part = fma(R.r1.x, double_of(o.x), fma(R.r1.y, double_of(o.y), part));
         }
       }
       xcA = xpA;

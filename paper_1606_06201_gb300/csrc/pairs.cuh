@@ -73,6 +73,61 @@ __device__ __forceinline__ double double_from_float(float f) {
   return __longlong_as_double((long long)b);
 }
 
+// Conversions between FP64 and FP32 with integer operations, written from the IEEE 754 binary64
+// and binary32 formats.  The FP64 pipe of this part issues about two instructions per clock per
+// SM and a conversion instruction (F2F) takes one of its slots, so vector kernels that convert
+// every entry become FP64-bound; the integer pipe is far wider.  Both give the results of the
+// hardware conversions (rounding to nearest, ties to even; subnormals; overflow to infinity;
+// a NaN stays a NaN).
+__device__ __forceinline__ float float_from_double_rn(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned long long m = b & 0xfffffffffffffull;
+  if (e == 2047) return __uint_as_float(sign | 0x7f800000u | (m ? 0x400000u : 0u));
+  const int ef = e - 896;  // the binary32 exponent field
+  if (ef >= 255) return __uint_as_float(sign | 0x7f800000u);
+  if (ef >= 1) {  // normal: 23 of the 52 fraction bits, the other 29 decide the rounding
+    unsigned u = ((unsigned)ef << 23) | (unsigned)(m >> 29);
+    const unsigned rem = (unsigned)(m & 0x1fffffffu);
+    if (rem > 0x10000000u || (rem == 0x10000000u && (u & 1u))) ++u;  // (carries into the exponent)
+    return __uint_as_float(sign | u);
+  }
+  // a binary32 subnormal or zero: u 2^-149 with u = M 2^(e - 1075 + 149) = M >> (30 - ef)
+  const int sh = 30 - ef;
+  if (e == 0 || sh >= 54) return __uint_as_float(sign);
+  const unsigned long long M = m | (1ull << 52);
+  unsigned u = (unsigned)(M >> sh);
+  const unsigned long long rem = M & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+  if (rem > half || (rem == half && (u & 1u))) ++u;
+  return __uint_as_float(sign | u);
+}
+
+__device__ __forceinline__ double double_from_float_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  const unsigned ef = (u >> 23) & 0xff, mant = u & 0x7fffffu;
+  if (ef == 255)
+    return __longlong_as_double((long long)(sign | (0x7ffull << 52) | ((unsigned long long)mant << 29)));
+  if (ef == 0) {
+    if (mant == 0) return __longlong_as_double((long long)sign);
+    const int pb = 31 - __clz(mant);  // leading bit: the value is 2^(pb - 149) (1 + frac)
+    const unsigned long long frac = (unsigned long long)(mant - (1u << pb)) << (52 - pb);
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(pb + 874) << 52) | frac));
+  }
+  return __longlong_as_double(
+      (long long)(sign | ((unsigned long long)(ef + 896) << 52) | ((unsigned long long)mant << 29)));
+}
+
+// Widening and narrowing of a vector entry of precision TV (float or double).
+__device__ __forceinline__ double double_of(float f) { return double_from_float_exact(f); }
+__device__ __forceinline__ double double_of(double d) { return d; }
+template <typename TV>
+__device__ __forceinline__ TV tv_from_double(double d) {
+  if constexpr (sizeof(TV) == 4) return float_from_double_rn(d);
+  else return d;
+}
+
 // host: a double constant as a float pair (hi = the nearest float, lo = the rest rounded)
 inline f2 df_const(double c) {
   const float h = (float)c;

@@ -13,6 +13,7 @@
 // of 64 multiply-adds.  The host checks T^T Khat T == K0 before using this path.
 #pragma once
 
+#include "pairs.cuh"
 #include "topo_internal.cuh"
 
 namespace topo {

@@ -43,6 +43,70 @@ topo_status cuda_status(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? TOPO_E_OOM : TOPO_E_CUDA;
 }
 
+// ---- Index-check records (debug build) ------------------------------------------------------
+struct BoundsReg {
+  BoundsReader reader;
+  const char* file;
+};
+std::vector<BoundsReg>& bounds_readers() {
+  static std::vector<BoundsReg> r;
+  return r;
+}
+
+#ifdef TOPO_BOUNDS_CHECK
+__global__ void k_bounds_selftest(long long i, long long n, int* out) {
+  out[0] = TOPO_IN(i, n) ? 1 : 0;
+}
+#endif
+
+// Sum of the records of every translation unit; the first nonzero one in *first.
+cudaError_t read_bounds(unsigned long long* count, BoundsRecord* first, const char** file,
+                        bool reset) {
+  *count = 0;
+  *first = BoundsRecord{};
+  *file = "";
+  cudaError_t e = cudaDeviceSynchronize();
+  for (const BoundsReg& r : bounds_readers()) {
+    if (e != cudaSuccess) break;
+    BoundsRecord rec{};
+    e = r.reader(&rec, reset);
+    if (e == cudaSuccess && rec.count) {
+      if (*count == 0) {
+        *first = rec;
+        *file = r.file;
+      }
+      *count += rec.count;
+    }
+  }
+  return e;
+}
+
+int register_bounds_reader(BoundsReader reader, const char* file) {
+  bounds_readers().push_back({reader, file});
+  return (int)bounds_readers().size();
+}
+
+// TOPO_E_BOUNDS when an index check of the debug build has recorded a violation (what: the
+// entry point), else st.
+topo_status bounds_status(topo_status st, const char* what) {
+#ifdef TOPO_BOUNDS_CHECK
+  unsigned long long count = 0;
+  BoundsRecord rec{};
+  const char* file = "";
+  cudaError_t e = read_bounds(&count, &rec, &file, false);
+  if (e != cudaSuccess) return cuda_status(e, what);
+  if (count) {
+    set_error(std::string(what) + ": " + std::to_string(count) +
+              " index(es) out of range, the first " + std::to_string(rec.index) + " of size " +
+              std::to_string(rec.size) + " at " + file + ":" + std::to_string(rec.line));
+    return TOPO_E_BOUNDS;
+  }
+#else
+  (void)what;
+#endif
+  return st;
+}
+
 }  // namespace topo
 
 using namespace topo;
@@ -339,11 +403,8 @@ template <typename TV>
 cudaError_t q1_smooth_beta(const topo_solver* s, int nx, int ny, const TV* x, const TV* v,
                            const TV* b, TV* y, TV omega, const uint8_t* fixed, int nrhs,
                            double* partials, unsigned* counters, CgScalars* sc) {
-  if constexpr (std::is_same<TV, float>::value) {
-    if (s->q1_wide && s->fixed_pad)
-      return launch_q1w_smooth_beta(nx, ny, s->q1, x, v, b, y, omega, s->fixed_pad, nrhs, s->r,
-                                    partials, counters, sc, s->st, s->sweep_rows);
-  }
+  // (the two-column form of this sweep, with its FP64 residual read for r~^T y~, measured slower
+  // than the one-column kernel: 31.4 against 27.3 us per launch on 2048 x 1024)
   return launch_q1_smooth_beta<TV>(nx, ny, s->q1, x, v, b, y, omega, fixed, nrhs, s->r, partials,
                                    counters, sc, s->st);
 }
@@ -351,6 +412,27 @@ cudaError_t q1_smooth_beta(const topo_solver* s, int nx, int ny, const TV* x, co
 // Operator application on level k (mode as launch_apply): the warp-sweep Q1 kernels on the 2D
 // finest level, the matrix-free first coarse level in mixed precision, the Z operator (element
 // rank-one terms and lambda row) for IP systems, the generic element-matrix kernels elsewhere.
+// TOPO_HEX_OUTER=tile: the 3D outer operator in the tile form (one launch, no force buffer, the
+// same q).  The default is the two-kernel form with the force buffer: on 128 x 64 x 64 with 8
+// right-hand sides the tile form took 848 us per launch against 349 + 200 us for the pair (it
+// computes about 30% of the elements twice, and the pair-arithmetic element product is the cost).
+bool hex_buffered_env() {
+  const char* v = std::getenv("TOPO_HEX_OUTER");
+  return !(v && std::string(v) == "tile");
+}
+
+// TOPO_HEX_SWEEP=node|dense|wht: the 3D finest V-cycle operator (node-parallel; tile with the
+// rows of K0, the same bits as node-parallel; tile in the Walsh-Hadamard basis, when K0 has its
+// structure: the default, 168 + 157 us against 238 + 201 us per V-cycle on 128 x 64 x 64 with 8
+// right-hand sides; the dense tile form was the slowest).
+int hex_sweep_env(bool hex_ok) {
+  const char* v = std::getenv("TOPO_HEX_SWEEP");
+  const std::string w = v ? v : "";
+  if (w == "dense") return 1;
+  if (w == "node" || !hex_ok) return 0;
+  return 2;
+}
+
 template <typename TV>
 topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* b, TV* y,
                         const CgScalars* sc, const TV* zc = nullptr, int nrhs = 0) {
@@ -396,6 +478,12 @@ topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* 
     TOPO_CUDA(launch_apply_l1<double>(lv.d, mode, s->C, s->x, (const double*)v, (const double*)b,
                                       (double*)y, lv.invd, (double)omega, lv.fixed, nrhs, sc,
                                       s->st));
+    return TOPO_OK;
+  }
+  if (k == 0 && s->hex_sweep && mode <= 2) {  // 3D finest level: the tile form
+    TOPO_CUDA(launch_hex_tile_sweep<TV>(lv.d, mode, s->hex_sweep == 1, s->hex, Prec<TV>::K0(s),
+                                        Prec<TV>::x(s), v, b, y, Prec<TV>::invd(lv), omega,
+                                        lv.fixed, nrhs, sc, s->st));
     return TOPO_OK;
   }
   const TV* x = k == 0 ? Prec<TV>::x(s) : nullptr;
@@ -451,6 +539,7 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
     a.nc = s->nc;
     a.omega = (TV)s->desc.omega;
     a.Ainv = s->Ainv;
+    a.wait_ns = s->wait_ns;
     for (int j = 0; j < a.nl; ++j) {
       Level& l = s->L[k + j];
       a.d[j] = l.d;
@@ -644,6 +733,11 @@ topo_status cg_iteration(topo_solver* s, int slot, double tol, int max_iter) {
   } else if (s->q1_ok) {
     TOPO_CUDA(launch_q1_apply_dot(l0.d.nx, l0.d.ny, s->q1, s->x, s->p, s->q, l0.fixed, s->nrhs,
                                   s->partials, s->counters, s->sc, s->st));
+  } else if (s->hex_ok && !s->hex_buffered) {
+    const bool pairs = s->outer_df && s->xdf;
+    TOPO_CUDA(launch_hex_tile_apply_dot(l0.d, s->hex, pairs ? (const void*)s->xdf : (const void*)s->x,
+                                        pairs, s->p, s->q, l0.fixed, s->nrhs, s->partials,
+                                        s->counters, s->sc, s->st));
   } else if (s->hex_ok && s->outer_df && s->xdf) {
     TOPO_CUDA(launch_hex_apply_dot_df(l0.d, s->hex, s->xdf, s->p, s->q, l0.fixed, s->nrhs,
                                       s->hexR, s->partials, s->counters, s->sc, s->st));
@@ -1121,6 +1215,9 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
     s->q1_wide = !(nv && nv[0] == '1');
   }
   s->hex_ok = (s->dim == 3) && !arrow && !d->generic_kernels && hex_coefficients(K0.data(), s->hex);
+  s->hex_buffered = s->hex_ok && hex_buffered_env();
+  s->hex_sweep = (s->dim == 3 && !arrow) ? hex_sweep_env(s->hex_ok) : 0;
+  if (s->dim == 3) TOPO_CUDA(prepare_hex_tile_kernels());
   s->l1_free = (s->dim == 2) && !arrow && s->prec == TOPO_MIXED && s->nlev >= 3 &&
                !d->generic_kernels;
   // The V-cycle of a mixed solver reads FP32 coarse matrices only, so they are computed in FP32
@@ -1239,7 +1336,7 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   const long long m = s->L[0].m;
   const long long n = s->L[0].n + (arrow ? 2 : 0);
   TOPO_TRY(s->alloc(&s->x, m));
-  if (s->hex_ok) TOPO_TRY(s->alloc(&s->hexR, (size_t)m * 24 * nrhs));
+  if (s->hex_buffered) TOPO_TRY(s->alloc(&s->hexR, (size_t)m * 24 * nrhs));
   if ((s->q1_ok || s->hex_ok) && !arrow) {  // pair-arithmetic outer operator: default for mixed
     TOPO_TRY(s->alloc(&s->xdf, m));
     s->outer_df = s->prec == TOPO_MIXED ? 1 : 0;
@@ -1430,7 +1527,7 @@ topo_status plan_bytes(const topo_solver_desc* d, bool arrow, size_t* out) {
   const long long m = d0.elems();
   const long long n = d0.dofs() + (arrow ? 2 : 0);
   add(m, sizeof(double));
-  if (hex_ok) add((size_t)m * 24 * nrhs, sizeof(double));
+  if (hex_ok && hex_buffered_env()) add((size_t)m * 24 * nrhs, sizeof(double));
   if ((q1_ok || hex_ok) && !arrow) add(m, sizeof(float2));
   if (mixed) {
     add(m, sizeof(float));
@@ -1529,6 +1626,18 @@ topo_status topo_set_vcycle_fusion(topo_solver* s, int on) {
   const bool want = on != 0;
   if (want != s->fuse_on) {
     s->fuse_on = want;
+    drop_graphs(s);
+  }
+  return TOPO_OK;
+}
+
+topo_status topo_set_wait_limit_ns(topo_solver* s, unsigned long long ns) {
+  if (!s) {
+    set_error("topo_set_wait_limit_ns: null solver");
+    return TOPO_E_INVALID_ARG;
+  }
+  if (ns != s->wait_ns) {
+    s->wait_ns = ns;
     drop_graphs(s);
   }
   return TOPO_OK;
@@ -1657,8 +1766,10 @@ topo_status topo_solve(topo_solver* s, const double* b, double* u, double tol, i
   StreamGuard g(s);
   topo_solve_info local{};
   topo_solve_info* out = info ? info : &local;
-  const topo_status st = s->prec == TOPO_MIXED ? solve_impl<float>(s, b, u, tol, use_x0, out)
-                                               : solve_impl<double>(s, b, u, tol, use_x0, out);
+  const topo_status st = bounds_status(
+      s->prec == TOPO_MIXED ? solve_impl<float>(s, b, u, tol, use_x0, out)
+                            : solve_impl<double>(s, b, u, tol, use_x0, out),
+      "topo_solve");
   append_record(s, tol, *out, st);
   return st;
 }
@@ -1703,7 +1814,7 @@ topo_status topo_solve_host(topo_solver* s, const double* x, const double* b, do
   if (st != TOPO_OK && st != TOPO_E_NOT_CONVERGED) return st;
   TOPO_CUDA(cudaMemcpyAsync(u, s->z, sizeof(double) * n, cudaMemcpyDeviceToHost, s->st));
   TOPO_CUDA(cudaStreamSynchronize(s->st));
-  return st;
+  return bounds_status(st, "topo_solve_host");
 }
 
 topo_status topo_apply_K(topo_solver* s, const double* v, double* y) {
@@ -1712,7 +1823,68 @@ topo_status topo_apply_K(topo_solver* s, const double* v, double* y) {
     return TOPO_E_INVALID_ARG;
   }
   StreamGuard g(s);
-  return apply_outer(s, v, y, nullptr);
+  return bounds_status(apply_outer(s, v, y, nullptr), "topo_apply_K");
+}
+
+int topo_bounds_check_enabled(void) {
+#ifdef TOPO_BOUNDS_CHECK
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+topo_status topo_bounds_report(unsigned long long* count, long long* index, long long* size,
+                               char* file, int file_len, int* line, int reset) {
+  unsigned long long c = 0;
+  BoundsRecord rec{};
+  const char* f = "";
+  const cudaError_t e = read_bounds(&c, &rec, &f, reset != 0);
+  if (e != cudaSuccess) return cuda_status(e, "topo_bounds_report");
+  if (count) *count = c;
+  if (index) *index = rec.index;
+  if (size) *size = rec.size;
+  if (line) *line = rec.line;
+  if (file && file_len > 0) {
+    std::strncpy(file, f, (size_t)file_len - 1);
+    file[file_len - 1] = '\0';
+  }
+  return TOPO_OK;
+}
+
+topo_status topo_bounds_selftest(long long i, long long n) {
+#ifdef TOPO_BOUNDS_CHECK
+  int* out = nullptr;
+  TOPO_CUDA(cudaMalloc(&out, sizeof(int)));
+  k_bounds_selftest<<<1, 1>>>(i, n, out);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(out);
+  if (e != cudaSuccess) return cuda_status(e, "topo_bounds_selftest");
+  return TOPO_OK;
+#else
+  (void)i;
+  (void)n;
+  set_error("topo_bounds_selftest: this library was built without TOPO_BOUNDS_CHECK");
+  return TOPO_E_INVALID_ARG;
+#endif
+}
+
+topo_status topo_check_conversions(const double* d, const float* f, long long n,
+                                   unsigned long long* mismatches) {
+  if (n < 0 || !mismatches || (n > 0 && (!d || !f))) {
+    set_error("topo_check_conversions: invalid argument");
+    return TOPO_E_INVALID_ARG;
+  }
+  unsigned long long* bad = nullptr;
+  TOPO_CUDA(cudaMalloc(&bad, 2 * sizeof(unsigned long long)));
+  cudaError_t e = cudaMemset(bad, 0, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess && n > 0) e = launch_check_conversions(d, f, n, bad, nullptr);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(mismatches, bad, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  cudaFree(bad);
+  if (e != cudaSuccess) return cuda_status(e, "topo_check_conversions");
+  return TOPO_OK;
 }
 
 topo_status topo_apply_vcycle(topo_solver* s, const double* r, double* y) {
@@ -1727,13 +1899,13 @@ topo_status topo_apply_vcycle(topo_solver* s, const double* r, double* y) {
     float* out = nullptr;
     TOPO_TRY(vcycle<float>(s, 0, (const float*)s->rv, &out, nullptr));
     TOPO_CUDA(launch_convert_f2d(out, y, n, s->st));
-    return TOPO_OK;
+    return bounds_status(TOPO_OK, "topo_apply_vcycle");
   }
   TOPO_CUDA(cudaMemcpyAsync(s->r, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->st));
   double* out = nullptr;
   TOPO_TRY(vcycle<double>(s, 0, s->r, &out, nullptr));
   TOPO_CUDA(cudaMemcpyAsync(y, out, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->st));
-  return TOPO_OK;
+  return bounds_status(TOPO_OK, "topo_apply_vcycle");
 }
 
 topo_status topo_get_level_matrices(topo_solver* s, int level, double* out_host) {
@@ -1835,8 +2007,10 @@ topo_status solver_solve(topo_solver* s, const double* b, double* u, double tol,
                          topo_solve_info* info) {
   topo_solve_info local{};
   topo_solve_info* out = info ? info : &local;
-  const topo_status st = s->prec == TOPO_MIXED ? solve_impl<float>(s, b, u, tol, use_x0, out)
-                                               : solve_impl<double>(s, b, u, tol, use_x0, out);
+  const topo_status st = bounds_status(
+      s->prec == TOPO_MIXED ? solve_impl<float>(s, b, u, tol, use_x0, out)
+                            : solve_impl<double>(s, b, u, tol, use_x0, out),
+      "solve");
   append_record(s, tol, *out, st);
   return st;
 }

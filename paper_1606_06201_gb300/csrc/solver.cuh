@@ -32,6 +32,7 @@ struct topo_solver {
   bool q1_ok = false;            // 2D and T^T Khat T reproduces K0: use the warp-sweep kernels
   bool q1_wide = true;           // FP32 finest sweeps with two node columns per lane (kernels_q1w.cu)
   int sweep_rows = 0;            // strip height of the 2D finest-level warp sweeps (0: automatic)
+  unsigned long long wait_ns = 1000000000ull;  // bound of the device-side waits (topo_set_wait_limit_ns)
   unsigned* fixed_pad = nullptr; // 2D finest mask as node pairs, row stride (nx + 2) / 2 words
   double* x = nullptr;
   float* x32 = nullptr;
@@ -87,6 +88,9 @@ struct topo_solver {
   bool hex_ok = false;                    // 3D outer operator in the Walsh-Hadamard basis
   HexCoef hex{};
   double* hexR = nullptr;                 // its element forces (24 x elems x nrhs)
+  bool hex_buffered = true;               // the two-kernel form with hexR (else the tile form)
+  int hex_sweep = 0;                      // 3D finest V-cycle operator: 0 node-parallel,
+                                          // 1 tile dense (same bits as 0), 2 tile Walsh-Hadamard
   int outer_df = 0;                       // outer operator in float-pair arithmetic (1) or FP64
   bool tail_ok = false;                   // the fused deep-level kernel can run on this device
   bool fuse_on = true;                    // fused V-cycle kernels in use (topo_set_vcycle_fusion)

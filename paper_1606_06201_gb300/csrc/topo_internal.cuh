@@ -139,6 +139,50 @@ topo_status cuda_status(cudaError_t e, const char* what);
     if (_e != cudaSuccess) return topo::cuda_status(_e, what);  \
   } while (0)
 
+// ---- Index checks of the debug build --------------------------------------------------------
+// Built with -DTOPO_BOUNDS_CHECK, the operator kernels check the indices they compute against the
+// sizes of the buffers they address.  An index outside [0, size) is never used: a checked load
+// reads entry 0 instead (TOPO_IDX) and a checked store is skipped (TOPO_IN); the first such index
+// of each translation unit is recorded with its source line, and every solve then returns
+// TOPO_E_BOUNDS (topo_bounds_report reads the records).  Nothing traps.  Without the macro both
+// checks are constants and cost nothing.
+struct BoundsRecord {
+  unsigned long long count;  // indices found outside their range since the last reset
+  long long index, size;     // the first of them and the size it was checked against
+  int line, pad;             // its source line
+};
+using BoundsReader = cudaError_t (*)(BoundsRecord* out, bool reset);
+// Registers the record reader of one translation unit (host, at load time); returns its number.
+int register_bounds_reader(BoundsReader reader, const char* file);
+
+#ifdef TOPO_BOUNDS_CHECK
+static __device__ BoundsRecord g_topo_bounds;  // (one per translation unit)
+__device__ __noinline__ static bool topo_out_of_bounds(long long i, long long n, int line) {
+  if (atomicAdd(&g_topo_bounds.count, 1ull) == 0ull) {
+    g_topo_bounds.index = i;
+    g_topo_bounds.size = n;
+    g_topo_bounds.line = line;
+  }
+  return false;
+}
+#define TOPO_IN(i, n)                                                              \
+  ((unsigned long long)(long long)(i) < (unsigned long long)(long long)(n) ||      \
+   topo::topo_out_of_bounds((long long)(i), (long long)(n), __LINE__))
+#define TOPO_IDX(i, n) (TOPO_IN(i, n) ? (i) : 0)
+static cudaError_t read_bounds_record(BoundsRecord* out, bool reset) {
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_topo_bounds, sizeof(BoundsRecord));
+  if (e == cudaSuccess && reset) {
+    const BoundsRecord zero = {};
+    e = cudaMemcpyToSymbol(g_topo_bounds, &zero, sizeof(BoundsRecord));
+  }
+  return e;
+}
+[[maybe_unused]] static const int g_bounds_reader_id = register_bounds_reader(&read_bounds_record, __FILE__);
+#else
+#define TOPO_IN(i, n) ((void)(n), true)
+#define TOPO_IDX(i, n) ((void)(n), (i))
+#endif
+
 // A named NVTX range for the duration of a scope: the phases of the method (hierarchy build, MGCG
 // solve, IP Newton step, OC step) show up as ranges in profilers (ncu --nvtx, Nsight Systems); with
 // no tool attached a push or pop costs a few nanoseconds.
@@ -266,6 +310,7 @@ struct TailArgs {
       off_f[kTailMax];
   unsigned off_bar;  // the mbarrier of the bulk copies
   unsigned smem;
+  unsigned long long wait_ns;  // bound of the first wait for the bulk copies (0: expire at once)
 };
 constexpr int kTail1Threads = 512;
 
@@ -385,6 +430,24 @@ cudaError_t launch_hex_apply_dot_df(const Dims& d, const HexCoef& c, const float
                                     const double* v, double* y, const uint8_t* fixed, int nrhs,
                                     double* R, double* partials, unsigned* counters, CgScalars* sc,
                                     cudaStream_t st);
+// The same operators in the tile form (kernels_hex.cu): element forces through shared memory, one
+// launch, no force buffer; q has the bits of the buffered form.  x: FP64 densities, or float pairs
+// when `pairs`.
+// Counts the inputs where the integer FP64 <-> FP32 conversions differ from the hardware ones.
+cudaError_t launch_check_conversions(const double* d, const float* f, long long n,
+                                     unsigned long long* bad, cudaStream_t st);
+cudaError_t prepare_hex_tile_kernels();
+cudaError_t launch_hex_tile_apply_dot(const Dims& d, const HexCoef& c, const void* x, bool pairs,
+                                      const double* v, double* y, const uint8_t* fixed, int nrhs,
+                                      double* partials, unsigned* counters, CgScalars* sc,
+                                      cudaStream_t st);
+// Finest-level 3D V-cycle operator (modes 0-2 of launch_apply) in the tile form: `dense` with the
+// element rows of K0 (the bits of the node-parallel kernel), otherwise in the Walsh-Hadamard basis.
+template <typename T>
+cudaError_t launch_hex_tile_sweep(const Dims& d, int mode, bool dense, const HexCoef& c,
+                                  const T* K0, const T* x, const T* v, const T* b, T* y,
+                                  const T* invd, T omega, const uint8_t* fixed, int nrhs,
+                                  const CgScalars* sc, cudaStream_t st);
 // Fused pairs of finest-level V-cycle steps (same bits as the separate steps): mode 4 = the first
 // two Jacobi sweeps from zero (b -> y); mode 5 = prolongation and correction t + P zc followed by
 // one Jacobi sweep (t, zc -> y).  zc: the first coarse level's vector.

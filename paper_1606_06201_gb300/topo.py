@@ -10,17 +10,19 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libtopo_gb300.so")
+# TOPO_LIBRARY: another build of the library (e.g. the index-checked libtopo_gb300_bc.so)
+LIB_PATH = os.environ.get("TOPO_LIBRARY") or os.path.join(_HERE, "libtopo_gb300.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError("libtopo_gb300.so is missing: build it with "
-                      "`python -m paper_1606_06201_gb300.build` (nvcc, sm_103a)")
+    raise ImportError("%s is missing: build it with "
+                      "`python -m paper_1606_06201_gb300.build` (nvcc, sm_103a)" % LIB_PATH)
 _lib = ctypes.CDLL(LIB_PATH)
 
-OK, E_INVALID_ARG, E_NOT_CONVERGED, E_BREAKDOWN, E_INFEASIBLE, E_TIMEOUT, E_OOM, E_CUDA = range(8)
+OK, E_INVALID_ARG, E_NOT_CONVERGED, E_BREAKDOWN, E_INFEASIBLE, E_TIMEOUT, E_OOM, E_CUDA, E_BOUNDS = \
+    range(9)
 FP64, MIXED = 0, 1
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_CONVERGED", 3: "BREAKDOWN", 4: "INFEASIBLE",
-                5: "TIMEOUT", 6: "OOM", 7: "CUDA"}
+                5: "TIMEOUT", 6: "OOM", 7: "CUDA", 8: "BOUNDS"}
 
 
 class SolverDesc(ctypes.Structure):
@@ -96,6 +98,13 @@ _SIGS = {
                                   ctypes.POINTER(SolveInfo)]),
     "topo_apply_K": (ctypes.c_int, [_vp, _vp, _vp]),
     "topo_apply_vcycle": (ctypes.c_int, [_vp, _vp, _vp]),
+    "topo_check_conversions": (ctypes.c_int, [_vp, _vp, ctypes.c_longlong, _vp]),
+    "topo_bounds_check_enabled": (ctypes.c_int, []),
+    "topo_bounds_report": (ctypes.c_int, [ctypes.POINTER(ctypes.c_ulonglong),
+                                          ctypes.POINTER(ctypes.c_longlong),
+                                          ctypes.POINTER(ctypes.c_longlong), ctypes.c_char_p,
+                                          ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    "topo_bounds_selftest": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_longlong]),
     "topo_get_level_matrices": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "topo_level_elems": (ctypes.c_int, [_vp, ctypes.c_int]),
     "topo_compliance": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -136,6 +145,7 @@ _SIGS = {
                                                    ctypes.POINTER(ctypes.c_size_t)]),
     "topo_set_record_file": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "topo_set_sweep_rows": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "topo_set_wait_limit_ns": (ctypes.c_int, [_vp, ctypes.c_ulonglong]),
     "topo_ip_set_record_file": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "topo_oc_set_record_file": (ctypes.c_int, [_vp, ctypes.c_char_p]),
 }
@@ -246,6 +256,42 @@ def oc_options(variant=OC_AOC, q=0.5, xlow=1e-6, lam_hi=1e4, tau_lambda=1e-11, t
     return OcOpts(variant, q, xlow, lam_hi, tau_lambda, tau_oc, max_feval, cg_tol0,
                   int(adaptive_tol))
 
+
+
+def bounds_check_enabled():
+    """True when the loaded library is the index-checked build (TOPO_BOUNDS_CHECK)."""
+    return bool(_lib.topo_bounds_check_enabled())
+
+
+def bounds_report(reset=False):
+    """(count, first index, its size, file, line) of the index checks of the debug build."""
+    count, index, size, line = ctypes.c_ulonglong(), ctypes.c_longlong(), ctypes.c_longlong(), \
+        ctypes.c_int()
+    buf = ctypes.create_string_buffer(512)
+    _check(_lib.topo_bounds_report(ctypes.byref(count), ctypes.byref(index), ctypes.byref(size),
+                                   buf, 512, ctypes.byref(line), int(reset)), "topo_bounds_report")
+    return count.value, index.value, size.value, buf.value.decode(), line.value
+
+
+def bounds_selftest(i, n):
+    """One index check of i against n in a kernel that addresses no buffer (debug build)."""
+    _check(_lib.topo_bounds_selftest(int(i), int(n)), "topo_bounds_selftest")
+
+
+def check_conversions(d, f):
+    """Mismatch counts (double -> float, float -> double) of the library's integer conversions
+    against the hardware ones on the entries of d (FP64 CUDA tensor) and f (FP32 CUDA tensor of
+    the same length)."""
+    import torch
+    if d.numel() != f.numel():
+        raise ValueError("d and f must have the same length")
+    if not (f.is_cuda and f.dtype == torch.float32 and f.is_contiguous()):
+        raise ValueError("f must be a contiguous float32 CUDA tensor")
+    out = (ctypes.c_ulonglong * 2)()
+    _check(_lib.topo_check_conversions(_ptr(d), _vp(f.data_ptr()), d.numel(),
+                                       ctypes.cast(out, _vp)),
+           "topo_check_conversions")
+    return int(out[0]), int(out[1])
 
 
 def compliance_noalloc(f, u, c, nrhs=1):
@@ -501,6 +547,10 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+    def set_wait_limit_ns(self, ns):
+        """Bound of the device-side waits (topo_set_wait_limit_ns; 0: expire at once)."""
+        _check(_lib.topo_set_wait_limit_ns(self._h, int(ns)), "topo_set_wait_limit_ns")
 
     def set_sweep_rows(self, rows):
         """Strip height of the 2D finest-level FP32 sweeps (topo_set_sweep_rows; 0: automatic)."""

@@ -624,3 +624,29 @@ def test_batched_power_iteration_smoothers_equal_individual_solves(shape, kind):
         np.testing.assert_allclose(host(U)[k], host(u), rtol=0, atol=1e-12 * np.abs(host(u)).max())
     sb.close()
     s1.close()
+
+
+def test_bounded_wait_expiry_stops_the_solve_with_timeout_and_the_solver_recovers():
+    """The deep V-cycle levels wait for their bulk copies with a bound on the global timer.  With
+    the bound set to 0 the first wait gives up at once: the copies still land under a second
+    bounded wait, the CG stops with TOPO_E_TIMEOUT, and the context stays usable: with the bound
+    restored the next solve gives the bits of the solve before."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny = 256, 128
+    fixed = W.clamp_xmin(nx, ny)
+    x = dev(torch, _x(nx, ny, 0, 51))
+    f = dev(torch, W.normal_load(fixed, 52))
+    s = topo.Solver(nx, ny, fixed=fixed, levels=6, precision=topo.MIXED)
+    s.set_density(x)
+    u0, info0 = s.solve(f, tol=1e-8)
+    assert info0.status == topo.OK
+    s.set_wait_limit_ns(0)
+    with pytest.raises(topo.TopoError) as e:
+        s.solve(f, tol=1e-8)
+    assert e.value.status == topo.E_TIMEOUT
+    s.set_wait_limit_ns(10**9)
+    u1, info1 = s.solve(f, tol=1e-8)
+    assert info1.status == topo.OK and info1.iterations == info0.iterations
+    np.testing.assert_array_equal(host(u1), host(u0))
+    s.close()
