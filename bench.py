@@ -668,6 +668,13 @@ def main():
                          "vcycle_first_coarse_level": (avg["vcycle_levels_ge1"] - avg["vcycle_levels_ge2"])
                          if avg["vcycle_levels_ge1"] and avg["vcycle_levels_ge2"] else None,
                          "vcycle_levels_ge2": avg["vcycle_levels_ge2"],
+                         # per coarse level (levels >= j minus levels >= j + 1); the fused deep
+                         # part counts as one span from its first level down
+                         "vcycle_per_level": {
+                             "level_%d" % j: (avg["vcycle_levels_ge%d" % j]
+                                              - (avg["vcycle_levels_ge%d" % (j + 1)] or 0.0))
+                             for j in range(2, 6) if avg["vcycle_levels_ge%d" % j]},
+                         "vcycle_levels_ge6": avg["vcycle_levels_ge6"],
                          "unit": "us per CG iteration (live CUDA events, mixed solver, separate fully "
                                  "profiled run)",
                          "step_us": step_us}

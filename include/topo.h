@@ -187,9 +187,9 @@ topo_status topo_get_profile(const topo_solver* s, double* operator_ms_total, lo
  * b - A z before restriction (with the restriction, where the V-cycle fuses the two), 3 = the
  * restriction P^T r (count 0 where fused into kind 2), 4 = the prolongation and correction
  * z += P z_c (fused with the first post-smoothing sweep where the V-cycle fuses).  Spans of several
- * kernels: 5 = the whole V-cycle (preconditioner), 6 = its part on levels >= 1, 7 = its part on
- * levels >= 2 (coarsest solve included).  A kind that the solver's V-cycle does not run has
- * count 0.  kind outside 0..7 -> E_INVALID_ARG. */
+ * kernels: 5 = the whole V-cycle (preconditioner), 6 + j = its part on levels >= j + 1 for
+ * j = 0..5 (coarsest solve included; a fused deep part counts from its first level).  A kind
+ * that the solver's V-cycle does not run has count 0.  kind outside 0..11 -> E_INVALID_ARG. */
 topo_status topo_get_profile_kernel(const topo_solver* s, int kind, double* ms_total,
                                     long long* count);
 

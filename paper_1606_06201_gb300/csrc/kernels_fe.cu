@@ -939,6 +939,90 @@ __device__ __forceinline__ void sm_apply(const Dims& d, int node, const T* M, co
   }
 }
 
+// The node rows of sm_apply with the element matrices element-major (kAemStride entries per
+// element, rows loc*2 and loc*2+1 contiguous: four 16-byte loads per element in FP32) and the
+// 3 x 3 node neighbourhood loaded once (18 values instead of 32).  The values, the FMA chains and
+// their order are those of sm_apply (the same bits).
+template <typename T>
+__device__ __forceinline__ void load16(const T* p, T out[16]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float4 w = q[u];
+      out[4 * u] = w.x;
+      out[4 * u + 1] = w.y;
+      out[4 * u + 2] = w.z;
+      out[4 * u + 3] = w.w;
+    }
+  } else {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const double2 w = q[u];
+      out[2 * u] = w.x;
+      out[2 * u + 1] = w.y;
+    }
+  }
+}
+
+template <int MODE, typename T, typename VIn>
+__device__ __forceinline__ void sm_apply_em(const Dims& d, int node, const T* Me, const VIn& vin,
+                                            const T* B, const T* D, const uint8_t* F, T* Y,
+                                            T omega) {
+  const int nnx = d.nx + 1;
+  const int i = node % nnx, j = node / nnx;
+  T acc[2] = {T(0), T(0)};
+  T own[2] = {T(0), T(0)};
+  if (MODE != 3) {
+    T nv[3][3][2];  // nodes (i - 1 + a, j - 1 + b) at nv[b][a]; outside the grid: unused zeros
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int ni = i - 1 + a, nj = j - 1 + b;
+        const bool ok = ni >= 0 && ni <= d.nx && nj >= 0 && nj <= d.ny;
+        const int nid = ok ? ni + nnx * nj : 0;
+        nv[b][a][0] = ok ? vin(2 * nid) : T(0);
+        nv[b][a][1] = ok ? vin(2 * nid + 1) : T(0);
+      }
+    own[0] = nv[1][1][0];
+    own[1] = nv[1][1][1];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int dx = s & 1, dy = s >> 1;
+      const int ex = i - 1 + dx, ey = j - 1 + dy;
+      if (!(ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny)) continue;
+      const int loc = loc_of(1 - dx, 1 - dy, 0);
+      T a[16];
+      load16(Me + (ex + d.nx * ey) * kAemStride + loc * 16, a);
+      T ve[8];
+#pragma unroll
+      for (int bq = 0; bq < 4; ++bq) {
+        ve[2 * bq] = nv[dy + loc_oy(bq)][dx + loc_ox(bq)][0];
+        ve[2 * bq + 1] = nv[dy + loc_oy(bq)][dx + loc_ox(bq)][1];
+      }
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        T t = T(0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t = fma(a[c * 8 + q], ve[q], t);
+        acc[c] += t;
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int id = 2 * node + c;
+    T out;
+    if (F[id]) out = T(0);
+    else if (MODE == 1) out = node_out<1, T>(acc[c], T(0), B[id], T(0), omega);
+    else if (MODE == 2 || MODE == 4) out = node_out<2, T>(acc[c], own[c], B[id], D[id], omega);
+    else out = node_out<3, T>(T(0), T(0), B[id], D[id], omega);
+    Y[id] = out;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void sm_restrict(const Dims& df, const Dims& dc, int node, const T* rf,
                                             T* rc, const uint8_t* fixed_c) {
@@ -1014,10 +1098,11 @@ __global__ void __launch_bounds__(tail1_threads<T>(), 1)
   if (tid == 0) {
     mbar_init(bar);
     unsigned bytes = 0;
-    for (int k = 0; k < L; ++k) bytes += (unsigned)(64 * A.d[k].elems() * sizeof(T));
+    for (int k = 0; k < L; ++k) bytes += (unsigned)(kAemStride * A.d[k].elems() * sizeof(T));
     mbar_expect_tx(bar, bytes);
     for (int k = 0; k < L; ++k)
-      bulk_g2s(smem_addr(sm + A.off_m[k]), A.Ae[k], (unsigned)(64 * A.d[k].elems() * sizeof(T)),
+      bulk_g2s(smem_addr(sm + A.off_m[k]), A.Aem[k],
+               (unsigned)(kAemStride * A.d[k].elems() * sizeof(T)),
                bar);
   }
 #pragma unroll 1
@@ -1062,14 +1147,14 @@ __global__ void __launch_bounds__(tail1_threads<T>(), 1)
     T* o = reinterpret_cast<T*>(sm + A.off_t[k]);
     if (A.nu1 >= 2) {  // the first two sweeps in one phase
       for (int nd = tid; nd < nodes; nd += nt)
-        sm_apply<4>(d, nd, M, SmJac0<T>{B, D, F, A.omega}, B, D, F, o, A.omega);
+        sm_apply_em<4>(d, nd, M, SmJac0<T>{B, D, F, A.omega}, B, D, F, o, A.omega);
       __syncthreads();
       T* tmp = c;
       c = o;
       o = tmp;
       for (int it = 2; it < A.nu1; ++it) {
         for (int nd = tid; nd < nodes; nd += nt)
-          sm_apply<2>(d, nd, M, SmVec<T>{c}, B, D, F, o, A.omega);
+          sm_apply_em<2>(d, nd, M, SmVec<T>{c}, B, D, F, o, A.omega);
         __syncthreads();
         tmp = c;
         c = o;
@@ -1077,14 +1162,14 @@ __global__ void __launch_bounds__(tail1_threads<T>(), 1)
       }
     } else if (A.nu1 == 1) {
       for (int nd = tid; nd < nodes; nd += nt)
-        sm_apply<3>(d, nd, M, SmVec<T>{c}, B, D, F, c, A.omega);
+        sm_apply_em<3>(d, nd, M, SmVec<T>{c}, B, D, F, c, A.omega);
       __syncthreads();
     } else {
       for (int q = tid; q < n; q += nt) c[q] = T(0);
       __syncthreads();
     }
     for (int nd = tid; nd < nodes; nd += nt)
-      sm_apply<1>(d, nd, M, SmVec<T>{c}, B, D, F, o, A.omega);
+      sm_apply_em<1>(d, nd, M, SmVec<T>{c}, B, D, F, o, A.omega);
     __syncthreads();
     const Dims dc = A.d[k + 1];
     T* bc = reinterpret_cast<T*>(sm + A.off_b[k + 1]);
@@ -1126,7 +1211,7 @@ __global__ void __launch_bounds__(tail1_threads<T>(), 1)
     __syncthreads();
     for (int it = 0; it < A.nu2; ++it) {
       for (int nd = tid; nd < nodes; nd += nt)
-        sm_apply<2>(d, nd, M, SmVec<T>{c}, B, D, F, o, A.omega);
+        sm_apply_em<2>(d, nd, M, SmVec<T>{c}, B, D, F, o, A.omega);
       __syncthreads();
       T* tmp = c;
       c = o;
@@ -1484,7 +1569,10 @@ bool tail1_layout(TailArgs<T>& a) {
     const unsigned long long m = (unsigned long long)a.d[k].elems();
     const bool coarsest = (k == a.nl - 1);
     a.off_m[k] = (unsigned)off;
-    if (!coarsest) off += align16u(64ull * m * sizeof(T));
+    if (!coarsest) {
+      if (!a.Aem[k]) return false;  // (no element-major copy of this level)
+      off += align16u((unsigned long long)kAemStride * m * sizeof(T));
+    }
     a.off_z[k] = (unsigned)off;
     off += align16u(n * sizeof(T));
     a.off_t[k] = (unsigned)off;
@@ -1503,6 +1591,26 @@ bool tail1_layout(TailArgs<T>& a) {
 }
 template bool tail1_layout<float>(TailArgs<float>&);
 template bool tail1_layout<double>(TailArgs<double>&);
+
+// Element-major copy of entry-major element matrices: Aem[e * kAemStride + r] = Ae[r * m + e]
+// (r < 64; the 4 padding entries are not written and never read).
+template <typename T>
+__global__ void k_pack_element_major(long long m, const T* __restrict__ Ae, T* __restrict__ Aem) {
+  pdl_prologue();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m * 64) return;
+  const long long r = i / m, e = i - r * m;
+  Aem[e * kAemStride + r] = Ae[i];
+}
+
+template <typename T>
+cudaError_t launch_pack_element_major(long long m, const T* Ae, T* Aem, cudaStream_t st) {
+  topo::launch(k_pack_element_major<T>, blocks_for(m * 64), kThreads, 0, st, m, Ae, Aem);
+  return cudaGetLastError();
+}
+template cudaError_t launch_pack_element_major<float>(long long, const float*, float*, cudaStream_t);
+template cudaError_t launch_pack_element_major<double>(long long, const double*, double*,
+                                                       cudaStream_t);
 
 template <typename T>
 cudaError_t launch_vcycle_tail1(const TailArgs<T>& a, int nrhs, const CgScalars* sc,

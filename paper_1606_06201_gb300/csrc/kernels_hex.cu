@@ -736,6 +736,165 @@ __global__ void __launch_bounds__(512) k_hex_tile_sweep(Dims d, HexTile tl, HexK
   }
 }
 
+
+// ---- Tensor-core form of the dense tile sweep (evaluation) ----------------------------------
+// The element rows of K0 times the element vectors as a warp-level matrix product on the tensor
+// cores: for the 32 elements of a warp, T[24 x 32] = K0[24 x 24] V[24 x 32] with mma.sync
+// m16n8k8 in TF32, K0 and V split into TF32 high and low parts and the three products hi hi,
+// hi lo, lo hi accumulated in FP32 (about the accuracy of FP32 products; other roundings than
+// the FMA chains of the dense form).  Rows 24..31 of the second M tile are zero.  The element
+// vectors reach the B fragments through a per-warp shared-memory transpose (stride 40 words:
+// the eight rows of a fragment fall in distinct banks); the products go to the force buffer of
+// the tile skeleton, and the node phase is that of the dense form (x_e t added by FMA).
+__device__ __forceinline__ unsigned tf32_rna(float f) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float c[4], const unsigned a[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+constexpr int kTcStride = 40;  // words per row of the per-warp transpose buffer
+
+template <int MODE>
+__global__ void __launch_bounds__(512) k_hex_tile_sweep_tc(Dims d, HexTile tl,
+                                                           const float* __restrict__ K0,
+                                                           const float* __restrict__ x,
+                                                           const float* __restrict__ v,
+                                                           const float* __restrict__ b,
+                                                           float* __restrict__ y,
+                                                           const float* __restrict__ invd,
+                                                           float omega,
+                                                           const uint8_t* __restrict__ fixed,
+                                                           const CgScalars* __restrict__ sc) {
+  pdl_prologue();
+  const int rhs = blockIdx.z;
+  if (sc && sc[rhs].done) return;
+  extern __shared__ float4 hex_tile_raw[];
+  const int TT = tl.tx * tl.ty;
+  float* F = reinterpret_cast<float*>(hex_tile_raw);  // [2][24][TT]
+  float* X = F + 2 * 24 * TT;                          // [2][TT]
+  float* Vs = X + 2 * TT;                              // [warps][24][kTcStride]
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int gid = lane >> 2, tig = lane & 3;
+  float* Vw = Vs + warp * 24 * kTcStride;
+  // A fragments of K0 (hi, lo): m tile mt (rows 16 mt + gid, + 8), k step ks (cols 8 ks + tig, + 4)
+  unsigned ah[2][3][4], al[2][3][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int ks = 0; ks < 3; ++ks)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int row = 16 * mt + gid + ((r & 1) ? 8 : 0), col = 8 * ks + tig + ((r & 2) ? 4 : 0);
+        const float a = row < 24 ? __ldg(K0 + row * 24 + col) : 0.0f;
+        ah[mt][ks][r] = tf32_rna(a);
+        al[mt][ks][r] = tf32_rna(a - __uint_as_float(ah[mt][ks][r]));
+      }
+  const int tx = t % tl.tx, ty = t / tl.tx;
+  const int bx = blockIdx.x % tl.tiles_x, by = blockIdx.x / tl.tiles_x;
+  const int ex = bx * (tl.tx - 1) - 1 + tx, ey = by * (tl.ty - 1) - 1 + ty;
+  const int nnx = d.nx + 1, nny = d.ny + 1, nnz = d.nz + 1;
+  const int k0 = blockIdx.y * tl.cz, k1 = min(k0 + tl.cz, nnz);
+  const long long n = d.nodes() * 3;
+  v += rhs * n;
+  y += rhs * n;
+  if (MODE != 0) b += rhs * n;
+  const bool e_xy = ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny;
+  const bool own = tx >= 1 && ty >= 1 && ex < nnx && ey < nny;
+  float acc[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll 1
+  for (int ez = k0 - 1; ez < k1; ++ez) {
+    const int buf = (ez - k0 + 1) & 1;
+    float* Fb = F + (size_t)buf * 24 * TT;
+    const bool live = e_xy && ez >= 0 && ez < d.nz;
+    // the element vector of this lane (zeros for no element) into the warp's transpose buffer
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      long long nid = 0;
+      if (live)
+        nid = TOPO_IDX((ex + hx_ox(a)) + (long long)nnx * ((ey + hx_oy(a)) + (long long)nny * (ez + hx_oz(a))),
+                       d.nodes());
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Vw[(a * 3 + c) * kTcStride + lane] = live ? __ldg(v + 3 * nid + c) : 0.0f;
+    }
+    if (live) X[buf * TT + t] = __ldg(x + ex + (long long)d.nx * (ey + (long long)d.ny * ez));
+    __syncwarp();
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      float cacc[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
+#pragma unroll
+      for (int ks = 0; ks < 3; ++ks) {
+        const float v0 = Vw[(8 * ks + tig) * kTcStride + 8 * nt + gid];
+        const float v1 = Vw[(8 * ks + tig + 4) * kTcStride + 8 * nt + gid];
+        const unsigned bh0 = tf32_rna(v0), bh1 = tf32_rna(v1);
+        const unsigned bl0 = tf32_rna(v0 - __uint_as_float(bh0)),
+                       bl1 = tf32_rna(v1 - __uint_as_float(bh1));
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          mma_tf32(cacc[mt], al[mt][ks], bh0, bh1);
+          mma_tf32(cacc[mt], ah[mt][ks], bl0, bl1);
+          mma_tf32(cacc[mt], ah[mt][ks], bh0, bh1);
+        }
+      }
+      // D (row 16 mt + gid (+ 8), element 8 nt + 2 tig (+ 1)) into the force buffer
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int row = 16 * mt + gid + ((r & 2) ? 8 : 0);
+          const int el = 32 * warp + 8 * nt + 2 * tig + (r & 1);
+          if (row < 24) Fb[row * TT + el] = cacc[mt][r];
+        }
+    }
+    __syncthreads();
+    if (own) {
+      const bool lay = ez >= 0 && ez < d.nz;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int dz = 1 - half;
+        if (half == 0 && ez < k0) continue;
+        if (half == 1 && ez + 1 >= k1) continue;
+        if (lay) {
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            const int dx = s & 1, dy = s >> 1;
+            const int gx = ex - 1 + dx, gy = ey - 1 + dy;
+            if (gx < 0 || gx >= d.nx || gy < 0 || gy >= d.ny) continue;
+            const int te = TOPO_IDX(t - (1 - dx) - (1 - dy) * tl.tx, TT);
+            const int loc = tile_loc(dx, dy, dz);
+            const float xe = X[buf * TT + te];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[c] = fmaf(xe, Fb[(loc * 3 + c) * TT + te], acc[c]);
+          }
+        }
+        if (half == 0) {
+          const long long node = ex + (long long)nnx * (ey + (long long)nny * ez);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const long long id = 3 * node + c;
+            if (!TOPO_IN(id, n)) continue;
+            float out;
+            if (fixed[id]) out = 0.0f;
+            else if (MODE == 0) out = acc[c];
+            else if (MODE == 1) out = node_out<1, float>(acc[c], 0.0f, __ldg(b + id), 0.0f, omega);
+            else out = node_out<2, float>(acc[c], __ldg(v + id), __ldg(b + id), invd[id], omega);
+            y[id] = out;
+            acc[c] = 0.0f;
+          }
+        }
+      }
+    }
+    __syncwarp();  // (the transpose buffer is rewritten by the next layer)
+  }
+}
+
 }  // namespace
 
 bool hex_coefficients(const double* K0, HexCoef& c) {
@@ -900,6 +1059,11 @@ cudaError_t prepare_hex_tile_kernels() {
   TOPO_HT_PREP(double, 1)
   TOPO_HT_PREP(double, 2)
 #undef TOPO_HT_PREP
+  const size_t tc_smem = (2 * 24 * kHexTileSweepThreads + 2 * kHexTileSweepThreads +
+                          (kHexTileSweepThreads / 32) * 24 * kTcStride) * sizeof(float);
+  if (e == cudaSuccess) e = hex_tile_smem(k_hex_tile_sweep_tc<0>, tc_smem);
+  if (e == cudaSuccess) e = hex_tile_smem(k_hex_tile_sweep_tc<1>, tc_smem);
+  if (e == cudaSuccess) e = hex_tile_smem(k_hex_tile_sweep_tc<2>, tc_smem);
   return e;
 }
 
@@ -925,15 +1089,34 @@ cudaError_t launch_hex_tile_apply_dot(const Dims& d, const HexCoef& c, const voi
 }
 
 template <typename T>
-cudaError_t launch_hex_tile_sweep(const Dims& d, int mode, bool dense, const HexCoef& c,
+cudaError_t launch_hex_tile_sweep(const Dims& d, int mode, int form, const HexCoef& c,
                                   const T* K0, const T* x, const T* v, const T* b, T* y,
                                   const T* invd, T omega, const uint8_t* fixed, int nrhs,
                                   const CgScalars* sc, cudaStream_t st) {
+  const bool dense = form == 1;
   const int maxt = sizeof(T) == 8 ? 256 : kHexTileSweepThreads;
   const HexTile tl = hex_tile_plan(d, nrhs, maxt, 152 * 4);
   if (tl.tx == 0) return cudaErrorInvalidConfiguration;
   const dim3 grid(tl.tiles_x * tl.tiles_y, tl.zchunks, nrhs);
   const int TT = tl.tx * tl.ty;
+  if constexpr (sizeof(T) == 4) {
+    if (form == 2) {  // the tensor-core form
+      const size_t smem = (size_t)(2 * 24 * TT + 2 * TT + (TT / 32) * 24 * kTcStride) * sizeof(float);
+      if (mode == 0)
+        topo::launch(k_hex_tile_sweep_tc<0>, grid, TT, smem, st, d, tl, K0, x, v, b, y, invd, omega,
+                     fixed, sc);
+      else if (mode == 1)
+        topo::launch(k_hex_tile_sweep_tc<1>, grid, TT, smem, st, d, tl, K0, x, v, b, y, invd, omega,
+                     fixed, sc);
+      else if (mode == 2)
+        topo::launch(k_hex_tile_sweep_tc<2>, grid, TT, smem, st, d, tl, K0, x, v, b, y, invd, omega,
+                     fixed, sc);
+      else
+        return cudaErrorInvalidValue;
+      return cudaGetLastError();
+    }
+  }
+  if (form == 2) return cudaErrorInvalidValue;  // (FP32 only)
   const size_t smem = (size_t)(2 * 24 * TT + (dense ? 2 * TT + 576 : 0)) * sizeof(T);
   const HexK<T> k{(T)c.a, (T)c.b, (T)c.s, (T)c.p, (T)c.q, (T)c.d, (T)c.e, (T)c.h};
 #define TOPO_HT(MODE, DENSE)                                                                     \
@@ -954,12 +1137,12 @@ cudaError_t launch_hex_tile_sweep(const Dims& d, int mode, bool dense, const Hex
   return cudaGetLastError();
 }
 
-template cudaError_t launch_hex_tile_sweep<float>(const Dims&, int, bool, const HexCoef&,
+template cudaError_t launch_hex_tile_sweep<float>(const Dims&, int, int, const HexCoef&,
                                                   const float*, const float*, const float*,
                                                   const float*, float*, const float*, float,
                                                   const uint8_t*, int, const CgScalars*,
                                                   cudaStream_t);
-template cudaError_t launch_hex_tile_sweep<double>(const Dims&, int, bool, const HexCoef&,
+template cudaError_t launch_hex_tile_sweep<double>(const Dims&, int, int, const HexCoef&,
                                                    const double*, const double*, const double*,
                                                    const double*, double*, const double*, double,
                                                    const uint8_t*, int, const CgScalars*,

@@ -412,6 +412,12 @@ cudaError_t q1_smooth_beta(const topo_solver* s, int nx, int ny, const TV* x, co
 // Operator application on level k (mode as launch_apply): the warp-sweep Q1 kernels on the 2D
 // finest level, the matrix-free first coarse level in mixed precision, the Z operator (element
 // rank-one terms and lambda row) for IP systems, the generic element-matrix kernels elsewhere.
+// Whether a level keeps an element-major copy of its V-cycle matrices for the single-block deep
+// tail: 2D K systems, stored matrices, not the coarsest, at most kTailNodes nodes.
+bool aem_level(int dim, bool arrow, bool coarsest, bool matrix_free, long long nodes) {
+  return dim == 2 && !arrow && !coarsest && !matrix_free && nodes <= kTailNodes;
+}
+
 // TOPO_HEX_OUTER=tile: the 3D outer operator in the tile form (one launch, no force buffer, the
 // same q).  The default is the two-kernel form with the force buffer: on 128 x 64 x 64 with 8
 // right-hand sides the tile form took 848 us per launch against 349 + 200 us for the pair (it
@@ -421,14 +427,16 @@ bool hex_buffered_env() {
   return !(v && std::string(v) == "tile");
 }
 
-// TOPO_HEX_SWEEP=node|dense|wht: the 3D finest V-cycle operator (node-parallel; tile with the
-// rows of K0, the same bits as node-parallel; tile in the Walsh-Hadamard basis, when K0 has its
+// TOPO_HEX_SWEEP=node|dense|tc|wht: the 3D finest V-cycle operator (node-parallel; tile with the
+// rows of K0, the same bits as node-parallel; the same product on the tensor cores, 3 x TF32;
+// tile in the Walsh-Hadamard basis, when K0 has its
 // structure: the default, 168 + 157 us against 238 + 201 us per V-cycle on 128 x 64 x 64 with 8
 // right-hand sides; the dense tile form was the slowest).
 int hex_sweep_env(bool hex_ok) {
   const char* v = std::getenv("TOPO_HEX_SWEEP");
   const std::string w = v ? v : "";
   if (w == "dense") return 1;
+  if (w == "tc") return 3;  // the dense product on the tensor cores (FP32 V-cycle; FP64: dense)
   if (w == "node" || !hex_ok) return 0;
   return 2;
 }
@@ -481,7 +489,8 @@ topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* 
     return TOPO_OK;
   }
   if (k == 0 && s->hex_sweep && mode <= 2) {  // 3D finest level: the tile form
-    TOPO_CUDA(launch_hex_tile_sweep<TV>(lv.d, mode, s->hex_sweep == 1, s->hex, Prec<TV>::K0(s),
+    const int form = s->hex_sweep == 2 ? 0 : (s->hex_sweep == 3 && sizeof(TV) == 4 ? 2 : 1);
+    TOPO_CUDA(launch_hex_tile_sweep<TV>(lv.d, mode, form, s->hex, Prec<TV>::K0(s),
                                         Prec<TV>::x(s), v, b, y, Prec<TV>::invd(lv), omega,
                                         lv.fixed, nrhs, sc, s->st));
     return TOPO_OK;
@@ -544,6 +553,7 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
       Level& l = s->L[k + j];
       a.d[j] = l.d;
       a.Ae[j] = Prec<TV>::Ae(l);
+      a.Aem[j] = (const TV*)l.Aem;
       a.invd[j] = Prec<TV>::invd(l);
       a.fixed[j] = l.fixed;
       a.b[j] = j == 0 ? const_cast<TV*>(b) : (TV*)l.b;
@@ -648,7 +658,7 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
     if (fine) TOPO_TRY(prof_mark(s, 3, 1));
   }
   TV* zc = nullptr;
-  const int sub_kind = (k == 0) ? 6 : (k == 1 ? 7 : -1);  // levels >= 1, levels >= 2
+  const int sub_kind = k <= 5 ? 6 + k : -1;  // levels >= k + 1
   if (sub_kind > 0) TOPO_TRY(prof_mark(s, sub_kind, 0));
   TOPO_TRY(vcycle<TV>(s, k + 1, (const TV*)lc.b, &zc, sc, false));
   if (sub_kind > 0) TOPO_TRY(prof_mark(s, sub_kind, 1));
@@ -1101,6 +1111,14 @@ topo_status enqueue_build(topo_solver* s, bool warm = false) {
   }
   if (s->arrow && mixed)
     for (int k = 0; k < nl; ++k) TOPO_CUDA(launch_convert_d2f(s->L[k].w, s->L[k].w32, s->L[k].n, st));
+  for (int k = 1; k < nl - 1; ++k) {  // element-major copies for the single-block deep tail
+    Level& lv = s->L[k];
+    if (!lv.Aem) continue;
+    if (mixed && lv.Ae32)
+      TOPO_CUDA(launch_pack_element_major<float>(lv.m, lv.Ae32, (float*)lv.Aem, st));
+    else if (!mixed && lv.Ae)
+      TOPO_CUDA(launch_pack_element_major<double>(lv.m, lv.Ae, (double*)lv.Aem, st));
+  }
   Level& lc = s->L[nl - 1];
   const bool fine_coarsest = (nl == 1);
   TOPO_CUDA(launch_assemble_dense(lc.d, s->K0, fine_coarsest ? s->x : nullptr, lc.Ae, lc.fixed,
@@ -1269,6 +1287,9 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
       if (!l1_matrix_free && (!s->h32 || coarsest)) TOPO_TRY(s->alloc(&lv.Ae, lv.m * ne * ne));
       if (s->prec == TOPO_MIXED && !coarsest && !l1_matrix_free)
         TOPO_TRY(s->alloc(&lv.Ae32, lv.m * ne * ne));
+      // element-major copy for the single-block deep tail (a level it may start at or cover)
+      if (aem_level(s->dim, arrow, coarsest, l1_matrix_free, dk.nodes()))
+        TOPO_TRY(s->alloc((char**)&lv.Aem, vbytes * lv.m * kAemStride));
     }
     if (arrow) {
       TOPO_TRY(s->alloc(&lv.w, lv.n));
@@ -1477,6 +1498,7 @@ topo_status plan_bytes(const topo_solver_desc* d, bool arrow, size_t* out) {
       const bool l1_matrix_free = k == 1 && l1_free;
       if (!l1_matrix_free && (!h32 || coarsest)) add(m * ne * ne, sizeof(double));
       if (mixed && !coarsest && !l1_matrix_free) add(m * ne * ne, sizeof(float));
+      if (aem_level(dim, arrow, coarsest, l1_matrix_free, dk.nodes())) add(vbytes * m * kAemStride, 1);
     }
     if (arrow) {
       add(n, sizeof(double));
@@ -1705,7 +1727,7 @@ topo_status topo_get_profile(const topo_solver* s, double* operator_ms_total, lo
 topo_status topo_get_profile_kernel(const topo_solver* s, int kind, double* ms_total,
                                     long long* count) {
   if (!s || !ms_total || !count || kind < 0 || kind >= topo_solver::kProfKinds) {
-    set_error("topo_get_profile_kernel: null argument or kind outside 0..7");
+    set_error("topo_get_profile_kernel: null argument or kind outside 0..11");
     return TOPO_E_INVALID_ARG;
   }
   *ms_total = s->prof_ms[kind];

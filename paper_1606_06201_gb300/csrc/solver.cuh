@@ -90,7 +90,8 @@ struct topo_solver {
   double* hexR = nullptr;                 // its element forces (24 x elems x nrhs)
   bool hex_buffered = true;               // the two-kernel form with hexR (else the tile form)
   int hex_sweep = 0;                      // 3D finest V-cycle operator: 0 node-parallel,
-                                          // 1 tile dense (same bits as 0), 2 tile Walsh-Hadamard
+                                          // 1 tile dense (same bits as 0), 2 tile Walsh-Hadamard,
+                                          // 3 tile dense on the tensor cores (3 x TF32)
   int outer_df = 0;                       // outer operator in float-pair arithmetic (1) or FP64
   bool tail_ok = false;                   // the fused deep-level kernel can run on this device
   bool fuse_on = true;                    // fused V-cycle kernels in use (topo_set_vcycle_fusion)
@@ -115,7 +116,7 @@ struct topo_solver {
   unsigned prof_mask = 0;                 // profiled kinds (bit k = kind k)
   // Profiling: event pairs per (kind, iteration slot) of the block graph; kinds as
   // topo_get_profile_kernel (0 outer operator, 1-4 finest-level V-cycle kernels, 5-7 V-cycle parts).
-  static constexpr int kProfKinds = 8;
+  static constexpr int kProfKinds = 12;
   std::vector<cudaEvent_t> prof_ev;
   double prof_ms[kProfKinds] = {};
   long long prof_count[kProfKinds] = {};

@@ -13,6 +13,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/topo.h"
+#include "pairs.cuh"
 
 namespace topo {
 
@@ -98,6 +99,8 @@ struct Level {
   uint8_t* fixed = nullptr;        // [n] 1 = fixed DOF
   double* Ae = nullptr;            // coarse levels: element matrices, entry-major [ne*ne][m] FP64
   float* Ae32 = nullptr;           // FP32 copy (mixed precision)
+  void* Aem = nullptr;             // the V-cycle's element matrices element-major, kAemStride
+                                   // entries per element (levels of the single-block deep tail)
   double* invd = nullptr;          // 1 / diag(A) [n] (1 on fixed DOFs)
   float* invd32 = nullptr;
   double* omega_dev = nullptr;     // per-level Jacobi damping (adaptive damping only)
@@ -263,7 +266,7 @@ __device__ __forceinline__ double dense_row_dot(int n, const double* __restrict_
     T bk;
     if constexpr (COH) bk = __ldcg(b + k);
     else bk = b[k];
-    s = fma(row[k], (double)bk, s);
+    s = fma(row[k], double_of(bk), s);  // (integer widening: no FP64 conversion instruction)
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -299,6 +302,7 @@ struct TailArgs {
   const double* Ainv;
   Dims d[kTailMax];
   const T* Ae[kTailMax];
+  const T* Aem[kTailMax];  // element-major copies (single-block form)
   const T* invd[kTailMax];
   const uint8_t* fixed[kTailMax];
   T* b[kTailMax];  // b[0]: the restricted residual from the level above
@@ -312,7 +316,17 @@ struct TailArgs {
   unsigned smem;
   unsigned long long wait_ns;  // bound of the first wait for the bulk copies (0: expire at once)
 };
-constexpr int kTail1Threads = 512;
+// Threads of the single-block deep tail (FP32; FP64 takes half): 1024 measured faster than 512
+// once the node rows fit in 64 registers (see the kernel).
+#ifndef TOPO_TAIL1_THREADS
+#define TOPO_TAIL1_THREADS 1024
+#endif
+constexpr int kTail1Threads = TOPO_TAIL1_THREADS;
+// Entries per element of the element-major copies of the deep levels' 8 x 8 matrices: 64 padded
+// to 68, so that 16-byte loads of consecutive elements fall in distinct shared-memory banks.
+constexpr int kAemStride = 68;
+template <typename T>
+cudaError_t launch_pack_element_major(long long m, const T* Ae, T* Aem, cudaStream_t st);
 
 inline unsigned blocks_for(long long n, int threads = kThreads) {
   return (unsigned)((n + threads - 1) / threads);
@@ -441,10 +455,11 @@ cudaError_t launch_hex_tile_apply_dot(const Dims& d, const HexCoef& c, const voi
                                       const double* v, double* y, const uint8_t* fixed, int nrhs,
                                       double* partials, unsigned* counters, CgScalars* sc,
                                       cudaStream_t st);
-// Finest-level 3D V-cycle operator (modes 0-2 of launch_apply) in the tile form: `dense` with the
-// element rows of K0 (the bits of the node-parallel kernel), otherwise in the Walsh-Hadamard basis.
+// Finest-level 3D V-cycle operator (modes 0-2 of launch_apply) in the tile form: form 0 in the
+// Walsh-Hadamard basis, 1 with the element rows of K0 (the bits of the node-parallel kernel), 2 the
+// same product on the tensor cores (3 x TF32, FP32 vectors only).
 template <typename T>
-cudaError_t launch_hex_tile_sweep(const Dims& d, int mode, bool dense, const HexCoef& c,
+cudaError_t launch_hex_tile_sweep(const Dims& d, int mode, int form, const HexCoef& c,
                                   const T* K0, const T* x, const T* v, const T* b, T* y,
                                   const T* invd, T omega, const uint8_t* fixed, int nrhs,
                                   const CgScalars* sc, cudaStream_t st);

@@ -596,7 +596,8 @@ class Solver:
 
     PROFILE_KINDS = ("outer_operator", "fine_smoothing_sweep", "fine_residual",
                      "fine_restriction", "fine_prolongation", "vcycle", "vcycle_levels_ge1",
-                     "vcycle_levels_ge2")
+                     "vcycle_levels_ge2", "vcycle_levels_ge3", "vcycle_levels_ge4",
+                     "vcycle_levels_ge5", "vcycle_levels_ge6")
 
     def profile_kernel(self, kind):
         """(summed ms, launches) of one profiled kernel kind (index into PROFILE_KINDS)."""

@@ -5,8 +5,9 @@ ragged edge in every direction, with several right-hand sides:
 * the V-cycle operator with the element rows of K0 (TOPO_HEX_SWEEP=dense) has the arithmetic of
   the node-parallel kernel (TOPO_HEX_SWEEP=node): V-cycle outputs and whole solves agree bit for
   bit;
-* the Walsh-Hadamard V-cycle operator (the default) is the same operator with other roundings:
-  the solves reach the exact solution of the oracle's sparse matrix;
+* the Walsh-Hadamard V-cycle operator (the default), and the dense one on the tensor cores
+  (TOPO_HEX_SWEEP=tc, 3 x TF32), are the same operator with other roundings: the solves reach the
+  node-parallel solutions and the exact solution of the oracle's sparse matrix;
 * the tile outer operator (TOPO_HEX_OUTER=tile) forms the buffered kernels' q; its p^T q sums in
   another order, so solves agree with the buffered form (the default) to rounding, with the same
   iteration counts.
@@ -66,12 +67,15 @@ def test_dense_tile_sweep_gives_the_node_parallel_bits(shape, nrhs, precision, m
     assert it0 == it1
 
 
+@pytest.mark.parametrize("form", ["wht", "tc"])
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("shape,nrhs", SHAPES)
 def test_walsh_hadamard_tile_sweep_agrees_with_the_node_parallel_operator(shape, nrhs, precision,
-                                                                          monkeypatch):
+                                                                          form, monkeypatch):
+    """(form tc: the dense element product on the tensor cores, 3 x TF32, in the FP32 V-cycle;
+    the FP64 V-cycle keeps FMA chains.)"""
     tol = 1e-11 if precision == 0 else 1e-10
-    U, it = _solve(monkeypatch, {}, shape, nrhs, precision, tol=tol)
+    U, it = _solve(monkeypatch, {"TOPO_HEX_SWEEP": form}, shape, nrhs, precision, tol=tol)
     Un, itn = _solve(monkeypatch, {"TOPO_HEX_SWEEP": "node"}, shape, nrhs, precision, tol=tol)
     assert abs(it - itn) <= 1
     assert rel_err(U, Un) <= 1e-8

@@ -427,10 +427,13 @@ def test_profiling_times_every_kernel_kind_and_keeps_results():
     u2, info2 = s.solve(f, tol=1e-9)
     assert torch.equal(u0, u2) and info0.iterations == info2.iterations
     fused_restriction = topo.Solver.PROFILE_KINDS.index("fine_restriction")
+    ge3 = topo.Solver.PROFILE_KINDS.index("vcycle_levels_ge3")
     for k in range(len(topo.Solver.PROFILE_KINDS)):
         ms, cnt = s.profile_kernel(k)
         if k == fused_restriction:  # one kernel with the residual (timed as fine_residual)
             assert cnt == 0, (k, ms, cnt)
+        elif k >= ge3:  # levels >= 3 of 4: inside the fused deep part; none beyond
+            assert cnt in (0, info2.iterations) and (k == ge3 or cnt == 0), (k, ms, cnt)
         else:
             assert cnt == info2.iterations and ms > 0.0, (k, ms, cnt)
     assert s.profile() == s.profile_kernel(0)
@@ -440,7 +443,10 @@ def test_profiling_times_every_kernel_kind_and_keeps_results():
     assert torch.equal(u0, u3) and info0.iterations == info3.iterations
     for k in range(len(topo.Solver.PROFILE_KINDS)):
         ms, cnt = s.profile_kernel(k)
-        assert cnt == info3.iterations and ms > 0.0, (k, ms, cnt)
+        if k > ge3:  # levels >= 4 of a 4-level hierarchy: none
+            assert cnt == 0, (k, ms, cnt)
+        else:
+            assert cnt == info3.iterations and ms > 0.0, (k, ms, cnt)
     with pytest.raises(topo.TopoError):
         s.set_profiling_mask(1 << len(topo.Solver.PROFILE_KINDS))
     with pytest.raises(topo.TopoError):
