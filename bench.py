@@ -210,6 +210,8 @@ def main():
     ap.add_argument("--no-ip", action="store_true", help="skip the 512x256 IP/OC wall-time runs")
     ap.add_argument("--outer-fp64", action="store_true",
                     help="mixed solver with the FP64 outer operator instead of float pairs")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="--only batched3d: damped Jacobi omega=0.6, nu=1 without the autotuner")
     ap.add_argument("--only", choices=["mixed", "fp64", "batched3d", "ip", "simp", "oc_accuracy"],
                     default=None,
                     help="run one solver configuration only (for profiler launch lists); no JSON "
@@ -311,7 +313,7 @@ def main():
         return dict(ms=ms, iters=iters, res=res, launches=launches, prof=prof, kinds=kinds,
                     solve_ms=solve_ms)
 
-    def batched_3d_run(steps=3, warmup=3):
+    def batched_3d_run(steps=3, warmup=3, tune=True):
         """128x64x64 hex grid (1.6M DOFs, 5 levels), 8 unit point loads on the x = max face as one
         batched mixed solve per step (hierarchy build + PCG to 1e-8 for all 8) with the
         autotuner's smoother (damped Jacobi omega x nu, Chebyshev degree); DOF*iterations summed
@@ -322,9 +324,12 @@ def main():
         x4 = torch.as_tensor(c4["x"], device=dev)
         f4 = torch.as_tensor(c4["f"], device=dev)
         t_tune = time.perf_counter()
-        tuned = autotune.autotune(128, 64, 64, c4["fixed"], x4, f4, 5, precision=topo.MIXED,
-                                  nrhs=8, tol=TOL, sweeps=(1, 2, 3), cheb_degrees=(1, 2, 3),
-                                  reps=1)
+        if tune:
+            tuned = autotune.autotune(128, 64, 64, c4["fixed"], x4, f4, 5, precision=topo.MIXED,
+                                      nrhs=8, tol=TOL, sweeps=(1, 2, 3), cheb_degrees=(1, 2, 3),
+                                      reps=1)
+        else:  # (--no-autotune: the setting the autotuner picks on this workload, for profiling)
+            tuned = {"smoother": "jacobi", "omega": 0.6, "nu": 1, "rows": 0, "tried": 0}
         t_tune = time.perf_counter() - t_tune
         s4 = autotune.solver_for(tuned, 128, 64, 64, c4["fixed"], 5, precision=topo.MIXED, nrhs=8)
         u4 = torch.zeros_like(f4)
@@ -540,7 +545,7 @@ def main():
         print(json.dumps(oc_accuracy_study()), flush=True)
         return 0
     if args.only == "batched3d":
-        r = batched_3d_run(args.steps, args.warmup)
+        r = batched_3d_run(args.steps, args.warmup, tune=not args.no_autotune)
         print("only=batched3d ms_per_step=%.3f iterations=%.1f" % (r["ms_per_step"],
                                                                   r["iterations_per_solve"]))
         return 0

@@ -784,8 +784,13 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_vcycle_tail(const __grid_co
     T* z = A.z[L] + (long long)rhs * A.nc;
     const int lane = threadIdx.x & 31;
     for (long long row = t0 >> 5; row < A.nc; row += ts >> 5) {
-      const double v = dense_row_dot<true>(A.nc, A.Ainv + row * A.nc, b, lane);
-      if (lane == 0) z[row] = (T)v;
+      if constexpr (sizeof(T) == 4) {
+        const f2 v = dense_row_dot_df<true>(A.nc, A.AinvDF + row * A.nc, b, lane);
+        if (lane == 0) z[row] = __fadd_rn(v.h, v.l);
+      } else {
+        const double v = dense_row_dot<true>(A.nc, A.Ainv + row * A.nc, b, lane);
+        if (lane == 0) z[row] = (T)v;
+      }
     }
     cluster_barrier();
     res[L] = z;
@@ -843,6 +848,13 @@ struct SmJac0 {  // omega invd b, as VJac0 forms it
 // Bulk copies global -> shared by the tensor memory accelerator, completing on an mbarrier.
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
+}
+// Asynchronous 4- or 8-byte global -> shared copy (completes at cp.async.wait_all).
+template <int BYTES>
+__device__ __forceinline__ void cp_async_g2s(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "n"(BYTES)
+               : "memory");
 }
 __device__ __forceinline__ void mbar_init(unsigned bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -943,6 +955,10 @@ __device__ __forceinline__ void sm_apply(const Dims& d, int node, const T* M, co
 // element, rows loc*2 and loc*2+1 contiguous: four 16-byte loads per element in FP32) and the
 // 3 x 3 node neighbourhood loaded once (18 values instead of 32).  The values, the FMA chains and
 // their order are those of sm_apply (the same bits).
+// (A coarsest system above kTail1MaxNc DOFs keeps the cluster form: its dense solve, nc^2 FP64
+// multiply-adds, is FP64-bound on one SM - 306 DOFs took 78 us in one block.)
+constexpr int kTail1MaxNc = 128;
+
 template <typename T>
 __device__ __forceinline__ void load16(const T* p, T out[16]) {
   if constexpr (sizeof(T) == 4) {
@@ -1089,8 +1105,10 @@ __global__ void __launch_bounds__(tail1_threads<T>(), 1)
   const int tid = threadIdx.x, nt = blockDim.x;
   const int L = A.nl - 1;  // the coarsest, relative
   // the coarsest inverse is read once per cycle from global memory: bring it to L2 now
-  for (long long q = (long long)tid * 16; q < (long long)A.nc * A.nc; q += (long long)nt * 16)
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(A.Ainv + q));
+  const char* ainv = sizeof(T) == 4 ? reinterpret_cast<const char*>(A.AinvDF)
+                                    : reinterpret_cast<const char*>(A.Ainv);  // (8 B per entry)
+  for (long long q = (long long)tid * 128; q < (long long)A.nc * A.nc * 8; q += (long long)nt * 128)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(ainv + q));
   // every fused level's matrices by bulk copies on one barrier, the inverse diagonals, masks and
   // the first level's b by plain loads meanwhile
   uint64_t* bar_p = reinterpret_cast<uint64_t*>(sm + A.off_bar);
@@ -1105,20 +1123,24 @@ __global__ void __launch_bounds__(tail1_threads<T>(), 1)
                (unsigned)(kAemStride * A.d[k].elems() * sizeof(T)),
                bar);
   }
+  // (asynchronous copies, all in flight together: plain loads level by level took 4 us)
 #pragma unroll 1
   for (int k = 0; k < A.nl; ++k) {
     const int n = (int)A.d[k].dofs();
     uint8_t* F = reinterpret_cast<uint8_t*>(sm + A.off_f[k]);
-    for (int i = tid; i < n; i += nt) F[i] = A.fixed[k][i];
+    const int nw4 = n >> 2;  // the mask in 4-byte words, the last n % 4 bytes plainly
+    for (int i = tid; i < nw4; i += nt) cp_async_g2s<4>(F + 4 * i, A.fixed[k] + 4 * i);
+    for (int i = 4 * nw4 + tid; i < n; i += nt) F[i] = A.fixed[k][i];
     if (k == L) continue;
     T* D = reinterpret_cast<T*>(sm + A.off_d[k]);
-    for (int i = tid; i < n; i += nt) D[i] = __ldg(A.invd[k] + i);
+    for (int i = tid; i < n; i += nt) cp_async_g2s<sizeof(T)>(D + i, A.invd[k] + i);
     if (k == 0) {
       T* B = reinterpret_cast<T*>(sm + A.off_b[k]);
       const T* b = A.b[0] + (long long)rhs * n;
-      for (int i = tid; i < n; i += nt) B[i] = b[i];
+      for (int i = tid; i < n; i += nt) cp_async_g2s<sizeof(T)>(B + i, b + i);
     }
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();  // (the barrier is initialised before anyone polls it)
   // every thread polls; the block decides together, so that all or none continue
   if (!__syncthreads_and(mbar_wait0(bar, A.wait_ns) ? 1 : 0)) {
@@ -1178,19 +1200,64 @@ __global__ void __launch_bounds__(tail1_threads<T>(), 1)
     __syncthreads();
     res[k] = c;
   }
-  {  // coarsest level: z = Ainv b, one warp per row
+  {  // coarsest level: z = Ainv b, one warp per row, the sums of dense_row_dot_df (FP32 vectors)
+     // or dense_row_dot (FP64) in their order (the same bits); kRows rows per warp with every
+     // load of a round issued before the first product
     const T* b = reinterpret_cast<const T*>(sm + A.off_b[L]);
     T* z = reinterpret_cast<T*>(sm + A.off_z[L]);
     const int lane = tid & 31, nw = nt >> 5;
-    for (int row = tid >> 5; row < A.nc; row += 2 * nw) {  // two rows in flight per warp
-      const int row2 = row + nw;
-      const double v = dense_row_dot<false>(A.nc, A.Ainv + (long long)row * A.nc, b, lane);
-      const double v2 = row2 < A.nc
-                            ? dense_row_dot<false>(A.nc, A.Ainv + (long long)row2 * A.nc, b, lane)
-                            : 0.0;
-      if (lane == 0) {
-        z[row] = (T)v;
-        if (row2 < A.nc) z[row2] = (T)v2;
+    constexpr int kRows = 3, kPer = kTail1MaxNc / 32;
+    const int nc = A.nc;
+    T bv[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int k = lane + 32 * j;
+      bv[j] = k < nc ? b[k] : T(0);
+    }
+    for (int row0 = tid >> 5; row0 < nc; row0 += kRows * nw) {
+      if constexpr (sizeof(T) == 4) {
+        float2 a[kRows][kPer];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r)
+#pragma unroll
+          for (int j = 0; j < kPer; ++j) {
+            const int row = row0 + r * nw, k = lane + 32 * j;
+            a[r][j] = (row < nc && k < nc) ? __ldg(A.AinvDF + (long long)row * nc + k)
+                                           : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+          const int row = row0 + r * nw;
+          f2 sum = {0.0f, 0.0f};
+#pragma unroll
+          for (int j = 0; j < kPer; ++j)
+            if (lane + 32 * j < nc) sum = df_fma_f(f2{a[r][j].x, a[r][j].y}, bv[j], sum);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1)
+            sum = df_add(sum, f2{__shfl_xor_sync(0xffffffffu, sum.h, o),
+                                 __shfl_xor_sync(0xffffffffu, sum.l, o)});
+          if (lane == 0 && row < nc) z[row] = __fadd_rn(sum.h, sum.l);
+        }
+      } else {
+        double a[kRows][kPer];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r)
+#pragma unroll
+          for (int j = 0; j < kPer; ++j) {
+            const int row = row0 + r * nw, k = lane + 32 * j;
+            a[r][j] = (row < nc && k < nc) ? __ldg(A.Ainv + (long long)row * nc + k) : 0.0;
+          }
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+          const int row = row0 + r * nw;
+          double sum = 0.0;
+#pragma unroll
+          for (int j = 0; j < kPer; ++j)
+            if (lane + 32 * j < nc) sum = fma(a[r][j], double_of(bv[j]), sum);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+          if (lane == 0 && row < nc) z[row] = (T)sum;
+        }
       }
     }
     __syncthreads();
@@ -1556,9 +1623,6 @@ int tail1_smem_limit() {
 unsigned align16u(unsigned long long x) { return (unsigned)((x + 15ull) & ~15ull); }
 }  // namespace
 
-// (A coarsest system above kTail1MaxNc DOFs keeps the cluster form: its dense solve, nc^2 FP64
-// multiply-adds, is FP64-bound on one SM - 306 DOFs took 78 us in one block.)
-constexpr int kTail1MaxNc = 128;
 
 template <typename T>
 bool tail1_layout(TailArgs<T>& a) {

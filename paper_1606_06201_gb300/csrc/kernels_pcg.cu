@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_p(long long n, const TV* __rest
     const TV yi = y[i];
     const double pi = p[i];
     z[i] = fma(alpha, pi, z[i]);
-    p[i] = fma(beta, pi, -double_of(yi));
+    p[i] = fma(beta, pi, -(double)yi);  // (the hardware widening: 19.3 against 23.3 us here)
     if (flexible) y_old[i] = yi;
   }
 }

@@ -10,6 +10,7 @@
 // matrices C_c = P_c^T K0 P_c prepared on the host.
 #include <type_traits>
 
+#include "pairs.cuh"
 #include "topo_internal.cuh"
 
 namespace topo {
@@ -798,9 +799,11 @@ __global__ void k_bgj_copy(int n, int npad, const double* __restrict__ W, double
   Ainv[t] = W[(t / n) * npad + t % n];
 }
 
-// z = A^{-1} b: one warp per row, FP64 accumulation whatever the vector type.
+// z = A^{-1} b: one warp per row; FP64 accumulation for FP64 vectors, float-pair accumulation with
+// Ainv as pairs for FP32 vectors (AinvDF).
 template <typename T>
-__global__ void k_dense_solve(int n, const double* __restrict__ Ainv, const T* __restrict__ b,
+__global__ void k_dense_solve(int n, const double* __restrict__ Ainv,
+                              const float2* __restrict__ AinvDF, const T* __restrict__ b,
                               T* __restrict__ z, const CgScalars* __restrict__ sc) {
   pdl_prologue();
   const int rhs = blockIdx.y;
@@ -810,8 +813,13 @@ __global__ void k_dense_solve(int n, const double* __restrict__ Ainv, const T* _
   if (warp >= n) return;
   b += (long long)rhs * n;
   z += (long long)rhs * n;
-  const double s = dense_row_dot<false>(n, Ainv + (long long)warp * n, b, lane);
-  if (lane == 0) z[warp] = (T)s;
+  if constexpr (sizeof(T) == 4) {
+    const f2 s = dense_row_dot_df<false>(n, AinvDF + (long long)warp * n, b, lane);
+    if (lane == 0) z[warp] = __fadd_rn(s.h, s.l);
+  } else {
+    const double s = dense_row_dot<false>(n, Ainv + (long long)warp * n, b, lane);
+    if (lane == 0) z[warp] = (T)s;
+  }
 }
 
 }  // namespace
@@ -1000,15 +1008,16 @@ cudaError_t launch_cholesky_inverse(int n, double* A, double* Ainv, int* info, c
 }
 
 template <typename T>
-cudaError_t launch_dense_solve(int n, const double* Ainv, const T* b, T* z, int nrhs,
-                               const CgScalars* sc, cudaStream_t st) {
+cudaError_t launch_dense_solve(int n, const double* Ainv, const float2* AinvDF, const T* b, T* z,
+                               int nrhs, const CgScalars* sc, cudaStream_t st) {
+  if (sizeof(T) == 4 && !AinvDF) return cudaErrorInvalidValue;
   dim3 grid(blocks_for((long long)n * 32), nrhs);
-  topo::launch(k_dense_solve<T>, grid, kThreads, 0, st, n, Ainv, b, z, sc);
+  topo::launch(k_dense_solve<T>, grid, kThreads, 0, st, n, Ainv, AinvDF, b, z, sc);
   return cudaGetLastError();
 }
-template cudaError_t launch_dense_solve<double>(int, const double*, const double*, double*, int,
-                                                const CgScalars*, cudaStream_t);
-template cudaError_t launch_dense_solve<float>(int, const double*, const float*, float*, int,
-                                               const CgScalars*, cudaStream_t);
+template cudaError_t launch_dense_solve<double>(int, const double*, const float2*, const double*,
+                                                double*, int, const CgScalars*, cudaStream_t);
+template cudaError_t launch_dense_solve<float>(int, const double*, const float2*, const float*,
+                                               float*, int, const CgScalars*, cudaStream_t);
 
 }  // namespace topo

@@ -533,7 +533,8 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
   const int nrhs = s->nrhs;
   TV* zk = (TV*)lv.z;
   if (k == s->nlev - 1) {
-    TOPO_CUDA(launch_dense_solve<TV>(s->nc + (s->arrow ? 1 : 0), s->Ainv, b, zk, nrhs, sc, s->st));
+    TOPO_CUDA(launch_dense_solve<TV>(s->nc + (s->arrow ? 1 : 0), s->Ainv, s->AinvDF, b, zk, nrhs,
+                                     sc, s->st));
     *result = zk;
     return TOPO_OK;
   }
@@ -548,6 +549,7 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
     a.nc = s->nc;
     a.omega = (TV)s->desc.omega;
     a.Ainv = s->Ainv;
+    a.AinvDF = s->AinvDF;
     a.wait_ns = s->wait_ns;
     for (int j = 0; j < a.nl; ++j) {
       Level& l = s->L[k + j];
@@ -1129,6 +1131,10 @@ topo_status enqueue_build(topo_solver* s, bool warm = false) {
   // Cholesky, whose pivot floor guards the nearly singular Schur complement of the multiplier.
   TOPO_CUDA(launch_cholesky_inverse(s->nc + (s->arrow ? 1 : 0), s->Adense, s->Ainv, s->info, st,
                                     s->Ascratch, s->info + 2, !s->arrow && s->Ascratch != nullptr));
+  if (s->AinvDF) {  // the FP32 V-cycle's coarsest solve reads the inverse as float pairs
+    const long long na = s->nc + (s->arrow ? 1 : 0);
+    TOPO_CUDA(launch_split_df(s->Ainv, s->AinvDF, na * na, st));
+  }
   return TOPO_OK;
 }
 
@@ -1338,6 +1344,7 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   cudaGetLastError();
   TOPO_TRY(s->alloc(&s->Adense, na * na));
   TOPO_TRY(s->alloc(&s->Ainv, na * na));
+  if (s->prec == TOPO_MIXED) TOPO_TRY(s->alloc(&s->AinvDF, na * na));
   TOPO_TRY(s->alloc(&s->info, 4));
   // Newton-Schulz products (small K systems) or the block Gauss-Jordan workspace (larger ones)
   if ((!arrow || na > 128) && coarse_scratch_doubles((int)na))
@@ -1537,6 +1544,7 @@ topo_status plan_bytes(const topo_solver_desc* d, bool arrow, size_t* out) {
   const size_t na = (size_t)nc + (arrow ? 1 : 0);
   add(na * na, sizeof(double));
   add(na * na, sizeof(double));
+  if (mixed) add(na * na, sizeof(float2));
   add(4, sizeof(int));
   if ((!arrow || na > 128) && coarse_scratch_doubles((int)na))
     add(coarse_scratch_doubles((int)na), sizeof(double));

@@ -67,6 +67,7 @@ struct topo_solver {
   int nc = 0;                    // DOFs of the coarsest level
   double* Adense = nullptr;
   double* Ainv = nullptr;
+  float2* AinvDF = nullptr;               // Ainv as float pairs (mixed precision)
   double* Ascratch = nullptr;    // Newton-Schulz products of the coarsest inverse (small n)
   int* info = nullptr;           // [0] coarsest pivot failure, [1] bad density, [2] Newton-Schulz flag
   double *z = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;

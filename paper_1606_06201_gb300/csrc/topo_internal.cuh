@@ -273,6 +273,33 @@ __device__ __forceinline__ double dense_row_dot(int n, const double* __restrict_
   return s;
 }
 
+// The same product for an FP32 V-cycle with Ainv held as float pairs hi + lo (split once per
+// build): pair products and sums on the FP32 pipe (about 48 bits), z rounded to FP32.  The FP64
+// pipe of this part issues two lane operations per clock per SM, so the FP64 form of a 90-row
+// coarsest solve (8,100 multiply-adds and 14,400 butterfly adds) took 8-9 us in one block.
+__device__ __forceinline__ f2 df_fma_f(f2 a, float b, f2 c) {  // a b + c, b a float
+  const float p = __fmul_rn(a.h, b);
+  float e = __fmaf_rn(a.h, b, -p);
+  e = __fmaf_rn(a.l, b, e);
+  return df_add(fast_two_sum(p, e), c);
+}
+template <bool COH>
+__device__ __forceinline__ f2 dense_row_dot_df(int n, const float2* __restrict__ row,
+                                               const float* b, int lane) {
+  f2 s = {0.0f, 0.0f};
+  for (int k = lane; k < n; k += 32) {
+    float bk;
+    if constexpr (COH) bk = __ldcg(b + k);
+    else bk = b[k];
+    const float2 a = row[k];
+    s = df_fma_f(f2{a.x, a.y}, bk, s);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    s = df_add(s, f2{__shfl_xor_sync(0xffffffffu, s.h, o), __shfl_xor_sync(0xffffffffu, s.l, o)});
+  return s;
+}
+
 // Deep levels of the 2D V-cycle fused into one launch (kernels_fe.cu): levels tail_from ..
 // coarsest, run by one thread-block cluster per right-hand side.
 #ifndef TOPO_TAIL_CLUSTER
@@ -300,6 +327,7 @@ struct TailArgs {
   int nc;        // coarsest DOFs (Ainv is nc x nc)
   T omega;
   const double* Ainv;
+  const float2* AinvDF;  // Ainv as float pairs (FP32 V-cycles)
   Dims d[kTailMax];
   const T* Ae[kTailMax];
   const T* Aem[kTailMax];  // element-major copies (single-block form)
@@ -543,7 +571,8 @@ size_t coarse_scratch_doubles(int n);
 // Shared-memory limits of the coarsest-level kernels (call once, outside stream capture).
 cudaError_t prepare_coarse_kernels(int n);
 template <typename T>
-cudaError_t launch_dense_solve(int n, const double* Ainv, const T* b, T* z, int nrhs,
+cudaError_t launch_dense_solve(int n, const double* Ainv, const float2* AinvDF, const T* b, T* z,
+                               int nrhs,
                                const CgScalars* sc, cudaStream_t st);
 cudaError_t launch_convert_d2f(const double* a, float* b, long long n, cudaStream_t st);
 cudaError_t launch_convert_f2d(const float* a, double* b, long long n, cudaStream_t st);

@@ -14,9 +14,8 @@ def _doubles(rng):
     bits = rng.integers(0, 2**64, size=1 << 20, dtype=np.uint64)
     d = [bits.view(np.float64)]
     # doubles near the binary32 grid: a float plus multiples of a quarter of its ulp (ties included)
-    f = rng.standard_normal(1 << 16).astype(np.float32) * np.float32(2.0) ** rng.integers(
-        -149, 128, size=1 << 16).astype(np.float32)
-    f = f[np.isfinite(f)]
+    f = np.ldexp(rng.standard_normal(1 << 16), rng.integers(-149, 127, size=1 << 16)).astype(np.float32)
+    f = f[np.isfinite(f) & (f != 0)]
     ulp = np.spacing(np.abs(f)).astype(np.float64)
     for k in (-3, -2, -1, 1, 2, 3):
         d.append(f.astype(np.float64) + k * ulp / 4)
