@@ -409,9 +409,6 @@ cudaError_t q1_smooth_beta(const topo_solver* s, int nx, int ny, const TV* x, co
                                    counters, sc, s->st);
 }
 
-// Operator application on level k (mode as launch_apply): the warp-sweep Q1 kernels on the 2D
-// finest level, the matrix-free first coarse level in mixed precision, the Z operator (element
-// rank-one terms and lambda row) for IP systems, the generic element-matrix kernels elsewhere.
 // Whether a level keeps an element-major copy of its V-cycle matrices for the single-block deep
 // tail: 2D K systems, stored matrices, not the coarsest, at most kTailNodes nodes.
 bool aem_level(int dim, bool arrow, bool coarsest, bool matrix_free, long long nodes) {
@@ -441,6 +438,9 @@ int hex_sweep_env(bool hex_ok) {
   return 2;
 }
 
+// Operator application on level k (mode as launch_apply): the warp-sweep Q1 kernels on the 2D
+// finest level, the matrix-free first coarse level in mixed precision, the Z operator (element
+// rank-one terms and lambda row) for IP systems, the generic element-matrix kernels elsewhere.
 template <typename TV>
 topo_status apply_level(topo_solver* s, int k, int mode, const TV* v, const TV* b, TV* y,
                         const CgScalars* sc, const TV* zc = nullptr, int nrhs = 0) {
