@@ -432,6 +432,107 @@ __global__ void __launch_bounds__(kApply3Threads) k_apply3_rhs(
   }
 }
 
+// Small coarse 3D levels: one thread per (node, element around it), NR right-hand sides per
+// thread.  Each thread forms the three rows of its element's contribution for its right-hand
+// sides (the multiply-add chains of k_apply3_rhs), writes them to shared memory, and one thread
+// per (node, right-hand side) adds the eight elements' rows in the node's element order and
+// writes the output: the arithmetic and its order are those of k_apply3_rhs (the same bits).
+constexpr long long kApply3SplitNodes = 16384;
+constexpr int kApply3SplitNodesPerBlock = 16;  // 128 threads
+
+template <typename T, int MODE, int NR>
+__global__ void __launch_bounds__(kApply3SplitNodesPerBlock * 8) k_apply3_split(
+    Dims d, const T* __restrict__ Ae, const T* __restrict__ v, const T* __restrict__ b,
+    T* __restrict__ y, const T* __restrict__ invd, T omega, const uint8_t* __restrict__ fixed,
+    const CgScalars* __restrict__ sc, int nrhs) {
+  pdl_prologue();
+  constexpr int NE = 24;
+  constexpr int NPB = kApply3SplitNodesPerBlock;
+  __shared__ T part[NPB][8][NR][3];
+  __shared__ bool has[NPB][8];
+  const int r0 = blockIdx.y * NR;
+  bool live[NR];
+  bool any = false;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    live[r] = (r0 + r < nrhs) && !(sc && sc[r0 + r].done);
+    any = any || live[r];
+  }
+  if (!any) return;  // (the same for the whole block)
+  const long long nodes = d.nodes();
+  const long long n = nodes * 3;
+  const int nnx = d.nx + 1, nny = d.ny + 1;
+  const long long m = d.elems();
+  const int ln = threadIdx.x >> 3, s = threadIdx.x & 7;  // local node, element slot
+  const long long node = (long long)blockIdx.x * NPB + ln;
+  bool ok = false;
+  if (node < nodes) {
+    int i, j, k;
+    node_coords(node, nnx, nny, 3, i, j, k);
+    const int dx = s & 1, dy = (s >> 1) & 1, dz = s >> 2;
+    const int ex = i - 1 + dx, ey = j - 1 + dy, ez = k - 1 + dz;
+    ok = !(ex < 0 || ex >= d.nx || ey < 0 || ey >= d.ny || ez < 0 || ez >= d.nz);
+    if (ok) {
+      const int loc = loc_of(1 - dx, 1 - dy, 1 - dz);
+      const long long e = TOPO_IDX(ex + (long long)d.nx * (ey + (long long)d.ny * ez), m);
+      T row[3][NE];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int q = 0; q < NE; ++q) row[c][q] = ldg(Ae + (long long)((loc * 3 + c) * NE + q) * m + e);
+      long long nid[8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+        nid[a] = TOPO_IDX((ex + loc_ox(a)) + (long long)nnx * ((ey + loc_oy(a)) +
+                                                               (long long)nny * (ez + loc_oz(a))),
+                          nodes);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (!live[r]) continue;
+        const T* vr = v + (long long)(r0 + r) * n;
+        T ve[NE];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) ve[a * 3 + c] = ldg(vr + 3 * nid[a] + c);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          T t = T(0);
+#pragma unroll
+          for (int q = 0; q < NE; ++q) t = fma(row[c][q], ve[q], t);
+          part[ln][s][r][c] = t;
+        }
+      }
+    }
+  }
+  has[ln][s] = ok;
+  __syncthreads();
+  // (node, right-hand side) pairs: the eight elements in slot order, as k_apply3_rhs adds them
+  for (int w = threadIdx.x; w < NPB * NR; w += blockDim.x) {
+    const int ln2 = w / NR, r = w % NR;
+    const long long nd = (long long)blockIdx.x * NPB + ln2;
+    if (nd >= nodes || !live[r]) continue;
+    T acc[3] = {T(0), T(0), T(0)};
+    for (int s2 = 0; s2 < 8; ++s2) {
+      if (!has[ln2][s2]) continue;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[c] += part[ln2][s2][r][c];
+    }
+    const long long off = (long long)(r0 + r) * n;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long id = 3 * nd + c;
+      if (!TOPO_IN(id, n)) continue;
+      T out;
+      if (fixed[id]) out = T(0);
+      else if (MODE == 0) out = acc[c];
+      else if (MODE == 1) out = node_out<1, T>(acc[c], T(0), ldg(b + off + id), T(0), omega);
+      else out = node_out<2, T>(acc[c], ldg(v + off + id), ldg(b + off + id), invd[id], omega);
+      y[off + id] = out;
+    }
+  }
+}
+
 template <typename T, int MODE, bool FINE>
 void apply3_rhs_dispatch(const Dims& d, const T* K0, const T* x, const T* Ae, const T* v,
                          const T* b, T* y, const T* invd, T omega, const uint8_t* fixed, int nrhs,
@@ -440,6 +541,22 @@ void apply3_rhs_dispatch(const Dims& d, const T* K0, const T* x, const T* Ae, co
 #define TOPO_A3(NR)                                                                          \
   topo::launch(k_apply3_rhs<T, MODE, FINE, NR>, dim3(gx, (nrhs + NR - 1) / NR), kApply3Threads, \
                0, st, d, K0, x, Ae, v, b, y, invd, omega, fixed, sc, nrhs)
+  // Small coarse levels (at most 16K nodes) with several right-hand sides: one thread per element
+  // of a node (k_apply3_split).  With all eight elements of a node in one thread the few blocks
+  // of these levels ran long serial chains of loads (the 32 x 16 x 16 and 16 x 8 x 8 levels of the
+  // 128 x 64 x 64 hierarchy took about 32 us per launch; one right-hand side per thread, which
+  // reads the matrices once per right-hand side, took 114-120 us).  On the 64 x 32 x 32 level
+  // (70K nodes, 151 MB of matrices) the split form was slower: 101 against 73 us.
+  if (!FINE && MODE != 3 && d.nodes() <= kApply3SplitNodes && nrhs >= 2) {
+    const unsigned gs = blocks_for(d.nodes(), kApply3SplitNodesPerBlock);
+#define TOPO_A3S(NRS)                                                                        \
+  topo::launch(k_apply3_split<T, MODE, NRS>, dim3(gs, (nrhs + NRS - 1) / NRS),                \
+               kApply3SplitNodesPerBlock * 8, 0, st, d, Ae, v, b, y, invd, omega, fixed, sc, nrhs)
+    if (nrhs >= 5) TOPO_A3S(8);
+    else TOPO_A3S(4);
+#undef TOPO_A3S
+    return;
+  }
   if (nrhs >= 5) TOPO_A3(8);
   else if (nrhs >= 3) TOPO_A3(4);
   else if (nrhs == 2) TOPO_A3(2);
