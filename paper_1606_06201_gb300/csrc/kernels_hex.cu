@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kThreads) k_hex_gather_dot_df(Dims d, const fl
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const float2 r = __ldg(R + (long long)(loc * 3 + c) * m + e);
-        acc[c] = df_add(acc[c], f2{r.x, r.y});
+        acc[c] = df_add_nr(acc[c], f2{r.x, r.y});
       }
     }
 #pragma unroll
@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(512) k_hex_tile_outer(Dims d, HexTile tl, HexK
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
               if constexpr (std::is_same<P, double>::value) acc[c] += Fb[(loc * 3 + c) * TT + te];
-              else acc[c] = df_add(acc[c], E::load(Fb[(loc * 3 + c) * TT + te]));
+              else acc[c] = df_add_nr(acc[c], E::load(Fb[(loc * 3 + c) * TT + te]));
             }
           }
         }
@@ -558,7 +558,7 @@ __global__ void __launch_bounds__(512) k_hex_tile_outer(Dims d, HexTile tl, HexK
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             if constexpr (std::is_same<P, double>::value) acc[c] += Fb[(loc * 3 + c) * TT + te];
-            else acc[c] = df_add(acc[c], E::load(Fb[(loc * 3 + c) * TT + te]));
+            else acc[c] = df_add_nr(acc[c], E::load(Fb[(loc * 3 + c) * TT + te]));
           }
         }
       }

@@ -556,28 +556,28 @@ struct Q1KD {
 // The butterfly of q1_element in pair arithmetic (the density applied after Khat).
 __device__ __forceinline__ void q1_element_df(const Q1KD& k, f2 xe, const f2 u[4], const f2 v[4],
                                               f2 ru[4], f2 rv[4]) {
-  const f2 d1 = df_sub(u[2], u[0]), d2 = df_sub(u[1], u[3]);
-  const f2 s1 = df_add(u[0], u[2]), s2 = df_add(u[1], u[3]);
-  const f2 X = df_add(d2, d1), Y = df_sub(d1, d2), H = df_sub(s1, s2);
-  const f2 e1 = df_sub(v[2], v[0]), e2 = df_sub(v[1], v[3]);
-  const f2 t1 = df_add(v[0], v[2]), t2 = df_add(v[1], v[3]);
-  const f2 Xp = df_add(e2, e1), Yp = df_sub(e1, e2), Hp = df_sub(t1, t2);
-  const f2 G = df_add(Y, Xp);
-  const f2 gX = df_mul(xe, df_add(df_mul(k.c11, X), df_mul(k.c12, Yp)));
-  const f2 gYp = df_mul(xe, df_add(df_mul(k.c12, X), df_mul(k.c22, Yp)));
+  const f2 d1 = df_sub_nr(u[2], u[0]), d2 = df_sub_nr(u[1], u[3]);
+  const f2 s1 = df_add_nr(u[0], u[2]), s2 = df_add_nr(u[1], u[3]);
+  const f2 X = df_add_nr(d2, d1), Y = df_sub_nr(d1, d2), H = df_sub_nr(s1, s2);
+  const f2 e1 = df_sub_nr(v[2], v[0]), e2 = df_sub_nr(v[1], v[3]);
+  const f2 t1 = df_add_nr(v[0], v[2]), t2 = df_add_nr(v[1], v[3]);
+  const f2 Xp = df_add_nr(e2, e1), Yp = df_sub_nr(e1, e2), Hp = df_sub_nr(t1, t2);
+  const f2 G = df_add_nr(Y, Xp);
+  const f2 gX = df_mul(xe, df_add_nr(df_mul(k.c11, X), df_mul(k.c12, Yp)));
+  const f2 gYp = df_mul(xe, df_add_nr(df_mul(k.c12, X), df_mul(k.c22, Yp)));
   const f2 gG = df_mul(xe, df_mul(k.c33, G));
   const f2 gH = df_mul(xe, df_mul(k.cH, H));
   const f2 gHp = df_mul(xe, df_mul(k.cHp, Hp));
-  const f2 A = df_add(gX, gG), B = df_sub(gX, gG);
-  ru[0] = df_sub(gH, A);
-  ru[1] = df_sub(B, gH);
-  ru[2] = df_add(A, gH);
-  ru[3] = df_sub(df_neg(B), gH);
-  const f2 C = df_add(gYp, gG), Dd = df_sub(gYp, gG);
-  rv[0] = df_sub(gHp, C);
-  rv[1] = df_sub(df_neg(Dd), gHp);
-  rv[2] = df_add(C, gHp);
-  rv[3] = df_sub(Dd, gHp);
+  const f2 A = df_add_nr(gX, gG), B = df_sub_nr(gX, gG);
+  ru[0] = df_sub_nr(gH, A);
+  ru[1] = df_sub_nr(B, gH);
+  ru[2] = df_add_nr(A, gH);
+  ru[3] = df_sub_nr(df_neg(B), gH);
+  const f2 C = df_add_nr(gYp, gG), Dd = df_sub_nr(gYp, gG);
+  rv[0] = df_sub_nr(gHp, C);
+  rv[1] = df_sub_nr(df_neg(Dd), gHp);
+  rv[2] = df_add_nr(C, gHp);
+  rv[3] = df_sub_nr(Dd, gHp);
 }
 
 __device__ __forceinline__ f2 shfl_dn_df(f2 a) { return {shfl_dn(a.h), shfl_dn(a.l)}; }
@@ -656,7 +656,7 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep_df(int nx, int ny, i
       const f2 l1u = shfl_up1_df(ru[1]), l1v = shfl_up1_df(rv[1]);
       const f2 l2u = shfl_up1_df(ru[2]), l2v = shfl_up1_df(rv[2]);
       if (ey >= j0 && out_lane) {
-        f2 qu = df_add(df_add(cu, ru[0]), l1u), qv = df_add(df_add(cv, rv[0]), l1v);
+        f2 qu = df_add_nr(df_add_nr(cu, ru[0]), l1u), qv = df_add_nr(df_add_nr(cv, rv[0]), l1v);
         if (fx & 0xff) qu = z;
         if (fx >> 8) qv = z;
         double2 out;
@@ -665,8 +665,8 @@ __global__ void __launch_bounds__(kQ1Warps * 32) k_q1_sweep_df(int nx, int ny, i
         reinterpret_cast<double2*>(y)[c + rs * ey] = out;
         part = df_add(part, df_add(df_mul(pbu, qu), df_mul(pbv, qv)));
       }
-      cu = df_add(ru[3], l2u);
-      cv = df_add(rv[3], l2v);
+      cu = df_add_nr(ru[3], l2u);
+      cv = df_add_nr(rv[3], l2v);
       pbu = ptu;
       pbv = ptv;
     }

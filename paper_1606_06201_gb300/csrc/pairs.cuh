@@ -29,6 +29,19 @@ __device__ __forceinline__ f2 df_add(f2 a, f2 b) {
 __device__ __forceinline__ f2 df_neg(f2 a) { return {-a.h, -a.l}; }
 __device__ __forceinline__ f2 df_sub(f2 a, f2 b) { return df_add(a, df_neg(b)); }
 
+// The sum without the closing renormalisation (8 operations instead of 11): hi = RN(a.h + b.h),
+// lo = its rounding error (TwoSum) plus the low parts.  hi + lo keeps about 48 bits relative to
+// the operands; after a cancellation lo may exceed half an ulp of hi, which the next products
+// (renormalised) and the final conversion to FP64 absorb.  For the short butterflies and node sums
+// of the element operators; long accumulations (dot products) keep df_add.
+__device__ __forceinline__ f2 df_add_nr(f2 a, f2 b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  return {s, __fadd_rn(e, __fadd_rn(a.l, b.l))};
+}
+__device__ __forceinline__ f2 df_sub_nr(f2 a, f2 b) { return df_add_nr(a, df_neg(b)); }
+
 __device__ __forceinline__ f2 df_mul(f2 a, f2 b) {
   const float p = __fmul_rn(a.h, b.h);
   float e = __fmaf_rn(a.h, b.h, -p);
@@ -137,13 +150,13 @@ inline f2 df_const(double c) {
 struct PairNum {
   f2 v;
 };
-__device__ __forceinline__ PairNum operator+(PairNum a, PairNum b) { return {df_add(a.v, b.v)}; }
-__device__ __forceinline__ PairNum operator-(PairNum a, PairNum b) { return {df_sub(a.v, b.v)}; }
+__device__ __forceinline__ PairNum operator+(PairNum a, PairNum b) { return {df_add_nr(a.v, b.v)}; }
+__device__ __forceinline__ PairNum operator-(PairNum a, PairNum b) { return {df_sub_nr(a.v, b.v)}; }
 __device__ __forceinline__ PairNum operator-(PairNum a) { return {df_neg(a.v)}; }
 __device__ __forceinline__ PairNum operator*(PairNum a, PairNum b) { return {df_mul(a.v, b.v)}; }
 using ::fma;  // (the float and double overloads stay visible next to the pair one)
 __device__ __forceinline__ PairNum fma(PairNum a, PairNum b, PairNum c) {
-  return {df_add(df_mul(a.v, b.v), c.v)};
+  return {df_add_nr(df_mul(a.v, b.v), c.v)};
 }
 
 }  // namespace topo
