@@ -57,19 +57,19 @@ FP64_PEAK_TOPS, FP32_PEAK_TOPS = derived_peaks(SM_COUNT_DEFAULT, SM_MHZ_DEFAULT)
 # per displacement component: 15 adds; 8 products; 14 multiply-adds for the scalings and the inverse
 # butterflies) + 6 node-assembly adds + 2 FMA of the fused p^T q per node.
 OPS_PER_ELEM, OPS_PER_NODE = 37.0, 8.0
-# FP32 operations of the same operator in float pairs: per element 29 pair additions (11 FP32
-# operations each: TwoSum, the low parts, a renormalising FastTwoSum) and 12 pair products (7:
-# product, FMA error term, two cross FMAs, FastTwoSum), plus the 2 pair additions of the carried
-# node sums; per output node 4 pair additions of the node sums and 2 products + 2 additions of
+# FP32 operations of the same operator in float pairs: per element 29 pair additions (8 FP32
+# operations each: TwoSum and the low parts, no renormalisation) and 12 pair products (7: product,
+# FMA error term, two cross FMAs, FastTwoSum), plus the 2 pair additions of the carried node sums;
+# per output node 4 pair additions of the node sums, 2 products + 2 renormalised additions (11) of
 # p^T q, and 2 FP32 multiplies of each of the two input splits.
-DF_OPS_PER_ELEM = 29 * 11 + 12 * 7 + 2 * 11
-DF_OPS_PER_NODE = 4 * 11 + 2 * 7 + 2 * 11 + 4
+DF_OPS_PER_ELEM = 29 * 8 + 12 * 7 + 2 * 8
+DF_OPS_PER_NODE = 4 * 8 + 2 * 7 + 2 * 11 + 4
 # DRAM bytes of one launch of the FP64 operator on this workload from an ncu capture; None until
 # the operator as built now (37-operation element product) has been captured.
 OPERATOR_DRAM_BYTES = None
 # The same for the float-pair operator (ncu capture of k_q1_sweep_df on this workload:
-# 54.94 MB read + 2.53 MB write).
-DF_OPERATOR_DRAM_BYTES = 57463808.0
+# 54.73 MB read + 2.74 MB write).
+DF_OPERATOR_DRAM_BYTES = 57469184.0
 
 
 def _measured_hbm_gbs():
@@ -606,8 +606,8 @@ def main():
                      "peak": fp32_peak, "unit": "T FP32-op/s",
                      "peak_source": peak_src % (sm_count, "128 FP32 lanes", sm_mhz),
                      "algorithmic_ops_per_launch": ops_per_launch,
-                     "note": "operations of the pair arithmetic as written (425 FP32 ops per "
-                             "element + 84 per node), against the derived FP32 issue rate"}
+                     "note": "operations of the pair arithmetic as written (332 FP32 ops per "
+                             "element + 72 per node), against the derived FP32 issue rate"}
             traffic = DF_OPERATOR_DRAM_BYTES
         issue["frac"] = issue["achieved"] / issue["peak"]
         achieved = alg_bytes / (op_avg_ms * 1e-3) / 1e9

@@ -808,6 +808,73 @@ __device__ __forceinline__ void prolong_node(const Dims& df, const Dims& dc, lon
   }
 }
 
+// 3D prolongation and correction for NR right-hand sides per thread: the coarse indices and
+// weights of a fine node are formed once and applied to every right-hand side; per right-hand
+// side the multiply-adds and their order are those of prolong_node (the same bits).
+template <typename T, int NR>
+__global__ void __launch_bounds__(kThreads) k_prolong_add3_rhs(Dims df, const T* __restrict__ zc,
+                                                               T* __restrict__ zf,
+                                                               const uint8_t* __restrict__ fixed_f,
+                                                               const CgScalars* __restrict__ sc,
+                                                               int nrhs) {
+  pdl_prologue();
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= df.nodes()) return;
+  const Dims dc{df.nx / 2, df.ny / 2, df.nz / 2, 3};
+  const long long nf = df.dofs(), ncd = dc.dofs();
+  const int fnx = df.nx + 1, fny = df.ny + 1;
+  int i, j, k;
+  node_coords(node, fnx, fny, 3, i, j, k);
+  const int cnx = dc.nx + 1, cny = dc.ny + 1;
+  const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1, k0 = k >> 1,
+            k1 = (k + 1) >> 1;
+  const T wxh = (i & 1) ? T(0.5) : T(1);
+  const T wyh = (j & 1) ? T(0.5) : T(1);
+  const T wzh = (k & 1) ? T(0.5) : T(1);
+  const T w = wxh * wyh * wzh;
+  const int nzi = (k & 1) ? 2 : 1, nyi = (j & 1) ? 2 : 1, nxi = (i & 1) ? 2 : 1;
+  int cid[8];  // (unrolled below: registers; grids hold < 2^31 nodes)
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int bq = 0; bq < 2; ++bq)
+#pragma unroll
+      for (int cq = 0; cq < 2; ++cq)
+        cid[(a * 2 + bq) * 2 + cq] =
+            (int)TOPO_IDX((cq ? i1 : i0) + (long long)cnx * ((bq ? j1 : j0) + (long long)cny * (a ? k1 : k0)),
+                          dc.nodes());
+  bool fx[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) fx[c] = fixed_f[3 * node + c] != 0;
+#pragma unroll 1
+  for (int r0 = 0; r0 < nrhs; r0 += NR) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const int rhs = r0 + r;
+      if (rhs >= nrhs || (sc && sc[rhs].done)) continue;
+      const T* zr = zc + (long long)rhs * ncd;
+      T* zo = zf + (long long)rhs * nf;
+      T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int bq = 0; bq < 2; ++bq)
+#pragma unroll
+          for (int cq = 0; cq < 2; ++cq) {
+            if (a >= nzi || bq >= nyi || cq >= nxi) continue;  // (the loop order of prolong_node)
+            const long long q = cid[(a * 2 + bq) * 2 + cq];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[c] = fma(w, __ldg(zr + 3 * q + c), acc[c]);
+          }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const long long id = 3 * node + c;
+        if (!fx[c] && TOPO_IN(id, nf)) zo[id] = zo[id] + acc[c];
+      }
+    }
+  }
+}
+
 template <int DIM, typename T>
 __global__ void __launch_bounds__(kThreads) k_prolong_add(Dims df, const T* __restrict__ zc,
                                                           T* __restrict__ zf,
@@ -1685,6 +1752,9 @@ cudaError_t launch_prolong_add(const Dims& fine, const T* zc, T* zf, const uint8
   dim3 grid(blocks_for(fine.nodes()), nrhs);
   if (fine.dim == 2)
     topo::launch(k_prolong_add<2, T>, grid, kThreads, 0, st, fine, zc, zf, fixed_f, sc, arrow);
+  else if (nrhs >= 2 && !arrow)  // (every right-hand side of a node in one thread)
+    topo::launch(k_prolong_add3_rhs<T, 1>, dim3(blocks_for(fine.nodes())), kThreads, 0, st, fine,
+                 zc, zf, fixed_f, sc, nrhs);
   else
     topo::launch(k_prolong_add<3, T>, grid, kThreads, 0, st, fine, zc, zf, fixed_f, sc, arrow);
   return cudaGetLastError();
