@@ -602,7 +602,10 @@ __global__ void __launch_bounds__(512) k_hex_tile_outer(Dims d, HexTile tl, HexK
 // of the node-parallel k_apply3_rhs, so the same bits.  Otherwise the Walsh-Hadamard form of
 // the element (about 180 operations instead of 576 multiply-adds) with x_e in the coefficients
 // and plain adds at the node (other roundings, the same operator).
-template <typename T, int MODE, bool DENSE>
+// DOT 2 (MODE 2, the last smoothing sweep of the preconditioner): also r~^T y~ against the FP64
+// CG residual rdot and, by the last block, beta = r~^T y~ / r^T y of Algorithm PCG (as the 2D
+// sweeps form it).
+template <typename T, int MODE, bool DENSE, int DOT = 0>
 __global__ void __launch_bounds__(512) k_hex_tile_sweep(Dims d, HexTile tl, HexK<T> k,
                                                         const T* __restrict__ K0,
                                                         const T* __restrict__ x,
@@ -611,10 +614,14 @@ __global__ void __launch_bounds__(512) k_hex_tile_sweep(Dims d, HexTile tl, HexK
                                                         T* __restrict__ y,
                                                         const T* __restrict__ invd, T omega,
                                                         const uint8_t* __restrict__ fixed,
-                                                        const CgScalars* __restrict__ sc) {
+                                                        const CgScalars* __restrict__ sc,
+                                                        const double* __restrict__ rdot = nullptr,
+                                                        double* partials = nullptr,
+                                                        unsigned* counters = nullptr) {
   pdl_prologue();
   const int rhs = blockIdx.z;
   if (sc && sc[rhs].done) return;
+  double part = 0.0;
   extern __shared__ float4 hex_tile_raw[];
   const int TT = tl.tx * tl.ty;
   T* F = reinterpret_cast<T*>(hex_tile_raw);  // [2][24][TT]
@@ -633,6 +640,7 @@ __global__ void __launch_bounds__(512) k_hex_tile_sweep(Dims d, HexTile tl, HexK
   v += rhs * n;
   y += rhs * n;
   if (MODE != 0) b += rhs * n;
+  if (DOT == 2) rdot += rhs * n;
   const bool e_xy = ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny;
   const bool own = tx >= 1 && ty >= 1 && ex < nnx && ey < nny;
   T acc[3] = {T(0), T(0), T(0)};
@@ -728,10 +736,38 @@ __global__ void __launch_bounds__(512) k_hex_tile_sweep(Dims d, HexTile tl, HexK
             else if (MODE == 1) out = node_out<1, T>(acc[c], T(0), __ldg(b + id), T(0), omega);
             else out = node_out<2, T>(acc[c], __ldg(v + id), __ldg(b + id), invd[id], omega);
             y[id] = out;
+            if (DOT == 2) part = fma(__ldg(rdot + id), double_of(out), part);
             acc[c] = T(0);
           }
         }
       }
+    }
+  }
+  if (DOT == 2) {  // beta by the last block, as the 2D sweeps finish it
+    const double bs = block_sum_hex(part);
+    const unsigned nb = gridDim.x * gridDim.y, bid = blockIdx.x + gridDim.x * blockIdx.y;
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+      partials[(long long)rhs * nb + bid] = bs;
+      __threadfence();
+      last = (atomicAdd(&counters[rhs], 1u) == nb - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    double s2 = 0.0;
+    for (unsigned u = threadIdx.x; u < nb; u += blockDim.x) s2 += __ldcg(partials + (long long)rhs * nb + u);
+    s2 = block_sum_hex(s2);
+    if (threadIdx.x == 0) {
+      CgScalars& S = const_cast<CgScalars&>(sc[rhs]);
+      const double beta = s2 / S.ry;
+      S.ry_new = s2;
+      S.beta = beta;
+      S.ry = s2;
+      if (!isfinite(beta)) {
+        S.status = TOPO_E_BREAKDOWN;
+        S.done = 1;
+      }
+      counters[rhs] = 0;
     }
   }
 }
@@ -1059,6 +1095,16 @@ cudaError_t prepare_hex_tile_kernels() {
   TOPO_HT_PREP(double, 1)
   TOPO_HT_PREP(double, 2)
 #undef TOPO_HT_PREP
+#define TOPO_HT_PREPB(T)                                                                           \
+  if (e == cudaSuccess)                                                                            \
+    e = hex_tile_smem(k_hex_tile_sweep<T, 2, true, 2>,                                             \
+                      (2 * 24 * kHexTileSweepThreads + 2 * kHexTileSweepThreads + 576) * sizeof(T)); \
+  if (e == cudaSuccess)                                                                            \
+    e = hex_tile_smem(k_hex_tile_sweep<T, 2, false, 2>,                                            \
+                      (2 * 24 * kHexTileSweepThreads + 2 * kHexTileSweepThreads + 576) * sizeof(T));
+  TOPO_HT_PREPB(float)
+  TOPO_HT_PREPB(double)
+#undef TOPO_HT_PREPB
   const size_t tc_smem = (2 * 24 * kHexTileSweepThreads + 2 * kHexTileSweepThreads +
                           (kHexTileSweepThreads / 32) * 24 * kTcStride) * sizeof(float);
   if (e == cudaSuccess) e = hex_tile_smem(k_hex_tile_sweep_tc<0>, tc_smem);
@@ -1121,7 +1167,8 @@ cudaError_t launch_hex_tile_sweep(const Dims& d, int mode, int form, const HexCo
   const HexK<T> k{(T)c.a, (T)c.b, (T)c.s, (T)c.p, (T)c.q, (T)c.d, (T)c.e, (T)c.h};
 #define TOPO_HT(MODE, DENSE)                                                                     \
   topo::launch(k_hex_tile_sweep<T, MODE, DENSE>, grid, TT, smem, st, d, tl, k, K0, x, v, b, y, \
-               invd, omega, fixed, sc)
+               invd, omega, fixed, sc, (const double*)nullptr, (double*)nullptr,                 \
+               (unsigned*)nullptr)
   if (dense) {
     if (mode == 0) TOPO_HT(0, true);
     else if (mode == 1) TOPO_HT(1, true);
@@ -1136,6 +1183,41 @@ cudaError_t launch_hex_tile_sweep(const Dims& d, int mode, int form, const HexCo
 #undef TOPO_HT
   return cudaGetLastError();
 }
+
+// The last smoothing sweep with r~^T y~ and beta (DOT 2): forms 0 (Walsh-Hadamard) and 1 (dense).
+template <typename T>
+cudaError_t launch_hex_tile_sweep_beta(const Dims& d, int form, const HexCoef& c, const T* K0,
+                                       const T* x, const T* v, const T* b, T* y, const T* invd,
+                                       T omega, const uint8_t* fixed, int nrhs, CgScalars* sc,
+                                       const double* rdot, double* partials, unsigned* counters,
+                                       cudaStream_t st) {
+  const int maxt = sizeof(T) == 8 ? 256 : kHexTileSweepThreads;
+  const HexTile tl = hex_tile_plan(d, nrhs, maxt, 152 * 4);
+  if (tl.tx == 0) return cudaErrorInvalidConfiguration;
+  const dim3 grid(tl.tiles_x * tl.tiles_y, tl.zchunks, nrhs);
+  const int TT = tl.tx * tl.ty;
+  const bool dense = form == 1;
+  const size_t smem = (size_t)(2 * 24 * TT + (dense ? 2 * TT + 576 : 0)) * sizeof(T);
+  const HexK<T> k{(T)c.a, (T)c.b, (T)c.s, (T)c.p, (T)c.q, (T)c.d, (T)c.e, (T)c.h};
+  if (dense)
+    topo::launch(k_hex_tile_sweep<T, 2, true, 2>, grid, TT, smem, st, d, tl, k, K0, x, v, b, y, invd,
+                 omega, fixed, (const CgScalars*)sc, rdot, partials, counters);
+  else
+    topo::launch(k_hex_tile_sweep<T, 2, false, 2>, grid, TT, smem, st, d, tl, k, K0, x, v, b, y,
+                 invd, omega, fixed, (const CgScalars*)sc, rdot, partials, counters);
+  return cudaGetLastError();
+}
+template cudaError_t launch_hex_tile_sweep_beta<float>(const Dims&, int, const HexCoef&, const float*,
+                                                       const float*, const float*, const float*,
+                                                       float*, const float*, float, const uint8_t*,
+                                                       int, CgScalars*, const double*, double*,
+                                                       unsigned*, cudaStream_t);
+template cudaError_t launch_hex_tile_sweep_beta<double>(const Dims&, int, const HexCoef&,
+                                                        const double*, const double*,
+                                                        const double*, const double*, double*,
+                                                        const double*, double, const uint8_t*, int,
+                                                        CgScalars*, const double*, double*,
+                                                        unsigned*, cudaStream_t);
 
 template cudaError_t launch_hex_tile_sweep<float>(const Dims&, int, int, const HexCoef&,
                                                   const float*, const float*, const float*,

@@ -682,10 +682,17 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
     if (fine) TOPO_TRY(prof_mark(s, 4, 1));
   }
   for (int it = it0; it < nu2; ++it) {
-    if (fuse_beta && k == 0 && it == nu2 - 1) {
+    if (fuse_beta && k == 0 && it == nu2 - 1 && s->q1_ok) {
       TOPO_CUDA(q1_smooth_beta<TV>(s, lv.d.nx, lv.d.ny, Prec<TV>::x(s), cur, b, oth,
                                    (TV)s->desc.omega, lv.fixed, nrhs, s->partials, s->counters,
                                    const_cast<CgScalars*>(sc)));
+    } else if (fuse_beta && k == 0 && it == nu2 - 1) {  // the 3D tile sweep with r~^T y~, beta
+      const TV omega = lv.omega_dev ? TV(1) : (TV)s->desc.omega;
+      TOPO_CUDA(launch_hex_tile_sweep_beta<TV>(lv.d, s->hex_sweep == 2 ? 0 : 1, s->hex,
+                                               Prec<TV>::K0(s), Prec<TV>::x(s), cur, b, oth,
+                                               Prec<TV>::invd(lv), omega, lv.fixed, nrhs,
+                                               const_cast<CgScalars*>(sc), s->r, s->partials,
+                                               s->counters, s->st));
     } else {
       const bool t = fine && !sweep_timed;
       if (t) TOPO_TRY(prof_mark(s, 1, 0));
@@ -765,7 +772,9 @@ topo_status cg_iteration(topo_solver* s, int slot, double tol, int max_iter) {
   TOPO_CUDA(launch_cg_update<TV>(n, s->nrhs, s->z, s->r, s->p, s->q, rv, s->partials, s->counters,
                                  s->sc, tol, max_iter, s->st));
   void* y = nullptr;
-  const bool fuse = s->q1_ok && !s->arrow && s->desc.nu2 >= 1 && !s->desc.flexible &&
+  // (2D: the Q1 sweeps; 3D: the tile sweeps of forms 1 and 2)
+  const bool fuse_ok = s->q1_ok || (s->dim == 3 && (s->hex_sweep == 1 || s->hex_sweep == 2));
+  const bool fuse = fuse_ok && !s->arrow && s->desc.nu2 >= 1 && !s->desc.flexible &&
                     s->nlev >= 2 && s->desc.smoother == 0;
   TOPO_TRY(prof_mark(s, 5, 0));
   TOPO_TRY(precondition<TV>(s, s->sc, &y, fuse));

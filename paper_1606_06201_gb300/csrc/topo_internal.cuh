@@ -478,6 +478,12 @@ cudaError_t launch_hex_apply_dot_df(const Dims& d, const HexCoef& c, const float
 // Counts the inputs where the integer FP64 <-> FP32 conversions differ from the hardware ones.
 cudaError_t launch_check_conversions(const double* d, const float* f, long long n,
                                      unsigned long long* bad, cudaStream_t st);
+template <typename T>
+cudaError_t launch_hex_tile_sweep_beta(const Dims& d, int form, const HexCoef& c, const T* K0,
+                                       const T* x, const T* v, const T* b, T* y, const T* invd,
+                                       T omega, const uint8_t* fixed, int nrhs, CgScalars* sc,
+                                       const double* rdot, double* partials, unsigned* counters,
+                                       cudaStream_t st);
 cudaError_t prepare_hex_tile_kernels();
 cudaError_t launch_hex_tile_apply_dot(const Dims& d, const HexCoef& c, const void* x, bool pairs,
                                       const double* v, double* y, const uint8_t* fixed, int nrhs,

@@ -3,8 +3,8 @@ against the node-parallel and buffered forms on grids that span several tiles, z
 ragged edge in every direction, with several right-hand sides:
 
 * the V-cycle operator with the element rows of K0 (TOPO_HEX_SWEEP=dense) has the arithmetic of
-  the node-parallel kernel (TOPO_HEX_SWEEP=node): V-cycle outputs and whole solves agree bit for
-  bit;
+  the node-parallel kernel (TOPO_HEX_SWEEP=node): V-cycle outputs agree bit for bit, whole solves
+  to rounding (the tile forms fuse r~^T y~ and beta into the last smoothing sweep);
 * the Walsh-Hadamard V-cycle operator (the default), and the dense one on the tensor cores
   (TOPO_HEX_SWEEP=tc, 3 x TF32), are the same operator with other roundings: the solves reach the
   node-parallel solutions and the exact solution of the oracle's sparse matrix;
@@ -63,8 +63,10 @@ def test_dense_tile_sweep_gives_the_node_parallel_bits(shape, nrhs, precision, m
     U1, it1, M1 = _solve(monkeypatch, {"TOPO_HEX_SWEEP": "dense"}, shape, nrhs, precision,
                          vcycle_input=a)
     np.testing.assert_array_equal(M0, M1)
-    np.testing.assert_array_equal(U0, U1)
-    assert it0 == it1
+    # (whole solves to rounding: the tile forms fuse r~^T y~ and beta into the last sweep, which
+    # sums the dot product in another order than the separate kernel)
+    assert abs(it0 - it1) <= 1
+    assert rel_err(U1, U0) <= (1e-12 if precision == 0 else 1e-8)
 
 
 @pytest.mark.parametrize("form", ["wht", "tc"])
