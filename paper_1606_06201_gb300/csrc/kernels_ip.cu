@@ -738,10 +738,29 @@ __global__ void __launch_bounds__(kThreads) k_oc_bisect(long long m, const doubl
     last = (atomicAdd(counter, 1u) == gridDim.x - 1);
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
+  // the last block combines the blocks' pairs: thread t takes blocks t, t + blockDim, ... in order,
+  // then the warp and block combinations above, in a fixed order (one thread walking all the
+  // blocks' pairs from L2 took about 0.25 ms per step)
   double h = 0.0, l = 0.0;
-  for (unsigned bidx = 0; bidx < gridDim.x; ++bidx)
+  for (unsigned bidx = threadIdx.x; bidx < gridDim.x; bidx += blockDim.x)
     dd_add(h, l, __ldcg(partials + 2 * bidx), __ldcg(partials + 2 * bidx + 1));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double bh = __shfl_down_sync(0xffffffffu, h, o);
+    const double bl = __shfl_down_sync(0xffffffffu, l, o);
+    dd_add(h, l, bh, bl);
+  }
+  __syncthreads();  // (sh is reused)
+  if (lane == 0) {
+    sh[0][wid] = h;
+    sh[1][wid] = l;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  h = 0.0;
+  l = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) dd_add(h, l, sh[0][w], sh[1][w]);
   const double total = h + l;  // round the double-double once
   if (total > oc->V) oc->lo = lam;
   else oc->hi = lam;
