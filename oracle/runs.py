@@ -16,14 +16,16 @@ from paper_1606_06201_gb300 import workloads as W
 from . import fe, ip, oc
 
 
-def spawn_pool(processes=2):
+def spawn_pool(processes=2, threads=None):
     """A spawn-context process pool for oracle runs beside a GPU process.  The host's cores are
     split between the workers (BLAS and OpenMP threads set before they start): workers that each
-    take every core spin against one another and run tens of times slower."""
+    take every core spin against one another and run tens of times slower.  ``threads`` fixes the
+    BLAS threads of each worker instead (1: the factorisations do not depend on how many cores the
+    host has)."""
     import multiprocessing as mp
     keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
     old = {k: os.environ.get(k) for k in keys}
-    share = max(1, _cores() // processes)
+    share = int(threads) if threads else max(1, _cores() // processes)
     for k in keys:
         os.environ[k] = str(share)
     try:

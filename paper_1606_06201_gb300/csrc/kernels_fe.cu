@@ -895,6 +895,144 @@ __global__ void __launch_bounds__(kThreads) k_prolong_add(Dims df, const T* __re
   prolong_node<DIM, T>(df, dc, node, zc + rhs * dc.dofs(), zf + rhs * df.dofs(), fixed_f);
 }
 
+// Floor of x / 2 for x >= -2 (folds to a constant for constant x).
+__host__ __device__ constexpr int floor_half(int x) { return (x + 2) / 2 - 1; }
+
+// The coarse-grid correction with the first post-smoothing sweep at one node (i, j) of a 2D level
+// with stored element matrices (Algorithm MG): y = v + omega D^-1 (b - A v) with v = z + P z_c
+// formed in the kernel.  The node's parities (PX, PY) = (i & 1, j & 1) are template arguments, so
+// that the coarse nodes every neighbour interpolates from, and the weights, are constants.  The
+// sweep reads v at the 3 x 3 neighbour nodes; each is formed once from a patch of (PX ? 2 : 3) x
+// (PY ? 2 : 3) coarse nodes, with the multiply-adds in the order of prolong_node (fixed DOFs keep
+// z), and the element products run as in node_apply: the bits of k_prolong_add followed by
+// apply_node MODE 2.
+template <typename T, int PX, int PY>
+__device__ __forceinline__ void apply2_prolong_node(const Dims& d, int i, int j,
+                                                    const T* __restrict__ Ae,
+                                                    const T* __restrict__ z,
+                                                    const T* __restrict__ zc,
+                                                    const T* __restrict__ b, T* __restrict__ y,
+                                                    const T* __restrict__ invd, T omega,
+                                                    const uint8_t* __restrict__ fixed) {
+  constexpr int NPX = PX ? 2 : 3, NPY = PY ? 2 : 3;  // the coarse patch
+  const int nnx = d.nx + 1, nny = d.ny + 1;
+  const long long nodes = (long long)nnx * nny, n = 2 * nodes, m = d.elems();
+  const int cnx = d.nx / 2 + 1, cny = d.ny / 2 + 1;
+  const long long ncn = (long long)cnx * cny;
+  const int cx0 = (i >> 1) - 1 + PX, cy0 = (j >> 1) - 1 + PY;  // floor((i - 1) / 2), likewise y
+  T C[NPY][NPX][2];
+#pragma unroll
+  for (int q = 0; q < NPY; ++q)
+#pragma unroll
+    for (int p = 0; p < NPX; ++p) {
+      const int cx = cx0 + p, cy = cy0 + q;
+      const bool in = cx >= 0 && cx < cnx && cy >= 0 && cy < cny;
+      const long long cid = in ? TOPO_IDX(cx + (long long)cnx * cy, ncn) : 0;
+      C[q][p][0] = in ? ldg(zc + 2 * cid) : T(0);
+      C[q][p][1] = in ? ldg(zc + 2 * cid + 1) : T(0);
+    }
+  // the element matrix rows of the four adjacent elements (loaded before v is formed)
+  T a[4][16];
+  bool ok[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int dx = s & 1, dy = s >> 1;
+    const int ex = i - 1 + dx, ey = j - 1 + dy;
+    ok[s] = ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny;
+    const int loc = loc_of(1 - dx, 1 - dy, 0);
+    const long long e = ok[s] ? TOPO_IDX(ex + (long long)d.nx * ey, m) : 0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        a[s][c * 8 + q] = ldg(Ae + (long long)((loc * 2 + c) * 8 + q) * m + e);
+  }
+  // v at the 3 x 3 neighbours (those outside the grid are never read)
+  T V[3][3][2];
+#pragma unroll
+  for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+    for (int di = 0; di < 3; ++di) {
+      const int bx = PX - 1 + di, by = PY - 1 + dj;  // ii = 2 (i >> 1) + bx, likewise jj
+      const int ox = bx & 1, oy = by & 1;
+      const int p0 = floor_half(bx) + 1 - PX, p1 = floor_half(bx + 1) + 1 - PX;
+      const int q0 = floor_half(by) + 1 - PY, q1 = floor_half(by + 1) + 1 - PY;
+      const T w = (ox ? T(0.5) : T(1)) * (oy ? T(0.5) : T(1));
+      const int ii = i - 1 + di, jj = j - 1 + dj;
+      const bool in = ii >= 0 && ii < nnx && jj >= 0 && jj < nny;
+      const long long nid = in ? TOPO_IDX(ii + (long long)nnx * jj, nodes) : 0;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        T acc = fma(w, C[q0][p0][c], T(0));          // (j0, i0)
+        if (ox) acc = fma(w, C[q0][p1][c], acc);      // (j0, i1)
+        if (oy) {
+          acc = fma(w, C[q1][p0][c], acc);            // (j1, i0)
+          if (ox) acc = fma(w, C[q1][p1][c], acc);    // (j1, i1)
+        }
+        const long long id = 2 * nid + c;
+        const T zv = in ? ldg(z + id) : T(0);
+        V[dj][di][c] = (in && !fixed[id]) ? zv + acc : zv;
+      }
+    }
+  T acc[2] = {T(0), T(0)};
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (!ok[s]) continue;
+    const int dx = s & 1, dy = s >> 1;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      T t = T(0);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int bq = q >> 1, cq = q & 1;
+        t = fma(a[s][c * 8 + q], V[dy + loc_oy(bq)][dx + loc_ox(bq)][cq], t);
+      }
+      acc[c] += t;
+    }
+  }
+  const long long node = i + (long long)nnx * j;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const long long id = 2 * node + c;
+    if (!TOPO_IN(id, n)) continue;
+    y[id] = fixed[id] ? T(0) : node_out<2, T>(acc[c], V[1][1][c], ldg(b + id), invd[id], omega);
+  }
+}
+
+// One thread per node; blockIdx.z is the node's parity class (i & 1) + 2 (j & 1), so that every
+// block runs one specialisation of apply2_prolong_node.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_apply2_prolong(Dims d, const T* __restrict__ Ae,
+                                                             const T* __restrict__ z,
+                                                             const T* __restrict__ zc,
+                                                             const T* __restrict__ b,
+                                                             T* __restrict__ y,
+                                                             const T* __restrict__ invd, T omega,
+                                                             const uint8_t* __restrict__ fixed,
+                                                             const CgScalars* __restrict__ sc) {
+  pdl_prologue();
+  const int rhs = blockIdx.y;
+  if (sc && sc[rhs].done) return;
+  const int px = blockIdx.z & 1, py = blockIdx.z >> 1;
+  const int nnx = d.nx + 1, nny = d.ny + 1;
+  const int ncx = (nnx - px + 1) >> 1, ncy = (nny - py + 1) >> 1;  // nodes of the class
+  const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= (long long)ncx * ncy) return;
+  const int i = 2 * (int)(l % ncx) + px, j = 2 * (int)(l / ncx) + py;
+  const long long n = 2LL * nnx * nny;
+  const long long nc = 2LL * (d.nx / 2 + 1) * (d.ny / 2 + 1);
+  z += rhs * n;
+  b += rhs * n;
+  y += rhs * n;
+  zc += rhs * nc;
+  switch (blockIdx.z) {
+    case 0: apply2_prolong_node<T, 0, 0>(d, i, j, Ae, z, zc, b, y, invd, omega, fixed); break;
+    case 1: apply2_prolong_node<T, 1, 0>(d, i, j, Ae, z, zc, b, y, invd, omega, fixed); break;
+    case 2: apply2_prolong_node<T, 0, 1>(d, i, j, Ae, z, zc, b, y, invd, omega, fixed); break;
+    default: apply2_prolong_node<T, 1, 1>(d, i, j, Ae, z, zc, b, y, invd, omega, fixed);
+  }
+}
+
 // ---- Fused deep levels of the 2D V-cycle ----------------------------------------------------
 // The levels below a few thousand nodes cost a launch per smoothing sweep, residual, restriction
 // and prolongation while their work is a few microseconds of L2 traffic.  One cluster of
@@ -1771,6 +1909,26 @@ template cudaError_t launch_prolong_add<double>(const Dims&, const double*, doub
                                                 cudaStream_t, int);
 template cudaError_t launch_prolong_add<float>(const Dims&, const float*, float*, const uint8_t*,
                                                int, const CgScalars*, cudaStream_t, int);
+
+template <typename T>
+cudaError_t launch_apply2_prolong(const Dims& d, const T* Ae, const T* z, const T* zc, const T* b,
+                                  T* y, const T* invd, T omega, const uint8_t* fixed, int nrhs,
+                                  const CgScalars* sc, cudaStream_t st) {
+  if (d.dim != 2 || (d.nx & 1) || (d.ny & 1) || !Ae) return cudaErrorInvalidValue;
+  // (the largest parity class: the even nodes, (nx / 2 + 1) (ny / 2 + 1))
+  dim3 grid(blocks_for((long long)(d.nx / 2 + 1) * (d.ny / 2 + 1)), nrhs, 4);
+  topo::launch(k_apply2_prolong<T>, grid, kThreads, 0, st, d, Ae, z, zc, b, y, invd, omega, fixed,
+               sc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_apply2_prolong<double>(const Dims&, const double*, const double*,
+                                                   const double*, const double*, double*,
+                                                   const double*, double, const uint8_t*, int,
+                                                   const CgScalars*, cudaStream_t);
+template cudaError_t launch_apply2_prolong<float>(const Dims&, const float*, const float*,
+                                                  const float*, const float*, float*, const float*,
+                                                  float, const uint8_t*, int, const CgScalars*,
+                                                  cudaStream_t);
 
 template <typename T>
 cudaError_t launch_vcycle_tail(const TailArgs<T>& a, int nrhs, const CgScalars* sc,

@@ -607,10 +607,10 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
   // the matrix-free first coarse level (2D mixed): both fusions in its warp sweep
   const bool l1_fused = k == 1 && s->fuse_on && s->l1_free && s->q1_ok && !s->arrow &&
                         std::is_same<TV, float>::value;
-  // coarse 2D levels with stored element matrices: the first two sweeps as one kernel (mode 4).
-  // (Prolongation with the first post-sweep measured slower there: a node-parallel kernel forms
-  // P z_c once per element entry it reads, 32 times per node.)
-  // IP systems: the same, with the lambda row in the kernel (k_apply_arrow).
+  // coarse 2D levels with stored element matrices: the first two sweeps as one kernel (mode 4),
+  // and the prolongation with the first post-sweep (v = z + P z_c formed once per neighbour node
+  // from a 3 x 3 coarse patch, k_apply2_prolong).
+  // IP systems: the first two sweeps, with the lambda row in the kernel (k_apply_arrow).
   const bool coarse_fused = !fine && s->fuse_on && s->dim == 2 && !(k == 1 && s->l1_free) &&
                             Prec<TV>::Ae(lv) != nullptr;
   bool sweep_timed = false;  // profiling: the first smoothing kernel of the finest level
@@ -674,6 +674,13 @@ topo_status vcycle(topo_solver* s, int k, const TV* b, TV** result, const CgScal
     it0 = 1;
   } else if (l1_fused && nu2 >= 1) {
     TOPO_TRY(apply_level<TV>(s, k, 5, cur, b, oth, sc, zc));
+    std::swap(cur, oth);
+    it0 = 1;
+  } else if (coarse_fused && !s->arrow && nu2 >= 1 && s->coarse_prolong &&
+             lv.d.nodes() <= kApply2ProlongNodes) {
+    const TV omega = lv.omega_dev ? TV(1) : (TV)s->desc.omega;
+    TOPO_CUDA(launch_apply2_prolong<TV>(lv.d, Prec<TV>::Ae(lv), cur, zc, b, oth,
+                                        Prec<TV>::invd(lv), omega, lv.fixed, nrhs, sc, s->st));
     std::swap(cur, oth);
     it0 = 1;
   } else {
@@ -1246,6 +1253,10 @@ static topo_status create_impl(const topo_solver_desc* d, topo_solver* s, bool a
   {
     const char* nv = std::getenv("TOPO_Q1_NARROW");
     s->q1_wide = !(nv && nv[0] == '1');
+  }
+  {  // TOPO_COARSE_PROLONG=0: separate prolongation and sweep kernels on the stored-matrix levels
+    const char* cp = std::getenv("TOPO_COARSE_PROLONG");
+    s->coarse_prolong = !(cp && cp[0] == '0');
   }
   s->hex_ok = (s->dim == 3) && !arrow && !d->generic_kernels && hex_coefficients(K0.data(), s->hex);
   s->hex_buffered = s->hex_ok && hex_buffered_env();

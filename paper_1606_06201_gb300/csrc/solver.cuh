@@ -93,6 +93,8 @@ struct topo_solver {
   int hex_sweep = 0;                      // 3D finest V-cycle operator: 0 node-parallel,
                                           // 1 tile dense (same bits as 0), 2 tile Walsh-Hadamard,
                                           // 3 tile dense on the tensor cores (3 x TF32)
+  bool coarse_prolong = true;             // 2D coarse levels with element matrices: prolongation
+                                          // and first post-sweep in one kernel
   int outer_df = 0;                       // outer operator in float-pair arithmetic (1) or FP64
   bool tail_ok = false;                   // the fused deep-level kernel can run on this device
   bool fuse_on = true;                    // fused V-cycle kernels in use (topo_set_vcycle_fusion)

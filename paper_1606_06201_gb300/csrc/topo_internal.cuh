@@ -409,6 +409,17 @@ cudaError_t launch_restrict(const Dims& fine, const T* rf, T* rc, const uint8_t*
 template <typename T>
 cudaError_t launch_prolong_add(const Dims& fine, const T* zc, T* zf, const uint8_t* fixed_f,
                                int nrhs, const CgScalars* sc, cudaStream_t st, int arrow = 0);
+// 2D level with stored element matrices Ae (no arrow): y = v + omega invd (b - A v) with
+// v = z + P zc (prolongation and correction, then the first post-smoothing sweep) in one launch,
+// with the bits of launch_prolong_add followed by launch_apply mode 2.
+// Levels at or below this many nodes take launch_apply2_prolong: on the 2048 x 1024 hierarchy
+// levels 3-5 gain 0.3-1.8 us each; on level 2 (132k nodes) the parity classes' strided accesses
+// made it 4 us slower than the two kernels.
+constexpr long long kApply2ProlongNodes = 65536;
+template <typename T>
+cudaError_t launch_apply2_prolong(const Dims& d, const T* Ae, const T* z, const T* zc, const T* b,
+                                  T* y, const T* invd, T omega, const uint8_t* fixed, int nrhs,
+                                  const CgScalars* sc, cudaStream_t st);
 cudaError_t launch_inv_diag(const Dims& d, const double* K0, const double* x, const double* Ae,
                             const uint8_t* fixed, double* invd, cudaStream_t st);
 // FP32 inverse diagonal of a coarse level from its FP32 element matrices.

@@ -9,8 +9,12 @@ D^{-1}), and the AOC compliance and lambda at every iteration within 1e-10 with 
 iterations within 1e-10 + 4 tau_lambda / lambda (the bisection's own resolution).  Mixed precision (FP32 V-cycle, FP64 recurrences): the final x
 and f^T u within 1e-6.
 
-The two oracle runs take a minute or two of CPU time; they run in two spawned CPU processes (the
-host's cores split between them) while the GPU runs its own part.
+The two oracle runs take a few minutes of CPU time; they run in two spawned CPU processes while the
+GPU runs its own part, each with single-threaded BLAS: the banded factorisation gains little from
+threads at this band (about 7% with eight), and it makes the factorisation independent of the
+host's core count.  (One run on a 16-core Arm host, eight BLAS threads per worker, gave an AOC
+compliance 6e-5 away from the GPU's at iteration 23, where x86 runs with 1, 4 and 8 threads agree
+with one another to 1e-12 and with the GPU to 1.3e-11.)
 """
 import numpy as np
 import pytest
@@ -32,7 +36,7 @@ def _rel(a, b):
 
 @pytest.fixture(scope="module")
 def oracle_c2():
-    pool, _ = oracle_runs.spawn_pool(2)
+    pool, _ = oracle_runs.spawn_pool(2, threads=1)
     ip_job = pool.apply_async(oracle_runs.ip_run, (NX, NY, VOLFRAC, IP_STEPS))
     oc_job = pool.apply_async(oracle_runs.aoc_run, (NX, NY, VOLFRAC, AOC_FEVAL, AOC_ITERS))
     pool.close()

@@ -301,6 +301,42 @@ def test_fused_deep_levels_give_identical_bits(precision, shape, nu, nrhs):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("shape,nu,nrhs,generic,omega_auto",
+                         [((256, 128, 0, 6), (2, 2), 1, False, False),
+                          ((96, 40, 0, 4), (1, 1), 2, False, False),
+                          ((128, 64, 0, 5), (2, 1), 3, True, False),
+                          ((64, 32, 0, 4), (0, 2), 1, False, True)])
+def test_coarse_prolongation_with_first_post_sweep_gives_identical_bits(
+        precision, shape, nu, nrhs, generic, omega_auto, monkeypatch):
+    """On the 2D levels with stored element matrices, the kernel that forms v = z + P z_c for the
+    3 x 3 neighbours of a node and sweeps on it gives the bits of the separate prolongation and
+    sweep kernels (TOPO_COARSE_PROLONG=0): V-cycle outputs and whole solves."""
+    torch = torch_cuda()
+    topo = topo_lib()
+    nx, ny, nz, levels = shape
+    fixed = W.clamp_xmin(nx, ny)
+    x = dev(torch, _x(nx, ny, 0, 39))
+    R = np.stack([W.random_vector(fixed.size, 80 + k, fixed) for k in range(nrhs)])
+    F = np.stack([W.normal_load(fixed, 90 + k) for k in range(nrhs)])
+    out = []
+    for sep in ("0", "1"):
+        monkeypatch.setenv("TOPO_COARSE_PROLONG", sep)
+        s = topo.Solver(nx, ny, fixed=fixed, levels=levels, precision=precision, nu1=nu[0],
+                        nu2=nu[1], nrhs=nrhs, max_iter=200, generic_kernels=generic,
+                        omega_auto=omega_auto)
+        s.set_density(x)
+        y = host(s.apply_vcycle(dev(torch, R if nrhs > 1 else R[0])))
+        u, info = s.solve(dev(torch, F if nrhs > 1 else F[0]), tol=1e-9,
+                          allow_not_converged=True)
+        out.append((y, host(u), info.iterations))
+        s.close()
+    monkeypatch.delenv("TOPO_COARSE_PROLONG")
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 def test_fused_levels_with_power_iteration_damping_give_identical_bits(precision):
     """Per-level damping from the power iteration (omega folded into the inverse diagonals):
     the fused kernels take each level's own damping, so fused and unfused V-cycles and solves
