@@ -528,27 +528,37 @@ constexpr double kNsTol = 1e-7;
 
 // Gauss-Jordan step k with pivot p maps a_kk -> 1/p, a_kj -> a_kj/p, a_ik -> -a_ik/p and
 // a_ij -> a_ij - a_ik a_kj / p (old values on the right); after n steps the array holds A^{-1}.
-// No pivoting: the pivots of an SPD matrix are its Schur-complement diagonals.  Thread (warp w,
-// lane l) keeps the 4 x 4 entries (w + 32a, l + 32b) in registers; the pivot row and column of
-// the next step are written to double-buffered shared arrays during a step, so one barrier per
-// step suffices.  Also clears info[0] and the Newton-Schulz flag.
-__global__ void __launch_bounds__(1024) k_gj32_start(int n, const double* __restrict__ A,
-                                                     double* __restrict__ X, int* info,
-                                                     int* ns_bad) {
+// No pivoting: the pivots of an SPD matrix are its Schur-complement diagonals.  512 threads: lane
+// tx and warp ty keep the EA x EB entries (ty + 16a, tx + 32b), EA = ceil(n / 16), EB = ceil(n / 32),
+// in registers.  A step is one multiply-add per entry (the general update), then the threads that
+// hold row k (one warp row) and column k (one lane) overwrite them with the old row times 1/p (the
+// old row is the staged pivot row) and -a_ik/p, and the holders of row and column k + 1 stage them
+// for the next step in double-buffered shared arrays: one barrier per step, registers indexed by
+// constants only.  (The per-entry branches or selects of the special cases, with 1024 or 256
+// threads, took 108-119 us for n = 90: about 415 dependent instructions per warp and step.)  Also
+// clears info[0] and the Newton-Schulz flag.
+constexpr int kGjLanes = 32, kGjRows = 16;
+
+template <int EA>
+__global__ void __launch_bounds__(kGjLanes * kGjRows) k_gj32_start(int n,
+                                                                   const double* __restrict__ A,
+                                                                   double* __restrict__ X,
+                                                                   int* info, int* ns_bad) {
+  constexpr int EB = (EA + 1) / 2;  // (n <= 16 EA gives ceil(n / 32) <= EB)
   pdl_prologue();
   __shared__ float Pb[2][kGjMaxN];  // pivot row (values before the step), by step parity
   __shared__ float Cb[2][kGjMaxN];  // pivot column (values before the step), by step parity
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int tx = threadIdx.x % kGjLanes, ty = threadIdx.x / kGjLanes;
   if (threadIdx.x == 0) {
     *info = 0;
     *ns_bad = 0;
   }
-  float r[4][4];
+  float r[EA][EB];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < EA; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int i = w + 32 * a, j = l + 32 * b;
+    for (int b = 0; b < EB; ++b) {
+      const int i = ty + kGjRows * a, j = tx + kGjLanes * b;
       const bool in = i < n && j < n;
       r[a][b] = in ? (float)A[(long long)i * n + j] : 0.0f;
       if (in && j == 0) Cb[0][i] = r[a][b];
@@ -557,54 +567,119 @@ __global__ void __launch_bounds__(1024) k_gj32_start(int n, const double* __rest
   __syncthreads();
   for (int k = 0; k < n; ++k) {
     const int cur = k & 1;
-    float* Pn = Pb[cur ^ 1];
-    float* Cn = Cb[cur ^ 1];
     const float rp = 1.0f / Pb[cur][k];
-    float pj[4], fi[4];
+    float pj[EB], fi[EA];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) pj[b] = (l + 32 * b < n) ? Pb[cur][l + 32 * b] : 0.0f;
+    for (int b = 0; b < EB; ++b)
+      pj[b] = (tx + kGjLanes * b < n) ? Pb[cur][tx + kGjLanes * b] : 0.0f;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) fi[a] = (w + 32 * a < n) ? Cb[cur][w + 32 * a] * rp : 0.0f;
+    for (int a = 0; a < EA; ++a)
+      fi[a] = (ty + kGjRows * a < n) ? Cb[cur][ty + kGjRows * a] * rp : 0.0f;
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < EA; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int i = w + 32 * a, j = l + 32 * b;
-        if (i < n && j < n) {
-          float v;
-          if (i == k) v = (j == k) ? rp : r[a][b] * rp;
-          else if (j == k) v = -fi[a];
-          else v = fmaf(-fi[a], pj[b], r[a][b]);
-          r[a][b] = v;
-          if (j == k + 1) Cn[i] = v;
-          if (i == k + 1) Pn[j] = v;
+      for (int b = 0; b < EB; ++b) r[a][b] = fmaf(-fi[a], pj[b], r[a][b]);
+    // (selects over every entry held, inside branches taken only by the holders: an indexed
+    // store of the same update would move the register array to local memory)
+    const int kb = k / kGjLanes, ka = k / kGjRows;
+    if (tx == k % kGjLanes) {  // column k: -a_ik / p
+#pragma unroll
+      for (int a = 0; a < EA; ++a)
+#pragma unroll
+        for (int b = 0; b < EB; ++b) r[a][b] = (b == kb) ? -fi[a] : r[a][b];
+    }
+    if (ty == k % kGjRows) {  // row k: a_kj / p, and 1 / p on the diagonal
+#pragma unroll
+      for (int a = 0; a < EA; ++a)
+#pragma unroll
+        for (int b = 0; b < EB; ++b) {
+          const float rowv = (tx + kGjLanes * b == k) ? rp : pj[b] * rp;
+          r[a][b] = (a == ka) ? rowv : r[a][b];
+        }
+    }
+    const int k1 = k + 1;  // stage row and column k + 1 for the next step
+    if (k1 < n) {
+      float* Pn = Pb[cur ^ 1];
+      float* Cn = Cb[cur ^ 1];
+      const int kb1 = k1 / kGjLanes, ka1 = k1 / kGjRows;
+      if (ty == k1 % kGjRows) {
+#pragma unroll
+        for (int b = 0; b < EB; ++b) {
+          float v = 0.0f;
+#pragma unroll
+          for (int a = 0; a < EA; ++a) v = (a == ka1) ? r[a][b] : v;
+          if (tx + kGjLanes * b < n) Pn[tx + kGjLanes * b] = v;
         }
       }
+      if (tx == k1 % kGjLanes) {
+#pragma unroll
+        for (int a = 0; a < EA; ++a) {
+          float v = 0.0f;
+#pragma unroll
+          for (int b = 0; b < EB; ++b) v = (b == kb1) ? r[a][b] : v;
+          if (ty + kGjRows * a < n) Cn[ty + kGjRows * a] = v;
+        }
+      }
+    }
     __syncthreads();
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < EA; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int i = w + 32 * a, j = l + 32 * b;
+    for (int b = 0; b < EB; ++b) {
+      const int i = ty + kGjRows * a, j = tx + kGjLanes * b;
       if (i < n && j < n) X[(long long)i * n + j] = (double)r[a][b];
     }
 }
 
-// C = alpha I + beta L R for n x n matrices: block i computes row i, thread j column j.  check:
-// set *bad if some |C_ij - delta_ij| > kNsTol or is not finite (C = 2I - A X gives I - A X).
-__global__ void __launch_bounds__(kGjMaxN) k_ns_gemm(int n, const double* __restrict__ L,
-                                                     const double* __restrict__ R,
-                                                     double* __restrict__ C, double alpha,
-                                                     double beta, int check, int* bad) {
+// C = alpha I + beta L R for n x n matrices: an 8 x 8 tile of C per block of 64 threads (about
+// 150 blocks for n = 90, so that the FP64 multiply-adds, 2 per clock on an SM, spread over the
+// GPU); the tile's rows of L and columns of R are staged in shared memory, and each entry sums
+// over k in increasing order from zero (the arithmetic of one dot product per entry; a form with
+// one block per row of C took 8.9 us per product for n = 90).  check: set *bad if some
+// |C_ij - delta_ij| > kNsTol or is not finite (C = 2I - A X gives I - A X).
+constexpr int kNsTile = 8;
+
+__global__ void __launch_bounds__(kNsTile * kNsTile) k_ns_gemm(int n, const double* __restrict__ L,
+                                                               const double* __restrict__ R,
+                                                               double* __restrict__ C,
+                                                               double alpha, double beta, int check,
+                                                               int* bad) {
   pdl_prologue();
-  __shared__ double Li[kGjMaxN];
-  const int i = blockIdx.x, j = threadIdx.x;
-  for (int k = j; k < n; k += blockDim.x) Li[k] = L[(long long)i * n + k];
+  __shared__ double Ls[kNsTile][kGjMaxN];  // rows i0 .. i0 + 7 of L
+  __shared__ double Rs[kGjMaxN][kNsTile];  // columns j0 .. j0 + 7 of R
+  const int i0 = blockIdx.y * kNsTile, j0 = blockIdx.x * kNsTile;
+  // every load of the tile in flight at once, then the stores (one L2 round trip)
+  constexpr int kPer = kNsTile * kGjMaxN / (kNsTile * kNsTile);
+  double lv[kPer], rv[kPer];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int q = threadIdx.x + u * kNsTile * kNsTile;
+    lv[u] = rv[u] = 0.0;
+    if (q < kNsTile * n) {
+      const int a = q / n, k = q - a * n;  // (row-major reads of L's rows)
+      if (i0 + a < n) lv[u] = L[(long long)(i0 + a) * n + k];
+      const int kk = q / kNsTile, b = q - kk * kNsTile;  // (R's rows, 8 columns each)
+      if (j0 + b < n) rv[u] = R[(long long)kk * n + j0 + b];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int q = threadIdx.x + u * kNsTile * kNsTile;
+    if (q < kNsTile * n) {
+      const int a = q / n, k = q - a * n;
+      Ls[a][k] = lv[u];
+      const int kk = q / kNsTile, b = q - kk * kNsTile;
+      Rs[kk][b] = rv[u];
+    }
+  }
   __syncthreads();
-  if (j >= n) return;
+  const int ti = threadIdx.x / kNsTile, tj = threadIdx.x % kNsTile;
+  const int i = i0 + ti, j = j0 + tj;
+  if (i >= n || j >= n) return;
   double acc = 0.0;
-  for (int k = 0; k < n; ++k) acc = fma(Li[k], R[(long long)k * n + j], acc);
+#pragma unroll 8
+  for (int k = 0; k < n; ++k) acc = fma(Ls[ti][k], Rs[k][tj], acc);
   const double c = fma(beta, acc, i == j ? alpha : 0.0);
   C[(long long)i * n + j] = c;
   if (check && !(fabs(c - (i == j ? 1.0 : 0.0)) <= kNsTol)) atomicOr(bad, 1);
@@ -974,17 +1049,35 @@ cudaError_t launch_cholesky_inverse(int n, double* A, double* Ainv, int* info, c
     static_assert(kNsSteps % 2 == 0, "Newton-Schulz ping-pong ends in Ainv");
     double* R = scratch;
     double* T = scratch + (size_t)n * n;
-    topo::launch(k_gj32_start, 1, 1024, 0, st, n, (const double*)A, Ainv, info, ns_bad);
+    switch ((n + kGjRows - 1) / kGjRows) {
+#define TOPO_GJ_CASE(E)                                                                            \
+  case E:                                                                                          \
+    topo::launch(k_gj32_start<E>, 1, kGjLanes * kGjRows, 0, st, n, (const double*)A, Ainv, info,  \
+                 ns_bad);                                                                          \
+    break;
+      TOPO_GJ_CASE(1)
+      TOPO_GJ_CASE(2)
+      TOPO_GJ_CASE(3)
+      TOPO_GJ_CASE(4)
+      TOPO_GJ_CASE(5)
+      TOPO_GJ_CASE(6)
+      TOPO_GJ_CASE(7)
+      default:
+        topo::launch(k_gj32_start<8>, 1, kGjLanes * kGjRows, 0, st, n, (const double*)A, Ainv,
+                     info, ns_bad);
+#undef TOPO_GJ_CASE
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     double* X = Ainv;
     double* Xn = T;
     for (int it = 0; it < kNsSteps; ++it) {
       const int last = (it == kNsSteps - 1) ? 1 : 0;
-      topo::launch(k_ns_gemm, n, kGjMaxN, 0, st, n, (const double*)A, (const double*)X, R, 2.0,
-                   -1.0, last, ns_bad);
-      topo::launch(k_ns_gemm, n, kGjMaxN, 0, st, n, (const double*)X, (const double*)R, Xn, 0.0,
-                   1.0, 0, ns_bad);
+      const dim3 tiles((n + kNsTile - 1) / kNsTile, (n + kNsTile - 1) / kNsTile);
+      topo::launch(k_ns_gemm, tiles, kNsTile * kNsTile, 0, st, n, (const double*)A,
+                   (const double*)X, R, 2.0, -1.0, last, ns_bad);
+      topo::launch(k_ns_gemm, tiles, kNsTile * kNsTile, 0, st, n, (const double*)X,
+                   (const double*)R, Xn, 0.0, 1.0, 0, ns_bad);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
       double* t = X;
