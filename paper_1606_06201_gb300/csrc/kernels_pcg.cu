@@ -264,12 +264,20 @@ __global__ void __launch_bounds__(kThreads, 4) k_cg_update(long long n, double* 
     };
     const int npi = (int)np, nti = (int)nt;  // (fewer than 2^31 entries)
     int j = (int)t0;
-    for (; j + nti < npi; j += 2 * nti) {  // both pairs' loads before either store
-      const double2 qa = q2[j], ra = r2[j], qb = q2[j + nti], rb = r2[j + nti];
-      put(j, make_double2(fma(alpha, qa.x, ra.x), fma(alpha, qa.y, ra.y)));
-      put(j + nti, make_double2(fma(alpha, qb.x, rb.x), fma(alpha, qb.y, rb.y)));
+    // four pairs' loads before any store (the fixed reduction grid keeps half the warps
+    // resident, so each thread keeps more bytes in flight)
+    for (; j + 3 * nti < npi; j += 4 * nti) {
+      double2 qv[4], rv4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        qv[u] = q2[j + u * nti];
+        rv4[u] = r2[j + u * nti];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        put(j + u * nti, make_double2(fma(alpha, qv[u].x, rv4[u].x), fma(alpha, qv[u].y, rv4[u].y)));
     }
-    if (j < npi) {
+    for (; j < npi; j += nti) {
       const double2 qa = q2[j], ra = r2[j];
       put(j, make_double2(fma(alpha, qa.x, ra.x), fma(alpha, qa.y, ra.y)));
     }
