@@ -58,11 +58,11 @@ FP64_PEAK_TOPS, FP32_PEAK_TOPS = derived_peaks(SM_COUNT_DEFAULT, SM_MHZ_DEFAULT)
 # butterflies) + 6 node-assembly adds + 2 FMA of the fused p^T q per node.
 OPS_PER_ELEM, OPS_PER_NODE = 37.0, 8.0
 # FP32 operations of the same operator in float pairs: per element 29 pair additions (8 FP32
-# operations each: TwoSum and the low parts, no renormalisation) and 12 pair products (7: product,
-# FMA error term, two cross FMAs, FastTwoSum), plus the 2 pair additions of the carried node sums;
-# per output node 4 pair additions of the node sums, 2 products + 2 renormalised additions (11) of
-# p^T q, and 2 FP32 multiplies of each of the two input splits.
-DF_OPS_PER_ELEM = 29 * 8 + 12 * 7 + 2 * 8
+# operations each: TwoSum and the low parts, no renormalisation) and 12 pair products (4: product,
+# FMA error term, two cross FMAs, no renormalisation), plus the 2 pair additions of the carried
+# node sums; per output node 4 pair additions of the node sums, 2 renormalised products (7) + 2
+# renormalised additions (11) of p^T q, and 2 FP32 multiplies of each of the two input splits.
+DF_OPS_PER_ELEM = 29 * 8 + 12 * 4 + 2 * 8
 DF_OPS_PER_NODE = 4 * 8 + 2 * 7 + 2 * 11 + 4
 # DRAM bytes of one launch of the FP64 operator on this workload from an ncu capture; None until
 # the operator as built now (37-operation element product) has been captured.

@@ -563,11 +563,11 @@ __device__ __forceinline__ void q1_element_df(const Q1KD& k, f2 xe, const f2 u[4
   const f2 t1 = df_add_nr(v[0], v[2]), t2 = df_add_nr(v[1], v[3]);
   const f2 Xp = df_add_nr(e2, e1), Yp = df_sub_nr(e1, e2), Hp = df_sub_nr(t1, t2);
   const f2 G = df_add_nr(Y, Xp);
-  const f2 gX = df_mul(xe, df_add_nr(df_mul(k.c11, X), df_mul(k.c12, Yp)));
-  const f2 gYp = df_mul(xe, df_add_nr(df_mul(k.c12, X), df_mul(k.c22, Yp)));
-  const f2 gG = df_mul(xe, df_mul(k.c33, G));
-  const f2 gH = df_mul(xe, df_mul(k.cH, H));
-  const f2 gHp = df_mul(xe, df_mul(k.cHp, Hp));
+  const f2 gX = df_mul_nr(xe, df_add_nr(df_mul_nr(k.c11, X), df_mul_nr(k.c12, Yp)));
+  const f2 gYp = df_mul_nr(xe, df_add_nr(df_mul_nr(k.c12, X), df_mul_nr(k.c22, Yp)));
+  const f2 gG = df_mul_nr(xe, df_mul_nr(k.c33, G));
+  const f2 gH = df_mul_nr(xe, df_mul_nr(k.cH, H));
+  const f2 gHp = df_mul_nr(xe, df_mul_nr(k.cHp, Hp));
   const f2 A = df_add_nr(gX, gG), B = df_sub_nr(gX, gG);
   ru[0] = df_sub_nr(gH, A);
   ru[1] = df_sub_nr(B, gH);
