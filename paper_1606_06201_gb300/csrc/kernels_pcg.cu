@@ -281,9 +281,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_cg_update(long long n, double* 
       const double2 qa = q2[j], ra = r2[j];
       put(j, make_double2(fma(alpha, qa.x, ra.x), fma(alpha, qa.y, ra.y)));
     }
-  } else {
-    for (long long i = t0; i < n; i += nt) {
-      const double ri = fma(alpha, q[i], r[i]);
+  } else {  // (odd n, e.g. 3D grids, or unaligned vectors)
+    auto put1 = [&](long long i, double ri) {
       r[i] = ri;
       if (rv) {
         const TV vi = tv_from_double<TV>(ri);
@@ -292,12 +291,25 @@ __global__ void __launch_bounds__(kThreads, 4) k_cg_update(long long n, double* 
           if (f32norm) {
             const float ui = vi * sinv;
             partf = fmaf(ui, ui, partf);
-            continue;
+            return;
           }
         }
       }
       part[0] = fma(ri, ri, part[0]);
+    };
+    long long i = t0;
+    // three entries' loads before any store, the sums in the same order as one at a time
+    for (; i + 2 * nt < n; i += 3 * nt) {
+      double qv[3], r0[3];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        qv[u] = q[i + u * nt];
+        r0[u] = r[i + u * nt];
+      }
+#pragma unroll
+      for (int u = 0; u < 3; ++u) put1(i + u * nt, fma(alpha, qv[u], r0[u]));
     }
+    for (; i < n; i += nt) put1(i, fma(alpha, q[i], r[i]));
   }
   if (f32norm) part[0] = (double)partf;
   double tot[1];
