@@ -554,12 +554,17 @@ def main():
         print("only=%s ms_per_step=%.3f iterations=%d launches=%d" % (
             args.only, r["ms"] / args.steps, r["iters"], r["launches"]), flush=True)
         return 0
-    # warm-up + timed steps: mixed (headline, with live operator timing), FP64, end-to-end
+    # warm-up + timed steps: mixed (headline), FP64, end-to-end, then the outer operators' live
+    # launch times in runs of their own
     with ClockSampler(dev.index) as clk:
-        # headline: event pairs around the outer operator only (one pair adds ~nothing)
-        mixed = run(topo.MIXED, args.steps, args.warmup, profile_mask=1)
-        fp64 = run(topo.FP64, args.steps, args.warmup, profile_mask=1)
+        # headline and FP64 without event nodes: an event pair around the outer operator in every
+        # CG iteration made the 2048 x 1024 mixed step 4.2% longer (4.72 against 4.53 ms)
+        mixed = run(topo.MIXED, args.steps, args.warmup)
+        fp64 = run(topo.FP64, args.steps, args.warmup)
         e2e = run(topo.MIXED, args.steps, args.warmup, host_io=True)
+        # the same solves with event pairs around the outer operator (its live launch time)
+        mixed_oprun = run(topo.MIXED, max(1, min(args.steps, 10)), args.warmup, profile_mask=1)
+        fp64_oprun = run(topo.FP64, max(1, min(args.steps, 5)), args.warmup, profile_mask=1)
         # separate run with every kind profiled, for the per-kernel and per-part times (its own
         # step time is longer by the extra event nodes and is not reported)
         kinds_run = run(topo.MIXED, max(1, min(args.steps, 5)), 3,
@@ -580,7 +585,7 @@ def main():
     if rank == 0:
         m, n = NX * NY, cfg["f"].size
         nodes = (NX + 1) * (NY + 1)
-        op_ms, op_cnt = mixed["prof"]
+        op_ms, op_cnt = mixed_oprun["prof"]
         op_avg_ms = op_ms / op_cnt if op_cnt else float("nan")
         # the method's bytes of one K(x) p (Sec. 8(d): p and q at 16 B per node each, x at 8 B per
         # element as a float pair, the fixed-DOF mask at 1 B per DOF)
@@ -617,8 +622,11 @@ def main():
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "bytes_model": "8 B per element (x) + 16 B per DOF (p, q) + 1 B per DOF (mask)",
                 "avg_launch_ms": op_avg_ms, "launches_timed": op_cnt,
+                "launch_timing": "CUDA event pairs around every launch on the solver's stream, in "
+                                 "a run of the same solve separate from the headline's timed "
+                                 "region (the event nodes lengthen the step by about 4%)",
                 "issue_view": issue}
-        f_ms, f_cnt = fp64["prof"]
+        f_ms, f_cnt = fp64_oprun["prof"]
         fp64_op = None
         if f_cnt:
             f_avg = f_ms / f_cnt
