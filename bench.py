@@ -96,6 +96,17 @@ def _dist():
     return ws, rank
 
 
+def max_over_ranks(v, ws, device):
+    """The largest of every rank's v (a time: the job ends with its slowest replica); v itself on
+    one rank.  device: where the process group's backend reduces (cuda for NCCL, cpu for gloo)."""
+    if ws == 1:
+        return v
+    import torch
+    t = torch.tensor([float(v)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def oracle_mgcg_sample(nx, ny, levels, seconds=None, reps=1):
     """Time the CPU oracle's MGCG (scipy sparse, Algorithm PCG + Algorithm MG) on the same recipe."""
     from oracle import fe, mg
@@ -571,11 +582,7 @@ def main():
                         profile_mask=(1 << len(topo.Solver.PROFILE_KINDS)) - 1)
 
     def gather_max(v):
-        if ws == 1:
-            return v
-        t = torch.tensor([v], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(v, ws, dev)
 
     ms_mixed = gather_max(mixed["ms"])
     ms_fp64 = gather_max(fp64["ms"])
